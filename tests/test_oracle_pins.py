@@ -1,0 +1,391 @@
+"""Pins for the CPU oracle: each check compares it with something other than itself.
+
+- Philox4x32-10 against published known-answer vectors (tests/golden).
+- The own log against the C library's log (<= 2 ulp) and E[-log xi] = 1.
+- Marsaglia directions: unit length, zero mean, E[w^2] = 1/3.
+- Hierarchical find_cell (Alg. 7, both tracker modes) against brute force over
+  every leaf instance evaluated in the global frame.
+- Segment sums along straight rays against closed-form chords (cylinder by
+  impact parameter, box and hex prism by the slab method).
+- Cauchy's mean-chord law 4V/S for cosine-law rays, whole body and per cell.
+- Track-length volume estimates in a reflecting box converging to pi r^2 h.
+- Collision count per history ~ Geometric(p_a); total path ~ Exp(p_a sigma).
+- rect-tracker mode vs CSG (pseudo-array) mode: identical histories.
+- Analytic transmission gradient against central finite differences.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2406_13849_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _geom(desc, mode=O.MODE_RECT):
+    return O.Geometry(I.to_json(desc), mode)
+
+
+# ---------------------------------------------------------------------------
+# random numbers
+# ---------------------------------------------------------------------------
+
+def test_philox_known_answers():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        out = O.philox4x32_10(v[0:4], v[4:6])
+        assert [int(x) for x in out] == v[6:10]
+
+
+def test_uniform_range_and_moments():
+    xs = np.array([O.uniform2(i, 0, 2, 0, 1, 0) for i in range(20000)]).ravel()
+    assert xs.min() > 0.0 and xs.max() <= 1.0
+    assert abs(xs.mean() - 0.5) < 5 * math.sqrt(1 / 12 / len(xs))
+    # the resolution is 2^-53: every value is an integer multiple of it
+    assert np.all(np.floor(xs * 2.0**53) == xs * 2.0**53)
+
+
+def test_log_within_two_ulp():
+    rng = np.random.default_rng(0)
+    xs = np.concatenate([rng.uniform(0, 1, 20000)[1:], 2.0 ** -rng.uniform(0, 53, 20000),
+                         rng.uniform(0.5, 2.0, 20000), [1.0, 0.5, 2.0, 2.0**-53, 1 - 2.0**-53]])
+    worst = 0.0
+    for x in xs:
+        a, b = O.own_log(x), math.log(x)
+        if a != b:
+            worst = max(worst, abs(a - b) / np.spacing(abs(b)))
+    assert worst <= 2.0
+    assert O.own_log(1.0) == 0.0
+
+
+def test_log_split_constant():
+    from decimal import Decimal, getcontext
+    from fractions import Fraction
+    getcontext().prec = 50
+    ln2 = Fraction(Decimal(2).ln())
+    hi = float.fromhex("0x1.62e42fefp-1")
+    lo = float.fromhex("0x1.473de6af278edp-34")
+    assert abs(float(ln2 - Fraction(hi) - Fraction(lo))) <= 0.5 * float(np.spacing(lo))
+    # exact -log of every xi = 2^-k, a case the series does not touch (m = 1)
+    for k in range(1, 54):
+        assert abs(-O.own_log(2.0**-k) - k * math.log(2.0)) <= 2 * np.spacing(k * math.log(2.0))
+
+
+def test_exponential_mean():
+    xi = np.array([O.uniform2(i, 0, 2, 0, 3, 0)[1] for i in range(40000)])
+    tau = np.array([-O.own_log(x) for x in xi])
+    assert abs(tau.mean() - 1.0) < 5 / math.sqrt(len(tau))
+    assert abs(tau.var() - 1.0) < 0.05
+
+
+def test_isotropic_directions():
+    d = np.array([O.isotropic(i, 1, 7, 0)[0] for i in range(30000)])
+    assert np.max(np.abs(np.linalg.norm(d, axis=1) - 1.0)) < 1e-15
+    n = len(d)
+    assert np.all(np.abs(d.mean(0)) < 5 * math.sqrt(1 / 3 / n))
+    assert abs((d[:, 2] ** 2).mean() - 1 / 3) < 5 * math.sqrt(4 / 45 / n)
+    assert abs((d[:, 0] * d[:, 1]).mean()) < 5 * math.sqrt(1 / 15 / n)
+
+
+# ---------------------------------------------------------------------------
+# find_cell against brute force over every leaf instance
+# ---------------------------------------------------------------------------
+
+def _points(desc, n, seed):
+    lo = np.array(desc["source_box"][:3])
+    hi = np.array(desc["source_box"][3:])
+    rng = np.random.default_rng(seed)
+    return lo + rng.uniform(0, 1, (n, 3)) * (hi - lo)
+
+
+@pytest.mark.parametrize("name,desc,modes", [
+    ("c1", I.config1(), (O.MODE_RECT, O.MODE_CSG)),
+    ("small_core", I.small_core(), (O.MODE_RECT, O.MODE_CSG)),
+    ("small_hex_core", I.small_hex_core(), (O.MODE_CSG,)),
+    ("hex_rot", I.small_hex(rings=3, rot30=True), (O.MODE_CSG,)),
+    ("tiny5", I.random_tiny(5), (O.MODE_RECT, O.MODE_CSG)),
+    ("tiny11", I.random_tiny(11), (O.MODE_RECT, O.MODE_CSG)),
+])
+def test_find_cell_matches_brute_force(name, desc, modes):
+    pts = _points(desc, 3000, 11)
+    for mode in modes:
+        g = _geom(desc, mode)
+        hier = g.find_cell(pts)
+        brute, count, near, nleaf = g.find_cell_brute(pts)
+        assert nleaf == g.n_inst
+        far = near > 1e-9
+        assert far.mean() > 0.99
+        # away from surfaces exactly one leaf instance holds the point
+        assert np.all(count[far & (brute >= 0)] == 1)
+        assert np.array_equal(hier[far], brute[far]), name
+
+
+def test_instance_counts():
+    assert _geom(I.config1()).n_inst == 867
+    assert _geom(I.config2()).n_inst == 191_929
+    assert _geom(I.config3(), O.MODE_CSG).n_inst == 27_686
+
+
+# ---------------------------------------------------------------------------
+# chords
+# ---------------------------------------------------------------------------
+
+def test_cylinder_chord_by_impact_parameter():
+    R, z0, z1 = 0.41, 0.0, 10.0
+    g = _geom(I.bare_cylinder(R, z0, z1), O.MODE_CSG)
+    rays = I.cylinder_rays(4000, R, z0, z1, seed=3)
+    res = g.transmission(rays.packed(), [0.0], grad=False)
+    o, d = rays.origin, rays.direction
+    sxy = np.hypot(d[:, 0], d[:, 1])
+    b = np.abs(o[:, 0] * d[:, 1] - o[:, 1] * d[:, 0]) / sxy   # impact parameter
+    s0 = (o[:, 0] * d[:, 0] + o[:, 1] * d[:, 1]) / sxy       # start along the projected line
+    # remaining half-chord beyond the closest approach, from the (inset) start point
+    chord = (np.sqrt(R * R - b * b) - s0) / sxy
+    # keep rays that enter and leave through the lateral face
+    lateral = np.abs(np.hypot(o[:, 0], o[:, 1]) - R) < 1e-6
+    zend = o[:, 2] + chord * d[:, 2]
+    ok = lateral & (zend > z0 + 1e-6) & (zend < z1 - 1e-6)
+    assert ok.sum() > 500
+    tot = res["lens"].sum(1)
+    assert np.all(res["status"][ok] == O.P_ESCAPED)
+    assert np.max(np.abs(tot[ok] - chord[ok]) / chord[ok]) < 1e-9
+
+
+def _slab_exit(o, d, lo, hi):
+    t = np.full(len(o), np.inf)
+    for k in range(3):
+        with np.errstate(divide="ignore", invalid="ignore"):
+            tk = np.where(d[:, k] > 0, (hi[k] - o[:, k]) / d[:, k],
+                          np.where(d[:, k] < 0, (lo[k] - o[:, k]) / d[:, k], np.inf))
+        t = np.minimum(t, tk)
+    return t
+
+
+@pytest.mark.parametrize("mode", [O.MODE_RECT, O.MODE_CSG])
+def test_box_chord_through_lattice(mode):
+    desc = I.config1(sigma=(0.0, 0.0, 0.0), bc="vacuum")
+    g = _geom(desc, mode)
+    lo, hi = np.array(desc["source_box"][:3]), np.array(desc["source_box"][3:])
+    rays = I.box_rays(2000, lo, hi, seed=4)
+    res = g.transmission(rays.packed(), [0, 0, 0], grad=False)
+    ref = _slab_exit(rays.origin, rays.direction, lo, hi)
+    assert np.all(res["status"] == O.P_ESCAPED)
+    assert np.max(np.abs(res["lens"].sum(1) - ref) / ref) < 1e-10
+
+
+def test_hex_prism_chord():
+    # a single hex cell (rings 0) is the intersection of 3 slabs and a z slab
+    pitch, h = 2.0, 4.0
+    desc = I.small_hex(rings=0, pitch=pitch, r_pin=0.3, height=h, sigma=(0.0, 0.0))
+    g = _geom(desc, O.MODE_CSG)
+    rng = np.random.default_rng(8)
+    n = 3000
+    apo = pitch / 2
+    o = np.stack([rng.uniform(-0.5, 0.5, n), rng.uniform(-0.5, 0.5, n), rng.uniform(0.5, 3.5, n)], 1)
+    d = rng.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    res = g.transmission(np.concatenate([o, d], 1), [0.0, 0.0], grad=False)
+    t = np.full(n, np.inf)
+    for ang in (0.0, 60.0, 120.0):
+        nv = np.array([math.cos(math.radians(ang)), math.sin(math.radians(ang)), 0.0])
+        on, dn = o @ nv, d @ nv
+        with np.errstate(divide="ignore"):
+            t = np.minimum(t, np.where(dn > 0, (apo - on) / dn, np.where(dn < 0, (-apo - on) / dn, np.inf)))
+    t = np.minimum(t, np.where(d[:, 2] > 0, (h - o[:, 2]) / d[:, 2], -o[:, 2] / d[:, 2]))
+    assert np.max(np.abs(res["lens"].sum(1) - t) / t) < 1e-9
+
+
+# ---------------------------------------------------------------------------
+# Cauchy mean chord and track-length volumes
+# ---------------------------------------------------------------------------
+
+def test_cauchy_cylinder():
+    R, H = 0.41, 3.0
+    g = _geom(I.bare_cylinder(R, 0.0, H), O.MODE_CSG)
+    rays = I.cylinder_rays(60000, R, 0.0, H, seed=12)
+    tot = g.transmission(rays.packed(), [0.0], grad=False)["lens"].sum(1)
+    expect = 2 * R * H / (H + R)
+    assert abs(tot.mean() - expect) < 5 * tot.std() / math.sqrt(len(tot))
+
+
+@pytest.mark.parametrize("mode", [O.MODE_RECT, O.MODE_CSG])
+def test_cauchy_box_per_cell(mode):
+    n, p, h = 3, 1.26, 4.0
+    desc = I.config1(sigma=(0.0, 0.0, 0.0), n=n, height=h, bc="vacuum")
+    g = _geom(desc, mode)
+    lo, hi = np.array(desc["source_box"][:3]), np.array(desc["source_box"][3:])
+    a, b, c = hi - lo
+    rays = I.box_rays(40000, lo, hi, seed=13)
+    lens = g.transmission(rays.packed(), [0, 0, 0], grad=False)["lens"]
+    S = 2 * (a * b + b * c + c * a)
+    tot = lens.sum(1)
+    assert abs(tot.mean() - 4 * a * b * c / S) < 5 * tot.std() / math.sqrt(len(tot))
+    vf = n * n * math.pi * 0.41**2 * h
+    vc = n * n * math.pi * (0.475**2 - 0.41**2) * h
+    for m, v in ((0, vf), (1, vc)):
+        assert abs(lens[:, m].mean() - 4 * v / S) < 5 * lens[:, m].std() / math.sqrt(len(tot))
+
+
+@pytest.mark.parametrize("mode", [O.MODE_RECT, O.MODE_CSG])
+def test_track_length_volumes(mode):
+    # sigma = 0, reflecting walls: uniform isotropic phase space stays so, and
+    # V_cell = V_box * tally_cell / (N L) for histories cut at path length L.
+    n, h = 17, 100.0
+    desc = I.config1(sigma=(0.0, 0.0, 0.0))
+    g = _geom(desc, mode)
+    L, N, B = 300.0, 400, 6
+    vbox = (n * 1.26) ** 2 * h
+    est = []
+    for b in range(B):
+        r = g.run(N, seed=21, p_absorb=0.3, first_id=b * N, max_path=L, records=False)
+        assert r["counters"][O.K_CUTOFF] == N
+        t = r["tally"].astype(np.float64).reshape(n * n, 3).sum(0) / 2.0**32
+        est.append(vbox * t / (N * L))
+    est = np.array(est)
+    m, s = est.mean(0), est.std(0, ddof=1) / math.sqrt(B)
+    exact = np.array([math.pi * 0.41**2 * h, math.pi * (0.475**2 - 0.41**2) * h,
+                      1.26**2 * h - math.pi * 0.475**2 * h]) * n * n
+    assert np.all(np.abs(m - exact) < 5 * s + 1e-3 * exact)
+    assert abs(m.sum() - vbox) < 1e-6 * vbox
+
+
+# ---------------------------------------------------------------------------
+# collision physics
+# ---------------------------------------------------------------------------
+
+def test_collision_count_geometric_and_path_exponential():
+    from scipy import stats
+    sig, pa = 0.5, 0.3
+    g = _geom(I.config1(sigma=(sig, sig, sig)))
+    ncoll, path = [], []
+    for pid in range(6000):
+        inst, ln, kind, st = g.trace(pid, seed=5, p_absorb=pa)
+        assert st == O.P_ABSORBED
+        ncoll.append(int((kind == 1).sum()))
+        path.append(ln.sum())
+    ncoll = np.array(ncoll)
+    kmax = 12
+    obs = np.array([(ncoll == k).sum() for k in range(1, kmax)] + [(ncoll >= kmax).sum()])
+    pk = np.array([(1 - pa) ** (k - 1) * pa for k in range(1, kmax)] + [(1 - pa) ** (kmax - 1)])
+    chi2 = ((obs - pk * len(ncoll)) ** 2 / (pk * len(ncoll))).sum()
+    assert stats.chi2.sf(chi2, kmax - 1) > 1e-4
+    # a geometric sum of Exp(sigma) free paths is Exp(p_a sigma)
+    assert stats.kstest(np.array(path), "expon", args=(0, 1 / (pa * sig))).pvalue > 1e-4
+
+
+def test_rect_and_csg_modes_identical():
+    for desc in (I.config1(), I.small_core(), I.random_tiny(3)):
+        ra = _geom(desc, O.MODE_RECT).run(1500, 1, 0.3)
+        rb = _geom(desc, O.MODE_CSG).run(1500, 1, 0.3)
+        assert np.array_equal(ra["hash"], rb["hash"])
+        assert np.array_equal(ra["tally"], rb["tally"])
+        assert np.array_equal(ra["counters"], rb["counters"])
+
+
+def test_thread_count_invariance():
+    g = _geom(I.small_core())
+    a = g.run(3000, 2, 0.25, threads=1)
+    b = g.run(3000, 2, 0.25, threads=4)
+    for k in ("tally", "counters", "hash", "nseg", "status"):
+        assert np.array_equal(a[k], b[k])
+
+
+def test_sharding_sums_to_whole():
+    g = _geom(I.config1())
+    whole = g.run(2000, 9, 0.3, records=False)
+    parts = [g.run(500, 9, 0.3, first_id=500 * k, records=False) for k in range(4)]
+    assert np.array_equal(sum(p["tally"] for p in parts), whole["tally"])
+    assert np.array_equal(sum(p["counters"] for p in parts), whole["counters"])
+
+
+def test_source_in_box_and_root():
+    desc = I.config2()
+    g = _geom(desc)
+    src, st = g.source(5000, 1)
+    assert np.all(st == 0)
+    r = np.hypot(src[:, 0], src[:, 1])
+    assert np.all(r < 170.0) and np.all((src[:, 2] >= 0) & (src[:, 2] < 366.0))
+    assert np.max(np.abs(np.linalg.norm(src[:, 3:6], axis=1) - 1)) < 1e-15
+    assert np.all(src[:, 6] >= 0)
+
+
+def test_max_segments_and_escape_status():
+    g = _geom(I.config1())
+    r = g.run(50, 1, 0.0, max_segments=10)
+    assert np.all(r["status"] == O.P_MAXSEG) and np.all(r["nseg"] == 10)
+    v = _geom(I.single_pin(bc="vacuum", sigma=(0.01, 0.01, 0.01))).run(500, 1, 0.3)
+    assert (v["status"] == O.P_ESCAPED).mean() > 0.9
+
+
+def test_bad_descriptions_rejected():
+    d = I.config1()
+    d["universes"][1]["fill"] = [0] * 5
+    with pytest.raises(ValueError):
+        _geom(d)
+    d = I.config1()
+    d["surfaces"][0]["bc"] = "reflect"
+    with pytest.raises(ValueError):
+        _geom(d)
+    with pytest.raises(ValueError):
+        O.Geometry("{not json", O.MODE_RECT)
+    with pytest.raises(ValueError):
+        _geom(I.config3(), O.MODE_RECT)   # no rect tracker for hex arrays
+
+
+# ---------------------------------------------------------------------------
+# transmission gradient
+# ---------------------------------------------------------------------------
+
+def test_transmission_sigma_gradient_exact():
+    desc = I.small_core(height=20.0)
+    g = _geom(desc)
+    rays = I.boundary_rays(300, r_outer=desc["surfaces"][9]["coef"][2], height=20.0, seed=2).packed()
+    sigma = np.array(desc["sigma"])
+    res = g.transmission(rays, sigma)
+    assert np.allclose(res["dT"][:, :4], -res["lens"] * res["T"][:, None], rtol=0, atol=0)
+    assert np.allclose(res["T"], np.exp(-(res["lens"] * sigma).sum(1)), rtol=1e-15)
+
+
+def test_transmission_geometry_gradient_vs_fd():
+    base = dict(n_core=3, n_assm=5, height=20.0)
+    r_out = 0.5 * 3 * 5 * 1.26 * 1.2
+    rays = I.boundary_rays(400, r_outer=r_out, height=20.0, seed=4).packed()
+    sigma = np.array([0.9, 0.4, 0.2, 0.6])
+    h = 1e-6
+    params = dict(r_fuel=0.41, r_clad=0.475, r_guide=0.56, pitch=1.26)
+
+    def run(**kw):
+        p = dict(params, **kw)
+        desc = I.small_core(**base, r_outer=r_out, sigma=sigma, **p)
+        return _geom(desc).transmission(rays, sigma, pitch=p["pitch"])
+
+    ref = run()
+    names = ["r_fuel", "r_clad", "r_guide", "pitch"]
+
+    def fd_err(j, nm, step):
+        hi_ = run(**{nm: params[nm] + step})
+        lo_ = run(**{nm: params[nm] - step})
+        same = (hi_["hash"] == ref["hash"]) & (lo_["hash"] == ref["hash"])
+        fd = (hi_["T"] - lo_["T"]) / (2 * step)
+        an = ref["dT"][:, 4 + j]
+        scale = np.maximum(np.abs(an), 1e-3 * ref["T"])
+        return np.abs(fd - an) / scale, same, an
+
+    for j, nm in enumerate(names):
+        err, same, an = fd_err(j, nm, h)
+        assert same.mean() > 0.95
+        assert np.any(np.abs(an[same]) > 0), nm
+        assert np.median(err[same]) < 1e-7, nm
+        assert np.quantile(err[same], 0.99) < 1e-4, nm
+        # the residual is central-difference truncation: it shrinks like h^2
+        err10, same10, _ = fd_err(j, nm, 10 * h)
+        both = same & same10
+        big = both & (err10 > 1e-6)
+        if big.any():
+            assert np.median(err[big] / err10[big]) < 0.05, nm
