@@ -1,0 +1,241 @@
+/*
+ * trk.h - C-ABI of the GB300 nested-geometry particle tracker.
+ *
+ * The library tracks neutral particles through nested constructive-solid-
+ * geometry universes (arXiv 2406.13849): the find_cell /
+ * distance_to_surface / move_within_cell / cross_surface loop of the
+ * paper's Table 1, run inside run_histories (Alg. 2) with synthetic
+ * physics.  Two trackers are built: a rect-array tracker chosen by static
+ * dispatch (Alg. 5, 6, 9, 10) and a single CSG tracker whose universes,
+ * arrays included, are CSG "pseudo-arrays" searched through a bounding
+ * volume hierarchy over cell boxes (Sec. 4.3).
+ *
+ * Conventions for every entry point:
+ *  - Plain pointers and sizes only.  "dev_" pointers are device memory on
+ *    the current CUDA device, owned and allocated by the caller; the
+ *    library allocates no device memory.  "host_" pointers are host memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Launches are asynchronous on it unless stated otherwise.
+ *  - Calls return a trk_status and never throw.  On failure
+ *    trk_last_error() returns a message (thread-local, valid until the next
+ *    call from the same thread).
+ *  - Failures found on the device (lost particles, segment caps, timeouts)
+ *    are counted in the caller's counter array (TRK_K_*); a kernel-level
+ *    failure also writes its status to counters[TRK_K_STATUS].
+ *  - Sizes are validated on the host before any launch.
+ */
+#ifndef TRK_H
+#define TRK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct trk_geom* trk_geom_t;   /* opaque, library-owned host object */
+
+typedef enum {
+    TRK_OK = 0,
+    TRK_E_INVALID = -1,       /* bad argument (null pointer, size, option) */
+    TRK_E_DESC = -2,          /* geometry description malformed or inconsistent */
+    TRK_E_CUDA = -3,          /* a CUDA runtime call failed */
+    TRK_E_NOMEM = -4,         /* caller buffer too small */
+    TRK_E_LOST = -5,          /* particle lost (no cell where one must exist) */
+    TRK_E_MAX_SEGMENTS = -6,  /* particle reached the segment cap */
+    TRK_E_TIMEOUT = -7,       /* persistent kernel gave up after its iteration limit */
+    TRK_E_UNSUPPORTED = -8,   /* option not supported for this geometry */
+    TRK_E_SOURCE = -9         /* source rejection sampling exceeded its cap */
+} trk_status;
+
+enum { TRK_TRACKER_RECT = 0, TRK_TRACKER_CSG = 1, TRK_TRACKER_AUTO = 2 };
+enum { TRK_MODE_HISTORY = 0, TRK_MODE_EVENT = 1 };
+enum { TRK_FP64 = 0, TRK_FP32_LOCAL = 1 };
+
+/* Counter slots (uint64 each, TRK_NCOUNTERS of them). */
+enum {
+    TRK_K_SEGMENTS = 0,     /* flights: surface crossings plus collision flights */
+    TRK_K_CROSSINGS = 1,
+    TRK_K_COLLISIONS = 2,
+    TRK_K_ABSORBED = 3,
+    TRK_K_ESCAPED = 4,
+    TRK_K_REFLECTIONS = 5,
+    TRK_K_LOST = 6,
+    TRK_K_MAXSEG = 7,
+    TRK_K_CUTOFF = 8,
+    TRK_K_SOURCE = 9,
+    TRK_K_CLOSE_CALLS = 10, /* FP32-local: decisions re-evaluated in FP64 */
+    TRK_K_STATUS = 15,      /* first kernel-level trk_status (0 = none), two's complement */
+    TRK_NCOUNTERS = 16
+};
+
+/* Per-particle terminal status written to records. */
+enum { TRK_P_ALIVE = 0, TRK_P_ABSORBED = 1, TRK_P_ESCAPED = 2, TRK_P_CUTOFF = 3 };
+
+typedef struct {
+    int tracker;            /* TRK_TRACKER_* */
+    int mode;               /* TRK_MODE_* */
+    int precision;          /* TRK_FP64 or TRK_FP32_LOCAL */
+    int block;              /* threads per block, 0 = default */
+    int grid;               /* blocks, 0 = default (a multiple of the SM count) */
+    int queue_depth;        /* event mode: particle slots per block, 0 = default */
+    int sort_interval;      /* event mode: regroup queues by cell every k rounds, 0 = never */
+    int reserved;
+    uint64_t seed;          /* low 32 bits key the Philox stream with the geometry id */
+    uint64_t first_id;      /* particle id of element 0 (ids key the random numbers) */
+    uint64_t max_segments;  /* per-particle segment cap (0 = 1e6) */
+    double p_absorb;        /* absorption probability per collision */
+    double max_path;        /* per-history path cutoff in cm (<= 0 or inf = none) */
+} trk_run_opts;
+
+/* Fills opts with the defaults: auto tracker, history mode, FP64, seed 1,
+ * p_absorb 0.3, max_segments 1e6, no cutoff. */
+void trk_default_opts(trk_run_opts* opts);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* trk_last_error(void);
+
+/* Library build flavour: 1 if compiled with --fmad=false (bit-exact against
+ * the FP64 reference arithmetic), 0 for the fast build. */
+int trk_exact_build(void);
+
+/*
+ * geometry_build - flatten a geometry description into device memory.
+ * Sec. 1 (Table 1 and the universes of Fig. 3), Sec. 3.2 (coincident
+ * lower-level surfaces removed), Sec. 4.3 (pseudo-array universes, cell
+ * bounding boxes, SAH partitioning with three candidates per axis).
+ *   json, len   description ("nested-csg-geometry-v1", see the package's
+ *               inputs module), host memory, need not be NUL-terminated.
+ *   dev_buf     device buffer of at least *dev_bytes bytes, 256-byte
+ *               aligned; NULL to query the size only (then *dev_bytes is
+ *               set, *out untouched).
+ *   dev_bytes   in: capacity of dev_buf; out: bytes needed.
+ *   stream      copies are enqueued on it; dev_buf must stay alive and
+ *               unmodified until geometry_destroy.
+ *   out         new handle (library-owned host object) on TRK_OK.
+ * Errors: TRK_E_DESC (parse/validation, message says where), TRK_E_NOMEM
+ * (dev_buf smaller than needed), TRK_E_INVALID, TRK_E_CUDA.
+ */
+trk_status geometry_build(const char* json, size_t len, void* dev_buf, size_t* dev_bytes,
+                          void* stream, trk_geom_t* out);
+
+/* Releases the host object (not the caller's device buffer).  NULL -> TRK_E_INVALID. */
+trk_status geometry_destroy(trk_geom_t g);
+
+/* Sizes of a built geometry: leaf cell instances (tally bins), materials,
+ * maximum nesting depth, and whether the rect tracker applies (no hex arrays). */
+trk_status geometry_info(trk_geom_t g, int64_t* n_instances, int32_t* n_materials,
+                         int32_t* max_depth, int32_t* rect_ok);
+
+/*
+ * source_init - sample the birth state of n particles (Alg. 2: position,
+ * isotropic direction, number of mean free paths tau).
+ *   Position uniform over the description's source box, rejected until it
+ *   lies in a root cell; direction by Marsaglia's method; tau = -log(xi).
+ *   Random numbers: Philox4x32-10, key (seed_lo32, geometry id), counter
+ *   (first_id + i, event 0, tag, attempt).
+ *   dev_particles  caller buffer of *particle_bytes bytes (8-byte aligned),
+ *                  NULL to query the size.  Layout (structure of arrays,
+ *                  n entries each): double x,y,z,u,v,w,tau; int32 status.
+ * Errors: TRK_E_INVALID, TRK_E_NOMEM, TRK_E_CUDA.  A particle whose source
+ * sampling hit the attempt cap gets status TRK_E_SOURCE.
+ */
+trk_status source_init(trk_geom_t g, int64_t n, uint64_t first_id, uint64_t seed,
+                       void* dev_particles, size_t* particle_bytes, void* stream);
+
+/* Work (scratch) bytes run_histories needs for n particles with these options. */
+trk_status run_histories_work_bytes(trk_geom_t g, int64_t n, const trk_run_opts* opts,
+                                    size_t* bytes);
+
+/*
+ * run_histories - track n particles from their birth states to absorption,
+ * escape or a cap (Alg. 2 with synthetic physics; find_cell Alg. 7,
+ * cross_surface Alg. 8; distances, moves and direction changes of Table 1).
+ *   dev_particles  birth states written by source_init (read only).
+ *   dev_tally      uint64[n_instances], track length per leaf cell instance
+ *                  in units of 2^-32 cm (added to, not cleared).
+ *   dev_counters   uint64[TRK_NCOUNTERS] (added to, not cleared).
+ *   dev_records    optional uint64[2n]: per particle {FNV-1a digest of the
+ *                  (instance, segment-length bits) sequence,
+ *                  (segments << 32) | (uint32)status}; NULL to skip.
+ *   dev_work       scratch of run_histories_work_bytes (256-byte aligned).
+ *   opts           NULL = defaults.
+ * Errors: TRK_E_INVALID, TRK_E_UNSUPPORTED (rect tracker on hex arrays,
+ * FP32-local in event mode), TRK_E_NOMEM, TRK_E_CUDA.
+ */
+trk_status run_histories(trk_geom_t g, const void* dev_particles, int64_t n, uint64_t* dev_tally,
+                         uint64_t* dev_counters, uint64_t* dev_records, void* dev_work,
+                         size_t work_bytes, const trk_run_opts* opts, void* stream);
+
+/* tally_read - copy the tally to host as cm (value * 2^-32).  Synchronises
+ * `stream`.  n_instances must equal the geometry's.  Also returns
+ * TRK_E_TIMEOUT/TRK_E_LOST... if dev_counters (optional) holds a kernel status. */
+trk_status tally_read(trk_geom_t g, const uint64_t* dev_tally, double* host_out, int64_t n_instances,
+                      const uint64_t* dev_counters, void* stream);
+
+/* trk_find_cell - Alg. 7 for n global points (dev_xyz: double[3n]); writes
+ * the leaf instance or -1 (outside / lost) to dev_inst (int64[n]). */
+trk_status trk_find_cell(trk_geom_t g, int tracker, int64_t n, const double* dev_xyz,
+                         int64_t* dev_inst, void* stream);
+
+/* trk_trace - run_histories (history mode, FP64) that also logs each
+ * particle's segments: for particle i and segment k < cap,
+ * dev_inst[i*cap+k] (int32 leaf instance, -1 past the end) and
+ * dev_len[i*cap+k] (segment length, cm).  Tallies and counters as in
+ * run_histories. */
+trk_status trk_trace(trk_geom_t g, const void* dev_particles, int64_t n, int32_t cap,
+                     int32_t* dev_inst, double* dev_len, uint64_t* dev_tally,
+                     uint64_t* dev_counters, const trk_run_opts* opts, void* stream);
+
+/*
+ * transmission_fwd - deterministic rays without collisions: per-material
+ * track lengths l_m and T = exp(-sum_m sigma_m l_m) (the optical depth of
+ * the track-length walk).
+ *   dev_rays   double[6n] (x,y,z,u,v,w) per ray, start inside the geometry.
+ *   dev_sigma  double[n_materials].
+ *   dev_T      double[n]; dev_lens double[n*n_materials] (may be NULL).
+ */
+trk_status transmission_fwd(trk_geom_t g, int tracker, int64_t n, const double* dev_rays,
+                            const double* dev_sigma, double* dev_T, double* dev_lens, void* stream);
+
+/* Parameters of the transmission gradient beyond sigma: pin radii r_0..r_2
+ * (surfaces tagged rparam) and the lattice pitch (surfaces tagged pscale). */
+enum { TRK_NGEOM_PARAMS = 4 };
+
+/* Work bytes of transmission_bwd for n rays. */
+trk_status transmission_bwd_work_bytes(trk_geom_t g, int64_t n, size_t* bytes);
+
+/*
+ * transmission_bwd - hand-written backward of transmission_fwd: given
+ * dL/dT per ray (dev_gT), writes dev_grad[n_materials + 4] =
+ * sum_rays dL/dT * dT/dtheta for theta = (sigma_0.., r_0, r_1, r_2, pitch).
+ * dT/dsigma_m = -l_m T; geometric parameters through the moved hit points:
+ * dt/dtheta = -(df/dtheta)/(grad f . Omega) at every crossing, segment
+ * lengths move by dt_exit - dt_entry.  Segments are recomputed, not stored.
+ * The reduction over rays is a fixed-order tree (deterministic).
+ */
+trk_status transmission_bwd(trk_geom_t g, int tracker, int64_t n, const double* dev_rays,
+                            const double* dev_sigma, double pitch, const double* dev_gT,
+                            double* dev_grad, void* dev_work, size_t work_bytes, void* stream);
+
+/*
+ * trk_peak_kernel - measurement support (the paper has no counterpart):
+ * launches a microbenchmark of `blocks` x 256 threads on `stream` and
+ * returns in *ops the number of operations it performs, for the caller to
+ * divide by its CUDA-event time.
+ *   kind 0  FP64 fused multiply-add chains (ops = flops, 2 per FMA)
+ *   kind 1  FP32 fused multiply-add chains (ops = flops)
+ *   kind 2  64-bit integer atomicAdd into nbins counters (ops = atomics)
+ *   dev_scratch  caller buffer: >= 2 KB for kinds 0/1, >= 8*nbins bytes for
+ *                kind 2 (its contents are overwritten).
+ * Errors: TRK_E_INVALID, TRK_E_NOMEM, TRK_E_CUDA.
+ */
+trk_status trk_peak_kernel(int kind, int blocks, int iters, int nbins, void* dev_scratch,
+                           size_t scratch_bytes, double* ops, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TRK_H */

@@ -1,0 +1,88 @@
+// trk_internal.h - flattened device geometry shared by the host builder
+// (geometry_build.cpp) and the kernels (trk_kernels.cu).  Not part of the ABI.
+//
+// Everything a tracker reads lives in one caller-owned device buffer as a
+// structure of arrays; DevGeom holds typed pointers into it and is passed to
+// every kernel by value.  Two views of the same universes coexist so that one
+// handle serves both trackers:
+//   CSG view   every universe is a list of CSG cells; array universes appear
+//              as pseudo-arrays (Sec. 4.3), one plane-bounded cell per element,
+//              searched through a BVH over cell boxes.
+//   rect view  rect array universes keep their grid planes (Alg. 5/6).
+#pragma once
+#include <stdint.h>
+#include <cuda_runtime.h>
+
+namespace trk {
+
+enum SurfType { S_PX = 0, S_PY = 1, S_PZ = 2, S_P = 3, S_CZ = 4 };
+enum Bc { BC_NONE = 0, BC_VACUUM = 1, BC_REFLECT = 2 };
+
+// Compiled nesting depth of the trackers' register-resident level stack.
+constexpr int MAXL = 4;
+// Cells per BVH leaf at most, and BVH traversal stack depth.
+constexpr int BVH_LEAF_MAX = 4;
+constexpr int BVH_STACK = 32;
+// Universes with at most this many cells are scanned linearly (Alg. 3).
+constexpr int LINEAR_MAX = 4;
+
+// BVH2 node holding both children's boxes (FP32, rounded outward).  The
+// child references sit in the w lanes of lo0 / lo1 as int bits:
+//   ref >= 0  internal node index
+//   ref <  0  leaf: ~ref = (first leaf slot << 4) | count
+struct alignas(16) BvhNode {
+    float4 lo0, hi0, lo1, hi1;
+};
+
+struct DevGeom {
+    // surfaces
+    const int* s_info;        // type | (bc << 4) | (rparam+1) << 8 | pscale << 12
+    const double* s_coef;     // 4 per surface; px/py/pz: (g,0,0,0); p: (nx,ny,nz,d); cz: (x0,y0,r,r*r)
+    // cells (CSG view)
+    const int2* c_range;      // (first, count) into cs
+    const int* cs;            // (surface << 1) | (sense > 0)
+    const int* c_fill;        // >= 0 daughter universe; < 0 material ~fill
+    const double* c_tr;       // translation into the daughter, 3 per cell
+    const int* c_off;         // leaf-instance offset of the cell
+    // universes
+    const int4* u_info;       // (first cell, cell count, BVH root or -1, rect lattice or -1)
+    // rect arrays (rect view)
+    const int4* l_dim;        // (nx, ny, nz, packed bc: 2 bits per face xlo..zhi)
+    const int4* l_off;        // (x grid offset, y grid offset, z grid offset, element offset)
+    const double* l_grid;     // grid planes; dim d of lattice k at l_grid[l_off[k].d]
+    const double* l_ctr;      // element centres (g_i + g_{i+1}) * 0.5, same offsets
+    const int* l_fill;        // element universe, at l_fill[l_off[k].w + e]
+    const int* l_eoff;        // element instance offset, same indexing
+    const int* l_pscale;      // grid planes scale with the pitch (gradient)
+    // BVH
+    const BvhNode* nodes;
+    const int* leaf_cells;
+    // materials
+    const double* sigma;
+    double src_lo[3], src_hi[3];
+    int root, n_inst, n_mat, gid, max_depth, n_univ, n_cells, n_surf;
+    int rect_ok;              // no hex arrays: the rect tracker applies
+};
+
+// Particle buffer written by source_init (structure of arrays).
+struct ParticlesView {
+    const double* x; const double* y; const double* z;
+    const double* u; const double* v; const double* w;
+    const double* tau; const int* status;
+};
+
+// Records the message returned by trk_last_error() and returns `st`.
+int set_error(int st, const char* fmt, ...);
+
+}  // namespace trk
+
+// The library-owned host object behind trk_geom_t.
+struct trk_geom {
+    trk::DevGeom dg;
+    size_t bytes = 0;
+    int64_t n_inst = 0;
+    int n_mat = 0, depth = 0, rect_ok = 0;
+    int n_nodes = 0;
+    unsigned magic = 0;
+};
+constexpr unsigned TRK_GEOM_MAGIC = 0x7472'6b67u;

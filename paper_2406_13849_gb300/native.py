@@ -1,0 +1,270 @@
+"""Thin Python binding of the C-ABI in include/trk.h (argument marshalling only).
+
+Every step of the tracking path runs in the library's CUDA kernels; PyTorch
+supplies device memory and streams.  The functions keep the ABI's names:
+``geometry_build``, ``source_init``, ``run_histories``, ``tally_read``,
+``trk_find_cell``, ``trk_trace``, ``transmission_fwd``, ``transmission_bwd``.
+
+There is no CPU fallback: if the compiled library is missing, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import threading
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+TRK_OK = 0
+STATUS = {0: "TRK_OK", -1: "TRK_E_INVALID", -2: "TRK_E_DESC", -3: "TRK_E_CUDA", -4: "TRK_E_NOMEM",
+          -5: "TRK_E_LOST", -6: "TRK_E_MAX_SEGMENTS", -7: "TRK_E_TIMEOUT", -8: "TRK_E_UNSUPPORTED",
+          -9: "TRK_E_SOURCE"}
+TRACKER_RECT, TRACKER_CSG, TRACKER_AUTO = 0, 1, 2
+MODE_HISTORY, MODE_EVENT = 0, 1
+FP64, FP32_LOCAL = 0, 1
+NCOUNTERS = 16
+K = dict(segments=0, crossings=1, collisions=2, absorbed=3, escaped=4, reflections=5, lost=6,
+         maxseg=7, cutoff=8, source=9, close_calls=10, status=15)
+NGEOM_PARAMS = 4
+
+
+class TrkError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class RunOpts(ctypes.Structure):
+    _fields_ = [("tracker", ctypes.c_int), ("mode", ctypes.c_int), ("precision", ctypes.c_int),
+                ("block", ctypes.c_int), ("grid", ctypes.c_int), ("queue_depth", ctypes.c_int),
+                ("sort_interval", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("seed", ctypes.c_uint64), ("first_id", ctypes.c_uint64),
+                ("max_segments", ctypes.c_uint64), ("p_absorb", ctypes.c_double),
+                ("max_path", ctypes.c_double)]
+
+
+_P = ctypes.c_void_p
+_LIBS: dict = {}
+_LOCK = threading.Lock()
+
+
+def library(exact: bool = False):
+    """Load libtrk.so (or libtrk_exact.so), building it first if it is stale."""
+    key = "exact" if exact else "fast"
+    with _LOCK:
+        if key in _LIBS:
+            return _LIBS[key]
+        path = _build.outputs()[key]
+        if not os.path.exists(path):
+            _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA tracking library missing: {path} (run paper_2406_13849_gb300.build)")
+        lib = ctypes.CDLL(path)
+        i64, u64, sz = ctypes.c_int64, ctypes.c_uint64, ctypes.c_size_t
+        pi64, pi32, psz = ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(sz)
+        sig = {
+            "trk_last_error": (ctypes.c_char_p, []),
+            "trk_exact_build": (ctypes.c_int, []),
+            "trk_default_opts": (None, [ctypes.POINTER(RunOpts)]),
+            "geometry_build": (ctypes.c_int, [ctypes.c_char_p, sz, _P, psz, _P, ctypes.POINTER(_P)]),
+            "geometry_destroy": (ctypes.c_int, [_P]),
+            "geometry_info": (ctypes.c_int, [_P, pi64, pi32, pi32, pi32]),
+            "source_init": (ctypes.c_int, [_P, i64, u64, u64, _P, psz, _P]),
+            "run_histories_work_bytes": (ctypes.c_int, [_P, i64, ctypes.POINTER(RunOpts), psz]),
+            "run_histories": (ctypes.c_int, [_P, _P, i64, _P, _P, _P, _P, sz, ctypes.POINTER(RunOpts), _P]),
+            "tally_read": (ctypes.c_int, [_P, _P, _P, i64, _P, _P]),
+            "trk_find_cell": (ctypes.c_int, [_P, ctypes.c_int, i64, _P, _P, _P]),
+            "trk_trace": (ctypes.c_int, [_P, _P, i64, ctypes.c_int32, _P, _P, _P, _P,
+                                         ctypes.POINTER(RunOpts), _P]),
+            "transmission_fwd": (ctypes.c_int, [_P, ctypes.c_int, i64, _P, _P, _P, _P, _P]),
+            "transmission_bwd_work_bytes": (ctypes.c_int, [_P, i64, psz]),
+            "transmission_bwd": (ctypes.c_int, [_P, ctypes.c_int, i64, _P, _P, ctypes.c_double, _P, _P,
+                                                _P, sz, _P]),
+            "trk_peak_kernel": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, sz,
+                                               ctypes.POINTER(ctypes.c_double), _P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _LIBS[key] = lib
+        return lib
+
+
+def _check(lib, code):
+    if code != TRK_OK:
+        raise TrkError(code, lib.trk_last_error().decode())
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def default_opts(**kw) -> RunOpts:
+    o = RunOpts()
+    library().trk_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+class Geometry:
+    """A description flattened into device memory (geometry_build)."""
+
+    def __init__(self, desc_json: str, device=None, exact: bool = False, stream=None):
+        self.lib = library(exact)
+        self.exact = exact
+        raw = desc_json.encode() if isinstance(desc_json, str) else bytes(desc_json)
+        self.device = torch.device(device if device is not None else "cuda")
+        nbytes = ctypes.c_size_t(0)
+        _check(self.lib, self.lib.geometry_build(raw, len(raw), None, ctypes.byref(nbytes), None, None))
+        # 256-byte aligned device buffer owned by this object
+        self.buf = torch.empty(nbytes.value + 256, dtype=torch.uint8, device=self.device)
+        off = (-self.buf.data_ptr()) % 256
+        self._base = self.buf.data_ptr() + off
+        h = ctypes.c_void_p()
+        cap = ctypes.c_size_t(nbytes.value)
+        _check(self.lib, self.lib.geometry_build(raw, len(raw), ctypes.c_void_p(self._base), ctypes.byref(cap),
+                                                 _stream(stream), ctypes.byref(h)))
+        self.h = h
+        ni, nm, dp, ro = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(self.lib, self.lib.geometry_info(h, ctypes.byref(ni), ctypes.byref(nm), ctypes.byref(dp),
+                                                ctypes.byref(ro)))
+        self.n_inst, self.n_mat, self.depth, self.rect_ok = ni.value, nm.value, dp.value, bool(ro.value)
+        self.device_bytes = nbytes.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.geometry_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- source_init -------------------------------------------------------
+    def particle_bytes(self, n: int) -> int:
+        b = ctypes.c_size_t(0)
+        _check(self.lib, self.lib.source_init(self.h, n, 0, 0, None, ctypes.byref(b), None))
+        return b.value
+
+    def source_init(self, n: int, seed: int = 1, first_id: int = 0, out=None, stream=None):
+        need = self.particle_bytes(n)
+        if out is None:
+            out = torch.empty(max(need, 8), dtype=torch.uint8, device=self.device)
+        b = ctypes.c_size_t(out.numel() * out.element_size())
+        _check(self.lib, self.lib.source_init(self.h, n, first_id, seed, _ptr(out), ctypes.byref(b),
+                                              _stream(stream)))
+        return out
+
+    @staticmethod
+    def particles_as_arrays(buf, n):
+        d = buf[: n * 56].view(torch.float64).view(7, n)
+        st = buf[n * 56: n * 60].view(torch.int32)
+        return d, st
+
+    # -- run_histories -----------------------------------------------------
+    def work_bytes(self, n: int, opts: RunOpts) -> int:
+        b = ctypes.c_size_t(0)
+        _check(self.lib, self.lib.run_histories_work_bytes(self.h, n, ctypes.byref(opts), ctypes.byref(b)))
+        return b.value
+
+    def run_histories(self, particles, n: int, tally=None, counters=None, records: bool = False,
+                      work=None, opts: RunOpts | None = None, stream=None, **kw):
+        opts = opts if opts is not None else default_opts(**kw)
+        if tally is None:
+            tally = torch.zeros(self.n_inst, dtype=torch.int64, device=self.device)
+        if counters is None:
+            counters = torch.zeros(NCOUNTERS, dtype=torch.int64, device=self.device)
+        rec = torch.zeros(2 * n, dtype=torch.int64, device=self.device) if records else None
+        wb = self.work_bytes(n, opts)
+        if work is None and wb:
+            work = torch.empty(wb + 256, dtype=torch.uint8, device=self.device)
+        wp, wlen = None, 0
+        if work is not None:
+            off = (-work.data_ptr()) % 256
+            wp = ctypes.c_void_p(work.data_ptr() + off)
+            wlen = work.numel() * work.element_size() - off
+        _check(self.lib, self.lib.run_histories(self.h, _ptr(particles), n, _ptr(tally), _ptr(counters), _ptr(rec),
+                                                wp, wlen, ctypes.byref(opts), _stream(stream)))
+        return tally, counters, rec
+
+    def tally_read(self, tally, counters=None, stream=None) -> np.ndarray:
+        out = np.zeros(self.n_inst, np.float64)
+        _check(self.lib, self.lib.tally_read(self.h, _ptr(tally), out.ctypes.data_as(_P), self.n_inst,
+                                             _ptr(counters), _stream(stream)))
+        return out
+
+    # -- diagnostics ---------------------------------------------------------
+    def find_cell(self, xyz, tracker=TRACKER_AUTO, stream=None):
+        xyz = xyz.contiguous()
+        out = torch.empty(xyz.shape[0], dtype=torch.int64, device=self.device)
+        _check(self.lib, self.lib.trk_find_cell(self.h, tracker, xyz.shape[0], _ptr(xyz), _ptr(out),
+                                                _stream(stream)))
+        return out
+
+    def trace(self, particles, n: int, cap: int, opts: RunOpts | None = None, stream=None, **kw):
+        opts = opts if opts is not None else default_opts(**kw)
+        inst = torch.empty(n * cap, dtype=torch.int32, device=self.device)
+        ln = torch.empty(n * cap, dtype=torch.float64, device=self.device)
+        tally = torch.zeros(self.n_inst, dtype=torch.int64, device=self.device)
+        cnt = torch.zeros(NCOUNTERS, dtype=torch.int64, device=self.device)
+        _check(self.lib, self.lib.trk_trace(self.h, _ptr(particles), n, cap, _ptr(inst), _ptr(ln), _ptr(tally),
+                                            _ptr(cnt), ctypes.byref(opts), _stream(stream)))
+        return inst.view(n, cap), ln.view(n, cap), tally, cnt
+
+    # -- transmission --------------------------------------------------------
+    def transmission_fwd(self, rays, sigma, tracker=TRACKER_AUTO, lens: bool = True, stream=None):
+        rays = rays.contiguous()
+        n = rays.shape[0]
+        T = torch.empty(n, dtype=torch.float64, device=self.device)
+        L = torch.empty(n, self.n_mat, dtype=torch.float64, device=self.device) if lens else None
+        _check(self.lib, self.lib.transmission_fwd(self.h, tracker, n, _ptr(rays), _ptr(sigma.contiguous()),
+                                                   _ptr(T), _ptr(L), _stream(stream)))
+        return T, L
+
+    def transmission_bwd(self, rays, sigma, pitch: float, gT, tracker=TRACKER_AUTO, stream=None):
+        rays = rays.contiguous()
+        n = rays.shape[0]
+        b = ctypes.c_size_t(0)
+        _check(self.lib, self.lib.transmission_bwd_work_bytes(self.h, n, ctypes.byref(b)))
+        work = torch.empty(max(b.value, 8), dtype=torch.uint8, device=self.device)
+        grad = torch.empty(self.n_mat + NGEOM_PARAMS, dtype=torch.float64, device=self.device)
+        _check(self.lib, self.lib.transmission_bwd(self.h, tracker, n, _ptr(rays), _ptr(sigma.contiguous()),
+                                                   float(pitch), _ptr(gT.contiguous()), _ptr(grad), _ptr(work),
+                                                   work.numel(), _stream(stream)))
+        return grad
+
+
+def unpack_records(rec: torch.Tensor):
+    """(hash uint64, segments, status) from run_histories records."""
+    r = rec.view(-1, 2).cpu().numpy().view(np.uint64)
+    h = r[:, 0]
+    nseg = (r[:, 1] >> np.uint64(32)).astype(np.int64)
+    st = (r[:, 1] & np.uint64(0xffffffff)).astype(np.uint32).view(np.int32)
+    return h, nseg, st
+
+
+def peak_kernel(kind: int, blocks: int, iters: int, nbins: int, scratch, stream=None) -> float:
+    """Launch one microbenchmark (trk_peak_kernel); returns its operation count."""
+    lib = library()
+    ops = ctypes.c_double(0)
+    _check(lib, lib.trk_peak_kernel(kind, blocks, iters, nbins, _ptr(scratch),
+                                    scratch.numel() * scratch.element_size(), ctypes.byref(ops),
+                                    _stream(stream)))
+    return ops.value

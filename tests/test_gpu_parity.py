@@ -1,0 +1,301 @@
+"""GPU parity: the CUDA path (through the C-ABI) against the CPU oracle.
+
+Bars:
+  --fmad=false build: bit-exact per particle (digest of the instance and
+    segment-length sequence, segment count, status), bit-exact u64 tallies
+    and counters, bit-exact birth states and find_cell.
+  fast build: identical instance sequences for all but a tiny fraction of
+    particles (a near-surface decision can go either way under contraction),
+    segment lengths within 1e-12 relative where sequences agree, totals
+    within 1e-9 relative.
+Sizes: several thousand histories per case (many blocks plus a ragged tail),
+plus sampled particles of the full-size workloads in the benchmark's launch
+configuration.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2406_13849_gb300 import inputs as I
+from paper_2406_13849_gb300 import native as N
+
+pytestmark = pytest.mark.gpu
+
+SEED = 1
+
+CASES = {
+    "c1": (I.config1(), 0.3, 10_007),
+    "small_core": (I.small_core(), 0.25, 6_001),
+    "c2": (I.config2(), 0.25, 3_001),
+    "tiny3": (I.random_tiny(3), 0.3, 4_099),
+    "tiny8": (I.random_tiny(8), 0.3, 4_099),
+    "pin_vacuum": (I.single_pin(bc="vacuum"), 0.3, 2_053),
+}
+HEX_CASES = {
+    "c3": (I.config3(), 0.25, 1_201),
+    "small_hex_core": (I.small_hex_core(), 0.25, 3_001),
+    "hex_rot": (I.small_hex(rings=3, rot30=True), 0.3, 2_003),
+}
+
+
+def _oracle(desc, mode):
+    return O.Geometry(I.to_json(desc), mode)
+
+
+def _gpu(desc, exact):
+    return N.Geometry(I.to_json(desc), exact=exact)
+
+
+def _u64(t):
+    return t.cpu().numpy().view(np.uint64)
+
+
+def _run_gpu(g, n, pa, tracker, records=True, **kw):
+    parts = g.source_init(n, seed=SEED)
+    tally, cnt, rec = g.run_histories(parts, n, records=records, tracker=tracker, p_absorb=pa, seed=SEED, **kw)
+    torch.cuda.synchronize()
+    return parts, _u64(tally), _u64(cnt), rec
+
+
+# ---------------------------------------------------------------------------
+# birth states and find_cell
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", list(CASES) + list(HEX_CASES))
+def test_source_bit_exact(name):
+    desc, pa, n = {**CASES, **HEX_CASES}[name]
+    o = _oracle(desc, O.MODE_CSG)
+    ref, st = o.source(n, SEED)
+    g = _gpu(desc, exact=True)
+    buf = g.source_init(n, seed=SEED)
+    d, gst = N.Geometry.particles_as_arrays(buf, n)
+    got = d.cpu().numpy().T
+    assert np.array_equal(gst.cpu().numpy(), st)
+    assert np.array_equal(got.view(np.uint64), ref.view(np.uint64))
+
+
+@pytest.mark.parametrize("name", list(CASES) + list(HEX_CASES))
+def test_find_cell_exact(name):
+    desc, _, _ = {**CASES, **HEX_CASES}[name]
+    lo, hi = np.array(desc["source_box"][:3]), np.array(desc["source_box"][3:])
+    pts = lo + np.random.default_rng(3).uniform(0, 1, (20_000, 3)) * (hi - lo)
+    g = _gpu(desc, exact=True)
+    xyz = torch.from_numpy(pts).cuda()
+    trackers = [(N.TRACKER_CSG, O.MODE_CSG)]
+    if name in CASES:
+        trackers.append((N.TRACKER_RECT, O.MODE_RECT))
+    for tr, mode in trackers:
+        ref = _oracle(desc, mode).find_cell(pts)
+        got = g.find_cell(xyz, tracker=tr).cpu().numpy()
+        assert np.array_equal(got, ref), (name, tr)
+
+
+# ---------------------------------------------------------------------------
+# histories: exact build, bit for bit
+# ---------------------------------------------------------------------------
+
+def _compare_exact(desc, pa, n, tracker, mode, **kw):
+    o = _oracle(desc, mode).run(n, SEED, pa, threads=8, **{k: v for k, v in kw.items()})
+    g = _gpu(desc, exact=True)
+    gkw = {}
+    if "max_segments" in kw:
+        gkw["max_segments"] = kw["max_segments"]
+    if "max_path" in kw:
+        gkw["max_path"] = kw["max_path"]
+    _, tally, cnt, rec = _run_gpu(g, n, pa, tracker, **gkw)
+    h, nseg, st = N.unpack_records(rec)
+    assert np.array_equal(st, o["status"])
+    assert np.array_equal(nseg, o["nseg"])
+    assert np.array_equal(h, o["hash"])
+    assert np.array_equal(tally, o["tally"])
+    assert np.array_equal(cnt[:10], o["counters"][:10])
+    assert cnt[N.K["status"]] == 0
+    return o
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("tracker,mode", [(N.TRACKER_RECT, O.MODE_RECT), (N.TRACKER_CSG, O.MODE_CSG)])
+def test_histories_bit_exact(name, tracker, mode):
+    desc, pa, n = CASES[name]
+    o = _compare_exact(desc, pa, n, tracker, mode)
+    assert o["counters"][O.K_SEGMENTS] > n
+
+
+@pytest.mark.parametrize("name", list(HEX_CASES))
+def test_histories_bit_exact_hex(name):
+    desc, pa, n = HEX_CASES[name]
+    _compare_exact(desc, pa, n, N.TRACKER_CSG, O.MODE_CSG)
+
+
+def test_segment_cap_and_cutoff_exact():
+    desc = I.config1()
+    o = _compare_exact(desc, 0.0, 1_000, N.TRACKER_RECT, O.MODE_RECT, max_segments=7)
+    assert np.all(o["status"] == O.P_MAXSEG)
+    d0 = I.config1(sigma=(0.0, 0.0, 0.0))
+    o = _compare_exact(d0, 0.3, 1_000, N.TRACKER_CSG, O.MODE_CSG, max_path=150.0)
+    assert np.all(o["status"] == O.P_CUTOFF)
+
+
+def test_rect_and_csg_trackers_identical_on_gpu():
+    for desc, pa, n in (CASES["c1"], CASES["small_core"]):
+        g = _gpu(desc, exact=False)
+        ra = _run_gpu(g, n, pa, N.TRACKER_RECT)
+        rb = _run_gpu(g, n, pa, N.TRACKER_CSG)
+        assert np.array_equal(ra[1], rb[1])
+        assert np.array_equal(_u64(ra[3]), _u64(rb[3]))
+
+
+# ---------------------------------------------------------------------------
+# histories: fast build, within tolerance
+# ---------------------------------------------------------------------------
+
+def _traces_oracle(o, ids, pa):
+    out = {}
+    for i in ids:
+        inst, ln, kind, st = o.trace(int(i), SEED, pa)
+        out[int(i)] = (inst, ln)
+    return out
+
+
+@pytest.mark.parametrize("name", ["c1", "small_core", "tiny3"])
+@pytest.mark.parametrize("tracker,mode", [(N.TRACKER_RECT, O.MODE_RECT), (N.TRACKER_CSG, O.MODE_CSG)])
+def test_histories_fast_within_tolerance(name, tracker, mode):
+    desc, pa, n = CASES[name]
+    n = min(n, 3000)
+    o = _oracle(desc, mode)
+    ref = o.run(n, SEED, pa, threads=8)
+    g = _gpu(desc, exact=False)
+    parts = g.source_init(n, seed=SEED)
+    cap = 4096
+    inst, ln, tally, cnt = g.trace(parts, n, cap, tracker=tracker, p_absorb=pa, seed=SEED)
+    inst, ln = inst.cpu().numpy(), ln.cpu().numpy()
+    mism = 0
+    for i in range(n):
+        oi, ol, _, _ = o.trace(i, SEED, pa, cap=cap)
+        k = len(oi)
+        gi, gl = inst[i], ln[i]
+        gk = int((gi >= 0).sum())
+        if gk != k or not np.array_equal(gi[:k], oi):
+            mism += 1
+            continue
+        rel = np.abs(gl[:k] - ol) / np.maximum(np.abs(ol), 1e-3)
+        assert rel.max() < 1e-12, (i, rel.max())
+    assert mism <= max(2, n // 1000), mism
+    t_ref = ref["tally"].astype(np.float64).sum()
+    t_got = tally.cpu().numpy().view(np.uint64).astype(np.float64).sum()
+    assert abs(t_got - t_ref) <= 1e-9 * t_ref + 1e-6 * 2**32 * mism * 100
+
+
+# ---------------------------------------------------------------------------
+# full-size workloads, sampled particles, benchmark launch configuration
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("exact", [True, False])
+def test_config2_full_size_sampled(exact):
+    desc = I.config2()
+    n, pa = 10_000_000, 0.25
+    g = _gpu(desc, exact=exact)
+    parts = g.source_init(n, seed=SEED)
+    tally, cnt, rec = g.run_histories(parts, n, records=True, tracker=N.TRACKER_CSG, p_absorb=pa, seed=SEED)
+    torch.cuda.synchronize()
+    h, nseg, st = N.unpack_records(rec)
+    c = _u64(cnt)
+    # properties that hold at any size
+    assert c[N.K["lost"]] == 0 and c[N.K["status"]] == 0
+    assert c[N.K["absorbed"]] + c[N.K["escaped"]] + c[N.K["maxseg"]] == n
+    assert c[N.K["segments"]] == c[N.K["crossings"]] + c[N.K["collisions"]]
+    assert nseg.sum() == c[N.K["segments"]]
+    # sampled particles one by one in the oracle
+    o = _oracle(desc, O.MODE_CSG)
+    ids = np.random.default_rng(7).choice(n, 200, replace=False)
+    same = 0
+    for i in ids:
+        r = o.run(1, SEED, pa, first_id=int(i))
+        if exact:
+            assert r["hash"][0] == h[i] and r["nseg"][0] == nseg[i] and r["status"][0] == st[i], int(i)
+        else:
+            same += int(r["nseg"][0] == nseg[i] and r["status"][0] == st[i])
+    if not exact:
+        assert same >= 198
+
+
+def test_config3_full_size_sampled():
+    desc = I.config3()
+    n, pa = 10_000_000, 0.25
+    g = _gpu(desc, exact=True)
+    parts = g.source_init(n, seed=SEED)
+    tally, cnt, rec = g.run_histories(parts, n, records=True, tracker=N.TRACKER_CSG, p_absorb=pa, seed=SEED)
+    torch.cuda.synchronize()
+    h, nseg, st = N.unpack_records(rec)
+    c = _u64(cnt)
+    assert c[N.K["status"]] == 0
+    assert c[N.K["lost"]] <= n * 1e-6
+    o = _oracle(desc, O.MODE_CSG)
+    for i in np.random.default_rng(8).choice(n, 60, replace=False):
+        r = o.run(1, SEED, pa, first_id=int(i))
+        assert r["hash"][0] == h[i] and r["nseg"][0] == nseg[i], int(i)
+
+
+# ---------------------------------------------------------------------------
+# edge cases and errors
+# ---------------------------------------------------------------------------
+
+def test_edge_cases():
+    desc = I.config1()
+    g = _gpu(desc, exact=True)
+    parts = g.source_init(1, seed=SEED)
+    tally, cnt, rec = g.run_histories(parts, 0, records=True)
+    assert _u64(cnt).sum() == 0
+    o = _oracle(desc, O.MODE_RECT).run(1, SEED, 0.3)
+    tally, cnt, rec = g.run_histories(parts, 1, records=True, p_absorb=0.3, seed=SEED)
+    h, nseg, st = N.unpack_records(rec)
+    assert h[0] == o["hash"][0] and nseg[0] == o["nseg"][0]
+    out = np.zeros(g.n_inst)
+    assert g.lib.tally_read(g.h, N._ptr(tally), out.ctypes.data_as(ctypes.c_void_p), g.n_inst - 1,
+                            None, None) == -1
+    assert g.lib.tally_read(g.h, N._ptr(tally), None, g.n_inst, None, None) == -1
+    hexg = _gpu(I.small_hex(), exact=False)
+    p = hexg.source_init(10)
+    with pytest.raises(N.TrkError) as e:
+        hexg.run_histories(p, 10, tracker=N.TRACKER_RECT)
+    assert e.value.code == -8
+    with pytest.raises(N.TrkError) as e:
+        g.run_histories(parts, 1, p_absorb=1.5)
+    assert e.value.code == -1
+
+
+def test_tally_read_units():
+    desc = I.config1()
+    g = _gpu(desc, exact=True)
+    n = 2000
+    parts = g.source_init(n, seed=SEED)
+    tally, cnt, _ = g.run_histories(parts, n, p_absorb=0.3, seed=SEED)
+    cm = g.tally_read(tally, cnt)
+    ref = _oracle(desc, O.MODE_RECT).run(n, SEED, 0.3)["tally"]
+    assert np.array_equal(cm, ref.astype(np.float64) * 2.0**-32)
+
+
+# ---------------------------------------------------------------------------
+# transmission forward / backward
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("tracker,mode", [(N.TRACKER_RECT, O.MODE_RECT), (N.TRACKER_CSG, O.MODE_CSG)])
+def test_transmission_against_oracle(tracker, mode):
+    r_out = 0.5 * 3 * 5 * 1.26 * 1.2
+    desc = I.small_core(height=20.0, r_outer=r_out)
+    sigma = np.array(desc["sigma"])
+    rays = I.boundary_rays(4000, r_outer=r_out, height=20.0, seed=11).packed()
+    ref = _oracle(desc, mode).transmission(rays, sigma, pitch=1.26)
+    g = _gpu(desc, exact=True)
+    R = torch.from_numpy(rays).cuda()
+    S = torch.from_numpy(sigma).cuda()
+    T, L = g.transmission_fwd(R, S, tracker=tracker)
+    assert np.array_equal(L.cpu().numpy(), ref["lens"])
+    assert np.allclose(T.cpu().numpy(), ref["T"], rtol=1e-14, atol=0)
+    gT = torch.from_numpy(np.random.default_rng(2).normal(size=len(rays))).cuda()
+    grad = g.transmission_bwd(R, S, 1.26, gT, tracker=tracker).cpu().numpy()
+    expect = (gT.cpu().numpy()[:, None] * ref["dT"]).sum(0)
+    assert np.allclose(grad, expect, rtol=1e-10, atol=1e-14 * np.abs(expect).max())
