@@ -667,14 +667,15 @@ float f_up(double v) {
 
 class BvhBuilder {
   public:
-    std::vector<BvhNode> nodes;
+    std::vector<SkipNode> nodes;
     std::vector<int> leaf_cells;
     Box proxy;   // finite stand-in for infinite extents in the cost
 
+    // Builds the tree over `cells` and returns its root node index.
     int build(std::vector<int>& cells, const std::vector<Box>& boxes) {
         ids_ = cells;
         boxes_ = &boxes;
-        return node(0, int(ids_.size()), 0);
+        return emit(0, int(ids_.size()), 0);
     }
 
   private:
@@ -700,14 +701,10 @@ class BvhBuilder {
         for (int k = 0; k < 3; ++k) e[k] = std::max(0.0, clampv(b.hi[k], k) - clampv(b.lo[k], k));
         return 2.0 * (e[0] * e[1] + e[1] * e[2] + e[2] * e[0]);
     }
-    int leaf(int lo, int hi) {
-        int first = int(leaf_cells.size());
-        for (int i = lo; i < hi; ++i) leaf_cells.push_back(ids_[size_t(i)]);
-        return ~((first << 4) | (hi - lo));
-    }
-    int node(int lo, int hi, int depth) {
+    // SAH split of [lo, hi): three equally spaced candidate planes per axis on
+    // the box centres, cost n_L area(L) + n_R area(R); median if none splits.
+    int split(int lo, int hi) {
         const int n = hi - lo;
-        if (n <= BVH_LEAF_MAX) return leaf(lo, hi);
         double cmin[3], cmax[3];
         for (int k = 0; k < 3; ++k) { cmin[k] = INF; cmax[k] = -INF; }
         for (int i = lo; i < hi; ++i)
@@ -735,34 +732,40 @@ class BvhBuilder {
                 if (cost < best_cost) { best_cost = cost; best_axis = k; best_plane = plane; }
             }
         }
-        int mid;
-        if (best_axis >= 0 && depth < BVH_STACK - 4) {
-            auto it = std::partition(ids_.begin() + lo, ids_.begin() + hi,
-                                     [&](int id) { return centre(id, best_axis) < best_plane; });
-            mid = int(it - ids_.begin());
-        } else {
-            // no useful split (all centres equal): halve the list
-            mid = lo + n / 2;
-        }
-        if (depth >= BVH_STACK - 4) {
-            // keep the stack bound: degenerate deep trees become wide leaves split in order
-            mid = lo + n / 2;
-        }
+        if (best_axis < 0) return lo + n / 2;
+        auto it = std::partition(ids_.begin() + lo, ids_.begin() + hi,
+                                 [&](int id) { return centre(id, best_axis) < best_plane; });
+        return int(it - ids_.begin());
+    }
+    int emit(int lo, int hi, int depth) {
         const int self = int(nodes.size());
-        nodes.push_back(BvhNode{});
-        Box bl = bound(lo, mid), br = bound(mid, hi);
-        int cl = node(lo, mid, depth + 1);
-        int cr = node(mid, hi, depth + 1);
-        BvhNode& nd = nodes[size_t(self)];
-        nd.lo0 = make_float4(f_down(bl.lo[0]), f_down(bl.lo[1]), f_down(bl.lo[2]), 0.f);
-        nd.hi0 = make_float4(f_up(bl.hi[0]), f_up(bl.hi[1]), f_up(bl.hi[2]), 0.f);
-        nd.lo1 = make_float4(f_down(br.lo[0]), f_down(br.lo[1]), f_down(br.lo[2]), 0.f);
-        nd.hi1 = make_float4(f_up(br.hi[0]), f_up(br.hi[1]), f_up(br.hi[2]), 0.f);
-        std::memcpy(&nd.lo0.w, &cl, 4);
-        std::memcpy(&nd.lo1.w, &cr, 4);
+        nodes.push_back(SkipNode{});
+        Box b = bound(lo, hi);
+        int leaf = -1;
+        if (hi - lo <= BVH_LEAF_MAX || depth > 60) {
+            int first = int(leaf_cells.size());
+            for (int i = lo; i < hi; ++i) leaf_cells.push_back(ids_[size_t(i)]);
+            leaf = (first << 4) | (hi - lo);
+        } else {
+            int mid = split(lo, hi);
+            emit(lo, mid, depth + 1);
+            emit(mid, hi, depth + 1);
+        }
+        SkipNode& nd = nodes[size_t(self)];
+        for (int k = 0; k < 3; ++k) { nd.lo[k] = f_down(b.lo[k]); nd.hi[k] = f_up(b.hi[k]); }
+        nd.leaf = leaf;
+        nd.skip = int(nodes.size());
         return self;
     }
 };
+
+// Order key of a double (see okey_bits): integer comparisons of keys agree
+// with IEEE comparisons of the values, -0 equal to +0.
+long long okey(double v) {
+    long long b;
+    std::memcpy(&b, &v, 8);
+    return okey_bits(b);
+}
 
 // ---------------------------------------------------------------------------
 // Flattening
@@ -844,8 +847,7 @@ int build_host(const char* json, size_t len, Built& B) {
             bvh.proxy.lo[k] = lo - m;
             bvh.proxy.hi[k] = hi + m;
         }
-        int r = bvh.build(ids, boxes);
-        U.bvh = r;
+        U.bvh = bvh.build(ids, boxes);
     }
     B.n_nodes = int(bvh.nodes.size());
 
@@ -859,14 +861,37 @@ int build_host(const char* json, size_t len, Built& B) {
         s_coef.push_back(s.c[2]);
         s_coef.push_back(s.type == S_CZ ? s.c[2] * s.c[2] : s.c[3]);
     }
-    std::vector<int2> c_range;
+    std::vector<long long> s_key;
+    for (auto& s : G.surf) s_key.push_back(s.type <= S_PZ ? okey(s.c[0]) : 0);
+    std::vector<int2> c_range, cs_adj;
     std::vector<int> cs, c_fill, c_off;
     std::vector<double> c_tr;
     std::vector<int4> u_info;
     for (auto& U : G.univ) {
-        for (auto& c : U.cells) {
+        // face adjacency: cells of this universe holding the same surface with
+        // the opposite sense whose boxes touch the cell's box
+        std::map<int, std::vector<std::pair<int, int>>> by_surf;
+        for (int ci = 0; ci < int(U.cells.size()); ++ci)
+            for (size_t k = 0; k < U.cells[size_t(ci)].surf.size(); ++k)
+                by_surf[U.cells[size_t(ci)].surf[k]].push_back({ci, U.cells[size_t(ci)].sense[k]});
+        auto overlap = [](const HCell& a, const HCell& b) {
+            for (int k = 0; k < 3; ++k)
+                if (a.box[k] > b.box[3 + k] || b.box[k] > a.box[3 + k]) return false;
+            return true;
+        };
+        for (int ci = 0; ci < int(U.cells.size()); ++ci) {
+            const HCell& c = U.cells[size_t(ci)];
             c_range.push_back(make_int2(int(cs.size()), int(c.surf.size())));
-            for (size_t i = 0; i < c.surf.size(); ++i) cs.push_back((c.surf[i] << 1) | (c.sense[i] > 0 ? 1 : 0));
+            for (size_t i = 0; i < c.surf.size(); ++i) {
+                const int type = G.surf[size_t(c.surf[i])].type;
+                cs.push_back((c.surf[i] << 4) | (type << 1) | (c.sense[i] > 0 ? 1 : 0));
+                std::vector<int> cand;
+                for (auto& pr : by_surf[c.surf[i]])
+                    if (pr.first != ci && pr.second == -c.sense[i] && overlap(c, U.cells[size_t(pr.first)]))
+                        cand.push_back(U.first_cell + pr.first);
+                if (cand.size() > 2) cs_adj.push_back(make_int2(-2, -2));
+                else cs_adj.push_back(make_int2(cand.size() > 0 ? cand[0] : -1, cand.size() > 1 ? cand[1] : -1));
+            }
             c_fill.push_back(c.fill);
             c_off.push_back(int(c.off));
             for (int d = 0; d < 3; ++d) c_tr.push_back(c.tr[d]);
@@ -875,6 +900,7 @@ int build_host(const char* json, size_t len, Built& B) {
     }
     std::vector<int4> l_dim, l_off;
     std::vector<double> l_grid, l_ctr;
+    std::vector<long long> l_gkey;
     std::vector<int> l_fill, l_eoff, l_pscale;
     for (auto& U : G.univ) {
         if (U.type != UT_RECT) continue;
@@ -884,7 +910,7 @@ int build_host(const char* json, size_t len, Built& B) {
         for (int d = 0; d < 3; ++d) {
             n[d] = int(U.grid[d].size()) - 1;
             go[d] = int(l_grid.size());
-            for (double g : U.grid[d]) l_grid.push_back(g);
+            for (double g : U.grid[d]) { l_grid.push_back(g); l_gkey.push_back(okey(g)); }
             for (int i = 0; i < n[d]; ++i) l_ctr.push_back((U.grid[d][size_t(i)] + U.grid[d][size_t(i) + 1]) * 0.5);
             l_ctr.push_back(0.0);   // keep l_ctr aligned with l_grid offsets
         }
@@ -898,13 +924,13 @@ int build_host(const char* json, size_t len, Built& B) {
         l_pscale.push_back(U.pscale);
     }
     if (l_dim.empty()) { l_dim.push_back(make_int4(0, 0, 0, 0)); l_off.push_back(make_int4(0, 0, 0, 0)); l_pscale.push_back(0); }
-    if (l_grid.empty()) { l_grid.push_back(0); l_ctr.push_back(0); }
+    if (l_grid.empty()) { l_grid.push_back(0); l_ctr.push_back(0); l_gkey.push_back(0); }
     if (l_fill.empty()) { l_fill.push_back(0); l_eoff.push_back(0); }
-    std::vector<BvhNode> nodes = bvh.nodes;
+    std::vector<SkipNode> nodes = bvh.nodes;
     std::vector<int> leaf = bvh.leaf_cells;
-    if (nodes.empty()) nodes.push_back(BvhNode{});
+    if (nodes.empty()) nodes.push_back(SkipNode{});
     if (leaf.empty()) leaf.push_back(0);
-    if (cs.empty()) cs.push_back(0);
+    if (cs.empty()) { cs.push_back(0); cs_adj.push_back(make_int2(-1, -1)); }
 
     Layout L;
     size_t* o = B.offs;
@@ -923,9 +949,12 @@ int build_host(const char* json, size_t len, Built& B) {
     o[12] = L.put(l_fill.size() * 4);
     o[13] = L.put(l_eoff.size() * 4);
     o[14] = L.put(l_pscale.size() * 4);
-    o[15] = L.put(nodes.size() * sizeof(BvhNode));
+    o[15] = L.put(nodes.size() * sizeof(SkipNode));
     o[16] = L.put(leaf.size() * 4);
     o[17] = L.put(G.sigma.size() * 8);
+    o[18] = L.put(s_key.size() * 8);
+    o[19] = L.put(cs_adj.size() * sizeof(int2));
+    o[20] = L.put(l_gkey.size() * 8);
     B.image.assign(L.total, 0);
     copy_into(B.image, o[0], s_info);
     copy_into(B.image, o[1], s_coef);
@@ -945,6 +974,9 @@ int build_host(const char* json, size_t len, Built& B) {
     copy_into(B.image, o[15], nodes);
     copy_into(B.image, o[16], leaf);
     copy_into(B.image, o[17], G.sigma);
+    copy_into(B.image, o[18], s_key);
+    copy_into(B.image, o[19], cs_adj);
+    copy_into(B.image, o[20], l_gkey);
     return TRK_OK;
 }
 
@@ -1012,9 +1044,12 @@ trk_status geometry_build(const char* json, size_t len, void* dev_buf, size_t* d
     d.l_fill = reinterpret_cast<const int*>(base + o[12]);
     d.l_eoff = reinterpret_cast<const int*>(base + o[13]);
     d.l_pscale = reinterpret_cast<const int*>(base + o[14]);
-    d.nodes = reinterpret_cast<const BvhNode*>(base + o[15]);
+    d.nodes = reinterpret_cast<const SkipNode*>(base + o[15]);
     d.leaf_cells = reinterpret_cast<const int*>(base + o[16]);
     d.sigma = reinterpret_cast<const double*>(base + o[17]);
+    d.s_key = reinterpret_cast<const long long*>(base + o[18]);
+    d.cs_adj = reinterpret_cast<const int2*>(base + o[19]);
+    d.l_gkey = reinterpret_cast<const long long*>(base + o[20]);
     const HGeom& G = B.G;
     for (int k = 0; k < 3; ++k) { d.src_lo[k] = G.src[k]; d.src_hi[k] = G.src[3 + k]; }
     d.root = G.root;

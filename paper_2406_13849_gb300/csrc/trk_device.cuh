@@ -1,0 +1,579 @@
+// trk_device.cuh - device side of the nested-geometry trackers (sm_103a).
+//
+// Paper: arXiv 2406.13849, Table 1 (find_cell, distance_to_surface,
+// move_within_cell, cross_surface, change_direction), Alg. 2-10, Sec. 4.3.
+//
+// GB300 notes.  The FP64 pipe issues one warp instruction per ~16 SM cycles,
+// whatever the active mask; it is the scarce unit.  So:
+//  - every FP64 comparison is done as an integer comparison of order keys
+//    (okey: the IEEE bit pattern made monotone, -0 equal to +0), exact for
+//    non-NaN values, on the integer pipe;
+//  - axis-plane senses compare the point's key against the plane's stored
+//    key: no FP64 instruction at all;
+//  - BVH boxes are FP32, and the point's FP32 bounds (round down / up) are
+//    produced from its bits with integer operations;
+//  - only the arithmetic of the reference formulas runs on the FP64 pipe,
+//    in the reference's order (bit-exact in the --fmad=false build).
+#pragma once
+#include <cstdint>
+
+#include "trk.h"
+#include "trk_internal.h"
+
+namespace trk {
+namespace dev {
+
+constexpr double DINF = __builtin_huge_val();
+constexpr int MAXMAT = 8;
+
+// ---------------------------------------------------------------------------
+// Exact comparisons on the integer pipe
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ long long okey(double x) { return okey_bits(dbits(x)); }
+__device__ __forceinline__ bool d_lt(double a, double b) { return okey(a) < okey(b); }
+__device__ __forceinline__ bool d_gt0(double x) { return dbits(x) > 0; }
+__device__ __forceinline__ bool d_lt0(double x) { const long long b = dbits(x); return b < 0 && b != (long long)0x8000000000000000ULL; }
+__device__ __forceinline__ bool d_ge0(double x) { return !d_lt0(x); }
+__device__ __forceinline__ bool d_le0(double x) { return !d_gt0(x); }
+__device__ __forceinline__ bool d_eq0(double x) { return (dbits(x) & 0x7fffffffffffffffLL) == 0; }
+__device__ __forceinline__ bool d_finite_lt_inf(double x) { return okey(x) < 0x7ff0000000000000LL; }
+
+// FP32 bounds lo <= x <= hi from the bits of x (integer operations only).
+__device__ __forceinline__ void f32_bounds(double x, float& lo, float& hi) {
+    const unsigned long long b = (unsigned long long)dbits(x);
+    const unsigned sign = unsigned(b >> 63);
+    const int e = int((b >> 52) & 0x7ff) - 1023 + 127;
+    if (e >= 255) {
+        lo = sign ? -__int_as_float(0x7f800000) : __int_as_float(0x7f7fffff);
+        hi = sign ? -__int_as_float(0x7f7fffff) : __int_as_float(0x7f800000);
+        return;
+    }
+    if (e <= 0) {
+        lo = -__int_as_float(0x00800000);
+        hi = __int_as_float(0x00800000);
+        return;
+    }
+    const unsigned t = (sign << 31) | (unsigned(e) << 23) | unsigned((b >> 29) & 0x7fffff);
+    const unsigned away = t + ((b & 0x1fffffffULL) ? 1u : 0u);
+    if (sign) { lo = __uint_as_float(away); hi = __uint_as_float(t); }
+    else { lo = __uint_as_float(t); hi = __uint_as_float(away); }
+}
+
+// ---------------------------------------------------------------------------
+// Random numbers: Philox4x32-10 (Salmon et al., SC'11), counter
+// (particle id, event, tag, k), key (seed_lo32, geometry id); two doubles in
+// (0, 1] per call: ((u64 >> 11) + 1) * 2^-53.
+// ---------------------------------------------------------------------------
+enum { TAG_POSITION = 0, TAG_DIRECTION = 1, TAG_SCALARS = 2 };
+
+__device__ __forceinline__ uint4 philox10(uint4 c, uint2 k) {
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k.x += W0; k.y += W1; }
+        const uint32_t lo0 = M0 * c.x, hi0 = __umulhi(M0, c.x);
+        const uint32_t lo1 = M1 * c.z, hi1 = __umulhi(M1, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+__device__ __forceinline__ void uniform2(uint32_t pid, uint32_t event, uint32_t tag, uint32_t k, uint32_t seed_lo,
+                                         uint32_t gid, double& a, double& b) {
+    const uint4 o = philox10(make_uint4(pid, event, tag, k), make_uint2(seed_lo, gid));
+    const uint64_t ua = (uint64_t(o.y) << 32) | o.x;
+    const uint64_t ub = (uint64_t(o.w) << 32) | o.z;
+    a = double((ua >> 11) + 1) * 0x1.0p-53;
+    b = double((ub >> 11) + 1) * 0x1.0p-53;
+}
+
+// log x from + - * / only: x = 2^k m, m in [sqrt(1/2), sqrt 2), s = (m-1)/(m+1),
+// log m = 2 s (1 + z/3 + z^2/5 + ... + z^13/27), z = s^2 (Horner, highest
+// first); log x = k LN2_HI + (log m + k LN2_LO), LN2_HI = ln 2 to 33 bits.
+__device__ __forceinline__ double own_log(double x) {
+    const uint64_t bits = uint64_t(dbits(x));
+    int k = int((bits >> 52) & 0x7ff) - 1023;
+    double m = __longlong_as_double((long long)((bits & 0x000fffffffffffffULL) | 0x3ff0000000000000ULL));
+    if (dbits(m) > dbits(1.4142135623730951)) { m = m * 0.5; k += 1; }
+    const double s = (m - 1.0) / (m + 1.0);
+    const double z = s * s;
+    double p = 0x1.2f684bda12f68p-5;                 // 1/27
+    p = p * z + 0x1.47ae147ae147bp-5;                // 1/25
+    p = p * z + 0x1.642c8590b2164p-5;                // 1/23
+    p = p * z + 0x1.8618618618618p-5;                // 1/21
+    p = p * z + 0x1.af286bca1af28p-5;                // 1/19
+    p = p * z + 0x1.e1e1e1e1e1e1ep-5;                // 1/17
+    p = p * z + 0x1.1111111111111p-4;                // 1/15
+    p = p * z + 0x1.3b13b13b13b14p-4;                // 1/13
+    p = p * z + 0x1.745d1745d1746p-4;                // 1/11
+    p = p * z + 0x1.c71c71c71c71cp-4;                // 1/9
+    p = p * z + 0x1.2492492492492p-3;                // 1/7
+    p = p * z + 0x1.999999999999ap-3;                // 1/5
+    p = p * z + 0x1.5555555555555p-2;                // 1/3
+    p = p * z + 1.0;
+    const double logm = (s + s) * p;
+    const double kd = double(k);
+    return kd * 0x1.62e42fefp-1 + (logm + kd * 0x1.473de6af278edp-34);
+}
+
+// Marsaglia (1972): u, v in (-1, 1], accept 0 < s = u^2+v^2 < 1,
+// Omega = (u f, v f, 1 - 2 s), f = 2 sqrt(1 - s); attempt k uses counter
+// (pid, event, TAG_DIRECTION, k), at most 64 attempts.
+__device__ __forceinline__ bool isotropic(uint32_t pid, uint32_t event, uint32_t seed_lo, uint32_t gid, double& ou,
+                                          double& ov, double& ow) {
+    for (uint32_t k = 0; k < 64; ++k) {
+        double xa, xb;
+        uniform2(pid, event, TAG_DIRECTION, k, seed_lo, gid, xa, xb);
+        const double u = 2.0 * xa - 1.0;
+        const double v = 2.0 * xb - 1.0;
+        const double s = u * u + v * v;
+        if (d_gt0(s) && dbits(s) < dbits(1.0)) {
+            const double f = 2.0 * sqrt(1.0 - s);
+            ou = u * f;
+            ov = v * f;
+            ow = 1.0 - 2.0 * s;
+            return true;
+        }
+    }
+    return false;
+}
+
+__device__ __forceinline__ uint64_t fnv(uint64_t h, uint64_t w) { return (h ^ w) * 0x100000001b3ULL; }
+constexpr uint64_t FNV0 = 0xcbf29ce484222325ULL;
+
+// ---------------------------------------------------------------------------
+// Geometry access
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void load_coef(const DevGeom& g, int s, double& c0, double& c1, double& c2, double& c3) {
+    const double2* p = reinterpret_cast<const double2*>(g.s_coef + 4 * s);
+    const double2 a = __ldg(p), b = __ldg(p + 1);
+    c0 = a.x; c1 = a.y; c2 = b.x; c3 = b.y;
+}
+
+// Point with precomputed order keys of its coordinates.
+struct Pt {
+    double x, y, z;
+    long long kx, ky, kz;
+};
+__device__ __forceinline__ Pt make_pt(double x, double y, double z) {
+    Pt p;
+    p.x = x; p.y = y; p.z = z;
+    p.kx = okey(x); p.ky = okey(y); p.kz = okey(z);
+    return p;
+}
+
+// Sense of the point relative to surface s (entry type `type`): f >= 0 is "+".
+//   px: x - g >= 0 <=> x >= g (integer key compare);
+//   p: ((nx x + ny y) + nz z) - d;  cz: (qx qx + qy qy) - r r.
+__device__ __forceinline__ int sense_at(const DevGeom& g, int s, int type, const Pt& p) {
+    if (type <= S_PZ) {
+        const long long kg = __ldg(g.s_key + s);
+        const long long kp = type == S_PX ? p.kx : (type == S_PY ? p.ky : p.kz);
+        return kp >= kg ? 1 : -1;
+    }
+    double c0, c1, c2, c3;
+    load_coef(g, s, c0, c1, c2, c3);
+    double f;
+    if (type == S_P) {
+        f = ((c0 * p.x + c1 * p.y) + c2 * p.z) - c3;
+    } else {
+        const double qx = p.x - c0, qy = p.y - c1;
+        f = (qx * qx + qy * qy) - c3;
+    }
+    return d_ge0(f) ? 1 : -1;
+}
+
+// Distance to surface s, leaving its `side` (+1/-1) of it; `on` is the logical
+// on-surface state.  Negative results (a point a rounding error outside the
+// cell) become 0; INF means no hit.
+//  planes: only the face the direction leaves through is a candidate;
+//    px: t = (g - x) * inv_u; p: t = (d - ((nx x + ny y) + nz z)) /
+//    ((nx u + ny v) + nz w); a plane the particle is on is never hit again.
+//  cz: a = u u + v v, b = qx u + qy v; on it and logically inside:
+//    t = -2 b / a if b < 0, else no hit; on it and outside: no hit;
+//    otherwise c = f, disc = b b - a c, no hit if a == 0 or disc <= 0;
+//    inside: t = b <= 0 ? (-b + sqrt disc) / a : -c / (b + sqrt disc);
+//    outside: hit only if b < 0, t = c / (-b + sqrt disc).
+struct Dir {
+    double u, v, w, iu, iv, iw;
+};
+
+__device__ __forceinline__ double surface_distance(const DevGeom& g, int s, int type, int side, bool on,
+                                                   double x, double y, double z, const Dir& d) {
+    double t;
+    if (type <= S_PZ) {
+        if (on) return DINF;
+        const double dd = type == S_PX ? d.u : (type == S_PY ? d.v : d.w);
+        const bool leaves = side > 0 ? d_lt0(dd) : d_gt0(dd);
+        if (!leaves) return DINF;
+        const double gval = __ldg(g.s_coef + 4 * s);
+        const double xx = type == S_PX ? x : (type == S_PY ? y : z);
+        const double ii = type == S_PX ? d.iu : (type == S_PY ? d.iv : d.iw);
+        t = (gval - xx) * ii;
+    } else if (type == S_P) {
+        if (on) return DINF;
+        double c0, c1, c2, c3;
+        load_coef(g, s, c0, c1, c2, c3);
+        const double den = (c0 * d.u + c1 * d.v) + c2 * d.w;
+        const bool leaves = side > 0 ? d_lt0(den) : d_gt0(den);
+        if (!leaves) return DINF;
+        const double num = c3 - ((c0 * x + c1 * y) + c2 * z);
+        t = num / den;
+    } else {
+        double c0, c1, c2, c3;
+        load_coef(g, s, c0, c1, c2, c3);
+        const double qx = x - c0, qy = y - c1;
+        const double a = d.u * d.u + d.v * d.v;
+        const double b = qx * d.u + qy * d.v;
+        if (on) {
+            if (side < 0 && d_lt0(b)) t = (-2.0 * b) / a;
+            else return DINF;
+        } else {
+            const double c = (qx * qx + qy * qy) - c3;
+            if (d_eq0(a)) return DINF;
+            const double disc = b * b - a * c;
+            if (d_le0(disc)) return DINF;
+            const double sq = sqrt(disc);
+            if (side < 0) {
+                t = d_le0(b) ? (-b + sq) / a : -c / (b + sq);
+            } else {
+                if (!d_lt0(b)) return DINF;
+                t = c / (-b + sq);
+            }
+        }
+    }
+    if (d_lt0(t)) t = 0.0;
+    return t;
+}
+
+// Cell test: all senses hold; the crossed surface xs (if >= 0) is taken
+// logically with sense xsn instead of being evaluated.
+__device__ __forceinline__ bool cell_holds(const DevGeom& g, int c, const Pt& p, int xs, int xsn) {
+    const int2 rg = __ldg(g.c_range + c);
+    for (int k = 0; k < rg.y; ++k) {
+        const int e = __ldg(g.cs + rg.x + k);
+        const int s = cs_surface(e), sn = cs_side(e);
+        if (s == xs) {
+            if (sn != xsn) return false;
+        } else if (sense_at(g, s, cs_type(e), p) != sn) {
+            return false;
+        }
+    }
+    return true;
+}
+
+// First cell of universe u (CSG view) holding the point, excluding cell `ex`:
+// linear scan for small universes (Alg. 3/4), otherwise a stackless walk of
+// the universe's BVH in preorder that stops at the first hit (Sec. 4.3).
+__device__ __forceinline__ int csg_search(const DevGeom& g, int u, const Pt& p, int ex, int xs, int xsn) {
+    const int4 ui = __ldg(g.u_info + u);
+    if (ui.z < 0) {
+        for (int c = ui.x; c < ui.x + ui.y; ++c) {
+            if (c == ex) continue;
+            if (cell_holds(g, c, p, xs, xsn)) return c;
+        }
+        return -1;
+    }
+    float xl, xh, yl, yh, zl, zh;
+    f32_bounds(p.x, xl, xh);
+    f32_bounds(p.y, yl, yh);
+    f32_bounds(p.z, zl, zh);
+    int i = ui.z;
+    const int end = __ldg(&g.nodes[i].skip);
+    while (i < end) {
+        const float4* np = reinterpret_cast<const float4*>(g.nodes + i);
+        const float4 a = __ldg(np), b = __ldg(np + 1);
+        const bool in = xh >= a.x && xl <= b.x && yh >= a.y && yl <= b.y && zh >= a.z && zl <= b.z;
+        if (!in) {
+            i = __float_as_int(a.w);
+            continue;
+        }
+        const int leaf = __float_as_int(b.w);
+        if (leaf >= 0) {
+            const int first = leaf >> 4, cnt = leaf & 15;
+            for (int k = 0; k < cnt; ++k) {
+                const int c = __ldg(g.leaf_cells + first + k);
+                if (c != ex && cell_holds(g, c, p, xs, xsn)) return c;
+            }
+        }
+        ++i;
+    }
+    return -1;
+}
+
+// Alg. 5: element index in one dimension by binary search on the planes'
+// order keys; element i holds g_i <= x < g_{i+1}; a root array has nothing
+// outside [g_0, g_n), a non-root array clamps.
+__device__ __forceinline__ int rect_index(const long long* gk, int n, long long kx, bool root) {
+    if (root && (!(__ldg(gk) <= kx) || !(kx < __ldg(gk + n)))) return -1;
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(gk + mid) <= kx) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------------------
+// Particle state (registers)
+// ---------------------------------------------------------------------------
+struct Lv {
+    int u, cell, i, j, k, off;
+    double tx, ty, tz;
+};
+
+struct St {
+    double x, y, z, tau;
+    Dir d;
+    int nlev, on_lev, on_surf, mat;
+    Lv lv[MAXL];
+};
+
+__device__ __forceinline__ void set_inverse(Dir& d) {
+    d.iu = 1.0 / d.u;
+    d.iv = 1.0 / d.v;
+    d.iw = 1.0 / d.w;
+}
+
+__device__ __forceinline__ void clear_levels(St& s) {
+    s.nlev = 0; s.mat = 0; s.on_lev = -1; s.on_surf = -1;
+#pragma unroll
+    for (int l = 0; l < MAXL; ++l) {
+        s.lv[l].u = 0; s.lv[l].cell = 0; s.lv[l].i = s.lv[l].j = s.lv[l].k = 0; s.lv[l].off = 0;
+        s.lv[l].tx = s.lv[l].ty = s.lv[l].tz = 0.0;
+    }
+}
+
+__device__ __forceinline__ int instance(const St& s) {
+    int t = 0;
+#pragma unroll
+    for (int l = 0; l < MAXL; ++l)
+        if (l < s.nlev) t += s.lv[l].off;
+    return t;
+}
+
+// Local position at level `lev`: global minus translations of levels
+// 0..lev-1, component by component in level order.
+__device__ __forceinline__ void local_at(const St& s, int lev, double& x, double& y, double& z) {
+    x = s.x; y = s.y; z = s.z;
+#pragma unroll
+    for (int l = 0; l < MAXL - 1; ++l) {
+        if (l < lev) { x = x - s.lv[l].tx; y = y - s.lv[l].ty; z = z - s.lv[l].tz; }
+    }
+}
+
+// Sets level L to rect element (i,j,k) of lattice `lat`; returns the daughter.
+__device__ __forceinline__ int enter_element(const DevGeom& g, Lv& L, int lat, int i, int j, int k) {
+    const int4 dm = __ldg(g.l_dim + lat), of = __ldg(g.l_off + lat);
+    const int e = i + dm.x * (j + dm.y * k);
+    L.i = i; L.j = j; L.k = k;
+    L.cell = e;
+    L.off = __ldg(g.l_eoff + of.w + e);
+    L.tx = __ldg(g.l_ctr + of.x + i);
+    L.ty = __ldg(g.l_ctr + of.y + j);
+    L.tz = __ldg(g.l_ctr + of.z + k);
+    return __ldg(g.l_fill + of.w + e);
+}
+
+__device__ __forceinline__ int enter_cell(const DevGeom& g, Lv& L, int c) {
+    L.cell = c;
+    L.off = __ldg(g.c_off + c);
+    L.tx = __ldg(g.c_tr + 3 * c);
+    L.ty = __ldg(g.c_tr + 3 * c + 1);
+    L.tz = __ldg(g.c_tr + 3 * c + 2);
+    return __ldg(g.c_fill + c);
+}
+
+// Alg. 7 from level `start` downward (rect view for rect arrays unless CSG).
+// Returns 0 on success, -1 if no cell holds the point.
+template <bool CSG>
+__device__ __forceinline__ int find_from(const DevGeom& g, St& s, int start) {
+    double x, y, z;
+    local_at(s, start, x, y, z);
+#pragma unroll
+    for (int l = 0; l < MAXL; ++l) {
+        if (l < start) continue;
+        Lv& L = s.lv[l];
+        const int4 ui = __ldg(g.u_info + L.u);
+        const Pt p = make_pt(x, y, z);
+        int dau;
+        if (!CSG && ui.w >= 0) {
+            const int4 dm = __ldg(g.l_dim + ui.w), of = __ldg(g.l_off + ui.w);
+            const bool root = (l == 0);
+            const int i = rect_index(g.l_gkey + of.x, dm.x, p.kx, root);
+            const int j = rect_index(g.l_gkey + of.y, dm.y, p.ky, root);
+            const int k = rect_index(g.l_gkey + of.z, dm.z, p.kz, root);
+            if (i < 0 || j < 0 || k < 0) return -1;
+            dau = enter_element(g, L, ui.w, i, j, k);
+        } else {
+            const int c = csg_search(g, L.u, p, -1, -1, 0);
+            if (c < 0) return -1;
+            dau = enter_cell(g, L, c);
+        }
+        if (dau < 0) {
+            s.nlev = l + 1;
+            s.mat = ~dau;
+            return 0;
+        }
+        if (l + 1 >= MAXL) return -1;
+        x = x - L.tx; y = y - L.ty; z = z - L.tz;
+        s.lv[l + 1 < MAXL ? l + 1 : l].u = dau;
+    }
+    return -1;
+}
+
+struct Hit {
+    double d;
+    int level, surf, side, dim, dsign, entry;
+};
+
+// distance_to_surface over the levels, top to bottom, strict '<' (the
+// top-most level wins ties); rect levels: x, y, z faces in the direction of
+// flight, outer faces only at the root; CSG levels: the cell's surfaces in
+// cell order.
+template <bool CSG>
+__device__ __forceinline__ Hit distance_to_boundary(const DevGeom& g, const St& s) {
+    Hit h;
+    h.d = DINF; h.level = -1; h.surf = -1; h.side = 0; h.dim = -1; h.dsign = 0; h.entry = -1;
+    long long hk = okey(DINF);
+    double x = s.x, y = s.y, z = s.z;
+#pragma unroll
+    for (int l = 0; l < MAXL; ++l) {
+        if (l >= s.nlev) break;
+        if (l > 0) { x = x - s.lv[l - 1].tx; y = y - s.lv[l - 1].ty; z = z - s.lv[l - 1].tz; }
+        const Lv& L = s.lv[l];
+        const int4 ui = __ldg(g.u_info + L.u);
+        if (!CSG && ui.w >= 0) {
+            const int4 dm = __ldg(g.l_dim + ui.w), of = __ldg(g.l_off + ui.w);
+            const int n3[3] = {dm.x, dm.y, dm.z};
+            const int o3[3] = {of.x, of.y, of.z};
+            const int i3[3] = {L.i, L.j, L.k};
+            const double p3[3] = {x, y, z};
+            const double d3[3] = {s.d.u, s.d.v, s.d.w};
+            const double v3[3] = {s.d.iu, s.d.iv, s.d.iw};
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                double t = DINF;
+                int sg = 0;
+                if (d_gt0(d3[d])) {
+                    if (i3[d] < n3[d] - 1 || l == 0) { t = (__ldg(g.l_grid + o3[d] + i3[d] + 1) - p3[d]) * v3[d]; sg = 1; }
+                } else if (d_lt0(d3[d])) {
+                    if (i3[d] > 0 || l == 0) { t = (__ldg(g.l_grid + o3[d] + i3[d]) - p3[d]) * v3[d]; sg = -1; }
+                }
+                if (sg != 0) {
+                    if (d_lt0(t)) t = 0.0;
+                    const long long tk = okey(t);
+                    if (tk < hk) {
+                        hk = tk; h.d = t; h.level = l; h.surf = -1 - (2 * d + (sg > 0)); h.dim = d; h.dsign = sg; h.side = 0;
+                    }
+                }
+            }
+        } else {
+            const int2 rg = __ldg(g.c_range + L.cell);
+            for (int k = 0; k < rg.y; ++k) {
+                const int e = __ldg(g.cs + rg.x + k);
+                const int sid = cs_surface(e), side = cs_side(e);
+                const bool on = (s.on_lev == l && s.on_surf == sid);
+                const double t = surface_distance(g, sid, cs_type(e), side, on, x, y, z, s.d);
+                const long long tk = okey(t);
+                if (tk < hk) { hk = tk; h.d = t; h.level = l; h.surf = sid; h.side = side; h.dim = -1; h.dsign = 0; h.entry = rg.x + k; }
+            }
+        }
+    }
+    return h;
+}
+
+enum { CR_OK = 0, CR_REFLECT = 1, CR_ESCAPE = 2, CR_LOST = 3, CR_FIND = 4 };
+
+__device__ __forceinline__ void reflect_plane(const DevGeom& g, St& s, int sid, int dim) {
+    int type = dim;
+    if (sid >= 0) type = __ldg(g.s_info + sid) & 15;
+    if (type == S_PX) s.d.u = -s.d.u;
+    else if (type == S_PY) s.d.v = -s.d.v;
+    else if (type == S_PZ) s.d.w = -s.d.w;
+    else {
+        double c0, c1, c2, c3;
+        load_coef(g, sid, c0, c1, c2, c3);
+        const double nd = (c0 * s.d.u + c1 * s.d.v) + c2 * s.d.w;
+        const double nn = (c0 * c0 + c1 * c1) + c2 * c2;
+        const double k = (2.0 * nd) / nn;
+        s.d.u = s.d.u - k * c0;
+        s.d.v = s.d.v - k * c1;
+        s.d.w = s.d.w - k * c2;
+    }
+    set_inverse(s.d);
+}
+
+// Alg. 4 with face adjacency: the cells on the far side of the crossed face
+// (precomputed from box overlap) are tried first; if none holds the point
+// the whole universe is searched.  In a geometry whose cells partition space
+// the holding cell is unique, so the result equals the linear scan's.
+__device__ __forceinline__ int csg_cross_search(const DevGeom& g, int u, int cell, const Pt& p, int xs, int xsn,
+                                                int entry) {
+    if (entry >= 0) {
+        const int2 adj = __ldg(g.cs_adj + entry);
+        if (adj.x >= 0 && cell_holds(g, adj.x, p, xs, xsn)) return adj.x;
+        if (adj.y >= 0 && cell_holds(g, adj.y, p, xs, xsn)) return adj.y;
+    }
+    return csg_search(g, u, p, cell, xs, xsn);
+}
+
+// Alg. 8 at the hit's level (Alg. 4 for CSG, Alg. 6 for rect).  Returns
+// CR_FIND when the levels below the crossing must be found again (the
+// caller runs find_from(find_level)), else a final result.
+template <bool CSG>
+__device__ __forceinline__ int cross_surface(const DevGeom& g, St& s, const Hit& h, int& find_level) {
+    find_level = -1;
+    int result = CR_LOST;
+#pragma unroll
+    for (int l = 0; l < MAXL; ++l) {
+        if (l != h.level) continue;
+        Lv& L = s.lv[l];
+        const int4 ui = __ldg(g.u_info + L.u);
+        s.on_lev = l;
+        s.on_surf = h.surf;
+        int dau;
+        if (!CSG && ui.w >= 0) {
+            int ijk[3] = {L.i, L.j, L.k};
+            const int4 dm = __ldg(g.l_dim + ui.w);
+            const int n3[3] = {dm.x, dm.y, dm.z};
+            int ni = 0, nn = 1;
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+                if (d == h.dim) { ijk[d] += h.dsign; ni = ijk[d]; nn = n3[d]; }
+            if (ni < 0 || ni >= nn) {
+                if (l != 0) return CR_LOST;
+                const int bc = (dm.w >> (2 * (2 * h.dim + (h.dsign > 0)))) & 3;
+                if (bc == BC_REFLECT) { reflect_plane(g, s, -1, h.dim); return CR_REFLECT; }
+                return CR_ESCAPE;
+            }
+            dau = enter_element(g, L, ui.w, ijk[0], ijk[1], ijk[2]);
+        } else {
+            double x, y, z;
+            local_at(s, l, x, y, z);
+            const Pt p = make_pt(x, y, z);
+            const int c = csg_cross_search(g, L.u, L.cell, p, h.surf, -h.side, h.entry);
+            if (c < 0) {
+                if (l != 0) return CR_LOST;
+                const int bc = (__ldg(g.s_info + h.surf) >> 4) & 3;
+                if (bc == BC_REFLECT) { reflect_plane(g, s, h.surf, -1); return CR_REFLECT; }
+                return CR_ESCAPE;
+            }
+            dau = enter_cell(g, L, c);
+        }
+        if (dau < 0) {
+            s.nlev = l + 1;
+            s.mat = ~dau;
+            return CR_OK;
+        }
+        if (l + 1 < MAXL) s.lv[l + 1 < MAXL ? l + 1 : l].u = dau;
+        find_level = l + 1;
+        result = CR_FIND;
+    }
+    return result;
+}
+
+}  // namespace dev
+}  // namespace trk

@@ -13,6 +13,12 @@
 #include <stdint.h>
 #include <cuda_runtime.h>
 
+#ifdef __CUDACC__
+#define TRK_HD_INLINE __host__ __device__ __forceinline__
+#else
+#define TRK_HD_INLINE inline
+#endif
+
 namespace trk {
 
 enum SurfType { S_PX = 0, S_PY = 1, S_PZ = 2, S_P = 3, S_CZ = 4 };
@@ -20,42 +26,55 @@ enum Bc { BC_NONE = 0, BC_VACUUM = 1, BC_REFLECT = 2 };
 
 // Compiled nesting depth of the trackers' register-resident level stack.
 constexpr int MAXL = 4;
-// Cells per BVH leaf at most, and BVH traversal stack depth.
+// Cells per BVH leaf at most.
 constexpr int BVH_LEAF_MAX = 4;
-constexpr int BVH_STACK = 32;
 // Universes with at most this many cells are scanned linearly (Alg. 3).
 constexpr int LINEAR_MAX = 4;
 
-// BVH2 node holding both children's boxes (FP32, rounded outward).  The
-// child references sit in the w lanes of lo0 / lo1 as int bits:
-//   ref >= 0  internal node index
-//   ref <  0  leaf: ~ref = (first leaf slot << 4) | count
-struct alignas(16) BvhNode {
-    float4 lo0, hi0, lo1, hi1;
+// BVH node in depth-first preorder ("skip list"): a traversal visits node i;
+// if the point is in its box it continues at i + 1 (first child, or the next
+// subtree after a leaf), otherwise at `skip` (the node after i's subtree).
+// Boxes are FP32, rounded outward from padded FP64 cell boxes.
+//   leaf < 0   internal node
+//   leaf >= 0  leaf: (first leaf slot << 4) | count
+struct alignas(16) SkipNode {
+    float lo[3];
+    int skip;
+    float hi[3];
+    int leaf;
 };
+
+// Packed cell-surface entry: (surface << 4) | (type << 1) | (sense > 0).
+TRK_HD_INLINE int cs_surface(int e) { return e >> 4; }
+TRK_HD_INLINE int cs_type(int e) { return (e >> 1) & 7; }
+TRK_HD_INLINE int cs_side(int e) { return (e & 1) ? 1 : -1; }
 
 struct DevGeom {
     // surfaces
     const int* s_info;        // type | (bc << 4) | (rparam+1) << 8 | pscale << 12
     const double* s_coef;     // 4 per surface; px/py/pz: (g,0,0,0); p: (nx,ny,nz,d); cz: (x0,y0,r,r*r)
+    const long long* s_key;   // order key of g for px/py/pz (sense tests as integer compares)
     // cells (CSG view)
     const int2* c_range;      // (first, count) into cs
-    const int* cs;            // (surface << 1) | (sense > 0)
+    const int* cs;            // packed cell-surface entries (see cs_surface / cs_type / cs_side)
+    const int2* cs_adj;       // per entry: up to two cells on the far side of that face, -1 none,
+                              // (-2,-2) too many (search the BVH directly)
     const int* c_fill;        // >= 0 daughter universe; < 0 material ~fill
     const double* c_tr;       // translation into the daughter, 3 per cell
     const int* c_off;         // leaf-instance offset of the cell
     // universes
-    const int4* u_info;       // (first cell, cell count, BVH root or -1, rect lattice or -1)
+    const int4* u_info;       // (first cell, cell count, BVH root node or -1, rect lattice or -1)
     // rect arrays (rect view)
     const int4* l_dim;        // (nx, ny, nz, packed bc: 2 bits per face xlo..zhi)
     const int4* l_off;        // (x grid offset, y grid offset, z grid offset, element offset)
     const double* l_grid;     // grid planes; dim d of lattice k at l_grid[l_off[k].d]
+    const long long* l_gkey;  // order keys of the grid planes, same offsets
     const double* l_ctr;      // element centres (g_i + g_{i+1}) * 0.5, same offsets
     const int* l_fill;        // element universe, at l_fill[l_off[k].w + e]
     const int* l_eoff;        // element instance offset, same indexing
     const int* l_pscale;      // grid planes scale with the pitch (gradient)
-    // BVH
-    const BvhNode* nodes;
+    // BVH (skip-list preorder per universe)
+    const SkipNode* nodes;
     const int* leaf_cells;
     // materials
     const double* sigma;
@@ -63,6 +82,12 @@ struct DevGeom {
     int root, n_inst, n_mat, gid, max_depth, n_univ, n_cells, n_surf;
     int rect_ok;              // no hex arrays: the rect tracker applies
 };
+
+// Order key of a double: a < b  <=>  okey(a) < okey(b) for non-NaN values,
+// with -0 and +0 equal (IEEE).  Lets FP64 comparisons run on the integer pipe.
+TRK_HD_INLINE long long okey_bits(long long b) {
+    return b < 0 ? -(b & 0x7fffffffffffffffLL) : b;
+}
 
 // Particle buffer written by source_init (structure of arrays).
 struct ParticlesView {

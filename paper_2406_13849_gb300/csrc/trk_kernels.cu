@@ -1,22 +1,16 @@
-// trk_kernels.cu - sm_103a kernels of the nested-geometry tracker and the
-// C-ABI entry points that launch them.
+// trk_kernels.cu - history-based kernels of the nested-geometry tracker and
+// the C-ABI entry points that launch them (sm_103a).
 //
-// Paper: arXiv 2406.13849.  Table 1 (find_cell, distance_to_surface,
-// move_within_cell, cross_surface, change_direction), Alg. 2
-// (run_histories), Alg. 3-6 (single-universe CSG and rect trackers),
-// Alg. 7-10 (multi-universe walk, RTK-style static dispatch), Sec. 4.3
-// (pseudo-array universes, bounding-volume search).
+// Paper: arXiv 2406.13849.  Alg. 2 (run_histories) with Table 1's tracking
+// operations; Alg. 7-10 (multi-universe walk, RTK-style static dispatch);
+// Sec. 4.3 (single CSG tracker over pseudo-arrays with a BVH).
 //
 // Design (GB300):
 //  - one thread per history, persistent grid sized from the SM count;
-//  - the level stack (universe, cell, indices, translation per level) lives
-//    in registers: every loop over levels is unrolled to MAXL with runtime
-//    guards, so no level is indexed by a runtime value;
+//  - the level stack lives in registers (every loop over levels unrolled to
+//    MAXL with runtime guards);
 //  - static dispatch per level (the SP idea of Listings 1-4): the rect
 //    tracker is compiled in or out by a template flag, never a virtual call;
-//  - the BVH keeps both child boxes in each node, FP32 rounded outward; a
-//    point is tested against them with its coordinates rounded down and up,
-//    so the pruning is conservative and the exact FP64 cell test decides;
 //  - tallies: one 64-bit integer atomic per segment (order-independent);
 //    counters: per-thread registers, warp-reduced, one atomic per warp.
 // Built twice: --fmad=false (TRK_EXACT, bit-exact against the FP64 reference
@@ -27,497 +21,13 @@
 #include <cstring>
 
 #include "trk.h"
+#include "trk_device.cuh"
 #include "trk_internal.h"
 
 using namespace trk;
+using namespace trk::dev;
 
 namespace {
-
-constexpr double DINF = __builtin_huge_val();
-constexpr int MAXMAT = 8;
-
-// ---------------------------------------------------------------------------
-// Random numbers: Philox4x32-10 (Salmon et al., SC'11), counter
-// (particle id, event, tag, k), key (seed_lo32, geometry id); two doubles in
-// (0, 1] per call: ((u64 >> 11) + 1) * 2^-53.
-// ---------------------------------------------------------------------------
-enum { TAG_POSITION = 0, TAG_DIRECTION = 1, TAG_SCALARS = 2 };
-
-__device__ __forceinline__ uint4 philox10(uint4 c, uint2 k) {
-    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        if (r > 0) { k.x += W0; k.y += W1; }
-        const uint32_t lo0 = M0 * c.x, hi0 = __umulhi(M0, c.x);
-        const uint32_t lo1 = M1 * c.z, hi1 = __umulhi(M1, c.z);
-        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
-    }
-    return c;
-}
-
-__device__ __forceinline__ void uniform2(uint32_t pid, uint32_t event, uint32_t tag, uint32_t k, uint32_t seed_lo,
-                                         uint32_t gid, double& a, double& b) {
-    const uint4 o = philox10(make_uint4(pid, event, tag, k), make_uint2(seed_lo, gid));
-    const uint64_t ua = (uint64_t(o.y) << 32) | o.x;
-    const uint64_t ub = (uint64_t(o.w) << 32) | o.z;
-    a = double((ua >> 11) + 1) * 0x1.0p-53;
-    b = double((ub >> 11) + 1) * 0x1.0p-53;
-}
-
-// log x from + - * / only: x = 2^k m, m in [sqrt(1/2), sqrt 2), s = (m-1)/(m+1),
-// log m = 2 s (1 + z/3 + z^2/5 + ... + z^13/27), z = s^2 (Horner, highest
-// first); log x = k LN2_HI + (log m + k LN2_LO), LN2_HI = ln 2 to 33 bits.
-__device__ __forceinline__ double own_log(double x) {
-    const uint64_t bits = uint64_t(__double_as_longlong(x));
-    int k = int((bits >> 52) & 0x7ff) - 1023;
-    double m = __longlong_as_double((long long)((bits & 0x000fffffffffffffULL) | 0x3ff0000000000000ULL));
-    if (m > 1.4142135623730951) { m = m * 0.5; k += 1; }
-    const double s = (m - 1.0) / (m + 1.0);
-    const double z = s * s;
-    double p = 0x1.2f684bda12f68p-5;                 // 1/27
-    p = p * z + 0x1.47ae147ae147bp-5;                // 1/25
-    p = p * z + 0x1.642c8590b2164p-5;                // 1/23
-    p = p * z + 0x1.8618618618618p-5;                // 1/21
-    p = p * z + 0x1.af286bca1af28p-5;                // 1/19
-    p = p * z + 0x1.e1e1e1e1e1e1ep-5;                // 1/17
-    p = p * z + 0x1.1111111111111p-4;                // 1/15
-    p = p * z + 0x1.3b13b13b13b14p-4;                // 1/13
-    p = p * z + 0x1.745d1745d1746p-4;                // 1/11
-    p = p * z + 0x1.c71c71c71c71cp-4;                // 1/9
-    p = p * z + 0x1.2492492492492p-3;                // 1/7
-    p = p * z + 0x1.999999999999ap-3;                // 1/5
-    p = p * z + 0x1.5555555555555p-2;                // 1/3
-    p = p * z + 1.0;
-    const double logm = (s + s) * p;
-    const double kd = double(k);
-    return kd * 0x1.62e42fefp-1 + (logm + kd * 0x1.473de6af278edp-34);
-}
-
-// Marsaglia (1972): u, v in (-1, 1], accept 0 < s = u^2+v^2 < 1,
-// Omega = (u f, v f, 1 - 2 s), f = 2 sqrt(1 - s); attempt k uses counter
-// (pid, event, TAG_DIRECTION, k), at most 64 attempts.
-__device__ __forceinline__ bool isotropic(uint32_t pid, uint32_t event, uint32_t seed_lo, uint32_t gid, double& ou,
-                                          double& ov, double& ow) {
-    for (uint32_t k = 0; k < 64; ++k) {
-        double xa, xb;
-        uniform2(pid, event, TAG_DIRECTION, k, seed_lo, gid, xa, xb);
-        const double u = 2.0 * xa - 1.0;
-        const double v = 2.0 * xb - 1.0;
-        const double s = u * u + v * v;
-        if (s > 0.0 && s < 1.0) {
-            const double f = 2.0 * sqrt(1.0 - s);
-            ou = u * f;
-            ov = v * f;
-            ow = 1.0 - 2.0 * s;
-            return true;
-        }
-    }
-    return false;
-}
-
-__device__ __forceinline__ uint64_t fnv(uint64_t h, uint64_t w) { return (h ^ w) * 0x100000001b3ULL; }
-constexpr uint64_t FNV0 = 0xcbf29ce484222325ULL;
-
-// ---------------------------------------------------------------------------
-// Geometry access
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void load_coef(const DevGeom& g, int s, double& c0, double& c1, double& c2, double& c3) {
-    const double2* p = reinterpret_cast<const double2*>(g.s_coef + 4 * s);
-    const double2 a = __ldg(p), b = __ldg(p + 1);
-    c0 = a.x; c1 = a.y; c2 = b.x; c3 = b.y;
-}
-
-// Sense of the point relative to surface s: f >= 0 is "+".
-//   px: x - g;  p: ((nx x + ny y) + nz z) - d;  cz: (qx qx + qy qy) - r r.
-__device__ __forceinline__ int sense_at(const DevGeom& g, int s, double x, double y, double z) {
-    const int type = __ldg(g.s_info + s) & 15;
-    double c0, c1, c2, c3;
-    load_coef(g, s, c0, c1, c2, c3);
-    double f;
-    if (type == S_PX) f = x - c0;
-    else if (type == S_PY) f = y - c0;
-    else if (type == S_PZ) f = z - c0;
-    else if (type == S_P) f = ((c0 * x + c1 * y) + c2 * z) - c3;
-    else {
-        const double qx = x - c0, qy = y - c1;
-        f = (qx * qx + qy * qy) - c3;
-    }
-    return f >= 0.0 ? 1 : -1;
-}
-
-// Distance to surface s, leaving its `side` (+1/-1) of it; `on` is the logical
-// on-surface state.  Negative results (a point a rounding error outside the
-// cell) become 0; INF means no hit.
-//  planes: only the face the direction leaves through is a candidate;
-//    px: t = (g - x) * inv_u; p: t = (d - ((nx x + ny y) + nz z)) /
-//    ((nx u + ny v) + nz w); a plane the particle is on is never hit again.
-//  cz: a = u u + v v, b = qx u + qy v; on it and logically inside:
-//    t = -2 b / a if b < 0, else no hit; on it and outside: no hit;
-//    otherwise c = f, disc = b b - a c, no hit if a == 0 or disc <= 0;
-//    inside: t = b <= 0 ? (-b + sqrt disc) / a : -c / (b + sqrt disc);
-//    outside: hit only if b < 0, t = c / (-b + sqrt disc).
-__device__ __forceinline__ double surface_distance(const DevGeom& g, int s, int side, bool on, double x, double y,
-                                                   double z, double u, double v, double w, double iu, double iv,
-                                                   double iw) {
-    const int type = __ldg(g.s_info + s) & 15;
-    double c0, c1, c2, c3;
-    load_coef(g, s, c0, c1, c2, c3);
-    double t;
-    if (type <= S_PZ) {
-        if (on) return DINF;
-        const double dd = type == S_PX ? u : (type == S_PY ? v : w);
-        const double xx = type == S_PX ? x : (type == S_PY ? y : z);
-        const double ii = type == S_PX ? iu : (type == S_PY ? iv : iw);
-        const bool leaves = side > 0 ? (dd < 0.0) : (dd > 0.0);
-        if (!leaves) return DINF;
-        t = (c0 - xx) * ii;
-    } else if (type == S_P) {
-        if (on) return DINF;
-        const double den = (c0 * u + c1 * v) + c2 * w;
-        const bool leaves = side > 0 ? (den < 0.0) : (den > 0.0);
-        if (!leaves) return DINF;
-        const double num = c3 - ((c0 * x + c1 * y) + c2 * z);
-        t = num / den;
-    } else {
-        const double qx = x - c0, qy = y - c1;
-        const double a = u * u + v * v;
-        const double b = qx * u + qy * v;
-        if (on) {
-            if (side < 0 && b < 0.0) t = (-2.0 * b) / a;
-            else return DINF;
-        } else {
-            const double c = (qx * qx + qy * qy) - c3;
-            if (a == 0.0) return DINF;
-            const double disc = b * b - a * c;
-            if (disc <= 0.0) return DINF;
-            const double sq = sqrt(disc);
-            if (side < 0) {
-                t = (b <= 0.0) ? (-b + sq) / a : -c / (b + sq);
-            } else {
-                if (!(b < 0.0)) return DINF;
-                t = c / (-b + sq);
-            }
-        }
-    }
-    if (t < 0.0) t = 0.0;
-    return t;
-}
-
-// Cell test: all senses hold; the crossed surface xs (if >= 0) is taken
-// logically with sense xsn instead of being evaluated.
-__device__ __forceinline__ bool cell_holds(const DevGeom& g, int c, double x, double y, double z, int xs, int xsn) {
-    const int2 rg = __ldg(g.c_range + c);
-    for (int k = 0; k < rg.y; ++k) {
-        const int e = __ldg(g.cs + rg.x + k);
-        const int s = e >> 1, sn = (e & 1) ? 1 : -1;
-        if (s == xs) {
-            if (sn != xsn) return false;
-        } else if (sense_at(g, s, x, y, z) != sn) {
-            return false;
-        }
-    }
-    return true;
-}
-
-// First cell of universe u (CSG view) holding the point, excluding cell `ex`
-// (-1 none); linear scan for small universes (Alg. 3/4), otherwise BVH
-// traversal (Sec. 4.3) that tests both children and stops at the first hit.
-// Returns -1 if none; -2 on BVH stack overflow.
-__device__ int csg_search(const DevGeom& g, int u, double x, double y, double z, int ex, int xs, int xsn) {
-    const int4 ui = __ldg(g.u_info + u);
-    if (ui.z < 0) {
-        for (int c = ui.x; c < ui.x + ui.y; ++c) {
-            if (c == ex) continue;
-            if (cell_holds(g, c, x, y, z, xs, xsn)) return c;
-        }
-        return -1;
-    }
-    const float xl = __double2float_rd(x), xh = __double2float_ru(x);
-    const float yl = __double2float_rd(y), yh = __double2float_ru(y);
-    const float zl = __double2float_rd(z), zh = __double2float_ru(z);
-    int stack[BVH_STACK];
-    int sp = 0;
-    int node = ui.z;
-    for (;;) {
-        const float4* np = reinterpret_cast<const float4*>(g.nodes + node);
-        const float4 lo0 = __ldg(np), hi0 = __ldg(np + 1), lo1 = __ldg(np + 2), hi1 = __ldg(np + 3);
-        const int c0 = __float_as_int(lo0.w), c1 = __float_as_int(lo1.w);
-        const bool in0 = xh >= lo0.x && xl <= hi0.x && yh >= lo0.y && yl <= hi0.y && zh >= lo0.z && zl <= hi0.z;
-        const bool in1 = xh >= lo1.x && xl <= hi1.x && yh >= lo1.y && yl <= hi1.y && zh >= lo1.z && zl <= hi1.z;
-        int next = -1;
-        if (in0) {
-            if (c0 < 0) {
-                const int r = ~c0, first = r >> 4, cnt = r & 15;
-                for (int k = 0; k < cnt; ++k) {
-                    const int c = __ldg(g.leaf_cells + first + k);
-                    if (c != ex && cell_holds(g, c, x, y, z, xs, xsn)) return c;
-                }
-            } else {
-                next = c0;
-            }
-        }
-        if (in1) {
-            if (c1 < 0) {
-                const int r = ~c1, first = r >> 4, cnt = r & 15;
-                for (int k = 0; k < cnt; ++k) {
-                    const int c = __ldg(g.leaf_cells + first + k);
-                    if (c != ex && cell_holds(g, c, x, y, z, xs, xsn)) return c;
-                }
-            } else if (next < 0) {
-                next = c1;
-            } else {
-                if (sp >= BVH_STACK) return -2;
-                stack[sp++] = c1;
-            }
-        }
-        if (next >= 0) {
-            node = next;
-        } else {
-            if (sp == 0) return -1;
-            node = stack[--sp];
-        }
-    }
-}
-
-// Alg. 5: element index in one dimension; element i holds g_i <= x < g_{i+1};
-// a root array has nothing outside [g_0, g_n), a non-root array clamps.
-__device__ __forceinline__ int rect_index(const double* gr, int n, double x, bool root) {
-    if (root && (!(__ldg(gr) <= x) || !(x < __ldg(gr + n)))) return -1;
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(gr + mid) <= x) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
-
-// ---------------------------------------------------------------------------
-// Particle state (registers)
-// ---------------------------------------------------------------------------
-struct Lv {
-    int u, cell, i, j, k, off;
-    double tx, ty, tz;
-};
-
-struct St {
-    double x, y, z, u, v, w, iu, iv, iw, tau;
-    int nlev, on_lev, on_surf, mat;
-    Lv lv[MAXL];
-};
-
-__device__ __forceinline__ void set_inverse(St& s) {
-    s.iu = 1.0 / s.u;
-    s.iv = 1.0 / s.v;
-    s.iw = 1.0 / s.w;
-}
-
-__device__ __forceinline__ int instance(const St& s) {
-    int t = 0;
-#pragma unroll
-    for (int l = 0; l < MAXL; ++l)
-        if (l < s.nlev) t += s.lv[l].off;
-    return t;
-}
-
-// Local position at level `lev`: global minus translations of levels
-// 0..lev-1, component by component in level order.
-__device__ __forceinline__ void local_at(const St& s, int lev, double& x, double& y, double& z) {
-    x = s.x; y = s.y; z = s.z;
-#pragma unroll
-    for (int l = 0; l < MAXL - 1; ++l) {
-        if (l < lev) { x = x - s.lv[l].tx; y = y - s.lv[l].ty; z = z - s.lv[l].tz; }
-    }
-}
-
-// Sets level l to rect element (i,j,k) of lattice `lat`; returns the daughter.
-__device__ __forceinline__ int enter_element(const DevGeom& g, Lv& L, int lat, int i, int j, int k) {
-    const int4 dm = __ldg(g.l_dim + lat), of = __ldg(g.l_off + lat);
-    const int e = i + dm.x * (j + dm.y * k);
-    L.i = i; L.j = j; L.k = k;
-    L.cell = e;
-    L.off = __ldg(g.l_eoff + of.w + e);
-    L.tx = __ldg(g.l_ctr + of.x + i);
-    L.ty = __ldg(g.l_ctr + of.y + j);
-    L.tz = __ldg(g.l_ctr + of.z + k);
-    return __ldg(g.l_fill + of.w + e);
-}
-
-__device__ __forceinline__ int enter_cell(const DevGeom& g, Lv& L, int c) {
-    L.cell = c;
-    L.off = __ldg(g.c_off + c);
-    L.tx = __ldg(g.c_tr + 3 * c);
-    L.ty = __ldg(g.c_tr + 3 * c + 1);
-    L.tz = __ldg(g.c_tr + 3 * c + 2);
-    return __ldg(g.c_fill + c);
-}
-
-// Alg. 7 from level `start` downward.  0 ok, -1 no cell, -2 BVH overflow.
-template <bool CSG>
-__device__ int find_from(const DevGeom& g, St& s, int start) {
-    double x, y, z;
-    local_at(s, start, x, y, z);
-#pragma unroll
-    for (int l = 0; l < MAXL; ++l) {
-        if (l < start) continue;
-        Lv& L = s.lv[l];
-        const int4 ui = __ldg(g.u_info + L.u);
-        int dau;
-        if (!CSG && ui.w >= 0) {
-            const int4 dm = __ldg(g.l_dim + ui.w), of = __ldg(g.l_off + ui.w);
-            const bool root = (l == 0);
-            const int i = rect_index(g.l_grid + of.x, dm.x, x, root);
-            const int j = rect_index(g.l_grid + of.y, dm.y, y, root);
-            const int k = rect_index(g.l_grid + of.z, dm.z, z, root);
-            if (i < 0 || j < 0 || k < 0) return -1;
-            dau = enter_element(g, L, ui.w, i, j, k);
-        } else {
-            const int c = csg_search(g, L.u, x, y, z, -1, -1, 0);
-            if (c < 0) return c;
-            dau = enter_cell(g, L, c);
-        }
-        if (dau < 0) {
-            s.nlev = l + 1;
-            s.mat = ~dau;
-            return 0;
-        }
-        if (l + 1 >= MAXL) return -1;
-        x = x - L.tx; y = y - L.ty; z = z - L.tz;
-        s.lv[l + 1 < MAXL ? l + 1 : l].u = dau;
-    }
-    return -1;
-}
-
-struct Hit {
-    double d;
-    int level, surf, side, dim, dsign;
-};
-
-// distance_to_surface over the levels, top to bottom, strict '<' (the
-// top-most level wins ties); rect levels: x, y, z faces in the direction of
-// flight, outer faces only at the root; CSG levels: the cell's surfaces.
-template <bool CSG>
-__device__ __forceinline__ Hit distance_to_boundary(const DevGeom& g, const St& s) {
-    Hit h;
-    h.d = DINF; h.level = -1; h.surf = -1; h.side = 0; h.dim = -1; h.dsign = 0;
-    double x = s.x, y = s.y, z = s.z;
-#pragma unroll
-    for (int l = 0; l < MAXL; ++l) {
-        if (l >= s.nlev) break;
-        if (l > 0) { x = x - s.lv[l - 1].tx; y = y - s.lv[l - 1].ty; z = z - s.lv[l - 1].tz; }
-        const Lv& L = s.lv[l];
-        const int4 ui = __ldg(g.u_info + L.u);
-        if (!CSG && ui.w >= 0) {
-            const int4 dm = __ldg(g.l_dim + ui.w), of = __ldg(g.l_off + ui.w);
-            const int n3[3] = {dm.x, dm.y, dm.z};
-            const int o3[3] = {of.x, of.y, of.z};
-            const int i3[3] = {L.i, L.j, L.k};
-            const double p3[3] = {x, y, z};
-            const double d3[3] = {s.u, s.v, s.w};
-            const double v3[3] = {s.iu, s.iv, s.iw};
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                double t = DINF;
-                int sg = 0;
-                if (d3[d] > 0.0) {
-                    if (i3[d] < n3[d] - 1 || l == 0) { t = (__ldg(g.l_grid + o3[d] + i3[d] + 1) - p3[d]) * v3[d]; sg = 1; }
-                } else if (d3[d] < 0.0) {
-                    if (i3[d] > 0 || l == 0) { t = (__ldg(g.l_grid + o3[d] + i3[d]) - p3[d]) * v3[d]; sg = -1; }
-                }
-                if (sg != 0 && t < 0.0) t = 0.0;
-                if (sg != 0 && t < h.d) {
-                    h.d = t; h.level = l; h.surf = -1 - (2 * d + (sg > 0)); h.dim = d; h.dsign = sg; h.side = 0;
-                }
-            }
-        } else {
-            const int2 rg = __ldg(g.c_range + L.cell);
-            for (int k = 0; k < rg.y; ++k) {
-                const int e = __ldg(g.cs + rg.x + k);
-                const int sid = e >> 1, side = (e & 1) ? 1 : -1;
-                const bool on = (s.on_lev == l && s.on_surf == sid);
-                const double t = surface_distance(g, sid, side, on, x, y, z, s.u, s.v, s.w, s.iu, s.iv, s.iw);
-                if (t < h.d) { h.d = t; h.level = l; h.surf = sid; h.side = side; h.dim = -1; h.dsign = 0; }
-            }
-        }
-    }
-    return h;
-}
-
-enum { CR_OK = 0, CR_REFLECT = 1, CR_ESCAPE = 2, CR_LOST = 3, CR_FIND = 4 };
-
-__device__ __forceinline__ void reflect_plane(const DevGeom& g, St& s, int sid, int dim) {
-    int type = dim;
-    if (sid >= 0) type = __ldg(g.s_info + sid) & 15;
-    if (type == S_PX) s.u = -s.u;
-    else if (type == S_PY) s.v = -s.v;
-    else if (type == S_PZ) s.w = -s.w;
-    else {
-        double c0, c1, c2, c3;
-        load_coef(g, sid, c0, c1, c2, c3);
-        const double nd = (c0 * s.u + c1 * s.v) + c2 * s.w;
-        const double nn = (c0 * c0 + c1 * c1) + c2 * c2;
-        const double k = (2.0 * nd) / nn;
-        s.u = s.u - k * c0;
-        s.v = s.v - k * c1;
-        s.w = s.w - k * c2;
-    }
-    set_inverse(s);
-}
-
-// Alg. 8 at the hit's level (Alg. 4 for CSG, Alg. 6 for rect).  Returns
-// CR_FIND when the levels below the crossing must be found again (the
-// caller runs find_from(level + 1)), else a final result.
-template <bool CSG>
-__device__ __forceinline__ int cross_surface(const DevGeom& g, St& s, const Hit& h, int& find_level) {
-    find_level = -1;
-    int result = CR_LOST;
-#pragma unroll
-    for (int l = 0; l < MAXL; ++l) {
-        if (l != h.level) continue;
-        Lv& L = s.lv[l];
-        const int4 ui = __ldg(g.u_info + L.u);
-        s.on_lev = l;
-        s.on_surf = h.surf;
-        int dau;
-        if (!CSG && ui.w >= 0) {
-            int ijk[3] = {L.i, L.j, L.k};
-            const int4 dm = __ldg(g.l_dim + ui.w);
-            const int n3[3] = {dm.x, dm.y, dm.z};
-            int ni = 0, nn = 1;
-#pragma unroll
-            for (int d = 0; d < 3; ++d)
-                if (d == h.dim) { ijk[d] += h.dsign; ni = ijk[d]; nn = n3[d]; }
-            if (ni < 0 || ni >= nn) {
-                if (l != 0) return CR_LOST;
-                const int bc = (dm.w >> (2 * (2 * h.dim + (h.dsign > 0)))) & 3;
-                if (bc == BC_REFLECT) { reflect_plane(g, s, -1, h.dim); return CR_REFLECT; }
-                return CR_ESCAPE;
-            }
-            dau = enter_element(g, L, ui.w, ijk[0], ijk[1], ijk[2]);
-        } else {
-            double x, y, z;
-            local_at(s, l, x, y, z);
-            const int c = csg_search(g, L.u, x, y, z, L.cell, h.surf, -h.side);
-            if (c == -2) return CR_LOST;
-            if (c < 0) {
-                if (l != 0) return CR_LOST;
-                const int bc = (__ldg(g.s_info + h.surf) >> 4) & 3;
-                if (bc == BC_REFLECT) { reflect_plane(g, s, h.surf, -1); return CR_REFLECT; }
-                return CR_ESCAPE;
-            }
-            dau = enter_cell(g, L, c);
-        }
-        if (dau < 0) {
-            s.nlev = l + 1;
-            s.mat = ~dau;
-            return CR_OK;
-        }
-        if (l + 1 < MAXL) s.lv[l + 1 < MAXL ? l + 1 : l].u = dau;
-        find_level = l + 1;
-        result = CR_FIND;
-    }
-    return result;
-}
 
 // ---------------------------------------------------------------------------
 // Run parameters and per-thread counters
@@ -531,13 +41,16 @@ struct RunP {
     int trace_cap;
 };
 
+// Per-thread event counts (32-bit: one thread tracks far fewer than 2^32
+// segments), reduced over the warp and added once per warp at kernel end.
+constexpr int NCOUNT = 11;
 struct Counts {
-    unsigned long long k[TRK_NCOUNTERS];
+    unsigned k[NCOUNT];
 };
 
 __device__ __forceinline__ void flush_counts(Counts& c, unsigned long long* out) {
 #pragma unroll
-    for (int i = 0; i < 11; ++i) {
+    for (int i = 0; i < NCOUNT; ++i) {
         unsigned long long v = c.k[i];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -574,18 +87,13 @@ __device__ __forceinline__ void history(const DevGeom& g, const ParticlesView& P
         cnt.k[TRK_K_SOURCE]++;
     } else {
         St s;
+        clear_levels(s);
         s.x = P.x[i]; s.y = P.y[i]; s.z = P.z[i];
-        s.u = P.u[i]; s.v = P.v[i]; s.w = P.w[i];
+        s.d.u = P.u[i]; s.d.v = P.v[i]; s.d.w = P.w[i];
         s.tau = P.tau[i];
-        set_inverse(s);
-        s.on_lev = -1; s.on_surf = -1;
-        s.nlev = 0; s.mat = 0;
-#pragma unroll
-        for (int l = 0; l < MAXL; ++l) { s.lv[l].u = 0; s.lv[l].cell = 0; s.lv[l].i = s.lv[l].j = s.lv[l].k = 0; s.lv[l].off = 0; s.lv[l].tx = s.lv[l].ty = s.lv[l].tz = 0.0; }
+        set_inverse(s.d);
         s.lv[0].u = g.root;
-        int fr = find_from<CSG>(g, s, 0);
-        if (fr != 0) {
-            if (fr == -2) kernel_status(kcnt, TRK_E_LOST);
+        if (find_from<CSG>(g, s, 0) != 0) {
             status = TRK_E_LOST;
             cnt.k[TRK_K_LOST]++;
         } else {
@@ -594,14 +102,14 @@ __device__ __forceinline__ void history(const DevGeom& g, const ParticlesView& P
             for (;;) {
                 const Hit h = distance_to_boundary<CSG>(g, s);
                 const double sig = __ldg(g.sigma + s.mat);
-                const double dc = sig > 0.0 ? s.tau / sig : DINF;
-                const bool crossing = h.d < dc;
+                const double dc = d_gt0(sig) ? s.tau / sig : DINF;
+                const bool crossing = d_lt(h.d, dc);
                 double len = crossing ? h.d : dc;
-                if (!(len < DINF)) { status = TRK_E_LOST; cnt.k[TRK_K_LOST]++; break; }
+                if (!d_finite_lt_inf(len)) { status = TRK_E_LOST; cnt.k[TRK_K_LOST]++; break; }
                 const int inst = instance(s);
                 bool stop_cut = false;
                 if (FLAGS & F_CUT) {
-                    if (path + len >= rp.max_path) { len = rp.max_path - path; stop_cut = true; }
+                    if (!d_lt(path + len, rp.max_path)) { len = rp.max_path - path; stop_cut = true; }
                     else path = path + len;
                 }
                 const long long q = __double2ll_rn(len * 4294967296.0);
@@ -613,9 +121,9 @@ __device__ __forceinline__ void history(const DevGeom& g, const ParticlesView& P
                         tr_len[i * rp.trace_cap + nseg] = len;
                     }
                 }
-                s.x = s.x + len * s.u;
-                s.y = s.y + len * s.v;
-                s.z = s.z + len * s.w;
+                s.x = s.x + len * s.d.u;
+                s.y = s.y + len * s.d.v;
+                s.z = s.z + len * s.d.w;
                 nseg++;
                 cnt.k[TRK_K_SEGMENTS]++;
                 if (stop_cut) { status = TRK_P_CUTOFF; cnt.k[TRK_K_CUTOFF]++; break; }
@@ -624,11 +132,7 @@ __device__ __forceinline__ void history(const DevGeom& g, const ParticlesView& P
                     cnt.k[TRK_K_CROSSINGS]++;
                     int fl;
                     int cr = cross_surface<CSG>(g, s, h, fl);
-                    if (cr == CR_FIND) {
-                        const int r = find_from<CSG>(g, s, fl);
-                        if (r == -2) kernel_status(kcnt, TRK_E_LOST);
-                        cr = (r == 0) ? CR_OK : CR_LOST;
-                    }
+                    if (cr == CR_FIND) cr = find_from<CSG>(g, s, fl) == 0 ? CR_OK : CR_LOST;
                     if (cr == CR_ESCAPE) { status = TRK_P_ESCAPED; cnt.k[TRK_K_ESCAPED]++; break; }
                     if (cr == CR_LOST) { status = TRK_E_LOST; cnt.k[TRK_K_LOST]++; break; }
                     if (cr == CR_REFLECT) cnt.k[TRK_K_REFLECTIONS]++;
@@ -637,9 +141,9 @@ __device__ __forceinline__ void history(const DevGeom& g, const ParticlesView& P
                     cnt.k[TRK_K_COLLISIONS]++;
                     double xa, xt;
                     uniform2(pid, event, TAG_SCALARS, 0, rp.seed_lo, gid, xa, xt);
-                    if (xa < rp.p_absorb) { status = TRK_P_ABSORBED; cnt.k[TRK_K_ABSORBED]++; break; }
-                    if (!isotropic(pid, event, rp.seed_lo, gid, s.u, s.v, s.w)) { status = TRK_E_LOST; cnt.k[TRK_K_LOST]++; break; }
-                    set_inverse(s);
+                    if (d_lt(xa, rp.p_absorb)) { status = TRK_P_ABSORBED; cnt.k[TRK_K_ABSORBED]++; break; }
+                    if (!isotropic(pid, event, rp.seed_lo, gid, s.d.u, s.d.v, s.d.w)) { status = TRK_E_LOST; cnt.k[TRK_K_LOST]++; break; }
+                    set_inverse(s.d);
                     s.tau = -own_log(xt);
                     s.on_lev = -1;
                     s.on_surf = -1;
@@ -665,7 +169,7 @@ __global__ void __launch_bounds__(128) k_history(const DevGeom g, const Particle
                                                  double* __restrict__ tr_len) {
     Counts c;
 #pragma unroll
-    for (int k = 0; k < TRK_NCOUNTERS; ++k) c.k[k] = 0;
+    for (int k = 0; k < NCOUNT; ++k) c.k[k] = 0;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
         history<CSG, FLAGS>(g, P, i, rp, tally, c, rec, tr_inst, tr_len, counters);
@@ -677,12 +181,13 @@ __global__ void __launch_bounds__(128) k_history(const DevGeom g, const Particle
 // ---------------------------------------------------------------------------
 __device__ bool inside_root(const DevGeom& g, double x, double y, double z) {
     const int4 ui = __ldg(g.u_info + g.root);
+    const Pt p = make_pt(x, y, z);
     if (ui.w >= 0) {
         const int4 dm = __ldg(g.l_dim + ui.w), of = __ldg(g.l_off + ui.w);
-        return rect_index(g.l_grid + of.x, dm.x, x, true) >= 0 && rect_index(g.l_grid + of.y, dm.y, y, true) >= 0 &&
-               rect_index(g.l_grid + of.z, dm.z, z, true) >= 0;
+        return rect_index(g.l_gkey + of.x, dm.x, p.kx, true) >= 0 && rect_index(g.l_gkey + of.y, dm.y, p.ky, true) >= 0 &&
+               rect_index(g.l_gkey + of.z, dm.z, p.kz, true) >= 0;
     }
-    return csg_search(g, g.root, x, y, z, -1, -1, 0) >= 0;
+    return csg_search(g, g.root, p, -1, -1, 0) >= 0;
 }
 
 __global__ void __launch_bounds__(128) k_source(const DevGeom g, long long n, uint64_t first_id, uint32_t seed_lo,
@@ -729,10 +234,8 @@ __global__ void __launch_bounds__(128) k_find(const DevGeom g, long long n, cons
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         St s;
+        clear_levels(s);
         s.x = xyz[3 * i]; s.y = xyz[3 * i + 1]; s.z = xyz[3 * i + 2];
-        s.nlev = 0;
-#pragma unroll
-        for (int l = 0; l < MAXL; ++l) { s.lv[l].u = 0; s.lv[l].off = 0; s.lv[l].tx = s.lv[l].ty = s.lv[l].tz = 0.0; }
         s.lv[0].u = g.root;
         out[i] = find_from<CSG>(g, s, 0) == 0 ? int64_t(instance(s)) : int64_t(-1);
     }
@@ -769,7 +272,7 @@ __device__ __forceinline__ void hit_derivative(const DevGeom& g, const St& s, co
         const int4 of = __ldg(g.l_off + lat);
         const int go = h.dim == 0 ? of.x : of.y;
         const double G = __ldg(g.l_grid + go + idx + (h.dsign > 0)) + (h.dim == 0 ? Tx : Ty);
-        dt[3] = (G / pitch) / (h.dim == 0 ? s.u : s.v);
+        dt[3] = (G / pitch) / (h.dim == 0 ? s.d.u : s.d.v);
         return;
     }
     const int info = __ldg(g.s_info + h.surf);
@@ -779,12 +282,12 @@ __device__ __forceinline__ void hit_derivative(const DevGeom& g, const St& s, co
     if (type == S_PX || type == S_PY) {
         if (pscale && pitch > 0.0) {
             const double G = c0 + (type == S_PX ? Tx : Ty);
-            dt[3] = (G / pitch) / (type == S_PX ? s.u : s.v);
+            dt[3] = (G / pitch) / (type == S_PX ? s.d.u : s.d.v);
         }
     } else if (type == S_CZ) {
         const double cx = c0 + Tx, cy = c1 + Ty;
         const double qx = s.x - cx, qy = s.y - cy;
-        const double gd = 2.0 * (qx * s.u + qy * s.v);
+        const double gd = 2.0 * (qx * s.d.u + qy * s.d.v);
         if (gd == 0.0) return;
         if (rparam >= 0 && rparam < 3) {
             const double v = -(-2.0 * c2) / gd;
@@ -806,26 +309,24 @@ __device__ __forceinline__ int walk_ray(const DevGeom& g, const double* ray, con
 #pragma unroll
     for (int j = 0; j < NGP; ++j) dtau[j] = 0.0;
     St s;
+    clear_levels(s);
     s.x = ray[0]; s.y = ray[1]; s.z = ray[2];
-    s.u = ray[3]; s.v = ray[4]; s.w = ray[5];
+    s.d.u = ray[3]; s.d.v = ray[4]; s.d.w = ray[5];
     s.tau = 0.0;
-    set_inverse(s);
-    s.on_lev = -1; s.on_surf = -1; s.nlev = 0; s.mat = 0;
-#pragma unroll
-    for (int l = 0; l < MAXL; ++l) { s.lv[l].u = 0; s.lv[l].cell = 0; s.lv[l].i = s.lv[l].j = s.lv[l].k = 0; s.lv[l].off = 0; s.lv[l].tx = s.lv[l].ty = s.lv[l].tz = 0.0; }
+    set_inverse(s.d);
     s.lv[0].u = g.root;
     if (find_from<CSG>(g, s, 0) != 0) return TRK_E_LOST;
     double din[NGP] = {0.0, 0.0, 0.0, 0.0};
     for (int seg = 0; seg < 10000000; ++seg) {
         const Hit h = distance_to_boundary<CSG>(g, s);
-        if (!(h.d < DINF)) return TRK_E_LOST;
+        if (!d_finite_lt_inf(h.d)) return TRK_E_LOST;
         const int m = s.mat;
 #pragma unroll
         for (int k = 0; k < MAXMAT; ++k)
             if (k == m) lens[k] += h.d;
-        s.x = s.x + h.d * s.u;
-        s.y = s.y + h.d * s.v;
-        s.z = s.z + h.d * s.w;
+        s.x = s.x + h.d * s.d.u;
+        s.y = s.y + h.d * s.d.v;
+        s.z = s.z + h.d * s.d.w;
         if (BWD) {
             double dout[NGP];
             hit_derivative<CSG>(g, s, h, pitch, dout);
