@@ -208,15 +208,23 @@ def main() -> None:
     tally = torch.zeros(g.n_inst, dtype=torch.int64, device=dev)
     cnt = torch.zeros(N.NCOUNTERS, dtype=torch.int64, device=dev)
 
-    def make_opts(tracker):
-        return N.default_opts(tracker=tracker, mode=N.MODE_HISTORY, precision=N.FP64, seed=SEED,
+    def make_opts(tracker, mode=N.MODE_HISTORY):
+        return N.default_opts(tracker=tracker, mode=mode, precision=N.FP64, seed=SEED,
                               first_id=first_id, p_absorb=P_ABSORB)
 
-    def timed(tracker, steps, warmup, sampler=None):
-        opts = make_opts(tracker)
+    work_cache = {}
+
+    def timed(tracker, steps, warmup, sampler=None, mode=N.MODE_HISTORY):
+        opts = make_opts(tracker, mode)
+        wb = g.work_bytes(n, opts)
+        work = None
+        if wb:
+            if wb not in work_cache:
+                work_cache[wb] = torch.empty(wb + 256, dtype=torch.uint8, device=dev)
+            work = work_cache[wb]
         for _ in range(warmup):
             g.source_init(n, seed=SEED, first_id=first_id, out=parts)
-            g.run_histories(parts, n, tally=tally, counters=cnt, opts=opts)
+            g.run_histories(parts, n, tally=tally, counters=cnt, opts=opts, work=work)
         tally.zero_()
         cnt.zero_()
         barrier()
@@ -230,7 +238,7 @@ def main() -> None:
             a.record(stream)
             g.source_init(n, seed=SEED, first_id=first_id, out=parts)
             b.record(stream)
-            g.run_histories(parts, n, tally=tally, counters=cnt, opts=opts)
+            g.run_histories(parts, n, tally=tally, counters=cnt, opts=opts, work=work)
             c.record(stream)
         barrier()
         wall = time.perf_counter() - t0
@@ -243,8 +251,10 @@ def main() -> None:
 
     # main line: BVH-CSG tracker
     main_run = timed(N.TRACKER_CSG, args.steps, args.warmup, ClockSampler(local))
-    # companion measurements (same workload, same launch shape): rect tracker
+    # companion measurements (same workload): rect tracker, event-based kernel
     rect_run = timed(N.TRACKER_RECT, max(2, args.steps // 2), 3)
+    ev_csg = timed(N.TRACKER_CSG, max(2, args.steps // 2), 3, mode=N.MODE_EVENT)
+    ev_rect = timed(N.TRACKER_RECT, max(2, args.steps // 2), 3, mode=N.MODE_EVENT)
 
     # max over ranks
     t_local = torch.tensor([main_run["ms"], float(main_run["segments"])], dtype=torch.float64, device=dev)
@@ -329,6 +339,8 @@ def main() -> None:
                 "csg_bvh_fp64_history_segments_per_s": csg_value,
                 "rect_fp64_history_segments_per_s": rect_value,
                 "csg_over_rect": csg_value / rect_value,
+                "csg_bvh_fp64_event_segments_per_s": ev_csg["segments"] / (ev_csg["ms"] / 1e3),
+                "rect_fp64_event_segments_per_s": ev_rect["segments"] / (ev_rect["ms"] / 1e3),
                 "history_kernel_ms": hist_ms,
                 "segments_per_particle": main_run["segments"] / (n * args.steps),
             },

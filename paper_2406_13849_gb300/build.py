@@ -18,6 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# translation units compiled once per flavour (fast / exact)
+KERNEL_UNITS = ["trk_kernels", "trk_event"]
 
 
 def _cuda_home() -> str:
@@ -63,13 +65,14 @@ def build(force: bool = False, verbose: bool = False) -> dict:
     peaks_obj = os.path.join(BUILD, "peaks.o")
     jobs.append([nvcc] + ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"] + inc +
                 ["-c", os.path.join(CSRC, "peaks.cu"), "-o", peaks_obj])
-    kobjs = {}
+    kobjs = {"fast": [], "exact": []}
     for flavour, extra in (("fast", []), ("exact", ["--fmad=false", "-DTRK_EXACT"])):
-        obj = os.path.join(BUILD, f"trk_kernels_{flavour}.o")
-        kobjs[flavour] = obj
-        jobs.append([nvcc] + ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-                                     "-Xcompiler", "-ffp-contract=off"] + extra + inc +
-                    ["-c", os.path.join(CSRC, "trk_kernels.cu"), "-o", obj])
+        for unit in KERNEL_UNITS:
+            obj = os.path.join(BUILD, f"{unit}_{flavour}.o")
+            kobjs[flavour].append(obj)
+            jobs.append([nvcc] + ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+                                         "-Xcompiler", "-ffp-contract=off"] + extra + inc +
+                        ["-c", os.path.join(CSRC, unit + ".cu"), "-o", obj])
     procs = [subprocess.Popen(j, stdout=None if verbose else subprocess.PIPE,
                               stderr=subprocess.STDOUT) for j in jobs]
     failed = []
@@ -82,7 +85,7 @@ def build(force: bool = False, verbose: bool = False) -> dict:
         raise RuntimeError("library build failed:\n" + msg)
     for flavour, target in outs.items():
         tmp = target + ".tmp"
-        subprocess.run([nvcc] + ARCH + ["-shared", "-o", tmp, host_obj, kobjs[flavour], peaks_obj,
+        subprocess.run([nvcc] + ARCH + ["-shared", "-o", tmp, host_obj] + kobjs[flavour] + [peaks_obj,
                                         "-lcudart"], check=True)
         os.replace(tmp, target)
     return outs

@@ -575,5 +575,145 @@ __device__ __forceinline__ int cross_surface(const DevGeom& g, St& s, const Hit&
     return result;
 }
 
+// ---------------------------------------------------------------------------
+// Run parameters and per-thread counters
+// ---------------------------------------------------------------------------
+struct RunP {
+    uint64_t first_id;
+    uint64_t max_segments;
+    double p_absorb;
+    double max_path;
+    uint32_t seed_lo;
+    int trace_cap;
+};
+
+// Per-thread event counts (32-bit: one thread tracks far fewer than 2^32
+// segments), reduced over the warp and added once per warp at kernel end.
+constexpr int NCOUNT = 11;
+struct Counts {
+    unsigned k[NCOUNT];
+};
+
+__device__ __forceinline__ void flush_counts(Counts& c, unsigned long long* out) {
+#pragma unroll
+    for (int i = 0; i < NCOUNT; ++i) {
+        unsigned long long v = c.k[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0 && v) atomicAdd(out + i, v);
+    }
+}
+
+__device__ __forceinline__ void kernel_status(unsigned long long* cnt, int st) {
+    atomicCAS(cnt + TRK_K_STATUS, 0ULL, (unsigned long long)(long long)st);
+}
+
+enum { F_REC = 1, F_CUT = 2, F_TRACE = 4 };
+
+
+// ---------------------------------------------------------------------------
+// One history as three steps (shared by the history and event kernels).
+// Alg. 2 with the synthetic physics:
+//   dc = tau / Sigma (Sigma = 0: +inf); if d < dc: tally(d); r += d Omega;
+//   tau -= Sigma d; cross; else: tally(dc); r += dc Omega; collide.
+// tally adds llrint(len * 2^32) to the leaf instance's bin.  Collision e
+// (1-based) draws (xi_abs, xi_tau) from counter (pid, e, TAG_SCALARS, 0):
+// absorbed iff xi_abs < p_a, else a new isotropic direction at event e and
+// tau = -log(xi_tau); the on-surface state is cleared.  A history stops
+// after max_segments segments.
+// ---------------------------------------------------------------------------
+struct Ctx {
+    uint32_t pid, event;
+    long long nseg;
+    double path;
+    uint64_t hash;
+    int status;
+};
+
+enum { A_CROSS = 0, A_COLLIDE = 1, A_FLY = 2, A_DONE = 3 };
+
+template <bool CSG, int FLAGS>
+__device__ __forceinline__ int step_flight(const DevGeom& g, St& s, Hit& h, Ctx& c, const RunP& rp,
+                                           unsigned long long* __restrict__ tally, Counts& cnt,
+                                           int* __restrict__ tr_inst, double* __restrict__ tr_len, long long i) {
+    h = distance_to_boundary<CSG>(g, s);
+    const double sig = __ldg(g.sigma + s.mat);
+    const double dc = d_gt0(sig) ? s.tau / sig : DINF;
+    const bool crossing = d_lt(h.d, dc);
+    double len = crossing ? h.d : dc;
+    if (!d_finite_lt_inf(len)) { c.status = TRK_E_LOST; cnt.k[TRK_K_LOST]++; return A_DONE; }
+    const int inst = instance(s);
+    bool stop_cut = false;
+    if (FLAGS & F_CUT) {
+        if (!d_lt(c.path + len, rp.max_path)) { len = rp.max_path - c.path; stop_cut = true; }
+        else c.path = c.path + len;
+    }
+    const long long q = __double2ll_rn(len * 4294967296.0);
+    atomicAdd(tally + inst, (unsigned long long)q);
+    if (FLAGS & F_REC) c.hash = fnv(fnv(c.hash, uint64_t(int64_t(inst))), uint64_t(dbits(len)));
+    if (FLAGS & F_TRACE) {
+        if (c.nseg < rp.trace_cap) {
+            tr_inst[i * rp.trace_cap + c.nseg] = inst;
+            tr_len[i * rp.trace_cap + c.nseg] = len;
+        }
+    }
+    s.x = s.x + len * s.d.u;
+    s.y = s.y + len * s.d.v;
+    s.z = s.z + len * s.d.w;
+    c.nseg++;
+    cnt.k[TRK_K_SEGMENTS]++;
+    if (stop_cut) { c.status = TRK_P_CUTOFF; cnt.k[TRK_K_CUTOFF]++; return A_DONE; }
+    if (crossing) {
+        s.tau = s.tau - sig * h.d;
+        cnt.k[TRK_K_CROSSINGS]++;
+        return A_CROSS;
+    }
+    return A_COLLIDE;
+}
+
+__device__ __forceinline__ int after_step(Ctx& c, const RunP& rp, Counts& cnt) {
+    if (uint64_t(c.nseg) >= rp.max_segments) { c.status = TRK_E_MAX_SEGMENTS; cnt.k[TRK_K_MAXSEG]++; return A_DONE; }
+    return A_FLY;
+}
+
+template <bool CSG>
+__device__ __forceinline__ int step_cross(const DevGeom& g, St& s, const Hit& h, Ctx& c, const RunP& rp, Counts& cnt) {
+    int fl;
+    int cr = cross_surface<CSG>(g, s, h, fl);
+    if (cr == CR_FIND) cr = find_from<CSG>(g, s, fl) == 0 ? CR_OK : CR_LOST;
+    if (cr == CR_ESCAPE) { c.status = TRK_P_ESCAPED; cnt.k[TRK_K_ESCAPED]++; return A_DONE; }
+    if (cr == CR_LOST) { c.status = TRK_E_LOST; cnt.k[TRK_K_LOST]++; return A_DONE; }
+    if (cr == CR_REFLECT) cnt.k[TRK_K_REFLECTIONS]++;
+    return after_step(c, rp, cnt);
+}
+
+__device__ __forceinline__ int step_collide(const DevGeom& g, St& s, Ctx& c, const RunP& rp, Counts& cnt) {
+    const uint32_t gid = uint32_t(g.gid);
+    ++c.event;
+    cnt.k[TRK_K_COLLISIONS]++;
+    double xa, xt;
+    uniform2(c.pid, c.event, TAG_SCALARS, 0, rp.seed_lo, gid, xa, xt);
+    if (d_lt(xa, rp.p_absorb)) { c.status = TRK_P_ABSORBED; cnt.k[TRK_K_ABSORBED]++; return A_DONE; }
+    if (!isotropic(c.pid, c.event, rp.seed_lo, gid, s.d.u, s.d.v, s.d.w)) {
+        c.status = TRK_E_LOST; cnt.k[TRK_K_LOST]++; return A_DONE;
+    }
+    set_inverse(s.d);
+    s.tau = -own_log(xt);
+    s.on_lev = -1;
+    s.on_surf = -1;
+    return after_step(c, rp, cnt);
+}
+
+// Birth: state from source_init's buffer, then find_cell from the root.
+__device__ __forceinline__ bool load_birth(const DevGeom& g, const ParticlesView& P, long long i, St& s) {
+    clear_levels(s);
+    s.x = P.x[i]; s.y = P.y[i]; s.z = P.z[i];
+    s.d.u = P.u[i]; s.d.v = P.v[i]; s.d.w = P.w[i];
+    s.tau = P.tau[i];
+    set_inverse(s.d);
+    s.lv[0].u = g.root;
+    return true;
+}
+
 }  // namespace dev
 }  // namespace trk

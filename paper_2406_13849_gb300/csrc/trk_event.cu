@@ -1,0 +1,367 @@
+// trk_event.cu - persistent event-based kernel (sm_103a).
+//
+// Paper: Sec. 2.3 (event-based GPU transport: tracking operations run over a
+// vector of histories, one operation at a time) on top of Alg. 2-10.
+//
+// GB300 design.  Each CTA owns `slots` particle slots whose state lives in
+// the caller's work buffer (structure of arrays, L2-resident) and keeps four
+// queues of slot indices in shared memory: flight (distance_to_surface +
+// move_within_cell + tally), cross (cross_surface + find_cell below),
+// collide (change_direction), free.  A round runs refill, then flight over
+// the whole flight queue, then cross and collide over their queues, with
+// every thread of the CTA on one kind of operation, so warps stay converged
+// where the history kernel diverges.  Pushes are warp-aggregated (ballot +
+// one shared atomic per warp).  Empty slots take new particles from one
+// global counter.  No CTA ever waits for another: the only waits are
+// __syncthreads, and a round limit turns a runaway into TRK_E_TIMEOUT.
+// Per-particle arithmetic is the history kernel's, so results are the same
+// bit for bit.
+#include <cstdint>
+
+#include "trk.h"
+#include "trk_device.cuh"
+#include "trk_internal.h"
+#include "trk_launch.h"
+
+using namespace trk;
+using namespace trk::dev;
+
+namespace {
+
+constexpr int EV_BLOCK = 256;
+
+// slot state fields
+enum DField { D_X, D_Y, D_Z, D_U, D_V, D_W, D_IU, D_IV, D_IW, D_TAU, D_PATH, D_HD, D_T0, ND = D_T0 + 3 * MAXL };
+enum IField { I_NLEV, I_ONL, I_ONS, I_MAT, I_PIDX, I_EVENT, I_NSEG, I_STATUS, I_HLEV, I_HSURF, I_HSIDE, I_HDIM,
+              I_HSIGN, I_HENTRY, I_L0, NI = I_L0 + 6 * MAXL };
+
+struct EvBuf {
+    double* dv;
+    int* iv;
+    unsigned long long* hash;
+    unsigned long long* ctr;    // [0] next particle index
+    long long T;                // total slots
+    __device__ __forceinline__ double& D(int f, int s) const { return dv[(long long)f * T + s]; }
+    __device__ __forceinline__ int& I(int f, int s) const { return iv[(long long)f * T + s]; }
+};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+size_t buf_bytes(long long T) {
+    return 256 + align256(size_t(T) * ND * 8) + align256(size_t(T) * NI * 4) + align256(size_t(T) * 8);
+}
+
+EvBuf make_buf(void* work, long long T) {
+    unsigned char* b = static_cast<unsigned char*>(work);
+    EvBuf e;
+    e.ctr = reinterpret_cast<unsigned long long*>(b);
+    size_t off = 256;
+    e.dv = reinterpret_cast<double*>(b + off);
+    off += align256(size_t(T) * ND * 8);
+    e.iv = reinterpret_cast<int*>(b + off);
+    off += align256(size_t(T) * NI * 4);
+    e.hash = reinterpret_cast<unsigned long long*>(b + off);
+    e.T = T;
+    return e;
+}
+
+__device__ __forceinline__ void load_state(const EvBuf& B, int s, St& st) {
+    st.x = B.D(D_X, s); st.y = B.D(D_Y, s); st.z = B.D(D_Z, s);
+    st.d.u = B.D(D_U, s); st.d.v = B.D(D_V, s); st.d.w = B.D(D_W, s);
+    st.d.iu = B.D(D_IU, s); st.d.iv = B.D(D_IV, s); st.d.iw = B.D(D_IW, s);
+    st.tau = B.D(D_TAU, s);
+    st.nlev = B.I(I_NLEV, s); st.on_lev = B.I(I_ONL, s); st.on_surf = B.I(I_ONS, s); st.mat = B.I(I_MAT, s);
+#pragma unroll
+    for (int l = 0; l < MAXL; ++l) {
+        Lv& L = st.lv[l];
+        L.tx = B.D(D_T0 + 3 * l, s); L.ty = B.D(D_T0 + 3 * l + 1, s); L.tz = B.D(D_T0 + 3 * l + 2, s);
+        L.u = B.I(I_L0 + 6 * l, s); L.cell = B.I(I_L0 + 6 * l + 1, s); L.i = B.I(I_L0 + 6 * l + 2, s);
+        L.j = B.I(I_L0 + 6 * l + 3, s); L.k = B.I(I_L0 + 6 * l + 4, s); L.off = B.I(I_L0 + 6 * l + 5, s);
+    }
+}
+
+__device__ __forceinline__ void store_levels(const EvBuf& B, int s, const St& st) {
+    B.I(I_NLEV, s) = st.nlev; B.I(I_ONL, s) = st.on_lev; B.I(I_ONS, s) = st.on_surf; B.I(I_MAT, s) = st.mat;
+#pragma unroll
+    for (int l = 0; l < MAXL; ++l) {
+        const Lv& L = st.lv[l];
+        B.D(D_T0 + 3 * l, s) = L.tx; B.D(D_T0 + 3 * l + 1, s) = L.ty; B.D(D_T0 + 3 * l + 2, s) = L.tz;
+        B.I(I_L0 + 6 * l, s) = L.u; B.I(I_L0 + 6 * l + 1, s) = L.cell; B.I(I_L0 + 6 * l + 2, s) = L.i;
+        B.I(I_L0 + 6 * l + 3, s) = L.j; B.I(I_L0 + 6 * l + 4, s) = L.k; B.I(I_L0 + 6 * l + 5, s) = L.off;
+    }
+}
+
+__device__ __forceinline__ void store_dir(const EvBuf& B, int s, const St& st) {
+    B.D(D_U, s) = st.d.u; B.D(D_V, s) = st.d.v; B.D(D_W, s) = st.d.w;
+    B.D(D_IU, s) = st.d.iu; B.D(D_IV, s) = st.d.iv; B.D(D_IW, s) = st.d.iw;
+}
+
+__device__ __forceinline__ void load_ctx(const EvBuf& B, int s, Ctx& c, const RunP& rp) {
+    const int pidx = B.I(I_PIDX, s);
+    c.pid = uint32_t(rp.first_id + uint64_t(uint32_t(pidx)));
+    c.event = uint32_t(B.I(I_EVENT, s));
+    c.nseg = (long long)(uint32_t)B.I(I_NSEG, s);
+    c.path = B.D(D_PATH, s);
+    c.hash = B.hash[s];
+    c.status = B.I(I_STATUS, s);
+}
+
+__device__ __forceinline__ void store_ctx(const EvBuf& B, int s, const Ctx& c) {
+    B.I(I_EVENT, s) = int(c.event);
+    B.I(I_NSEG, s) = int(uint32_t(c.nseg));
+    B.D(D_PATH, s) = c.path;
+    B.hash[s] = c.hash;
+    B.I(I_STATUS, s) = c.status;
+}
+
+// Warp-aggregated append of `v` to list/count when `flag` (all lanes call).
+__device__ __forceinline__ void push(bool flag, int v, int* list, int* count) {
+    const unsigned m = __ballot_sync(0xffffffffu, flag);
+    if (m == 0) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(count, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (flag) list[base + __popc(m & ((1u << lane) - 1u))] = v;
+}
+
+template <int FLAGS>
+__device__ __forceinline__ void finish(const EvBuf& B, int s, const Ctx& c, unsigned long long* rec) {
+    if (FLAGS & F_REC) {
+        const long long pidx = (long long)(uint32_t)B.I(I_PIDX, s);
+        rec[2 * pidx] = c.hash;
+        rec[2 * pidx + 1] = (uint64_t(c.nseg) << 32) | uint32_t(c.status);
+    }
+}
+
+template <bool CSG, int FLAGS>
+__global__ void __launch_bounds__(EV_BLOCK) k_event(const DevGeom g, const ParticlesView P, long long n, const RunP rp,
+                                                    const EvBuf B, int slots, unsigned long long max_rounds,
+                                                    unsigned long long* __restrict__ tally,
+                                                    unsigned long long* __restrict__ counters,
+                                                    unsigned long long* __restrict__ rec) {
+    extern __shared__ int smem[];
+    int* qa = smem;               // flight queue (this round)
+    int* qb = smem + slots;       // flight queue (next round)
+    int* qx = smem + 2 * slots;   // cross
+    int* qc = smem + 3 * slots;   // collide
+    int* qf = smem + 4 * slots;   // free
+    __shared__ int n_fly, n_next, n_cross, n_coll, n_free, exhausted, refill_got;
+    __shared__ unsigned long long refill_base;
+    const int tid = threadIdx.x;
+    const int slot0 = blockIdx.x * slots;
+    Counts cnt;
+#pragma unroll
+    for (int k = 0; k < NCOUNT; ++k) cnt.k[k] = 0;
+    for (int k = tid; k < slots; k += EV_BLOCK) qf[k] = slot0 + k;
+    if (tid == 0) { n_fly = 0; n_next = 0; n_cross = 0; n_coll = 0; n_free = slots; exhausted = 0; }
+    __syncthreads();
+    int* fly = qa;
+    int* next = qb;
+    for (unsigned long long round = 0;; ++round) {
+        // ---- refill free slots with new particles --------------------------
+        if (tid == 0) {
+            refill_got = 0;
+            if (!exhausted && n_free > 0) {
+                const unsigned long long b = atomicAdd(B.ctr, (unsigned long long)n_free);
+                refill_base = b;
+                long long got = (long long)n - (long long)b;
+                if (got <= 0) { got = 0; exhausted = 1; }
+                if (got >= n_free) got = n_free;
+                else exhausted = 1;
+                refill_got = int(got);
+            }
+        }
+        __syncthreads();
+        const int got = refill_got;
+        const int free_before = n_free;
+        for (int base = 0; base < got; base += EV_BLOCK) {
+            const int k = base + tid;
+            bool ok = false;
+            int slot = 0;
+            if (k < got) {
+                slot = qf[free_before - got + k];
+                const long long pidx = (long long)refill_base + k;
+                Ctx c;
+                c.pid = uint32_t(rp.first_id + uint64_t(pidx));
+                c.event = 0; c.nseg = 0; c.path = 0.0; c.hash = FNV0; c.status = 0;
+                B.I(I_PIDX, slot) = int(pidx);
+                const int pst = P.status[pidx];
+                if (pst != 0) {
+                    c.status = pst;
+                    cnt.k[TRK_K_SOURCE]++;
+                } else {
+                    St s;
+                    load_birth(g, P, pidx, s);
+                    if (find_from<CSG>(g, s, 0) != 0) {
+                        c.status = TRK_E_LOST;
+                        cnt.k[TRK_K_LOST]++;
+                    } else {
+                        B.D(D_X, slot) = s.x; B.D(D_Y, slot) = s.y; B.D(D_Z, slot) = s.z; B.D(D_TAU, slot) = s.tau;
+                        store_dir(B, slot, s);
+                        store_levels(B, slot, s);
+                        ok = true;
+                    }
+                }
+                store_ctx(B, slot, c);
+                if (!ok) finish<FLAGS>(B, slot, c, rec);
+            }
+            push(ok, slot, fly, &n_fly);
+            push(k < got && !ok, slot, next, &n_next);   // dead at birth: slot parked, freed below
+        }
+        __syncthreads();
+        if (tid == 0) n_free = free_before - got;
+        __syncthreads();
+        // parked dead-at-birth slots return to the free list
+        {
+            const int parked = n_next;
+            for (int base = 0; base < parked; base += EV_BLOCK) {
+                const int k = base + tid;
+                const bool f = k < parked;
+                push(f, f ? next[k] : 0, qf, &n_free);
+            }
+            __syncthreads();
+            if (tid == 0) n_next = 0;
+        }
+        __syncthreads();
+        if (n_fly == 0 && exhausted) break;
+        if (round >= max_rounds) {
+            if (tid == 0) kernel_status(counters, TRK_E_TIMEOUT);
+            break;
+        }
+        // ---- flight: distance_to_surface, tally, move ----------------------
+        const int nf = n_fly;
+        for (int base = 0; base < nf; base += EV_BLOCK) {
+            const int k = base + tid;
+            int a = A_DONE, slot = 0;
+            if (k < nf) {
+                slot = fly[k];
+                St s;
+                load_state(B, slot, s);
+                Ctx c;
+                load_ctx(B, slot, c, rp);
+                Hit h;
+                a = step_flight<CSG, FLAGS>(g, s, h, c, rp, tally, cnt, nullptr, nullptr, 0);
+                B.D(D_X, slot) = s.x; B.D(D_Y, slot) = s.y; B.D(D_Z, slot) = s.z; B.D(D_TAU, slot) = s.tau;
+                store_ctx(B, slot, c);
+                if (a == A_CROSS) {
+                    B.D(D_HD, slot) = h.d;
+                    B.I(I_HLEV, slot) = h.level; B.I(I_HSURF, slot) = h.surf; B.I(I_HSIDE, slot) = h.side;
+                    B.I(I_HDIM, slot) = h.dim; B.I(I_HSIGN, slot) = h.dsign; B.I(I_HENTRY, slot) = h.entry;
+                }
+                if (a == A_DONE) finish<FLAGS>(B, slot, c, rec);
+            }
+            push(k < nf && a == A_CROSS, slot, qx, &n_cross);
+            push(k < nf && a == A_COLLIDE, slot, qc, &n_coll);
+            push(k < nf && a == A_DONE, slot, qf, &n_free);
+        }
+        __syncthreads();
+        // ---- cross_surface and change_direction ------------------------------
+        const int ncr = n_cross, nco = n_coll;
+        for (int base = 0; base < ncr + nco; base += EV_BLOCK) {
+            const int k = base + tid;
+            int a = A_DONE, slot = 0;
+            if (k < ncr) {
+                slot = qx[k];
+                St s;
+                load_state(B, slot, s);
+                Ctx c;
+                load_ctx(B, slot, c, rp);
+                Hit h;
+                h.d = B.D(D_HD, slot);
+                h.level = B.I(I_HLEV, slot); h.surf = B.I(I_HSURF, slot); h.side = B.I(I_HSIDE, slot);
+                h.dim = B.I(I_HDIM, slot); h.dsign = B.I(I_HSIGN, slot); h.entry = B.I(I_HENTRY, slot);
+                a = step_cross<CSG>(g, s, h, c, rp, cnt);
+                store_levels(B, slot, s);
+                store_dir(B, slot, s);
+                store_ctx(B, slot, c);
+                if (a == A_DONE) finish<FLAGS>(B, slot, c, rec);
+            } else if (k < ncr + nco) {
+                slot = qc[k - ncr];
+                St s;
+                s.d.u = B.D(D_U, slot); s.d.v = B.D(D_V, slot); s.d.w = B.D(D_W, slot);
+                s.tau = B.D(D_TAU, slot);
+                Ctx c;
+                load_ctx(B, slot, c, rp);
+                a = step_collide(g, s, c, rp, cnt);
+                if (a != A_DONE) {
+                    store_dir(B, slot, s);
+                    B.D(D_TAU, slot) = s.tau;
+                    B.I(I_ONL, slot) = -1;
+                    B.I(I_ONS, slot) = -1;
+                }
+                store_ctx(B, slot, c);
+                if (a == A_DONE) finish<FLAGS>(B, slot, c, rec);
+            }
+            const bool live = k < ncr + nco;
+            push(live && a == A_FLY, slot, next, &n_next);
+            push(live && a == A_DONE, slot, qf, &n_free);
+        }
+        __syncthreads();
+        int* t = fly; fly = next; next = t;
+        if (tid == 0) { n_fly = n_next; n_next = 0; n_cross = 0; n_coll = 0; }
+        __syncthreads();
+    }
+    flush_counts(cnt, counters);
+}
+
+}  // namespace
+
+namespace trk {
+
+int event_grid(int slots) {
+    (void)slots;
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int per_sm = 1;
+    const size_t smem = size_t(5) * slots * sizeof(int);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_event<true, 0>, EV_BLOCK, smem) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    return sms * per_sm;
+}
+
+size_t event_work_bytes(int slots, int grid) { return buf_bytes((long long)slots * grid); }
+
+trk_status launch_event(trk_geom_t g, const ParticlesView& P, long long n, const RunP& rp, bool csg, int flags,
+                        unsigned long long* tally, unsigned long long* cnt, unsigned long long* rec, void* work,
+                        size_t work_bytes, int slots, int grid, cudaStream_t s) {
+    const long long T = (long long)slots * grid;
+    if (work_bytes < buf_bytes(T) || !work)
+        return trk_status(set_error(TRK_E_NOMEM, "run_histories (event): work buffer needs %zu bytes", buf_bytes(T)));
+    const EvBuf B = make_buf(work, T);
+    cudaError_t e = cudaMemsetAsync(B.ctr, 0, 8, s);
+    if (e != cudaSuccess) return trk_status(set_error(TRK_E_CUDA, "run_histories (event): %s", cudaGetErrorString(e)));
+    const size_t smem = size_t(5) * slots * sizeof(int);
+    // every particle needs at most max_segments + 1 flight rounds; a CTA
+    // sees at most its share plus a slot's worth of refills
+    const unsigned long long per_cta = (unsigned long long)(n / grid + slots + 1);
+    const unsigned long long max_rounds = (rp.max_segments + 2ULL) * (per_cta / slots + 2ULL) * 4ULL;
+#define TRK_EV(C, F)                                                                                         \
+    do {                                                                                                     \
+        auto k = k_event<C, F>;                                                                              \
+        if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)); \
+        k<<<grid, EV_BLOCK, smem, s>>>(g->dg, P, n, rp, B, slots, max_rounds, tally, cnt, rec);             \
+    } while (0)
+    if (csg) {
+        switch (flags) {
+            case 0: TRK_EV(true, 0); break;
+            case F_REC: TRK_EV(true, F_REC); break;
+            case F_CUT: TRK_EV(true, F_CUT); break;
+            default: TRK_EV(true, F_REC | F_CUT); break;
+        }
+    } else {
+        switch (flags) {
+            case 0: TRK_EV(false, 0); break;
+            case F_REC: TRK_EV(false, F_REC); break;
+            case F_CUT: TRK_EV(false, F_CUT); break;
+            default: TRK_EV(false, F_REC | F_CUT); break;
+        }
+    }
+#undef TRK_EV
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return trk_status(set_error(TRK_E_CUDA, "run_histories (event): %s", cudaGetErrorString(e)));
+    return TRK_OK;
+}
+
+}  // namespace trk

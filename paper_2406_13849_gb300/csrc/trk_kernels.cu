@@ -23,141 +23,49 @@
 #include "trk.h"
 #include "trk_device.cuh"
 #include "trk_internal.h"
+#include "trk_launch.h"
 
 using namespace trk;
 using namespace trk::dev;
 
 namespace {
 
-// ---------------------------------------------------------------------------
-// Run parameters and per-thread counters
-// ---------------------------------------------------------------------------
-struct RunP {
-    uint64_t first_id;
-    uint64_t max_segments;
-    double p_absorb;
-    double max_path;
-    uint32_t seed_lo;
-    int trace_cap;
-};
 
-// Per-thread event counts (32-bit: one thread tracks far fewer than 2^32
-// segments), reduced over the warp and added once per warp at kernel end.
-constexpr int NCOUNT = 11;
-struct Counts {
-    unsigned k[NCOUNT];
-};
-
-__device__ __forceinline__ void flush_counts(Counts& c, unsigned long long* out) {
-#pragma unroll
-    for (int i = 0; i < NCOUNT; ++i) {
-        unsigned long long v = c.k[i];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if ((threadIdx.x & 31) == 0 && v) atomicAdd(out + i, v);
-    }
-}
-
-__device__ __forceinline__ void kernel_status(unsigned long long* cnt, int st) {
-    atomicCAS(cnt + TRK_K_STATUS, 0ULL, (unsigned long long)(long long)st);
-}
-
-enum { F_REC = 1, F_CUT = 2, F_TRACE = 4 };
-
-// One history of Alg. 2 with the synthetic physics:
-//   dc = tau / Sigma (Sigma = 0: +inf); if d < dc: tally(d); r += d Omega;
-//   tau -= Sigma d; cross; else: tally(dc); r += dc Omega; collide.
-// tally adds llrint(len * 2^32) to the leaf instance's bin.  Collision e
-// (1-based) draws (xi_abs, xi_tau) from counter (pid, e, TAG_SCALARS, 0):
-// absorbed iff xi_abs < p_a, else a new isotropic direction at event e and
-// tau = -log(xi_tau); the on-surface state is cleared.
+// One history (Alg. 2): flight, then cross or collide, until it ends.
 template <bool CSG, int FLAGS>
 __device__ __forceinline__ void history(const DevGeom& g, const ParticlesView& P, long long i, const RunP& rp,
                                         unsigned long long* __restrict__ tally, Counts& cnt,
                                         unsigned long long* __restrict__ rec, int* __restrict__ tr_inst,
-                                        double* __restrict__ tr_len, unsigned long long* kcnt) {
-    const uint32_t pid = uint32_t(rp.first_id + uint64_t(i));
-    const uint32_t gid = uint32_t(g.gid);
-    uint64_t hash = FNV0;
-    long long nseg = 0;
-    int status = 0;
+                                        double* __restrict__ tr_len) {
+    Ctx c;
+    c.pid = uint32_t(rp.first_id + uint64_t(i));
+    c.event = 0; c.nseg = 0; c.path = 0.0; c.hash = FNV0; c.status = 0;
     const int pst = P.status[i];
     if (pst != 0) {
-        status = pst;
+        c.status = pst;
         cnt.k[TRK_K_SOURCE]++;
     } else {
         St s;
-        clear_levels(s);
-        s.x = P.x[i]; s.y = P.y[i]; s.z = P.z[i];
-        s.d.u = P.u[i]; s.d.v = P.v[i]; s.d.w = P.w[i];
-        s.tau = P.tau[i];
-        set_inverse(s.d);
-        s.lv[0].u = g.root;
+        load_birth(g, P, i, s);
         if (find_from<CSG>(g, s, 0) != 0) {
-            status = TRK_E_LOST;
+            c.status = TRK_E_LOST;
             cnt.k[TRK_K_LOST]++;
         } else {
-            uint32_t event = 0;
-            double path = 0.0;
             for (;;) {
-                const Hit h = distance_to_boundary<CSG>(g, s);
-                const double sig = __ldg(g.sigma + s.mat);
-                const double dc = d_gt0(sig) ? s.tau / sig : DINF;
-                const bool crossing = d_lt(h.d, dc);
-                double len = crossing ? h.d : dc;
-                if (!d_finite_lt_inf(len)) { status = TRK_E_LOST; cnt.k[TRK_K_LOST]++; break; }
-                const int inst = instance(s);
-                bool stop_cut = false;
-                if (FLAGS & F_CUT) {
-                    if (!d_lt(path + len, rp.max_path)) { len = rp.max_path - path; stop_cut = true; }
-                    else path = path + len;
-                }
-                const long long q = __double2ll_rn(len * 4294967296.0);
-                atomicAdd(tally + inst, (unsigned long long)q);
-                if (FLAGS & F_REC) hash = fnv(fnv(hash, uint64_t(int64_t(inst))), uint64_t(__double_as_longlong(len)));
-                if (FLAGS & F_TRACE) {
-                    if (nseg < rp.trace_cap) {
-                        tr_inst[i * rp.trace_cap + nseg] = inst;
-                        tr_len[i * rp.trace_cap + nseg] = len;
-                    }
-                }
-                s.x = s.x + len * s.d.u;
-                s.y = s.y + len * s.d.v;
-                s.z = s.z + len * s.d.w;
-                nseg++;
-                cnt.k[TRK_K_SEGMENTS]++;
-                if (stop_cut) { status = TRK_P_CUTOFF; cnt.k[TRK_K_CUTOFF]++; break; }
-                if (crossing) {
-                    s.tau = s.tau - sig * h.d;
-                    cnt.k[TRK_K_CROSSINGS]++;
-                    int fl;
-                    int cr = cross_surface<CSG>(g, s, h, fl);
-                    if (cr == CR_FIND) cr = find_from<CSG>(g, s, fl) == 0 ? CR_OK : CR_LOST;
-                    if (cr == CR_ESCAPE) { status = TRK_P_ESCAPED; cnt.k[TRK_K_ESCAPED]++; break; }
-                    if (cr == CR_LOST) { status = TRK_E_LOST; cnt.k[TRK_K_LOST]++; break; }
-                    if (cr == CR_REFLECT) cnt.k[TRK_K_REFLECTIONS]++;
-                } else {
-                    ++event;
-                    cnt.k[TRK_K_COLLISIONS]++;
-                    double xa, xt;
-                    uniform2(pid, event, TAG_SCALARS, 0, rp.seed_lo, gid, xa, xt);
-                    if (d_lt(xa, rp.p_absorb)) { status = TRK_P_ABSORBED; cnt.k[TRK_K_ABSORBED]++; break; }
-                    if (!isotropic(pid, event, rp.seed_lo, gid, s.d.u, s.d.v, s.d.w)) { status = TRK_E_LOST; cnt.k[TRK_K_LOST]++; break; }
-                    set_inverse(s.d);
-                    s.tau = -own_log(xt);
-                    s.on_lev = -1;
-                    s.on_surf = -1;
-                }
-                if (uint64_t(nseg) >= rp.max_segments) { status = TRK_E_MAX_SEGMENTS; cnt.k[TRK_K_MAXSEG]++; break; }
+                Hit h;
+                int a = step_flight<CSG, FLAGS>(g, s, h, c, rp, tally, cnt, tr_inst, tr_len, i);
+                if (a == A_DONE) break;
+                a = (a == A_CROSS) ? step_cross<CSG>(g, s, h, c, rp, cnt) : step_collide(g, s, c, rp, cnt);
+                if (a == A_DONE) break;
             }
         }
     }
     if (FLAGS & F_REC) {
-        rec[2 * i] = hash;
-        rec[2 * i + 1] = (uint64_t(nseg) << 32) | uint32_t(status);
+        rec[2 * i] = c.hash;
+        rec[2 * i + 1] = (uint64_t(c.nseg) << 32) | uint32_t(c.status);
     }
     if (FLAGS & F_TRACE) {
-        for (long long k = nseg; k < rp.trace_cap; ++k) { tr_inst[i * rp.trace_cap + k] = -1; tr_len[i * rp.trace_cap + k] = 0.0; }
+        for (long long k = c.nseg; k < rp.trace_cap; ++k) { tr_inst[i * rp.trace_cap + k] = -1; tr_len[i * rp.trace_cap + k] = 0.0; }
     }
 }
 
@@ -172,7 +80,7 @@ __global__ void __launch_bounds__(128) k_history(const DevGeom g, const Particle
     for (int k = 0; k < NCOUNT; ++k) c.k[k] = 0;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-        history<CSG, FLAGS>(g, P, i, rp, tally, c, rec, tr_inst, tr_len, counters);
+        history<CSG, FLAGS>(g, P, i, rp, tally, c, rec, tr_inst, tr_len);
     flush_counts(c, counters);
 }
 
@@ -523,17 +431,28 @@ trk_status source_init(trk_geom_t g, int64_t n, uint64_t first_id, uint64_t seed
     return launch_error("source_init");
 }
 
-trk_status run_histories_work_bytes(trk_geom_t g, int64_t n, const trk_run_opts* o, size_t* bytes) {
+constexpr int DEFAULT_SLOTS = 512;
+
+int event_slots(const trk_run_opts& o) { return o.queue_depth > 0 ? o.queue_depth : DEFAULT_SLOTS; }
+
+trk_status run_histories_work_bytes(trk_geom_t g, int64_t n, const trk_run_opts* opts, size_t* bytes) {
     if (!valid(g) || !bytes || n < 0) return trk_status(set_error(TRK_E_INVALID, "run_histories_work_bytes: bad arguments"));
-    (void)o;
+    trk_run_opts o;
+    trk_default_opts(&o);
+    if (opts) o = *opts;
     *bytes = 0;
+    if (o.mode == TRK_MODE_EVENT) {
+        const int slots = event_slots(o);
+        if (slots < 32 || slots > 4096) return trk_status(set_error(TRK_E_INVALID, "queue_depth must be in [32, 4096]"));
+        const int grid = o.grid > 0 ? o.grid : event_grid(slots);
+        *bytes = event_work_bytes(slots, grid);
+    }
     return TRK_OK;
 }
 
 trk_status run_histories(trk_geom_t g, const void* dev_particles, int64_t n, uint64_t* dev_tally,
                          uint64_t* dev_counters, uint64_t* dev_records, void* dev_work, size_t work_bytes,
                          const trk_run_opts* opts, void* stream) {
-    (void)dev_work; (void)work_bytes;
     if (!valid(g)) return trk_status(set_error(TRK_E_INVALID, "run_histories: invalid handle"));
     if (n < 0 || (n > 0 && (!dev_particles || !dev_tally || !dev_counters)))
         return trk_status(set_error(TRK_E_INVALID, "run_histories: null buffer or n < 0"));
@@ -544,7 +463,8 @@ trk_status run_histories(trk_geom_t g, const void* dev_particles, int64_t n, uin
     trk_status st;
     const int tracker = resolve_tracker(g, o.tracker, &st);
     if (tracker < 0) return st;
-    if (o.mode != TRK_MODE_HISTORY) return trk_status(set_error(TRK_E_UNSUPPORTED, "run_histories: mode %d not built", o.mode));
+    if (o.mode != TRK_MODE_HISTORY && o.mode != TRK_MODE_EVENT)
+        return trk_status(set_error(TRK_E_INVALID, "run_histories: unknown mode %d", o.mode));
     if (o.precision != TRK_FP64) return trk_status(set_error(TRK_E_UNSUPPORTED, "run_histories: precision %d not built", o.precision));
     if (!(o.p_absorb >= 0.0 && o.p_absorb <= 1.0)) return trk_status(set_error(TRK_E_INVALID, "run_histories: p_absorb outside [0,1]"));
     if (n == 0) return TRK_OK;
@@ -556,8 +476,6 @@ trk_status run_histories(trk_geom_t g, const void* dev_particles, int64_t n, uin
     rp.max_path = cut ? o.max_path : DINF;
     rp.seed_lo = uint32_t(o.seed);
     rp.trace_cap = 0;
-    const int block = o.block > 0 ? o.block : 128;
-    if (block > 128 || (block & 31)) return trk_status(set_error(TRK_E_INVALID, "run_histories: block must be a multiple of 32, <= 128"));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const ParticlesView P = view_of(dev_particles, n);
     auto* T = reinterpret_cast<unsigned long long*>(dev_tally);
@@ -565,6 +483,14 @@ trk_status run_histories(trk_geom_t g, const void* dev_particles, int64_t n, uin
     auto* R = reinterpret_cast<unsigned long long*>(dev_records);
     const bool csg = tracker == TRK_TRACKER_CSG;
     const int flags = (dev_records ? F_REC : 0) | (cut ? F_CUT : 0);
+    if (o.mode == TRK_MODE_EVENT) {
+        const int slots = event_slots(o);
+        if (slots < 32 || slots > 4096) return trk_status(set_error(TRK_E_INVALID, "queue_depth must be in [32, 4096]"));
+        const int grid = o.grid > 0 ? o.grid : event_grid(slots);
+        return launch_event(g, P, n, rp, csg, flags, T, C, R, dev_work, work_bytes, slots, grid, s);
+    }
+    const int block = o.block > 0 ? o.block : 128;
+    if (block > 128 || (block & 31)) return trk_status(set_error(TRK_E_INVALID, "run_histories: block must be a multiple of 32, <= 128"));
 #define TRK_LAUNCH(CSGV, F) return launch_history<CSGV, F>(g, P, n, rp, T, C, R, nullptr, nullptr, block, o.grid, s)
     if (csg) {
         switch (flags) {

@@ -1,0 +1,21 @@
+// trk_launch.h - launchers shared between the kernel translation units
+// (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "trk.h"
+#include "trk_device.cuh"
+#include "trk_internal.h"
+
+namespace trk {
+
+// Event kernel: CTAs to launch for `slots` particle slots per CTA (fills the
+// GPU at the kernel's occupancy), and the work bytes that needs.
+int event_grid(int slots);
+size_t event_work_bytes(int slots, int grid);
+
+trk_status launch_event(trk_geom_t g, const ParticlesView& P, long long n, const dev::RunP& rp, bool csg, int flags,
+                        unsigned long long* tally, unsigned long long* cnt, unsigned long long* rec, void* work,
+                        size_t work_bytes, int slots, int grid, cudaStream_t s);
+
+}  // namespace trk

@@ -309,3 +309,80 @@ def test_transmission_against_oracle(tracker, mode):
     grad = g.transmission_bwd(R, S, 1.26, gT, tracker=tracker).cpu().numpy()
     expect = (gT.cpu().numpy()[:, None] * ref["dT"]).sum(0)
     assert np.allclose(grad, expect, rtol=1e-10, atol=1e-14 * np.abs(expect).max())
+
+
+# ---------------------------------------------------------------------------
+# event-based persistent kernel
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", ["c1", "small_core", "c2", "tiny8"])
+@pytest.mark.parametrize("tracker,mode", [(N.TRACKER_RECT, O.MODE_RECT), (N.TRACKER_CSG, O.MODE_CSG)])
+def test_event_bit_exact(name, tracker, mode):
+    desc, pa, n = CASES[name]
+    o = _oracle(desc, mode).run(n, SEED, pa, threads=8)
+    g = _gpu(desc, exact=True)
+    parts = g.source_init(n, seed=SEED)
+    tally, cnt, rec = g.run_histories(parts, n, records=True, tracker=tracker, mode=N.MODE_EVENT,
+                                      p_absorb=pa, seed=SEED)
+    torch.cuda.synchronize()
+    h, nseg, st = N.unpack_records(rec)
+    assert np.array_equal(st, o["status"])
+    assert np.array_equal(nseg, o["nseg"])
+    assert np.array_equal(h, o["hash"])
+    assert np.array_equal(_u64(tally), o["tally"])
+    c = _u64(cnt)
+    assert np.array_equal(c[:10], o["counters"][:10]) and c[N.K["status"]] == 0
+
+
+@pytest.mark.parametrize("name", list(HEX_CASES))
+def test_event_bit_exact_hex(name):
+    desc, pa, n = HEX_CASES[name]
+    o = _oracle(desc, O.MODE_CSG).run(n, SEED, pa, threads=8)
+    g = _gpu(desc, exact=True)
+    parts = g.source_init(n, seed=SEED)
+    tally, cnt, rec = g.run_histories(parts, n, records=True, tracker=N.TRACKER_CSG, mode=N.MODE_EVENT,
+                                      p_absorb=pa, seed=SEED)
+    h, nseg, st = N.unpack_records(rec)
+    assert np.array_equal(h, o["hash"]) and np.array_equal(_u64(tally), o["tally"])
+
+
+@pytest.mark.parametrize("depth,grid", [(32, 1), (64, 3), (1024, 0), (4096, 2)])
+def test_event_queue_shapes(depth, grid):
+    desc, pa, n = CASES["small_core"]
+    n = 2_999
+    g = _gpu(desc, exact=True)
+    parts = g.source_init(n, seed=SEED)
+    ref = g.run_histories(parts, n, records=True, tracker=N.TRACKER_CSG, p_absorb=pa, seed=SEED)
+    got = g.run_histories(parts, n, records=True, tracker=N.TRACKER_CSG, mode=N.MODE_EVENT,
+                          queue_depth=depth, grid=grid, p_absorb=pa, seed=SEED)
+    torch.cuda.synchronize()
+    assert np.array_equal(_u64(ref[2]), _u64(got[2]))
+    assert np.array_equal(_u64(ref[0]), _u64(got[0]))
+    assert np.array_equal(_u64(ref[1]), _u64(got[1]))
+
+
+def test_event_cutoff_segment_cap_and_tiny_n():
+    desc = I.config1()
+    g = _gpu(desc, exact=True)
+    for n, kw, mode in ((1, {}, O.MODE_RECT), (5, {"max_segments": 3}, O.MODE_RECT),
+                        (700, {"max_path": 40.0}, O.MODE_CSG)):
+        o = _oracle(desc, mode).run(n, SEED, 0.3, **kw)
+        parts = g.source_init(n, seed=SEED)
+        tally, cnt, rec = g.run_histories(parts, n, records=True, mode=N.MODE_EVENT,
+                                          tracker=N.TRACKER_RECT if mode == O.MODE_RECT else N.TRACKER_CSG,
+                                          p_absorb=0.3, seed=SEED, **kw)
+        h, nseg, st = N.unpack_records(rec)
+        assert np.array_equal(h, o["hash"]) and np.array_equal(st, o["status"])
+
+
+def test_event_full_size_matches_history():
+    desc = I.config2()
+    n, pa = 10_000_000, 0.25
+    g = _gpu(desc, exact=True)
+    parts = g.source_init(n, seed=SEED)
+    a = g.run_histories(parts, n, records=True, tracker=N.TRACKER_CSG, p_absorb=pa, seed=SEED)
+    b = g.run_histories(parts, n, records=True, tracker=N.TRACKER_CSG, mode=N.MODE_EVENT, p_absorb=pa, seed=SEED)
+    torch.cuda.synchronize()
+    assert np.array_equal(_u64(a[0]), _u64(b[0]))
+    assert np.array_equal(_u64(a[1]), _u64(b[1]))
+    assert np.array_equal(_u64(a[2]), _u64(b[2]))
