@@ -79,7 +79,7 @@ typedef struct {
     int precision;          /* TRK_FP64 or TRK_FP32_LOCAL */
     int block;              /* threads per block, 0 = default */
     int grid;               /* blocks, 0 = default (a multiple of the SM count) */
-    int queue_depth;        /* event mode: particle slots per block, 0 = default */
+    int queue_depth;        /* event mode: particle slots per warp (32..1024), 0 = default 128 */
     int sort_interval;      /* event mode: regroup queues by cell every k rounds, 0 = never */
     int reserved;
     uint64_t seed;          /* low 32 bits key the Philox stream with the geometry id */

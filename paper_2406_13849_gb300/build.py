@@ -49,7 +49,10 @@ def outputs():
 
 
 def build(force: bool = False, verbose: bool = False) -> dict:
-    """Compile (if stale) and return the paths of both libraries."""
+    """Compile (if stale) and return the paths of both libraries.
+
+    TRK_NVCC_FLAGS (environment) adds flags to the kernel compiles, e.g.
+    -DTRK_EV_MINB=2 to change a kernel's register budget."""
     outs = outputs()
     if not force and not any(_stale(p) for p in outs.values()):
         return outs
@@ -65,13 +68,14 @@ def build(force: bool = False, verbose: bool = False) -> dict:
     peaks_obj = os.path.join(BUILD, "peaks.o")
     jobs.append([nvcc] + ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"] + inc +
                 ["-c", os.path.join(CSRC, "peaks.cu"), "-o", peaks_obj])
+    extra_flags = os.environ.get("TRK_NVCC_FLAGS", "").split()
     kobjs = {"fast": [], "exact": []}
     for flavour, extra in (("fast", []), ("exact", ["--fmad=false", "-DTRK_EXACT"])):
         for unit in KERNEL_UNITS:
             obj = os.path.join(BUILD, f"{unit}_{flavour}.o")
             kobjs[flavour].append(obj)
             jobs.append([nvcc] + ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-                                         "-Xcompiler", "-ffp-contract=off"] + extra + inc +
+                                         "-Xcompiler", "-ffp-contract=off"] + extra + extra_flags + inc +
                         ["-c", os.path.join(CSRC, unit + ".cu"), "-o", obj])
     procs = [subprocess.Popen(j, stdout=None if verbose else subprocess.PIPE,
                               stderr=subprocess.STDOUT) for j in jobs]

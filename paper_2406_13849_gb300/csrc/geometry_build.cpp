@@ -864,6 +864,7 @@ int build_host(const char* json, size_t len, Built& B) {
     std::vector<long long> s_key;
     for (auto& s : G.surf) s_key.push_back(s.type <= S_PZ ? okey(s.c[0]) : 0);
     std::vector<int2> c_range, cs_adj;
+    std::vector<int4> c_slab0, c_slab1;
     std::vector<int> cs, c_fill, c_off;
     std::vector<double> c_tr;
     std::vector<int4> u_info;
@@ -892,6 +893,21 @@ int build_host(const char* json, size_t len, Built& B) {
                 if (cand.size() > 2) cs_adj.push_back(make_int2(-2, -2));
                 else cs_adj.push_back(make_int2(cand.size() > 0 ? cand[0] : -1, cand.size() > 1 ? cand[1] : -1));
             }
+            // slab view for cells bounded by axis planes only, at most one
+            // lower and one upper plane per dimension
+            int slab[6] = {-1, -1, -1, -1, -1, -1};
+            bool pure = true;
+            const int first_entry = c_range.back().x;
+            for (size_t i = 0; i < c.surf.size(); ++i) {
+                const int type = G.surf[size_t(c.surf[i])].type;
+                const int slot = 2 * type + (c.sense[i] > 0 ? 0 : 1);
+                if (type > S_PZ || slab[slot] >= 0) { pure = false; break; }
+                slab[slot] = first_entry + int(i);
+            }
+            if (!pure) for (int k = 0; k < 6; ++k) slab[k] = -1;
+            else c_range.back().y |= CS_SLAB_FLAG;
+            c_slab0.push_back(make_int4(slab[0], slab[1], slab[2], slab[3]));
+            c_slab1.push_back(make_int4(slab[4], slab[5], 0, 0));
             c_fill.push_back(c.fill);
             c_off.push_back(int(c.off));
             for (int d = 0; d < 3; ++d) c_tr.push_back(c.tr[d]);
@@ -955,6 +971,8 @@ int build_host(const char* json, size_t len, Built& B) {
     o[18] = L.put(s_key.size() * 8);
     o[19] = L.put(cs_adj.size() * sizeof(int2));
     o[20] = L.put(l_gkey.size() * 8);
+    o[21] = L.put(c_slab0.size() * sizeof(int4));
+    o[22] = L.put(c_slab1.size() * sizeof(int4));
     B.image.assign(L.total, 0);
     copy_into(B.image, o[0], s_info);
     copy_into(B.image, o[1], s_coef);
@@ -977,6 +995,8 @@ int build_host(const char* json, size_t len, Built& B) {
     copy_into(B.image, o[18], s_key);
     copy_into(B.image, o[19], cs_adj);
     copy_into(B.image, o[20], l_gkey);
+    copy_into(B.image, o[21], c_slab0);
+    copy_into(B.image, o[22], c_slab1);
     return TRK_OK;
 }
 
@@ -1050,6 +1070,8 @@ trk_status geometry_build(const char* json, size_t len, void* dev_buf, size_t* d
     d.s_key = reinterpret_cast<const long long*>(base + o[18]);
     d.cs_adj = reinterpret_cast<const int2*>(base + o[19]);
     d.l_gkey = reinterpret_cast<const long long*>(base + o[20]);
+    d.c_slab0 = reinterpret_cast<const int4*>(base + o[21]);
+    d.c_slab1 = reinterpret_cast<const int4*>(base + o[22]);
     const HGeom& G = B.G;
     for (int k = 0; k < 3; ++k) { d.src_lo[k] = G.src[k]; d.src_hi[k] = G.src[3 + k]; }
     d.root = G.root;

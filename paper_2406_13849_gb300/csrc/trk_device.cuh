@@ -251,7 +251,8 @@ __device__ __forceinline__ double surface_distance(const DevGeom& g, int s, int 
 // logically with sense xsn instead of being evaluated.
 __device__ __forceinline__ bool cell_holds(const DevGeom& g, int c, const Pt& p, int xs, int xsn) {
     const int2 rg = __ldg(g.c_range + c);
-    for (int k = 0; k < rg.y; ++k) {
+    const int cnt = rg.y & CS_COUNT_MASK;
+    for (int k = 0; k < cnt; ++k) {
         const int e = __ldg(g.cs + rg.x + k);
         const int s = cs_surface(e), sn = cs_side(e);
         if (s == xs) {
@@ -471,14 +472,43 @@ __device__ __forceinline__ Hit distance_to_boundary(const DevGeom& g, const St& 
                 }
             }
         } else {
+            // CSG cell: candidates are its faces in cell order, strict '<'.
             const int2 rg = __ldg(g.c_range + L.cell);
-            for (int k = 0; k < rg.y; ++k) {
-                const int e = __ldg(g.cs + rg.x + k);
-                const int sid = cs_surface(e), side = cs_side(e);
-                const bool on = (s.on_lev == l && s.on_surf == sid);
-                const double t = surface_distance(g, sid, cs_type(e), side, on, x, y, z, s.d);
-                const long long tk = okey(t);
-                if (tk < hk) { hk = tk; h.d = t; h.level = l; h.surf = sid; h.side = side; h.dim = -1; h.dsign = 0; h.entry = rg.x + k; }
+            if (rg.y & CS_SLAB_FLAG) {
+                // Cell bounded by axis planes only (a pseudo-array element):
+                // per dimension the one face the direction leaves through, as
+                // in the rect tracker; ties go to the lower entry index, which
+                // is the cell-order scan's result.
+                const int4 s0 = __ldg(g.c_slab0 + L.cell), s1 = __ldg(g.c_slab1 + L.cell);
+                const int lo3[3] = {s0.x, s0.z, s1.x};
+                const int hi3[3] = {s0.y, s0.w, s1.y};
+                const double p3[3] = {x, y, z};
+                const double d3[3] = {s.d.u, s.d.v, s.d.w};
+                const double v3[3] = {s.d.iu, s.d.iv, s.d.iw};
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    const int e = d_gt0(d3[d]) ? hi3[d] : (d_lt0(d3[d]) ? lo3[d] : -1);
+                    if (e < 0) continue;
+                    const int sid = cs_surface(__ldg(g.cs + e));
+                    if (s.on_lev == l && s.on_surf == sid) continue;
+                    double t = (__ldg(g.s_coef + 4 * sid) - p3[d]) * v3[d];
+                    if (d_lt0(t)) t = 0.0;
+                    const long long tk = okey(t);
+                    if (tk < hk || (tk == hk && h.level == l && e < h.entry)) {
+                        hk = tk; h.d = t; h.level = l; h.surf = sid; h.side = d_gt0(d3[d]) ? -1 : 1;
+                        h.dim = -1; h.dsign = 0; h.entry = e;
+                    }
+                }
+            } else {
+                const int cnt = rg.y & CS_COUNT_MASK;
+                for (int k = 0; k < cnt; ++k) {
+                    const int e = __ldg(g.cs + rg.x + k);
+                    const int sid = cs_surface(e), side = cs_side(e);
+                    const bool on = (s.on_lev == l && s.on_surf == sid);
+                    const double t = surface_distance(g, sid, cs_type(e), side, on, x, y, z, s.d);
+                    const long long tk = okey(t);
+                    if (tk < hk) { hk = tk; h.d = t; h.level = l; h.surf = sid; h.side = side; h.dim = -1; h.dsign = 0; h.entry = rg.x + k; }
+                }
             }
         }
     }

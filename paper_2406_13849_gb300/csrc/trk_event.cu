@@ -3,17 +3,17 @@
 // Paper: Sec. 2.3 (event-based GPU transport: tracking operations run over a
 // vector of histories, one operation at a time) on top of Alg. 2-10.
 //
-// GB300 design.  Each CTA owns `slots` particle slots whose state lives in
-// the caller's work buffer (structure of arrays, L2-resident) and keeps four
-// queues of slot indices in shared memory: flight (distance_to_surface +
+// GB300 design.  Each warp owns `slots` particle slots whose state lives in
+// the caller's work buffer (structure of arrays, L2-resident) and keeps its
+// own queues of slot indices in shared memory: flight (distance_to_surface +
 // move_within_cell + tally), cross (cross_surface + find_cell below),
 // collide (change_direction), free.  A round runs refill, then flight over
-// the whole flight queue, then cross and collide over their queues, with
-// every thread of the CTA on one kind of operation, so warps stay converged
-// where the history kernel diverges.  Pushes are warp-aggregated (ballot +
-// one shared atomic per warp).  Empty slots take new particles from one
-// global counter.  No CTA ever waits for another: the only waits are
-// __syncthreads, and a round limit turns a runaway into TRK_E_TIMEOUT.
+// the whole flight queue, then cross and collide over theirs, all 32 lanes
+// on one kind of operation, so the warp stays converged where the history
+// kernel diverges.  Queue counts are warp-uniform registers advanced by
+// ballot/popc; empty slots take new particles from one global counter.  No
+// warp ever waits for another (only __syncwarp), and a round limit turns a
+// runaway into TRK_E_TIMEOUT.
 // Per-particle arithmetic is the history kernel's, so results are the same
 // bit for bit.
 #include <cstdint>
@@ -29,6 +29,18 @@ using namespace trk::dev;
 namespace {
 
 constexpr int EV_BLOCK = 256;
+
+// Minimum resident CTAs per SM the register allocation must allow (0: let
+// the compiler choose).  One CTA of 8 warps keeps the whole particle state in
+// registers; the compiler's own choice (two CTAs) spills it to local memory.
+#ifndef TRK_EV_MINB
+#define TRK_EV_MINB 1
+#endif
+#if TRK_EV_MINB > 0
+#define TRK_EV_BOUNDS __launch_bounds__(EV_BLOCK, TRK_EV_MINB)
+#else
+#define TRK_EV_BOUNDS __launch_bounds__(EV_BLOCK)
+#endif
 
 // slot state fields
 enum DField { D_X, D_Y, D_Z, D_U, D_V, D_W, D_IU, D_IV, D_IW, D_TAU, D_PATH, D_HD, D_T0, ND = D_T0 + 3 * MAXL };
@@ -114,16 +126,13 @@ __device__ __forceinline__ void store_ctx(const EvBuf& B, int s, const Ctx& c) {
     B.I(I_STATUS, s) = c.status;
 }
 
-// Warp-aggregated append of `v` to list/count when `flag` (all lanes call).
-__device__ __forceinline__ void push(bool flag, int v, int* list, int* count) {
+// Warp-level append of `v` to `list` when `flag` (all 32 lanes call);
+// `count` is warp-uniform and advanced in every lane.
+__device__ __forceinline__ void wpush(bool flag, int v, int* list, int& count) {
     const unsigned m = __ballot_sync(0xffffffffu, flag);
-    if (m == 0) return;
     const int lane = threadIdx.x & 31;
-    const int leader = __ffs(m) - 1;
-    int base = 0;
-    if (lane == leader) base = atomicAdd(count, __popc(m));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (flag) list[base + __popc(m & ((1u << lane) - 1u))] = v;
+    if (flag) list[count + __popc(m & ((1u << lane) - 1u))] = v;
+    count += __popc(m);
 }
 
 template <int FLAGS>
@@ -135,54 +144,50 @@ __device__ __forceinline__ void finish(const EvBuf& B, int s, const Ctx& c, unsi
     }
 }
 
+// Each warp owns `slots` particle slots and its own five queues in shared
+// memory; warps never synchronise with each other.
 template <bool CSG, int FLAGS>
-__global__ void __launch_bounds__(EV_BLOCK) k_event(const DevGeom g, const ParticlesView P, long long n, const RunP rp,
+__global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, long long n, const RunP rp,
                                                     const EvBuf B, int slots, unsigned long long max_rounds,
                                                     unsigned long long* __restrict__ tally,
                                                     unsigned long long* __restrict__ counters,
                                                     unsigned long long* __restrict__ rec) {
     extern __shared__ int smem[];
-    int* qa = smem;               // flight queue (this round)
-    int* qb = smem + slots;       // flight queue (next round)
-    int* qx = smem + 2 * slots;   // cross
-    int* qc = smem + 3 * slots;   // collide
-    int* qf = smem + 4 * slots;   // free
-    __shared__ int n_fly, n_next, n_cross, n_coll, n_free, exhausted, refill_got;
-    __shared__ unsigned long long refill_base;
-    const int tid = threadIdx.x;
-    const int slot0 = blockIdx.x * slots;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int* base_q = smem + warp * 5 * slots;
+    int* fly = base_q;
+    int* next = base_q + slots;
+    int* qx = base_q + 2 * slots;
+    int* qc = base_q + 3 * slots;
+    int* qf = base_q + 4 * slots;
+    const int slot0 = (blockIdx.x * (EV_BLOCK / 32) + warp) * slots;
     Counts cnt;
 #pragma unroll
     for (int k = 0; k < NCOUNT; ++k) cnt.k[k] = 0;
-    for (int k = tid; k < slots; k += EV_BLOCK) qf[k] = slot0 + k;
-    if (tid == 0) { n_fly = 0; n_next = 0; n_cross = 0; n_coll = 0; n_free = slots; exhausted = 0; }
-    __syncthreads();
-    int* fly = qa;
-    int* next = qb;
+    for (int k = lane; k < slots; k += 32) qf[k] = slot0 + k;
+    int n_fly = 0, n_free = slots;
+    bool exhausted = false;
+    __syncwarp();
     for (unsigned long long round = 0;; ++round) {
         // ---- refill free slots with new particles --------------------------
-        if (tid == 0) {
-            refill_got = 0;
-            if (!exhausted && n_free > 0) {
-                const unsigned long long b = atomicAdd(B.ctr, (unsigned long long)n_free);
-                refill_base = b;
-                long long got = (long long)n - (long long)b;
-                if (got <= 0) { got = 0; exhausted = 1; }
-                if (got >= n_free) got = n_free;
-                else exhausted = 1;
-                refill_got = int(got);
-            }
+        int got = 0;
+        unsigned long long first = 0;
+        if (!exhausted && n_free > 0) {
+            if (lane == 0) first = atomicAdd(B.ctr, (unsigned long long)n_free);
+            first = __shfl_sync(0xffffffffu, first, 0);
+            long long avail = (long long)n - (long long)first;
+            if (avail <= 0) { avail = 0; exhausted = true; }
+            if (avail >= n_free) got = n_free;
+            else { got = int(avail); exhausted = true; }
         }
-        __syncthreads();
-        const int got = refill_got;
-        const int free_before = n_free;
-        for (int base = 0; base < got; base += EV_BLOCK) {
-            const int k = base + tid;
+        int n_park = 0;
+        for (int b = 0; b < got; b += 32) {
+            const int k = b + lane;
             bool ok = false;
             int slot = 0;
             if (k < got) {
-                slot = qf[free_before - got + k];
-                const long long pidx = (long long)refill_base + k;
+                slot = qf[n_free - got + k];
+                const long long pidx = (long long)first + k;
                 Ctx c;
                 c.pid = uint32_t(rp.first_id + uint64_t(pidx));
                 c.event = 0; c.nseg = 0; c.path = 0.0; c.hash = FNV0; c.status = 0;
@@ -207,35 +212,27 @@ __global__ void __launch_bounds__(EV_BLOCK) k_event(const DevGeom g, const Parti
                 store_ctx(B, slot, c);
                 if (!ok) finish<FLAGS>(B, slot, c, rec);
             }
-            push(ok, slot, fly, &n_fly);
-            push(k < got && !ok, slot, next, &n_next);   // dead at birth: slot parked, freed below
+            wpush(ok, slot, fly, n_fly);
+            wpush(k < got && !ok, slot, next, n_park);
         }
-        __syncthreads();
-        if (tid == 0) n_free = free_before - got;
-        __syncthreads();
-        // parked dead-at-birth slots return to the free list
-        {
-            const int parked = n_next;
-            for (int base = 0; base < parked; base += EV_BLOCK) {
-                const int k = base + tid;
-                const bool f = k < parked;
-                push(f, f ? next[k] : 0, qf, &n_free);
-            }
-            __syncthreads();
-            if (tid == 0) n_next = 0;
+        __syncwarp();
+        n_free -= got;
+        for (int b = 0; b < n_park; b += 32) {
+            const int k = b + lane;
+            wpush(k < n_park, k < n_park ? next[k] : 0, qf, n_free);
         }
-        __syncthreads();
+        __syncwarp();
         if (n_fly == 0 && exhausted) break;
         if (round >= max_rounds) {
-            if (tid == 0) kernel_status(counters, TRK_E_TIMEOUT);
+            if (lane == 0) kernel_status(counters, TRK_E_TIMEOUT);
             break;
         }
         // ---- flight: distance_to_surface, tally, move ----------------------
-        const int nf = n_fly;
-        for (int base = 0; base < nf; base += EV_BLOCK) {
-            const int k = base + tid;
+        int n_cross = 0, n_coll = 0;
+        for (int b = 0; b < n_fly; b += 32) {
+            const int k = b + lane;
             int a = A_DONE, slot = 0;
-            if (k < nf) {
+            if (k < n_fly) {
                 slot = fly[k];
                 St s;
                 load_state(B, slot, s);
@@ -252,17 +249,18 @@ __global__ void __launch_bounds__(EV_BLOCK) k_event(const DevGeom g, const Parti
                 }
                 if (a == A_DONE) finish<FLAGS>(B, slot, c, rec);
             }
-            push(k < nf && a == A_CROSS, slot, qx, &n_cross);
-            push(k < nf && a == A_COLLIDE, slot, qc, &n_coll);
-            push(k < nf && a == A_DONE, slot, qf, &n_free);
+            const bool live = k < n_fly;
+            wpush(live && a == A_CROSS, slot, qx, n_cross);
+            wpush(live && a == A_COLLIDE, slot, qc, n_coll);
+            wpush(live && a == A_DONE, slot, qf, n_free);
         }
-        __syncthreads();
-        // ---- cross_surface and change_direction ------------------------------
-        const int ncr = n_cross, nco = n_coll;
-        for (int base = 0; base < ncr + nco; base += EV_BLOCK) {
-            const int k = base + tid;
+        __syncwarp();
+        // ---- cross_surface, then change_direction ---------------------------
+        int n_next = 0;
+        for (int b = 0; b < n_cross; b += 32) {
+            const int k = b + lane;
             int a = A_DONE, slot = 0;
-            if (k < ncr) {
+            if (k < n_cross) {
                 slot = qx[k];
                 St s;
                 load_state(B, slot, s);
@@ -277,8 +275,16 @@ __global__ void __launch_bounds__(EV_BLOCK) k_event(const DevGeom g, const Parti
                 store_dir(B, slot, s);
                 store_ctx(B, slot, c);
                 if (a == A_DONE) finish<FLAGS>(B, slot, c, rec);
-            } else if (k < ncr + nco) {
-                slot = qc[k - ncr];
+            }
+            const bool live = k < n_cross;
+            wpush(live && a == A_FLY, slot, next, n_next);
+            wpush(live && a == A_DONE, slot, qf, n_free);
+        }
+        for (int b = 0; b < n_coll; b += 32) {
+            const int k = b + lane;
+            int a = A_DONE, slot = 0;
+            if (k < n_coll) {
+                slot = qc[k];
                 St s;
                 s.d.u = B.D(D_U, slot); s.d.v = B.D(D_V, slot); s.d.w = B.D(D_W, slot);
                 s.tau = B.D(D_TAU, slot);
@@ -294,14 +300,13 @@ __global__ void __launch_bounds__(EV_BLOCK) k_event(const DevGeom g, const Parti
                 store_ctx(B, slot, c);
                 if (a == A_DONE) finish<FLAGS>(B, slot, c, rec);
             }
-            const bool live = k < ncr + nco;
-            push(live && a == A_FLY, slot, next, &n_next);
-            push(live && a == A_DONE, slot, qf, &n_free);
+            const bool live = k < n_coll;
+            wpush(live && a == A_FLY, slot, next, n_next);
+            wpush(live && a == A_DONE, slot, qf, n_free);
         }
-        __syncthreads();
+        __syncwarp();
         int* t = fly; fly = next; next = t;
-        if (tid == 0) { n_fly = n_next; n_next = 0; n_cross = 0; n_coll = 0; }
-        __syncthreads();
+        n_fly = n_next;
     }
     flush_counts(cnt, counters);
 }
@@ -310,33 +315,34 @@ __global__ void __launch_bounds__(EV_BLOCK) k_event(const DevGeom g, const Parti
 
 namespace trk {
 
+constexpr int EV_WARPS = EV_BLOCK / 32;
+
 int event_grid(int slots) {
-    (void)slots;
     int dev = 0, sms = 152;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int per_sm = 1;
-    const size_t smem = size_t(5) * slots * sizeof(int);
+    const size_t smem = size_t(5) * slots * EV_WARPS * sizeof(int);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_event<true, 0>, EV_BLOCK, smem) != cudaSuccess || per_sm < 1)
         per_sm = 1;
     return sms * per_sm;
 }
 
-size_t event_work_bytes(int slots, int grid) { return buf_bytes((long long)slots * grid); }
+size_t event_work_bytes(int slots, int grid) { return buf_bytes((long long)slots * EV_WARPS * grid); }
 
 trk_status launch_event(trk_geom_t g, const ParticlesView& P, long long n, const RunP& rp, bool csg, int flags,
                         unsigned long long* tally, unsigned long long* cnt, unsigned long long* rec, void* work,
                         size_t work_bytes, int slots, int grid, cudaStream_t s) {
-    const long long T = (long long)slots * grid;
+    const long long T = (long long)slots * EV_WARPS * grid;
     if (work_bytes < buf_bytes(T) || !work)
         return trk_status(set_error(TRK_E_NOMEM, "run_histories (event): work buffer needs %zu bytes", buf_bytes(T)));
     const EvBuf B = make_buf(work, T);
     cudaError_t e = cudaMemsetAsync(B.ctr, 0, 8, s);
     if (e != cudaSuccess) return trk_status(set_error(TRK_E_CUDA, "run_histories (event): %s", cudaGetErrorString(e)));
-    const size_t smem = size_t(5) * slots * sizeof(int);
-    // every particle needs at most max_segments + 1 flight rounds; a CTA
-    // sees at most its share plus a slot's worth of refills
-    const unsigned long long per_cta = (unsigned long long)(n / grid + slots + 1);
-    const unsigned long long max_rounds = (rp.max_segments + 2ULL) * (per_cta / slots + 2ULL) * 4ULL;
+    const size_t smem = size_t(5) * slots * EV_WARPS * sizeof(int);
+    // a particle needs at most max_segments + 1 flight rounds; a warp holds
+    // `slots` particles at a time and refills every round
+    const unsigned long long per_warp = (unsigned long long)(n / (T / slots) + slots + 1);
+    const unsigned long long max_rounds = (rp.max_segments + 2ULL) * (per_warp / slots + 2ULL) * 4ULL;
 #define TRK_EV(C, F)                                                                                         \
     do {                                                                                                     \
         auto k = k_event<C, F>;                                                                              \

@@ -44,6 +44,11 @@ struct alignas(16) SkipNode {
     int leaf;
 };
 
+// c_range count field: low bits count, CS_SLAB_FLAG marks a cell bounded
+// by axis planes only, at most one lower and one upper per dimension.
+constexpr int CS_SLAB_FLAG = 1 << 30;
+constexpr int CS_COUNT_MASK = CS_SLAB_FLAG - 1;
+
 // Packed cell-surface entry: (surface << 4) | (type << 1) | (sense > 0).
 TRK_HD_INLINE int cs_surface(int e) { return e >> 4; }
 TRK_HD_INLINE int cs_type(int e) { return (e >> 1) & 7; }
@@ -55,10 +60,13 @@ struct DevGeom {
     const double* s_coef;     // 4 per surface; px/py/pz: (g,0,0,0); p: (nx,ny,nz,d); cz: (x0,y0,r,r*r)
     const long long* s_key;   // order key of g for px/py/pz (sense tests as integer compares)
     // cells (CSG view)
-    const int2* c_range;      // (first, count) into cs
+    const int2* c_range;      // (first, count | CS_SLAB_FLAG) into cs
     const int* cs;            // packed cell-surface entries (see cs_surface / cs_type / cs_side)
     const int2* cs_adj;       // per entry: up to two cells on the far side of that face, -1 none,
                               // (-2,-2) too many (search the BVH directly)
+    const int4* c_slab0;      // slab view of cells bounded by axis planes only: entry index of
+                              // the lower / upper face on x, y (lo_x, hi_x, lo_y, hi_y), -1 absent
+    const int4* c_slab1;      // (lo_z, hi_z, -, -)
     const int* c_fill;        // >= 0 daughter universe; < 0 material ~fill
     const double* c_tr;       // translation into the daughter, 3 per cell
     const int* c_off;         // leaf-instance offset of the cell

@@ -28,6 +28,17 @@
 using namespace trk;
 using namespace trk::dev;
 
+// Minimum resident 128-thread CTAs per SM the history kernel's register
+// allocation must allow (0: let the compiler choose).
+#ifndef TRK_HIST_MINB
+#define TRK_HIST_MINB 0
+#endif
+#if TRK_HIST_MINB > 0
+#define TRK_HIST_BOUNDS __launch_bounds__(128, TRK_HIST_MINB)
+#else
+#define TRK_HIST_BOUNDS __launch_bounds__(128)
+#endif
+
 namespace {
 
 
@@ -70,7 +81,7 @@ __device__ __forceinline__ void history(const DevGeom& g, const ParticlesView& P
 }
 
 template <bool CSG, int FLAGS>
-__global__ void __launch_bounds__(128) k_history(const DevGeom g, const ParticlesView P, long long n, const RunP rp,
+__global__ void TRK_HIST_BOUNDS k_history(const DevGeom g, const ParticlesView P, long long n, const RunP rp,
                                                  unsigned long long* __restrict__ tally,
                                                  unsigned long long* __restrict__ counters,
                                                  unsigned long long* __restrict__ rec, int* __restrict__ tr_inst,
@@ -431,7 +442,7 @@ trk_status source_init(trk_geom_t g, int64_t n, uint64_t first_id, uint64_t seed
     return launch_error("source_init");
 }
 
-constexpr int DEFAULT_SLOTS = 512;
+constexpr int DEFAULT_SLOTS = 128;
 
 int event_slots(const trk_run_opts& o) { return o.queue_depth > 0 ? o.queue_depth : DEFAULT_SLOTS; }
 
@@ -443,7 +454,7 @@ trk_status run_histories_work_bytes(trk_geom_t g, int64_t n, const trk_run_opts*
     *bytes = 0;
     if (o.mode == TRK_MODE_EVENT) {
         const int slots = event_slots(o);
-        if (slots < 32 || slots > 4096) return trk_status(set_error(TRK_E_INVALID, "queue_depth must be in [32, 4096]"));
+        if (slots < 32 || slots > 1024) return trk_status(set_error(TRK_E_INVALID, "queue_depth must be in [32, 1024]"));
         const int grid = o.grid > 0 ? o.grid : event_grid(slots);
         *bytes = event_work_bytes(slots, grid);
     }
@@ -485,7 +496,7 @@ trk_status run_histories(trk_geom_t g, const void* dev_particles, int64_t n, uin
     const int flags = (dev_records ? F_REC : 0) | (cut ? F_CUT : 0);
     if (o.mode == TRK_MODE_EVENT) {
         const int slots = event_slots(o);
-        if (slots < 32 || slots > 4096) return trk_status(set_error(TRK_E_INVALID, "queue_depth must be in [32, 4096]"));
+        if (slots < 32 || slots > 1024) return trk_status(set_error(TRK_E_INVALID, "queue_depth must be in [32, 1024]"));
         const int grid = o.grid > 0 ? o.grid : event_grid(slots);
         return launch_event(g, P, n, rp, csg, flags, T, C, R, dev_work, work_bytes, slots, grid, s);
     }

@@ -346,7 +346,7 @@ def test_event_bit_exact_hex(name):
     assert np.array_equal(h, o["hash"]) and np.array_equal(_u64(tally), o["tally"])
 
 
-@pytest.mark.parametrize("depth,grid", [(32, 1), (64, 3), (1024, 0), (4096, 2)])
+@pytest.mark.parametrize("depth,grid", [(32, 1), (64, 3), (128, 0), (1024, 2)])
 def test_event_queue_shapes(depth, grid):
     desc, pa, n = CASES["small_core"]
     n = 2_999
