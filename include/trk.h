@@ -79,7 +79,7 @@ typedef struct {
     int precision;          /* TRK_FP64 or TRK_FP32_LOCAL */
     int block;              /* threads per block, 0 = default */
     int grid;               /* blocks, 0 = default (a multiple of the SM count) */
-    int queue_depth;        /* event mode: particle slots per warp (32..1024), 0 = default 128 */
+    int queue_depth;        /* event mode: particle slots per warp (32..512), 0 = default 128 */
     int sort_interval;      /* event mode: regroup queues by cell every k rounds, 0 = never */
     int reserved;
     uint64_t seed;          /* low 32 bits key the Philox stream with the geometry id */
@@ -179,7 +179,7 @@ trk_status tally_read(trk_geom_t g, const uint64_t* dev_tally, double* host_out,
 trk_status trk_find_cell(trk_geom_t g, int tracker, int64_t n, const double* dev_xyz,
                          int64_t* dev_inst, void* stream);
 
-/* trk_trace - run_histories (history mode, FP64) that also logs each
+/* trk_trace - run_histories (history mode, FP64 or FP32-local) that also logs each
  * particle's segments: for particle i and segment k < cap,
  * dev_inst[i*cap+k] (int32 leaf instance, -1 past the end) and
  * dev_len[i*cap+k] (segment length, cm).  Tallies and counters as in

@@ -863,6 +863,12 @@ int build_host(const char* json, size_t len, Built& B) {
     }
     std::vector<long long> s_key;
     for (auto& s : G.surf) s_key.push_back(s.type <= S_PZ ? okey(s.c[0]) : 0);
+    std::vector<float4> s_coeff;
+    for (auto& s : G.surf) {
+        if (s.type == S_CZ) s_coeff.push_back(make_float4(float(s.c[0]), float(s.c[1]), float(s.c[2] * s.c[2]), float(s.c[2])));
+        else s_coeff.push_back(make_float4(float(s.c[0]), float(s.c[1]), float(s.c[2]), float(s.c[3])));
+    }
+    std::vector<float> c_slabf;
     std::vector<int2> c_range, cs_adj;
     std::vector<int4> c_slab0, c_slab1;
     std::vector<int> cs, c_fill, c_off;
@@ -875,9 +881,16 @@ int build_host(const char* json, size_t len, Built& B) {
         for (int ci = 0; ci < int(U.cells.size()); ++ci)
             for (size_t k = 0; k < U.cells[size_t(ci)].surf.size(); ++k)
                 by_surf[U.cells[size_t(ci)].surf[k]].push_back({ci, U.cells[size_t(ci)].sense[k]});
-        auto overlap = [](const HCell& a, const HCell& b) {
-            for (int k = 0; k < 3; ++k)
-                if (a.box[k] > b.box[3 + k] || b.box[k] > a.box[3 + k]) return false;
+        // boxes overlap; across an axis plane the overlap must have positive
+        // area in the plane (cells that only share an edge are not neighbours)
+        auto overlap = [](const HCell& a, const HCell& b, int axis) {
+            for (int k = 0; k < 3; ++k) {
+                const double lo = std::max(a.box[k], b.box[k]), hi = std::min(a.box[3 + k], b.box[3 + k]);
+                if (lo > hi) return false;
+                if (k != axis && axis >= 0 && std::isfinite(lo) && std::isfinite(hi) &&
+                    hi - lo <= 1e-6 * std::max(1.0, std::max(std::fabs(lo), std::fabs(hi))))
+                    return false;
+            }
             return true;
         };
         for (int ci = 0; ci < int(U.cells.size()); ++ci) {
@@ -887,8 +900,9 @@ int build_host(const char* json, size_t len, Built& B) {
                 const int type = G.surf[size_t(c.surf[i])].type;
                 cs.push_back((c.surf[i] << 4) | (type << 1) | (c.sense[i] > 0 ? 1 : 0));
                 std::vector<int> cand;
+                const int axis = type <= S_PZ ? type : -1;
                 for (auto& pr : by_surf[c.surf[i]])
-                    if (pr.first != ci && pr.second == -c.sense[i] && overlap(c, U.cells[size_t(pr.first)]))
+                    if (pr.first != ci && pr.second == -c.sense[i] && overlap(c, U.cells[size_t(pr.first)], axis))
                         cand.push_back(U.first_cell + pr.first);
                 if (cand.size() > 2) cs_adj.push_back(make_int2(-2, -2));
                 else cs_adj.push_back(make_int2(cand.size() > 0 ? cand[0] : -1, cand.size() > 1 ? cand[1] : -1));
@@ -906,6 +920,10 @@ int build_host(const char* json, size_t len, Built& B) {
             }
             if (!pure) for (int k = 0; k < 6; ++k) slab[k] = -1;
             else c_range.back().y |= CS_SLAB_FLAG;
+            for (int k = 0; k < 6; ++k) {
+                const int e = slab[k];
+                c_slabf.push_back(e >= 0 ? float(G.surf[size_t(c.surf[size_t(e - first_entry)])].c[0] - c.tr[k / 2]) : 0.f);
+            }
             c_slab0.push_back(make_int4(slab[0], slab[1], slab[2], slab[3]));
             c_slab1.push_back(make_int4(slab[4], slab[5], 0, 0));
             c_fill.push_back(c.fill);
@@ -917,6 +935,7 @@ int build_host(const char* json, size_t len, Built& B) {
     std::vector<int4> l_dim, l_off;
     std::vector<double> l_grid, l_ctr;
     std::vector<long long> l_gkey;
+    std::vector<float> l_lof, l_hif;
     std::vector<int> l_fill, l_eoff, l_pscale;
     for (auto& U : G.univ) {
         if (U.type != UT_RECT) continue;
@@ -927,8 +946,15 @@ int build_host(const char* json, size_t len, Built& B) {
             n[d] = int(U.grid[d].size()) - 1;
             go[d] = int(l_grid.size());
             for (double g : U.grid[d]) { l_grid.push_back(g); l_gkey.push_back(okey(g)); }
-            for (int i = 0; i < n[d]; ++i) l_ctr.push_back((U.grid[d][size_t(i)] + U.grid[d][size_t(i) + 1]) * 0.5);
+            for (int i = 0; i < n[d]; ++i) {
+                const double c = (U.grid[d][size_t(i)] + U.grid[d][size_t(i) + 1]) * 0.5;
+                l_ctr.push_back(c);
+                l_lof.push_back(float(U.grid[d][size_t(i)] - c));
+                l_hif.push_back(float(U.grid[d][size_t(i) + 1] - c));
+            }
             l_ctr.push_back(0.0);   // keep l_ctr aligned with l_grid offsets
+            l_lof.push_back(0.f);
+            l_hif.push_back(0.f);
         }
         int bcp = 0;
         for (int k = 0; k < 6; ++k) bcp |= (U.bc[k] & 3) << (2 * k);
@@ -940,7 +966,8 @@ int build_host(const char* json, size_t len, Built& B) {
         l_pscale.push_back(U.pscale);
     }
     if (l_dim.empty()) { l_dim.push_back(make_int4(0, 0, 0, 0)); l_off.push_back(make_int4(0, 0, 0, 0)); l_pscale.push_back(0); }
-    if (l_grid.empty()) { l_grid.push_back(0); l_ctr.push_back(0); l_gkey.push_back(0); }
+    if (l_grid.empty()) { l_grid.push_back(0); l_ctr.push_back(0); l_gkey.push_back(0); l_lof.push_back(0); l_hif.push_back(0); }
+    if (c_slabf.empty()) c_slabf.push_back(0);
     if (l_fill.empty()) { l_fill.push_back(0); l_eoff.push_back(0); }
     std::vector<SkipNode> nodes = bvh.nodes;
     std::vector<int> leaf = bvh.leaf_cells;
@@ -973,6 +1000,10 @@ int build_host(const char* json, size_t len, Built& B) {
     o[20] = L.put(l_gkey.size() * 8);
     o[21] = L.put(c_slab0.size() * sizeof(int4));
     o[22] = L.put(c_slab1.size() * sizeof(int4));
+    o[23] = L.put(s_coeff.size() * sizeof(float4));
+    o[24] = L.put(l_lof.size() * 4);
+    o[25] = L.put(l_hif.size() * 4);
+    o[26] = L.put(c_slabf.size() * 4);
     B.image.assign(L.total, 0);
     copy_into(B.image, o[0], s_info);
     copy_into(B.image, o[1], s_coef);
@@ -997,6 +1028,10 @@ int build_host(const char* json, size_t len, Built& B) {
     copy_into(B.image, o[20], l_gkey);
     copy_into(B.image, o[21], c_slab0);
     copy_into(B.image, o[22], c_slab1);
+    copy_into(B.image, o[23], s_coeff);
+    copy_into(B.image, o[24], l_lof);
+    copy_into(B.image, o[25], l_hif);
+    copy_into(B.image, o[26], c_slabf);
     return TRK_OK;
 }
 
@@ -1072,6 +1107,10 @@ trk_status geometry_build(const char* json, size_t len, void* dev_buf, size_t* d
     d.l_gkey = reinterpret_cast<const long long*>(base + o[20]);
     d.c_slab0 = reinterpret_cast<const int4*>(base + o[21]);
     d.c_slab1 = reinterpret_cast<const int4*>(base + o[22]);
+    d.s_coeff = reinterpret_cast<const float4*>(base + o[23]);
+    d.l_lof = reinterpret_cast<const float*>(base + o[24]);
+    d.l_hif = reinterpret_cast<const float*>(base + o[25]);
+    d.c_slabf = reinterpret_cast<const float*>(base + o[26]);
     const HGeom& G = B.G;
     for (int k = 0; k < 3; ++k) { d.src_lo[k] = G.src[k]; d.src_hi[k] = G.src[3 + k]; }
     d.root = G.root;

@@ -515,6 +515,168 @@ __device__ __forceinline__ Hit distance_to_boundary(const DevGeom& g, const St& 
     return h;
 }
 
+// ---------------------------------------------------------------------------
+// FP32-local distances.  Every level's coordinates come from the FP64 chain
+// (global position minus the FP64 translations), rounded once to FP32 in the
+// frame where they are small: array and slab faces are measured in the
+// element's own frame (|coordinates| < half a pitch), other CSG surfaces in
+// their universe's frame.  All distance formulas then run in FP32.  The two
+// smallest candidates are kept; when they are within CLOSE_REL of each other
+// (or of the collision distance) the step is redone exactly in FP64.
+// ---------------------------------------------------------------------------
+constexpr float CLOSE_REL = 2e-5f;
+constexpr float FINF = __builtin_huge_valf();
+
+struct DirF {
+    float u, v, w, iu, iv, iw;
+};
+
+__device__ __forceinline__ DirF dir_f32(const Dir& d) {
+    DirF f;
+    f.u = float(d.u); f.v = float(d.v); f.w = float(d.w);
+    f.iu = 1.0f / f.u; f.iv = 1.0f / f.v; f.iw = 1.0f / f.w;
+    return f;
+}
+
+// `ill` is set when the FP32 result cannot be trusted to the close-call
+// margin: a cylinder hit or miss whose discriminant is small against the
+// terms it cancels (near-tangent rays amplify FP32 rounding by 1/sqrt(disc)).
+constexpr float ILL_DISC = 1e-3f;
+
+__device__ __forceinline__ float surface_distance_f(const DevGeom& g, int s, int type, int side, bool on, float x,
+                                                    float y, float z, const DirF& d, bool& ill) {
+    const float4 c = __ldg(g.s_coeff + s);
+    float t;
+    if (type <= S_PZ) {
+        if (on) return FINF;
+        const float dd = type == S_PX ? d.u : (type == S_PY ? d.v : d.w);
+        if (!(side > 0 ? dd < 0.f : dd > 0.f)) return FINF;
+        const float xx = type == S_PX ? x : (type == S_PY ? y : z);
+        const float ii = type == S_PX ? d.iu : (type == S_PY ? d.iv : d.iw);
+        t = (c.x - xx) * ii;
+    } else if (type == S_P) {
+        if (on) return FINF;
+        const float den = (c.x * d.u + c.y * d.v) + c.z * d.w;
+        if (!(side > 0 ? den < 0.f : den > 0.f)) return FINF;
+        t = (c.w - ((c.x * x + c.y * y) + c.z * z)) / den;
+    } else {
+        const float qx = x - c.x, qy = y - c.y;
+        const float a = d.u * d.u + d.v * d.v;
+        const float b = qx * d.u + qy * d.v;
+        if (on) {
+            if (side < 0 && b < 0.f) t = (-2.0f * b) / a;
+            else return FINF;
+        } else {
+            const float cc = (qx * qx + qy * qy) - c.z;
+            if (a == 0.f) return FINF;
+            const float bb = b * b, ac = a * cc;
+            const float disc = bb - ac;
+            if (fabsf(disc) <= ILL_DISC * (bb + fabsf(ac)) && (side < 0 || b < 0.f)) ill = true;
+            if (disc <= 0.f) return FINF;
+            const float sq = sqrtf(disc);
+            if (side < 0) t = (b <= 0.f) ? (-b + sq) / a : -cc / (b + sq);
+            else {
+                if (!(b < 0.f)) return FINF;
+                t = cc / (-b + sq);
+            }
+        }
+    }
+    return t < 0.f ? 0.f : t;
+}
+
+struct Best2 {
+    float d1, d2;
+    bool ill;
+    Hit h;
+    double wx, wy, wz;   // FP64 coordinates of the winner's level frame
+    __device__ __forceinline__ void offer(float t, int level, int surf, int side, int dim, int dsign, int entry,
+                                          double x, double y, double z) {
+        if (t < d1) {
+            d2 = d1; d1 = t;
+            h.level = level; h.surf = surf; h.side = side; h.dim = dim; h.dsign = dsign; h.entry = entry;
+            wx = x; wy = y; wz = z;
+        } else if (t < d2) {
+            d2 = t;
+        }
+    }
+};
+
+template <bool CSG>
+__device__ __forceinline__ Best2 distance_f32(const DevGeom& g, const St& s, const DirF& df) {
+    Best2 b;
+    b.d1 = FINF; b.d2 = FINF; b.ill = false; b.wx = b.wy = b.wz = 0.0;
+    b.h.d = DINF; b.h.level = -1; b.h.surf = -1; b.h.side = 0; b.h.dim = -1; b.h.dsign = 0; b.h.entry = -1;
+    double x = s.x, y = s.y, z = s.z;
+    const float d3[3] = {df.u, df.v, df.w};
+    const float v3[3] = {df.iu, df.iv, df.iw};
+#pragma unroll
+    for (int l = 0; l < MAXL; ++l) {
+        if (l >= s.nlev) break;
+        const Lv& L = s.lv[l];
+        // the next level's frame is this level's element frame: one FP64
+        // subtraction chain serves both
+        const double xn = x - L.tx, yn = y - L.ty, zn = z - L.tz;
+        const int4 ui = __ldg(g.u_info + L.u);
+        if (!CSG && ui.w >= 0) {
+            const int4 dm = __ldg(g.l_dim + ui.w), of = __ldg(g.l_off + ui.w);
+            const int n3[3] = {dm.x, dm.y, dm.z};
+            const int o3[3] = {of.x, of.y, of.z};
+            const int i3[3] = {L.i, L.j, L.k};
+            const float e3[3] = {float(xn), float(yn), float(zn)};
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                if (d3[d] > 0.f) {
+                    if (i3[d] < n3[d] - 1 || l == 0) {
+                        float t = (__ldg(g.l_hif + o3[d] + i3[d]) - e3[d]) * v3[d];
+                        b.offer(t < 0.f ? 0.f : t, l, -1 - (2 * d + 1), 0, d, 1, -1, x, y, z);
+                    }
+                } else if (d3[d] < 0.f) {
+                    if (i3[d] > 0 || l == 0) {
+                        float t = (__ldg(g.l_lof + o3[d] + i3[d]) - e3[d]) * v3[d];
+                        b.offer(t < 0.f ? 0.f : t, l, -1 - (2 * d), 0, d, -1, -1, x, y, z);
+                    }
+                }
+            }
+        } else {
+            const int2 rg = __ldg(g.c_range + L.cell);
+            if (rg.y & CS_SLAB_FLAG) {
+                const int4 s0 = __ldg(g.c_slab0 + L.cell), s1 = __ldg(g.c_slab1 + L.cell);
+                const int lo3[3] = {s0.x, s0.z, s1.x};
+                const int hi3[3] = {s0.y, s0.w, s1.y};
+                const float e3[3] = {float(xn), float(yn), float(zn)};
+                const float* fs = g.c_slabf + 6 * L.cell;
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    const bool up = d3[d] > 0.f;
+                    const int e = up ? hi3[d] : (d3[d] < 0.f ? lo3[d] : -1);
+                    if (e < 0) continue;
+                    const int sid = cs_surface(__ldg(g.cs + e));
+                    if (s.on_lev == l && s.on_surf == sid) continue;
+                    const float t = (__ldg(fs + 2 * d + (up ? 1 : 0)) - e3[d]) * v3[d];
+                    b.offer(t < 0.f ? 0.f : t, l, sid, up ? -1 : 1, -1, 0, e, x, y, z);
+                }
+            } else {
+                const float xf = float(x), yf = float(y), zf = float(z);
+                const int cnt = rg.y & CS_COUNT_MASK;
+                for (int k = 0; k < cnt; ++k) {
+                    const int e = __ldg(g.cs + rg.x + k);
+                    const int sid = cs_surface(e), side = cs_side(e);
+                    const bool on = (s.on_lev == l && s.on_surf == sid);
+                    const float t = surface_distance_f(g, sid, cs_type(e), side, on, xf, yf, zf, df, b.ill);
+                    b.offer(t, l, sid, side, -1, 0, rg.x + k, x, y, z);
+                }
+            }
+        }
+        x = xn; y = yn; z = zn;
+    }
+    b.h.d = double(b.d1);
+    return b;
+}
+
+__device__ __forceinline__ bool close_call(float a, float b) {
+    return fabsf(a - b) <= CLOSE_REL * fmaxf(fmaxf(a, b) < FINF ? fmaxf(a, b) : 1.0f, 1.0f);
+}
+
 enum { CR_OK = 0, CR_REFLECT = 1, CR_ESCAPE = 2, CR_LOST = 3, CR_FIND = 4 };
 
 __device__ __forceinline__ void reflect_plane(const DevGeom& g, St& s, int sid, int dim) {
@@ -699,6 +861,106 @@ __device__ __forceinline__ int step_flight(const DevGeom& g, St& s, Hit& h, Ctx&
         return A_CROSS;
     }
     return A_COLLIDE;
+}
+
+// FP32-local flight: distances and the flight decision in FP32, position
+// and tau in FP64; close calls are redone by the FP64 step.
+template <bool CSG, int FLAGS>
+__device__ __forceinline__ int step_flight_f32(const DevGeom& g, St& s, Hit& h, Ctx& c, const RunP& rp,
+                                               unsigned long long* __restrict__ tally, Counts& cnt,
+                                               int* __restrict__ tr_inst, double* __restrict__ tr_len, long long i) {
+    const DirF df = dir_f32(s.d);
+    const Best2 b = distance_f32<CSG>(g, s, df);
+    const double sig = __ldg(g.sigma + s.mat);
+    const float sigf = float(sig);
+    const float dcf = sigf > 0.f ? float(s.tau) / sigf : FINF;
+    if (b.ill || close_call(b.d1, b.d2) || close_call(b.d1, dcf) || !(fminf(b.d1, dcf) < FINF)) {
+        cnt.k[TRK_K_CLOSE_CALLS]++;
+        return step_flight<CSG, FLAGS>(g, s, h, c, rp, tally, cnt, tr_inst, tr_len, i);
+    }
+    h = b.h;
+    const bool crossing = b.d1 < dcf;
+    const float lenf = crossing ? b.d1 : dcf;
+    double len = double(lenf);
+    bool exact_len = false;
+    if (crossing) {
+        // A plane crossing is re-evaluated in FP64 from the FP64 frame
+        // coordinates (the same arithmetic as the FP64 path), so the particle
+        // lands on the plane and the array and universe searches that follow
+        // see what they would in FP64.  Cylinder crossings keep the FP32
+        // length: only small linear cell scans follow them.
+        double t = 0.0;
+        bool plane = false;
+        if (h.surf < 0) {
+            int lat = 0, idx = 0;
+#pragma unroll
+            for (int l = 0; l < MAXL; ++l)
+                if (l == h.level) {
+                    lat = __ldg(g.u_info + s.lv[l].u).w;
+                    idx = h.dim == 0 ? s.lv[l].i : (h.dim == 1 ? s.lv[l].j : s.lv[l].k);
+                }
+            const int4 of = __ldg(g.l_off + lat);
+            const int go = h.dim == 0 ? of.x : (h.dim == 1 ? of.y : of.z);
+            const double gv = __ldg(g.l_grid + go + idx + (h.dsign > 0 ? 1 : 0));
+            const double pv = h.dim == 0 ? b.wx : (h.dim == 1 ? b.wy : b.wz);
+            const double iv = h.dim == 0 ? s.d.iu : (h.dim == 1 ? s.d.iv : s.d.iw);
+            t = (gv - pv) * iv;
+            plane = true;
+        } else {
+            const int type = __ldg(g.s_info + h.surf) & 15;
+            if (type <= S_PZ) {
+                const double gv = __ldg(g.s_coef + 4 * h.surf);
+                const double pv = type == S_PX ? b.wx : (type == S_PY ? b.wy : b.wz);
+                const double iv = type == S_PX ? s.d.iu : (type == S_PY ? s.d.iv : s.d.iw);
+                t = (gv - pv) * iv;
+                plane = true;
+            } else if (type == S_P) {
+                t = surface_distance(g, h.surf, type, h.side, false, b.wx, b.wy, b.wz, s.d);
+                plane = true;
+            }
+        }
+        if (plane) {
+            if (d_lt0(t)) t = 0.0;
+            len = t;
+            exact_len = true;
+        }
+    }
+    const int inst = instance(s);
+    bool stop_cut = false;
+    if (FLAGS & F_CUT) {
+        if (!d_lt(c.path + len, rp.max_path)) { len = rp.max_path - c.path; stop_cut = true; }
+        else c.path = c.path + len;
+    }
+    const unsigned long long q = (stop_cut || exact_len) ? (unsigned long long)__double2ll_rn(len * 4294967296.0)
+                                                        : __float2ull_rn(lenf * 4294967296.0f);
+    atomicAdd(tally + inst, q);
+    if (FLAGS & F_REC) c.hash = fnv(fnv(c.hash, uint64_t(int64_t(inst))), uint64_t(dbits(len)));
+    if (FLAGS & F_TRACE) {
+        if (c.nseg < rp.trace_cap) {
+            tr_inst[i * rp.trace_cap + c.nseg] = inst;
+            tr_len[i * rp.trace_cap + c.nseg] = len;
+        }
+    }
+    s.x = s.x + len * s.d.u;
+    s.y = s.y + len * s.d.v;
+    s.z = s.z + len * s.d.w;
+    c.nseg++;
+    cnt.k[TRK_K_SEGMENTS]++;
+    if (stop_cut) { c.status = TRK_P_CUTOFF; cnt.k[TRK_K_CUTOFF]++; return A_DONE; }
+    if (crossing) {
+        s.tau = s.tau - sig * len;
+        cnt.k[TRK_K_CROSSINGS]++;
+        return A_CROSS;
+    }
+    return A_COLLIDE;
+}
+
+template <bool CSG, bool F32, int FLAGS>
+__device__ __forceinline__ int step_fly(const DevGeom& g, St& s, Hit& h, Ctx& c, const RunP& rp,
+                                        unsigned long long* __restrict__ tally, Counts& cnt,
+                                        int* __restrict__ tr_inst, double* __restrict__ tr_len, long long i) {
+    if (F32) return step_flight_f32<CSG, FLAGS>(g, s, h, c, rp, tally, cnt, tr_inst, tr_len, i);
+    return step_flight<CSG, FLAGS>(g, s, h, c, rp, tally, cnt, tr_inst, tr_len, i);
 }
 
 __device__ __forceinline__ int after_step(Ctx& c, const RunP& rp, Counts& cnt) {

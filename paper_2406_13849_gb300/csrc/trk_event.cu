@@ -29,6 +29,7 @@ using namespace trk::dev;
 namespace {
 
 constexpr int EV_BLOCK = 256;
+constexpr int EV_QUEUES = 4 + MAXL;   // flight, next flight, collide, free, cross per level
 
 // Minimum resident CTAs per SM the register allocation must allow (0: let
 // the compiler choose).  One CTA of 8 warps keeps the whole particle state in
@@ -146,7 +147,7 @@ __device__ __forceinline__ void finish(const EvBuf& B, int s, const Ctx& c, unsi
 
 // Each warp owns `slots` particle slots and its own five queues in shared
 // memory; warps never synchronise with each other.
-template <bool CSG, int FLAGS>
+template <bool CSG, bool F32, int FLAGS>
 __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, long long n, const RunP rp,
                                                     const EvBuf B, int slots, unsigned long long max_rounds,
                                                     unsigned long long* __restrict__ tally,
@@ -154,12 +155,12 @@ __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, lo
                                                     unsigned long long* __restrict__ rec) {
     extern __shared__ int smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int* base_q = smem + warp * 5 * slots;
+    int* base_q = smem + warp * EV_QUEUES * slots;
     int* fly = base_q;
     int* next = base_q + slots;
-    int* qx = base_q + 2 * slots;
-    int* qc = base_q + 3 * slots;
-    int* qf = base_q + 4 * slots;
+    int* qc = base_q + 2 * slots;
+    int* qf = base_q + 3 * slots;
+    int* qx = base_q + 4 * slots;      // MAXL cross queues, one per crossing level
     const int slot0 = (blockIdx.x * (EV_BLOCK / 32) + warp) * slots;
     Counts cnt;
 #pragma unroll
@@ -228,7 +229,9 @@ __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, lo
             break;
         }
         // ---- flight: distance_to_surface, tally, move ----------------------
-        int n_cross = 0, n_coll = 0;
+        int n_cross[MAXL], n_coll = 0;
+#pragma unroll
+        for (int l = 0; l < MAXL; ++l) n_cross[l] = 0;
         for (int b = 0; b < n_fly; b += 32) {
             const int k = b + lane;
             int a = A_DONE, slot = 0;
@@ -239,7 +242,7 @@ __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, lo
                 Ctx c;
                 load_ctx(B, slot, c, rp);
                 Hit h;
-                a = step_flight<CSG, FLAGS>(g, s, h, c, rp, tally, cnt, nullptr, nullptr, 0);
+                a = step_fly<CSG, F32, FLAGS>(g, s, h, c, rp, tally, cnt, nullptr, nullptr, 0);
                 B.D(D_X, slot) = s.x; B.D(D_Y, slot) = s.y; B.D(D_Z, slot) = s.z; B.D(D_TAU, slot) = s.tau;
                 store_ctx(B, slot, c);
                 if (a == A_CROSS) {
@@ -250,18 +253,24 @@ __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, lo
                 if (a == A_DONE) finish<FLAGS>(B, slot, c, rec);
             }
             const bool live = k < n_fly;
-            wpush(live && a == A_CROSS, slot, qx, n_cross);
+            // crossings are queued by level, so each pass runs one code path
+            // (array index step, universe search, pin cell test)
+            const int hl = (a == A_CROSS) ? B.I(I_HLEV, slot) : -1;
+#pragma unroll
+            for (int l = 0; l < MAXL; ++l) wpush(live && hl == l, slot, qx + l * slots, n_cross[l]);
             wpush(live && a == A_COLLIDE, slot, qc, n_coll);
             wpush(live && a == A_DONE, slot, qf, n_free);
         }
         __syncwarp();
         // ---- cross_surface, then change_direction ---------------------------
         int n_next = 0;
-        for (int b = 0; b < n_cross; b += 32) {
+#pragma unroll 1
+        for (int lq = 0; lq < MAXL; ++lq)
+        for (int b = 0; b < n_cross[lq]; b += 32) {
             const int k = b + lane;
             int a = A_DONE, slot = 0;
-            if (k < n_cross) {
-                slot = qx[k];
+            if (k < n_cross[lq]) {
+                slot = qx[lq * slots + k];
                 St s;
                 load_state(B, slot, s);
                 Ctx c;
@@ -276,7 +285,7 @@ __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, lo
                 store_ctx(B, slot, c);
                 if (a == A_DONE) finish<FLAGS>(B, slot, c, rec);
             }
-            const bool live = k < n_cross;
+            const bool live = k < n_cross[lq];
             wpush(live && a == A_FLY, slot, next, n_next);
             wpush(live && a == A_DONE, slot, qf, n_free);
         }
@@ -321,47 +330,57 @@ int event_grid(int slots) {
     int dev = 0, sms = 152;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int per_sm = 1;
-    const size_t smem = size_t(5) * slots * EV_WARPS * sizeof(int);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_event<true, 0>, EV_BLOCK, smem) != cudaSuccess || per_sm < 1)
+    const size_t smem = size_t(EV_QUEUES) * slots * EV_WARPS * sizeof(int);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_event<true, false, 0>, EV_BLOCK, smem) != cudaSuccess || per_sm < 1)
         per_sm = 1;
     return sms * per_sm;
 }
 
 size_t event_work_bytes(int slots, int grid) { return buf_bytes((long long)slots * EV_WARPS * grid); }
 
-trk_status launch_event(trk_geom_t g, const ParticlesView& P, long long n, const RunP& rp, bool csg, int flags,
-                        unsigned long long* tally, unsigned long long* cnt, unsigned long long* rec, void* work,
-                        size_t work_bytes, int slots, int grid, cudaStream_t s) {
+trk_status launch_event(trk_geom_t g, const ParticlesView& P, long long n, const RunP& rp, bool csg, bool f32,
+                        int flags, unsigned long long* tally, unsigned long long* cnt, unsigned long long* rec,
+                        void* work, size_t work_bytes, int slots, int grid, cudaStream_t s) {
     const long long T = (long long)slots * EV_WARPS * grid;
     if (work_bytes < buf_bytes(T) || !work)
         return trk_status(set_error(TRK_E_NOMEM, "run_histories (event): work buffer needs %zu bytes", buf_bytes(T)));
     const EvBuf B = make_buf(work, T);
     cudaError_t e = cudaMemsetAsync(B.ctr, 0, 8, s);
     if (e != cudaSuccess) return trk_status(set_error(TRK_E_CUDA, "run_histories (event): %s", cudaGetErrorString(e)));
-    const size_t smem = size_t(5) * slots * EV_WARPS * sizeof(int);
+    const size_t smem = size_t(EV_QUEUES) * slots * EV_WARPS * sizeof(int);
     // a particle needs at most max_segments + 1 flight rounds; a warp holds
     // `slots` particles at a time and refills every round
     const unsigned long long per_warp = (unsigned long long)(n / (T / slots) + slots + 1);
     const unsigned long long max_rounds = (rp.max_segments + 2ULL) * (per_warp / slots + 2ULL) * 4ULL;
-#define TRK_EV(C, F)                                                                                         \
+#define TRK_EV(C, F32V, F)                                                                                   \
     do {                                                                                                     \
-        auto k = k_event<C, F>;                                                                              \
+        auto k = k_event<C, F32V, F>;                                                                        \
         if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)); \
         k<<<grid, EV_BLOCK, smem, s>>>(g->dg, P, n, rp, B, slots, max_rounds, tally, cnt, rec);             \
     } while (0)
-    if (csg) {
+    if (f32) {
+#ifndef TRK_EXACT
+        if (csg) {
+            if (flags & F_REC) TRK_EV(true, true, F_REC);
+            else TRK_EV(true, true, 0);
+        } else {
+            if (flags & F_REC) TRK_EV(false, true, F_REC);
+            else TRK_EV(false, true, 0);
+        }
+#endif
+    } else if (csg) {
         switch (flags) {
-            case 0: TRK_EV(true, 0); break;
-            case F_REC: TRK_EV(true, F_REC); break;
-            case F_CUT: TRK_EV(true, F_CUT); break;
-            default: TRK_EV(true, F_REC | F_CUT); break;
+            case 0: TRK_EV(true, false, 0); break;
+            case F_REC: TRK_EV(true, false, F_REC); break;
+            case F_CUT: TRK_EV(true, false, F_CUT); break;
+            default: TRK_EV(true, false, F_REC | F_CUT); break;
         }
     } else {
         switch (flags) {
-            case 0: TRK_EV(false, 0); break;
-            case F_REC: TRK_EV(false, F_REC); break;
-            case F_CUT: TRK_EV(false, F_CUT); break;
-            default: TRK_EV(false, F_REC | F_CUT); break;
+            case 0: TRK_EV(false, false, 0); break;
+            case F_REC: TRK_EV(false, false, F_REC); break;
+            case F_CUT: TRK_EV(false, false, F_CUT); break;
+            default: TRK_EV(false, false, F_REC | F_CUT); break;
         }
     }
 #undef TRK_EV

@@ -81,6 +81,12 @@ struct DevGeom {
     const int* l_fill;        // element universe, at l_fill[l_off[k].w + e]
     const int* l_eoff;        // element instance offset, same indexing
     const int* l_pscale;      // grid planes scale with the pitch (gradient)
+    // FP32 copies for the FP32-local precision mode
+    const float4* s_coeff;    // px/py/pz: (g,0,0,0); p: (nx,ny,nz,d); cz: (x0,y0,r*r,r)
+    const float* l_lof;       // face below element i relative to its centre: g_i - c_i, l_grid offsets
+    const float* l_hif;       // face above: g_{i+1} - c_i
+    const float* c_slabf;     // 6 per cell: slab faces (lo_x, hi_x, lo_y, hi_y, lo_z, hi_z)
+                              // relative to the cell's translation
     // BVH (skip-list preorder per universe)
     const SkipNode* nodes;
     const int* leaf_cells;

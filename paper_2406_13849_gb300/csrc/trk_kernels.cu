@@ -43,7 +43,7 @@ namespace {
 
 
 // One history (Alg. 2): flight, then cross or collide, until it ends.
-template <bool CSG, int FLAGS>
+template <bool CSG, bool F32, int FLAGS>
 __device__ __forceinline__ void history(const DevGeom& g, const ParticlesView& P, long long i, const RunP& rp,
                                         unsigned long long* __restrict__ tally, Counts& cnt,
                                         unsigned long long* __restrict__ rec, int* __restrict__ tr_inst,
@@ -64,7 +64,7 @@ __device__ __forceinline__ void history(const DevGeom& g, const ParticlesView& P
         } else {
             for (;;) {
                 Hit h;
-                int a = step_flight<CSG, FLAGS>(g, s, h, c, rp, tally, cnt, tr_inst, tr_len, i);
+                int a = step_fly<CSG, F32, FLAGS>(g, s, h, c, rp, tally, cnt, tr_inst, tr_len, i);
                 if (a == A_DONE) break;
                 a = (a == A_CROSS) ? step_cross<CSG>(g, s, h, c, rp, cnt) : step_collide(g, s, c, rp, cnt);
                 if (a == A_DONE) break;
@@ -80,7 +80,7 @@ __device__ __forceinline__ void history(const DevGeom& g, const ParticlesView& P
     }
 }
 
-template <bool CSG, int FLAGS>
+template <bool CSG, bool F32, int FLAGS>
 __global__ void TRK_HIST_BOUNDS k_history(const DevGeom g, const ParticlesView P, long long n, const RunP rp,
                                                  unsigned long long* __restrict__ tally,
                                                  unsigned long long* __restrict__ counters,
@@ -91,7 +91,7 @@ __global__ void TRK_HIST_BOUNDS k_history(const DevGeom g, const ParticlesView P
     for (int k = 0; k < NCOUNT; ++k) c.k[k] = 0;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-        history<CSG, FLAGS>(g, P, i, rp, tally, c, rec, tr_inst, tr_len);
+        history<CSG, F32, FLAGS>(g, P, i, rp, tally, c, rec, tr_inst, tr_len);
     flush_counts(c, counters);
 }
 
@@ -400,15 +400,23 @@ int resolve_tracker(trk_geom_t g, int tracker, trk_status* st) {
     return tracker;
 }
 
-template <bool CSG, int FLAGS>
+template <bool CSG, bool F32, int FLAGS>
 trk_status launch_history(trk_geom_t g, const ParticlesView& P, long long n, const RunP& rp,
                           unsigned long long* tally, unsigned long long* cnt, unsigned long long* rec, int* ti,
                           double* tl, int block, int grid, cudaStream_t s) {
-    auto k = k_history<CSG, FLAGS>;
+    auto k = k_history<CSG, F32, FLAGS>;
     const int gr = persistent_grid(k, block, n, grid);
     k<<<gr, block, 0, s>>>(g->dg, P, n, rp, tally, cnt, rec, ti, tl);
     return launch_error("run_histories");
 }
+
+// The FP32-local kernels exist in the fast build only (the exact build is
+// the bit-exact FP64 reference path).
+#ifdef TRK_EXACT
+constexpr bool HAVE_F32 = false;
+#else
+constexpr bool HAVE_F32 = true;
+#endif
 
 }  // namespace
 
@@ -454,7 +462,7 @@ trk_status run_histories_work_bytes(trk_geom_t g, int64_t n, const trk_run_opts*
     *bytes = 0;
     if (o.mode == TRK_MODE_EVENT) {
         const int slots = event_slots(o);
-        if (slots < 32 || slots > 1024) return trk_status(set_error(TRK_E_INVALID, "queue_depth must be in [32, 1024]"));
+        if (slots < 32 || slots > 512) return trk_status(set_error(TRK_E_INVALID, "queue_depth must be in [32, 512]"));
         const int grid = o.grid > 0 ? o.grid : event_grid(slots);
         *bytes = event_work_bytes(slots, grid);
     }
@@ -476,7 +484,11 @@ trk_status run_histories(trk_geom_t g, const void* dev_particles, int64_t n, uin
     if (tracker < 0) return st;
     if (o.mode != TRK_MODE_HISTORY && o.mode != TRK_MODE_EVENT)
         return trk_status(set_error(TRK_E_INVALID, "run_histories: unknown mode %d", o.mode));
-    if (o.precision != TRK_FP64) return trk_status(set_error(TRK_E_UNSUPPORTED, "run_histories: precision %d not built", o.precision));
+    if (o.precision != TRK_FP64 && o.precision != TRK_FP32_LOCAL)
+        return trk_status(set_error(TRK_E_INVALID, "run_histories: unknown precision %d", o.precision));
+    const bool f32 = o.precision == TRK_FP32_LOCAL;
+    if (f32 && !HAVE_F32)
+        return trk_status(set_error(TRK_E_UNSUPPORTED, "run_histories: FP32-local is not in the exact (--fmad=false) build"));
     if (!(o.p_absorb >= 0.0 && o.p_absorb <= 1.0)) return trk_status(set_error(TRK_E_INVALID, "run_histories: p_absorb outside [0,1]"));
     if (n == 0) return TRK_OK;
     RunP rp;
@@ -494,28 +506,39 @@ trk_status run_histories(trk_geom_t g, const void* dev_particles, int64_t n, uin
     auto* R = reinterpret_cast<unsigned long long*>(dev_records);
     const bool csg = tracker == TRK_TRACKER_CSG;
     const int flags = (dev_records ? F_REC : 0) | (cut ? F_CUT : 0);
+    if (f32 && cut) return trk_status(set_error(TRK_E_UNSUPPORTED, "run_histories: path cutoff needs FP64 precision"));
     if (o.mode == TRK_MODE_EVENT) {
         const int slots = event_slots(o);
-        if (slots < 32 || slots > 1024) return trk_status(set_error(TRK_E_INVALID, "queue_depth must be in [32, 1024]"));
+        if (slots < 32 || slots > 512) return trk_status(set_error(TRK_E_INVALID, "queue_depth must be in [32, 512]"));
         const int grid = o.grid > 0 ? o.grid : event_grid(slots);
-        return launch_event(g, P, n, rp, csg, flags, T, C, R, dev_work, work_bytes, slots, grid, s);
+        return launch_event(g, P, n, rp, csg, f32, flags, T, C, R, dev_work, work_bytes, slots, grid, s);
     }
     const int block = o.block > 0 ? o.block : 128;
     if (block > 128 || (block & 31)) return trk_status(set_error(TRK_E_INVALID, "run_histories: block must be a multiple of 32, <= 128"));
-#define TRK_LAUNCH(CSGV, F) return launch_history<CSGV, F>(g, P, n, rp, T, C, R, nullptr, nullptr, block, o.grid, s)
+#define TRK_LAUNCH(CSGV, F32V, F) return launch_history<CSGV, F32V, F>(g, P, n, rp, T, C, R, nullptr, nullptr, block, o.grid, s)
+    if (f32) {
+#ifndef TRK_EXACT
+        if (csg) {
+            if (flags & F_REC) TRK_LAUNCH(true, true, F_REC);
+            TRK_LAUNCH(true, true, 0);
+        }
+        if (flags & F_REC) TRK_LAUNCH(false, true, F_REC);
+        TRK_LAUNCH(false, true, 0);
+#endif
+    }
     if (csg) {
         switch (flags) {
-            case 0: TRK_LAUNCH(true, 0);
-            case F_REC: TRK_LAUNCH(true, F_REC);
-            case F_CUT: TRK_LAUNCH(true, F_CUT);
-            default: TRK_LAUNCH(true, F_REC | F_CUT);
+            case 0: TRK_LAUNCH(true, false, 0);
+            case F_REC: TRK_LAUNCH(true, false, F_REC);
+            case F_CUT: TRK_LAUNCH(true, false, F_CUT);
+            default: TRK_LAUNCH(true, false, F_REC | F_CUT);
         }
     } else {
         switch (flags) {
-            case 0: TRK_LAUNCH(false, 0);
-            case F_REC: TRK_LAUNCH(false, F_REC);
-            case F_CUT: TRK_LAUNCH(false, F_CUT);
-            default: TRK_LAUNCH(false, F_REC | F_CUT);
+            case 0: TRK_LAUNCH(false, false, 0);
+            case F_REC: TRK_LAUNCH(false, false, F_REC);
+            case F_CUT: TRK_LAUNCH(false, false, F_CUT);
+            default: TRK_LAUNCH(false, false, F_REC | F_CUT);
         }
     }
 #undef TRK_LAUNCH
@@ -545,9 +568,18 @@ trk_status trk_trace(trk_geom_t g, const void* dev_particles, int64_t n, int32_t
     auto* C = reinterpret_cast<unsigned long long*>(dev_counters);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const ParticlesView P = view_of(dev_particles, n);
+    if (o.precision == TRK_FP32_LOCAL) {
+#ifndef TRK_EXACT
+        if (tracker == TRK_TRACKER_CSG)
+            return launch_history<true, true, F_TRACE>(g, P, n, rp, T, C, nullptr, dev_inst, dev_len, 128, 0, s);
+        return launch_history<false, true, F_TRACE>(g, P, n, rp, T, C, nullptr, dev_inst, dev_len, 128, 0, s);
+#else
+        return trk_status(set_error(TRK_E_UNSUPPORTED, "trk_trace: FP32-local is not in the exact build"));
+#endif
+    }
     if (tracker == TRK_TRACKER_CSG)
-        return launch_history<true, F_TRACE>(g, P, n, rp, T, C, nullptr, dev_inst, dev_len, 128, 0, s);
-    return launch_history<false, F_TRACE>(g, P, n, rp, T, C, nullptr, dev_inst, dev_len, 128, 0, s);
+        return launch_history<true, false, F_TRACE>(g, P, n, rp, T, C, nullptr, dev_inst, dev_len, 128, 0, s);
+    return launch_history<false, false, F_TRACE>(g, P, n, rp, T, C, nullptr, dev_inst, dev_len, 128, 0, s);
 }
 
 trk_status tally_read(trk_geom_t g, const uint64_t* dev_tally, double* host_out, int64_t n_inst,
