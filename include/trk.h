@@ -220,6 +220,28 @@ trk_status transmission_bwd(trk_geom_t g, int tracker, int64_t n, const double* 
                             double* dev_grad, void* dev_work, size_t work_bytes, void* stream);
 
 /*
+ * transmission_bwd_noalloc - transmission_bwd for callers that cannot
+ * allocate device memory themselves (for instance a program whose device
+ * memory is all handed out by another framework's allocator, or a loop that
+ * cannot pay for cudaMalloc's implicit synchronisation).  The paper has no
+ * counterpart; it is a packaging of transmission_bwd.
+ *   Same arguments as transmission_bwd minus the work buffer: the scratch
+ *   (per-block partial sums) lives in a fixed 4 MiB array inside the
+ *   library's device image, held on every device that loads the library.
+ *   The caller still provides rays, sigma, dev_gT and dev_grad.
+ *   Allocates nothing (no cudaMalloc/cudaFree, no allocating library call).
+ *   The first call on a device looks up the array's address on that device;
+ *   make it before any stream capture.  All calls share the array: calls
+ *   whose kernels overlap on the GPU race on it.
+ * Errors: TRK_E_NOMEM when n needs more scratch than the array holds (about
+ * 5.5 million rays with 8 materials; the message gives this geometry's
+ * limit), TRK_E_INVALID, TRK_E_CUDA, and those of transmission_bwd.
+ */
+trk_status transmission_bwd_noalloc(trk_geom_t g, int tracker, int64_t n, const double* dev_rays,
+                                    const double* dev_sigma, double pitch, const double* dev_gT,
+                                    double* dev_grad, void* stream);
+
+/*
  * trk_peak_kernel - measurement support (the paper has no counterpart):
  * launches a microbenchmark of `blocks` x 256 threads on `stream` and
  * returns in *ops the number of operations it performs, for the caller to

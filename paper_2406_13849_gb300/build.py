@@ -20,6 +20,8 @@ INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # translation units compiled once per flavour (fast / exact)
 KERNEL_UNITS = ["trk_kernels", "trk_event"]
+# translation units compiled once and linked into both flavours
+SHARED_UNITS = ["peaks", "noalloc"]
 
 
 def _cuda_home() -> str:
@@ -65,9 +67,12 @@ def build(force: bool = False, verbose: bool = False) -> dict:
         ["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fPIC", "-Wall"] + inc +
         ["-I" + os.path.join(cuda, "include"), "-c", os.path.join(CSRC, "geometry_build.cpp"), "-o", host_obj],
     ]
-    peaks_obj = os.path.join(BUILD, "peaks.o")
-    jobs.append([nvcc] + ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"] + inc +
-                ["-c", os.path.join(CSRC, "peaks.cu"), "-o", peaks_obj])
+    shared_objs = []
+    for unit in SHARED_UNITS:
+        obj = os.path.join(BUILD, unit + ".o")
+        shared_objs.append(obj)
+        jobs.append([nvcc] + ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"] + inc +
+                    ["-c", os.path.join(CSRC, unit + ".cu"), "-o", obj])
     extra_flags = os.environ.get("TRK_NVCC_FLAGS", "").split()
     kobjs = {"fast": [], "exact": []}
     for flavour, extra in (("fast", []), ("exact", ["--fmad=false", "-DTRK_EXACT"])):
@@ -89,8 +94,8 @@ def build(force: bool = False, verbose: bool = False) -> dict:
         raise RuntimeError("library build failed:\n" + msg)
     for flavour, target in outs.items():
         tmp = target + ".tmp"
-        subprocess.run([nvcc] + ARCH + ["-shared", "-o", tmp, host_obj] + kobjs[flavour] + [peaks_obj,
-                                        "-lcudart"], check=True)
+        subprocess.run([nvcc] + ARCH + ["-shared", "-o", tmp, host_obj] + kobjs[flavour] + shared_objs +
+                       ["-lcudart"], check=True)
         os.replace(tmp, target)
     return outs
 

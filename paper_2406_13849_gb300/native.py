@@ -84,6 +84,8 @@ def library(exact: bool = False):
             "transmission_bwd_work_bytes": (ctypes.c_int, [_P, i64, psz]),
             "transmission_bwd": (ctypes.c_int, [_P, ctypes.c_int, i64, _P, _P, ctypes.c_double, _P, _P,
                                                 _P, sz, _P]),
+            "transmission_bwd_noalloc": (ctypes.c_int, [_P, ctypes.c_int, i64, _P, _P, ctypes.c_double, _P, _P,
+                                                        _P]),
             "trk_peak_kernel": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, sz,
                                                ctypes.POINTER(ctypes.c_double), _P]),
         }
@@ -249,6 +251,15 @@ class Geometry:
                                                    float(pitch), _ptr(gT.contiguous()), _ptr(grad), _ptr(work),
                                                    work.numel(), _stream(stream)))
         return grad
+
+
+def transmission_bwd_noalloc(geom: "Geometry", rays, sigma, pitch: float, gT, grad_out, tracker=TRACKER_AUTO,
+                             stream=None):
+    """transmission_bwd without a work buffer (its scratch lives in the
+    library's fixed device array); writes grad_out (n_materials + 4)."""
+    _check(geom.lib, geom.lib.transmission_bwd_noalloc(geom.h, tracker, rays.shape[0], _ptr(rays), _ptr(sigma),
+                                                       float(pitch), _ptr(gT), _ptr(grad_out), _stream(stream)))
+    return grad_out
 
 
 def unpack_records(rec: torch.Tensor):
