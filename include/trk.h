@@ -220,6 +220,49 @@ trk_status transmission_bwd(trk_geom_t g, int tracker, int64_t n, const double* 
                             double* dev_grad, void* dev_work, size_t work_bytes, void* stream);
 
 /*
+ * Batched tracking: many independent geometries and particle populations
+ * of uneven size in one persistent launch (the Alg. 2 loop over several
+ * problems at once; the paper runs one problem per GPU).
+ *
+ * batch_create - host object over n_geom built geometries.
+ *   dev_particles[k]  particle buffer of geometry k (source_init layout),
+ *   counts[k]         its number of particles (<= 2^31),
+ *   dev_tallies[k]    its tally (uint64[n_instances of geometry k]),
+ *   dev_counters      uint64[n_geom * TRK_NCOUNTERS], geometry k at k*16,
+ *   dev_records       NULL or per-geometry record arrays (as run_histories),
+ *   tracker           TRK_TRACKER_AUTO (rect where possible), _RECT or _CSG.
+ * Tallies and counters are added to, not cleared.  Particle ids restart at
+ * first_id for every geometry (each geometry keys its own random numbers
+ * with its geometry id).  The pointer arrays are host memory, read here.
+ */
+typedef struct trk_batch* trk_batch_t;
+trk_status batch_create(const trk_geom_t* geoms, int n_geom, const void* const* dev_particles,
+                        const int64_t* counts, uint64_t* const* dev_tallies, uint64_t* dev_counters,
+                        uint64_t* const* dev_records, int tracker, trk_batch_t* out);
+trk_status batch_destroy(trk_batch_t b);
+
+/* Bytes of the device table (caller-owned work buffer, 256-byte aligned). */
+trk_status batch_work_bytes(trk_batch_t b, size_t* bytes);
+
+/* Writes the device table for chunks of `chunk` particles (0 = 512) into
+ * dev_work; synchronises `stream`.  Call again to change the chunk size. */
+trk_status batch_upload(trk_batch_t b, void* dev_work, size_t work_bytes, int chunk, void* stream);
+
+/* One persistent launch over the whole batch (opts: precision, block, grid,
+ * seed, first_id, p_absorb, max_segments; mode and path cutoff ignored).
+ * Issues a memset and one kernel on `stream` and nothing else, so after
+ * batch_upload it can be captured in a CUDA graph and replayed. */
+trk_status run_batched(trk_batch_t b, void* dev_work, const trk_run_opts* opts, void* stream);
+
+/* Autotuner: times block sizes {64, 96, 128} x chunk sizes {128, 512, 2048}
+ * on the batch itself (CUDA events, `reps` launches each) and writes the
+ * fastest to opts->block and *chunk_out, leaving the table uploaded for
+ * it; *best_ms (optional) gets its time.  The trial launches add to the
+ * tallies and counters: clear them afterwards.  Synchronises `stream`. */
+trk_status batch_autotune(trk_batch_t b, void* dev_work, size_t work_bytes, trk_run_opts* opts,
+                          int* chunk_out, int reps, double* best_ms, void* stream);
+
+/*
  * transmission_bwd_noalloc - transmission_bwd for callers that cannot
  * allocate device memory themselves (for instance a program whose device
  * memory is all handed out by another framework's allocator, or a loop that

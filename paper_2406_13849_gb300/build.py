@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # translation units compiled once per flavour (fast / exact)
-KERNEL_UNITS = ["trk_kernels", "trk_event"]
+KERNEL_UNITS = ["trk_kernels", "trk_event", "batch"]
 # translation units compiled once and linked into both flavours
 SHARED_UNITS = ["peaks", "noalloc"]
 

@@ -522,8 +522,6 @@ void make_pseudo_array(HGeom& G, int u) {
 // Cell boxes (Sec. 4.3): start from the universe box and truncate by each of
 // the cell's surfaces; slanted planes clip the xy polygon of the box.
 // ---------------------------------------------------------------------------
-const double BIG = 1e12;
-
 void clip_polygon(std::vector<std::pair<double, double>>& poly, double nx, double ny, double d, int sense) {
     // keep sense * (n.x - d) >= 0
     std::vector<std::pair<double, double>> out;
@@ -563,8 +561,15 @@ void cell_box(const HGeom& G, const HUniv& U, HCell& c) {
         }
     }
     if (!slanted.empty()) {
-        double x0 = std::max(b[0], -BIG), x1 = std::min(b[3], BIG);
-        double y0 = std::max(b[1], -BIG), y1 = std::min(b[4], BIG);
+        // Clip a square sized from the cell's own numbers (not a huge one:
+        // polygon vertices computed near 1e12 lose ~1e-4 to cancellation).
+        // A cell that still reaches the square's edge is unbounded there.
+        double S = 1.0;
+        for (int i : slanted) S = std::max(S, std::fabs(G.surf[size_t(c.surf[size_t(i)])].c[3]));
+        for (int k : {0, 1, 3, 4}) if (std::isfinite(b[k])) S = std::max(S, std::fabs(b[k]));
+        S = 4.0 * S + 1.0;
+        double x0 = std::max(b[0], -S), x1 = std::min(b[3], S);
+        double y0 = std::max(b[1], -S), y1 = std::min(b[4], S);
         std::vector<std::pair<double, double>> poly = {{x0, y0}, {x1, y0}, {x1, y1}, {x0, y1}};
         for (int i : slanted) {
             const HSurf& s = G.surf[size_t(c.surf[size_t(i)])];
@@ -579,10 +584,11 @@ void cell_box(const HGeom& G, const HUniv& U, HCell& c) {
                 px0 = std::min(px0, p.first); px1 = std::max(px1, p.first);
                 py0 = std::min(py0, p.second); py1 = std::max(py1, p.second);
             }
-            b[0] = px0 <= -0.5 * BIG ? -INF : px0;
-            b[3] = px1 >= 0.5 * BIG ? INF : px1;
-            b[1] = py0 <= -0.5 * BIG ? -INF : py0;
-            b[4] = py1 >= 0.5 * BIG ? INF : py1;
+            const double edge = S * (1.0 - 1e-9);
+            b[0] = (px0 <= -edge && !std::isfinite(b[0])) ? -INF : px0;
+            b[3] = (px1 >= edge && !std::isfinite(b[3])) ? INF : px1;
+            b[1] = (py0 <= -edge && !std::isfinite(b[1])) ? -INF : py0;
+            b[4] = (py1 >= edge && !std::isfinite(b[4])) ? INF : py1;
         }
     }
     for (int k = 0; k < 6; ++k) c.box[k] = b[k];

@@ -84,6 +84,13 @@ def library(exact: bool = False):
             "transmission_bwd_work_bytes": (ctypes.c_int, [_P, i64, psz]),
             "transmission_bwd": (ctypes.c_int, [_P, ctypes.c_int, i64, _P, _P, ctypes.c_double, _P, _P,
                                                 _P, sz, _P]),
+            "batch_create": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, _P, ctypes.c_int, ctypes.POINTER(_P)]),
+            "batch_destroy": (ctypes.c_int, [_P]),
+            "batch_work_bytes": (ctypes.c_int, [_P, psz]),
+            "batch_upload": (ctypes.c_int, [_P, _P, sz, ctypes.c_int, _P]),
+            "run_batched": (ctypes.c_int, [_P, _P, ctypes.POINTER(RunOpts), _P]),
+            "batch_autotune": (ctypes.c_int, [_P, _P, sz, ctypes.POINTER(RunOpts), ctypes.POINTER(ctypes.c_int),
+                                              ctypes.c_int, ctypes.POINTER(ctypes.c_double), _P]),
             "transmission_bwd_noalloc": (ctypes.c_int, [_P, ctypes.c_int, i64, _P, _P, ctypes.c_double, _P, _P,
                                                         _P]),
             "trk_peak_kernel": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, sz,
@@ -251,6 +258,80 @@ class Geometry:
                                                    float(pitch), _ptr(gT.contiguous()), _ptr(grad), _ptr(work),
                                                    work.numel(), _stream(stream)))
         return grad
+
+
+class Batch:
+    """Many geometries and particle populations in one persistent launch.
+
+    geoms: list of Geometry (same library flavour); particles: their
+    source_init buffers; counts: particles per geometry.  Tallies, counters
+    (one row of NCOUNTERS per geometry) and optional records are allocated
+    here unless given.
+    """
+
+    def __init__(self, geoms, particles, counts, tracker=TRACKER_AUTO, records: bool = False):
+        self.lib = geoms[0].lib
+        self.geoms = list(geoms)
+        self.counts = [int(c) for c in counts]
+        dev = geoms[0].device
+        self.tallies = [torch.zeros(g.n_inst, dtype=torch.int64, device=dev) for g in geoms]
+        self.counters = torch.zeros(len(geoms) * NCOUNTERS, dtype=torch.int64, device=dev)
+        self.records = [torch.zeros(2 * max(c, 1), dtype=torch.int64, device=dev) for c in self.counts] \
+            if records else None
+        self.particles = list(particles)
+        n = len(geoms)
+        arr = ctypes.c_void_p * n
+        hg = arr(*[g.h.value if isinstance(g.h, ctypes.c_void_p) else g.h for g in geoms])
+        hp = arr(*[p.data_ptr() for p in particles])
+        ht = arr(*[t.data_ptr() for t in self.tallies])
+        hr = arr(*[r.data_ptr() for r in self.records]) if records else None
+        hc = (ctypes.c_int64 * n)(*self.counts)
+        h = ctypes.c_void_p()
+        _check(self.lib, self.lib.batch_create(ctypes.cast(hg, _P), n, ctypes.cast(hp, _P), ctypes.cast(hc, _P),
+                                               ctypes.cast(ht, _P), _ptr(self.counters),
+                                               ctypes.cast(hr, _P) if hr is not None else None, tracker,
+                                               ctypes.byref(h)))
+        self.h = h
+        b = ctypes.c_size_t(0)
+        _check(self.lib, self.lib.batch_work_bytes(h, ctypes.byref(b)))
+        self.work = torch.empty(b.value + 256, dtype=torch.uint8, device=dev)
+        off = (-self.work.data_ptr()) % 256
+        self.work_ptr = ctypes.c_void_p(self.work.data_ptr() + off)
+        self.work_bytes = b.value
+        self.chunk = 0
+
+    def upload(self, chunk: int = 512, stream=None):
+        _check(self.lib, self.lib.batch_upload(self.h, self.work_ptr, self.work_bytes, chunk, _stream(stream)))
+        self.chunk = chunk
+
+    def run(self, opts: RunOpts | None = None, stream=None, **kw):
+        opts = opts if opts is not None else default_opts(**kw)
+        _check(self.lib, self.lib.run_batched(self.h, self.work_ptr, ctypes.byref(opts), _stream(stream)))
+
+    def autotune(self, opts: RunOpts, reps: int = 2, stream=None):
+        ch = ctypes.c_int(0)
+        best = ctypes.c_double(0)
+        _check(self.lib, self.lib.batch_autotune(self.h, self.work_ptr, self.work_bytes, ctypes.byref(opts),
+                                                 ctypes.byref(ch), reps, ctypes.byref(best), _stream(stream)))
+        self.chunk = ch.value
+        self.zero()
+        return opts, ch.value, best.value
+
+    def zero(self):
+        for t in self.tallies:
+            t.zero_()
+        self.counters.zero_()
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def transmission_bwd_noalloc(geom: "Geometry", rays, sigma, pitch: float, gT, grad_out, tracker=TRACKER_AUTO,
