@@ -5,7 +5,11 @@ Workload: the three-level nested rectilinear core (15x15 assemblies of 17x17
 pins inside a vacuum cylinder r=170 cm, h=366 cm, 4 materials, absorption
 0.25), 1e7 particles per GPU per step, synthetic inputs from the seeded
 generator.  One step = source_init + run_histories (BVH-CSG tracker, FP64,
-history kernel) over the whole batch: every step of the hot path.
+event-based kernel) over the whole batch: every step of the hot path.
+Companion lines: the rect tracker and the history kernel on the same
+workload, FP32-local precision, and the 64-geometry batched workload
+(FP32-local persistent launch replayed from a CUDA graph vs the plain FP64
+history kernel launched once per geometry).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -34,6 +38,10 @@ PARTICLES = 10_000_000
 P_ABSORB = 0.25
 SEED = 1
 CPU_SAMPLE = 1_000_000
+EVENT_SLOTS = 256
+# DRAM bytes per launch of the dominant kernel from the ncu capture (null
+# until a capture of the current kernel is recorded in profiles/)
+TRAFFIC_PER_LAUNCH = None
 
 
 def _env_int(k, d):
@@ -207,21 +215,24 @@ def main() -> None:
     parts = torch.empty(g.particle_bytes(n), dtype=torch.uint8, device=dev)
     tally = torch.zeros(g.n_inst, dtype=torch.int64, device=dev)
     cnt = torch.zeros(N.NCOUNTERS, dtype=torch.int64, device=dev)
-
-    def make_opts(tracker, mode=N.MODE_HISTORY):
-        return N.default_opts(tracker=tracker, mode=mode, precision=N.FP64, seed=SEED,
-                              first_id=first_id, p_absorb=P_ABSORB)
-
     work_cache = {}
 
-    def timed(tracker, steps, warmup, sampler=None, mode=N.MODE_HISTORY):
-        opts = make_opts(tracker, mode)
+    def make_opts(tracker, mode, prec=N.FP64):
+        return N.default_opts(tracker=tracker, mode=mode, precision=prec, seed=SEED, first_id=first_id,
+                              p_absorb=P_ABSORB, queue_depth=EVENT_SLOTS)
+
+    def work_for(opts):
         wb = g.work_bytes(n, opts)
-        work = None
-        if wb:
-            if wb not in work_cache:
-                work_cache[wb] = torch.empty(wb + 256, dtype=torch.uint8, device=dev)
-            work = work_cache[wb]
+        if not wb:
+            return None
+        if wb not in work_cache:
+            work_cache[wb] = torch.empty(wb + 256, dtype=torch.uint8, device=dev)
+        return work_cache[wb]
+
+    def timed(tracker, mode, steps, warmup, prec=N.FP64, sampler=None):
+        """K steps of source_init + run_histories; CUDA events on the stream."""
+        opts = make_opts(tracker, mode, prec)
+        work = work_for(opts)
         for _ in range(warmup):
             g.source_init(n, seed=SEED, first_id=first_id, out=parts)
             g.run_histories(parts, n, tally=tally, counters=cnt, opts=opts, work=work)
@@ -233,7 +244,6 @@ def main() -> None:
         if sampler:
             sampler.start()
         barrier()
-        t0 = time.perf_counter()
         for a, b, c in ev:
             a.record(stream)
             g.source_init(n, seed=SEED, first_id=first_id, out=parts)
@@ -241,22 +251,16 @@ def main() -> None:
             g.run_histories(parts, n, tally=tally, counters=cnt, opts=opts, work=work)
             c.record(stream)
         barrier()
-        wall = time.perf_counter() - t0
         clocks = sampler.stop() if sampler else None
-        step_ms = [a.elapsed_time(c) for a, b, c in ev]
-        hist_ms = [b.elapsed_time(c) for a, b, c in ev]
         c_host = cnt.cpu().numpy().view(np.uint64)
-        return {"ms": sum(step_ms), "hist_ms": hist_ms, "segments": int(c_host[0]), "wall": wall,
-                "counters": c_host.copy(), "clocks": clocks}
+        return {"ms": sum(a.elapsed_time(c) for a, b, c in ev), "kernel_ms": [b.elapsed_time(c) for a, b, c in ev],
+                "segments": int(c_host[0]), "counters": c_host.copy(), "clocks": clocks}
 
-    # main line: BVH-CSG tracker
-    main_run = timed(N.TRACKER_CSG, args.steps, args.warmup, ClockSampler(local))
-    # companion measurements (same workload): rect tracker, event-based kernel
-    rect_run = timed(N.TRACKER_RECT, max(2, args.steps // 2), 3)
-    ev_csg = timed(N.TRACKER_CSG, max(2, args.steps // 2), 3, mode=N.MODE_EVENT)
-    ev_rect = timed(N.TRACKER_RECT, max(2, args.steps // 2), 3, mode=N.MODE_EVENT)
+    def rate(r):
+        return r["segments"] / (r["ms"] / 1e3)
 
-    # max over ranks
+    # ---- main line: BVH-CSG tracker, FP64, event-based kernel ---------------
+    main_run = timed(N.TRACKER_CSG, N.MODE_EVENT, args.steps, args.warmup, sampler=ClockSampler(local))
     t_local = torch.tensor([main_run["ms"], float(main_run["segments"])], dtype=torch.float64, device=dev)
     if world > 1:
         tmax = t_local.clone()
@@ -268,66 +272,72 @@ def main() -> None:
         total_ms, total_seg = main_run["ms"], float(main_run["segments"])
     value = total_seg / (total_ms / 1e3)
 
-    # end to end through the C-ABI with host buffers: births from pinned host
-    # memory, tally and counters read back, every step
+    # ---- companions on the same workload ----------------------------------
+    k2 = max(2, args.steps // 2)
+    rect_ev = timed(N.TRACKER_RECT, N.MODE_EVENT, k2, 3)
+    csg_hist = timed(N.TRACKER_CSG, N.MODE_HISTORY, k2, 3)
+    rect_hist = timed(N.TRACKER_RECT, N.MODE_HISTORY, k2, 3)
+    csg_ev32 = timed(N.TRACKER_CSG, N.MODE_EVENT, k2, 3, prec=N.FP32_LOCAL)
+
+    # ---- end to end through the C-ABI with host buffers ---------------------
     host_parts = torch.empty(parts.numel(), dtype=torch.uint8, pin_memory=True)
     g.source_init(n, seed=SEED, first_id=first_id, out=parts)
     host_parts.copy_(parts)
-    host_tally = np.zeros(g.n_inst)
-    e2e_steps = max(2, args.steps // 2)
-    opts = make_opts(N.TRACKER_CSG)
+    opts = make_opts(N.TRACKER_CSG, N.MODE_EVENT)
+    work = work_for(opts)
     cnt.zero_()
     barrier()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(e2e_steps):
+    for _ in range(k2):
         parts.copy_(host_parts, non_blocking=True)
         tally.zero_()
-        g.run_histories(parts, n, tally=tally, counters=cnt, opts=opts)
-        host_tally = g.tally_read(tally, cnt)          # synchronises the stream
+        g.run_histories(parts, n, tally=tally, counters=cnt, opts=opts, work=work)
+        g.tally_read(tally, cnt)          # device -> host, synchronises the stream
     e1.record(stream)
     barrier()
-    e2e_ms = e0.elapsed_time(e1)
     e2e_seg = int(cnt.cpu().numpy().view(np.uint64)[0])
-    e2e = {"value": world * e2e_seg / (e2e_ms / 1e3), "unit": UNIT,
+    e2e = {"value": world * e2e_seg / (e0.elapsed_time(e1) / 1e3), "unit": UNIT,
            "h2d_bytes_per_step": int(parts.numel()), "d2h_bytes_per_step": int(g.n_inst * 8 + 8)}
 
-    # roofline of the dominant kernel (the history kernel)
+    # ---- batched: 64 geometries, FP32-local graph replay vs FP64 launch loop
+    batch = run_config4(N, I, dev, stream, barrier, rank, k2)
+
+    # ---- roofline of the dominant kernel (the event kernel, CSG, FP64) ------
     fps = flops_per_segment(desc)
-    hist_ms = statistics.mean(main_run["hist_ms"])
+    kern_ms = statistics.mean(main_run["kernel_ms"])
     seg_per_launch = main_run["segments"] / args.steps
-    achieved = fps["per_segment"] * seg_per_launch / (hist_ms / 1e3) / 1e12
+    achieved = fps["per_segment"] * seg_per_launch / (kern_ms / 1e3) / 1e12
     scratch = torch.empty(1 << 16, dtype=torch.uint8, device=dev)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    pk_best = 0.0
+    pk = 0.0
     for _ in range(3):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         ops = N.peak_kernel(0, sms * 8, 4096, 0, scratch)
         b.record(stream)
         torch.cuda.synchronize()
-        pk_best = max(pk_best, ops / (a.elapsed_time(b) / 1e3) / 1e12)
-    roofline = {"bound": "alu", "achieved": achieved, "peak": pk_best, "unit": "TFLOP/s",
-                "frac": achieved / pk_best if pk_best else None, "traffic": None,
-                "kernel": "k_history<CSG> (FP64)",
-                "peak_source": "measured FP64 FMA issue rate (trk_peak_kernel, same run)",
-                "flops_per_segment": fps["per_segment"]}
+        pk = max(pk, ops / (a.elapsed_time(b) / 1e3) / 1e12)
+    roofline = {"bound": "alu", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
+                "frac": achieved / pk if pk else None, "traffic": TRAFFIC_PER_LAUNCH,
+                "kernel": "k_event<CSG,FP64> (run_histories, event mode)",
+                "peak_source": "measured FP64 FMA rate (trk_peak_kernel, same run; of measured)",
+                "flops_per_segment": fps["per_segment"],
+                "flops_definition": "FP64 add/sub, mul, div, sqrt per segment counted by the oracle's counting "
+                                    "build in rect-tracker mode on this workload"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(desc, CPU_SAMPLE)
 
-    rect_value = rect_run["segments"] / (rect_run["ms"] / 1e3)
-    csg_value = main_run["segments"] / (main_run["ms"] / 1e3)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "particles_per_gpu": n, "tracker": "csg_bvh",
-                       "mode": "history", "precision": "fp64", "build": "fast",
-                       "l2": "inputs larger than L2 (particle buffer %d MB per step)" % (parts.numel() >> 20),
+            "config": {"workload": WORKLOAD, "particles_per_gpu": n, "tracker": "csg_bvh", "mode": "event",
+                       "precision": "fp64", "build": "fast", "queue_depth": EVENT_SLOTS,
+                       "l2": "inputs larger than L2 (particle buffer %d MB rewritten every step)" % (parts.numel() >> 20),
                        "step": "source_init + run_histories"},
             "particles_per_s": world * n * args.steps / (total_ms / 1e3),
             "clocks": main_run["clocks"],
@@ -336,18 +346,99 @@ def main() -> None:
             "roofline": roofline,
             "cpu_baseline": cpu,
             "variants": {
-                "csg_bvh_fp64_history_segments_per_s": csg_value,
-                "rect_fp64_history_segments_per_s": rect_value,
-                "csg_over_rect": csg_value / rect_value,
-                "csg_bvh_fp64_event_segments_per_s": ev_csg["segments"] / (ev_csg["ms"] / 1e3),
-                "rect_fp64_event_segments_per_s": ev_rect["segments"] / (ev_rect["ms"] / 1e3),
-                "history_kernel_ms": hist_ms,
+                "csg_fp64_event": rate(main_run),
+                "rect_fp64_event": rate(rect_ev),
+                "csg_over_rect_event": rate(main_run) / rate(rect_ev),
+                "csg_fp64_history": rate(csg_hist),
+                "rect_fp64_history": rate(rect_hist),
+                "csg_over_rect_history": rate(csg_hist) / rate(rect_hist),
+                "csg_fp32local_event": rate(csg_ev32),
+                "fp32local_close_call_fraction": float(csg_ev32["counters"][10]) / max(1, csg_ev32["segments"]),
                 "segments_per_particle": main_run["segments"] / (n * args.steps),
+                "event_kernel_ms": kern_ms,
             },
+            "batched": batch,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_config4(N, I, dev, stream, barrier, rank, steps):
+    """64 geometries (3x3..17x17 rect/hex, 2-3 levels, 1e4..1e6 particles):
+    one autotuned persistent launch, FP32-local, replayed from a CUDA graph,
+    against the plain FP64 history kernel launched once per geometry."""
+    import numpy as np
+    import torch
+    members = I.config4()
+    geoms = [N.Geometry(I.to_json(d), device=dev) for d, _ in members]
+    counts = [c for _, c in members]
+    parts = [g.source_init(c, seed=SEED) for g, c in zip(geoms, counts)]
+    b = N.Batch(geoms, parts, counts)
+    opts32 = N.default_opts(seed=SEED, p_absorb=P_ABSORB, precision=N.FP32_LOCAL)
+    opts32, chunk, _ = b.autotune(opts32, reps=2)
+    s = torch.cuda.Stream(device=dev)
+    s.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        b.run(opts32)
+    graph.replay()
+    torch.cuda.synchronize()
+    b.zero()
+    barrier()
+    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        graph.replay()
+    e.record(stream)
+    barrier()
+    ms_b = a.elapsed_time(e)
+    seg_b = int(b.counters.cpu().numpy().view(np.uint64).reshape(-1, 16)[:, 0].sum())
+    # per-geometry loop, plain FP64 history kernel
+    tallies = [torch.zeros(gg.n_inst, dtype=torch.int64, device=dev) for gg in geoms]
+    cnt = torch.zeros(16, dtype=torch.int64, device=dev)
+    o64 = N.default_opts(seed=SEED, p_absorb=P_ABSORB, precision=N.FP64, mode=N.MODE_HISTORY)
+    for gg, pp, cc, tt in zip(geoms, parts, counts, tallies):
+        gg.run_histories(pp, cc, tally=tt, counters=cnt, opts=o64)
+    cnt.zero_()
+    barrier()
+    a.record(stream)
+    for _ in range(steps):
+        for gg, pp, cc, tt in zip(geoms, parts, counts, tallies):
+            gg.run_histories(pp, cc, tally=tt, counters=cnt, opts=o64)
+    e.record(stream)
+    barrier()
+    ms_l = a.elapsed_time(e)
+    seg_l = int(cnt.cpu().numpy().view(np.uint64)[0])
+    # same launch loop in FP32-local, and the batch in FP64, to separate the two effects
+    cnt.zero_()
+    o32 = N.default_opts(seed=SEED, p_absorb=P_ABSORB, precision=N.FP32_LOCAL, mode=N.MODE_HISTORY)
+    a.record(stream)
+    for gg, pp, cc, tt in zip(geoms, parts, counts, tallies):
+        gg.run_histories(pp, cc, tally=tt, counters=cnt, opts=o32)
+    e.record(stream)
+    barrier()
+    ms_l32 = a.elapsed_time(e)
+    seg_l32 = int(cnt.cpu().numpy().view(np.uint64)[0])
+    b.zero()
+    o64b = N.default_opts(seed=SEED, p_absorb=P_ABSORB, precision=N.FP64, block=opts32.block)
+    a.record(stream)
+    b.run(o64b)
+    e.record(stream)
+    barrier()
+    ms_b64 = a.elapsed_time(e)
+    seg_b64 = int(b.counters.cpu().numpy().view(np.uint64).reshape(-1, 16)[:, 0].sum())
+    r_b = seg_b / (ms_b / 1e3)
+    r_l = seg_l / (ms_l / 1e3)
+    return {"workload": "64 geometries: 3x3..17x17 rect/hex lattices, 2-3 levels, 1e4..1e6 particles "
+                        "(log-uniform), %d particles" % sum(counts),
+            "batched_fp32local_graph_segments_per_s": r_b,
+            "loop_fp64_history_segments_per_s": r_l,
+            "batched_over_loop": r_b / r_l,
+            "loop_fp32local_history_segments_per_s": seg_l32 / (ms_l32 / 1e3),
+            "batched_fp64_segments_per_s": seg_b64 / (ms_b64 / 1e3),
+            "autotuned": {"block": opts32.block, "chunk": chunk},
+            "launches_per_pass": {"batched": 1, "loop": len(geoms)}}
 
 
 if __name__ == "__main__":

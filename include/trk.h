@@ -81,7 +81,8 @@ typedef struct {
     int grid;               /* blocks, 0 = default (a multiple of the SM count) */
     int queue_depth;        /* event mode: particle slots per warp (32..512), 0 = default 128 */
     int sort_interval;      /* event mode: regroup queues by cell every k rounds, 0 = never */
-    int reserved;
+    int max_rounds;         /* event mode: round limit per warp, 0 = from max_segments; past it the
+                               kernel stops and reports TRK_E_TIMEOUT in counters[TRK_K_STATUS] */
     uint64_t seed;          /* low 32 bits key the Philox stream with the geometry id */
     uint64_t first_id;      /* particle id of element 0 (ids key the random numbers) */
     uint64_t max_segments;  /* per-particle segment cap (0 = 1e6) */

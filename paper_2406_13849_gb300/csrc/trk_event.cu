@@ -340,7 +340,7 @@ size_t event_work_bytes(int slots, int grid) { return buf_bytes((long long)slots
 
 trk_status launch_event(trk_geom_t g, const ParticlesView& P, long long n, const RunP& rp, bool csg, bool f32,
                         int flags, unsigned long long* tally, unsigned long long* cnt, unsigned long long* rec,
-                        void* work, size_t work_bytes, int slots, int grid, cudaStream_t s) {
+                        void* work, size_t work_bytes, int slots, int grid, int max_rounds_opt, cudaStream_t s) {
     const long long T = (long long)slots * EV_WARPS * grid;
     if (work_bytes < buf_bytes(T) || !work)
         return trk_status(set_error(TRK_E_NOMEM, "run_histories (event): work buffer needs %zu bytes", buf_bytes(T)));
@@ -351,7 +351,8 @@ trk_status launch_event(trk_geom_t g, const ParticlesView& P, long long n, const
     // a particle needs at most max_segments + 1 flight rounds; a warp holds
     // `slots` particles at a time and refills every round
     const unsigned long long per_warp = (unsigned long long)(n / (T / slots) + slots + 1);
-    const unsigned long long max_rounds = (rp.max_segments + 2ULL) * (per_warp / slots + 2ULL) * 4ULL;
+    unsigned long long max_rounds = (rp.max_segments + 2ULL) * (per_warp / slots + 2ULL) * 4ULL;
+    if (max_rounds_opt > 0) max_rounds = (unsigned long long)max_rounds_opt;
 #define TRK_EV(C, F32V, F)                                                                                   \
     do {                                                                                                     \
         auto k = k_event<C, F32V, F>;                                                                        \

@@ -511,7 +511,8 @@ trk_status run_histories(trk_geom_t g, const void* dev_particles, int64_t n, uin
         const int slots = event_slots(o);
         if (slots < 32 || slots > 512) return trk_status(set_error(TRK_E_INVALID, "queue_depth must be in [32, 512]"));
         const int grid = o.grid > 0 ? o.grid : event_grid(slots);
-        return launch_event(g, P, n, rp, csg, f32, flags, T, C, R, dev_work, work_bytes, slots, grid, s);
+        if (o.max_rounds < 0) return trk_status(set_error(TRK_E_INVALID, "max_rounds must be >= 0"));
+        return launch_event(g, P, n, rp, csg, f32, flags, T, C, R, dev_work, work_bytes, slots, grid, o.max_rounds, s);
     }
     const int block = o.block > 0 ? o.block : 128;
     if (block > 128 || (block & 31)) return trk_status(set_error(TRK_E_INVALID, "run_histories: block must be a multiple of 32, <= 128"));

@@ -41,7 +41,7 @@ class TrkError(RuntimeError):
 class RunOpts(ctypes.Structure):
     _fields_ = [("tracker", ctypes.c_int), ("mode", ctypes.c_int), ("precision", ctypes.c_int),
                 ("block", ctypes.c_int), ("grid", ctypes.c_int), ("queue_depth", ctypes.c_int),
-                ("sort_interval", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("sort_interval", ctypes.c_int), ("max_rounds", ctypes.c_int),
                 ("seed", ctypes.c_uint64), ("first_id", ctypes.c_uint64),
                 ("max_segments", ctypes.c_uint64), ("p_absorb", ctypes.c_double),
                 ("max_path", ctypes.c_double)]

@@ -470,3 +470,25 @@ def test_fp32_local_full_size_counts(mode):
     assert same.mean() > 0.995
     ta, tb = _u64(a[0]).astype(np.float64), _u64(b[0]).astype(np.float64)
     assert abs(tb.sum() - ta.sum()) / ta.sum() < 1e-4
+
+
+# ---------------------------------------------------------------------------
+# failure detection without a GPU fault: the event kernel's round limit
+# ---------------------------------------------------------------------------
+
+def test_event_round_limit_reports_timeout():
+    desc, pa, n = CASES["small_core"]
+    g = _gpu(desc, exact=False)
+    parts = g.source_init(n, seed=SEED)
+    tally, cnt, _ = g.run_histories(parts, n, tracker=N.TRACKER_CSG, mode=N.MODE_EVENT, max_rounds=2,
+                                    p_absorb=pa, seed=SEED)
+    torch.cuda.synchronize()
+    c = cnt.cpu().numpy()
+    assert c[N.K["status"]] == -7                       # TRK_E_TIMEOUT, read on the host
+    with pytest.raises(N.TrkError) as e:
+        g.tally_read(tally, cnt)
+    assert e.value.code == -7
+    # the context stays usable: a normal run afterwards completes
+    tally2, cnt2, _ = g.run_histories(parts, n, tracker=N.TRACKER_CSG, mode=N.MODE_EVENT, p_absorb=pa, seed=SEED)
+    g.tally_read(tally2, cnt2)
+    assert int(cnt2.cpu()[N.K["status"]]) == 0
