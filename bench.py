@@ -39,9 +39,11 @@ P_ABSORB = 0.25
 SEED = 1
 CPU_SAMPLE = 1_000_000
 EVENT_SLOTS = 256
-# DRAM bytes per launch of the dominant kernel from the ncu capture (null
-# until a capture of the current kernel is recorded in profiles/)
-TRAFFIC_PER_LAUNCH = None
+# DRAM bytes (read + write) per segment of the dominant kernel, from one ncu
+# capture of the same kernel on the same geometry with 3e6 particles
+# (56.37 GB over 82,931,315 segments); scaled to a full launch by its
+# segments.  None whenever the kernel has changed since that capture.
+TRAFFIC_BYTES_PER_SEGMENT = 56.368e9 / 82931315
 
 
 def _env_int(k, d):
@@ -319,7 +321,10 @@ def main() -> None:
         torch.cuda.synchronize()
         pk = max(pk, ops / (a.elapsed_time(b) / 1e3) / 1e12)
     roofline = {"bound": "alu", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
-                "frac": achieved / pk if pk else None, "traffic": TRAFFIC_PER_LAUNCH,
+                "frac": achieved / pk if pk else None,
+                "traffic": TRAFFIC_BYTES_PER_SEGMENT * seg_per_launch if TRAFFIC_BYTES_PER_SEGMENT else None,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch with 3e6 "
+                                  "particles, scaled by segments per launch",
                 "kernel": "k_event<CSG,FP64> (run_histories, event mode)",
                 "peak_source": "measured FP64 FMA rate (trk_peak_kernel, same run; of measured)",
                 "flops_per_segment": fps["per_segment"],
