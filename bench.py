@@ -38,12 +38,12 @@ PARTICLES = 10_000_000
 P_ABSORB = 0.25
 SEED = 1
 CPU_SAMPLE = 1_000_000
-EVENT_SLOTS = 256
+EVENT_SLOTS = 384
 # DRAM bytes (read + write) per segment of the dominant kernel, from one ncu
 # capture of the same kernel on the same geometry with 3e6 particles
 # (56.37 GB over 82,931,315 segments); scaled to a full launch by its
 # segments.  None whenever the kernel has changed since that capture.
-TRAFFIC_BYTES_PER_SEGMENT = 56.368e9 / 82931315
+TRAFFIC_BYTES_PER_SEGMENT = None
 
 
 def _env_int(k, d):

@@ -79,7 +79,7 @@ typedef struct {
     int precision;          /* TRK_FP64 or TRK_FP32_LOCAL */
     int block;              /* threads per block, 0 = default */
     int grid;               /* blocks, 0 = default (a multiple of the SM count) */
-    int queue_depth;        /* event mode: particle slots per warp (32..512), 0 = default 128 */
+    int queue_depth;        /* event mode: particle slots per warp (32..512), 0 = default 256 */
     int sort_interval;      /* event mode: regroup queues by cell every k rounds, 0 = never */
     int max_rounds;         /* event mode: round limit per warp, 0 = from max_segments; past it the
                                kernel stops and reports TRK_E_TIMEOUT in counters[TRK_K_STATUS] */

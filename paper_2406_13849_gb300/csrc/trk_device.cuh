@@ -226,22 +226,27 @@ __device__ __forceinline__ double surface_distance(const DevGeom& g, int s, int 
         const double qx = x - c0, qy = y - c1;
         const double a = d.u * d.u + d.v * d.v;
         const double b = qx * d.u + qy * d.v;
+        // every case is one quotient num / den, so lanes that take different
+        // cases still share one square root and one division
+        double num, den;
         if (on) {
-            if (side < 0 && d_lt0(b)) t = (-2.0 * b) / a;
+            if (side < 0 && d_lt0(b)) { num = -2.0 * b; den = a; }
             else return DINF;
         } else {
             const double c = (qx * qx + qy * qy) - c3;
             if (d_eq0(a)) return DINF;
             const double disc = b * b - a * c;
             if (d_le0(disc)) return DINF;
+            if (side > 0 && !d_lt0(b)) return DINF;
             const double sq = sqrt(disc);
             if (side < 0) {
-                t = d_le0(b) ? (-b + sq) / a : -c / (b + sq);
+                if (d_le0(b)) { num = -b + sq; den = a; }
+                else { num = -c; den = b + sq; }
             } else {
-                if (!d_lt0(b)) return DINF;
-                t = c / (-b + sq);
+                num = c; den = -b + sq;
             }
         }
+        t = num / den;
     }
     if (d_lt0(t)) t = 0.0;
     return t;
@@ -332,6 +337,39 @@ struct St {
     Lv lv[MAXL];
 };
 
+// Level access by a run-time level index.  The level stack stays in
+// registers (an indexed array would go to local memory); these select among
+// the MAXL entries, so a loop over levels can keep one copy of its body
+// instead of MAXL unrolled copies (the kernels' instruction footprint is
+// what the instruction caches see).
+static_assert(MAXL == 4, "level selects assume four levels");
+__device__ __forceinline__ Lv lv_get(const St& s, int l) {
+    Lv L = s.lv[0];
+    if (l == 1) L = s.lv[1];
+    if (l == 2) L = s.lv[2];
+    if (l == 3) L = s.lv[3];
+    return L;
+}
+__device__ __forceinline__ void lv_set(St& s, int l, const Lv& L) {
+    if (l == 0) s.lv[0] = L;
+    if (l == 1) s.lv[1] = L;
+    if (l == 2) s.lv[2] = L;
+    if (l == 3) s.lv[3] = L;
+}
+__device__ __forceinline__ void lv_set_u(St& s, int l, int u) {
+    if (l == 0) s.lv[0].u = u;
+    if (l == 1) s.lv[1].u = u;
+    if (l == 2) s.lv[2].u = u;
+    if (l == 3) s.lv[3].u = u;
+}
+__device__ __forceinline__ double sel4(int l, double a0, double a1, double a2, double a3) {
+    double v = a0;
+    if (l == 1) v = a1;
+    if (l == 2) v = a2;
+    if (l == 3) v = a3;
+    return v;
+}
+
 __device__ __forceinline__ void set_inverse(Dir& d) {
     d.iu = 1.0 / d.u;
     d.iv = 1.0 / d.v;
@@ -391,12 +429,12 @@ __device__ __forceinline__ int enter_cell(const DevGeom& g, Lv& L, int c) {
 // Returns 0 on success, -1 if no cell holds the point.
 template <bool CSG>
 __device__ __forceinline__ int find_from(const DevGeom& g, St& s, int start) {
+    if (start < 0 || start >= MAXL) return -1;
     double x, y, z;
     local_at(s, start, x, y, z);
-#pragma unroll
-    for (int l = 0; l < MAXL; ++l) {
-        if (l < start) continue;
-        Lv& L = s.lv[l];
+#pragma unroll 1
+    for (int l = start; l < MAXL; ++l) {
+        Lv L = lv_get(s, l);
         const int4 ui = __ldg(g.u_info + L.u);
         const Pt p = make_pt(x, y, z);
         int dau;
@@ -413,6 +451,7 @@ __device__ __forceinline__ int find_from(const DevGeom& g, St& s, int start) {
             if (c < 0) return -1;
             dau = enter_cell(g, L, c);
         }
+        lv_set(s, l, L);
         if (dau < 0) {
             s.nlev = l + 1;
             s.mat = ~dau;
@@ -420,7 +459,7 @@ __device__ __forceinline__ int find_from(const DevGeom& g, St& s, int start) {
         }
         if (l + 1 >= MAXL) return -1;
         x = x - L.tx; y = y - L.ty; z = z - L.tz;
-        s.lv[l + 1 < MAXL ? l + 1 : l].u = dau;
+        lv_set_u(s, l + 1, dau);
     }
     return -1;
 }
@@ -430,21 +469,45 @@ struct Hit {
     int level, surf, side, dim, dsign, entry;
 };
 
-// distance_to_surface over the levels, top to bottom, strict '<' (the
-// top-most level wins ties); rect levels: x, y, z faces in the direction of
-// flight, outer faces only at the root; CSG levels: the cell's surfaces in
-// cell order.
+// distance_to_surface over the levels (Table 1, Alg. 2): the smallest
+// distance wins; a tie goes to the top-most level, and within a level to the
+// first candidate in the level's order (rect levels: x, y, z faces in the
+// direction of flight, outer faces only at the root; CSG levels: the cell's
+// surfaces in cell order, which for a slab cell means the lower entry index).
+// The levels are scanned bottom-up, each level's winner replacing the running
+// best on a tie, which gives the same winner as a top-down scan with strict
+// '<'.  Scanning bottom-up lets an upper level skip a cylinder it is inside
+// of when the cylinder certainly lies beyond the running best: a ray from a
+// point at distance rho from the axis of a cylinder of radius r travels at
+// least r - rho >= (r^2 - rho^2) / (2 r) before reaching it.  The test keeps
+// a relative margin of 2^-40 over the rounding errors of c = rho^2 - r^2 and
+// of the distance formula (both a few ulp: inside a cylinder disc >= b^2), so
+// a skipped candidate is never the winner and the result is unchanged.
 template <bool CSG>
 __device__ __forceinline__ Hit distance_to_boundary(const DevGeom& g, const St& s) {
     Hit h;
     h.d = DINF; h.level = -1; h.surf = -1; h.side = 0; h.dim = -1; h.dsign = 0; h.entry = -1;
-    long long hk = okey(DINF);
-    double x = s.x, y = s.y, z = s.z;
+    const long long kinf = okey(DINF);
+    long long hk = kinf;
+    double lx[MAXL], ly[MAXL], lz[MAXL];
+    lx[0] = s.x; ly[0] = s.y; lz[0] = s.z;
 #pragma unroll
-    for (int l = 0; l < MAXL; ++l) {
-        if (l >= s.nlev) break;
-        if (l > 0) { x = x - s.lv[l - 1].tx; y = y - s.lv[l - 1].ty; z = z - s.lv[l - 1].tz; }
-        const Lv& L = s.lv[l];
+    for (int l = 1; l < MAXL; ++l) {
+        if (l < s.nlev) {
+            lx[l] = lx[l - 1] - s.lv[l - 1].tx; ly[l] = ly[l - 1] - s.lv[l - 1].ty; lz[l] = lz[l - 1] - s.lv[l - 1].tz;
+        } else {
+            lx[l] = lx[l - 1]; ly[l] = ly[l - 1]; lz[l] = lz[l - 1];
+        }
+    }
+#pragma unroll 1
+    for (int l = s.nlev - 1; l >= 0; --l) {
+        const double x = sel4(l, lx[0], lx[1], lx[2], lx[3]);
+        const double y = sel4(l, ly[0], ly[1], ly[2], ly[3]);
+        const double z = sel4(l, lz[0], lz[1], lz[2], lz[3]);
+        const Lv L = lv_get(s, l);
+        Hit c;
+        c.d = DINF; c.level = -1; c.surf = -1; c.side = 0; c.dim = -1; c.dsign = 0; c.entry = -1;
+        long long ck = kinf;
         const int4 ui = __ldg(g.u_info + L.u);
         if (!CSG && ui.w >= 0) {
             const int4 dm = __ldg(g.l_dim + ui.w), of = __ldg(g.l_off + ui.w);
@@ -466,19 +529,19 @@ __device__ __forceinline__ Hit distance_to_boundary(const DevGeom& g, const St& 
                 if (sg != 0) {
                     if (d_lt0(t)) t = 0.0;
                     const long long tk = okey(t);
-                    if (tk < hk) {
-                        hk = tk; h.d = t; h.level = l; h.surf = -1 - (2 * d + (sg > 0)); h.dim = d; h.dsign = sg; h.side = 0;
+                    if (tk < ck) {
+                        ck = tk; c.d = t; c.level = l; c.surf = -1 - (2 * d + (sg > 0)); c.dim = d; c.dsign = sg;
+                        c.side = 0; c.entry = -1;
                     }
                 }
             }
         } else {
-            // CSG cell: candidates are its faces in cell order, strict '<'.
             const int2 rg = __ldg(g.c_range + L.cell);
             if (rg.y & CS_SLAB_FLAG) {
                 // Cell bounded by axis planes only (a pseudo-array element):
                 // per dimension the one face the direction leaves through, as
-                // in the rect tracker; ties go to the lower entry index, which
-                // is the cell-order scan's result.
+                // in the rect tracker; a tie goes to the lower entry index,
+                // which is the cell-order scan's result.
                 const int4 s0 = __ldg(g.c_slab0 + L.cell), s1 = __ldg(g.c_slab1 + L.cell);
                 const int lo3[3] = {s0.x, s0.z, s1.x};
                 const int hi3[3] = {s0.y, s0.w, s1.y};
@@ -494,23 +557,36 @@ __device__ __forceinline__ Hit distance_to_boundary(const DevGeom& g, const St& 
                     double t = (__ldg(g.s_coef + 4 * sid) - p3[d]) * v3[d];
                     if (d_lt0(t)) t = 0.0;
                     const long long tk = okey(t);
-                    if (tk < hk || (tk == hk && h.level == l && e < h.entry)) {
-                        hk = tk; h.d = t; h.level = l; h.surf = sid; h.side = d_gt0(d3[d]) ? -1 : 1;
-                        h.dim = -1; h.dsign = 0; h.entry = e;
+                    if (tk < ck || (tk == ck && c.level >= 0 && e < c.entry)) {
+                        ck = tk; c.d = t; c.level = l; c.surf = sid; c.side = d_gt0(d3[d]) ? -1 : 1;
+                        c.dim = -1; c.dsign = 0; c.entry = e;
                     }
                 }
             } else {
                 const int cnt = rg.y & CS_COUNT_MASK;
                 for (int k = 0; k < cnt; ++k) {
                     const int e = __ldg(g.cs + rg.x + k);
-                    const int sid = cs_surface(e), side = cs_side(e);
+                    const int sid = cs_surface(e), side = cs_side(e), type = cs_type(e);
                     const bool on = (s.on_lev == l && s.on_surf == sid);
-                    const double t = surface_distance(g, sid, cs_type(e), side, on, x, y, z, s.d);
+                    if (type == S_CZ && side < 0 && !on && (hk != kinf || ck != kinf)) {
+                        const double bd = ck < hk ? c.d : h.d;
+                        double c0, c1, c2, c3;
+                        load_coef(g, sid, c0, c1, c2, c3);
+                        const double qx = x - c0, qy = y - c1;
+                        const double f = (qx * qx + qy * qy) - c3;
+                        if (d_lt0(f)) {
+                            const double tb = (c2 + c2) * bd;
+                            const double rhs = tb + (tb + c3) * 0x1p-40;
+                            if (okey(-f) > okey(rhs)) continue;
+                        }
+                    }
+                    const double t = surface_distance(g, sid, type, side, on, x, y, z, s.d);
                     const long long tk = okey(t);
-                    if (tk < hk) { hk = tk; h.d = t; h.level = l; h.surf = sid; h.side = side; h.dim = -1; h.dsign = 0; h.entry = rg.x + k; }
+                    if (tk < ck) { ck = tk; c.d = t; c.level = l; c.surf = sid; c.side = side; c.dim = -1; c.dsign = 0; c.entry = rg.x + k; }
                 }
             }
         }
+        if (c.level >= 0 && ck <= hk) { hk = ck; h = c; }
     }
     return h;
 }
@@ -718,53 +794,50 @@ __device__ __forceinline__ int csg_cross_search(const DevGeom& g, int u, int cel
 template <bool CSG>
 __device__ __forceinline__ int cross_surface(const DevGeom& g, St& s, const Hit& h, int& find_level) {
     find_level = -1;
-    int result = CR_LOST;
+    const int l = h.level;
+    if (l < 0 || l >= MAXL) return CR_LOST;
+    Lv L = lv_get(s, l);
+    const int4 ui = __ldg(g.u_info + L.u);
+    s.on_lev = l;
+    s.on_surf = h.surf;
+    int dau;
+    if (!CSG && ui.w >= 0) {
+        int ijk[3] = {L.i, L.j, L.k};
+        const int4 dm = __ldg(g.l_dim + ui.w);
+        const int n3[3] = {dm.x, dm.y, dm.z};
+        int ni = 0, nn = 1;
 #pragma unroll
-    for (int l = 0; l < MAXL; ++l) {
-        if (l != h.level) continue;
-        Lv& L = s.lv[l];
-        const int4 ui = __ldg(g.u_info + L.u);
-        s.on_lev = l;
-        s.on_surf = h.surf;
-        int dau;
-        if (!CSG && ui.w >= 0) {
-            int ijk[3] = {L.i, L.j, L.k};
-            const int4 dm = __ldg(g.l_dim + ui.w);
-            const int n3[3] = {dm.x, dm.y, dm.z};
-            int ni = 0, nn = 1;
-#pragma unroll
-            for (int d = 0; d < 3; ++d)
-                if (d == h.dim) { ijk[d] += h.dsign; ni = ijk[d]; nn = n3[d]; }
-            if (ni < 0 || ni >= nn) {
-                if (l != 0) return CR_LOST;
-                const int bc = (dm.w >> (2 * (2 * h.dim + (h.dsign > 0)))) & 3;
-                if (bc == BC_REFLECT) { reflect_plane(g, s, -1, h.dim); return CR_REFLECT; }
-                return CR_ESCAPE;
-            }
-            dau = enter_element(g, L, ui.w, ijk[0], ijk[1], ijk[2]);
-        } else {
-            double x, y, z;
-            local_at(s, l, x, y, z);
-            const Pt p = make_pt(x, y, z);
-            const int c = csg_cross_search(g, L.u, L.cell, p, h.surf, -h.side, h.entry);
-            if (c < 0) {
-                if (l != 0) return CR_LOST;
-                const int bc = (__ldg(g.s_info + h.surf) >> 4) & 3;
-                if (bc == BC_REFLECT) { reflect_plane(g, s, h.surf, -1); return CR_REFLECT; }
-                return CR_ESCAPE;
-            }
-            dau = enter_cell(g, L, c);
+        for (int d = 0; d < 3; ++d)
+            if (d == h.dim) { ijk[d] += h.dsign; ni = ijk[d]; nn = n3[d]; }
+        if (ni < 0 || ni >= nn) {
+            if (l != 0) return CR_LOST;
+            const int bc = (dm.w >> (2 * (2 * h.dim + (h.dsign > 0)))) & 3;
+            if (bc == BC_REFLECT) { reflect_plane(g, s, -1, h.dim); return CR_REFLECT; }
+            return CR_ESCAPE;
         }
-        if (dau < 0) {
-            s.nlev = l + 1;
-            s.mat = ~dau;
-            return CR_OK;
+        dau = enter_element(g, L, ui.w, ijk[0], ijk[1], ijk[2]);
+    } else {
+        double x, y, z;
+        local_at(s, l, x, y, z);
+        const Pt p = make_pt(x, y, z);
+        const int c = csg_cross_search(g, L.u, L.cell, p, h.surf, -h.side, h.entry);
+        if (c < 0) {
+            if (l != 0) return CR_LOST;
+            const int bc = (__ldg(g.s_info + h.surf) >> 4) & 3;
+            if (bc == BC_REFLECT) { reflect_plane(g, s, h.surf, -1); return CR_REFLECT; }
+            return CR_ESCAPE;
         }
-        if (l + 1 < MAXL) s.lv[l + 1 < MAXL ? l + 1 : l].u = dau;
-        find_level = l + 1;
-        result = CR_FIND;
+        dau = enter_cell(g, L, c);
     }
-    return result;
+    lv_set(s, l, L);
+    if (dau < 0) {
+        s.nlev = l + 1;
+        s.mat = ~dau;
+        return CR_OK;
+    }
+    if (l + 1 < MAXL) lv_set_u(s, l + 1, dau);
+    find_level = l + 1;
+    return CR_FIND;
 }
 
 // ---------------------------------------------------------------------------

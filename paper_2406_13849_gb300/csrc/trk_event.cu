@@ -4,7 +4,8 @@
 // vector of histories, one operation at a time) on top of Alg. 2-10.
 //
 // GB300 design.  Each warp owns `slots` particle slots whose state lives in
-// the caller's work buffer (structure of arrays, L2-resident) and keeps its
+// the caller's work buffer (one compact record per slot, 176 bytes for the
+// CSG tracker, sized to stay in L2) and keeps its
 // own queues of slot indices in shared memory: flight (distance_to_surface +
 // move_within_cell + tally), cross (cross_surface + find_cell below),
 // collide (change_direction), free.  A round runs refill, then flight over
@@ -32,10 +33,11 @@ constexpr int EV_BLOCK = 256;
 constexpr int EV_QUEUES = 4 + MAXL;   // flight, next flight, collide, free, cross per level
 
 // Minimum resident CTAs per SM the register allocation must allow (0: let
-// the compiler choose).  One CTA of 8 warps keeps the whole particle state in
-// registers; the compiler's own choice (two CTAs) spills it to local memory.
+// the compiler choose).  Two CTAs (16 warps, 128 registers a thread) hide
+// more latency than one CTA with the whole state in registers; the spills
+// this costs are a few dozen bytes in the rect and FP32 variants.
 #ifndef TRK_EV_MINB
-#define TRK_EV_MINB 1
+#define TRK_EV_MINB 2
 #endif
 #if TRK_EV_MINB > 0
 #define TRK_EV_BOUNDS __launch_bounds__(EV_BLOCK, TRK_EV_MINB)
@@ -43,88 +45,148 @@ constexpr int EV_QUEUES = 4 + MAXL;   // flight, next flight, collide, free, cro
 #define TRK_EV_BOUNDS __launch_bounds__(EV_BLOCK)
 #endif
 
-// slot state fields
-enum DField { D_X, D_Y, D_Z, D_U, D_V, D_W, D_IU, D_IV, D_IW, D_TAU, D_PATH, D_HD, D_T0, ND = D_T0 + 3 * MAXL };
-enum IField { I_NLEV, I_ONL, I_ONS, I_MAT, I_PIDX, I_EVENT, I_NSEG, I_STATUS, I_HLEV, I_HSURF, I_HSIDE, I_HDIM,
-              I_HSIGN, I_HENTRY, I_L0, NI = I_L0 + 6 * MAXL };
+// Slot record: one 16-byte-aligned record per slot, read and written in
+// 16-byte chunks (a lane's fields share sectors whatever order the queues
+// put the slots in).  Only what a history needs between operations is kept:
+// per level the universe and cell (rect levels also i, j, k); translations
+// and instance offsets are reloaded from the geometry tables.
+static_assert(MAXL == 4, "the slot record keeps one int4 per level field");
+constexpr int R_XY = 0,     // x, y
+              R_ZT = 16,    // z, tau
+              R_UV = 32,    // u, v
+              R_WI = 48,    // w, 1/u
+              R_II = 64,    // 1/v, 1/w
+              R_HP = 80,    // record hash, path length (only with records / path cutoff)
+              R_LV = 96,    // nlev, on_lev, on_surf, mat
+              R_CT = 112,   // particle index, event, segments, packed hit (level, side, dim, sign)
+              R_HT = 128,   // hit surface, hit entry
+              R_LU = 144,   // universe per level
+              R_LC = 160,   // cell (rect: element) per level
+              R_LI = 176, R_LJ = 192, R_LK = 208;   // rect levels: i, j, k
+template <bool CSG>
+__host__ __device__ constexpr int rec_bytes() { return CSG ? 176 : 224; }
 
 struct EvBuf {
-    double* dv;
-    int* iv;
-    unsigned long long* hash;
+    unsigned char* rec;
     unsigned long long* ctr;    // [0] next particle index
     long long T;                // total slots
-    __device__ __forceinline__ double& D(int f, int s) const { return dv[(long long)f * T + s]; }
-    __device__ __forceinline__ int& I(int f, int s) const { return iv[(long long)f * T + s]; }
 };
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-size_t buf_bytes(long long T) {
-    return 256 + align256(size_t(T) * ND * 8) + align256(size_t(T) * NI * 4) + align256(size_t(T) * 8);
-}
+size_t buf_bytes(long long T) { return 256 + align256(size_t(T) * size_t(rec_bytes<false>())); }
 
 EvBuf make_buf(void* work, long long T) {
     unsigned char* b = static_cast<unsigned char*>(work);
     EvBuf e;
     e.ctr = reinterpret_cast<unsigned long long*>(b);
-    size_t off = 256;
-    e.dv = reinterpret_cast<double*>(b + off);
-    off += align256(size_t(T) * ND * 8);
-    e.iv = reinterpret_cast<int*>(b + off);
-    off += align256(size_t(T) * NI * 4);
-    e.hash = reinterpret_cast<unsigned long long*>(b + off);
+    e.rec = b + 256;
     e.T = T;
     return e;
 }
 
-__device__ __forceinline__ void load_state(const EvBuf& B, int s, St& st) {
-    st.x = B.D(D_X, s); st.y = B.D(D_Y, s); st.z = B.D(D_Z, s);
-    st.d.u = B.D(D_U, s); st.d.v = B.D(D_V, s); st.d.w = B.D(D_W, s);
-    st.d.iu = B.D(D_IU, s); st.d.iv = B.D(D_IV, s); st.d.iw = B.D(D_IW, s);
-    st.tau = B.D(D_TAU, s);
-    st.nlev = B.I(I_NLEV, s); st.on_lev = B.I(I_ONL, s); st.on_surf = B.I(I_ONS, s); st.mat = B.I(I_MAT, s);
+template <bool CSG>
+__device__ __forceinline__ unsigned char* rec_at(const EvBuf& B, int s) {
+    return B.rec + (size_t)s * rec_bytes<CSG>();
+}
+__device__ __forceinline__ double2& D2(unsigned char* r, int off) { return *reinterpret_cast<double2*>(r + off); }
+__device__ __forceinline__ int4& I4(unsigned char* r, int off) { return *reinterpret_cast<int4*>(r + off); }
+__device__ __forceinline__ longlong2& L2(unsigned char* r, int off) { return *reinterpret_cast<longlong2*>(r + off); }
+
+__device__ __forceinline__ int pack_hit(const Hit& h) {
+    return (h.level + 1) | ((h.side + 1) << 3) | ((h.dim + 1) << 5) | ((h.dsign + 1) << 7);
+}
+__device__ __forceinline__ void unpack_hit(int p, Hit& h) {
+    h.level = (p & 7) - 1; h.side = ((p >> 3) & 3) - 1; h.dim = ((p >> 5) & 3) - 1; h.dsign = ((p >> 7) & 3) - 1;
+}
+
+// Translation and instance offset of every occupied level, from the tables
+// the find and cross steps take them from (the same values, bit for bit).
+template <bool CSG>
+__device__ __forceinline__ void reload_frames(const DevGeom& g, St& st) {
 #pragma unroll
     for (int l = 0; l < MAXL; ++l) {
         Lv& L = st.lv[l];
-        L.tx = B.D(D_T0 + 3 * l, s); L.ty = B.D(D_T0 + 3 * l + 1, s); L.tz = B.D(D_T0 + 3 * l + 2, s);
-        L.u = B.I(I_L0 + 6 * l, s); L.cell = B.I(I_L0 + 6 * l + 1, s); L.i = B.I(I_L0 + 6 * l + 2, s);
-        L.j = B.I(I_L0 + 6 * l + 3, s); L.k = B.I(I_L0 + 6 * l + 4, s); L.off = B.I(I_L0 + 6 * l + 5, s);
+        if (l >= st.nlev) { L.tx = L.ty = L.tz = 0.0; L.off = 0; continue; }
+        const int lat = CSG ? -1 : __ldg(g.u_info + L.u).w;
+        if (lat >= 0) {
+            const int4 of = __ldg(g.l_off + lat);
+            L.off = __ldg(g.l_eoff + of.w + L.cell);
+            L.tx = __ldg(g.l_ctr + of.x + L.i);
+            L.ty = __ldg(g.l_ctr + of.y + L.j);
+            L.tz = __ldg(g.l_ctr + of.z + L.k);
+        } else {
+            L.off = __ldg(g.c_off + L.cell);
+            L.tx = __ldg(g.c_tr + 3 * L.cell);
+            L.ty = __ldg(g.c_tr + 3 * L.cell + 1);
+            L.tz = __ldg(g.c_tr + 3 * L.cell + 2);
+        }
     }
 }
 
-__device__ __forceinline__ void store_levels(const EvBuf& B, int s, const St& st) {
-    B.I(I_NLEV, s) = st.nlev; B.I(I_ONL, s) = st.on_lev; B.I(I_ONS, s) = st.on_surf; B.I(I_MAT, s) = st.mat;
+template <bool CSG>
+__device__ __forceinline__ void load_levels(const DevGeom& g, unsigned char* r, St& st) {
+    const int4 lv = I4(r, R_LV);
+    st.nlev = lv.x; st.on_lev = lv.y; st.on_surf = lv.z; st.mat = lv.w;
+    const int4 lu = I4(r, R_LU), lc = I4(r, R_LC);
+    const int u4[4] = {lu.x, lu.y, lu.z, lu.w}, c4[4] = {lc.x, lc.y, lc.z, lc.w};
 #pragma unroll
-    for (int l = 0; l < MAXL; ++l) {
-        const Lv& L = st.lv[l];
-        B.D(D_T0 + 3 * l, s) = L.tx; B.D(D_T0 + 3 * l + 1, s) = L.ty; B.D(D_T0 + 3 * l + 2, s) = L.tz;
-        B.I(I_L0 + 6 * l, s) = L.u; B.I(I_L0 + 6 * l + 1, s) = L.cell; B.I(I_L0 + 6 * l + 2, s) = L.i;
-        B.I(I_L0 + 6 * l + 3, s) = L.j; B.I(I_L0 + 6 * l + 4, s) = L.k; B.I(I_L0 + 6 * l + 5, s) = L.off;
+    for (int l = 0; l < MAXL; ++l) { st.lv[l].u = u4[l]; st.lv[l].cell = c4[l]; st.lv[l].i = st.lv[l].j = st.lv[l].k = 0; }
+    if (!CSG) {
+        const int4 li = I4(r, R_LI), lj = I4(r, R_LJ), lk = I4(r, R_LK);
+        const int i4[4] = {li.x, li.y, li.z, li.w}, j4[4] = {lj.x, lj.y, lj.z, lj.w}, k4[4] = {lk.x, lk.y, lk.z, lk.w};
+#pragma unroll
+        for (int l = 0; l < MAXL; ++l) { st.lv[l].i = i4[l]; st.lv[l].j = j4[l]; st.lv[l].k = k4[l]; }
+    }
+    reload_frames<CSG>(g, st);
+}
+
+template <bool CSG>
+__device__ __forceinline__ void store_levels(unsigned char* r, const St& st) {
+    I4(r, R_LV) = make_int4(st.nlev, st.on_lev, st.on_surf, st.mat);
+    I4(r, R_LU) = make_int4(st.lv[0].u, st.lv[1].u, st.lv[2].u, st.lv[3].u);
+    I4(r, R_LC) = make_int4(st.lv[0].cell, st.lv[1].cell, st.lv[2].cell, st.lv[3].cell);
+    if (!CSG) {
+        I4(r, R_LI) = make_int4(st.lv[0].i, st.lv[1].i, st.lv[2].i, st.lv[3].i);
+        I4(r, R_LJ) = make_int4(st.lv[0].j, st.lv[1].j, st.lv[2].j, st.lv[3].j);
+        I4(r, R_LK) = make_int4(st.lv[0].k, st.lv[1].k, st.lv[2].k, st.lv[3].k);
     }
 }
 
-__device__ __forceinline__ void store_dir(const EvBuf& B, int s, const St& st) {
-    B.D(D_U, s) = st.d.u; B.D(D_V, s) = st.d.v; B.D(D_W, s) = st.d.w;
-    B.D(D_IU, s) = st.d.iu; B.D(D_IV, s) = st.d.iv; B.D(D_IW, s) = st.d.iw;
+__device__ __forceinline__ void load_dir(unsigned char* r, St& st) {
+    const double2 uv = D2(r, R_UV), wi = D2(r, R_WI), ii = D2(r, R_II);
+    st.d.u = uv.x; st.d.v = uv.y; st.d.w = wi.x; st.d.iu = wi.y; st.d.iv = ii.x; st.d.iw = ii.y;
 }
 
-__device__ __forceinline__ void load_ctx(const EvBuf& B, int s, Ctx& c, const RunP& rp) {
-    const int pidx = B.I(I_PIDX, s);
-    c.pid = uint32_t(rp.first_id + uint64_t(uint32_t(pidx)));
-    c.event = uint32_t(B.I(I_EVENT, s));
-    c.nseg = (long long)(uint32_t)B.I(I_NSEG, s);
-    c.path = B.D(D_PATH, s);
-    c.hash = B.hash[s];
-    c.status = B.I(I_STATUS, s);
+__device__ __forceinline__ void store_dir(unsigned char* r, const St& st) {
+    D2(r, R_UV) = make_double2(st.d.u, st.d.v);
+    D2(r, R_WI) = make_double2(st.d.w, st.d.iu);
+    D2(r, R_II) = make_double2(st.d.iv, st.d.iw);
 }
 
-__device__ __forceinline__ void store_ctx(const EvBuf& B, int s, const Ctx& c) {
-    B.I(I_EVENT, s) = int(c.event);
-    B.I(I_NSEG, s) = int(uint32_t(c.nseg));
-    B.D(D_PATH, s) = c.path;
-    B.hash[s] = c.hash;
-    B.I(I_STATUS, s) = c.status;
+// Context of a live history (status is 0 while it lives).  Returns the
+// particle's index in this launch.
+template <int FLAGS>
+__device__ __forceinline__ int load_ctx(unsigned char* r, Ctx& c, int& hpack, const RunP& rp) {
+    const int4 ct = I4(r, R_CT);
+    c.pid = uint32_t(rp.first_id + uint64_t(uint32_t(ct.x)));
+    c.event = uint32_t(ct.y);
+    c.nseg = (long long)(uint32_t)ct.z;
+    hpack = ct.w;
+    c.status = 0;
+    c.hash = 0; c.path = 0.0;
+    if (FLAGS & (F_REC | F_CUT)) {
+        const longlong2 hp = L2(r, R_HP);
+        c.hash = (uint64_t)hp.x;
+        c.path = __longlong_as_double(hp.y);
+    }
+    return ct.x;
+}
+
+template <int FLAGS>
+__device__ __forceinline__ void store_ctx(unsigned char* r, int pidx, const Ctx& c, int hpack) {
+    I4(r, R_CT) = make_int4(pidx, int(c.event), int(uint32_t(c.nseg)), hpack);
+    if (FLAGS & (F_REC | F_CUT)) L2(r, R_HP) = make_longlong2((long long)c.hash, __double_as_longlong(c.path));
 }
 
 // Warp-level append of `v` to `list` when `flag` (all 32 lanes call);
@@ -137,22 +199,21 @@ __device__ __forceinline__ void wpush(bool flag, int v, int* list, int& count) {
 }
 
 template <int FLAGS>
-__device__ __forceinline__ void finish(const EvBuf& B, int s, const Ctx& c, unsigned long long* rec) {
+__device__ __forceinline__ void finish(long long pidx, const Ctx& c, unsigned long long* rec) {
     if (FLAGS & F_REC) {
-        const long long pidx = (long long)(uint32_t)B.I(I_PIDX, s);
         rec[2 * pidx] = c.hash;
         rec[2 * pidx + 1] = (uint64_t(c.nseg) << 32) | uint32_t(c.status);
     }
 }
 
-// Each warp owns `slots` particle slots and its own five queues in shared
-// memory; warps never synchronise with each other.
+// Each warp owns `slots` particle slots and its own queues in shared memory;
+// warps never synchronise with each other.
 template <bool CSG, bool F32, int FLAGS>
 __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, long long n, const RunP rp,
-                                                    const EvBuf B, int slots, unsigned long long max_rounds,
-                                                    unsigned long long* __restrict__ tally,
-                                                    unsigned long long* __restrict__ counters,
-                                                    unsigned long long* __restrict__ rec) {
+                                      const EvBuf B, int slots, unsigned long long max_rounds,
+                                      unsigned long long* __restrict__ tally,
+                                      unsigned long long* __restrict__ counters,
+                                      unsigned long long* __restrict__ rec) {
     extern __shared__ int smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int* base_q = smem + warp * EV_QUEUES * slots;
@@ -192,7 +253,6 @@ __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, lo
                 Ctx c;
                 c.pid = uint32_t(rp.first_id + uint64_t(pidx));
                 c.event = 0; c.nseg = 0; c.path = 0.0; c.hash = FNV0; c.status = 0;
-                B.I(I_PIDX, slot) = int(pidx);
                 const int pst = P.status[pidx];
                 if (pst != 0) {
                     c.status = pst;
@@ -204,14 +264,16 @@ __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, lo
                         c.status = TRK_E_LOST;
                         cnt.k[TRK_K_LOST]++;
                     } else {
-                        B.D(D_X, slot) = s.x; B.D(D_Y, slot) = s.y; B.D(D_Z, slot) = s.z; B.D(D_TAU, slot) = s.tau;
-                        store_dir(B, slot, s);
-                        store_levels(B, slot, s);
+                        unsigned char* r = rec_at<CSG>(B, slot);
+                        D2(r, R_XY) = make_double2(s.x, s.y);
+                        D2(r, R_ZT) = make_double2(s.z, s.tau);
+                        store_dir(r, s);
+                        store_levels<CSG>(r, s);
+                        store_ctx<FLAGS>(r, int(pidx), c, 0);
                         ok = true;
                     }
                 }
-                store_ctx(B, slot, c);
-                if (!ok) finish<FLAGS>(B, slot, c, rec);
+                if (!ok) finish<FLAGS>(pidx, c, rec);
             }
             wpush(ok, slot, fly, n_fly);
             wpush(k < got && !ok, slot, next, n_park);
@@ -234,28 +296,37 @@ __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, lo
         for (int l = 0; l < MAXL; ++l) n_cross[l] = 0;
         for (int b = 0; b < n_fly; b += 32) {
             const int k = b + lane;
-            int a = A_DONE, slot = 0;
+            int a = A_DONE, slot = 0, hl = -1;
             if (k < n_fly) {
                 slot = fly[k];
+                unsigned char* r = rec_at<CSG>(B, slot);
                 St s;
-                load_state(B, slot, s);
+                const double2 xy = D2(r, R_XY), zt = D2(r, R_ZT);
+                s.x = xy.x; s.y = xy.y; s.z = zt.x; s.tau = zt.y;
+                load_dir(r, s);
+                load_levels<CSG>(g, r, s);
                 Ctx c;
-                load_ctx(B, slot, c, rp);
+                int hpack;
+                const int pidx = load_ctx<FLAGS>(r, c, hpack, rp);
                 Hit h;
                 a = step_fly<CSG, F32, FLAGS>(g, s, h, c, rp, tally, cnt, nullptr, nullptr, 0);
-                B.D(D_X, slot) = s.x; B.D(D_Y, slot) = s.y; B.D(D_Z, slot) = s.z; B.D(D_TAU, slot) = s.tau;
-                store_ctx(B, slot, c);
-                if (a == A_CROSS) {
-                    B.D(D_HD, slot) = h.d;
-                    B.I(I_HLEV, slot) = h.level; B.I(I_HSURF, slot) = h.surf; B.I(I_HSIDE, slot) = h.side;
-                    B.I(I_HDIM, slot) = h.dim; B.I(I_HSIGN, slot) = h.dsign; B.I(I_HENTRY, slot) = h.entry;
+                if (a == A_DONE) {
+                    finish<FLAGS>(pidx, c, rec);
+                } else {
+                    D2(r, R_XY) = make_double2(s.x, s.y);
+                    D2(r, R_ZT) = make_double2(s.z, s.tau);
+                    if (a == A_CROSS) {
+                        hl = h.level;
+                        store_ctx<FLAGS>(r, pidx, c, pack_hit(h));
+                        I4(r, R_HT) = make_int4(h.surf, h.entry, 0, 0);
+                    } else {
+                        store_ctx<FLAGS>(r, pidx, c, hpack);
+                    }
                 }
-                if (a == A_DONE) finish<FLAGS>(B, slot, c, rec);
             }
             const bool live = k < n_fly;
             // crossings are queued by level, so each pass runs one code path
             // (array index step, universe search, pin cell test)
-            const int hl = (a == A_CROSS) ? B.I(I_HLEV, slot) : -1;
 #pragma unroll
             for (int l = 0; l < MAXL; ++l) wpush(live && hl == l, slot, qx + l * slots, n_cross[l]);
             wpush(live && a == A_COLLIDE, slot, qc, n_coll);
@@ -271,19 +342,27 @@ __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, lo
             int a = A_DONE, slot = 0;
             if (k < n_cross[lq]) {
                 slot = qx[lq * slots + k];
+                unsigned char* r = rec_at<CSG>(B, slot);
                 St s;
-                load_state(B, slot, s);
+                const double2 xy = D2(r, R_XY), zt = D2(r, R_ZT);
+                s.x = xy.x; s.y = xy.y; s.z = zt.x; s.tau = zt.y;
+                load_dir(r, s);
+                load_levels<CSG>(g, r, s);
                 Ctx c;
-                load_ctx(B, slot, c, rp);
+                int hpack;
+                const int pidx = load_ctx<FLAGS>(r, c, hpack, rp);
                 Hit h;
-                h.d = B.D(D_HD, slot);
-                h.level = B.I(I_HLEV, slot); h.surf = B.I(I_HSURF, slot); h.side = B.I(I_HSIDE, slot);
-                h.dim = B.I(I_HDIM, slot); h.dsign = B.I(I_HSIGN, slot); h.entry = B.I(I_HENTRY, slot);
+                unpack_hit(hpack, h);
+                const int4 ht = I4(r, R_HT);
+                h.surf = ht.x; h.entry = ht.y; h.d = 0.0;
+                const unsigned refl0 = cnt.k[TRK_K_REFLECTIONS];
                 a = step_cross<CSG>(g, s, h, c, rp, cnt);
-                store_levels(B, slot, s);
-                store_dir(B, slot, s);
-                store_ctx(B, slot, c);
-                if (a == A_DONE) finish<FLAGS>(B, slot, c, rec);
+                if (a == A_DONE) {
+                    finish<FLAGS>(pidx, c, rec);
+                } else {
+                    store_levels<CSG>(r, s);
+                    if (cnt.k[TRK_K_REFLECTIONS] != refl0) store_dir(r, s);
+                }
             }
             const bool live = k < n_cross[lq];
             wpush(live && a == A_FLY, slot, next, n_next);
@@ -294,20 +373,22 @@ __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, lo
             int a = A_DONE, slot = 0;
             if (k < n_coll) {
                 slot = qc[k];
+                unsigned char* r = rec_at<CSG>(B, slot);
                 St s;
-                s.d.u = B.D(D_U, slot); s.d.v = B.D(D_V, slot); s.d.w = B.D(D_W, slot);
-                s.tau = B.D(D_TAU, slot);
                 Ctx c;
-                load_ctx(B, slot, c, rp);
+                int hpack;
+                const int pidx = load_ctx<FLAGS>(r, c, hpack, rp);
                 a = step_collide(g, s, c, rp, cnt);
-                if (a != A_DONE) {
-                    store_dir(B, slot, s);
-                    B.D(D_TAU, slot) = s.tau;
-                    B.I(I_ONL, slot) = -1;
-                    B.I(I_ONS, slot) = -1;
+                if (a == A_DONE) {
+                    finish<FLAGS>(pidx, c, rec);
+                } else {
+                    store_dir(r, s);
+                    const double z = D2(r, R_ZT).x;
+                    D2(r, R_ZT) = make_double2(z, s.tau);
+                    const int4 lv = I4(r, R_LV);
+                    I4(r, R_LV) = make_int4(lv.x, -1, -1, lv.w);
+                    store_ctx<FLAGS>(r, pidx, c, hpack);
                 }
-                store_ctx(B, slot, c);
-                if (a == A_DONE) finish<FLAGS>(B, slot, c, rec);
             }
             const bool live = k < n_coll;
             wpush(live && a == A_FLY, slot, next, n_next);
@@ -326,13 +407,20 @@ namespace trk {
 
 constexpr int EV_WARPS = EV_BLOCK / 32;
 
+// Resident CTAs per SM: the register budget's minimum (TRK_EV_MINB), capped
+// by shared memory.  Deterministic, so the work-buffer size a caller queries
+// always matches the launch.
 int event_grid(int slots) {
-    int dev = 0, sms = 152;
-    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int per_sm = 1;
+    int dev = 0, sms = 152, smem_sm = 228 * 1024;
+    if (cudaGetDevice(&dev) == cudaSuccess) {
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    }
     const size_t smem = size_t(EV_QUEUES) * slots * EV_WARPS * sizeof(int);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_event<true, false, 0>, EV_BLOCK, smem) != cudaSuccess || per_sm < 1)
-        per_sm = 1;
+    const int by_smem = int(size_t(smem_sm) / (smem + 1024));
+    int per_sm = TRK_EV_MINB > 0 ? TRK_EV_MINB : 1;
+    if (per_sm > by_smem) per_sm = by_smem;
+    if (per_sm < 1) per_sm = 1;
     return sms * per_sm;
 }
 
@@ -344,6 +432,8 @@ trk_status launch_event(trk_geom_t g, const ParticlesView& P, long long n, const
     const long long T = (long long)slots * EV_WARPS * grid;
     if (work_bytes < buf_bytes(T) || !work)
         return trk_status(set_error(TRK_E_NOMEM, "run_histories (event): work buffer needs %zu bytes", buf_bytes(T)));
+    if ((reinterpret_cast<uintptr_t>(work) & 255) != 0)
+        return trk_status(set_error(TRK_E_INVALID, "run_histories (event): work buffer must be 256-byte aligned"));
     const EvBuf B = make_buf(work, T);
     cudaError_t e = cudaMemsetAsync(B.ctr, 0, 8, s);
     if (e != cudaSuccess) return trk_status(set_error(TRK_E_CUDA, "run_histories (event): %s", cudaGetErrorString(e)));

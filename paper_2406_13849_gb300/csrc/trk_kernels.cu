@@ -29,9 +29,10 @@ using namespace trk;
 using namespace trk::dev;
 
 // Minimum resident 128-thread CTAs per SM the history kernel's register
-// allocation must allow (0: let the compiler choose).
+// allocation must allow (0: let the compiler choose).  Four CTAs (128
+// registers a thread) beat the compiler's own choice of ~170 registers.
 #ifndef TRK_HIST_MINB
-#define TRK_HIST_MINB 0
+#define TRK_HIST_MINB 4
 #endif
 #if TRK_HIST_MINB > 0
 #define TRK_HIST_BOUNDS __launch_bounds__(128, TRK_HIST_MINB)
@@ -450,7 +451,7 @@ trk_status source_init(trk_geom_t g, int64_t n, uint64_t first_id, uint64_t seed
     return launch_error("source_init");
 }
 
-constexpr int DEFAULT_SLOTS = 128;
+constexpr int DEFAULT_SLOTS = 256;
 
 int event_slots(const trk_run_opts& o) { return o.queue_depth > 0 ? o.queue_depth : DEFAULT_SLOTS; }
 
