@@ -876,7 +876,8 @@ int build_host(const char* json, size_t len, Built& B) {
     }
     std::vector<float> c_slabf;
     std::vector<int2> c_range, cs_adj;
-    std::vector<int4> c_slab0, c_slab1;
+    std::vector<int4> c_slab0, c_slab1, c_slabs;
+    std::vector<longlong2> c_slabk;
     std::vector<int> cs, c_fill, c_off;
     std::vector<double> c_tr;
     std::vector<int4> u_info;
@@ -932,6 +933,17 @@ int build_host(const char* json, size_t len, Built& B) {
             }
             c_slab0.push_back(make_int4(slab[0], slab[1], slab[2], slab[3]));
             c_slab1.push_back(make_int4(slab[4], slab[5], 0, 0));
+            int sid6[6];
+            for (int k = 0; k < 6; ++k) sid6[k] = slab[k] >= 0 ? c.surf[size_t(slab[k] - first_entry)] : -1;
+            for (int d = 0; d < 3; ++d) {
+                const int lo = sid6[2 * d], hi = sid6[2 * d + 1];
+                longlong2 kk;
+                kk.x = lo >= 0 ? okey(G.surf[size_t(lo)].c[0]) : std::numeric_limits<long long>::min();
+                kk.y = hi >= 0 ? okey(G.surf[size_t(hi)].c[0]) : std::numeric_limits<long long>::max();
+                c_slabk.push_back(kk);
+            }
+            c_slabs.push_back(make_int4(sid6[0], sid6[1], sid6[2], sid6[3]));
+            c_slabs.push_back(make_int4(sid6[4], sid6[5], -1, -1));
             c_fill.push_back(c.fill);
             c_off.push_back(int(c.off));
             for (int d = 0; d < 3; ++d) c_tr.push_back(c.tr[d]);
@@ -1010,6 +1022,9 @@ int build_host(const char* json, size_t len, Built& B) {
     o[24] = L.put(l_lof.size() * 4);
     o[25] = L.put(l_hif.size() * 4);
     o[26] = L.put(c_slabf.size() * 4);
+    if (c_slabk.empty()) { c_slabk.push_back(longlong2{0, 0}); c_slabs.push_back(make_int4(-1, -1, -1, -1)); }
+    o[27] = L.put(c_slabk.size() * sizeof(longlong2));
+    o[28] = L.put(c_slabs.size() * sizeof(int4));
     B.image.assign(L.total, 0);
     copy_into(B.image, o[0], s_info);
     copy_into(B.image, o[1], s_coef);
@@ -1038,6 +1053,8 @@ int build_host(const char* json, size_t len, Built& B) {
     copy_into(B.image, o[24], l_lof);
     copy_into(B.image, o[25], l_hif);
     copy_into(B.image, o[26], c_slabf);
+    copy_into(B.image, o[27], c_slabk);
+    copy_into(B.image, o[28], c_slabs);
     return TRK_OK;
 }
 
@@ -1117,6 +1134,8 @@ trk_status geometry_build(const char* json, size_t len, void* dev_buf, size_t* d
     d.l_lof = reinterpret_cast<const float*>(base + o[24]);
     d.l_hif = reinterpret_cast<const float*>(base + o[25]);
     d.c_slabf = reinterpret_cast<const float*>(base + o[26]);
+    d.c_slabk = reinterpret_cast<const longlong2*>(base + o[27]);
+    d.c_slabs = reinterpret_cast<const int4*>(base + o[28]);
     const HGeom& G = B.G;
     for (int k = 0; k < 3; ++k) { d.src_lo[k] = G.src[k]; d.src_hi[k] = G.src[3 + k]; }
     d.root = G.root;

@@ -256,6 +256,25 @@ __device__ __forceinline__ double surface_distance(const DevGeom& g, int s, int 
 // logically with sense xsn instead of being evaluated.
 __device__ __forceinline__ bool cell_holds(const DevGeom& g, int c, const Pt& p, int xs, int xsn) {
     const int2 rg = __ldg(g.c_range + c);
+    if (rg.y & CS_SLAB_FLAG) {
+        // axis planes only: per dimension x >= g_lo ("+" side of the lower
+        // face) and x < g_hi ("-" side of the upper face), as order-key
+        // compares; the same conjunction as the entry loop below
+        const longlong2* K = g.c_slabk + 3 * c;
+        const longlong2 kx = __ldg(K), ky = __ldg(K + 1), kz = __ldg(K + 2);
+        const int4 s0 = __ldg(g.c_slabs + 2 * c), s1 = __ldg(g.c_slabs + 2 * c + 1);
+        const long long lo3[3] = {kx.x, ky.x, kz.x}, hi3[3] = {kx.y, ky.y, kz.y};
+        const int ls3[3] = {s0.x, s0.z, s1.x}, hs3[3] = {s0.y, s0.w, s1.y};
+        const long long kp3[3] = {p.kx, p.ky, p.kz};
+        bool ok = true;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const bool lo_ok = (ls3[d] >= 0 && ls3[d] == xs) ? (xsn > 0) : (kp3[d] >= lo3[d]);
+            const bool hi_ok = (hs3[d] >= 0 && hs3[d] == xs) ? (xsn < 0) : (kp3[d] < hi3[d]);
+            ok = ok && lo_ok && hi_ok;
+        }
+        return ok;
+    }
     const int cnt = rg.y & CS_COUNT_MASK;
     for (int k = 0; k < cnt; ++k) {
         const int e = __ldg(g.cs + rg.x + k);
@@ -685,10 +704,9 @@ __device__ __forceinline__ Best2 distance_f32(const DevGeom& g, const St& s, con
     double x = s.x, y = s.y, z = s.z;
     const float d3[3] = {df.u, df.v, df.w};
     const float v3[3] = {df.iu, df.iv, df.iw};
-#pragma unroll
-    for (int l = 0; l < MAXL; ++l) {
-        if (l >= s.nlev) break;
-        const Lv& L = s.lv[l];
+#pragma unroll 1
+    for (int l = 0; l < s.nlev; ++l) {
+        const Lv L = lv_get(s, l);
         // the next level's frame is this level's element frame: one FP64
         // subtraction chain serves both
         const double xn = x - L.tx, yn = y - L.ty, zn = z - L.tz;

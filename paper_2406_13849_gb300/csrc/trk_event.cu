@@ -191,10 +191,14 @@ __device__ __forceinline__ void store_ctx(unsigned char* r, int pidx, const Ctx&
 
 // Warp-level append of `v` to `list` when `flag` (all 32 lanes call);
 // `count` is warp-uniform and advanced in every lane.
-__device__ __forceinline__ void wpush(bool flag, int v, int* list, int& count) {
+// Queue entries are slot indices within the warp's own range (< 512), 16 bits
+// each: half the shared memory of 32-bit entries, which the L1 cache gets.
+using QIdx = unsigned short;
+
+__device__ __forceinline__ void wpush(bool flag, int v, QIdx* list, int& count) {
     const unsigned m = __ballot_sync(0xffffffffu, flag);
     const int lane = threadIdx.x & 31;
-    if (flag) list[count + __popc(m & ((1u << lane) - 1u))] = v;
+    if (flag) list[count + __popc(m & ((1u << lane) - 1u))] = QIdx(v);
     count += __popc(m);
 }
 
@@ -214,19 +218,19 @@ __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, lo
                                       unsigned long long* __restrict__ tally,
                                       unsigned long long* __restrict__ counters,
                                       unsigned long long* __restrict__ rec) {
-    extern __shared__ int smem[];
+    extern __shared__ QIdx smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int* base_q = smem + warp * EV_QUEUES * slots;
-    int* fly = base_q;
-    int* next = base_q + slots;
-    int* qc = base_q + 2 * slots;
-    int* qf = base_q + 3 * slots;
-    int* qx = base_q + 4 * slots;      // MAXL cross queues, one per crossing level
+    QIdx* base_q = smem + warp * EV_QUEUES * slots;
+    QIdx* fly = base_q;
+    QIdx* next = base_q + slots;
+    QIdx* qc = base_q + 2 * slots;
+    QIdx* qf = base_q + 3 * slots;
+    QIdx* qx = base_q + 4 * slots;      // MAXL cross queues, one per crossing level
     const int slot0 = (blockIdx.x * (EV_BLOCK / 32) + warp) * slots;
     Counts cnt;
 #pragma unroll
     for (int k = 0; k < NCOUNT; ++k) cnt.k[k] = 0;
-    for (int k = lane; k < slots; k += 32) qf[k] = slot0 + k;
+    for (int k = lane; k < slots; k += 32) qf[k] = QIdx(k);
     int n_fly = 0, n_free = slots;
     bool exhausted = false;
     __syncwarp();
@@ -248,7 +252,7 @@ __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, lo
             bool ok = false;
             int slot = 0;
             if (k < got) {
-                slot = qf[n_free - got + k];
+                slot = slot0 + qf[n_free - got + k];
                 const long long pidx = (long long)first + k;
                 Ctx c;
                 c.pid = uint32_t(rp.first_id + uint64_t(pidx));
@@ -275,8 +279,8 @@ __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, lo
                 }
                 if (!ok) finish<FLAGS>(pidx, c, rec);
             }
-            wpush(ok, slot, fly, n_fly);
-            wpush(k < got && !ok, slot, next, n_park);
+            wpush(ok, slot - slot0, fly, n_fly);
+            wpush(k < got && !ok, slot - slot0, next, n_park);
         }
         __syncwarp();
         n_free -= got;
@@ -298,7 +302,7 @@ __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, lo
             const int k = b + lane;
             int a = A_DONE, slot = 0, hl = -1;
             if (k < n_fly) {
-                slot = fly[k];
+                slot = slot0 + fly[k];
                 unsigned char* r = rec_at<CSG>(B, slot);
                 St s;
                 const double2 xy = D2(r, R_XY), zt = D2(r, R_ZT);
@@ -328,9 +332,9 @@ __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, lo
             // crossings are queued by level, so each pass runs one code path
             // (array index step, universe search, pin cell test)
 #pragma unroll
-            for (int l = 0; l < MAXL; ++l) wpush(live && hl == l, slot, qx + l * slots, n_cross[l]);
-            wpush(live && a == A_COLLIDE, slot, qc, n_coll);
-            wpush(live && a == A_DONE, slot, qf, n_free);
+            for (int l = 0; l < MAXL; ++l) wpush(live && hl == l, slot - slot0, qx + l * slots, n_cross[l]);
+            wpush(live && a == A_COLLIDE, slot - slot0, qc, n_coll);
+            wpush(live && a == A_DONE, slot - slot0, qf, n_free);
         }
         __syncwarp();
         // ---- cross_surface, then change_direction ---------------------------
@@ -341,7 +345,7 @@ __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, lo
             const int k = b + lane;
             int a = A_DONE, slot = 0;
             if (k < n_cross[lq]) {
-                slot = qx[lq * slots + k];
+                slot = slot0 + qx[lq * slots + k];
                 unsigned char* r = rec_at<CSG>(B, slot);
                 St s;
                 const double2 xy = D2(r, R_XY), zt = D2(r, R_ZT);
@@ -365,14 +369,14 @@ __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, lo
                 }
             }
             const bool live = k < n_cross[lq];
-            wpush(live && a == A_FLY, slot, next, n_next);
-            wpush(live && a == A_DONE, slot, qf, n_free);
+            wpush(live && a == A_FLY, slot - slot0, next, n_next);
+            wpush(live && a == A_DONE, slot - slot0, qf, n_free);
         }
         for (int b = 0; b < n_coll; b += 32) {
             const int k = b + lane;
             int a = A_DONE, slot = 0;
             if (k < n_coll) {
-                slot = qc[k];
+                slot = slot0 + qc[k];
                 unsigned char* r = rec_at<CSG>(B, slot);
                 St s;
                 Ctx c;
@@ -391,11 +395,11 @@ __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, lo
                 }
             }
             const bool live = k < n_coll;
-            wpush(live && a == A_FLY, slot, next, n_next);
-            wpush(live && a == A_DONE, slot, qf, n_free);
+            wpush(live && a == A_FLY, slot - slot0, next, n_next);
+            wpush(live && a == A_DONE, slot - slot0, qf, n_free);
         }
         __syncwarp();
-        int* t = fly; fly = next; next = t;
+        QIdx* t = fly; fly = next; next = t;
         n_fly = n_next;
     }
     flush_counts(cnt, counters);
@@ -416,7 +420,7 @@ int event_grid(int slots) {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     }
-    const size_t smem = size_t(EV_QUEUES) * slots * EV_WARPS * sizeof(int);
+    const size_t smem = size_t(EV_QUEUES) * slots * EV_WARPS * sizeof(QIdx);
     const int by_smem = int(size_t(smem_sm) / (smem + 1024));
     int per_sm = TRK_EV_MINB > 0 ? TRK_EV_MINB : 1;
     if (per_sm > by_smem) per_sm = by_smem;
@@ -437,7 +441,7 @@ trk_status launch_event(trk_geom_t g, const ParticlesView& P, long long n, const
     const EvBuf B = make_buf(work, T);
     cudaError_t e = cudaMemsetAsync(B.ctr, 0, 8, s);
     if (e != cudaSuccess) return trk_status(set_error(TRK_E_CUDA, "run_histories (event): %s", cudaGetErrorString(e)));
-    const size_t smem = size_t(EV_QUEUES) * slots * EV_WARPS * sizeof(int);
+    const size_t smem = size_t(EV_QUEUES) * slots * EV_WARPS * sizeof(QIdx);
     // a particle needs at most max_segments + 1 flight rounds; a warp holds
     // `slots` particles at a time and refills every round
     const unsigned long long per_warp = (unsigned long long)(n / (T / slots) + slots + 1);

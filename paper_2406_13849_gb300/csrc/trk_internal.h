@@ -67,6 +67,10 @@ struct DevGeom {
     const int4* c_slab0;      // slab view of cells bounded by axis planes only: entry index of
                               // the lower / upper face on x, y (lo_x, hi_x, lo_y, hi_y), -1 absent
     const int4* c_slab1;      // (lo_z, hi_z, -, -)
+    const longlong2* c_slabk; // slab cells, 3 per cell: order keys of the (lower, upper) face per
+                              // dimension, LLONG_MIN / LLONG_MAX where absent (containment test)
+    const int4* c_slabs;      // slab cells, 2 per cell: surface ids (lo_x, hi_x, lo_y, hi_y),
+                              // (lo_z, hi_z, -1, -1); -1 absent
     const int* c_fill;        // >= 0 daughter universe; < 0 material ~fill
     const double* c_tr;       // translation into the daughter, 3 per cell
     const int* c_off;         // leaf-instance offset of the cell
