@@ -38,7 +38,7 @@ PARTICLES = 10_000_000
 P_ABSORB = 0.25
 SEED = 1
 CPU_SAMPLE = 1_000_000
-EVENT_SLOTS = 384
+EVENT_SLOTS = 512
 # DRAM bytes (read + write) per segment of the dominant kernel, from one ncu
 # capture of the same kernel on the same geometry with 3e6 particles
 # (56.37 GB over 82,931,315 segments); scaled to a full launch by its

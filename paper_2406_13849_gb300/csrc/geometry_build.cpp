@@ -792,7 +792,7 @@ void copy_into(std::vector<unsigned char>& img, size_t off, const std::vector<T>
 
 struct Built {
     std::vector<unsigned char> image;
-    size_t offs[32] = {};
+    size_t offs[40] = {};
     HGeom G;
     int n_nodes = 0;
 };
@@ -878,7 +878,8 @@ int build_host(const char* json, size_t len, Built& B) {
     std::vector<int2> c_range, cs_adj;
     std::vector<int4> c_slab0, c_slab1, c_slabs;
     std::vector<longlong2> c_slabk;
-    std::vector<int> cs, c_fill, c_off;
+    std::vector<int> cs, c_fill, c_off, c_fcls, rest_e;
+    std::vector<int2> c_rest;
     std::vector<double> c_tr;
     std::vector<int4> u_info;
     for (auto& U : G.univ) {
@@ -914,19 +915,32 @@ int build_host(const char* json, size_t len, Built& B) {
                 if (cand.size() > 2) cs_adj.push_back(make_int2(-2, -2));
                 else cs_adj.push_back(make_int2(cand.size() > 0 ? cand[0] : -1, cand.size() > 1 ? cand[1] : -1));
             }
-            // slab view for cells bounded by axis planes only, at most one
-            // lower and one upper plane per dimension
+            // slab view: at most one lower and one upper axis plane per
+            // dimension; the other surfaces (cylinders, general planes) are
+            // listed as the cell's remaining entries
             int slab[6] = {-1, -1, -1, -1, -1, -1};
-            bool pure = true;
+            bool fits = true;
             const int first_entry = c_range.back().x;
+            std::vector<int> rest;
             for (size_t i = 0; i < c.surf.size(); ++i) {
                 const int type = G.surf[size_t(c.surf[i])].type;
+                if (type > S_PZ) { rest.push_back(first_entry + int(i)); continue; }
                 const int slot = 2 * type + (c.sense[i] > 0 ? 0 : 1);
-                if (type > S_PZ || slab[slot] >= 0) { pure = false; break; }
+                if (slab[slot] >= 0) { fits = false; break; }
                 slab[slot] = first_entry + int(i);
             }
-            if (!pure) for (int k = 0; k < 6; ++k) slab[k] = -1;
-            else c_range.back().y |= CS_SLAB_FLAG;
+            // a cell with no axis plane at all (a pin cell bounded by
+            // cylinders) keeps the plain entry loop
+            if (rest.size() == c.surf.size()) fits = false;
+            if (!fits) {
+                for (int k = 0; k < 6; ++k) slab[k] = -1;
+                rest.clear();
+                c_rest.push_back(make_int2(int(rest_e.size()), 0));
+            } else {
+                c_range.back().y |= CS_SLAB_FLAG;
+                c_rest.push_back(make_int2(int(rest_e.size()), int(rest.size())));
+                rest_e.insert(rest_e.end(), rest.begin(), rest.end());
+            }
             for (int k = 0; k < 6; ++k) {
                 const int e = slab[k];
                 c_slabf.push_back(e >= 0 ? float(G.surf[size_t(c.surf[size_t(e - first_entry)])].c[0] - c.tr[k / 2]) : 0.f);
@@ -944,6 +958,18 @@ int build_host(const char* json, size_t len, Built& B) {
             }
             c_slabs.push_back(make_int4(sid6[0], sid6[1], sid6[2], sid6[3]));
             c_slabs.push_back(make_int4(sid6[4], sid6[5], -1, -1));
+            {
+                int curved = 0, general = 0, cyl_side = 0;
+                for (size_t i = 0; i < c.surf.size(); ++i) {
+                    const int type = G.surf[size_t(c.surf[i])].type;
+                    if (type == S_CZ) { ++curved; cyl_side = c.sense[i]; }
+                    else if (type == S_P) ++general;
+                }
+                int cls = 3;
+                if (general == 0 && curved == 0) cls = 0;
+                else if (general == 0 && curved == 1) cls = cyl_side < 0 ? 1 : 2;
+                c_fcls.push_back(cls);
+            }
             c_fill.push_back(c.fill);
             c_off.push_back(int(c.off));
             for (int d = 0; d < 3; ++d) c_tr.push_back(c.tr[d]);
@@ -1025,6 +1051,12 @@ int build_host(const char* json, size_t len, Built& B) {
     if (c_slabk.empty()) { c_slabk.push_back(longlong2{0, 0}); c_slabs.push_back(make_int4(-1, -1, -1, -1)); }
     o[27] = L.put(c_slabk.size() * sizeof(longlong2));
     o[28] = L.put(c_slabs.size() * sizeof(int4));
+    if (c_fcls.empty()) c_fcls.push_back(0);
+    o[29] = L.put(c_fcls.size() * 4);
+    if (c_rest.empty()) c_rest.push_back(make_int2(0, 0));
+    if (rest_e.empty()) rest_e.push_back(0);
+    o[30] = L.put(c_rest.size() * sizeof(int2));
+    o[31] = L.put(rest_e.size() * 4);
     B.image.assign(L.total, 0);
     copy_into(B.image, o[0], s_info);
     copy_into(B.image, o[1], s_coef);
@@ -1055,6 +1087,9 @@ int build_host(const char* json, size_t len, Built& B) {
     copy_into(B.image, o[26], c_slabf);
     copy_into(B.image, o[27], c_slabk);
     copy_into(B.image, o[28], c_slabs);
+    copy_into(B.image, o[29], c_fcls);
+    copy_into(B.image, o[30], c_rest);
+    copy_into(B.image, o[31], rest_e);
     return TRK_OK;
 }
 
@@ -1136,6 +1171,9 @@ trk_status geometry_build(const char* json, size_t len, void* dev_buf, size_t* d
     d.c_slabf = reinterpret_cast<const float*>(base + o[26]);
     d.c_slabk = reinterpret_cast<const longlong2*>(base + o[27]);
     d.c_slabs = reinterpret_cast<const int4*>(base + o[28]);
+    d.c_fcls = reinterpret_cast<const int*>(base + o[29]);
+    d.c_rest = reinterpret_cast<const int2*>(base + o[30]);
+    d.rest_e = reinterpret_cast<const int*>(base + o[31]);
     const HGeom& G = B.G;
     for (int k = 0; k < 3; ++k) { d.src_lo[k] = G.src[k]; d.src_hi[k] = G.src[3 + k]; }
     d.root = G.root;

@@ -257,9 +257,9 @@ __device__ __forceinline__ double surface_distance(const DevGeom& g, int s, int 
 __device__ __forceinline__ bool cell_holds(const DevGeom& g, int c, const Pt& p, int xs, int xsn) {
     const int2 rg = __ldg(g.c_range + c);
     if (rg.y & CS_SLAB_FLAG) {
-        // axis planes only: per dimension x >= g_lo ("+" side of the lower
-        // face) and x < g_hi ("-" side of the upper face), as order-key
-        // compares; the same conjunction as the entry loop below
+        // slab view: per dimension x >= g_lo ("+" side of the lower face) and
+        // x < g_hi ("-" side of the upper face), as order-key compares, then
+        // the remaining entries; the same conjunction as the entry loop below
         const longlong2* K = g.c_slabk + 3 * c;
         const longlong2 kx = __ldg(K), ky = __ldg(K + 1), kz = __ldg(K + 2);
         const int4 s0 = __ldg(g.c_slabs + 2 * c), s1 = __ldg(g.c_slabs + 2 * c + 1);
@@ -273,7 +273,18 @@ __device__ __forceinline__ bool cell_holds(const DevGeom& g, int c, const Pt& p,
             const bool hi_ok = (hs3[d] >= 0 && hs3[d] == xs) ? (xsn < 0) : (kp3[d] < hi3[d]);
             ok = ok && lo_ok && hi_ok;
         }
-        return ok;
+        if (!ok) return false;
+        const int2 rr = __ldg(g.c_rest + c);
+        for (int k = 0; k < rr.y; ++k) {
+            const int e = __ldg(g.cs + __ldg(g.rest_e + rr.x + k));
+            const int sf = cs_surface(e), sn = cs_side(e);
+            if (sf == xs) {
+                if (sn != xsn) return false;
+            } else if (sense_at(g, sf, cs_type(e), p) != sn) {
+                return false;
+            }
+        }
+        return true;
     }
     const int cnt = rg.y & CS_COUNT_MASK;
     for (int k = 0; k < cnt; ++k) {
@@ -518,8 +529,12 @@ __device__ __forceinline__ Hit distance_to_boundary(const DevGeom& g, const St& 
             lx[l] = lx[l - 1]; ly[l] = ly[l - 1]; lz[l] = lz[l - 1];
         }
     }
+    // the loop runs over all MAXL levels so that the lanes of a warp stay
+    // on the same level (a lane with fewer levels idles through the deeper
+    // ones) instead of each starting at its own deepest level
 #pragma unroll 1
-    for (int l = s.nlev - 1; l >= 0; --l) {
+    for (int l = MAXL - 1; l >= 0; --l) {
+        if (l >= s.nlev) continue;
         const double x = sel4(l, lx[0], lx[1], lx[2], lx[3]);
         const double y = sel4(l, ly[0], ly[1], ly[2], ly[3]);
         const double z = sel4(l, lz[0], lz[1], lz[2], lz[3]);
@@ -556,11 +571,14 @@ __device__ __forceinline__ Hit distance_to_boundary(const DevGeom& g, const St& 
             }
         } else {
             const int2 rg = __ldg(g.c_range + L.cell);
+            int first = rg.x, cnt = rg.y & CS_COUNT_MASK;
+            const int* ents = g.cs;
+            bool by_index = false;
             if (rg.y & CS_SLAB_FLAG) {
-                // Cell bounded by axis planes only (a pseudo-array element):
-                // per dimension the one face the direction leaves through, as
-                // in the rect tracker; a tie goes to the lower entry index,
-                // which is the cell-order scan's result.
+                // Slab view: per dimension the one axis face the direction
+                // leaves through, as in the rect tracker; then the cell's other
+                // surfaces.  Ties go to the lower entry index, which is the
+                // cell-order scan's result.
                 const int4 s0 = __ldg(g.c_slab0 + L.cell), s1 = __ldg(g.c_slab1 + L.cell);
                 const int lo3[3] = {s0.x, s0.z, s1.x};
                 const int hi3[3] = {s0.y, s0.w, s1.y};
@@ -581,27 +599,31 @@ __device__ __forceinline__ Hit distance_to_boundary(const DevGeom& g, const St& 
                         c.dim = -1; c.dsign = 0; c.entry = e;
                     }
                 }
-            } else {
-                const int cnt = rg.y & CS_COUNT_MASK;
-                for (int k = 0; k < cnt; ++k) {
-                    const int e = __ldg(g.cs + rg.x + k);
-                    const int sid = cs_surface(e), side = cs_side(e), type = cs_type(e);
-                    const bool on = (s.on_lev == l && s.on_surf == sid);
-                    if (type == S_CZ && side < 0 && !on && (hk != kinf || ck != kinf)) {
-                        const double bd = ck < hk ? c.d : h.d;
-                        double c0, c1, c2, c3;
-                        load_coef(g, sid, c0, c1, c2, c3);
-                        const double qx = x - c0, qy = y - c1;
-                        const double f = (qx * qx + qy * qy) - c3;
-                        if (d_lt0(f)) {
-                            const double tb = (c2 + c2) * bd;
-                            const double rhs = tb + (tb + c3) * 0x1p-40;
-                            if (okey(-f) > okey(rhs)) continue;
-                        }
+                const int2 rr = __ldg(g.c_rest + L.cell);
+                first = rr.x; cnt = rr.y; ents = g.rest_e; by_index = true;
+            }
+            // remaining entries (all of them for a cell without a slab view)
+            for (int k = 0; k < cnt; ++k) {
+                const int ei = by_index ? __ldg(ents + first + k) : first + k;
+                const int e = __ldg(g.cs + ei);
+                const int sid = cs_surface(e), side = cs_side(e), type = cs_type(e);
+                const bool on = (s.on_lev == l && s.on_surf == sid);
+                if (type == S_CZ && side < 0 && !on && (hk != kinf || ck != kinf)) {
+                    const double bd = ck < hk ? c.d : h.d;
+                    double c0, c1, c2, c3;
+                    load_coef(g, sid, c0, c1, c2, c3);
+                    const double qx = x - c0, qy = y - c1;
+                    const double f = (qx * qx + qy * qy) - c3;
+                    if (d_lt0(f)) {
+                        const double tb = (c2 + c2) * bd;
+                        const double rhs = tb + (tb + c3) * 0x1p-40;
+                        if (okey(-f) > okey(rhs)) continue;
                     }
-                    const double t = surface_distance(g, sid, type, side, on, x, y, z, s.d);
-                    const long long tk = okey(t);
-                    if (tk < ck) { ck = tk; c.d = t; c.level = l; c.surf = sid; c.side = side; c.dim = -1; c.dsign = 0; c.entry = rg.x + k; }
+                }
+                const double t = surface_distance(g, sid, type, side, on, x, y, z, s.d);
+                const long long tk = okey(t);
+                if (tk < ck || (tk == ck && c.level >= 0 && ei < c.entry)) {
+                    ck = tk; c.d = t; c.level = l; c.surf = sid; c.side = side; c.dim = -1; c.dsign = 0; c.entry = ei;
                 }
             }
         }
@@ -733,6 +755,8 @@ __device__ __forceinline__ Best2 distance_f32(const DevGeom& g, const St& s, con
             }
         } else {
             const int2 rg = __ldg(g.c_range + L.cell);
+            int first = rg.x, cnt = rg.y & CS_COUNT_MASK;
+            bool by_index = false;
             if (rg.y & CS_SLAB_FLAG) {
                 const int4 s0 = __ldg(g.c_slab0 + L.cell), s1 = __ldg(g.c_slab1 + L.cell);
                 const int lo3[3] = {s0.x, s0.z, s1.x};
@@ -749,15 +773,18 @@ __device__ __forceinline__ Best2 distance_f32(const DevGeom& g, const St& s, con
                     const float t = (__ldg(fs + 2 * d + (up ? 1 : 0)) - e3[d]) * v3[d];
                     b.offer(t < 0.f ? 0.f : t, l, sid, up ? -1 : 1, -1, 0, e, x, y, z);
                 }
-            } else {
+                const int2 rr = __ldg(g.c_rest + L.cell);
+                first = rr.x; cnt = rr.y; by_index = true;
+            }
+            if (cnt > 0) {
                 const float xf = float(x), yf = float(y), zf = float(z);
-                const int cnt = rg.y & CS_COUNT_MASK;
                 for (int k = 0; k < cnt; ++k) {
-                    const int e = __ldg(g.cs + rg.x + k);
+                    const int ei = by_index ? __ldg(g.rest_e + first + k) : first + k;
+                    const int e = __ldg(g.cs + ei);
                     const int sid = cs_surface(e), side = cs_side(e);
                     const bool on = (s.on_lev == l && s.on_surf == sid);
                     const float t = surface_distance_f(g, sid, cs_type(e), side, on, xf, yf, zf, df, b.ill);
-                    b.offer(t, l, sid, side, -1, 0, rg.x + k, x, y, z);
+                    b.offer(t, l, sid, side, -1, 0, ei, x, y, z);
                 }
             }
         }

@@ -30,7 +30,22 @@ using namespace trk::dev;
 namespace {
 
 constexpr int EV_BLOCK = 256;
-constexpr int EV_QUEUES = 4 + MAXL;   // flight, next flight, collide, free, cross per level
+// Flight queues by the class of the particle's leaf cell (cells whose
+// distance code takes the same path: no curved surface, one cylinder from
+// inside, one from outside, other), so a flight batch's lanes mostly run the
+// same branches; the classes are concatenated in one pass, so a partial batch
+// occurs only once per flight phase.  Measured on the three-level core, the
+// sorting does not pay for its extra queue traffic (4 classes: -2 to -5%), so
+// the default is one class.
+#ifndef TRK_EV_NFC
+#define TRK_EV_NFC 1
+#endif
+constexpr int NFC = TRK_EV_NFC;
+// Free slots a warp collects before it refills them (see the refill step).
+#ifndef TRK_EV_REFILL_MIN
+#define TRK_EV_REFILL_MIN 32
+#endif
+constexpr int EV_QUEUES = NFC + 2 + MAXL;   // flight by class, collide, free, cross per level
 
 // Minimum resident CTAs per SM the register allocation must allow (0: let
 // the compiler choose).  Two CTAs (16 warps, 128 registers a thread) hide
@@ -57,7 +72,7 @@ constexpr int R_XY = 0,     // x, y
               R_WI = 48,    // w, 1/u
               R_II = 64,    // 1/v, 1/w
               R_HP = 80,    // record hash, path length (only with records / path cutoff)
-              R_LV = 96,    // nlev, on_lev, on_surf, mat
+              R_LV = 96,    // nlev | flight class << 16, on_lev, on_surf, mat
               R_CT = 112,   // particle index, event, segments, packed hit (level, side, dim, sign)
               R_HT = 128,   // hit surface, hit entry
               R_LU = 144,   // universe per level
@@ -127,7 +142,7 @@ __device__ __forceinline__ void reload_frames(const DevGeom& g, St& st) {
 template <bool CSG>
 __device__ __forceinline__ void load_levels(const DevGeom& g, unsigned char* r, St& st) {
     const int4 lv = I4(r, R_LV);
-    st.nlev = lv.x; st.on_lev = lv.y; st.on_surf = lv.z; st.mat = lv.w;
+    st.nlev = lv.x & 0xffff; st.on_lev = lv.y; st.on_surf = lv.z; st.mat = lv.w;
     const int4 lu = I4(r, R_LU), lc = I4(r, R_LC);
     const int u4[4] = {lu.x, lu.y, lu.z, lu.w}, c4[4] = {lc.x, lc.y, lc.z, lc.w};
 #pragma unroll
@@ -141,9 +156,20 @@ __device__ __forceinline__ void load_levels(const DevGeom& g, unsigned char* r, 
     reload_frames<CSG>(g, st);
 }
 
+// Flight class of the particle's leaf cell (a rect-array leaf is class 0).
 template <bool CSG>
-__device__ __forceinline__ void store_levels(unsigned char* r, const St& st) {
-    I4(r, R_LV) = make_int4(st.nlev, st.on_lev, st.on_surf, st.mat);
+__device__ __forceinline__ int flight_class(const DevGeom& g, const St& st) {
+    if (NFC == 1) return 0;
+    const Lv L = lv_get(st, st.nlev - 1);
+    if (!CSG && __ldg(g.u_info + L.u).w >= 0) return 0;
+    const int c = __ldg(g.c_fcls + L.cell);
+    return c < NFC ? c : NFC - 1;
+}
+
+// The level fields; the flight class rides in the upper half of nlev's word.
+template <bool CSG>
+__device__ __forceinline__ void store_levels(unsigned char* r, const St& st, int cls) {
+    I4(r, R_LV) = make_int4(st.nlev | (cls << 16), st.on_lev, st.on_surf, st.mat);
     I4(r, R_LU) = make_int4(st.lv[0].u, st.lv[1].u, st.lv[2].u, st.lv[3].u);
     I4(r, R_LC) = make_int4(st.lv[0].cell, st.lv[1].cell, st.lv[2].cell, st.lv[3].cell);
     if (!CSG) {
@@ -221,24 +247,32 @@ __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, lo
     extern __shared__ QIdx smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     QIdx* base_q = smem + warp * EV_QUEUES * slots;
-    QIdx* fly = base_q;
-    QIdx* next = base_q + slots;
-    QIdx* qc = base_q + 2 * slots;
-    QIdx* qf = base_q + 3 * slots;
-    QIdx* qx = base_q + 4 * slots;      // MAXL cross queues, one per crossing level
+    QIdx* qfl = base_q;                  // NFC flight queues
+    QIdx* qc = base_q + NFC * slots;     // collide (at refill: failed births)
+    QIdx* qf = base_q + (NFC + 1) * slots;
+    QIdx* qx = base_q + (NFC + 2) * slots;   // MAXL cross queues, one per crossing level
     const int slot0 = (blockIdx.x * (EV_BLOCK / 32) + warp) * slots;
     Counts cnt;
 #pragma unroll
     for (int k = 0; k < NCOUNT; ++k) cnt.k[k] = 0;
     for (int k = lane; k < slots; k += 32) qf[k] = QIdx(k);
-    int n_fly = 0, n_free = slots;
+    int n_fl[NFC];
+#pragma unroll
+    for (int c = 0; c < NFC; ++c) n_fl[c] = 0;
+    int n_free = slots;
     bool exhausted = false;
     __syncwarp();
     for (unsigned long long round = 0;; ++round) {
         // ---- refill free slots with new particles --------------------------
+        // in batches of at least a warp's width (birth runs the universe
+        // searches from the root, whose lanes diverge least when the batch
+        // is full), unless the flight queues are running low
+        int n_live = 0;
+#pragma unroll
+        for (int q = 0; q < NFC; ++q) n_live += n_fl[q];
         int got = 0;
         unsigned long long first = 0;
-        if (!exhausted && n_free > 0) {
+        if (!exhausted && n_free > 0 && (n_free >= TRK_EV_REFILL_MIN || n_live < 32)) {
             if (lane == 0) first = atomicAdd(B.ctr, (unsigned long long)n_free);
             first = __shfl_sync(0xffffffffu, first, 0);
             long long avail = (long long)n - (long long)first;
@@ -250,7 +284,7 @@ __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, lo
         for (int b = 0; b < got; b += 32) {
             const int k = b + lane;
             bool ok = false;
-            int slot = 0;
+            int slot = 0, cls = 0;
             if (k < got) {
                 slot = slot0 + qf[n_free - got + k];
                 const long long pidx = (long long)first + k;
@@ -269,32 +303,38 @@ __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, lo
                         cnt.k[TRK_K_LOST]++;
                     } else {
                         unsigned char* r = rec_at<CSG>(B, slot);
+                        cls = flight_class<CSG>(g, s);
                         D2(r, R_XY) = make_double2(s.x, s.y);
                         D2(r, R_ZT) = make_double2(s.z, s.tau);
                         store_dir(r, s);
-                        store_levels<CSG>(r, s);
+                        store_levels<CSG>(r, s, cls);
                         store_ctx<FLAGS>(r, int(pidx), c, 0);
                         ok = true;
                     }
                 }
                 if (!ok) finish<FLAGS>(pidx, c, rec);
             }
-            wpush(ok, slot - slot0, fly, n_fly);
-            wpush(k < got && !ok, slot - slot0, next, n_park);
+#pragma unroll
+            for (int q = 0; q < NFC; ++q) wpush(ok && cls == q, slot - slot0, qfl + q * slots, n_fl[q]);
+            wpush(k < got && !ok, slot - slot0, qc, n_park);
         }
         __syncwarp();
         n_free -= got;
         for (int b = 0; b < n_park; b += 32) {
             const int k = b + lane;
-            wpush(k < n_park, k < n_park ? next[k] : 0, qf, n_free);
+            wpush(k < n_park, k < n_park ? qc[k] : 0, qf, n_free);
         }
         __syncwarp();
+        int n_fly = 0;
+#pragma unroll
+        for (int q = 0; q < NFC; ++q) n_fly += n_fl[q];
         if (n_fly == 0 && exhausted) break;
         if (round >= max_rounds) {
             if (lane == 0) kernel_status(counters, TRK_E_TIMEOUT);
             break;
         }
         // ---- flight: distance_to_surface, tally, move ----------------------
+        // the class queues are walked as one concatenated list
         int n_cross[MAXL], n_coll = 0;
 #pragma unroll
         for (int l = 0; l < MAXL; ++l) n_cross[l] = 0;
@@ -302,7 +342,11 @@ __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, lo
             const int k = b + lane;
             int a = A_DONE, slot = 0, hl = -1;
             if (k < n_fly) {
-                slot = slot0 + fly[k];
+                int q = 0, kk = k;
+#pragma unroll
+                for (int c = 0; c < NFC - 1; ++c)
+                    if (q == c && kk >= n_fl[c]) { kk -= n_fl[c]; q = c + 1; }
+                slot = slot0 + qfl[q * slots + kk];
                 unsigned char* r = rec_at<CSG>(B, slot);
                 St s;
                 const double2 xy = D2(r, R_XY), zt = D2(r, R_ZT);
@@ -337,13 +381,14 @@ __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, lo
             wpush(live && a == A_DONE, slot - slot0, qf, n_free);
         }
         __syncwarp();
+#pragma unroll
+        for (int q = 0; q < NFC; ++q) n_fl[q] = 0;
         // ---- cross_surface, then change_direction ---------------------------
-        int n_next = 0;
 #pragma unroll 1
         for (int lq = 0; lq < MAXL; ++lq)
         for (int b = 0; b < n_cross[lq]; b += 32) {
             const int k = b + lane;
-            int a = A_DONE, slot = 0;
+            int a = A_DONE, slot = 0, cls = 0;
             if (k < n_cross[lq]) {
                 slot = slot0 + qx[lq * slots + k];
                 unsigned char* r = rec_at<CSG>(B, slot);
@@ -364,17 +409,19 @@ __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, lo
                 if (a == A_DONE) {
                     finish<FLAGS>(pidx, c, rec);
                 } else {
-                    store_levels<CSG>(r, s);
+                    cls = flight_class<CSG>(g, s);
+                    store_levels<CSG>(r, s, cls);
                     if (cnt.k[TRK_K_REFLECTIONS] != refl0) store_dir(r, s);
                 }
             }
             const bool live = k < n_cross[lq];
-            wpush(live && a == A_FLY, slot - slot0, next, n_next);
+#pragma unroll
+            for (int q = 0; q < NFC; ++q) wpush(live && a == A_FLY && cls == q, slot - slot0, qfl + q * slots, n_fl[q]);
             wpush(live && a == A_DONE, slot - slot0, qf, n_free);
         }
         for (int b = 0; b < n_coll; b += 32) {
             const int k = b + lane;
-            int a = A_DONE, slot = 0;
+            int a = A_DONE, slot = 0, cls = 0;
             if (k < n_coll) {
                 slot = slot0 + qc[k];
                 unsigned char* r = rec_at<CSG>(B, slot);
@@ -390,17 +437,17 @@ __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, lo
                     const double z = D2(r, R_ZT).x;
                     D2(r, R_ZT) = make_double2(z, s.tau);
                     const int4 lv = I4(r, R_LV);
+                    cls = lv.x >> 16;
                     I4(r, R_LV) = make_int4(lv.x, -1, -1, lv.w);
                     store_ctx<FLAGS>(r, pidx, c, hpack);
                 }
             }
             const bool live = k < n_coll;
-            wpush(live && a == A_FLY, slot - slot0, next, n_next);
+#pragma unroll
+            for (int q = 0; q < NFC; ++q) wpush(live && a == A_FLY && cls == q, slot - slot0, qfl + q * slots, n_fl[q]);
             wpush(live && a == A_DONE, slot - slot0, qf, n_free);
         }
         __syncwarp();
-        QIdx* t = fly; fly = next; next = t;
-        n_fly = n_next;
     }
     flush_counts(cnt, counters);
 }

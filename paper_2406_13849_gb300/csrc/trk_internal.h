@@ -44,8 +44,9 @@ struct alignas(16) SkipNode {
     int leaf;
 };
 
-// c_range count field: low bits count, CS_SLAB_FLAG marks a cell bounded
-// by axis planes only, at most one lower and one upper per dimension.
+// c_range count field: low bits count, CS_SLAB_FLAG marks a cell with a
+// slab view: at most one lower and one upper axis plane per dimension (its
+// other surfaces are the cell's remaining entries, c_rest / rest_e).
 constexpr int CS_SLAB_FLAG = 1 << 30;
 constexpr int CS_COUNT_MASK = CS_SLAB_FLAG - 1;
 
@@ -64,7 +65,7 @@ struct DevGeom {
     const int* cs;            // packed cell-surface entries (see cs_surface / cs_type / cs_side)
     const int2* cs_adj;       // per entry: up to two cells on the far side of that face, -1 none,
                               // (-2,-2) too many (search the BVH directly)
-    const int4* c_slab0;      // slab view of cells bounded by axis planes only: entry index of
+    const int4* c_slab0;      // slab view (CS_SLAB_FLAG cells): entry index of
                               // the lower / upper face on x, y (lo_x, hi_x, lo_y, hi_y), -1 absent
     const int4* c_slab1;      // (lo_z, hi_z, -, -)
     const longlong2* c_slabk; // slab cells, 3 per cell: order keys of the (lower, upper) face per
@@ -72,6 +73,12 @@ struct DevGeom {
     const int4* c_slabs;      // slab cells, 2 per cell: surface ids (lo_x, hi_x, lo_y, hi_y),
                               // (lo_z, hi_z, -1, -1); -1 absent
     const int* c_fill;        // >= 0 daughter universe; < 0 material ~fill
+    const int2* c_rest;       // slab-view cells: (first, count) into rest_e, the entries that are
+                              // not axis planes, in cell order
+    const int* rest_e;
+    const int* c_fcls;        // flight class of the cell as a leaf: 0 axis planes only, 1 one
+                              // cylinder (inside) and axis planes, 2 one cylinder (outside) and
+                              // axis planes, 3 anything else
     const double* c_tr;       // translation into the daughter, 3 per cell
     const int* c_off;         // leaf-instance offset of the cell
     // universes

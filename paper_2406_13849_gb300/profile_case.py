@@ -32,7 +32,7 @@ def main() -> None:
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--particles", type=int, default=3_000_000)
     ap.add_argument("--launches", type=int, default=1)
-    ap.add_argument("--queue-depth", type=int, default=384)
+    ap.add_argument("--queue-depth", type=int, default=512)
     args = ap.parse_args()
     dev = torch.device("cuda", 0)
     g = N.Geometry(I.to_json(I.config2()), device=dev)
