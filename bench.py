@@ -37,13 +37,14 @@ WORKLOAD = "core_15x15_assemblies_17x17_pins_r170_h366_4mat_pabs0.25"
 PARTICLES = 10_000_000
 P_ABSORB = 0.25
 SEED = 1
-CPU_SAMPLE = 1_000_000
+CPU_SAMPLE = 4_000_000
+CPU_SAMPLE_ONE_CORE = 200_000
 EVENT_SLOTS = 512
 # DRAM bytes (read + write) per segment of the dominant kernel, from one ncu
 # capture of the same kernel on the same geometry with 3e6 particles
-# (56.37 GB over 82,931,315 segments); scaled to a full launch by its
+# (37.58 GB over 82,931,315 segments); scaled to a full launch by its
 # segments.  None whenever the kernel has changed since that capture.
-TRAFFIC_BYTES_PER_SEGMENT = None
+TRAFFIC_BYTES_PER_SEGMENT = 37.577e9 / 82931315
 
 
 def _env_int(k, d):
@@ -114,7 +115,8 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU oracle baseline (bounded sample)
 # ---------------------------------------------------------------------------
-def cpu_baseline(desc_json: str, n: int, first_id: int = 0) -> dict:
+def cpu_baseline(desc_json: str, n: int, n_one: int, first_id: int = 0) -> dict:
+    """The oracle on all host cores (n particles) and on one core (n_one)."""
     import oracle as O
     g = O.Geometry(desc_json, O.MODE_CSG)
     cores = host_cores()
@@ -122,9 +124,15 @@ def cpu_baseline(desc_json: str, n: int, first_id: int = 0) -> dict:
     r = g.run(n, SEED, P_ABSORB, first_id=first_id, threads=cores, records=False)
     dt = time.perf_counter() - t0
     seg = int(r["counters"][O.K_SEGMENTS])
+    t0 = time.perf_counter()
+    r1 = g.run(n_one, SEED, P_ABSORB, first_id=first_id, threads=1, records=False)
+    dt1 = time.perf_counter() - t0
+    seg1 = int(r1["counters"][O.K_SEGMENTS])
     return {"value": seg / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "one_core": seg1 / dt1,
             "sample": f"{n} particles (ids {first_id}..{first_id + n - 1}) of the same workload, CSG-mode "
-                      f"oracle, {seg} segments in {dt:.2f} s"}
+                      f"oracle, {seg} segments in {dt:.2f} s on {cores} threads; one core: {n_one} particles, "
+                      f"{seg1} segments in {dt1:.2f} s"}
 
 
 def flops_per_segment(desc_json: str) -> dict:
@@ -331,9 +339,14 @@ def main() -> None:
                 "flops_definition": "FP64 add/sub, mul, div, sqrt per segment counted by the oracle's counting "
                                     "build in rect-tracker mode on this workload"}
 
+    # ---- configuration 1 size sweep and the transmission workload ----------
+    sweep = run_config1_sweep(N, I, dev, stream, barrier)
+    trans = run_config5(N, I, dev, stream, barrier, k2)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(desc, CPU_SAMPLE)
+        cpu = cpu_baseline(desc, CPU_SAMPLE, CPU_SAMPLE_ONE_CORE)
+        cpu["gpu_core_equivalents"] = value / cpu["one_core"]
 
     if rank == 0:
         line = {
@@ -363,6 +376,8 @@ def main() -> None:
                 "event_kernel_ms": kern_ms,
             },
             "batched": batch,
+            "config1_sweep": sweep,
+            "transmission": trans,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -444,6 +459,79 @@ def run_config4(N, I, dev, stream, barrier, rank, steps):
             "batched_fp64_segments_per_s": seg_b64 / (ms_b64 / 1e3),
             "autotuned": {"block": opts32.block, "chunk": chunk},
             "launches_per_pass": {"batched": 1, "loop": len(geoms)}}
+
+
+def run_config1_sweep(N, I, dev, stream, barrier):
+    """One 17x17 pin lattice in a reflecting box (absorption 0.3): segments/s
+    of the rect and BVH-CSG trackers (event kernel) from 1e4 to 1e8 particles,
+    and the history kernel at the small sizes, where the event kernel's
+    persistent grid is mostly idle."""
+    import numpy as np
+    import torch
+    g = N.Geometry(I.to_json(I.config1()), device=dev)
+    rows = []
+    for n in (10_000, 100_000, 1_000_000, 10_000_000, 100_000_000):
+        parts = torch.empty(g.particle_bytes(n), dtype=torch.uint8, device=dev)
+        g.source_init(n, seed=SEED, out=parts)
+        tally = torch.zeros(g.n_inst, dtype=torch.int64, device=dev)
+        cnt = torch.zeros(N.NCOUNTERS, dtype=torch.int64, device=dev)
+        row = {"particles": n}
+        modes = [("event", N.MODE_EVENT)] + ([("history", N.MODE_HISTORY)] if n <= 1_000_000 else [])
+        for mname, mode in modes:
+            for tname, tr in (("rect", N.TRACKER_RECT), ("csg", N.TRACKER_CSG)):
+                opts = N.default_opts(tracker=tr, mode=mode, seed=SEED, p_absorb=0.3, queue_depth=EVENT_SLOTS)
+                wb = g.work_bytes(n, opts)
+                work = torch.empty(wb + 256, dtype=torch.uint8, device=dev) if wb else None
+                g.run_histories(parts, n, tally=tally, counters=cnt, opts=opts, work=work)
+                reps = 1 if n >= 10_000_000 else 3
+                cnt.zero_()
+                barrier()
+                a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                for _ in range(reps):
+                    g.run_histories(parts, n, tally=tally, counters=cnt, opts=opts, work=work)
+                e.record(stream)
+                barrier()
+                seg = int(cnt.cpu().numpy().view(np.uint64)[0])
+                row[f"{tname}_{mname}"] = seg / (a.elapsed_time(e) / 1e3)
+                del work
+            row[f"csg_over_rect_{mname}"] = row[f"csg_{mname}"] / row[f"rect_{mname}"]
+        rows.append(row)
+        del parts
+    return {"workload": "17x17 pins (pitch 1.26, radii 0.41/0.475) in a reflecting box 21.42 x 21.42 x 100, "
+                        "3 materials, absorption 0.3", "unit": UNIT, "rows": rows}
+
+
+def run_config5(N, I, dev, stream, barrier, steps):
+    """Transmission of 2^20 boundary rays through the three-level core:
+    forward (T per ray) and backward (gradients with respect to the four
+    cross sections and the radii and pitch) times."""
+    import torch
+    desc, rays = I.config5()
+    g = N.Geometry(I.to_json(desc), device=dev)
+    R = torch.from_numpy(rays.packed()).to(dev)
+    sigma = torch.tensor(desc["sigma"], dtype=torch.float64, device=dev)
+    gT = torch.ones(R.shape[0], dtype=torch.float64, device=dev)
+    pitch = 1.26
+    for _ in range(2):
+        T, _ = g.transmission_fwd(R, sigma, lens=False)
+        g.transmission_bwd(R, sigma, pitch, gT)
+    barrier()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    fwd = bwd = 0.0
+    for _ in range(steps):
+        ev[0].record(stream)
+        T, _ = g.transmission_fwd(R, sigma, lens=False)
+        ev[1].record(stream)
+        g.transmission_bwd(R, sigma, pitch, gT)
+        ev[2].record(stream)
+        barrier()
+        fwd += ev[0].elapsed_time(ev[1])
+        bwd += ev[1].elapsed_time(ev[2])
+    n = R.shape[0]
+    return {"workload": "2^20 inward rays on the r=170, h=366 boundary of the three-level core",
+            "rays": n, "fwd_ms": fwd / steps, "bwd_ms": bwd / steps,
+            "rays_per_s_fwd_bwd": n / ((fwd + bwd) / steps / 1e3)}
 
 
 if __name__ == "__main__":
