@@ -386,8 +386,9 @@ def main() -> None:
 
 def run_config4(N, I, dev, stream, barrier, rank, steps):
     """64 geometries (3x3..17x17 rect/hex, 2-3 levels, 1e4..1e6 particles):
-    one autotuned persistent launch, FP32-local, replayed from a CUDA graph,
-    against the plain FP64 history kernel launched once per geometry."""
+    the batched event kernel (warp queues over chunks of one geometry at a
+    time), FP32-local, autotuned and replayed from a CUDA graph, against the
+    plain FP64 history kernel launched once per geometry."""
     import numpy as np
     import torch
     members = I.config4()
@@ -395,70 +396,66 @@ def run_config4(N, I, dev, stream, barrier, rank, steps):
     counts = [c for _, c in members]
     parts = [g.source_init(c, seed=SEED) for g, c in zip(geoms, counts)]
     b = N.Batch(geoms, parts, counts)
-    opts32 = N.default_opts(seed=SEED, p_absorb=P_ABSORB, precision=N.FP32_LOCAL)
-    opts32, chunk, _ = b.autotune(opts32, reps=2)
-    s = torch.cuda.Stream(device=dev)
-    s.wait_stream(torch.cuda.current_stream())
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph, stream=s):
-        b.run(opts32)
-    graph.replay()
-    torch.cuda.synchronize()
-    b.zero()
-    barrier()
-    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    for _ in range(steps):
+
+    def graph_rate(opts):
+        s = torch.cuda.Stream(device=dev)
+        s.wait_stream(torch.cuda.current_stream())
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=s):
+            b.run(opts)
         graph.replay()
-    e.record(stream)
-    barrier()
-    ms_b = a.elapsed_time(e)
-    seg_b = int(b.counters.cpu().numpy().view(np.uint64).reshape(-1, 16)[:, 0].sum())
+        torch.cuda.synchronize()
+        b.zero()
+        barrier()
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            graph.replay()
+        e.record(stream)
+        barrier()
+        seg = int(b.counters.cpu().numpy().view(np.uint64).reshape(-1, 16)[:, 0].sum())
+        return seg / (a.elapsed_time(e) / 1e3)
+
+    ev32 = N.default_opts(seed=SEED, p_absorb=P_ABSORB, precision=N.FP32_LOCAL, mode=N.MODE_EVENT)
+    ev32, chunk_ev, _ = b.autotune(ev32, reps=2)
+    r_ev32 = graph_rate(ev32)
+    ev64 = N.default_opts(seed=SEED, p_absorb=P_ABSORB, precision=N.FP64, mode=N.MODE_EVENT,
+                          queue_depth=ev32.queue_depth)
+    r_ev64 = graph_rate(ev64)
+    hi32 = N.default_opts(seed=SEED, p_absorb=P_ABSORB, precision=N.FP32_LOCAL)
+    hi32, chunk_hi, _ = b.autotune(hi32, reps=2)
+    r_hi32 = graph_rate(hi32)
     # per-geometry loop, plain FP64 history kernel
     tallies = [torch.zeros(gg.n_inst, dtype=torch.int64, device=dev) for gg in geoms]
     cnt = torch.zeros(16, dtype=torch.int64, device=dev)
-    o64 = N.default_opts(seed=SEED, p_absorb=P_ABSORB, precision=N.FP64, mode=N.MODE_HISTORY)
-    for gg, pp, cc, tt in zip(geoms, parts, counts, tallies):
-        gg.run_histories(pp, cc, tally=tt, counters=cnt, opts=o64)
-    cnt.zero_()
-    barrier()
-    a.record(stream)
-    for _ in range(steps):
+    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def loop_rate(opts, reps):
         for gg, pp, cc, tt in zip(geoms, parts, counts, tallies):
-            gg.run_histories(pp, cc, tally=tt, counters=cnt, opts=o64)
-    e.record(stream)
-    barrier()
-    ms_l = a.elapsed_time(e)
-    seg_l = int(cnt.cpu().numpy().view(np.uint64)[0])
-    # same launch loop in FP32-local, and the batch in FP64, to separate the two effects
-    cnt.zero_()
-    o32 = N.default_opts(seed=SEED, p_absorb=P_ABSORB, precision=N.FP32_LOCAL, mode=N.MODE_HISTORY)
-    a.record(stream)
-    for gg, pp, cc, tt in zip(geoms, parts, counts, tallies):
-        gg.run_histories(pp, cc, tally=tt, counters=cnt, opts=o32)
-    e.record(stream)
-    barrier()
-    ms_l32 = a.elapsed_time(e)
-    seg_l32 = int(cnt.cpu().numpy().view(np.uint64)[0])
-    b.zero()
-    o64b = N.default_opts(seed=SEED, p_absorb=P_ABSORB, precision=N.FP64, block=opts32.block)
-    a.record(stream)
-    b.run(o64b)
-    e.record(stream)
-    barrier()
-    ms_b64 = a.elapsed_time(e)
-    seg_b64 = int(b.counters.cpu().numpy().view(np.uint64).reshape(-1, 16)[:, 0].sum())
-    r_b = seg_b / (ms_b / 1e3)
-    r_l = seg_l / (ms_l / 1e3)
+            gg.run_histories(pp, cc, tally=tt, counters=cnt, opts=opts)
+        cnt.zero_()
+        barrier()
+        a.record(stream)
+        for _ in range(reps):
+            for gg, pp, cc, tt in zip(geoms, parts, counts, tallies):
+                gg.run_histories(pp, cc, tally=tt, counters=cnt, opts=opts)
+        e.record(stream)
+        barrier()
+        return int(cnt.cpu().numpy().view(np.uint64)[0]) / (a.elapsed_time(e) / 1e3)
+
+    r_l = loop_rate(N.default_opts(seed=SEED, p_absorb=P_ABSORB, precision=N.FP64, mode=N.MODE_HISTORY), steps)
+    r_l32 = loop_rate(N.default_opts(seed=SEED, p_absorb=P_ABSORB, precision=N.FP32_LOCAL, mode=N.MODE_HISTORY), 1)
     return {"workload": "64 geometries: 3x3..17x17 rect/hex lattices, 2-3 levels, 1e4..1e6 particles "
                         "(log-uniform), %d particles" % sum(counts),
-            "batched_fp32local_graph_segments_per_s": r_b,
+            "batched_fp32local_graph_segments_per_s": r_ev32,
             "loop_fp64_history_segments_per_s": r_l,
-            "batched_over_loop": r_b / r_l,
-            "loop_fp32local_history_segments_per_s": seg_l32 / (ms_l32 / 1e3),
-            "batched_fp64_segments_per_s": seg_b64 / (ms_b64 / 1e3),
-            "autotuned": {"block": opts32.block, "chunk": chunk},
-            "launches_per_pass": {"batched": 1, "loop": len(geoms)}}
+            "batched_over_loop": r_ev32 / r_l,
+            "batched_fp64_event_graph_segments_per_s": r_ev64,
+            "batched_fp32local_history_graph_segments_per_s": r_hi32,
+            "loop_fp32local_history_segments_per_s": r_l32,
+            "autotuned": {"event": {"queue_depth": ev32.queue_depth, "chunk": chunk_ev},
+                          "history": {"block": hi32.block, "chunk": chunk_hi}},
+            "launches_per_pass": {"batched_event": 2, "batched_history": 1, "loop": len(geoms)}}
 
 
 def run_config1_sweep(N, I, dev, stream, barrier):

@@ -242,24 +242,35 @@ trk_status batch_create(const trk_geom_t* geoms, int n_geom, const void* const* 
                         uint64_t* const* dev_records, int tracker, trk_batch_t* out);
 trk_status batch_destroy(trk_batch_t b);
 
-/* Bytes of the device table (caller-owned work buffer, 256-byte aligned). */
+/* Bytes of the caller-owned work buffer (256-byte aligned): the device table
+ * and, for event mode, the slot records of the batched event kernel at the
+ * largest queue depth (512); enough for every mode and queue depth. */
 trk_status batch_work_bytes(trk_batch_t b, size_t* bytes);
 
 /* Writes the device table for chunks of `chunk` particles (0 = 512) into
  * dev_work; synchronises `stream`.  Call again to change the chunk size. */
 trk_status batch_upload(trk_batch_t b, void* dev_work, size_t work_bytes, int chunk, void* stream);
 
-/* One persistent launch over the whole batch (opts: precision, block, grid,
- * seed, first_id, p_absorb, max_segments; mode and path cutoff ignored).
- * Issues a memset and one kernel on `stream` and nothing else, so after
- * batch_upload it can be captured in a CUDA graph and replayed. */
+/* Persistent launches over the whole batch (opts: mode, precision, block,
+ * grid, queue_depth, max_rounds, seed, first_id, p_absorb, max_segments;
+ * path cutoff ignored).  History mode: one kernel, one history per lane,
+ * warps pull chunks of one geometry.  Event mode: the event kernel's queues
+ * and slot records per warp, each warp working through chunks of one
+ * geometry at a time (a chunk of another geometry starts once the warp's
+ * slots have drained); rect-tracker and CSG entries are two launches.
+ * Issues memsets and kernels on `stream` and nothing else, so after
+ * batch_upload it can be captured in a CUDA graph and replayed.  A kernel
+ * that reaches the round limit writes TRK_E_TIMEOUT to the status counter of
+ * the geometry it was on. */
 trk_status run_batched(trk_batch_t b, void* dev_work, const trk_run_opts* opts, void* stream);
 
 /* Autotuner: times block sizes {64, 96, 128} x chunk sizes {128, 512, 2048}
- * on the batch itself (CUDA events, `reps` launches each) and writes the
- * fastest to opts->block and *chunk_out, leaving the table uploaded for
- * it; *best_ms (optional) gets its time.  The trial launches add to the
- * tallies and counters: clear them afterwards.  Synchronises `stream`. */
+ * (history mode) or queue depths {256, 384, 512} x chunk sizes {4096, 16384,
+ * 65536} (event mode, opts->mode) on the batch itself (CUDA events, `reps`
+ * launches each) and writes the fastest to opts->block or opts->queue_depth
+ * and *chunk_out, leaving the table uploaded for it; *best_ms (optional) gets
+ * its time.  The trial launches add to the tallies and counters: clear them
+ * afterwards.  Synchronises `stream`. */
 trk_status batch_autotune(trk_batch_t b, void* dev_work, size_t work_bytes, trk_run_opts* opts,
                           int* chunk_out, int reps, double* best_ms, void* stream);
 

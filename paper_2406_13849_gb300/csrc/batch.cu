@@ -21,6 +21,8 @@
 #include "trk.h"
 #include "trk_device.cuh"
 #include "trk_internal.h"
+#include "trk_event.cuh"
+#include "trk_launch.h"
 
 using namespace trk;
 using namespace trk::dev;
@@ -44,6 +46,8 @@ struct BatchHeader {
     unsigned long long total_chunks;
     int n_geom;
     int chunk;
+    unsigned long long next_ev[2];   // event mode: chunk counters of the rect and CSG launches
+    unsigned long long split;        // first chunk of the CSG-tracker entries
 };
 
 size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -113,6 +117,244 @@ __global__ void __launch_bounds__(128) k_batched(BatchHeader* __restrict__ hdr, 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Event mode: each warp runs the event loop of the single-geometry event
+// kernel (slot records, queues by operation) over chunks of one geometry at
+// a time.  It keeps refilling from the next chunk while that chunk belongs
+// to the same geometry; a chunk of another geometry waits until the warp's
+// slots have drained, so the geometry and tracker stay warp-uniform.  Rect-
+// and CSG-tracker entries run as two launches (the rect chunks come first).
+// ---------------------------------------------------------------------------
+using namespace trk::ev;
+constexpr int BEV_QUEUES = 4 + MAXL;   // flight, next flight, collide, free, cross per level
+
+__device__ __forceinline__ int entry_of(const BatchEntry* table, int ng, unsigned long long c) {
+    int lo = 0, hi = ng - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((unsigned long long)table[mid].first_chunk <= c) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <bool CSG, bool F32, int FLAGS>
+__global__ void TRK_EV_BOUNDS k_batched_ev(BatchHeader* __restrict__ hdr, const BatchEntry* __restrict__ table,
+                                           const RunP rp, const EvBuf B, int slots, int side,
+                                           unsigned long long c_begin, unsigned long long c_end,
+                                           unsigned long long max_rounds) {
+    extern __shared__ QIdx smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    QIdx* base_q = smem + warp * BEV_QUEUES * slots;
+    QIdx* fly = base_q;
+    QIdx* next = base_q + slots;
+    QIdx* qc = base_q + 2 * slots;
+    QIdx* qf = base_q + 3 * slots;
+    QIdx* qx = base_q + 4 * slots;
+    const int slot0 = (blockIdx.x * (EV_BLOCK / 32) + warp) * slots;
+    const int ng = hdr->n_geom;
+    const long long chunk = hdr->chunk;
+    Counts cnt;
+#pragma unroll
+    for (int k = 0; k < NCOUNT; ++k) cnt.k[k] = 0;
+    for (int k = lane; k < slots; k += 32) qf[k] = QIdx(k);
+    int n_fly = 0, n_free = slots;
+    int ge = -1;                   // current entry, warp-uniform
+    long long pn = 0, pb = 0;      // next particle and end of the current chunk
+    long long pend = -1;           // chunk pulled for another entry
+    bool exhausted = false;
+    __syncwarp();
+    for (unsigned long long round = 0;; ++round) {
+        // ---- chunks: pull the next one when the current is used up ----------
+        if (pn >= pb && pend < 0 && !exhausted) {
+            unsigned long long c = 0;
+            if (lane == 0) c = c_begin + atomicAdd(&hdr->next_ev[side], 1ULL);
+            c = __shfl_sync(0xffffffffu, c, 0);
+            if (c >= c_end) exhausted = true;
+            else pend = (long long)c;
+        }
+        if (pend >= 0) {
+            const int e = entry_of(table, ng, (unsigned long long)pend);
+            if (e == ge || n_fly == 0) {
+                if (e != ge) {
+                    if (ge >= 0) flush_counts(cnt, table[ge].counters);
+#pragma unroll
+                    for (int k = 0; k < NCOUNT; ++k) cnt.k[k] = 0;
+                    ge = e;
+                }
+                pn = (pend - table[e].first_chunk) * chunk;
+                pb = pn + chunk < table[e].n ? pn + chunk : table[e].n;
+                pend = -1;
+            }
+        }
+        if (ge < 0) break;   // no chunk at all for this warp
+        const BatchEntry& E = table[ge];
+        const DevGeom& g = E.g;
+        unsigned long long* rec = (FLAGS & F_REC) ? E.records : nullptr;
+        // ---- refill free slots from the current chunk ------------------------
+        int got = 0;
+        const long long first = pn;
+        if (n_free > 0 && pn < pb && (n_free >= TRK_EV_REFILL_MIN || n_fly < 32)) {
+            got = pb - pn < (long long)n_free ? int(pb - pn) : n_free;
+            pn += got;
+        }
+        int n_park = 0;
+        for (int b = 0; b < got; b += 32) {
+            const int k = b + lane;
+            bool ok = false;
+            int slot = 0;
+            if (k < got) {
+                slot = slot0 + qf[n_free - got + k];
+                const long long pidx = first + k;
+                Ctx c;
+                c.pid = uint32_t(rp.first_id + uint64_t(pidx));
+                c.event = 0; c.nseg = 0; c.path = 0.0; c.hash = FNV0; c.status = 0;
+                const int pst = E.P.status[pidx];
+                if (pst != 0) {
+                    c.status = pst;
+                    cnt.k[TRK_K_SOURCE]++;
+                } else {
+                    St s;
+                    load_birth(g, E.P, pidx, s);
+                    if (find_from<CSG>(g, s, 0) != 0) {
+                        c.status = TRK_E_LOST;
+                        cnt.k[TRK_K_LOST]++;
+                    } else {
+                        unsigned char* r = rec_at<CSG>(B, slot);
+                        D2(r, R_XY) = make_double2(s.x, s.y);
+                        D2(r, R_ZT) = make_double2(s.z, s.tau);
+                        store_dir(r, s);
+                        store_levels<CSG>(r, s, 0);
+                        store_ctx<FLAGS>(r, int(pidx), c, 0);
+                        ok = true;
+                    }
+                }
+                if (!ok && rec) finish<FLAGS>(pidx, c, rec);
+            }
+            wpush(ok, slot - slot0, fly, n_fly);
+            wpush(k < got && !ok, slot - slot0, next, n_park);
+        }
+        __syncwarp();
+        n_free -= got;
+        for (int b = 0; b < n_park; b += 32) {
+            const int k = b + lane;
+            wpush(k < n_park, k < n_park ? next[k] : 0, qf, n_free);
+        }
+        __syncwarp();
+        if (n_fly == 0 && exhausted && pend < 0 && pn >= pb) break;
+        if (round >= max_rounds) {
+            if (lane == 0) kernel_status(E.counters, TRK_E_TIMEOUT);
+            break;
+        }
+        // ---- flight ------------------------------------------------------------
+        int n_cross[MAXL], n_coll = 0;
+#pragma unroll
+        for (int l = 0; l < MAXL; ++l) n_cross[l] = 0;
+        for (int b = 0; b < n_fly; b += 32) {
+            const int k = b + lane;
+            int a = A_DONE, slot = 0, hl = -1;
+            if (k < n_fly) {
+                slot = slot0 + fly[k];
+                unsigned char* r = rec_at<CSG>(B, slot);
+                St s;
+                const double2 xy = D2(r, R_XY), zt = D2(r, R_ZT);
+                s.x = xy.x; s.y = xy.y; s.z = zt.x; s.tau = zt.y;
+                load_dir(r, s);
+                load_levels<CSG>(g, r, s);
+                Ctx c;
+                int hpack;
+                const int pidx = load_ctx<FLAGS>(r, c, hpack, rp);
+                Hit h;
+                a = step_fly<CSG, F32, FLAGS>(g, s, h, c, rp, E.tally, cnt, nullptr, nullptr, 0);
+                if (a == A_DONE) {
+                    if (rec) finish<FLAGS>(pidx, c, rec);
+                } else {
+                    D2(r, R_XY) = make_double2(s.x, s.y);
+                    D2(r, R_ZT) = make_double2(s.z, s.tau);
+                    if (a == A_CROSS) {
+                        hl = h.level;
+                        store_ctx<FLAGS>(r, pidx, c, pack_hit(h));
+                        I4(r, R_HT) = make_int4(h.surf, h.entry, 0, 0);
+                    } else {
+                        store_ctx<FLAGS>(r, pidx, c, hpack);
+                    }
+                }
+            }
+            const bool live = k < n_fly;
+#pragma unroll
+            for (int l = 0; l < MAXL; ++l) wpush(live && hl == l, slot - slot0, qx + l * slots, n_cross[l]);
+            wpush(live && a == A_COLLIDE, slot - slot0, qc, n_coll);
+            wpush(live && a == A_DONE, slot - slot0, qf, n_free);
+        }
+        __syncwarp();
+        // ---- cross_surface, then change_direction -------------------------------
+        int n_next = 0;
+#pragma unroll 1
+        for (int lq = 0; lq < MAXL; ++lq)
+        for (int b = 0; b < n_cross[lq]; b += 32) {
+            const int k = b + lane;
+            int a = A_DONE, slot = 0;
+            if (k < n_cross[lq]) {
+                slot = slot0 + qx[lq * slots + k];
+                unsigned char* r = rec_at<CSG>(B, slot);
+                St s;
+                const double2 xy = D2(r, R_XY), zt = D2(r, R_ZT);
+                s.x = xy.x; s.y = xy.y; s.z = zt.x; s.tau = zt.y;
+                load_dir(r, s);
+                load_levels<CSG>(g, r, s);
+                Ctx c;
+                int hpack;
+                const int pidx = load_ctx<FLAGS>(r, c, hpack, rp);
+                Hit h;
+                unpack_hit(hpack, h);
+                const int4 ht = I4(r, R_HT);
+                h.surf = ht.x; h.entry = ht.y; h.d = 0.0;
+                const unsigned refl0 = cnt.k[TRK_K_REFLECTIONS];
+                a = step_cross<CSG>(g, s, h, c, rp, cnt);
+                if (a == A_DONE) {
+                    if (rec) finish<FLAGS>(pidx, c, rec);
+                } else {
+                    store_levels<CSG>(r, s, 0);
+                    if (cnt.k[TRK_K_REFLECTIONS] != refl0) store_dir(r, s);
+                }
+            }
+            const bool live = k < n_cross[lq];
+            wpush(live && a == A_FLY, slot - slot0, next, n_next);
+            wpush(live && a == A_DONE, slot - slot0, qf, n_free);
+        }
+        for (int b = 0; b < n_coll; b += 32) {
+            const int k = b + lane;
+            int a = A_DONE, slot = 0;
+            if (k < n_coll) {
+                slot = slot0 + qc[k];
+                unsigned char* r = rec_at<CSG>(B, slot);
+                St s;
+                Ctx c;
+                int hpack;
+                const int pidx = load_ctx<FLAGS>(r, c, hpack, rp);
+                a = step_collide(g, s, c, rp, cnt);
+                if (a == A_DONE) {
+                    if (rec) finish<FLAGS>(pidx, c, rec);
+                } else {
+                    store_dir(r, s);
+                    const double z = D2(r, R_ZT).x;
+                    D2(r, R_ZT) = make_double2(z, s.tau);
+                    const int4 lv = I4(r, R_LV);
+                    I4(r, R_LV) = make_int4(lv.x, -1, -1, lv.w);
+                    store_ctx<FLAGS>(r, pidx, c, hpack);
+                }
+            }
+            const bool live = k < n_coll;
+            wpush(live && a == A_FLY, slot - slot0, next, n_next);
+            wpush(live && a == A_DONE, slot - slot0, qf, n_free);
+        }
+        __syncwarp();
+        QIdx* t = fly; fly = next; next = t;
+        n_fly = n_next;
+    }
+    if (ge >= 0) flush_counts(cnt, table[ge].counters);
+}
+
 }  // namespace
 
 // Host object behind trk_batch_t.
@@ -123,6 +365,7 @@ struct trk_batch {
     int chunk = 0;                     // chunk size the uploaded table was built for
     bool uploaded = false;
     void* work = nullptr;
+    size_t work_bytes = 0;
     unsigned magic = 0;
 };
 constexpr unsigned TRK_BATCH_MAGIC = 0x74726b62u;
@@ -138,6 +381,61 @@ int sm_count_b() {
 }
 
 size_t table_bytes(int n) { return a256(sizeof(BatchHeader)) + a256(size_t(n) * sizeof(BatchEntry)); }
+
+// Event mode: slot records after the table, `slots` per warp.
+size_t event_bytes(int n, int slots) { return table_bytes(n) + event_work_bytes(slots, event_grid(slots)); }
+constexpr int BEV_MAX_SLOTS = 512;
+
+}  // namespace
+
+namespace {
+
+// Event mode: the rect-tracker chunks [0, split) and the CSG ones
+// [split, total) as two launches of the batched event kernel.
+trk_status run_batched_event(trk_batch_t b, void* dev_work, const trk_run_opts& o, const RunP& rp, bool f32, bool rec,
+                             cudaStream_t s) {
+    const int slots = o.queue_depth > 0 ? o.queue_depth : 256;
+    if (slots < 32 || slots > BEV_MAX_SLOTS) return trk_status(set_error(TRK_E_INVALID, "run_batched: queue_depth must be in [32, 512]"));
+    if (o.max_rounds < 0) return trk_status(set_error(TRK_E_INVALID, "run_batched: max_rounds must be >= 0"));
+    const int grid = event_grid(slots);
+    const size_t need = event_bytes(b->n_geom, slots);
+    if (b->work_bytes < need)
+        return trk_status(set_error(TRK_E_NOMEM, "run_batched (event): work buffer needs %zu bytes", need));
+    BatchHeader* hdr = static_cast<BatchHeader*>(dev_work);
+    const BatchEntry* table = reinterpret_cast<const BatchEntry*>(static_cast<unsigned char*>(dev_work) + a256(sizeof(BatchHeader)));
+    const long long T = (long long)slots * (EV_BLOCK / 32) * grid;
+    const EvBuf B = make_buf(static_cast<unsigned char*>(dev_work) + table_bytes(b->n_geom), T);
+    cudaError_t e = cudaMemsetAsync(hdr->next_ev, 0, sizeof(hdr->next_ev), s);
+    if (e != cudaSuccess) return trk_status(set_error(TRK_E_CUDA, "run_batched: %s", cudaGetErrorString(e)));
+    long long total = 0, split = -1, npart = 0;
+    for (auto& en : b->entries) {
+        if (en.csg && split < 0) split = en.first_chunk;
+        total = en.first_chunk + (en.n + b->chunk - 1) / b->chunk;
+        npart += en.n;
+    }
+    if (split < 0) split = total;
+    unsigned long long max_rounds = (rp.max_segments + 2ULL) * (unsigned long long)(npart / 32 + 2);
+    if (o.max_rounds > 0) max_rounds = (unsigned long long)o.max_rounds;
+    const size_t smem = size_t(BEV_QUEUES) * slots * (EV_BLOCK / 32) * sizeof(QIdx);
+    auto launch = [&](auto kernel, int side, long long c0, long long c1) {
+        if (c1 <= c0) return;
+        if (smem > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        kernel<<<grid, EV_BLOCK, smem, s>>>(hdr, table, rp, B, slots, side, (unsigned long long)c0,
+                                            (unsigned long long)c1, max_rounds);
+    };
+    if (f32) {
+#ifndef TRK_EXACT
+        if (rec) { launch(k_batched_ev<false, true, F_REC>, 0, 0, split); launch(k_batched_ev<true, true, F_REC>, 1, split, total); }
+        else { launch(k_batched_ev<false, true, 0>, 0, 0, split); launch(k_batched_ev<true, true, 0>, 1, split, total); }
+#endif
+    } else {
+        if (rec) { launch(k_batched_ev<false, false, F_REC>, 0, 0, split); launch(k_batched_ev<true, false, F_REC>, 1, split, total); }
+        else { launch(k_batched_ev<false, false, 0>, 0, 0, split); launch(k_batched_ev<true, false, 0>, 1, split, total); }
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return trk_status(set_error(TRK_E_CUDA, "run_batched: %s", cudaGetErrorString(e)));
+    return TRK_OK;
+}
 
 }  // namespace
 
@@ -203,7 +501,7 @@ trk_status batch_destroy(trk_batch_t b) {
 
 trk_status batch_work_bytes(trk_batch_t b, size_t* bytes) {
     if (!valid_batch(b) || !bytes) return trk_status(set_error(TRK_E_INVALID, "batch_work_bytes: bad arguments"));
-    *bytes = table_bytes(b->n_geom);
+    *bytes = event_bytes(b->n_geom, BEV_MAX_SLOTS);
     return TRK_OK;
 }
 
@@ -214,17 +512,21 @@ trk_status batch_upload(trk_batch_t b, void* dev_work, size_t work_bytes, int ch
         return trk_status(set_error(TRK_E_INVALID, "batch_upload: work buffer must be 256-byte aligned"));
     if (chunk <= 0) chunk = 512;
     if (chunk < 32 || chunk > (1 << 20)) return trk_status(set_error(TRK_E_INVALID, "batch_upload: chunk must be in [32, 2^20]"));
-    long long total = 0;
+    long long total = 0, split = -1;
     for (auto& e : b->entries) {
+        if (e.csg && split < 0) split = total;
         e.first_chunk = total;
         total += (e.n + chunk - 1) / chunk;
     }
+    if (split < 0) split = total;
     std::vector<unsigned char> img(table_bytes(b->n_geom), 0);
     BatchHeader h;
+    std::memset(&h, 0, sizeof h);
     h.next_chunk = 0;
     h.total_chunks = (unsigned long long)total;
     h.n_geom = b->n_geom;
     h.chunk = chunk;
+    h.split = (unsigned long long)split;
     std::memcpy(img.data(), &h, sizeof h);
     std::memcpy(img.data() + a256(sizeof(BatchHeader)), b->entries.data(), b->entries.size() * sizeof(BatchEntry));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -234,6 +536,7 @@ trk_status batch_upload(trk_batch_t b, void* dev_work, size_t work_bytes, int ch
     b->chunk = chunk;
     b->uploaded = true;
     b->work = dev_work;
+    b->work_bytes = work_bytes;
     return TRK_OK;
 }
 
@@ -260,13 +563,15 @@ trk_status run_batched(trk_batch_t b, void* dev_work, const trk_run_opts* opts, 
     rp.max_path = DINF;
     rp.seed_lo = uint32_t(o.seed);
     rp.trace_cap = 0;
-    const int block = o.block > 0 ? o.block : 128;
-    if (block > 128 || (block & 31)) return trk_status(set_error(TRK_E_INVALID, "run_batched: block must be a multiple of 32, <= 128"));
     bool rec = false;
     for (auto& e : b->entries) rec |= e.records != nullptr;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     BatchHeader* hdr = static_cast<BatchHeader*>(dev_work);
     const BatchEntry* table = reinterpret_cast<const BatchEntry*>(static_cast<unsigned char*>(dev_work) + a256(sizeof(BatchHeader)));
+    if (o.mode == TRK_MODE_EVENT) return run_batched_event(b, dev_work, o, rp, f32, rec, s);
+    if (o.mode != TRK_MODE_HISTORY) return trk_status(set_error(TRK_E_INVALID, "run_batched: unknown mode %d", o.mode));
+    const int block = o.block > 0 ? o.block : 128;
+    if (block > 128 || (block & 31)) return trk_status(set_error(TRK_E_INVALID, "run_batched: block must be a multiple of 32, <= 128"));
     cudaError_t e = cudaMemsetAsync(&hdr->next_chunk, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return trk_status(set_error(TRK_E_CUDA, "run_batched: %s", cudaGetErrorString(e)));
     int per_sm = 1;
@@ -292,30 +597,39 @@ trk_status run_batched(trk_batch_t b, void* dev_work, const trk_run_opts* opts, 
     return TRK_OK;
 }
 
-// Autotuner: times every (block, chunk) candidate on the batch itself with
-// CUDA events (one warm-up and `reps` timed launches each) and returns the
-// fastest in opts->block and *chunk_out; the table is left uploaded for the
-// winner.  The launches add to the caller's tallies and counters: clear
+// Autotuner: times every (block, chunk) candidate (history mode) or every
+// (queue depth, chunk) candidate (event mode) on the batch itself with CUDA
+// events (one warm-up and `reps` timed launches each) and returns the fastest
+// in opts->block or opts->queue_depth and *chunk_out; the table is left
+// uploaded for the winner.  The launches add to the caller's tallies and counters: clear
 // them afterwards.  Synchronises `stream`.
 trk_status batch_autotune(trk_batch_t b, void* dev_work, size_t work_bytes, trk_run_opts* opts, int* chunk_out,
                           int reps, double* best_ms, void* stream) {
     if (!valid_batch(b) || !dev_work || !opts || !chunk_out) return trk_status(set_error(TRK_E_INVALID, "batch_autotune: bad arguments"));
     if (reps <= 0) reps = 2;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const int blocks[] = {64, 96, 128};
-    const int chunks[] = {128, 512, 2048};
+    // history mode: (block, chunk); event mode: (queue depth, chunk), with
+    // chunks large enough that a warp rarely drains between chunks
+    const bool event = opts->mode == TRK_MODE_EVENT;
+    const int hist_blocks[] = {64, 96, 128}, hist_chunks[] = {128, 512, 2048};
+    const int ev_depths[] = {256, 384, 512}, ev_chunks[] = {4096, 16384, 65536};
+    const int* blocks = event ? ev_depths : hist_blocks;
+    const int* chunks = event ? ev_chunks : hist_chunks;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return trk_status(set_error(TRK_E_CUDA, "batch_autotune: cudaEventCreate failed"));
     float best = 1e30f;
-    int best_block = 128, best_chunk = 512;
+    int best_block = event ? 256 : 128, best_chunk = event ? 16384 : 512;
     trk_status st = TRK_OK;
-    for (int ch : chunks) {
+    for (int ci = 0; ci < 3; ++ci) {
+        const int ch = chunks[ci];
         st = batch_upload(b, dev_work, work_bytes, ch, stream);
         if (st != TRK_OK) break;
-        for (int bl : blocks) {
+        for (int bi = 0; bi < 3; ++bi) {
+            const int bl = blocks[bi];
             trk_run_opts o = *opts;
-            o.block = bl;
+            if (event) o.queue_depth = bl;
+            else o.block = bl;
             o.grid = 0;
             st = run_batched(b, dev_work, &o, stream);
             if (st != TRK_OK) break;
@@ -338,7 +652,8 @@ trk_status batch_autotune(trk_batch_t b, void* dev_work, size_t work_bytes, trk_
     if (st != TRK_OK) return st;
     st = batch_upload(b, dev_work, work_bytes, best_chunk, stream);
     if (st != TRK_OK) return st;
-    opts->block = best_block;
+    if (event) opts->queue_depth = best_block;
+    else opts->block = best_block;
     opts->grid = 0;
     *chunk_out = best_chunk;
     if (best_ms) *best_ms = double(best);
