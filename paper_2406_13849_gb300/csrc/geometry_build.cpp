@@ -673,11 +673,13 @@ float f_up(double v) {
 
 class BvhBuilder {
   public:
-    std::vector<SkipNode> nodes;
+    std::vector<BvhNode> nodes;
     std::vector<int> leaf_cells;
+    int max_depth = 0;
     Box proxy;   // finite stand-in for infinite extents in the cost
 
-    // Builds the tree over `cells` and returns its root node index.
+    // Builds the tree over `cells` and returns its root reference (a node
+    // index, or a leaf reference for a universe of at most BVH_LEAF_MAX cells).
     int build(std::vector<int>& cells, const std::vector<Box>& boxes) {
         ids_ = cells;
         boxes_ = &boxes;
@@ -743,24 +745,29 @@ class BvhBuilder {
                                  [&](int id) { return centre(id, best_axis) < best_plane; });
         return int(it - ids_.begin());
     }
+    // SAH splits; below depth 24 the median, so the depth stays below
+    // 24 + log2(cells) (the device walk's stack holds BVH_STACK entries).
     int emit(int lo, int hi, int depth) {
-        const int self = int(nodes.size());
-        nodes.push_back(SkipNode{});
-        Box b = bound(lo, hi);
-        int leaf = -1;
-        if (hi - lo <= BVH_LEAF_MAX || depth > 60) {
-            int first = int(leaf_cells.size());
+        max_depth = std::max(max_depth, depth);
+        if (hi - lo <= BVH_LEAF_MAX) {
+            const int first = int(leaf_cells.size());
             for (int i = lo; i < hi; ++i) leaf_cells.push_back(ids_[size_t(i)]);
-            leaf = (first << 4) | (hi - lo);
-        } else {
-            int mid = split(lo, hi);
-            emit(lo, mid, depth + 1);
-            emit(mid, hi, depth + 1);
+            return -1 - ((first << 4) | (hi - lo));
         }
-        SkipNode& nd = nodes[size_t(self)];
-        for (int k = 0; k < 3; ++k) { nd.lo[k] = f_down(b.lo[k]); nd.hi[k] = f_up(b.hi[k]); }
-        nd.leaf = leaf;
-        nd.skip = int(nodes.size());
+        const int self = int(nodes.size());
+        nodes.push_back(BvhNode{});
+        const int mid = depth > 24 ? lo + (hi - lo) / 2 : split(lo, hi);
+        const Box b0 = bound(lo, mid), b1 = bound(mid, hi);
+        const int r0 = emit(lo, mid, depth + 1);
+        const int r1 = emit(mid, hi, depth + 1);
+        BvhNode& nd = nodes[size_t(self)];
+        for (int k = 0; k < 3; ++k) {
+            nd.lo0[k] = f_down(b0.lo[k]); nd.hi0[k] = f_up(b0.hi[k]);
+            nd.lo1[k] = f_down(b1.lo[k]); nd.hi1[k] = f_up(b1.hi[k]);
+        }
+        nd.ref0 = r0;
+        nd.ref1 = r1;
+        nd.pad0 = nd.pad1 = 0;
         return self;
     }
 };
@@ -854,7 +861,9 @@ int build_host(const char* json, size_t len, Built& B) {
             bvh.proxy.hi[k] = hi + m;
         }
         U.bvh = bvh.build(ids, boxes);
+        if (U.bvh < 0) U.bvh = -1;   // a single leaf: the linear scan does the same
     }
+    if (bvh.max_depth >= BVH_STACK) return set_error(TRK_E_DESC, "BVH depth %d exceeds %d", bvh.max_depth, BVH_STACK);
     B.n_nodes = int(bvh.nodes.size());
 
     // SoA arrays
@@ -1013,9 +1022,9 @@ int build_host(const char* json, size_t len, Built& B) {
     if (l_grid.empty()) { l_grid.push_back(0); l_ctr.push_back(0); l_gkey.push_back(0); l_lof.push_back(0); l_hif.push_back(0); }
     if (c_slabf.empty()) c_slabf.push_back(0);
     if (l_fill.empty()) { l_fill.push_back(0); l_eoff.push_back(0); }
-    std::vector<SkipNode> nodes = bvh.nodes;
+    std::vector<BvhNode> nodes = bvh.nodes;
     std::vector<int> leaf = bvh.leaf_cells;
-    if (nodes.empty()) nodes.push_back(SkipNode{});
+    if (nodes.empty()) nodes.push_back(BvhNode{});
     if (leaf.empty()) leaf.push_back(0);
     if (cs.empty()) { cs.push_back(0); cs_adj.push_back(make_int2(-1, -1)); }
 
@@ -1036,7 +1045,7 @@ int build_host(const char* json, size_t len, Built& B) {
     o[12] = L.put(l_fill.size() * 4);
     o[13] = L.put(l_eoff.size() * 4);
     o[14] = L.put(l_pscale.size() * 4);
-    o[15] = L.put(nodes.size() * sizeof(SkipNode));
+    o[15] = L.put(nodes.size() * sizeof(BvhNode));
     o[16] = L.put(leaf.size() * 4);
     o[17] = L.put(G.sigma.size() * 8);
     o[18] = L.put(s_key.size() * 8);
@@ -1157,7 +1166,7 @@ trk_status geometry_build(const char* json, size_t len, void* dev_buf, size_t* d
     d.l_fill = reinterpret_cast<const int*>(base + o[12]);
     d.l_eoff = reinterpret_cast<const int*>(base + o[13]);
     d.l_pscale = reinterpret_cast<const int*>(base + o[14]);
-    d.nodes = reinterpret_cast<const SkipNode*>(base + o[15]);
+    d.nodes = reinterpret_cast<const BvhNode*>(base + o[15]);
     d.leaf_cells = reinterpret_cast<const int*>(base + o[16]);
     d.sigma = reinterpret_cast<const double*>(base + o[17]);
     d.s_key = reinterpret_cast<const long long*>(base + o[18]);

@@ -31,18 +31,19 @@ constexpr int BVH_LEAF_MAX = 4;
 // Universes with at most this many cells are scanned linearly (Alg. 3).
 constexpr int LINEAR_MAX = 4;
 
-// BVH node in depth-first preorder ("skip list"): a traversal visits node i;
-// if the point is in its box it continues at i + 1 (first child, or the next
-// subtree after a leaf), otherwise at `skip` (the node after i's subtree).
-// Boxes are FP32, rounded outward from padded FP64 cell boxes.
-//   leaf < 0   internal node
-//   leaf >= 0  leaf: (first leaf slot << 4) | count
-struct alignas(16) SkipNode {
-    float lo[3];
-    int skip;
-    float hi[3];
-    int leaf;
+// BVH node holding both children's boxes (FP32, rounded outward from padded
+// FP64 cell boxes), so one node load tests both children.  A child reference
+// >= 0 is an internal node; < 0 is a leaf, -1 - ((first leaf slot << 4) |
+// count).  Children are laid out left before right (preorder), and a point
+// query walks left before right, so the first holding cell is that of the
+// preorder walk.
+struct alignas(16) BvhNode {
+    float lo0[3], hi0[3];
+    float lo1[3], hi1[3];
+    int ref0, ref1, pad0, pad1;
 };
+// Largest BVH depth the builder produces (the walk's stack size).
+constexpr int BVH_STACK = 64;
 
 // c_range count field: low bits count, CS_SLAB_FLAG marks a cell with a
 // slab view: at most one lower and one upper axis plane per dimension (its
@@ -99,7 +100,7 @@ struct DevGeom {
     const float* c_slabf;     // 6 per cell: slab faces (lo_x, hi_x, lo_y, hi_y, lo_z, hi_z)
                               // relative to the cell's translation
     // BVH (skip-list preorder per universe)
-    const SkipNode* nodes;
+    const BvhNode* nodes;
     const int* leaf_cells;
     // materials
     const double* sigma;
