@@ -395,6 +395,19 @@ struct St {
     Lv lv[MAXL];
 };
 
+// Inlining of the less frequent steps (build knobs, measured per kernel):
+// out of line they leave the hot flight code a smaller footprint, at the
+// price of a call.
+#ifndef TRK_COLLIDE_INLINE
+#define TRK_COLLIDE_INLINE __forceinline__
+#endif
+#ifndef TRK_FIND_INLINE
+#define TRK_FIND_INLINE __forceinline__
+#endif
+#ifndef TRK_CROSS_INLINE
+#define TRK_CROSS_INLINE __forceinline__
+#endif
+
 // Level access by a run-time level index.  The level stack stays in
 // registers (an indexed array would go to local memory); these select among
 // the MAXL entries, so a loop over levels can keep one copy of its body
@@ -486,7 +499,7 @@ __device__ __forceinline__ int enter_cell(const DevGeom& g, Lv& L, int c) {
 // Alg. 7 from level `start` downward (rect view for rect arrays unless CSG).
 // Returns 0 on success, -1 if no cell holds the point.
 template <bool CSG>
-__device__ __forceinline__ int find_from(const DevGeom& g, St& s, int start) {
+__device__ TRK_FIND_INLINE int find_from(const DevGeom& g, St& s, int start) {
     if (start < 0 || start >= MAXL) return -1;
     double x, y, z;
     local_at(s, start, x, y, z);
@@ -1115,7 +1128,7 @@ __device__ __forceinline__ int after_step(Ctx& c, const RunP& rp, Counts& cnt) {
 }
 
 template <bool CSG>
-__device__ __forceinline__ int step_cross(const DevGeom& g, St& s, const Hit& h, Ctx& c, const RunP& rp, Counts& cnt) {
+__device__ TRK_CROSS_INLINE int step_cross(const DevGeom& g, St& s, const Hit& h, Ctx& c, const RunP& rp, Counts& cnt) {
     int fl;
     int cr = cross_surface<CSG>(g, s, h, fl);
     if (cr == CR_FIND) cr = find_from<CSG>(g, s, fl) == 0 ? CR_OK : CR_LOST;
@@ -1125,7 +1138,7 @@ __device__ __forceinline__ int step_cross(const DevGeom& g, St& s, const Hit& h,
     return after_step(c, rp, cnt);
 }
 
-__device__ __forceinline__ int step_collide(const DevGeom& g, St& s, Ctx& c, const RunP& rp, Counts& cnt) {
+static __device__ TRK_COLLIDE_INLINE int step_collide(const DevGeom& g, St& s, Ctx& c, const RunP& rp, Counts& cnt) {
     const uint32_t gid = uint32_t(g.gid);
     ++c.event;
     cnt.k[TRK_K_COLLISIONS]++;

@@ -21,6 +21,11 @@
 #include <cstring>
 
 #include "trk.h"
+// In the history kernel (one history per lane, every step inline) an out-of-
+// line find_cell measured faster: 1.33x for the rect tracker, 1.06x for CSG.
+#ifndef TRK_FIND_INLINE
+#define TRK_FIND_INLINE __noinline__
+#endif
 #include "trk_device.cuh"
 #include "trk_internal.h"
 #include "trk_launch.h"
