@@ -42,9 +42,9 @@ CPU_SAMPLE_ONE_CORE = 200_000
 EVENT_SLOTS = 512
 # DRAM bytes (read + write) per segment of the dominant kernel, from one ncu
 # capture of the same kernel on the same geometry with 3e6 particles
-# (37.58 GB over 82,931,315 segments); scaled to a full launch by its
+# (41.24 GB over 82,931,315 segments); scaled to a full launch by its
 # segments.  None whenever the kernel has changed since that capture.
-TRAFFIC_BYTES_PER_SEGMENT = 37.577e9 / 82931315
+TRAFFIC_BYTES_PER_SEGMENT = 41.235e9 / 82931315
 
 
 def _env_int(k, d):
