@@ -341,6 +341,7 @@ def main() -> None:
 
     # ---- configuration 1 size sweep and the transmission workload ----------
     sweep = run_config1_sweep(N, I, dev, stream, barrier)
+    hexcore = run_config3(N, I, dev, stream, barrier, k2)
     trans = run_config5(N, I, dev, stream, barrier, k2)
 
     cpu = None
@@ -377,6 +378,7 @@ def main() -> None:
             },
             "batched": batch,
             "config1_sweep": sweep,
+            "config3": hexcore,
             "transmission": trans,
         }
         print(json.dumps(line), flush=True)
@@ -497,6 +499,48 @@ def run_config1_sweep(N, I, dev, stream, barrier):
         del parts
     return {"workload": "17x17 pins (pitch 1.26, radii 0.41/0.475) in a reflecting box 21.42 x 21.42 x 100, "
                         "3 materials, absorption 0.3", "unit": UNIT, "rows": rows}
+
+
+def run_config3(N, I, dev, stream, barrier, steps):
+    """Hex core (127 assemblies of 91 pins, rings 6 of ring-6 lattices turned
+    by 30 degrees), 1e7 particles, event kernel: the BVH-CSG tracker in FP64
+    and FP32-local, and the array tracker (closed-form hex element search)
+    in FP64."""
+    import numpy as np
+    import torch
+    g = N.Geometry(I.to_json(I.config3()), device=dev)
+    n = 10_000_000
+    parts = torch.empty(g.particle_bytes(n), dtype=torch.uint8, device=dev)
+    g.source_init(n, seed=SEED, out=parts)
+    tally = torch.zeros(g.n_inst, dtype=torch.int64, device=dev)
+    cnt = torch.zeros(N.NCOUNTERS, dtype=torch.int64, device=dev)
+    out = {"workload": "hex core: 127 assemblies x 91 pins (rings 6 of ring-6 pin lattices turned 30 deg), "
+                       "h=200, 5 materials, absorption 0.25, 1e7 particles", "unit": UNIT}
+    for name, tr, prec in (("csg_fp64_event", N.TRACKER_CSG, N.FP64),
+                           ("csg_fp32local_event", N.TRACKER_CSG, N.FP32_LOCAL),
+                           ("array_fp64_event", N.TRACKER_RECT, N.FP64)):
+        opts = N.default_opts(tracker=tr, mode=N.MODE_EVENT, precision=prec, seed=SEED,
+                              p_absorb=P_ABSORB, queue_depth=EVENT_SLOTS)
+        work = torch.empty(g.work_bytes(n, opts) + 256, dtype=torch.uint8, device=dev)
+        g.run_histories(parts, n, tally=tally, counters=cnt, opts=opts, work=work)
+        cnt.zero_()
+        barrier()
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            g.run_histories(parts, n, tally=tally, counters=cnt, opts=opts, work=work)
+        e.record(stream)
+        barrier()
+        c = cnt.cpu().numpy().view(np.uint64)
+        out[name] = int(c[0]) / (a.elapsed_time(e) / 1e3)
+        if prec == N.FP32_LOCAL:
+            out["fp32local_close_call_fraction"] = float(c[10]) / max(1, int(c[0]))
+        else:
+            out["segments_per_particle"] = int(c[0]) / (n * steps)
+        del work
+    out["fp32local_over_fp64"] = out["csg_fp32local_event"] / out["csg_fp64_event"]
+    out["csg_over_array"] = out["csg_fp64_event"] / out["array_fp64_event"]
+    return out
 
 
 def run_config5(N, I, dev, stream, barrier, steps):

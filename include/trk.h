@@ -49,6 +49,12 @@ typedef enum {
     TRK_E_SOURCE = -9         /* source rejection sampling exceeded its cap */
 } trk_status;
 
+/* Trackers.  RECT: the array tracker (static dispatch per universe type):
+ * rect arrays by index (Alg. 5/6/9/10), hex arrays by a closed-form
+ * element search checked against the element's pseudo-array cell (the paper
+ * gives no hex array tracker; results are those of the pseudo-array scan),
+ * CSG universes by search.  CSG: every array as its pseudo-array, searched
+ * through a BVH of cell boxes (Sec. 4.3).  AUTO: RECT. */
 enum { TRK_TRACKER_RECT = 0, TRK_TRACKER_CSG = 1, TRK_TRACKER_AUTO = 2 };
 enum { TRK_MODE_HISTORY = 0, TRK_MODE_EVENT = 1 };
 enum { TRK_FP64 = 0, TRK_FP32_LOCAL = 1 };
@@ -125,7 +131,7 @@ trk_status geometry_build(const char* json, size_t len, void* dev_buf, size_t* d
 trk_status geometry_destroy(trk_geom_t g);
 
 /* Sizes of a built geometry: leaf cell instances (tally bins), materials,
- * maximum nesting depth, and whether the rect tracker applies (no hex arrays). */
+ * maximum nesting depth, and whether the array tracker applies (always 1). */
 trk_status geometry_info(trk_geom_t g, int64_t* n_instances, int32_t* n_materials,
                          int32_t* max_depth, int32_t* rect_ok);
 
@@ -162,8 +168,8 @@ trk_status run_histories_work_bytes(trk_geom_t g, int64_t n, const trk_run_opts*
  *                  (segments << 32) | (uint32)status}; NULL to skip.
  *   dev_work       scratch of run_histories_work_bytes (256-byte aligned).
  *   opts           NULL = defaults.
- * Errors: TRK_E_INVALID, TRK_E_UNSUPPORTED (rect tracker on hex arrays,
- * FP32-local in event mode), TRK_E_NOMEM, TRK_E_CUDA.
+ * Errors: TRK_E_INVALID, TRK_E_UNSUPPORTED (FP32-local in the exact build,
+ * FP32-local with a path cutoff), TRK_E_NOMEM, TRK_E_CUDA.
  */
 trk_status run_histories(trk_geom_t g, const void* dev_particles, int64_t n, uint64_t* dev_tally,
                          uint64_t* dev_counters, uint64_t* dev_records, void* dev_work,
@@ -231,7 +237,7 @@ trk_status transmission_bwd(trk_geom_t g, int tracker, int64_t n, const double* 
  *   dev_tallies[k]    its tally (uint64[n_instances of geometry k]),
  *   dev_counters      uint64[n_geom * TRK_NCOUNTERS], geometry k at k*16,
  *   dev_records       NULL or per-geometry record arrays (as run_histories),
- *   tracker           TRK_TRACKER_AUTO (rect where possible), _RECT or _CSG.
+ *   tracker           TRK_TRACKER_AUTO (the array tracker), _RECT or _CSG.
  * Tallies and counters are added to, not cleared.  Particle ids restart at
  * first_id for every geometry (each geometry keys its own random numbers
  * with its geometry id).  The pointer arrays are host memory, read here.

@@ -25,7 +25,7 @@ _SRC = os.path.join(_HERE, "oracle.cpp")
 _LOCK = threading.Lock()
 _LIBS: dict = {}
 
-MODE_RECT = 0   # array universes tracked by the rect tracker (Alg. 5/6)
+MODE_RECT = 0   # rect arrays tracked by index (Alg. 5/6); hex arrays as pseudo-arrays
 MODE_CSG = 1    # every universe a CSG universe; arrays become pseudo-arrays (Sec. 4.3)
 
 # counters (same meaning as the library's device counters)

@@ -508,12 +508,14 @@ static Geometry* load_geometry(const char* json, size_t len, int mode, std::stri
     }
     if (count_instances(*g, g->root, 0, err) < 0) return nullptr;
     g->max_depth = depth_of(*g, g->root);
-    if (mode == 1) {
-        for (int u = 0; u < int(g->univ.size()); ++u)
-            if (g->univ[u].type != U_CSG) to_pseudo_array(*g, u, u == g->root);
-    } else {
-        for (auto& U : g->univ)
-            if (U.type == U_HEX) { err = "the rect tracker has no hex array tracker; use the CSG tracker"; return nullptr; }
+    // CSG mode: every array as its pseudo-array.  Rect mode: rect arrays by
+    // index (Alg. 5/6/9/10); hex arrays, for which the paper gives no array
+    // tracker, as their pseudo-arrays (the array tracker's closed-form hex
+    // search must return the cell this scan returns).
+    for (int u = 0; u < int(g->univ.size()); ++u) {
+        const int t = g->univ[u].type;
+        if (t == U_CSG) continue;
+        if (mode == 1 || t == U_HEX) to_pseudo_array(*g, u, u == g->root);
     }
     return g.release();
 }

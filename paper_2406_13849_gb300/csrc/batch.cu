@@ -457,7 +457,7 @@ trk_status batch_create(const trk_geom_t* geoms, int n_geom, const void* const* 
         }
         if (tracker == TRK_TRACKER_RECT && !g->rect_ok) {
             delete b;
-            return trk_status(set_error(TRK_E_UNSUPPORTED, "batch_create: entry %d has hex arrays (no rect tracker)", k));
+            return trk_status(set_error(TRK_E_UNSUPPORTED, "batch_create: entry %d: array tracker not available", k));
         }
         idx[size_t(k)] = k;
     }

@@ -338,7 +338,6 @@ int parse(const char* json, size_t len, HGeom& G) {
             if (num(J, uo, "pscale", x)) U.pscale = int(x);
         } else if (t == "hex") {
             U.type = UT_HEX;
-            G.rect_ok = false;
             std::vector<double> a1, a2, zz;
             double rings, hp;
             if (!num(J, uo, "rings", rings) || rings < 0 || rings > 64 || !read_nums(J, J.member(uo, "a1"), a1) ||
@@ -348,6 +347,7 @@ int parse(const char* json, size_t len, HGeom& G) {
             U.rings = int(rings);
             U.a1[0] = a1[0]; U.a1[1] = a1[1]; U.a2[0] = a2[0]; U.a2[1] = a2[1];
             U.z[0] = zz[0]; U.z[1] = zz[1]; U.hp = hp;
+            if (!(std::fabs(a1[0] * a2[1] - a2[0] * a1[1]) > 0)) DESC_FAIL("universe %d: hex lattice vectors are parallel", ui);
             int nl = J.member(uo, "normals");
             if (nl < 0 || J.at(nl).t != 'a' || J.at(nl).kids.size() != 3) DESC_FAIL("universe %d: hex needs 3 normals", ui);
             for (int k = 0; k < 3; ++k) {
@@ -822,7 +822,11 @@ int build_host(const char* json, size_t len, Built& B) {
     const int nu = int(G.univ.size());
     std::vector<int> lat_of(size_t(nu), -1);
     int nlat = 0;
-    for (int u = 0; u < nu; ++u) if (G.univ[size_t(u)].type == UT_RECT) lat_of[size_t(u)] = nlat++;
+    int nhex = 0;
+    for (int u = 0; u < nu; ++u) {
+        if (G.univ[size_t(u)].type == UT_RECT) lat_of[size_t(u)] = nlat++;
+        else if (G.univ[size_t(u)].type == UT_HEX) lat_of[size_t(u)] = -2 - nhex++;
+    }
     for (int u = 0; u < nu; ++u) {
         HUniv& U = G.univ[size_t(u)];
         if (U.type == UT_HEX && u == G.root && U.bc[0] == BC_REFLECT)
@@ -1019,6 +1023,29 @@ int build_host(const char* json, size_t len, Built& B) {
         l_pscale.push_back(U.pscale);
     }
     if (l_dim.empty()) { l_dim.push_back(make_int4(0, 0, 0, 0)); l_off.push_back(make_int4(0, 0, 0, 0)); l_pscale.push_back(0); }
+    // hex lattices (array tracker): inverse lattice matrix and row starts
+    std::vector<HexInfo> hx;
+    std::vector<int> hx_row;
+    for (auto& U : G.univ) {
+        if (U.type != UT_HEX) continue;
+        HexInfo h;
+        std::memset(&h, 0, sizeof h);
+        const double det = U.a1[0] * U.a2[1] - U.a2[0] * U.a1[1];
+        h.i00 = U.a2[1] / det; h.i01 = -U.a2[0] / det;
+        h.i10 = -U.a1[1] / det; h.i11 = U.a1[0] / det;
+        h.rings = U.rings;
+        h.first_cell = U.first_cell;
+        h.row = int(hx_row.size());
+        const int R = U.rings;
+        int e = 0;
+        for (int r = -R; r <= R; ++r) {
+            hx_row.push_back(e);
+            e += std::min(R, R - r) - std::max(-R, -R - r) + 1;
+        }
+        hx.push_back(h);
+    }
+    if (hx.empty()) { HexInfo h; std::memset(&h, 0, sizeof h); hx.push_back(h); }
+    if (hx_row.empty()) hx_row.push_back(0);
     if (l_grid.empty()) { l_grid.push_back(0); l_ctr.push_back(0); l_gkey.push_back(0); l_lof.push_back(0); l_hif.push_back(0); }
     if (c_slabf.empty()) c_slabf.push_back(0);
     if (l_fill.empty()) { l_fill.push_back(0); l_eoff.push_back(0); }
@@ -1066,6 +1093,8 @@ int build_host(const char* json, size_t len, Built& B) {
     if (rest_e.empty()) rest_e.push_back(0);
     o[30] = L.put(c_rest.size() * sizeof(int2));
     o[31] = L.put(rest_e.size() * 4);
+    o[32] = L.put(hx.size() * sizeof(HexInfo));
+    o[33] = L.put(hx_row.size() * 4);
     B.image.assign(L.total, 0);
     copy_into(B.image, o[0], s_info);
     copy_into(B.image, o[1], s_coef);
@@ -1099,6 +1128,8 @@ int build_host(const char* json, size_t len, Built& B) {
     copy_into(B.image, o[29], c_fcls);
     copy_into(B.image, o[30], c_rest);
     copy_into(B.image, o[31], rest_e);
+    copy_into(B.image, o[32], hx);
+    copy_into(B.image, o[33], hx_row);
     return TRK_OK;
 }
 
@@ -1183,6 +1214,8 @@ trk_status geometry_build(const char* json, size_t len, void* dev_buf, size_t* d
     d.c_fcls = reinterpret_cast<const int*>(base + o[29]);
     d.c_rest = reinterpret_cast<const int2*>(base + o[30]);
     d.rest_e = reinterpret_cast<const int*>(base + o[31]);
+    d.hx = reinterpret_cast<const HexInfo*>(base + o[32]);
+    d.hx_row = reinterpret_cast<const int*>(base + o[33]);
     const HGeom& G = B.G;
     for (int k = 0; k < 3; ++k) { d.src_lo[k] = G.src[k]; d.src_hi[k] = G.src[3 + k]; }
     d.root = G.root;

@@ -496,6 +496,39 @@ __device__ __forceinline__ int enter_cell(const DevGeom& g, Lv& L, int c) {
     return __ldg(g.c_fill + c);
 }
 
+// Array tracker, hex lattice h of universe u: the element holding the point
+// by closed form.  Axial coordinates from the inverse lattice matrix, cube
+// rounding to the nearest element, then the exact test of that element's
+// pseudo-array cell (its face planes' senses, as the CSG search evaluates
+// them) and of its six neighbours; if none holds, the universe search.  In a
+// lattice whose cells partition its region the holding cell is unique, so
+// this returns what the pseudo-array scan returns.
+__device__ __forceinline__ int hex_find(const DevGeom& g, int h, int u, const Pt& p) {
+    const double2* hp = reinterpret_cast<const double2*>(g.hx + h);
+    const double2 m0 = __ldg(hp), m1 = __ldg(hp + 1);
+    const int4 hi = __ldg(reinterpret_cast<const int4*>(g.hx + h) + 2);
+    const int R = hi.x;
+    const double qf = m0.x * p.x + m0.y * p.y, rf = m1.x * p.x + m1.y * p.y;
+    const double sf = -qf - rf;
+    double qr = rint(qf), rr = rint(rf);
+    const double sr = rint(sf);
+    const double dq = fabs(qr - qf), dr = fabs(rr - rf), ds = fabs(sr - sf);
+    if (dq > dr && dq > ds) qr = -rr - sr;
+    else if (dr > ds) rr = -qr - sr;
+    const int q0 = int(qr), r0 = int(rr);
+#pragma unroll 1
+    for (int k = 0; k < 7; ++k) {
+        // the candidate, then its neighbours (q+1, q-1, r+1, r-1, (q+1, r-1), (q-1, r+1))
+        const int q = q0 + (k == 1 || k == 5 ? 1 : (k == 2 || k == 6 ? -1 : 0));
+        const int r = r0 + (k == 3 || k == 6 ? 1 : (k == 4 || k == 5 ? -1 : 0));
+        if (max(abs(q), max(abs(r), abs(q + r))) > R) continue;
+        const int e = __ldg(g.hx_row + hi.z + r + R) + q - max(-R, -R - r);
+        const int c = hi.y + e;
+        if (cell_holds(g, c, p, -1, 0)) return c;
+    }
+    return csg_search(g, u, p, -1, -1, 0);
+}
+
 // Alg. 7 from level `start` downward (rect view for rect arrays unless CSG).
 // Returns 0 on success, -1 if no cell holds the point.
 template <bool CSG>
@@ -518,7 +551,7 @@ __device__ TRK_FIND_INLINE int find_from(const DevGeom& g, St& s, int start) {
             if (i < 0 || j < 0 || k < 0) return -1;
             dau = enter_element(g, L, ui.w, i, j, k);
         } else {
-            const int c = csg_search(g, L.u, p, -1, -1, 0);
+            const int c = (!CSG && ui.w <= -2) ? hex_find(g, -2 - ui.w, L.u, p) : csg_search(g, L.u, p, -1, -1, 0);
             if (c < 0) return -1;
             dau = enter_cell(g, L, c);
         }

@@ -42,6 +42,15 @@ struct alignas(16) BvhNode {
     float lo1[3], hi1[3];
     int ref0, ref1, pad0, pad1;
 };
+// Hex lattice for the array tracker's closed-form search: the inverse of
+// the lattice-vector matrix (axial q, r from the universe-frame x, y), the
+// ring count, the first pseudo-array cell (elements in order: rows
+// r = -R..R, q ascending) and the offset of its row-start table in hx_row.
+struct alignas(16) HexInfo {
+    double i00, i01, i10, i11;
+    int rings, first_cell, row, pad;
+};
+
 // Largest BVH depth the builder produces (the walk's stack size).
 constexpr int BVH_STACK = 64;
 
@@ -83,7 +92,10 @@ struct DevGeom {
     const double* c_tr;       // translation into the daughter, 3 per cell
     const int* c_off;         // leaf-instance offset of the cell
     // universes
-    const int4* u_info;       // (first cell, cell count, BVH root node or -1, rect lattice or -1)
+    const int4* u_info;       // (first cell, cell count, BVH root node or -1, rect lattice >= 0,
+                              //  hex lattice -2 - h, or -1)
+    const HexInfo* hx;        // hex lattices (array tracker)
+    const int* hx_row;        // per hex lattice: first element of row r at hx_row[row + r + rings]
     // rect arrays (rect view)
     const int4* l_dim;        // (nx, ny, nz, packed bc: 2 bits per face xlo..zhi)
     const int4* l_off;        // (x grid offset, y grid offset, z grid offset, element offset)
@@ -106,7 +118,7 @@ struct DevGeom {
     const double* sigma;
     double src_lo[3], src_hi[3];
     int root, n_inst, n_mat, gid, max_depth, n_univ, n_cells, n_surf;
-    int rect_ok;              // no hex arrays: the rect tracker applies
+    int rect_ok;              // the array tracker applies (always 1: hex arrays by closed-form search)
 };
 
 // Order key of a double: a < b  <=>  okey(a) < okey(b) for non-NaN values,

@@ -396,7 +396,7 @@ int resolve_tracker(trk_geom_t g, int tracker, trk_status* st) {
     *st = TRK_OK;
     if (tracker == TRK_TRACKER_AUTO) return g->rect_ok ? TRK_TRACKER_RECT : TRK_TRACKER_CSG;
     if (tracker == TRK_TRACKER_RECT && !g->rect_ok) {
-        *st = trk_status(set_error(TRK_E_UNSUPPORTED, "rect tracker requested on a geometry with hex arrays"));
+        *st = trk_status(set_error(TRK_E_UNSUPPORTED, "array tracker not available for this geometry"));
         return -1;
     }
     if (tracker != TRK_TRACKER_RECT && tracker != TRK_TRACKER_CSG) {

@@ -475,7 +475,7 @@ def random_tiny(seed: int) -> dict:
 
 def small_hex(rings=2, pitch=1.0, r_pin=0.4, height=5.0, rot30=False, bc="vacuum",
               sigma=(0.6, 0.2)):
-    """Root hex lattice of 2-cell pins (CSG tracker only)."""
+    """Root hex lattice of 2-cell pins."""
     a1, a2, nrm = _hex_frame(pitch, rot30=rot30)
     S = [{"type": "cz", "coef": [0.0, 0.0, r_pin]}]
     pin = {"type": "csg", "cells": [{"surfaces": [[0, -1]], "material": 0},

@@ -85,9 +85,7 @@ def test_find_cell_exact(name):
     pts = lo + np.random.default_rng(3).uniform(0, 1, (20_000, 3)) * (hi - lo)
     g = _gpu(desc, exact=True)
     xyz = torch.from_numpy(pts).cuda()
-    trackers = [(N.TRACKER_CSG, O.MODE_CSG)]
-    if name in CASES:
-        trackers.append((N.TRACKER_RECT, O.MODE_RECT))
+    trackers = [(N.TRACKER_CSG, O.MODE_CSG), (N.TRACKER_RECT, O.MODE_RECT)]
     for tr, mode in trackers:
         ref = _oracle(desc, mode).find_cell(pts)
         got = g.find_cell(xyz, tracker=tr).cpu().numpy()
@@ -126,9 +124,51 @@ def test_histories_bit_exact(name, tracker, mode):
 
 
 @pytest.mark.parametrize("name", list(HEX_CASES))
-def test_histories_bit_exact_hex(name):
+@pytest.mark.parametrize("tracker,mode", [(N.TRACKER_RECT, O.MODE_RECT), (N.TRACKER_CSG, O.MODE_CSG)])
+def test_histories_bit_exact_hex(name, tracker, mode):
+    # the array tracker on hex arrays: closed-form element search, checked
+    # against the oracle's pseudo-array scan
     desc, pa, n = HEX_CASES[name]
-    _compare_exact(desc, pa, n, N.TRACKER_CSG, O.MODE_CSG)
+    _compare_exact(desc, pa, n, tracker, mode)
+
+
+@pytest.mark.parametrize("name", list(HEX_CASES))
+def test_hex_array_and_csg_trackers_identical(name):
+    # same histories from the closed-form hex search and the BVH search,
+    # history and event kernels (exact build)
+    desc, pa, n = HEX_CASES[name]
+    g = _gpu(desc, exact=True)
+    res = []
+    for tr in (N.TRACKER_RECT, N.TRACKER_CSG):
+        for mode in (N.MODE_HISTORY, N.MODE_EVENT):
+            _, tally, cnt, rec = _run_gpu(g, n, pa, tr, mode=mode)
+            res.append((tally, _u64(rec)))
+    for t, r in res[1:]:
+        assert np.array_equal(t, res[0][0]) and np.array_equal(r, res[0][1])
+
+
+def test_hex_find_points_on_faces():
+    # points on element faces and vertices of a hex lattice (the + side of a
+    # face holds it): the closed-form search against the oracle's scan
+    desc = I.small_hex(rings=3, rot30=True)
+    g = _gpu(desc, exact=True)
+    hp = 0.5
+    pts = []
+    rng = np.random.default_rng(11)
+    a1, a2, nrm = I._hex_frame(1.0, rot30=True)
+    for q in range(-3, 4):
+        for r in range(-3, 4):
+            cx, cy = q * a1[0] + r * a2[0], q * a1[1] + r * a2[1]
+            for k in range(3):
+                for sgn in (-1, 1):
+                    nx, ny = nrm[k]
+                    t = rng.uniform(-0.2, 0.2)
+                    # face midpoint plus a shift along the face
+                    pts.append([cx + sgn * hp * nx - t * ny, cy + sgn * hp * ny + t * nx, 1.0])
+    pts = np.array(pts)
+    ref = _oracle(desc, O.MODE_RECT).find_cell(pts)
+    got = g.find_cell(torch.from_numpy(pts).cuda(), tracker=N.TRACKER_RECT).cpu().numpy()
+    assert np.array_equal(got, ref)
 
 
 def test_segment_cap_and_cutoff_exact():
@@ -269,9 +309,11 @@ def test_edge_cases():
     assert g.lib.tally_read(g.h, N._ptr(tally), None, g.n_inst, None, None) == -1
     hexg = _gpu(I.small_hex(), exact=False)
     p = hexg.source_init(10)
+    assert hexg.rect_ok   # the array tracker runs hex arrays (closed-form search)
+    hexg.run_histories(p, 10, tracker=N.TRACKER_RECT)
     with pytest.raises(N.TrkError) as e:
-        hexg.run_histories(p, 10, tracker=N.TRACKER_RECT)
-    assert e.value.code == -8
+        hexg.run_histories(p, 10, tracker=7)
+    assert e.value.code == -1
     with pytest.raises(N.TrkError) as e:
         g.run_histories(parts, 1, p_absorb=1.5)
     assert e.value.code == -1

@@ -334,8 +334,16 @@ def test_bad_descriptions_rejected():
         _geom(d)
     with pytest.raises(ValueError):
         O.Geometry("{not json", O.MODE_RECT)
-    with pytest.raises(ValueError):
-        _geom(I.config3(), O.MODE_RECT)   # no rect tracker for hex arrays
+
+
+def test_rect_mode_tracks_hex_arrays_as_pseudo_arrays():
+    # the rect-mode oracle keeps rect arrays by index and turns hex arrays
+    # into pseudo-arrays: on hex geometries (two and three hex levels) it
+    # must agree with CSG mode, as on a rect geometry
+    for d in (I.small_hex_core(), I.config4_member(1)[0], I.config4_member(4)[0]):
+        a = _geom(d, O.MODE_RECT).run(300, 1, 0.3, threads=4)
+        b = _geom(d, O.MODE_CSG).run(300, 1, 0.3, threads=4)
+        assert np.array_equal(a["hash"], b["hash"]) and np.array_equal(a["tally"], b["tally"])
 
 
 # ---------------------------------------------------------------------------
