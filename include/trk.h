@@ -54,7 +54,8 @@ typedef enum {
  * element search checked against the element's pseudo-array cell (the paper
  * gives no hex array tracker; results are those of the pseudo-array scan),
  * CSG universes by search.  CSG: every array as its pseudo-array, searched
- * through a BVH of cell boxes (Sec. 4.3).  AUTO: RECT. */
+ * through a BVH of cell boxes (Sec. 4.3).  AUTO: RECT, or CSG for a geometry
+ * with hex arrays (measured as fast or faster there). */
 enum { TRK_TRACKER_RECT = 0, TRK_TRACKER_CSG = 1, TRK_TRACKER_AUTO = 2 };
 enum { TRK_MODE_HISTORY = 0, TRK_MODE_EVENT = 1 };
 enum { TRK_FP64 = 0, TRK_FP32_LOCAL = 1 };
@@ -237,7 +238,7 @@ trk_status transmission_bwd(trk_geom_t g, int tracker, int64_t n, const double* 
  *   dev_tallies[k]    its tally (uint64[n_instances of geometry k]),
  *   dev_counters      uint64[n_geom * TRK_NCOUNTERS], geometry k at k*16,
  *   dev_records       NULL or per-geometry record arrays (as run_histories),
- *   tracker           TRK_TRACKER_AUTO (the array tracker), _RECT or _CSG.
+ *   tracker           TRK_TRACKER_AUTO (as run_histories), _RECT or _CSG.
  * Tallies and counters are added to, not cleared.  Particle ids restart at
  * first_id for every geometry (each geometry keys its own random numbers
  * with its geometry id).  The pointer arrays are host memory, read here.

@@ -463,7 +463,7 @@ trk_status batch_create(const trk_geom_t* geoms, int n_geom, const void* const* 
     }
     auto use_csg = [&](int k) {
         if (tracker == TRK_TRACKER_CSG) return true;
-        return !geoms[k]->rect_ok;
+        return !geoms[k]->rect_ok || geoms[k]->has_hex != 0;
     };
     // rect-tracker geometries first, larger populations first within a type
     std::stable_sort(idx.begin(), idx.end(), [&](int a, int c) {

@@ -893,6 +893,7 @@ int build_host(const char* json, size_t len, Built& B) {
     std::vector<longlong2> c_slabk;
     std::vector<int> cs, c_fill, c_off, c_fcls, rest_e;
     std::vector<int2> c_rest;
+    std::vector<int4> c_pair;
     std::vector<double> c_tr;
     std::vector<int4> u_info;
     for (auto& U : G.univ) {
@@ -942,18 +943,48 @@ int build_host(const char* json, size_t len, Built& B) {
                 if (slab[slot] >= 0) { fits = false; break; }
                 slab[slot] = first_entry + int(i);
             }
-            // a cell with no axis plane at all (a pin cell bounded by
-            // cylinders) keeps the plain entry loop
-            if (rest.size() == c.surf.size()) fits = false;
+            // plane pairs: general planes with one normal (exactly equal
+            // coefficients), at most one "+" and one "-" entry each (the two
+            // faces of a hex element across one face family); up to three
+            int pair[6] = {-1, -1, -1, -1, -1, -1};
+            int npair = 0;
+            if (fits) {
+                std::vector<int> keep;
+                for (int e : rest) {
+                    const HSurf& sf = G.surf[size_t(c.surf[size_t(e - first_entry)])];
+                    const int sense = c.sense[size_t(e - first_entry)];
+                    if (sf.type != S_P) { keep.push_back(e); continue; }
+                    int f = 0;
+                    for (; f < npair; ++f) {
+                        const int e0 = pair[2 * f] >= 0 ? pair[2 * f] : pair[2 * f + 1];
+                        const HSurf& s0 = G.surf[size_t(c.surf[size_t(e0 - first_entry)])];
+                        if (s0.c[0] == sf.c[0] && s0.c[1] == sf.c[1] && s0.c[2] == sf.c[2]) break;
+                    }
+                    const int slot = sense > 0 ? 0 : 1;
+                    if (f < npair && pair[2 * f + slot] < 0) { pair[2 * f + slot] = e; continue; }
+                    if (f == npair && npair < 3) { pair[2 * f + slot] = e; ++npair; continue; }
+                    keep.push_back(e);
+                }
+                rest.swap(keep);
+            }
+            // a cell with neither axis planes nor plane pairs (a pin cell
+            // bounded by cylinders) keeps the plain entry loop
+            bool any_axis = false;
+            for (int k = 0; k < 6; ++k) any_axis |= slab[k] >= 0;
+            if (!any_axis && npair == 0) fits = false;
             if (!fits) {
-                for (int k = 0; k < 6; ++k) slab[k] = -1;
+                for (int k = 0; k < 6; ++k) slab[k] = pair[k] = -1;
+                npair = 0;
                 rest.clear();
                 c_rest.push_back(make_int2(int(rest_e.size()), 0));
             } else {
                 c_range.back().y |= CS_SLAB_FLAG;
+                if (npair > 0) c_range.back().y |= CS_PAIR_FLAG;
                 c_rest.push_back(make_int2(int(rest_e.size()), int(rest.size())));
                 rest_e.insert(rest_e.end(), rest.begin(), rest.end());
             }
+            c_pair.push_back(make_int4(pair[0], pair[1], pair[2], pair[3]));
+            c_pair.push_back(make_int4(pair[4], pair[5], -1, -1));
             for (int k = 0; k < 6; ++k) {
                 const int e = slab[k];
                 c_slabf.push_back(e >= 0 ? float(G.surf[size_t(c.surf[size_t(e - first_entry)])].c[0] - c.tr[k / 2]) : 0.f);
@@ -1095,6 +1126,8 @@ int build_host(const char* json, size_t len, Built& B) {
     o[31] = L.put(rest_e.size() * 4);
     o[32] = L.put(hx.size() * sizeof(HexInfo));
     o[33] = L.put(hx_row.size() * 4);
+    if (c_pair.empty()) { c_pair.push_back(make_int4(-1, -1, -1, -1)); c_pair.push_back(make_int4(-1, -1, -1, -1)); }
+    o[34] = L.put(c_pair.size() * sizeof(int4));
     B.image.assign(L.total, 0);
     copy_into(B.image, o[0], s_info);
     copy_into(B.image, o[1], s_coef);
@@ -1130,6 +1163,7 @@ int build_host(const char* json, size_t len, Built& B) {
     copy_into(B.image, o[31], rest_e);
     copy_into(B.image, o[32], hx);
     copy_into(B.image, o[33], hx_row);
+    copy_into(B.image, o[34], c_pair);
     return TRK_OK;
 }
 
@@ -1216,6 +1250,7 @@ trk_status geometry_build(const char* json, size_t len, void* dev_buf, size_t* d
     d.rest_e = reinterpret_cast<const int*>(base + o[31]);
     d.hx = reinterpret_cast<const HexInfo*>(base + o[32]);
     d.hx_row = reinterpret_cast<const int*>(base + o[33]);
+    d.c_pair = reinterpret_cast<const int4*>(base + o[34]);
     const HGeom& G = B.G;
     for (int k = 0; k < 3; ++k) { d.src_lo[k] = G.src[k]; d.src_hi[k] = G.src[3 + k]; }
     d.root = G.root;
@@ -1234,6 +1269,7 @@ trk_status geometry_build(const char* json, size_t len, void* dev_buf, size_t* d
     h->n_mat = d.n_mat;
     h->depth = d.max_depth;
     h->rect_ok = d.rect_ok;
+    for (auto& U : G.univ) h->has_hex |= U.type == UT_HEX ? 1 : 0;
     h->n_nodes = B.n_nodes;
     h->magic = TRK_GEOM_MAGIC;
     *out = h;

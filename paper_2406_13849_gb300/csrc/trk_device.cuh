@@ -254,7 +254,30 @@ __device__ __forceinline__ double surface_distance(const DevGeom& g, int s, int 
 
 // Cell test: all senses hold; the crossed surface xs (if >= 0) is taken
 // logically with sense xsn instead of being evaluated.
-__device__ __forceinline__ bool cell_holds(const DevGeom& g, int c, const Pt& p, int xs, int xsn) {
+// The plane-pair part of the cell test, out of line: only cells with
+// general planes (hex elements) call it, and the kernels of geometries
+// without them keep a smaller instruction footprint.
+static __device__ __noinline__ bool pairs_hold(const DevGeom& g, int c, const Pt& p, int xs, int xsn) {
+    const int4 p0 = __ldg(g.c_pair + 2 * c), p1 = __ldg(g.c_pair + 2 * c + 1);
+    const int pe[6] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y};
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        if (pe[k] < 0) continue;
+        const int e = __ldg(g.cs + pe[k]);
+        const int sf = cs_surface(e), sn = cs_side(e);
+        if (sf == xs) {
+            if (sn != xsn) return false;
+        } else if (sense_at(g, sf, S_P, p) != sn) {
+            return false;
+        }
+    }
+    return true;
+}
+
+#ifndef TRK_HOLDS_INLINE
+#define TRK_HOLDS_INLINE __forceinline__
+#endif
+static __device__ TRK_HOLDS_INLINE bool cell_holds(const DevGeom& g, int c, const Pt& p, int xs, int xsn) {
     const int2 rg = __ldg(g.c_range + c);
     if (rg.y & CS_SLAB_FLAG) {
         // slab view: per dimension x >= g_lo ("+" side of the lower face) and
@@ -274,6 +297,7 @@ __device__ __forceinline__ bool cell_holds(const DevGeom& g, int c, const Pt& p,
             ok = ok && lo_ok && hi_ok;
         }
         if (!ok) return false;
+        if ((rg.y & CS_PAIR_FLAG) && !pairs_hold(g, c, p, xs, xsn)) return false;
         const int2 rr = __ldg(g.c_rest + c);
         for (int k = 0; k < rr.y; ++k) {
             const int e = __ldg(g.cs + __ldg(g.rest_e + rr.x + k));
@@ -673,10 +697,38 @@ __device__ __forceinline__ Hit distance_to_boundary(const DevGeom& g, const St& 
                         c.dim = -1; c.dsign = 0; c.entry = e;
                     }
                 }
+                if (rg.y & CS_PAIR_FLAG) {
+                    // plane pairs: per pair the one face the direction leaves
+                    // through (n.u < 0: the "+" entry), the S_P distance of
+                    // surface_distance
+                    const int4 p0 = __ldg(g.c_pair + 2 * L.cell), p1 = __ldg(g.c_pair + 2 * L.cell + 1);
+                    const int lo3p[3] = {p0.x, p0.z, p1.x};
+                    const int hi3p[3] = {p0.y, p0.w, p1.y};
+#pragma unroll
+                    for (int f = 0; f < 3; ++f) {
+                        const int ea = lo3p[f] >= 0 ? lo3p[f] : hi3p[f];
+                        if (ea < 0) continue;
+                        double c0, c1, c2, c3;
+                        load_coef(g, cs_surface(__ldg(g.cs + ea)), c0, c1, c2, c3);
+                        const double den = (c0 * s.d.u + c1 * s.d.v) + c2 * s.d.w;
+                        const int e = d_lt0(den) ? lo3p[f] : (d_gt0(den) ? hi3p[f] : -1);
+                        if (e < 0) continue;
+                        const int sid = cs_surface(__ldg(g.cs + e));
+                        if (s.on_lev == l && s.on_surf == sid) continue;
+                        const double d3c = __ldg(g.s_coef + 4 * sid + 3);
+                        double t = (d3c - ((c0 * x + c1 * y) + c2 * z)) / den;
+                        if (d_lt0(t)) t = 0.0;
+                        const long long tk = okey(t);
+                        if (tk < ck || (tk == ck && c.level >= 0 && e < c.entry)) {
+                            ck = tk; c.d = t; c.level = l; c.surf = sid; c.side = d_lt0(den) ? 1 : -1;
+                            c.dim = -1; c.dsign = 0; c.entry = e;
+                        }
+                    }
+                }
                 const int2 rr = __ldg(g.c_rest + L.cell);
                 first = rr.x; cnt = rr.y; ents = g.rest_e; by_index = true;
             }
-            // remaining entries (all of them for a cell without a slab view)
+            // remaining entries (all of them for a cell without a view)
             for (int k = 0; k < cnt; ++k) {
                 const int ei = by_index ? __ldg(ents + first + k) : first + k;
                 const int e = __ldg(g.cs + ei);
@@ -847,6 +899,26 @@ __device__ __forceinline__ Best2 distance_f32(const DevGeom& g, const St& s, con
                     const float t = (__ldg(fs + 2 * d + (up ? 1 : 0)) - e3[d]) * v3[d];
                     b.offer(t < 0.f ? 0.f : t, l, sid, up ? -1 : 1, -1, 0, e, x, y, z);
                 }
+                if (rg.y & CS_PAIR_FLAG) {
+                    const float xf = float(x), yf = float(y), zf = float(z);
+                    const int4 p0 = __ldg(g.c_pair + 2 * L.cell), p1 = __ldg(g.c_pair + 2 * L.cell + 1);
+                    const int lo3p[3] = {p0.x, p0.z, p1.x};
+                    const int hi3p[3] = {p0.y, p0.w, p1.y};
+#pragma unroll
+                    for (int f = 0; f < 3; ++f) {
+                        const int ea = lo3p[f] >= 0 ? lo3p[f] : hi3p[f];
+                        if (ea < 0) continue;
+                        const float4 cf = __ldg(g.s_coeff + cs_surface(__ldg(g.cs + ea)));
+                        const float den = (cf.x * df.u + cf.y * df.v) + cf.z * df.w;
+                        const int e = den < 0.f ? lo3p[f] : (den > 0.f ? hi3p[f] : -1);
+                        if (e < 0) continue;
+                        const int sid = cs_surface(__ldg(g.cs + e));
+                        if (s.on_lev == l && s.on_surf == sid) continue;
+                        const float dw = __ldg(g.s_coeff + sid).w;
+                        const float t = (dw - ((cf.x * xf + cf.y * yf) + cf.z * zf)) / den;
+                        b.offer(t < 0.f ? 0.f : t, l, sid, den < 0.f ? 1 : -1, -1, 0, e, x, y, z);
+                    }
+                }
                 const int2 rr = __ldg(g.c_rest + L.cell);
                 first = rr.x; cnt = rr.y; by_index = true;
             }
@@ -901,8 +973,11 @@ __device__ __forceinline__ int csg_cross_search(const DevGeom& g, int u, int cel
                                                 int entry) {
     if (entry >= 0) {
         const int2 adj = __ldg(g.cs_adj + entry);
-        if (adj.x >= 0 && cell_holds(g, adj.x, p, xs, xsn)) return adj.x;
-        if (adj.y >= 0 && cell_holds(g, adj.y, p, xs, xsn)) return adj.y;
+#pragma unroll 1
+        for (int k = 0; k < 2; ++k) {
+            const int cand = k == 0 ? adj.x : adj.y;
+            if (cand >= 0 && cell_holds(g, cand, p, xs, xsn)) return cand;
+        }
     }
     return csg_search(g, u, p, cell, xs, xsn);
 }

@@ -55,10 +55,13 @@ struct alignas(16) HexInfo {
 constexpr int BVH_STACK = 64;
 
 // c_range count field: low bits count, CS_SLAB_FLAG marks a cell with a
-// slab view: at most one lower and one upper axis plane per dimension (its
-// other surfaces are the cell's remaining entries, c_rest / rest_e).
+// view: at most one lower and one upper axis plane per dimension, up to
+// three pairs of general planes with one normal (CS_PAIR_FLAG), and the
+// other surfaces as the cell's remaining entries (c_rest / rest_e).
 constexpr int CS_SLAB_FLAG = 1 << 30;
-constexpr int CS_COUNT_MASK = CS_SLAB_FLAG - 1;
+// CS_PAIR_FLAG: the view also has plane pairs (c_pair).
+constexpr int CS_PAIR_FLAG = 1 << 29;
+constexpr int CS_COUNT_MASK = CS_PAIR_FLAG - 1;
 
 // Packed cell-surface entry: (surface << 4) | (type << 1) | (sense > 0).
 TRK_HD_INLINE int cs_surface(int e) { return e >> 4; }
@@ -86,6 +89,9 @@ struct DevGeom {
     const int2* c_rest;       // slab-view cells: (first, count) into rest_e, the entries that are
                               // not axis planes, in cell order
     const int* rest_e;
+    const int4* c_pair;       // view cells, 2 per cell: entries of up to three plane pairs (general
+                              // planes with one normal), (lo0, hi0, lo1, hi1), (lo2, hi2, -1, -1);
+                              // lo = the "+" entry (left when n.u < 0), hi = the "-" entry
     const int* c_fcls;        // flight class of the cell as a leaf: 0 axis planes only, 1 one
                               // cylinder (inside) and axis planes, 2 one cylinder (outside) and
                               // axis planes, 3 anything else
@@ -145,6 +151,7 @@ struct trk_geom {
     size_t bytes = 0;
     int64_t n_inst = 0;
     int n_mat = 0, depth = 0, rect_ok = 0;
+    int has_hex = 0;          // hex arrays present: TRK_TRACKER_AUTO picks the CSG tracker
     int n_nodes = 0;
     unsigned magic = 0;
 };

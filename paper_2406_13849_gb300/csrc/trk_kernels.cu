@@ -394,7 +394,10 @@ trk_status launch_error(const char* where) {
 
 int resolve_tracker(trk_geom_t g, int tracker, trk_status* st) {
     *st = TRK_OK;
-    if (tracker == TRK_TRACKER_AUTO) return g->rect_ok ? TRK_TRACKER_RECT : TRK_TRACKER_CSG;
+    // AUTO: the array tracker, except for geometries with hex arrays, where
+    // the BVH-CSG tracker measured as fast or faster (its BVH walk and the
+    // closed-form hex search cost about the same; the CSG kernels are smaller)
+    if (tracker == TRK_TRACKER_AUTO) return (g->rect_ok && !g->has_hex) ? TRK_TRACKER_RECT : TRK_TRACKER_CSG;
     if (tracker == TRK_TRACKER_RECT && !g->rect_ok) {
         *st = trk_status(set_error(TRK_E_UNSUPPORTED, "array tracker not available for this geometry"));
         return -1;
