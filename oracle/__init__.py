@@ -94,6 +94,10 @@ def _lib(counting: bool = False):
         lib.orc_log.argtypes = [_D]
         lib.orc_isotropic.argtypes = [_U, _U, _U, _U, _P]
         lib.orc_flop_counts.argtypes = [_P, _I]
+        lib.orc_run_mesh.argtypes = [_P, _LL, _LL, _ULL, _D, _I, _P, _P, _P]
+        lib.orc_mesh_segment.argtypes = [_P, _P, _P, _D, _P]
+        lib.orc_mesh_bins.restype = _LL
+        lib.orc_mesh_bins.argtypes = [_P]
         _LIBS[key] = lib
         return lib
 
@@ -117,12 +121,31 @@ class Geometry:
         self.n_inst = int(self.lib.orc_n_instances(h))
         self.n_mat = int(self.lib.orc_n_materials(h))
         self.depth = int(self.lib.orc_max_depth(h))
+        self.mesh_bins = int(self.lib.orc_mesh_bins(h))
 
     def __del__(self):
         h = getattr(self, "h", None)
         if h:
             self.lib.orc_geometry_free(h)
             self.h = None
+
+    def run_mesh(self, n: int, seed: int, p_absorb: float, first_id: int = 0, threads: int = 1):
+        """run() with the superimposed mesh's track-length tally (uint64 per
+        bin, x fastest); the description must carry a mesh."""
+        if not self.mesh_bins:
+            raise ValueError("description has no mesh")
+        tally = np.zeros(self.n_inst, np.uint64)
+        cnt = np.zeros(N_COUNTERS, np.uint64)
+        mesh = np.zeros(self.mesh_bins, np.uint64)
+        self.lib.orc_run_mesh(self.h, n, first_id, seed, p_absorb, threads, _ptr(tally), _ptr(cnt), _ptr(mesh))
+        return {"tally": tally, "counters": cnt, "mesh": mesh}
+
+    def mesh_segment(self, r, d, length: float) -> np.ndarray:
+        """Mesh tally of one segment (start r, direction d, length)."""
+        mesh = np.zeros(self.mesh_bins, np.uint64)
+        self.lib.orc_mesh_segment(self.h, _ptr(np.ascontiguousarray(r, np.float64)),
+                                  _ptr(np.ascontiguousarray(d, np.float64)), float(length), _ptr(mesh))
+        return mesh
 
     def source(self, n: int, seed: int, first_id: int = 0):
         out = np.zeros((n, 7), np.float64)

@@ -202,7 +202,18 @@ struct Universe {
     }
 };
 
+// Superimposed rectilinear mesh for the track-length tally (the paper's
+// "active cycle" flux tally, Sec. 5): increasing plane lists per axis.
+struct Mesh {
+    std::vector<double> grid[3];
+    bool on() const { return !grid[0].empty(); }
+    long long bins() const {
+        return on() ? (long long)(grid[0].size() - 1) * (long long)(grid[1].size() - 1) * (long long)(grid[2].size() - 1) : 0;
+    }
+};
+
 struct Geometry {
+    Mesh mesh;
     int mode = 0;                  // 0: rect trackers for rect arrays; 1: all-CSG (pseudo-arrays)
     int gid = 0;
     std::vector<double> sigma;
@@ -498,6 +509,15 @@ static Geometry* load_geometry(const char* json, size_t len, int mode, std::stri
     if (g->root < 0 || g->root >= int(g->univ.size())) { err = "bad root"; return nullptr; }
     std::vector<double> sb;
     if (!nums(doc.get("source_box"), sb) || sb.size() != 6) { err = "missing source_box"; return nullptr; }
+    if ((v = doc.get("mesh"))) {
+        const oj::Val* mg = v->get("grid");
+        if (!mg || mg->kind != oj::Val::ARR || mg->arr.size() != 3) { err = "mesh needs 3 grids"; return nullptr; }
+        for (int d = 0; d < 3; ++d) {
+            if (!nums(&mg->arr[size_t(d)], g->mesh.grid[d]) || g->mesh.grid[d].size() < 2) { err = "bad mesh grid"; return nullptr; }
+            for (size_t i = 1; i < g->mesh.grid[d].size(); ++i)
+                if (!(g->mesh.grid[d][i] > g->mesh.grid[d][i - 1])) { err = "mesh grid not increasing"; return nullptr; }
+        }
+    }
     for (int i = 0; i < 6; ++i) g->src[i] = sb[i];
     // references
     for (auto& U : g->univ) {
@@ -975,6 +995,51 @@ struct HistoryOut {
     double fin[3] = {0, 0, 0};
 };
 
+// Mesh track-length tally of one segment (reading): the segment starts at
+// p.r and runs `len` along p.dir.  Per axis, with planes g_0 < ... < g_n,
+// the start's index is the largest i in -1..n with g_i <= x (g_-1 = -inf):
+// -1 and n are the two sides outside the mesh.  From the start, per axis
+// with a nonzero direction component, the next plane is g_{i+1} moving up
+// (none from index n) or g_i moving down (none from index -1), at
+// t = (g - x0) * (1/u) measured from the segment start.  A piece ends at the
+// smallest such t below len (ties: x before y before z; a t equal to len is
+// no crossing); a t below the piece's start counts as the start.  A piece
+// whose three indices are inside the mesh is tallied as
+// llrint(length * 2^32) into its bin (x fastest, then y, then z); the index
+// then steps along the crossing axis, until the walk reaches len.
+static void mesh_walk(const Geometry& g, const Particle& p, Real len, uint64_t* mesh) {
+    const Mesh& M = g.mesh;
+    int n[3], idx[3];
+    for (int d = 0; d < 3; ++d) {
+        const std::vector<double>& gr = M.grid[d];
+        n[d] = int(gr.size()) - 1;
+        const double x = dv(p.r[d]);
+        int i = -1;
+        while (i + 1 <= n[d] && gr[size_t(i + 1)] <= x) ++i;
+        idx[d] = i;
+    }
+    Real t0 = 0.0;
+    for (;;) {
+        Real tn = len;
+        int ax = -1;
+        for (int d = 0; d < 3; ++d) {
+            Real t;
+            if (p.dir[d] > Real(0.0) && idx[d] < n[d]) t = (Real(M.grid[d][size_t(idx[d] + 1)]) - p.r[d]) * p.inv[d];
+            else if (p.dir[d] < Real(0.0) && idx[d] >= 0) t = (Real(M.grid[d][size_t(idx[d])]) - p.r[d]) * p.inv[d];
+            else continue;
+            if (t < tn) { tn = t; ax = d; }
+        }
+        if (tn < t0) tn = t0;
+        if (idx[0] >= 0 && idx[0] < n[0] && idx[1] >= 0 && idx[1] < n[1] && idx[2] >= 0 && idx[2] < n[2]) {
+            const long long b = idx[0] + (long long)n[0] * (idx[1] + (long long)n[1] * idx[2]);
+            mesh[b] += uint64_t(std::llrint(dv((tn - t0) * 4294967296.0)));
+        }
+        if (ax < 0) break;
+        t0 = tn;
+        idx[ax] += p.dir[ax] > Real(0.0) ? 1 : -1;
+    }
+}
+
 // One history of Alg. 2 with the synthetic physics.  Reading (flight):
 //   dc = tau / Sigma (Sigma = 0 -> +inf);
 //   if d < dc: tally(d); r = r + d*Omega; tau = tau - Sigma*d; cross;
@@ -987,7 +1052,7 @@ struct HistoryOut {
 // track length reaches max_path, tallying only the part up to it.
 template <class Trace>
 static HistoryOut run_one(const Geometry& g, uint32_t pid, uint32_t seed_lo, const RunOpts& o,
-                          uint64_t* tally, unsigned long long* cnt, Trace&& trace) {
+                          uint64_t* tally, unsigned long long* cnt, Trace&& trace, uint64_t* mesh = nullptr) {
     HistoryOut out;
     Particle p;
     Real tau;
@@ -1013,6 +1078,7 @@ static HistoryOut run_one(const Geometry& g, uint32_t pid, uint32_t seed_lo, con
         else path = path + len;
         long long q = std::llrint(dv(len * 4294967296.0));
         tally[inst] += uint64_t(q);
+        if (mesh) mesh_walk(g, p, len, mesh);
         uint64_t lb;
         double ld = dv(len);
         std::memcpy(&lb, &ld, 8);
@@ -1277,6 +1343,65 @@ int orc_run(void* gp, long long n, long long first_id, unsigned long long seed, 
     }
     return 0;
 }
+
+// orc_run plus the mesh track-length tally (uint64[bins], x fastest).
+int orc_run_mesh(void* gp, long long n, long long first_id, unsigned long long seed, double p_absorb, int nthreads,
+                 unsigned long long* tally, unsigned long long* counters, unsigned long long* mesh) {
+    Geometry* g = static_cast<Geometry*>(gp);
+    if (!g->mesh.on()) return -1;
+    RunOpts o;
+    o.p_absorb = p_absorb;
+    o.max_segments = 1000000;
+    o.max_path = INF;
+    const long long ninst = g->univ[g->root].ninst, nb = g->mesh.bins();
+    if (nthreads < 1) nthreads = 1;
+    if (n < nthreads) nthreads = int(std::max<long long>(1, n));
+    std::vector<std::vector<uint64_t>> tl(size_t(nthreads), std::vector<uint64_t>(size_t(ninst), 0));
+    std::vector<std::vector<uint64_t>> ml(size_t(nthreads), std::vector<uint64_t>(size_t(nb), 0));
+    std::vector<std::vector<unsigned long long>> cl(size_t(nthreads), std::vector<unsigned long long>(K_NCOUNTERS, 0));
+    auto work = [&](int t) {
+        long long lo = n * t / nthreads, hi = n * (t + 1) / nthreads;
+        for (long long i = lo; i < hi; ++i)
+            run_one(*g, uint32_t(first_id + i), uint32_t(seed), o, tl[size_t(t)].data(), cl[size_t(t)].data(),
+                    [](long long, double, int) {}, ml[size_t(t)].data());
+    };
+    if (nthreads == 1) work(0);
+    else {
+        std::vector<std::thread> th;
+        for (int t = 0; t < nthreads; ++t) th.emplace_back(work, t);
+        for (auto& x : th) x.join();
+    }
+    for (long long b = 0; b < ninst; ++b) {
+        uint64_t s = 0;
+        for (int t = 0; t < nthreads; ++t) s += tl[size_t(t)][size_t(b)];
+        tally[b] = s;
+    }
+    for (long long b = 0; b < nb; ++b) {
+        uint64_t s = 0;
+        for (int t = 0; t < nthreads; ++t) s += ml[size_t(t)][size_t(b)];
+        mesh[b] = s;
+    }
+    for (int k = 0; k < K_NCOUNTERS; ++k) {
+        unsigned long long s = 0;
+        for (int t = 0; t < nthreads; ++t) s += cl[size_t(t)][size_t(k)];
+        counters[k] = s;
+    }
+    return 0;
+}
+
+// Mesh tally of one segment from (x, y, z) along (u, v, w), length len, with
+// the direction's reciprocals computed as the tracker does (a test hook).
+int orc_mesh_segment(void* gp, const double* r, const double* dir, double len, unsigned long long* mesh) {
+    Geometry* g = static_cast<Geometry*>(gp);
+    if (!g->mesh.on()) return -1;
+    Particle p;
+    for (int d = 0; d < 3; ++d) { p.r[d] = r[d]; p.dir[d] = dir[d]; }
+    set_direction_inverse(p);
+    mesh_walk(*g, p, len, reinterpret_cast<uint64_t*>(mesh));
+    return 0;
+}
+
+long long orc_mesh_bins(void* gp) { return static_cast<Geometry*>(gp)->mesh.bins(); }
 
 // Per-segment trace of one history: instance, length, kind (0 cross, 1 collide, 2 cutoff).
 long long orc_trace(void* gp, long long pid, unsigned long long seed, double p_absorb, long long max_segments,

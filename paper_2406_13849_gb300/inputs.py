@@ -510,3 +510,22 @@ CONFIGS = {
     "c2": config2,
     "c3": config3,
 }
+
+
+# ---------------------------------------------------------------------------
+# Superimposed mesh for the track-length tally
+# ---------------------------------------------------------------------------
+
+def with_mesh(desc: dict, nx: int, ny: int, nz: int, box=None) -> dict:
+    """A copy of `desc` with a superimposed rectilinear mesh of nx x ny x nz
+    equal bins over `box` (default: the source box); plane i of an axis is
+    lo + (hi - lo) * i / n in FP64, written out explicitly."""
+    d = dict(desc)
+    lo = list((box or desc["source_box"])[:3])
+    hi = list((box or desc["source_box"])[3:])
+    grid = []
+    for a, n in enumerate((nx, ny, nz)):
+        g = [lo[a] + (hi[a] - lo[a]) * i / n for i in range(n)] + [hi[a]]
+        grid.append([float(v) for v in g])
+    d["mesh"] = {"grid": grid}
+    return d

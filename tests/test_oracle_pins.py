@@ -397,3 +397,73 @@ def test_transmission_geometry_gradient_vs_fd():
         big = both & (err10 > 1e-6)
         if big.any():
             assert np.median(err[big] / err10[big]) < 0.05, nm
+
+
+# ---------------------------------------------------------------------------
+# superimposed mesh track-length tally
+# ---------------------------------------------------------------------------
+
+def _clip_len(r, d, length, lo, hi):
+    """Length of the segment r + t d, 0 <= t <= length, inside the box
+    [lo, hi] (slab clipping, an independent computation)."""
+    t0, t1 = 0.0, length
+    for a in range(3):
+        if d[a] == 0.0:
+            if not (lo[a] <= r[a] <= hi[a]):
+                return 0.0
+            continue
+        ta, tb = (lo[a] - r[a]) / d[a], (hi[a] - r[a]) / d[a]
+        t0, t1 = max(t0, min(ta, tb)), min(t1, max(ta, tb))
+    return max(0.0, t1 - t0)
+
+
+def test_mesh_segment_against_box_clipping():
+    # random segments, many starting outside the mesh, against the length
+    # inside each bin box by slab clipping (brute force over all bins)
+    d = I.with_mesh(I.single_pin(), 4, 3, 5, box=[-0.5, -0.4, 1.0, 0.7, 0.5, 8.0])
+    o = _geom(d, O.MODE_CSG)
+    gx, gy, gz = d["mesh"]["grid"]
+    rng = np.random.default_rng(7)
+    for _ in range(200):
+        r = rng.uniform([-1.0, -1.0, 0.0], [1.0, 1.0, 10.0])
+        v = rng.normal(size=3)
+        v /= np.linalg.norm(v)
+        length = rng.uniform(0.0, 6.0)
+        got = o.mesh_segment(r, v, length).astype(np.float64) / 2**32
+        exp = np.zeros(len(got))
+        for k in range(5):
+            for j in range(3):
+                for i in range(4):
+                    exp[i + 4 * (j + 3 * k)] = _clip_len(r, v, length, (gx[i], gy[j], gz[k]),
+                                                         (gx[i + 1], gy[j + 1], gz[k + 1]))
+        assert np.abs(got - exp).max() <= 1e-9, (r, v, length)
+
+
+def test_mesh_segment_along_an_axis():
+    # a segment along +x from the middle of bin 0 for 3.5 bin widths: pieces
+    # of half, one, one and one width (closed form), nothing elsewhere
+    d = I.with_mesh(I.single_pin(), 8, 2, 2, box=[0.0, 0.0, 0.0, 8.0, 2.0, 2.0])
+    o = _geom(d, O.MODE_CSG)
+    got = o.mesh_segment([0.5, 0.5, 0.5], [1.0, 0.0, 0.0], 3.5)
+    exp = np.zeros(32, np.uint64)
+    exp[0] = 2**31
+    exp[1:4] = 2**32
+    assert np.array_equal(got, exp)
+    # the same backwards from the far side, starting outside the mesh
+    got = o.mesh_segment([9.0, 1.5, 1.5], [-1.0, 0.0, 0.0], 3.0)
+    exp = np.zeros(32, np.uint64)
+    exp[7 + 8 * (1 + 2 * 1)] = 2**32
+    exp[6 + 8 * (1 + 2 * 1)] = 2**32
+    assert np.array_equal(got, exp)
+
+
+def test_mesh_total_equals_track_length():
+    # every segment lies in the geometry, which the mesh covers: the mesh
+    # tally's total is the cell tally's total up to each piece's rounding to
+    # 2^-32 cm
+    for d in (I.with_mesh(I.config1(), 17, 17, 10), I.with_mesh(I.small_core(), 9, 7, 5)):
+        r = _geom(d, O.MODE_RECT).run_mesh(2000, 1, 0.3, threads=4)
+        a = float(r["mesh"].sum()) / 2**32
+        b = float(r["tally"].sum()) / 2**32
+        assert abs(a - b) <= 1e-9 * b
+        assert (r["mesh"] > 0).mean() > 0.5
