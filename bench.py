@@ -342,6 +342,7 @@ def main() -> None:
     # ---- configuration 1 size sweep and the transmission workload ----------
     sweep = run_config1_sweep(N, I, dev, stream, barrier)
     hexcore = run_config3(N, I, dev, stream, barrier, k2)
+    meshline = run_mesh_tally(N, I, dev, stream, barrier, k2, rate(main_run), rate(rect_ev))
     trans = run_config5(N, I, dev, stream, barrier, k2)
 
     cpu = None
@@ -379,6 +380,7 @@ def main() -> None:
             "batched": batch,
             "config1_sweep": sweep,
             "config3": hexcore,
+            "mesh_tally": meshline,
             "transmission": trans,
         }
         print(json.dumps(line), flush=True)
@@ -540,6 +542,43 @@ def run_config3(N, I, dev, stream, barrier, steps):
         del work
     out["fp32local_over_fp64"] = out["csg_fp32local_event"] / out["csg_fp64_event"]
     out["csg_over_array"] = out["csg_fp64_event"] / out["array_fp64_event"]
+    return out
+
+
+def run_mesh_tally(N, I, dev, stream, barrier, steps, csg_plain, rect_plain):
+    """The main workload with the paper's active-cycle tally: track length on
+    a superimposed 119 x 119 x 30 mesh over the core's box, event kernel,
+    FP64, both trackers; the rates without the mesh tally are the main
+    line's."""
+    import numpy as np
+    import torch
+    desc = I.with_mesh(I.config2(), 119, 119, 30)
+    g = N.Geometry(I.to_json(desc), device=dev)
+    n = 10_000_000
+    parts = torch.empty(g.particle_bytes(n), dtype=torch.uint8, device=dev)
+    g.source_init(n, seed=SEED, out=parts)
+    tally = torch.zeros(g.n_inst, dtype=torch.int64, device=dev)
+    mesh = torch.zeros(g.mesh_bins, dtype=torch.int64, device=dev)
+    cnt = torch.zeros(N.NCOUNTERS, dtype=torch.int64, device=dev)
+    out = {"workload": "the main workload with a 119 x 119 x 30 superimposed mesh (424,830 bins) over the "
+                       "core's box, track-length tally per segment", "unit": UNIT, "mesh_bins": g.mesh_bins}
+    for name, tr, plain in (("csg", N.TRACKER_CSG, csg_plain), ("rect", N.TRACKER_RECT, rect_plain)):
+        opts = N.default_opts(tracker=tr, mode=N.MODE_EVENT, seed=SEED, p_absorb=P_ABSORB, queue_depth=EVENT_SLOTS)
+        opts.mesh_tally = mesh.data_ptr()
+        work = torch.empty(g.work_bytes(n, opts) + 256, dtype=torch.uint8, device=dev)
+        g.run_histories(parts, n, tally=tally, counters=cnt, opts=opts, work=work)
+        cnt.zero_()
+        barrier()
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            g.run_histories(parts, n, tally=tally, counters=cnt, opts=opts, work=work)
+        e.record(stream)
+        barrier()
+        r = int(cnt.cpu().numpy().view(np.uint64)[0]) / (a.elapsed_time(e) / 1e3)
+        out[f"{name}_fp64_event_with_mesh"] = r
+        out[f"{name}_degradation"] = 1.0 - r / plain
+        del work
     return out
 
 

@@ -87,7 +87,8 @@ typedef struct {
     int block;              /* threads per block, 0 = default */
     int grid;               /* blocks, 0 = default (a multiple of the SM count) */
     int queue_depth;        /* event mode: particle slots per warp (32..512), 0 = default 256 */
-    int sort_interval;      /* event mode: regroup queues by cell every k rounds, 0 = never */
+    int sort_interval;      /* reserved, ignored: the event kernel groups crossings by level every
+                               round; flight queues sorted by leaf-cell class are a build option */
     int max_rounds;         /* event mode: round limit per warp, 0 = from max_segments; past it the
                                kernel stops and reports TRK_E_TIMEOUT in counters[TRK_K_STATUS] */
     uint64_t seed;          /* low 32 bits key the Philox stream with the geometry id */
@@ -95,6 +96,9 @@ typedef struct {
     uint64_t max_segments;  /* per-particle segment cap (0 = 1e6) */
     double p_absorb;        /* absorption probability per collision */
     double max_path;        /* per-history path cutoff in cm (<= 0 or inf = none) */
+    uint64_t* mesh_tally;   /* device uint64[mesh bins] (x fastest) or NULL: superimposed mesh
+                               track-length tally, added to like the cell tally (the paper's active-
+                               cycle flux tally); needs a mesh in the description, FP64, no cutoff */
 } trk_run_opts;
 
 /* Fills opts with the defaults: auto tracker, history mode, FP64, seed 1,
@@ -135,6 +139,13 @@ trk_status geometry_destroy(trk_geom_t g);
  * maximum nesting depth, and whether the array tracker applies (always 1). */
 trk_status geometry_info(trk_geom_t g, int64_t* n_instances, int32_t* n_materials,
                          int32_t* max_depth, int32_t* rect_ok);
+
+/* Bins of the description's superimposed mesh ("mesh": {"grid": [x planes,
+ * y planes, z planes]}, increasing planes per axis), 0 without one.  The mesh
+ * tally (trk_run_opts.mesh_tally) walks each segment across the mesh planes
+ * from its start and adds each piece inside the mesh to its bin (the paper's
+ * active-cycle flux tally on a superimposed mesh, Sec. 5). */
+trk_status geometry_mesh_bins(trk_geom_t g, int64_t* bins);
 
 /*
  * source_init - sample the birth state of n particles (Alg. 2: position,

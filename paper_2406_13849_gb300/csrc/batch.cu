@@ -563,6 +563,8 @@ trk_status run_batched(trk_batch_t b, void* dev_work, const trk_run_opts* opts, 
     rp.max_path = DINF;
     rp.seed_lo = uint32_t(o.seed);
     rp.trace_cap = 0;
+    rp.mesh = nullptr;
+    if (o.mesh_tally) return trk_status(set_error(TRK_E_UNSUPPORTED, "run_batched: no mesh tally in batched mode"));
     bool rec = false;
     for (auto& e : b->entries) rec |= e.records != nullptr;
     cudaStream_t s = static_cast<cudaStream_t>(stream);

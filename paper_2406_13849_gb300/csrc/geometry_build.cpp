@@ -196,6 +196,7 @@ struct HUniv {
     int first_cell = 0, bvh = -1, lat = -1;
 };
 struct HGeom {
+    std::vector<double> mesh[3];   // superimposed mesh planes (empty: none)
     int gid = 0;
     std::vector<double> sigma;
     std::vector<HSurf> surf;
@@ -378,6 +379,23 @@ int parse(const char* json, size_t len, HGeom& G) {
     G.root = int(x);
     std::vector<double> sb;
     if (!read_nums(J, J.member(root, "source_box"), sb) || sb.size() != 6) DESC_FAIL("'source_box' needs 6 numbers");
+    {
+        const int mo = J.member(root, "mesh");
+        if (mo >= 0) {
+            const int mg = J.member(mo, "grid");
+            if (mg < 0 || J.at(mg).t != 'a' || J.at(mg).kids.size() != 3) DESC_FAIL("'mesh' needs 3 grids");
+            long long bins = 1;
+            for (int d = 0; d < 3; ++d) {
+                if (!read_nums(J, J.at(mg).kids[size_t(d)], G.mesh[d]) || G.mesh[d].size() < 2) DESC_FAIL("mesh grid %d malformed", d);
+                for (size_t i = 0; i < G.mesh[d].size(); ++i) {
+                    if (!std::isfinite(G.mesh[d][i])) DESC_FAIL("mesh grid %d: non-finite plane", d);
+                    if (i > 0 && !(G.mesh[d][i] > G.mesh[d][i - 1])) DESC_FAIL("mesh grid %d not increasing", d);
+                }
+                bins *= (long long)(G.mesh[d].size() - 1);
+            }
+            if (bins > (1LL << 31)) DESC_FAIL("mesh has more than 2^31 bins");
+        }
+    }
     for (int k = 0; k < 3; ++k) if (!(sb[size_t(k + 3)] > sb[size_t(k)])) DESC_FAIL("'source_box' is empty");
     for (int k = 0; k < 6; ++k) G.src[k] = sb[size_t(k)];
     return TRK_OK;
@@ -1128,6 +1146,13 @@ int build_host(const char* json, size_t len, Built& B) {
     o[33] = L.put(hx_row.size() * 4);
     if (c_pair.empty()) { c_pair.push_back(make_int4(-1, -1, -1, -1)); c_pair.push_back(make_int4(-1, -1, -1, -1)); }
     o[34] = L.put(c_pair.size() * sizeof(int4));
+    std::vector<double> m_grid;
+    std::vector<long long> m_key;
+    for (int d = 0; d < 3; ++d)
+        for (double v : G.mesh[d]) { m_grid.push_back(v); m_key.push_back(okey(v)); }
+    if (m_grid.empty()) { m_grid.push_back(0.0); m_key.push_back(0); }
+    o[35] = L.put(m_grid.size() * 8);
+    o[36] = L.put(m_key.size() * 8);
     B.image.assign(L.total, 0);
     copy_into(B.image, o[0], s_info);
     copy_into(B.image, o[1], s_coef);
@@ -1164,6 +1189,8 @@ int build_host(const char* json, size_t len, Built& B) {
     copy_into(B.image, o[32], hx);
     copy_into(B.image, o[33], hx_row);
     copy_into(B.image, o[34], c_pair);
+    copy_into(B.image, o[35], m_grid);
+    copy_into(B.image, o[36], m_key);
     return TRK_OK;
 }
 
@@ -1251,6 +1278,19 @@ trk_status geometry_build(const char* json, size_t len, void* dev_buf, size_t* d
     d.hx = reinterpret_cast<const HexInfo*>(base + o[32]);
     d.hx_row = reinterpret_cast<const int*>(base + o[33]);
     d.c_pair = reinterpret_cast<const int4*>(base + o[34]);
+    d.m_grid = reinterpret_cast<const double*>(base + o[35]);
+    d.m_key = reinterpret_cast<const long long*>(base + o[36]);
+    {
+        int go = 0;
+        for (int k = 0; k < 3; ++k) {
+            const std::vector<double>& mg = B.G.mesh[k];
+            d.m_n[k] = mg.empty() ? 0 : int(mg.size()) - 1;
+            d.m_go[k] = go;
+            d.m_lo[k] = mg.empty() ? 0.0 : mg.front();
+            d.m_inv[k] = mg.empty() ? 0.0 : double(d.m_n[k]) / (mg.back() - mg.front());
+            go += int(mg.size());
+        }
+    }
     const HGeom& G = B.G;
     for (int k = 0; k < 3; ++k) { d.src_lo[k] = G.src[k]; d.src_hi[k] = G.src[3 + k]; }
     d.root = G.root;
@@ -1290,6 +1330,12 @@ trk_status geometry_info(trk_geom_t g, int64_t* n_instances, int32_t* n_material
     if (n_materials) *n_materials = g->n_mat;
     if (max_depth) *max_depth = g->depth;
     if (rect_ok) *rect_ok = g->rect_ok;
+    return TRK_OK;
+}
+
+trk_status geometry_mesh_bins(trk_geom_t g, int64_t* bins) {
+    if (!g || g->magic != TRK_GEOM_MAGIC || !bins) return trk_status(set_error(TRK_E_INVALID, "geometry_mesh_bins: bad arguments"));
+    *bins = (int64_t)g->dg.m_n[0] * g->dg.m_n[1] * g->dg.m_n[2];
     return TRK_OK;
 }
 

@@ -1044,6 +1044,7 @@ struct RunP {
     double max_path;
     uint32_t seed_lo;
     int trace_cap;
+    unsigned long long* mesh;   // mesh track-length tally (F_MESH)
 };
 
 // Per-thread event counts (32-bit: one thread tracks far fewer than 2^32
@@ -1067,7 +1068,59 @@ __device__ __forceinline__ void kernel_status(unsigned long long* cnt, int st) {
     atomicCAS(cnt + TRK_K_STATUS, 0ULL, (unsigned long long)(long long)st);
 }
 
-enum { F_REC = 1, F_CUT = 2, F_TRACE = 4 };
+enum { F_REC = 1, F_CUT = 2, F_TRACE = 4, F_MESH = 8 };
+
+// Mesh index per axis: the largest i in -1..n with g_i <= x (-1 and n are the
+// two sides outside the mesh), by order keys; the start guess from the
+// planes' span only saves steps, the key compares decide.
+__device__ __forceinline__ int mesh_index(const DevGeom& g, int d, double x, long long kx) {
+    const int n = g.m_n[d];
+    const long long* key = g.m_key + g.m_go[d];
+    double e = floor((x - g.m_lo[d]) * g.m_inv[d]);
+    int i = e < -1.0 ? -1 : (e > double(n) ? n : int(e));
+    while (i >= 0 && __ldg(key + i) > kx) --i;
+    while (i < n && __ldg(key + i + 1) <= kx) ++i;
+    return i;
+}
+
+// Superimposed mesh track-length tally of one segment (start s.x, s.y, s.z,
+// length len along the direction): from the start, per axis the next mesh
+// plane in the direction of flight (none beyond the outermost) at
+// t = (g - x0) * (1/u); a piece ends at the smallest t below len (x before y
+// before z on ties), a t below the piece's start counts as the start; pieces
+// inside the mesh add llrint(length * 2^32) to their bin (x fastest).
+__device__ __forceinline__ void mesh_walk(const DevGeom& g, const St& s, double len, unsigned long long* mesh) {
+    const double p3[3] = {s.x, s.y, s.z};
+    const double d3[3] = {s.d.u, s.d.v, s.d.w};
+    const double v3[3] = {s.d.iu, s.d.iv, s.d.iw};
+    int idx[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) idx[d] = mesh_index(g, d, p3[d], okey(p3[d]));
+    double t0 = 0.0;
+    for (;;) {
+        double tn = len;
+        long long kn = okey(len);
+        int ax = -1;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            int pl = -1;
+            if (d_gt0(d3[d]) && idx[d] < g.m_n[d]) pl = idx[d] + 1;
+            else if (d_lt0(d3[d]) && idx[d] >= 0) pl = idx[d];
+            if (pl < 0) continue;
+            const double t = (__ldg(g.m_grid + g.m_go[d] + pl) - p3[d]) * v3[d];
+            const long long kt = okey(t);
+            if (kt < kn) { tn = t; kn = kt; ax = d; }
+        }
+        if (kn < okey(t0)) tn = t0;
+        if (idx[0] >= 0 && idx[0] < g.m_n[0] && idx[1] >= 0 && idx[1] < g.m_n[1] && idx[2] >= 0 && idx[2] < g.m_n[2]) {
+            const long long b = idx[0] + (long long)g.m_n[0] * (idx[1] + (long long)g.m_n[1] * idx[2]);
+            atomicAdd(mesh + b, (unsigned long long)__double2ll_rn((tn - t0) * 4294967296.0));
+        }
+        if (ax < 0) break;
+        t0 = tn;
+        idx[ax] += d_gt0(ax == 0 ? d3[0] : (ax == 1 ? d3[1] : d3[2])) ? 1 : -1;
+    }
+}
 
 
 // ---------------------------------------------------------------------------
@@ -1109,6 +1162,7 @@ __device__ __forceinline__ int step_flight(const DevGeom& g, St& s, Hit& h, Ctx&
     }
     const long long q = __double2ll_rn(len * 4294967296.0);
     atomicAdd(tally + inst, (unsigned long long)q);
+    if (FLAGS & F_MESH) mesh_walk(g, s, len, rp.mesh);
     if (FLAGS & F_REC) c.hash = fnv(fnv(c.hash, uint64_t(int64_t(inst))), uint64_t(dbits(len)));
     if (FLAGS & F_TRACE) {
         if (c.nseg < rp.trace_cap) {

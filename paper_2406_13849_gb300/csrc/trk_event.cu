@@ -310,6 +310,8 @@ trk_status launch_event(trk_geom_t g, const ParticlesView& P, long long n, const
             case 0: TRK_EV(true, false, 0); break;
             case F_REC: TRK_EV(true, false, F_REC); break;
             case F_CUT: TRK_EV(true, false, F_CUT); break;
+            case F_MESH: TRK_EV(true, false, F_MESH); break;
+            case F_MESH | F_REC: TRK_EV(true, false, F_MESH | F_REC); break;
             default: TRK_EV(true, false, F_REC | F_CUT); break;
         }
     } else {
@@ -317,6 +319,8 @@ trk_status launch_event(trk_geom_t g, const ParticlesView& P, long long n, const
             case 0: TRK_EV(false, false, 0); break;
             case F_REC: TRK_EV(false, false, F_REC); break;
             case F_CUT: TRK_EV(false, false, F_CUT); break;
+            case F_MESH: TRK_EV(false, false, F_MESH); break;
+            case F_MESH | F_REC: TRK_EV(false, false, F_MESH | F_REC); break;
             default: TRK_EV(false, false, F_REC | F_CUT); break;
         }
     }

@@ -117,7 +117,12 @@ struct DevGeom {
     const float* l_hif;       // face above: g_{i+1} - c_i
     const float* c_slabf;     // 6 per cell: slab faces (lo_x, hi_x, lo_y, hi_y, lo_z, hi_z)
                               // relative to the cell's translation
-    // BVH (skip-list preorder per universe)
+    // superimposed mesh (track-length tally): planes per axis and their order keys
+    const double* m_grid;     // axis d at m_grid[m_go[d]], m_n[d] + 1 planes
+    const long long* m_key;
+    double m_lo[3], m_inv[3]; // first plane and n / (g_n - g_0) per axis (search start only)
+    int m_n[3], m_go[3];      // bins and plane offsets per axis; m_n[0] == 0: no mesh
+    // BVH nodes (two child boxes per node)
     const BvhNode* nodes;
     const int* leaf_cells;
     // materials

@@ -514,8 +514,14 @@ trk_status run_histories(trk_geom_t g, const void* dev_particles, int64_t n, uin
     auto* C = reinterpret_cast<unsigned long long*>(dev_counters);
     auto* R = reinterpret_cast<unsigned long long*>(dev_records);
     const bool csg = tracker == TRK_TRACKER_CSG;
-    const int flags = (dev_records ? F_REC : 0) | (cut ? F_CUT : 0);
+    const bool mesh = o.mesh_tally != nullptr;
+    rp.mesh = reinterpret_cast<unsigned long long*>(o.mesh_tally);
+    const int flags = (dev_records ? F_REC : 0) | (cut ? F_CUT : 0) | (mesh ? F_MESH : 0);
     if (f32 && cut) return trk_status(set_error(TRK_E_UNSUPPORTED, "run_histories: path cutoff needs FP64 precision"));
+    if (mesh && !g->dg.m_n[0])
+        return trk_status(set_error(TRK_E_INVALID, "run_histories: mesh tally given but the geometry has no mesh"));
+    if (mesh && (f32 || cut))
+        return trk_status(set_error(TRK_E_UNSUPPORTED, "run_histories: the mesh tally needs FP64 precision and no path cutoff"));
     if (o.mode == TRK_MODE_EVENT) {
         const int slots = event_slots(o);
         if (slots < 32 || slots > 512) return trk_status(set_error(TRK_E_INVALID, "queue_depth must be in [32, 512]"));
@@ -541,6 +547,8 @@ trk_status run_histories(trk_geom_t g, const void* dev_particles, int64_t n, uin
             case 0: TRK_LAUNCH(true, false, 0);
             case F_REC: TRK_LAUNCH(true, false, F_REC);
             case F_CUT: TRK_LAUNCH(true, false, F_CUT);
+            case F_MESH: TRK_LAUNCH(true, false, F_MESH);
+            case F_MESH | F_REC: TRK_LAUNCH(true, false, F_MESH | F_REC);
             default: TRK_LAUNCH(true, false, F_REC | F_CUT);
         }
     } else {
@@ -548,6 +556,8 @@ trk_status run_histories(trk_geom_t g, const void* dev_particles, int64_t n, uin
             case 0: TRK_LAUNCH(false, false, 0);
             case F_REC: TRK_LAUNCH(false, false, F_REC);
             case F_CUT: TRK_LAUNCH(false, false, F_CUT);
+            case F_MESH: TRK_LAUNCH(false, false, F_MESH);
+            case F_MESH | F_REC: TRK_LAUNCH(false, false, F_MESH | F_REC);
             default: TRK_LAUNCH(false, false, F_REC | F_CUT);
         }
     }
@@ -574,6 +584,7 @@ trk_status trk_trace(trk_geom_t g, const void* dev_particles, int64_t n, int32_t
     rp.max_path = DINF;
     rp.seed_lo = uint32_t(o.seed);
     rp.trace_cap = cap;
+    rp.mesh = nullptr;
     auto* T = reinterpret_cast<unsigned long long*>(dev_tally);
     auto* C = reinterpret_cast<unsigned long long*>(dev_counters);
     cudaStream_t s = static_cast<cudaStream_t>(stream);

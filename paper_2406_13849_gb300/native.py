@@ -44,7 +44,7 @@ class RunOpts(ctypes.Structure):
                 ("sort_interval", ctypes.c_int), ("max_rounds", ctypes.c_int),
                 ("seed", ctypes.c_uint64), ("first_id", ctypes.c_uint64),
                 ("max_segments", ctypes.c_uint64), ("p_absorb", ctypes.c_double),
-                ("max_path", ctypes.c_double)]
+                ("max_path", ctypes.c_double), ("mesh_tally", ctypes.c_void_p)]
 
 
 _P = ctypes.c_void_p
@@ -73,6 +73,7 @@ def library(exact: bool = False):
             "geometry_build": (ctypes.c_int, [ctypes.c_char_p, sz, _P, psz, _P, ctypes.POINTER(_P)]),
             "geometry_destroy": (ctypes.c_int, [_P]),
             "geometry_info": (ctypes.c_int, [_P, pi64, pi32, pi32, pi32]),
+            "geometry_mesh_bins": (ctypes.c_int, [_P, pi64]),
             "source_init": (ctypes.c_int, [_P, i64, u64, u64, _P, psz, _P]),
             "run_histories_work_bytes": (ctypes.c_int, [_P, i64, ctypes.POINTER(RunOpts), psz]),
             "run_histories": (ctypes.c_int, [_P, _P, i64, _P, _P, _P, _P, sz, ctypes.POINTER(RunOpts), _P]),
@@ -153,6 +154,9 @@ class Geometry:
         _check(self.lib, self.lib.geometry_info(h, ctypes.byref(ni), ctypes.byref(nm), ctypes.byref(dp),
                                                 ctypes.byref(ro)))
         self.n_inst, self.n_mat, self.depth, self.rect_ok = ni.value, nm.value, dp.value, bool(ro.value)
+        mb = ctypes.c_int64()
+        _check(self.lib, self.lib.geometry_mesh_bins(h, ctypes.byref(mb)))
+        self.mesh_bins = mb.value
         self.device_bytes = nbytes.value
 
     def close(self):
@@ -194,8 +198,13 @@ class Geometry:
         return b.value
 
     def run_histories(self, particles, n: int, tally=None, counters=None, records: bool = False,
-                      work=None, opts: RunOpts | None = None, stream=None, **kw):
+                      work=None, opts: RunOpts | None = None, stream=None, mesh=None, **kw):
+        """mesh: an int64 device tensor of mesh_bins to add the superimposed
+        mesh tally to (sets opts.mesh_tally)."""
         opts = opts if opts is not None else default_opts(**kw)
+        if mesh is not None:
+            opts = RunOpts.from_buffer_copy(opts)
+            opts.mesh_tally = mesh.data_ptr()
         if tally is None:
             tally = torch.zeros(self.n_inst, dtype=torch.int64, device=self.device)
         if counters is None:
