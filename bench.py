@@ -288,6 +288,11 @@ def main() -> None:
     csg_hist = timed(N.TRACKER_CSG, N.MODE_HISTORY, k2, 3)
     rect_hist = timed(N.TRACKER_RECT, N.MODE_HISTORY, k2, 3)
     csg_ev32 = timed(N.TRACKER_CSG, N.MODE_EVENT, k2, 3, prec=N.FP32_LOCAL)
+    # the same workload with the bounding interval hierarchy (Sec. 4.3) as the CSG search
+    g_bvh = g
+    g = N.Geometry(I.to_json(dict(I.config2(), accel="bih")), device=dev)
+    csg_ev_bih = timed(N.TRACKER_CSG, N.MODE_EVENT, k2, 3)
+    g = g_bvh
 
     # ---- end to end through the C-ABI with host buffers ---------------------
     host_parts = torch.empty(parts.numel(), dtype=torch.uint8, pin_memory=True)
@@ -373,6 +378,8 @@ def main() -> None:
                 "rect_fp64_history": rate(rect_hist),
                 "csg_over_rect_history": rate(csg_hist) / rate(rect_hist),
                 "csg_fp32local_event": rate(csg_ev32),
+                "csg_fp64_event_bih": rate(csg_ev_bih),
+                "bih_over_bvh_event": rate(csg_ev_bih) / rate(main_run),
                 "fp32local_close_call_fraction": float(csg_ev32["counters"][10]) / max(1, csg_ev32["segments"]),
                 "segments_per_particle": main_run["segments"] / (n * args.steps),
                 "event_kernel_ms": kern_ms,
@@ -518,19 +525,21 @@ def run_config3(N, I, dev, stream, barrier, steps):
     cnt = torch.zeros(N.NCOUNTERS, dtype=torch.int64, device=dev)
     out = {"workload": "hex core: 127 assemblies x 91 pins (rings 6 of ring-6 pin lattices turned 30 deg), "
                        "h=200, 5 materials, absorption 0.25, 1e7 particles", "unit": UNIT}
-    for name, tr, prec in (("csg_fp64_event", N.TRACKER_CSG, N.FP64),
-                           ("csg_fp32local_event", N.TRACKER_CSG, N.FP32_LOCAL),
-                           ("array_fp64_event", N.TRACKER_RECT, N.FP64)):
+    g_bih = N.Geometry(I.to_json(dict(I.config3(), accel="bih")), device=dev)
+    for name, tr, prec, gg in (("csg_fp64_event", N.TRACKER_CSG, N.FP64, g),
+                               ("csg_fp32local_event", N.TRACKER_CSG, N.FP32_LOCAL, g),
+                               ("array_fp64_event", N.TRACKER_RECT, N.FP64, g),
+                               ("csg_fp64_event_bih", N.TRACKER_CSG, N.FP64, g_bih)):
         opts = N.default_opts(tracker=tr, mode=N.MODE_EVENT, precision=prec, seed=SEED,
                               p_absorb=P_ABSORB, queue_depth=EVENT_SLOTS)
-        work = torch.empty(g.work_bytes(n, opts) + 256, dtype=torch.uint8, device=dev)
-        g.run_histories(parts, n, tally=tally, counters=cnt, opts=opts, work=work)
+        work = torch.empty(gg.work_bytes(n, opts) + 256, dtype=torch.uint8, device=dev)
+        gg.run_histories(parts, n, tally=tally, counters=cnt, opts=opts, work=work)
         cnt.zero_()
         barrier()
         a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         for _ in range(steps):
-            g.run_histories(parts, n, tally=tally, counters=cnt, opts=opts, work=work)
+            gg.run_histories(parts, n, tally=tally, counters=cnt, opts=opts, work=work)
         e.record(stream)
         barrier()
         c = cnt.cpu().numpy().view(np.uint64)
@@ -542,6 +551,7 @@ def run_config3(N, I, dev, stream, barrier, steps):
         del work
     out["fp32local_over_fp64"] = out["csg_fp32local_event"] / out["csg_fp64_event"]
     out["csg_over_array"] = out["csg_fp64_event"] / out["array_fp64_event"]
+    out["bih_over_bvh"] = out["csg_fp64_event_bih"] / out["csg_fp64_event"]
     return out
 
 

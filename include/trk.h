@@ -49,7 +49,12 @@ typedef enum {
     TRK_E_SOURCE = -9         /* source rejection sampling exceeded its cap */
 } trk_status;
 
-/* Trackers.  RECT: the array tracker (static dispatch per universe type):
+/* Geometry descriptions may carry "accel": "bvh" (default) or "bih": the
+ * acceleration structure of the CSG cell search, a BVH whose nodes hold both
+ * children's boxes (64 B) or the bounding interval hierarchy of Sec. 4.3
+ * (two bounding planes per node, 16 B).  Both return the same cells.
+ *
+ * Trackers.  RECT: the array tracker (static dispatch per universe type):
  * rect arrays by index (Alg. 5/6/9/10), hex arrays by a closed-form
  * element search checked against the element's pseudo-array cell (the paper
  * gives no hex array tracker; results are those of the pseudo-array scan),

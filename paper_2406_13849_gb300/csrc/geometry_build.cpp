@@ -193,10 +193,11 @@ struct HUniv {
     long long ninst = -1;
     double box[6] = {INF, INF, INF, -INF, -INF, -INF};   // universe box (own frame), grown from parents
     bool box_set = false;
-    int first_cell = 0, bvh = -1, lat = -1;
+    int first_cell = 0, bvh = -1, bih = -1, lat = -1;
 };
 struct HGeom {
     std::vector<double> mesh[3];   // superimposed mesh planes (empty: none)
+    int accel = 0;                 // CSG cell search: 0 BVH, 1 BIH
     int gid = 0;
     std::vector<double> sigma;
     std::vector<HSurf> surf;
@@ -379,6 +380,13 @@ int parse(const char* json, size_t len, HGeom& G) {
     G.root = int(x);
     std::vector<double> sb;
     if (!read_nums(J, J.member(root, "source_box"), sb) || sb.size() != 6) DESC_FAIL("'source_box' needs 6 numbers");
+    {
+        const int ao = J.member(root, "accel");
+        if (ao >= 0) {
+            if (J.at(ao).t != 's' || (J.at(ao).s != "bvh" && J.at(ao).s != "bih")) DESC_FAIL("'accel' must be \"bvh\" or \"bih\"");
+            G.accel = J.at(ao).s == "bih" ? 1 : 0;
+        }
+    }
     {
         const int mo = J.member(root, "mesh");
         if (mo >= 0) {
@@ -758,11 +766,69 @@ class BvhBuilder {
                 if (cost < best_cost) { best_cost = cost; best_axis = k; best_plane = plane; }
             }
         }
-        if (best_axis < 0) return lo + n / 2;
+        if (best_axis < 0) {
+            // median fallback; the BIH takes the axis of widest centre spread
+            last_axis = 0;
+            for (int k = 1; k < 3; ++k)
+                if (cmax[k] - cmin[k] > cmax[last_axis] - cmin[last_axis]) last_axis = k;
+            return lo + n / 2;
+        }
+        last_axis = best_axis;
         auto it = std::partition(ids_.begin() + lo, ids_.begin() + hi,
                                  [&](int id) { return centre(id, best_axis) < best_plane; });
         return int(it - ids_.begin());
     }
+    int last_axis = 0;
+
+  public:
+    // Bounding interval hierarchy over the same cells (Sec. 4.3): the same
+    // SAH partition of the box centres; each node keeps the split axis, the
+    // largest upper bound of the left set's boxes and the smallest lower
+    // bound of the right set's along it (FP32, rounded outward).  Returns
+    // the root reference.
+    std::vector<BihNode> bih;
+    int bih_depth = 0;
+    int build_bih(std::vector<int>& cells, const std::vector<Box>& boxes) {
+        ids_ = cells;
+        boxes_ = &boxes;
+        return emit_bih(0, int(ids_.size()), 0);
+    }
+
+  private:
+    int emit_bih(int lo, int hi, int depth) {
+        bih_depth = std::max(bih_depth, depth);
+        if (hi - lo <= BVH_LEAF_MAX) {
+            const int first = int(leaf_cells.size());
+            for (int i = lo; i < hi; ++i) leaf_cells.push_back(ids_[size_t(i)]);
+            return -1 - ((first << 4) | (hi - lo));
+        }
+        const int self = int(bih.size());
+        bih.push_back(BihNode{});
+        const int mid = depth > 24 ? lo + (hi - lo) / 2 : split(lo, hi);
+        int axis = last_axis;
+        if (depth > 24) {
+            // median split below depth 24: axis of the widest centre spread
+            double cmin[3] = {INF, INF, INF}, cmax[3] = {-INF, -INF, -INF};
+            for (int i = lo; i < hi; ++i)
+                for (int k = 0; k < 3; ++k) {
+                    const double c = centre(ids_[size_t(i)], k);
+                    cmin[k] = std::min(cmin[k], c); cmax[k] = std::max(cmax[k], c);
+                }
+            axis = 0;
+            for (int k = 1; k < 3; ++k)
+                if (cmax[k] - cmin[k] > cmax[axis] - cmin[axis]) axis = k;
+        }
+        const Box b0 = bound(lo, mid), b1 = bound(mid, hi);
+        const int r0 = emit_bih(lo, mid, depth + 1);
+        const int r1 = emit_bih(mid, hi, depth + 1);
+        BihNode& nd = bih[size_t(self)];
+        nd.clip_l = f_up(b0.hi[axis]);
+        nd.clip_r = f_down(b1.lo[axis]);
+        nd.ref0 = r0;
+        nd.ref1_axis = r1 * 4 + axis;
+        return self;
+    }
+  public:
     // SAH splits; below depth 24 the median, so the depth stays below
     // 24 + log2(cells) (the device walk's stack holds BVH_STACK entries).
     int emit(int lo, int hi, int depth) {
@@ -884,7 +950,13 @@ int build_host(const char* json, size_t len, Built& B) {
         }
         U.bvh = bvh.build(ids, boxes);
         if (U.bvh < 0) U.bvh = -1;   // a single leaf: the linear scan does the same
+        if (U.bvh >= 0) {
+            std::vector<int> ids2;
+            for (int i = 0; i < int(U.cells.size()); ++i) ids2.push_back(U.first_cell + i);
+            U.bih = bvh.build_bih(ids2, boxes);
+        }
     }
+    if (bvh.bih_depth >= BVH_STACK) return set_error(TRK_E_DESC, "BIH depth %d exceeds %d", bvh.bih_depth, BVH_STACK);
     if (bvh.max_depth >= BVH_STACK) return set_error(TRK_E_DESC, "BVH depth %d exceeds %d", bvh.max_depth, BVH_STACK);
     B.n_nodes = int(bvh.nodes.size());
 
@@ -1146,6 +1218,12 @@ int build_host(const char* json, size_t len, Built& B) {
     o[33] = L.put(hx_row.size() * 4);
     if (c_pair.empty()) { c_pair.push_back(make_int4(-1, -1, -1, -1)); c_pair.push_back(make_int4(-1, -1, -1, -1)); }
     o[34] = L.put(c_pair.size() * sizeof(int4));
+    std::vector<int> u_bih;
+    for (auto& U : G.univ) u_bih.push_back(U.bih);
+    std::vector<BihNode> bihn = bvh.bih;
+    if (bihn.empty()) bihn.push_back(BihNode{});
+    o[37] = L.put(u_bih.size() * 4);
+    o[38] = L.put(bihn.size() * sizeof(BihNode));
     std::vector<double> m_grid;
     std::vector<long long> m_key;
     for (int d = 0; d < 3; ++d)
@@ -1189,6 +1267,8 @@ int build_host(const char* json, size_t len, Built& B) {
     copy_into(B.image, o[32], hx);
     copy_into(B.image, o[33], hx_row);
     copy_into(B.image, o[34], c_pair);
+    copy_into(B.image, o[37], u_bih);
+    copy_into(B.image, o[38], bihn);
     copy_into(B.image, o[35], m_grid);
     copy_into(B.image, o[36], m_key);
     return TRK_OK;
@@ -1278,6 +1358,9 @@ trk_status geometry_build(const char* json, size_t len, void* dev_buf, size_t* d
     d.hx = reinterpret_cast<const HexInfo*>(base + o[32]);
     d.hx_row = reinterpret_cast<const int*>(base + o[33]);
     d.c_pair = reinterpret_cast<const int4*>(base + o[34]);
+    d.u_bih = reinterpret_cast<const int*>(base + o[37]);
+    d.bih = reinterpret_cast<const BihNode*>(base + o[38]);
+    d.accel = B.G.accel;
     d.m_grid = reinterpret_cast<const double*>(base + o[35]);
     d.m_key = reinterpret_cast<const long long*>(base + o[36]);
     {

@@ -376,8 +376,51 @@ static __device__ TRK_SEARCH_INLINE int bvh_search(const DevGeom& g, int root, c
     }
 }
 
+// Walk of universe u's bounding interval hierarchy (Sec. 4.3): at each node
+// both edge conditions are tested (the half-spaces may overlap): left if the
+// point can be at or below clip_l along the node's axis, right if it can be
+// at or above clip_r; left before right, first holding cell returned.
+static __device__ TRK_SEARCH_INLINE int bih_search(const DevGeom& g, int root, const Pt& p, int ex, int xs, int xsn) {
+    float lo3[3], hi3[3];
+    f32_bounds(p.x, lo3[0], hi3[0]);
+    f32_bounds(p.y, lo3[1], hi3[1]);
+    f32_bounds(p.z, lo3[2], hi3[2]);
+    int stack[BVH_STACK];
+    int sp = 0;
+    int ref = root;
+    for (;;) {
+        if (ref >= 0) {
+            const float4 nd = __ldg(reinterpret_cast<const float4*>(g.bih + ref));
+            const int r0 = __float_as_int(nd.z), r1a = __float_as_int(nd.w);
+            const int ax = r1a & 3, r1 = r1a >> 2;
+            const float pl = ax == 0 ? lo3[0] : (ax == 1 ? lo3[1] : lo3[2]);
+            const float ph = ax == 0 ? hi3[0] : (ax == 1 ? hi3[1] : hi3[2]);
+            const bool in0 = pl <= nd.x, in1 = ph >= nd.y;
+            if (in0) {
+                if (in1 && sp < BVH_STACK) stack[sp++] = r1;
+                ref = r0;
+                continue;
+            }
+            if (in1) {
+                ref = r1;
+                continue;
+            }
+        } else {
+            const int leaf = -1 - ref;
+            const int first = leaf >> 4, cnt = leaf & 15;
+            for (int k = 0; k < cnt; ++k) {
+                const int c = __ldg(g.leaf_cells + first + k);
+                if (c != ex && cell_holds(g, c, p, xs, xsn)) return c;
+            }
+        }
+        if (sp == 0) return -1;
+        ref = stack[--sp];
+    }
+}
+
 // First cell of universe u (CSG view) holding the point, excluding cell `ex`:
-// linear scan for small universes (Alg. 3/4), otherwise the BVH walk.
+// linear scan for small universes (Alg. 3/4), otherwise the walk of the
+// geometry's acceleration structure (BVH, or BIH with "accel": "bih").
 __device__ __forceinline__ int csg_search(const DevGeom& g, int u, const Pt& p, int ex, int xs, int xsn) {
     const int4 ui = __ldg(g.u_info + u);
     if (ui.z < 0) {
@@ -387,6 +430,7 @@ __device__ __forceinline__ int csg_search(const DevGeom& g, int u, const Pt& p, 
         }
         return -1;
     }
+    if (g.accel) return bih_search(g, __ldg(g.u_bih + u), p, ex, xs, xsn);
     return bvh_search(g, ui.z, p, ex, xs, xsn);
 }
 

@@ -51,6 +51,15 @@ struct alignas(16) HexInfo {
     int rings, first_cell, row, pad;
 };
 
+// Bounding interval hierarchy node (Sec. 4.3): along `axis` the left
+// child's boxes end at or below clip_l and the right child's start at or
+// above clip_r (FP32, rounded outward); the half-spaces may overlap.
+// ref0: left child, ref1_axis = ref1 * 4 + axis (references as in BvhNode).
+struct alignas(16) BihNode {
+    float clip_l, clip_r;
+    int ref0, ref1_axis;
+};
+
 // Largest BVH depth the builder produces (the walk's stack size).
 constexpr int BVH_STACK = 64;
 
@@ -122,8 +131,11 @@ struct DevGeom {
     const long long* m_key;
     double m_lo[3], m_inv[3]; // first plane and n / (g_n - g_0) per axis (search start only)
     int m_n[3], m_go[3];      // bins and plane offsets per axis; m_n[0] == 0: no mesh
-    // BVH nodes (two child boxes per node)
+    // BVH nodes (two child boxes per node); BIH nodes and roots per universe
     const BvhNode* nodes;
+    const BihNode* bih;
+    const int* u_bih;         // BIH root reference per universe (-1: linear scan)
+    int accel;                // CSG cell search: 0 BVH, 1 BIH
     const int* leaf_cells;
     // materials
     const double* sigma;
