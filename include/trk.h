@@ -113,8 +113,9 @@ void trk_default_opts(trk_run_opts* opts);
 /* Message of the last failing call on this thread ("" if none). */
 const char* trk_last_error(void);
 
-/* Library build flavour: 1 if compiled with --fmad=false (bit-exact against
- * the FP64 reference arithmetic), 0 for the fast build. */
+/* Library build flavour: 1 if compiled with --fmad=false (every FP64
+ * operation rounded once, in the order the method's formulas are written:
+ * bit-exact against an FP64 evaluation of them), 0 for the fast build. */
 int trk_exact_build(void);
 
 /*

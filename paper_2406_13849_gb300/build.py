@@ -2,7 +2,7 @@
 
 Produces, under ``paper_2406_13849_gb300/_build/``:
   libtrk.so        fast build (FP64 contraction allowed)
-  libtrk_exact.so  --fmad=false build, bit-exact against FP64 reference arithmetic
+  libtrk_exact.so  --fmad=false build, bit-exact against the FP64 oracle
 Both link the same host object (geometry_build.cpp, -ffp-contract=off).
 """
 from __future__ import annotations

@@ -12,8 +12,9 @@
 //    key: no FP64 instruction at all;
 //  - BVH boxes are FP32, and the point's FP32 bounds (round down / up) are
 //    produced from its bits with integer operations;
-//  - only the arithmetic of the reference formulas runs on the FP64 pipe,
-//    in the reference's order (bit-exact in the --fmad=false build).
+//  - only the arithmetic of the method's formulas runs on the FP64 pipe, in
+//    the order they are written (bit-exact with the FP64 oracle in the
+//    --fmad=false build).
 #pragma once
 #include <cstdint>
 

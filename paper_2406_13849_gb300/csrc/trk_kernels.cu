@@ -13,8 +13,8 @@
 //    tracker is compiled in or out by a template flag, never a virtual call;
 //  - tallies: one 64-bit integer atomic per segment (order-independent);
 //    counters: per-thread registers, warp-reduced, one atomic per warp.
-// Built twice: --fmad=false (TRK_EXACT, bit-exact against the FP64 reference
-// arithmetic) and with contraction (fast).
+// Built twice: --fmad=false (TRK_EXACT, bit-exact against the FP64 oracle)
+// and with contraction (fast).
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -420,7 +420,7 @@ trk_status launch_history(trk_geom_t g, const ParticlesView& P, long long n, con
 }
 
 // The FP32-local kernels exist in the fast build only (the exact build is
-// the bit-exact FP64 reference path).
+// the path that is bit-exact against the FP64 oracle).
 #ifdef TRK_EXACT
 constexpr bool HAVE_F32 = false;
 #else
