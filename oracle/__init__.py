@@ -96,6 +96,7 @@ def _lib(counting: bool = False):
         lib.orc_flop_counts.argtypes = [_P, _I]
         lib.orc_run_mesh.argtypes = [_P, _LL, _LL, _ULL, _D, _I, _P, _P, _P]
         lib.orc_mesh_segment.argtypes = [_P, _P, _P, _D, _P]
+        lib.orc_power.argtypes = [_P, _LL, _LL, _ULL, _D, _I, _I, _I, _P, _P, _P, _P]
         lib.orc_mesh_bins.restype = _LL
         lib.orc_mesh_bins.argtypes = [_P]
         _LIBS[key] = lib
@@ -139,6 +140,18 @@ class Geometry:
         mesh = np.zeros(self.mesh_bins, np.uint64)
         self.lib.orc_run_mesh(self.h, n, first_id, seed, p_absorb, threads, _ptr(tally), _ptr(cnt), _ptr(mesh))
         return {"tally": tally, "counters": cnt, "mesh": mesh}
+
+    def power(self, n: int, seed: int, p_absorb: float, inactive: int, cycles: int, first_id: int = 0,
+              threads: int = 1):
+        """Power iteration: k per cycle, sites banked per cycle, tally and
+        counters of the active cycles."""
+        k = np.zeros(cycles, np.float64)
+        bank = np.zeros(cycles, np.int64)
+        tally = np.zeros(self.n_inst, np.uint64)
+        cnt = np.zeros(N_COUNTERS, np.uint64)
+        rc = self.lib.orc_power(self.h, n, first_id, seed, p_absorb, inactive, cycles, threads, _ptr(k), _ptr(bank),
+                                _ptr(tally), _ptr(cnt))
+        return {"k": k, "bank": bank, "tally": tally, "counters": cnt, "ok": rc == 0}
 
     def mesh_segment(self, r, d, length: float) -> np.ndarray:
         """Mesh tally of one segment (start r, direction d, length)."""

@@ -217,6 +217,7 @@ struct Geometry {
     int mode = 0;                  // 0: rect trackers for rect arrays; 1: all-CSG (pseudo-arrays)
     int gid = 0;
     std::vector<double> sigma;
+    std::vector<double> nu;        // per material, 0: no fission (power iteration)
     std::vector<Surface> surf;
     std::vector<Universe> univ;
     int root = 0;
@@ -398,6 +399,11 @@ static Geometry* load_geometry(const char* json, size_t len, int mode, std::stri
     const oj::Val* v;
     if ((v = doc.get("geometry_id")) && v->kind == oj::Val::NUM) g->gid = int(v->num);
     if (!nums(doc.get("sigma"), g->sigma) || g->sigma.empty()) { err = "missing sigma"; return nullptr; }
+    g->nu.assign(g->sigma.size(), 0.0);
+    if (doc.get("nu")) {
+        if (!nums(doc.get("nu"), g->nu) || g->nu.size() != g->sigma.size()) { err = "bad nu"; return nullptr; }
+        for (double v : g->nu) if (!(v >= 0.0 && v <= 7.0)) { err = "nu must be in [0, 7]"; return nullptr; }
+    }
     v = doc.get("surfaces");
     if (!v || v->kind != oj::Val::ARR) { err = "missing surfaces"; return nullptr; }
     for (auto& sv : v->arr) {
@@ -564,7 +570,7 @@ static void philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], ui
 // Reading (counter layout): key = (seed_lo32, geometry_id), counter =
 // (particle id, event, tag, k).  Two uniform doubles in (0, 1] per call:
 // xi = ((u64 >> 11) + 1) * 2^-53 with u64 = (o1<<32)|o0 and (o3<<32)|o2.
-enum { TAG_POSITION = 0, TAG_DIRECTION = 1, TAG_SCALARS = 2 };
+enum { TAG_POSITION = 0, TAG_DIRECTION = 1, TAG_SCALARS = 2, TAG_FISSION = 3, TAG_BANK = 4 };
 static void uniform2(uint32_t pid, uint32_t event, uint32_t tag, uint32_t k, uint32_t seed_lo,
                      uint32_t gid, double out[2]) {
     uint32_t ctr[4] = {pid, event, tag, k}, key[2] = {seed_lo, gid}, o[4];
@@ -993,7 +999,17 @@ struct HistoryOut {
     long long nseg = 0;
     uint64_t hash = FNV0;
     double fin[3] = {0, 0, 0};
+    int nsites = 0;                 // fission sites banked at the absorption (power iteration)
+    uint64_t nu_fixed = 0;          // llrint(nu * 2^32) of the absorbing material
 };
+
+// Power iteration (reading of Alg. 1 with a synthetic fission source): an
+// absorption in material m with nu_m > 0 banks floor(nu_m / k + xi) sites at
+// the absorption point, at most FISSION_MAX (k: the previous cycle's
+// estimate, 1 in the first; xi: first value of counter (pid, e, TAG_FISSION,
+// 0), e the absorbing collision's event number) and adds llrint(nu_m * 2^32)
+// to the cycle's nu sum.
+constexpr int FISSION_MAX = 8;
 
 // Mesh track-length tally of one segment (reading): the segment starts at
 // p.r and runs `len` along p.dir.  Per axis, with planes g_0 < ... < g_n,
@@ -1050,13 +1066,34 @@ static void mesh_walk(const Geometry& g, const Particle& p, Real len, uint64_t* 
 // tau = -log(xi_tau); the on-surface state is cleared.
 // A path cutoff (test-only option) ends the history once the accumulated
 // track length reaches max_path, tallying only the part up to it.
+// Birth from a fission bank of B sites (xyz triples, B > 0): site
+// floor(xi * B) (xi: first value of counter (pid, 0, TAG_BANK, 0), B - 1 at
+// xi = 1), direction and tau as from the source box.
+static int sample_birth_bank(const Geometry& g, uint32_t pid, uint32_t seed_lo, const std::vector<double>& bank,
+                             Real r[3], Real dir[3], Real& tau) {
+    const uint32_t gid = uint32_t(g.gid);
+    const long long B = (long long)(bank.size() / 3);
+    double xb[2];
+    uniform2(pid, 0, TAG_BANK, 0, seed_lo, gid, xb);
+    long long j = (long long)std::floor(xb[0] * double(B));
+    if (j >= B) j = B - 1;
+    for (int d = 0; d < 3; ++d) r[d] = bank[size_t(3 * j + d)];
+    if (!isotropic(pid, 0, seed_lo, gid, dir)) return P_SOURCE;
+    double sc[2];
+    uniform2(pid, 0, TAG_SCALARS, 0, seed_lo, gid, sc);
+    tau = -own_log(sc[1]);
+    return P_ALIVE;
+}
+
 template <class Trace>
 static HistoryOut run_one(const Geometry& g, uint32_t pid, uint32_t seed_lo, const RunOpts& o,
-                          uint64_t* tally, unsigned long long* cnt, Trace&& trace, uint64_t* mesh = nullptr) {
+                          uint64_t* tally, unsigned long long* cnt, Trace&& trace, uint64_t* mesh = nullptr,
+                          const std::vector<double>* bank = nullptr, double knorm = 0.0) {
     HistoryOut out;
     Particle p;
     Real tau;
-    out.status = sample_birth(g, pid, seed_lo, p.r, p.dir, tau);
+    out.status = bank ? sample_birth_bank(g, pid, seed_lo, *bank, p.r, p.dir, tau)
+                      : sample_birth(g, pid, seed_lo, p.r, p.dir, tau);
     if (out.status != P_ALIVE) { cnt[K_SOURCE]++; return out; }
     p.tau = tau;
     set_direction_inverse(p);
@@ -1100,7 +1137,19 @@ static HistoryOut run_one(const Geometry& g, uint32_t pid, uint32_t seed_lo, con
             cnt[K_COLLISIONS]++;
             double sc[2];
             uniform2(pid, event, TAG_SCALARS, 0, seed_lo, uint32_t(g.gid), sc);
-            if (sc[0] < o.p_absorb) { out.status = P_ABSORBED; cnt[K_ABSORBED]++; break; }
+            if (sc[0] < o.p_absorb) {
+                out.status = P_ABSORBED;
+                cnt[K_ABSORBED]++;
+                const double nu = g.nu[size_t(p.material)];
+                if (knorm > 0.0 && nu > 0.0) {
+                    double xf[2];
+                    uniform2(pid, event, TAG_FISSION, 0, seed_lo, uint32_t(g.gid), xf);
+                    const double ns = std::floor(nu / knorm + xf[0]);
+                    out.nsites = ns > double(FISSION_MAX) ? FISSION_MAX : int(ns);
+                    out.nu_fixed = uint64_t(std::llrint(nu * 4294967296.0));
+                }
+                break;
+            }
             if (!isotropic(pid, event, seed_lo, uint32_t(g.gid), p.dir)) { out.status = P_LOST; cnt[K_LOST]++; break; }
             set_direction_inverse(p);
             p.tau = -own_log(sc[1]);
@@ -1386,6 +1435,73 @@ int orc_run_mesh(void* gp, long long n, long long first_id, unsigned long long s
         for (int t = 0; t < nthreads; ++t) s += cl[size_t(t)][size_t(k)];
         counters[k] = s;
     }
+    return 0;
+}
+
+// Power iteration (Alg. 1): `cycles` cycles of n histories, the first
+// `inactive` of them not tallied.  Cycle c's particle ids are
+// first_id + c*n .. first_id + c*n + n - 1; cycle 0 is born in the source
+// box, cycle c > 0 from cycle c-1's bank (its sites in history order).
+// k_c = (double(sum over the cycle's fissile absorptions of
+// llrint(nu * 2^32)) * 2^-32) / n.  Writes k_out[c] and bank_out[c] (sites
+// banked); returns 0, or -1 when a cycle banks no site.
+int orc_power(void* gp, long long n, long long first_id, unsigned long long seed, double p_absorb, int inactive,
+              int cycles, int nthreads, double* k_out, long long* bank_out, unsigned long long* tally,
+              unsigned long long* counters) {
+    Geometry* g = static_cast<Geometry*>(gp);
+    RunOpts o;
+    o.p_absorb = p_absorb;
+    o.max_segments = 1000000;
+    o.max_path = INF;
+    const long long ninst = g->univ[g->root].ninst;
+    if (nthreads < 1) nthreads = 1;
+    if (n < nthreads) nthreads = int(std::max<long long>(1, n));
+    std::vector<double> bank;
+    double knorm = 1.0;
+    std::vector<uint64_t> tsum(size_t(ninst), 0);
+    std::vector<unsigned long long> csum(K_NCOUNTERS, 0);
+    for (int c = 0; c < cycles; ++c) {
+        const bool active = c >= inactive;
+        std::vector<HistoryOut> hist(static_cast<size_t>(n));
+        std::vector<std::vector<uint64_t>> tl(size_t(nthreads), std::vector<uint64_t>(size_t(ninst), 0));
+        std::vector<std::vector<unsigned long long>> cl(size_t(nthreads), std::vector<unsigned long long>(K_NCOUNTERS, 0));
+        const std::vector<double>* src = c == 0 ? nullptr : &bank;
+        auto work = [&](int t) {
+            long long lo = n * t / nthreads, hi = n * (t + 1) / nthreads;
+            for (long long i = lo; i < hi; ++i)
+                hist[size_t(i)] = run_one(*g, uint32_t(first_id + (long long)c * n + i), uint32_t(seed), o,
+                                          tl[size_t(t)].data(), cl[size_t(t)].data(), [](long long, double, int) {},
+                                          nullptr, src, knorm);
+        };
+        if (nthreads == 1) work(0);
+        else {
+            std::vector<std::thread> th;
+            for (int t = 0; t < nthreads; ++t) th.emplace_back(work, t);
+            for (auto& x : th) x.join();
+        }
+        uint64_t nusum = 0;
+        std::vector<double> next;
+        for (long long i = 0; i < n; ++i) {
+            const HistoryOut& h = hist[size_t(i)];
+            nusum += h.nu_fixed;
+            for (int k = 0; k < h.nsites; ++k)
+                for (int d = 0; d < 3; ++d) next.push_back(h.fin[d]);
+        }
+        const double kc = (double(nusum) * 0x1p-32) / double(n);
+        k_out[c] = kc;
+        bank_out[c] = (long long)(next.size() / 3);
+        if (active) {
+            for (int t = 0; t < nthreads; ++t) {
+                for (long long b = 0; b < ninst; ++b) tsum[size_t(b)] += tl[size_t(t)][size_t(b)];
+                for (int k = 0; k < K_NCOUNTERS; ++k) csum[size_t(k)] += cl[size_t(t)][size_t(k)];
+            }
+        }
+        if (next.empty()) return -1;
+        bank.swap(next);
+        knorm = kc;
+    }
+    for (long long b = 0; b < ninst; ++b) tally[b] = tsum[size_t(b)];
+    for (int k = 0; k < K_NCOUNTERS; ++k) counters[k] = csum[size_t(k)];
     return 0;
 }
 

@@ -529,3 +529,11 @@ def with_mesh(desc: dict, nx: int, ny: int, nz: int, box=None) -> dict:
         grid.append([float(v) for v in g])
     d["mesh"] = {"grid": grid}
     return d
+
+
+def with_nu(desc: dict, nu) -> dict:
+    """A copy of `desc` with per-material fission yields nu (0: no fission),
+    for the power iteration."""
+    d = dict(desc)
+    d["nu"] = [float(v) for v in nu]
+    return d

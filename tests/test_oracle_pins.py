@@ -467,3 +467,46 @@ def test_mesh_total_equals_track_length():
         b = float(r["tally"].sum()) / 2**32
         assert abs(a - b) <= 1e-9 * b
         assert (r["mesh"] > 0).mean() > 0.5
+
+
+# ---------------------------------------------------------------------------
+# power iteration with the synthetic fission source
+# ---------------------------------------------------------------------------
+
+def test_power_infinite_medium_k_equals_nu():
+    # one material everywhere, reflecting box: every history ends in an
+    # absorption, so every cycle's estimate is nu exactly; after the first
+    # cycle (normalised by k = 1) each history banks floor(1 + xi) = 1 site
+    d = I.with_nu(I.config1(sigma=(0.5, 0.5, 0.5)), (2.5, 2.5, 2.5))
+    n = 2000
+    r = _geom(d).power(n, 1, 0.3, 2, 5, threads=4)
+    assert r["ok"] and np.all(r["k"] == 2.5)
+    assert np.all(r["bank"][1:] == n)
+    assert abs(r["bank"][0] - 2.5 * n) <= 5 * np.sqrt(n)
+
+
+def test_power_bank_size_matches_estimate():
+    # E[sites] = sum(nu) / k_prev = n k_c / k_{c-1}; each history's count
+    # varies by less than one site
+    d = I.with_nu(I.small_core(), (2.4, 0.0, 0.0, 0.0))
+    n = 20_000
+    r = _geom(d).power(n, 1, 0.25, 2, 6, threads=8)
+    assert r["ok"]
+    k, b = r["k"], r["bank"]
+    assert abs(b[0] - n * k[0]) <= 5 * np.sqrt(n)
+    for c in range(1, 6):
+        assert abs(b[c] - n * k[c] / k[c - 1]) <= 5 * np.sqrt(n), c
+    assert 0.3 < k.mean() < 2.4
+
+
+def test_power_deterministic_and_sharded_threads():
+    d = I.with_nu(I.config1(), (2.0, 0.0, 0.0))
+    a = _geom(d).power(3000, 3, 0.3, 1, 3, threads=1)
+    b = _geom(d).power(3000, 3, 0.3, 1, 3, threads=7)
+    assert np.array_equal(a["k"], b["k"]) and np.array_equal(a["bank"], b["bank"])
+    assert np.array_equal(a["tally"], b["tally"])
+
+
+def test_power_without_fissile_material_stops():
+    r = _geom(I.config1()).power(500, 1, 0.3, 1, 3)
+    assert not r["ok"] and r["k"][0] == 0.0
