@@ -146,6 +146,38 @@ trk_status geometry_destroy(trk_geom_t g);
 trk_status geometry_info(trk_geom_t g, int64_t* n_instances, int32_t* n_materials,
                          int32_t* max_depth, int32_t* rect_ok);
 
+/*
+ * power_iteration - Alg. 1: `cycles` cycles of n histories, the first
+ * `inactive` of them untallied, with a synthetic fission source.  The
+ * description's optional "nu" (one value per material in [0, 7], 0 = none)
+ * gives the fission yield: an absorption in material m with nu_m > 0 banks
+ * floor(nu_m / k + xi) sites at the absorption point (at most 8; k the
+ * previous cycle's estimate, 1 in the first cycle; xi from counter
+ * (pid, e, 3, 0), e the absorbing collision).  Cycle 0 is born in the source
+ * box, cycle c > 0 from cycle c-1's sites (kept in history order): particle
+ * i of cycle c has id first_id + c*n + i and takes site floor(xi * B) (xi
+ * from counter (pid, 0, 4, 0)), the direction and tau of source_init.
+ *   dev_k      out: double[cycles], k_c = (double(sum of llrint(nu * 2^32)
+ *              over the cycle's fissile absorptions) * 2^-32) / n
+ *   dev_bank   out: int64[cycles], sites banked per cycle
+ *   dev_tally, dev_counters: added to over the active cycles only
+ *   dev_work   scratch of power_iteration_work_bytes (256-byte aligned):
+ *              the particles, per-history sites, the bank (8n sites) and,
+ *              in event mode, the event kernel's slot records
+ *   opts       tracker, mode (history or event), seed, first_id, p_absorb,
+ *              max_segments, queue_depth, mesh_tally (tallied in active
+ *              cycles); FP64 only, no path cutoff.
+ * Everything runs on `stream` without a host synchronisation (the cycle
+ * count is fixed), so the whole iteration can be captured in a CUDA graph.
+ * A cycle that banks no site writes TRK_E_SOURCE to counters[TRK_K_STATUS].
+ * The paper's fission physics (nuclear data, energy) is out of scope: this
+ * source stands in for it.
+ */
+trk_status power_iteration_work_bytes(trk_geom_t g, int64_t n, const trk_run_opts* opts, size_t* bytes);
+trk_status power_iteration(trk_geom_t g, int64_t n, int inactive, int cycles, double* dev_k, int64_t* dev_bank,
+                           uint64_t* dev_tally, uint64_t* dev_counters, void* dev_work, size_t work_bytes,
+                           const trk_run_opts* opts, void* stream);
+
 /* Bins of the description's superimposed mesh ("mesh": {"grid": [x planes,
  * y planes, z planes]}, increasing planes per axis), 0 without one.  The mesh
  * tally (trk_run_opts.mesh_tally) walks each segment across the mesh planes

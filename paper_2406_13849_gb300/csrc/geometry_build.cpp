@@ -200,6 +200,7 @@ struct HGeom {
     int accel = 0;                 // CSG cell search: 0 BVH, 1 BIH
     int gid = 0;
     std::vector<double> sigma;
+    std::vector<double> nu;
     std::vector<HSurf> surf;
     std::vector<HUniv> univ;
     int root = 0;
@@ -244,6 +245,11 @@ int parse(const char* json, size_t len, HGeom& G) {
     if (num(J, root, "geometry_id", x)) G.gid = int(x);
     if (!read_nums(J, J.member(root, "sigma"), G.sigma) || G.sigma.empty()) DESC_FAIL("'sigma' missing or empty");
     for (double s : G.sigma) if (!(s >= 0.0) || !std::isfinite(s)) DESC_FAIL("sigma must be finite and >= 0");
+    G.nu.assign(G.sigma.size(), 0.0);
+    if (J.member(root, "nu") >= 0) {
+        if (!read_nums(J, J.member(root, "nu"), G.nu) || G.nu.size() != G.sigma.size()) DESC_FAIL("'nu' needs one value per material");
+        for (double v : G.nu) if (!(v >= 0.0 && v <= 7.0)) DESC_FAIL("nu must be in [0, 7]");
+    }
     int sl = J.member(root, "surfaces");
     if (sl < 0 || J.at(sl).t != 'a') DESC_FAIL("'surfaces' missing");
     for (size_t i = 0; i < J.at(sl).kids.size(); ++i) {
@@ -883,7 +889,7 @@ void copy_into(std::vector<unsigned char>& img, size_t off, const std::vector<T>
 
 struct Built {
     std::vector<unsigned char> image;
-    size_t offs[40] = {};
+    size_t offs[48] = {};
     HGeom G;
     int n_nodes = 0;
 };
@@ -1196,6 +1202,7 @@ int build_host(const char* json, size_t len, Built& B) {
     o[15] = L.put(nodes.size() * sizeof(BvhNode));
     o[16] = L.put(leaf.size() * 4);
     o[17] = L.put(G.sigma.size() * 8);
+    o[39] = L.put(G.nu.size() * 8);
     o[18] = L.put(s_key.size() * 8);
     o[19] = L.put(cs_adj.size() * sizeof(int2));
     o[20] = L.put(l_gkey.size() * 8);
@@ -1250,6 +1257,7 @@ int build_host(const char* json, size_t len, Built& B) {
     copy_into(B.image, o[15], nodes);
     copy_into(B.image, o[16], leaf);
     copy_into(B.image, o[17], G.sigma);
+    copy_into(B.image, o[39], G.nu);
     copy_into(B.image, o[18], s_key);
     copy_into(B.image, o[19], cs_adj);
     copy_into(B.image, o[20], l_gkey);
@@ -1341,6 +1349,7 @@ trk_status geometry_build(const char* json, size_t len, void* dev_buf, size_t* d
     d.nodes = reinterpret_cast<const BvhNode*>(base + o[15]);
     d.leaf_cells = reinterpret_cast<const int*>(base + o[16]);
     d.sigma = reinterpret_cast<const double*>(base + o[17]);
+    d.nu = reinterpret_cast<const double*>(base + o[39]);
     d.s_key = reinterpret_cast<const long long*>(base + o[18]);
     d.cs_adj = reinterpret_cast<const int2*>(base + o[19]);
     d.l_gkey = reinterpret_cast<const long long*>(base + o[20]);

@@ -66,7 +66,7 @@ __device__ __forceinline__ void f32_bounds(double x, float& lo, float& hi) {
 // (particle id, event, tag, k), key (seed_lo32, geometry id); two doubles in
 // (0, 1] per call: ((u64 >> 11) + 1) * 2^-53.
 // ---------------------------------------------------------------------------
-enum { TAG_POSITION = 0, TAG_DIRECTION = 1, TAG_SCALARS = 2 };
+enum { TAG_POSITION = 0, TAG_DIRECTION = 1, TAG_SCALARS = 2, TAG_FISSION = 3, TAG_BANK = 4 };
 
 __device__ __forceinline__ uint4 philox10(uint4 c, uint2 k) {
     const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
@@ -1090,6 +1090,12 @@ struct RunP {
     uint32_t seed_lo;
     int trace_cap;
     unsigned long long* mesh;   // mesh track-length tally (F_MESH)
+    // power iteration (F_FISS): the previous cycle's k, per-history fission
+    // outputs, the cycle's nu sum
+    const double* knorm;
+    double* fis_pos;            // 3 per history
+    int* fis_n;                 // sites per history
+    unsigned long long* nu_sum;
 };
 
 // Per-thread event counts (32-bit: one thread tracks far fewer than 2^32
@@ -1113,7 +1119,7 @@ __device__ __forceinline__ void kernel_status(unsigned long long* cnt, int st) {
     atomicCAS(cnt + TRK_K_STATUS, 0ULL, (unsigned long long)(long long)st);
 }
 
-enum { F_REC = 1, F_CUT = 2, F_TRACE = 4, F_MESH = 8 };
+enum { F_REC = 1, F_CUT = 2, F_TRACE = 4, F_MESH = 8, F_FISS = 16 };
 
 // Mesh index per axis: the largest i in -1..n with g_i <= x (-1 and n are the
 // two sides outside the mesh), by order keys; the start guess from the
@@ -1167,6 +1173,31 @@ __device__ __forceinline__ void mesh_walk(const DevGeom& g, const St& s, double 
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Power iteration (Alg. 1) with a synthetic fission source: an absorption in
+// a material with nu > 0 banks floor(nu / k + xi) sites (at most
+// FISSION_MAX) at the absorption point, k the previous cycle's estimate
+// (*rp.knorm) and xi the first value of counter (pid, e, TAG_FISSION, 0), e
+// the absorbing collision's event number; the cycle's nu sum gains
+// llrint(nu * 2^32).  Returns the site count.
+constexpr int FISSION_MAX = 8;
+
+__device__ __forceinline__ int fission_sites(const DevGeom& g, uint32_t pid, uint32_t event, int mat, const RunP& rp) {
+    const double nu = __ldg(g.nu + mat);
+    const double k = *rp.knorm;
+    if (!d_gt0(k) || !d_gt0(nu)) return 0;
+    double xf, unused;
+    uniform2(pid, event, TAG_FISSION, 0, rp.seed_lo, uint32_t(g.gid), xf, unused);
+    const double ns = floor(nu / k + xf);
+    atomicAdd(rp.nu_sum, (unsigned long long)__double2ll_rn(nu * 4294967296.0));
+    return d_lt(ns, double(FISSION_MAX)) ? int(ns) : FISSION_MAX;
+}
+
+__device__ __forceinline__ void fission_out(const RunP& rp, long long i, int ns, double x, double y, double z) {
+    rp.fis_n[i] = ns;
+    if (ns > 0) { rp.fis_pos[3 * i] = x; rp.fis_pos[3 * i + 1] = y; rp.fis_pos[3 * i + 2] = z; }
+}
 
 // ---------------------------------------------------------------------------
 // One history as three steps (shared by the history and event kernels).

@@ -107,7 +107,10 @@ __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, lo
                         ok = true;
                     }
                 }
-                if (!ok) finish<FLAGS>(pidx, c, rec);
+                if (!ok) {
+                    finish<FLAGS>(pidx, c, rec);
+                    if (FLAGS & F_FISS) fission_out(rp, pidx, 0, 0.0, 0.0, 0.0);
+                }
             }
 #pragma unroll
             for (int q = 0; q < NFC; ++q) wpush(ok && cls == q, slot - slot0, qfl + q * slots, n_fl[q]);
@@ -155,6 +158,7 @@ __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, lo
                 a = step_fly<CSG, F32, FLAGS>(g, s, h, c, rp, tally, cnt, nullptr, nullptr, 0);
                 if (a == A_DONE) {
                     finish<FLAGS>(pidx, c, rec);
+                    if (FLAGS & F_FISS) fission_out(rp, pidx, 0, 0.0, 0.0, 0.0);
                 } else {
                     D2(r, R_XY) = make_double2(s.x, s.y);
                     D2(r, R_ZT) = make_double2(s.z, s.tau);
@@ -203,6 +207,7 @@ __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, lo
                 a = step_cross<CSG>(g, s, h, c, rp, cnt);
                 if (a == A_DONE) {
                     finish<FLAGS>(pidx, c, rec);
+                    if (FLAGS & F_FISS) fission_out(rp, pidx, 0, 0.0, 0.0, 0.0);
                 } else {
                     cls = flight_class<CSG>(g, s);
                     store_levels<CSG>(r, s, cls);
@@ -227,6 +232,16 @@ __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, lo
                 a = step_collide(g, s, c, rp, cnt);
                 if (a == A_DONE) {
                     finish<FLAGS>(pidx, c, rec);
+                    if (FLAGS & F_FISS) {
+                        int nf = 0;
+                        double fx = 0.0, fy = 0.0, fz = 0.0;
+                        if (c.status == TRK_P_ABSORBED) {
+                            const double2 xy = D2(r, R_XY), zt = D2(r, R_ZT);
+                            fx = xy.x; fy = xy.y; fz = zt.x;
+                            nf = fission_sites(g, c.pid, c.event, I4(r, R_LV).w, rp);
+                        }
+                        fission_out(rp, pidx, nf, fx, fy, fz);
+                    }
                 } else {
                     store_dir(r, s);
                     const double z = D2(r, R_ZT).x;
@@ -312,6 +327,8 @@ trk_status launch_event(trk_geom_t g, const ParticlesView& P, long long n, const
             case F_CUT: TRK_EV(true, false, F_CUT); break;
             case F_MESH: TRK_EV(true, false, F_MESH); break;
             case F_MESH | F_REC: TRK_EV(true, false, F_MESH | F_REC); break;
+            case F_FISS: TRK_EV(true, false, F_FISS); break;
+            case F_FISS | F_MESH: TRK_EV(true, false, F_FISS | F_MESH); break;
             default: TRK_EV(true, false, F_REC | F_CUT); break;
         }
     } else {
@@ -321,6 +338,8 @@ trk_status launch_event(trk_geom_t g, const ParticlesView& P, long long n, const
             case F_CUT: TRK_EV(false, false, F_CUT); break;
             case F_MESH: TRK_EV(false, false, F_MESH); break;
             case F_MESH | F_REC: TRK_EV(false, false, F_MESH | F_REC); break;
+            case F_FISS: TRK_EV(false, false, F_FISS); break;
+            case F_FISS | F_MESH: TRK_EV(false, false, F_FISS | F_MESH); break;
             default: TRK_EV(false, false, F_REC | F_CUT); break;
         }
     }

@@ -139,6 +139,7 @@ struct DevGeom {
     const int* leaf_cells;
     // materials
     const double* sigma;
+    const double* nu;         // fission yield per material (0: none), power iteration
     double src_lo[3], src_hi[3];
     int root, n_inst, n_mat, gid, max_depth, n_univ, n_cells, n_surf;
     int rect_ok;              // the array tracker applies (always 1: hex arrays by closed-form search)

@@ -57,6 +57,8 @@ __device__ __forceinline__ void history(const DevGeom& g, const ParticlesView& P
     Ctx c;
     c.pid = uint32_t(rp.first_id + uint64_t(i));
     c.event = 0; c.nseg = 0; c.path = 0.0; c.hash = FNV0; c.status = 0;
+    int nfis = 0;
+    double fx = 0.0, fy = 0.0, fz = 0.0;
     const int pst = P.status[i];
     if (pst != 0) {
         c.status = pst;
@@ -75,8 +77,13 @@ __device__ __forceinline__ void history(const DevGeom& g, const ParticlesView& P
                 a = (a == A_CROSS) ? step_cross<CSG>(g, s, h, c, rp, cnt) : step_collide(g, s, c, rp, cnt);
                 if (a == A_DONE) break;
             }
+            if ((FLAGS & F_FISS) && c.status == TRK_P_ABSORBED) {
+                nfis = fission_sites(g, c.pid, c.event, s.mat, rp);
+                fx = s.x; fy = s.y; fz = s.z;
+            }
         }
     }
+    if (FLAGS & F_FISS) fission_out(rp, i, nfis, fx, fy, fz);
     if (FLAGS & F_REC) {
         rec[2 * i] = c.hash;
         rec[2 * i + 1] = (uint64_t(c.nseg) << 32) | uint32_t(c.status);
@@ -694,6 +701,277 @@ trk_status transmission_bwd(trk_geom_t g, int tracker, int64_t n, const double* 
     if (e != TRK_OK) return e;
     k_reduce_partials<<<1, 32, 0, s>>>(partial, nb, nq, dev_grad);
     return launch_error("transmission_bwd reduce");
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Power iteration (Alg. 1): cycles of run_histories whose births come from
+// the previous cycle's fission bank.  The bank keeps the sites in history
+// order (a block scan of the per-history counts), so the births of the next
+// cycle, which pick sites by index, do not depend on thread timing.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int BANK_BLOCK = 1024;
+
+// Exclusive scan over a block of BANK_BLOCK threads; *total gets the sum.
+__device__ long long block_exclusive_scan(long long v, long long* total) {
+    __shared__ long long wsum[BANK_BLOCK / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        long long t = wsum[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        wsum[lane] = t;
+    }
+    __syncthreads();
+    const long long before = w > 0 ? wsum[w - 1] : 0;
+    *total = wsum[BANK_BLOCK / 32 - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+__global__ void __launch_bounds__(BANK_BLOCK) k_bank_count(const int* __restrict__ fis_n, long long n,
+                                                           long long* __restrict__ bsum) {
+    const long long i = (long long)blockIdx.x * BANK_BLOCK + threadIdx.x;
+    long long tot;
+    block_exclusive_scan(i < n ? fis_n[i] : 0, &tot);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+// One block: block sums to offsets, the bank size, and the cycle's
+// k = (double(nu sum) * 2^-32) / n, the next cycle's normalisation.
+__global__ void __launch_bounds__(BANK_BLOCK) k_bank_scan(long long* __restrict__ bsum, long long nb, long long n,
+                                                          const unsigned long long* __restrict__ nu_sum,
+                                                          double* __restrict__ knorm, double* __restrict__ k_out,
+                                                          long long* __restrict__ bank_out,
+                                                          long long* __restrict__ bank_size,
+                                                          unsigned long long* __restrict__ counters) {
+    long long carry = 0;
+    for (long long base = 0; base < nb; base += BANK_BLOCK) {
+        const long long idx = base + threadIdx.x;
+        const long long v = idx < nb ? bsum[idx] : 0;
+        long long tot;
+        const long long ex = block_exclusive_scan(v, &tot);
+        if (idx < nb) bsum[idx] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) {
+        *bank_size = carry;
+        *bank_out = carry;
+        const double k = (double(*nu_sum) * 0x1p-32) / double(n);
+        *k_out = k;
+        *knorm = k;
+        if (carry == 0) kernel_status(counters, TRK_E_SOURCE);
+    }
+}
+
+__global__ void __launch_bounds__(BANK_BLOCK) k_bank_write(const int* __restrict__ fis_n,
+                                                           const double* __restrict__ fis_pos, long long n,
+                                                           const long long* __restrict__ boff,
+                                                           double* __restrict__ bank) {
+    const long long i = (long long)blockIdx.x * BANK_BLOCK + threadIdx.x;
+    const int v = i < n ? fis_n[i] : 0;
+    long long tot;
+    const long long off = boff[blockIdx.x] + block_exclusive_scan(v, &tot);
+    for (int j = 0; j < v; ++j) {
+        bank[3 * (off + j)] = fis_pos[3 * i];
+        bank[3 * (off + j) + 1] = fis_pos[3 * i + 1];
+        bank[3 * (off + j) + 2] = fis_pos[3 * i + 2];
+    }
+}
+
+// Births from a bank of *bank_size sites: particle i (id first_id + i) takes
+// site floor(xi * B) (xi: first value of counter (pid, 0, TAG_BANK, 0); B - 1
+// at xi = 1), the direction and tau of the source-box births.
+__global__ void __launch_bounds__(128) k_source_bank(const DevGeom g, long long n, uint64_t first_id, uint32_t seed_lo,
+                                                     const double* __restrict__ bank,
+                                                     const long long* __restrict__ bank_size, double* __restrict__ buf) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const uint32_t gid = uint32_t(g.gid);
+    const long long B = *bank_size;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint32_t pid = uint32_t(first_id + uint64_t(i));
+        double x = 0, y = 0, z = 0, u = 0, v = 0, w = 1, tau = 0;
+        int st = TRK_E_SOURCE;
+        if (B > 0) {
+            double xb, unused;
+            uniform2(pid, 0, TAG_BANK, 0, seed_lo, gid, xb, unused);
+            long long j = (long long)floor(xb * double(B));
+            if (j >= B) j = B - 1;
+            x = bank[3 * j]; y = bank[3 * j + 1]; z = bank[3 * j + 2];
+            if (isotropic(pid, 0, seed_lo, gid, u, v, w)) {
+                double unused2, xt;
+                uniform2(pid, 0, TAG_SCALARS, 0, seed_lo, gid, unused2, xt);
+                tau = -own_log(xt);
+                st = 0;
+            }
+        }
+        buf[i] = x; buf[n + i] = y; buf[2 * n + i] = z;
+        buf[3 * n + i] = u; buf[4 * n + i] = v; buf[5 * n + i] = w;
+        buf[6 * n + i] = tau;
+        reinterpret_cast<int*>(buf + 7 * n)[i] = st;
+    }
+}
+
+__global__ void k_set_double(double* p, double v) { *p = v; }
+
+// A kernel-level status of an inactive cycle (whose counters are scratch)
+// is carried to the caller's counters.
+__global__ void k_carry_status(const unsigned long long* from, unsigned long long* to) {
+    if (from[TRK_K_STATUS] != 0ULL) atomicCAS(to + TRK_K_STATUS, 0ULL, from[TRK_K_STATUS]);
+}
+
+size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct PowerLayout {
+    size_t parts, fis_pos, fis_n, bsum, bank, tally, cnt, scal, ev, total;
+};
+
+PowerLayout power_layout(trk_geom_t g, long long n, const trk_run_opts& o) {
+    PowerLayout L;
+    const long long nb = (n + BANK_BLOCK - 1) / BANK_BLOCK;
+    size_t off = 0;
+    L.parts = off; off += al256(particle_bytes(n));
+    L.fis_pos = off; off += al256(size_t(n) * 3 * sizeof(double));
+    L.fis_n = off; off += al256(size_t(n) * sizeof(int));
+    L.bsum = off; off += al256(size_t(nb > 0 ? nb : 1) * sizeof(long long));
+    L.bank = off; off += al256(size_t(n) * FISSION_MAX * 3 * sizeof(double));
+    L.tally = off; off += al256(size_t(g->n_inst) * sizeof(unsigned long long));
+    L.cnt = off; off += al256(TRK_NCOUNTERS * sizeof(unsigned long long));
+    L.scal = off; off += 256;   // knorm, nu sum, bank size
+    L.ev = off;
+    if (o.mode == TRK_MODE_EVENT) {
+        const int slots = event_slots(o);
+        off += al256(event_work_bytes(slots, o.grid > 0 ? o.grid : event_grid(slots)));
+    }
+    L.total = off;
+    return L;
+}
+
+}  // namespace
+
+extern "C" {
+
+trk_status power_iteration_work_bytes(trk_geom_t g, int64_t n, const trk_run_opts* opts, size_t* bytes) {
+    if (!valid(g) || n <= 0 || !bytes) return trk_status(set_error(TRK_E_INVALID, "power_iteration_work_bytes: bad arguments"));
+    trk_run_opts o;
+    trk_default_opts(&o);
+    if (opts) o = *opts;
+    if (o.mode == TRK_MODE_EVENT) {
+        const int slots = event_slots(o);
+        if (slots < 32 || slots > 512) return trk_status(set_error(TRK_E_INVALID, "queue_depth must be in [32, 512]"));
+    }
+    *bytes = power_layout(g, n, o).total;
+    return TRK_OK;
+}
+
+trk_status power_iteration(trk_geom_t g, int64_t n, int inactive, int cycles, double* dev_k, int64_t* dev_bank,
+                           uint64_t* dev_tally, uint64_t* dev_counters, void* dev_work, size_t work_bytes,
+                           const trk_run_opts* opts, void* stream) {
+    if (!valid(g) || n <= 0 || cycles <= 0 || inactive < 0 || inactive > cycles || !dev_k || !dev_bank || !dev_tally ||
+        !dev_counters)
+        return trk_status(set_error(TRK_E_INVALID, "power_iteration: bad arguments"));
+    if (n > (int64_t(1) << 31) || (long long)cycles * n > (int64_t(1) << 32))
+        return trk_status(set_error(TRK_E_INVALID, "power_iteration: cycles * n exceeds 2^32 particle ids"));
+    trk_run_opts o;
+    trk_default_opts(&o);
+    if (opts) o = *opts;
+    trk_status st;
+    const int tracker = resolve_tracker(g, o.tracker, &st);
+    if (tracker < 0) return st;
+    if (o.precision != TRK_FP64) return trk_status(set_error(TRK_E_UNSUPPORTED, "power_iteration: FP64 only"));
+    if (o.mode != TRK_MODE_HISTORY && o.mode != TRK_MODE_EVENT)
+        return trk_status(set_error(TRK_E_INVALID, "power_iteration: unknown mode %d", o.mode));
+    if (o.max_path > 0.0 && o.max_path < DINF)
+        return trk_status(set_error(TRK_E_UNSUPPORTED, "power_iteration: no path cutoff"));
+    if (o.mesh_tally && !g->dg.m_n[0])
+        return trk_status(set_error(TRK_E_INVALID, "power_iteration: mesh tally given but the geometry has no mesh"));
+    if (!(o.p_absorb >= 0.0 && o.p_absorb <= 1.0)) return trk_status(set_error(TRK_E_INVALID, "power_iteration: p_absorb outside [0,1]"));
+    if (o.mode == TRK_MODE_EVENT && o.max_rounds < 0) return trk_status(set_error(TRK_E_INVALID, "max_rounds must be >= 0"));
+    const PowerLayout L = power_layout(g, n, o);
+    if (!dev_work || work_bytes < L.total)
+        return trk_status(set_error(TRK_E_NOMEM, "power_iteration: work buffer needs %zu bytes", L.total));
+    if ((reinterpret_cast<uintptr_t>(dev_work) & 255) != 0)
+        return trk_status(set_error(TRK_E_INVALID, "power_iteration: work buffer must be 256-byte aligned"));
+    unsigned char* w = static_cast<unsigned char*>(dev_work);
+    double* parts = reinterpret_cast<double*>(w + L.parts);
+    double* fis_pos = reinterpret_cast<double*>(w + L.fis_pos);
+    int* fis_n = reinterpret_cast<int*>(w + L.fis_n);
+    long long* bsum = reinterpret_cast<long long*>(w + L.bsum);
+    double* bank = reinterpret_cast<double*>(w + L.bank);
+    auto* scratch_tally = reinterpret_cast<unsigned long long*>(w + L.tally);
+    auto* scratch_cnt = reinterpret_cast<unsigned long long*>(w + L.cnt);
+    double* knorm = reinterpret_cast<double*>(w + L.scal);
+    auto* nu_sum = reinterpret_cast<unsigned long long*>(w + L.scal + 8);
+    long long* bank_size = reinterpret_cast<long long*>(w + L.scal + 16);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const long long nb = (n + BANK_BLOCK - 1) / BANK_BLOCK;
+    const bool csg = tracker == TRK_TRACKER_CSG;
+    k_set_double<<<1, 1, 0, s>>>(knorm, 1.0);
+    const ParticlesView P = view_of(parts, n);
+    for (int c = 0; c < cycles; ++c) {
+        const bool active = c >= inactive;
+        const uint64_t first = o.first_id + uint64_t(c) * uint64_t(n);
+        if (c == 0) {
+            k_source<<<persistent_grid(k_source, 128, n, 0), 128, 0, s>>>(g->dg, n, first, uint32_t(o.seed), parts);
+        } else {
+            k_source_bank<<<persistent_grid(k_source_bank, 128, n, 0), 128, 0, s>>>(g->dg, n, first, uint32_t(o.seed),
+                                                                                     bank, bank_size, parts);
+        }
+        if ((st = launch_error("power_iteration source")) != TRK_OK) return st;
+        cudaMemsetAsync(nu_sum, 0, sizeof(unsigned long long), s);
+        // an inactive cycle's counters are scratch; its status must start at 0
+        if (!active) cudaMemsetAsync(scratch_cnt, 0, TRK_NCOUNTERS * sizeof(unsigned long long), s);
+        RunP rp;
+        rp.first_id = first;
+        rp.max_segments = o.max_segments ? o.max_segments : 1000000ULL;
+        rp.p_absorb = o.p_absorb;
+        rp.max_path = DINF;
+        rp.seed_lo = uint32_t(o.seed);
+        rp.trace_cap = 0;
+        rp.mesh = active ? reinterpret_cast<unsigned long long*>(o.mesh_tally) : nullptr;
+        rp.knorm = knorm;
+        rp.fis_pos = fis_pos;
+        rp.fis_n = fis_n;
+        rp.nu_sum = nu_sum;
+        auto* T = active ? reinterpret_cast<unsigned long long*>(dev_tally) : scratch_tally;
+        auto* C = active ? reinterpret_cast<unsigned long long*>(dev_counters) : scratch_cnt;
+        const int flags = F_FISS | (rp.mesh ? F_MESH : 0);
+        if (o.mode == TRK_MODE_EVENT) {
+            const int slots = event_slots(o);
+            const int grid = o.grid > 0 ? o.grid : event_grid(slots);
+            st = launch_event(g, P, n, rp, csg, false, flags, T, C, nullptr, w + L.ev, L.total - L.ev, slots, grid,
+                              o.max_rounds, s);
+        } else {
+            const int block = o.block > 0 ? o.block : 128;
+            if (block > 128 || (block & 31)) return trk_status(set_error(TRK_E_INVALID, "power_iteration: block must be a multiple of 32, <= 128"));
+            if (csg) st = flags & F_MESH ? launch_history<true, false, F_FISS | F_MESH>(g, P, n, rp, T, C, nullptr, nullptr, nullptr, block, o.grid, s)
+                                        : launch_history<true, false, F_FISS>(g, P, n, rp, T, C, nullptr, nullptr, nullptr, block, o.grid, s);
+            else st = flags & F_MESH ? launch_history<false, false, F_FISS | F_MESH>(g, P, n, rp, T, C, nullptr, nullptr, nullptr, block, o.grid, s)
+                                    : launch_history<false, false, F_FISS>(g, P, n, rp, T, C, nullptr, nullptr, nullptr, block, o.grid, s);
+        }
+        if (st != TRK_OK) return st;
+        if (!active) k_carry_status<<<1, 1, 0, s>>>(scratch_cnt, reinterpret_cast<unsigned long long*>(dev_counters));
+        k_bank_count<<<unsigned(nb), BANK_BLOCK, 0, s>>>(fis_n, n, bsum);
+        k_bank_scan<<<1, BANK_BLOCK, 0, s>>>(bsum, nb, n, nu_sum, knorm, dev_k + c, reinterpret_cast<long long*>(dev_bank) + c,
+                                             bank_size, reinterpret_cast<unsigned long long*>(dev_counters));
+        k_bank_write<<<unsigned(nb), BANK_BLOCK, 0, s>>>(fis_n, fis_pos, n, bsum, bank);
+        if ((st = launch_error("power_iteration bank")) != TRK_OK) return st;
+    }
+    return TRK_OK;
 }
 
 }  // extern "C"

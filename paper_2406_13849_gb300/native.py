@@ -74,6 +74,9 @@ def library(exact: bool = False):
             "geometry_destroy": (ctypes.c_int, [_P]),
             "geometry_info": (ctypes.c_int, [_P, pi64, pi32, pi32, pi32]),
             "geometry_mesh_bins": (ctypes.c_int, [_P, pi64]),
+            "power_iteration_work_bytes": (ctypes.c_int, [_P, i64, ctypes.POINTER(RunOpts), psz]),
+            "power_iteration": (ctypes.c_int, [_P, i64, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P, sz,
+                                               ctypes.POINTER(RunOpts), _P]),
             "source_init": (ctypes.c_int, [_P, i64, u64, u64, _P, psz, _P]),
             "run_histories_work_bytes": (ctypes.c_int, [_P, i64, ctypes.POINTER(RunOpts), psz]),
             "run_histories": (ctypes.c_int, [_P, _P, i64, _P, _P, _P, _P, sz, ctypes.POINTER(RunOpts), _P]),
@@ -221,6 +224,29 @@ class Geometry:
         _check(self.lib, self.lib.run_histories(self.h, _ptr(particles), n, _ptr(tally), _ptr(counters), _ptr(rec),
                                                 wp, wlen, ctypes.byref(opts), _stream(stream)))
         return tally, counters, rec
+
+    def power_iteration(self, n: int, inactive: int, cycles: int, tally=None, counters=None, mesh=None,
+                        opts: RunOpts | None = None, stream=None, **kw):
+        """Alg. 1 with the synthetic fission source ("nu" in the description):
+        returns (k per cycle, sites banked per cycle) as device tensors, and
+        the tally and counters of the active cycles."""
+        opts = RunOpts.from_buffer_copy(opts) if opts is not None else default_opts(**kw)
+        if mesh is not None:
+            opts.mesh_tally = mesh.data_ptr()
+        if tally is None:
+            tally = torch.zeros(self.n_inst, dtype=torch.int64, device=self.device)
+        if counters is None:
+            counters = torch.zeros(NCOUNTERS, dtype=torch.int64, device=self.device)
+        k = torch.zeros(cycles, dtype=torch.float64, device=self.device)
+        bank = torch.zeros(cycles, dtype=torch.int64, device=self.device)
+        b = ctypes.c_size_t(0)
+        _check(self.lib, self.lib.power_iteration_work_bytes(self.h, n, ctypes.byref(opts), ctypes.byref(b)))
+        work = torch.empty(b.value + 256, dtype=torch.uint8, device=self.device)
+        off = (-work.data_ptr()) % 256
+        _check(self.lib, self.lib.power_iteration(self.h, n, inactive, cycles, _ptr(k), _ptr(bank), _ptr(tally),
+                                                  _ptr(counters), ctypes.c_void_p(work.data_ptr() + off), b.value,
+                                                  ctypes.byref(opts), _stream(stream)))
+        return k, bank, tally, counters
 
     def tally_read(self, tally, counters=None, stream=None) -> np.ndarray:
         out = np.zeros(self.n_inst, np.float64)
