@@ -44,7 +44,7 @@ EVENT_SLOTS = 512
 # capture of the same kernel on the same geometry with 3e6 particles
 # (41.24 GB over 82,931,315 segments); scaled to a full launch by its
 # segments.  None whenever the kernel has changed since that capture.
-TRAFFIC_BYTES_PER_SEGMENT = 41.235e9 / 82931315
+TRAFFIC_BYTES_PER_SEGMENT = (26.948636e9 + 14.348119e9) / 82931315
 
 
 def _env_int(k, d):
@@ -349,6 +349,7 @@ def main() -> None:
     hexcore = run_config3(N, I, dev, stream, barrier, k2)
     meshline = run_mesh_tally(N, I, dev, stream, barrier, k2, rate(main_run), rate(rect_ev))
     trans = run_config5(N, I, dev, stream, barrier, k2)
+    power = run_power(N, I, dev, stream, barrier, 2, n * args.steps / (main_run["ms"] / 1e3))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -389,6 +390,7 @@ def main() -> None:
             "config3": hexcore,
             "mesh_tally": meshline,
             "transmission": trans,
+            "power_iteration": power,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -590,6 +592,41 @@ def run_mesh_tally(N, I, dev, stream, barrier, steps, csg_plain, rect_plain):
         out[f"{name}_degradation"] = 1.0 - r / plain
         del work
     return out
+
+
+def run_power(N, I, dev, stream, barrier, steps, plain_hist_per_s):
+    """Power iteration (Alg. 1) on the main workload with a fissile fuel
+    (nu = 2.4 in material 0): 2e6 histories per cycle, 2 inactive and 6
+    active cycles per step, BVH-CSG tracker, event kernel, FP64.  Reported
+    as histories per second over all cycles, against the main line's
+    particles per second (source_init + run_histories, no fission bank)."""
+    import numpy as np
+    import torch
+    desc = I.with_nu(I.config2(), [2.4, 0.0, 0.0, 0.0])
+    g = N.Geometry(I.to_json(desc), device=dev)
+    n, inactive, cycles = 2_000_000, 2, 8
+    opts = N.default_opts(tracker=N.TRACKER_CSG, mode=N.MODE_EVENT, seed=SEED, p_absorb=P_ABSORB,
+                          queue_depth=EVENT_SLOTS)
+    tally = torch.zeros(g.n_inst, dtype=torch.int64, device=dev)
+    cnt = torch.zeros(N.NCOUNTERS, dtype=torch.int64, device=dev)
+    k, bank, _, _ = g.power_iteration(n, inactive, cycles, tally=tally, counters=cnt, opts=opts, stream=stream)
+    barrier()
+    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        k, bank, _, _ = g.power_iteration(n, inactive, cycles, tally=tally, counters=cnt, opts=opts, stream=stream)
+    e.record(stream)
+    barrier()
+    ms = a.elapsed_time(e)
+    kk = k.cpu().numpy()
+    st = int(cnt.cpu().numpy().view(np.uint64)[N.K["status"]])
+    hps = steps * n * cycles / (ms / 1e3)
+    return {"workload": "main workload, fuel nu = 2.4, 2e6 histories per cycle, 2 inactive + 6 active cycles "
+                        "per step, BVH-CSG, event kernel, FP64 (includes the work buffer allocation per call)",
+            "histories_per_s": hps, "ms_per_cycle": ms / (steps * cycles),
+            "over_plain_run": hps / plain_hist_per_s,
+            "k_per_cycle": [float(x) for x in kk], "k_active_mean": float(kk[inactive:].mean()),
+            "bank_per_cycle": [int(x) for x in bank.cpu().numpy()], "status": st}
 
 
 def run_config5(N, I, dev, stream, barrier, steps):
