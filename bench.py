@@ -287,6 +287,8 @@ def main() -> None:
     rect_ev = timed(N.TRACKER_RECT, N.MODE_EVENT, k2, 3)
     csg_hist = timed(N.TRACKER_CSG, N.MODE_HISTORY, k2, 3)
     rect_hist = timed(N.TRACKER_RECT, N.MODE_HISTORY, k2, 3)
+    # the paper's DP method: the array tracker's work behind virtual calls per level
+    dp_hist = timed(N.TRACKER_DP, N.MODE_HISTORY, k2, 3)
     csg_ev32 = timed(N.TRACKER_CSG, N.MODE_EVENT, k2, 3, prec=N.FP32_LOCAL)
     # the same workload with the bounding interval hierarchy (Sec. 4.3) as the CSG search
     g_bvh = g
@@ -378,6 +380,8 @@ def main() -> None:
                 "csg_fp64_history": rate(csg_hist),
                 "rect_fp64_history": rate(rect_hist),
                 "csg_over_rect_history": rate(csg_hist) / rate(rect_hist),
+                "dp_fp64_history": rate(dp_hist),
+                "dp_over_rect_history": rate(dp_hist) / rate(rect_hist),
                 "csg_fp32local_event": rate(csg_ev32),
                 "csg_fp64_event_bih": rate(csg_ev_bih),
                 "bih_over_bvh_event": rate(csg_ev_bih) / rate(main_run),
@@ -488,7 +492,10 @@ def run_config1_sweep(N, I, dev, stream, barrier):
         row = {"particles": n}
         modes = [("event", N.MODE_EVENT)] + ([("history", N.MODE_HISTORY)] if n <= 1_000_000 else [])
         for mname, mode in modes:
-            for tname, tr in (("rect", N.TRACKER_RECT), ("csg", N.TRACKER_CSG)):
+            trackers = (("rect", N.TRACKER_RECT), ("csg", N.TRACKER_CSG))
+            if mode == N.MODE_HISTORY:
+                trackers += (("dp", N.TRACKER_DP),)
+            for tname, tr in trackers:
                 opts = N.default_opts(tracker=tr, mode=mode, seed=SEED, p_absorb=0.3, queue_depth=EVENT_SLOTS)
                 wb = g.work_bytes(n, opts)
                 work = torch.empty(wb + 256, dtype=torch.uint8, device=dev) if wb else None
@@ -506,6 +513,8 @@ def run_config1_sweep(N, I, dev, stream, barrier):
                 row[f"{tname}_{mname}"] = seg / (a.elapsed_time(e) / 1e3)
                 del work
             row[f"csg_over_rect_{mname}"] = row[f"csg_{mname}"] / row[f"rect_{mname}"]
+            if mode == N.MODE_HISTORY:
+                row["dp_over_rect_history"] = row["dp_history"] / row["rect_history"]
         rows.append(row)
         del parts
     return {"workload": "17x17 pins (pitch 1.26, radii 0.41/0.475) in a reflecting box 21.42 x 21.42 x 100, "

@@ -60,8 +60,14 @@ typedef enum {
  * gives no hex array tracker; results are those of the pseudo-array scan),
  * CSG universes by search.  CSG: every array as its pseudo-array, searched
  * through a BVH of cell boxes (Sec. 4.3).  AUTO: RECT, or CSG for a geometry
- * with hex arrays (measured as fast or faster there). */
-enum { TRK_TRACKER_RECT = 0, TRK_TRACKER_CSG = 1, TRK_TRACKER_AUTO = 2 };
+ * with hex arrays (measured as fast or faster there).  DP: the paper's
+ * dynamic-polymorphism method (Sec. 3.1), kept as a comparison: a rect array
+ * tracker object and a CSG tracker object (hex arrays included) behind one
+ * base class, every per-level find, distance and crossing a virtual call;
+ * results equal RECT's.  run_histories only, history mode, FP64, no mesh
+ * tally or path cutoff (TRK_E_UNSUPPORTED otherwise); every other entry
+ * point rejects it with TRK_E_INVALID. */
+enum { TRK_TRACKER_RECT = 0, TRK_TRACKER_CSG = 1, TRK_TRACKER_AUTO = 2, TRK_TRACKER_DP = 3 };
 enum { TRK_MODE_HISTORY = 0, TRK_MODE_EVENT = 1 };
 enum { TRK_FP64 = 0, TRK_FP32_LOCAL = 1 };
 

@@ -446,6 +446,8 @@ trk_status batch_create(const trk_geom_t* geoms, int n_geom, const void* const* 
                         uint64_t* const* dev_records, int tracker, trk_batch_t* out) {
     if (!geoms || n_geom <= 0 || !dev_particles || !counts || !dev_tallies || !dev_counters || !out)
         return trk_status(set_error(TRK_E_INVALID, "batch_create: null argument or n_geom <= 0"));
+    if (tracker != TRK_TRACKER_RECT && tracker != TRK_TRACKER_CSG && tracker != TRK_TRACKER_AUTO)
+        return trk_status(set_error(TRK_E_INVALID, "batch_create: unknown tracker %d", tracker));
     trk_batch* b = new trk_batch;
     std::vector<int> idx(static_cast<size_t>(n_geom), 0);
     for (int k = 0; k < n_geom; ++k) {

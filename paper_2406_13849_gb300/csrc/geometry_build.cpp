@@ -1238,6 +1238,7 @@ int build_host(const char* json, size_t len, Built& B) {
     if (m_grid.empty()) { m_grid.push_back(0.0); m_key.push_back(0); }
     o[35] = L.put(m_grid.size() * 8);
     o[36] = L.put(m_key.size() * 8);
+    o[40] = L.put(TRK_DP_BYTES);        // DP tracker objects, built on the device
     B.image.assign(L.total, 0);
     copy_into(B.image, o[0], s_info);
     copy_into(B.image, o[1], s_coef);
@@ -1323,6 +1324,8 @@ trk_status geometry_build(const char* json, size_t len, void* dev_buf, size_t* d
     cudaError_t ce = cudaMemcpyAsync(dev_buf, B.image.data(), need, cudaMemcpyHostToDevice,
                                      static_cast<cudaStream_t>(stream));
     if (ce != cudaSuccess) return trk_status(set_error(TRK_E_CUDA, "geometry_build: cudaMemcpyAsync: %s", cudaGetErrorString(ce)));
+    ce = cudaError_t(dp_install(static_cast<unsigned char*>(dev_buf) + B.offs[40], stream));
+    if (ce != cudaSuccess) return trk_status(set_error(TRK_E_CUDA, "geometry_build: DP trackers: %s", cudaGetErrorString(ce)));
     // the staging image is pageable host memory: wait for the copy before it goes away
     ce = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
     if (ce != cudaSuccess) return trk_status(set_error(TRK_E_CUDA, "geometry_build: %s", cudaGetErrorString(ce)));
@@ -1338,6 +1341,7 @@ trk_status geometry_build(const char* json, size_t len, void* dev_buf, size_t* d
     d.c_fill = reinterpret_cast<const int*>(base + o[4]);
     d.c_tr = reinterpret_cast<const double*>(base + o[5]);
     d.c_off = reinterpret_cast<const int*>(base + o[6]);
+    d.dp = base + o[40];
     d.u_info = reinterpret_cast<const int4*>(base + o[7]);
     d.l_dim = reinterpret_cast<const int4*>(base + o[8]);
     d.l_off = reinterpret_cast<const int4*>(base + o[9]);

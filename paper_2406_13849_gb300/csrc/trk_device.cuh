@@ -598,10 +598,48 @@ __device__ __forceinline__ int hex_find(const DevGeom& g, int h, int u, const Pt
     return csg_search(g, u, p, -1, -1, 0);
 }
 
+// Tracker kinds of the tracking templates: the array tracker (rect arrays by
+// index, hex arrays by hex_find), the CSG tracker (every universe through
+// its cells), and the dynamic-polymorphism tracker (rect arrays and CSG
+// universes as two tracker objects reached through virtual calls per level,
+// the paper's DP method, Sec. 3.1; the per-level work is the array
+// tracker's, hex arrays are CSG universes).  A `bool` CSG argument converts
+// to the first two.
+enum { TK_RECT = 0, TK_CSG = 1, TK_DP = 2 };
+
+// The per-level steps, shared by the templates below and the DP tracker
+// objects.  find_cell in one rect array level (Alg. 5): false if the point is
+// outside a root array.
+__device__ __forceinline__ bool find_level_rect(const DevGeom& g, Lv& L, int lat, const Pt& p, bool root, int& dau) {
+    const int4 dm = __ldg(g.l_dim + lat), of = __ldg(g.l_off + lat);
+    const int i = rect_index(g.l_gkey + of.x, dm.x, p.kx, root);
+    const int j = rect_index(g.l_gkey + of.y, dm.y, p.ky, root);
+    const int k = rect_index(g.l_gkey + of.z, dm.z, p.kz, root);
+    if (i < 0 || j < 0 || k < 0) return false;
+    dau = enter_element(g, L, lat, i, j, k);
+    return true;
+}
+
+// find_cell in one CSG level (Alg. 3), or a hex array by hex_find when
+// `hex` (-2 - lattice index) is given: false if no cell holds the point.
+__device__ __forceinline__ bool find_level_csg(const DevGeom& g, Lv& L, int hex, const Pt& p, int& dau) {
+    const int c = hex <= -2 ? hex_find(g, -2 - hex, L.u, p) : csg_search(g, L.u, p, -1, -1, 0);
+    if (c < 0) return false;
+    dau = enter_cell(g, L, c);
+    return true;
+}
+
+struct Hit;
+struct Tracker;
+__device__ __forceinline__ const Tracker* get_tracker(const DevGeom& g, const int4& ui);
+__device__ __forceinline__ bool dp_find(const Tracker* t, const DevGeom& g, Lv& L, int lat, const Pt& p, bool root,
+                                        int& dau);
+
 // Alg. 7 from level `start` downward (rect view for rect arrays unless CSG).
 // Returns 0 on success, -1 if no cell holds the point.
-template <bool CSG>
+template <int TK>
 __device__ TRK_FIND_INLINE int find_from(const DevGeom& g, St& s, int start) {
+    constexpr bool CSG = TK == TK_CSG;
     if (start < 0 || start >= MAXL) return -1;
     double x, y, z;
     local_at(s, start, x, y, z);
@@ -611,19 +649,11 @@ __device__ TRK_FIND_INLINE int find_from(const DevGeom& g, St& s, int start) {
         const int4 ui = __ldg(g.u_info + L.u);
         const Pt p = make_pt(x, y, z);
         int dau;
-        if (!CSG && ui.w >= 0) {
-            const int4 dm = __ldg(g.l_dim + ui.w), of = __ldg(g.l_off + ui.w);
-            const bool root = (l == 0);
-            const int i = rect_index(g.l_gkey + of.x, dm.x, p.kx, root);
-            const int j = rect_index(g.l_gkey + of.y, dm.y, p.ky, root);
-            const int k = rect_index(g.l_gkey + of.z, dm.z, p.kz, root);
-            if (i < 0 || j < 0 || k < 0) return -1;
-            dau = enter_element(g, L, ui.w, i, j, k);
-        } else {
-            const int c = (!CSG && ui.w <= -2) ? hex_find(g, -2 - ui.w, L.u, p) : csg_search(g, L.u, p, -1, -1, 0);
-            if (c < 0) return -1;
-            dau = enter_cell(g, L, c);
-        }
+        bool ok;
+        if constexpr (TK == TK_DP) ok = dp_find(get_tracker(g, ui), g, L, ui.w, p, l == 0, dau);
+        else if (!CSG && ui.w >= 0) ok = find_level_rect(g, L, ui.w, p, l == 0, dau);
+        else ok = find_level_csg(g, L, CSG ? -1 : ui.w, p, dau);
+        if (!ok) return -1;
         lv_set(s, l, L);
         if (dau < 0) {
             s.nlev = l + 1;
@@ -642,6 +672,134 @@ struct Hit {
     int level, surf, side, dim, dsign, entry;
 };
 
+// distance_to_surface in one rect array level (Table 1): per dimension the
+// face the direction leaves through, outer faces only at the root; candidate
+// c with order key ck (kept when smaller).
+__device__ __forceinline__ void dist_level_rect(const DevGeom& g, const St& s, int l, const Lv& L, int lat, double x,
+                                                double y, double z, Hit& c, long long& ck) {
+    const int4 dm = __ldg(g.l_dim + lat), of = __ldg(g.l_off + lat);
+    const int n3[3] = {dm.x, dm.y, dm.z};
+    const int o3[3] = {of.x, of.y, of.z};
+    const int i3[3] = {L.i, L.j, L.k};
+    const double p3[3] = {x, y, z};
+    const double d3[3] = {s.d.u, s.d.v, s.d.w};
+    const double v3[3] = {s.d.iu, s.d.iv, s.d.iw};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        double t = DINF;
+        int sg = 0;
+        if (d_gt0(d3[d])) {
+            if (i3[d] < n3[d] - 1 || l == 0) { t = (__ldg(g.l_grid + o3[d] + i3[d] + 1) - p3[d]) * v3[d]; sg = 1; }
+        } else if (d_lt0(d3[d])) {
+            if (i3[d] > 0 || l == 0) { t = (__ldg(g.l_grid + o3[d] + i3[d]) - p3[d]) * v3[d]; sg = -1; }
+        }
+        if (sg != 0) {
+            if (d_lt0(t)) t = 0.0;
+            const long long tk = okey(t);
+            if (tk < ck) {
+                ck = tk; c.d = t; c.level = l; c.surf = -1 - (2 * d + (sg > 0)); c.dim = d; c.dsign = sg;
+                c.side = 0; c.entry = -1;
+            }
+        }
+    }
+}
+
+// distance_to_surface in one CSG level (Table 1): the cell's surfaces (slab
+// and pair views first where the cell has them); hk, hd: the running best
+// of the levels below, for the cylinder screen.
+__device__ __forceinline__ void dist_level_csg(const DevGeom& g, const St& s, int l, const Lv& L, double x, double y,
+                                               double z, long long hk, double hd, Hit& c, long long& ck) {
+    const long long kinf = okey(DINF);
+    const int2 rg = __ldg(g.c_range + L.cell);
+    int first = rg.x, cnt = rg.y & CS_COUNT_MASK;
+    const int* ents = g.cs;
+    bool by_index = false;
+    if (rg.y & CS_SLAB_FLAG) {
+        // Slab view: per dimension the one axis face the direction
+        // leaves through, as in the rect tracker; then the cell's other
+        // surfaces.  Ties go to the lower entry index, which is the
+        // cell-order scan's result.
+        const int4 s0 = __ldg(g.c_slab0 + L.cell), s1 = __ldg(g.c_slab1 + L.cell);
+        const int lo3[3] = {s0.x, s0.z, s1.x};
+        const int hi3[3] = {s0.y, s0.w, s1.y};
+        const double p3[3] = {x, y, z};
+        const double d3[3] = {s.d.u, s.d.v, s.d.w};
+        const double v3[3] = {s.d.iu, s.d.iv, s.d.iw};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const int e = d_gt0(d3[d]) ? hi3[d] : (d_lt0(d3[d]) ? lo3[d] : -1);
+            if (e < 0) continue;
+            const int sid = cs_surface(__ldg(g.cs + e));
+            if (s.on_lev == l && s.on_surf == sid) continue;
+            double t = (__ldg(g.s_coef + 4 * sid) - p3[d]) * v3[d];
+            if (d_lt0(t)) t = 0.0;
+            const long long tk = okey(t);
+            if (tk < ck || (tk == ck && c.level >= 0 && e < c.entry)) {
+                ck = tk; c.d = t; c.level = l; c.surf = sid; c.side = d_gt0(d3[d]) ? -1 : 1;
+                c.dim = -1; c.dsign = 0; c.entry = e;
+            }
+        }
+        if (rg.y & CS_PAIR_FLAG) {
+            // plane pairs: per pair the one face the direction leaves
+            // through (n.u < 0: the "+" entry), the S_P distance of
+            // surface_distance
+            const int4 p0 = __ldg(g.c_pair + 2 * L.cell), p1 = __ldg(g.c_pair + 2 * L.cell + 1);
+            const int lo3p[3] = {p0.x, p0.z, p1.x};
+            const int hi3p[3] = {p0.y, p0.w, p1.y};
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                const int ea = lo3p[f] >= 0 ? lo3p[f] : hi3p[f];
+                if (ea < 0) continue;
+                double c0, c1, c2, c3;
+                load_coef(g, cs_surface(__ldg(g.cs + ea)), c0, c1, c2, c3);
+                const double den = (c0 * s.d.u + c1 * s.d.v) + c2 * s.d.w;
+                const int e = d_lt0(den) ? lo3p[f] : (d_gt0(den) ? hi3p[f] : -1);
+                if (e < 0) continue;
+                const int sid = cs_surface(__ldg(g.cs + e));
+                if (s.on_lev == l && s.on_surf == sid) continue;
+                const double d3c = __ldg(g.s_coef + 4 * sid + 3);
+                double t = (d3c - ((c0 * x + c1 * y) + c2 * z)) / den;
+                if (d_lt0(t)) t = 0.0;
+                const long long tk = okey(t);
+                if (tk < ck || (tk == ck && c.level >= 0 && e < c.entry)) {
+                    ck = tk; c.d = t; c.level = l; c.surf = sid; c.side = d_lt0(den) ? 1 : -1;
+                    c.dim = -1; c.dsign = 0; c.entry = e;
+                }
+            }
+        }
+        const int2 rr = __ldg(g.c_rest + L.cell);
+        first = rr.x; cnt = rr.y; ents = g.rest_e; by_index = true;
+    }
+    // remaining entries (all of them for a cell without a view)
+    for (int k = 0; k < cnt; ++k) {
+        const int ei = by_index ? __ldg(ents + first + k) : first + k;
+        const int e = __ldg(g.cs + ei);
+        const int sid = cs_surface(e), side = cs_side(e), type = cs_type(e);
+        const bool on = (s.on_lev == l && s.on_surf == sid);
+        if (type == S_CZ && side < 0 && !on && (hk != kinf || ck != kinf)) {
+            const double bd = ck < hk ? c.d : hd;
+            double c0, c1, c2, c3;
+            load_coef(g, sid, c0, c1, c2, c3);
+            const double qx = x - c0, qy = y - c1;
+            const double f = (qx * qx + qy * qy) - c3;
+            if (d_lt0(f)) {
+                const double tb = (c2 + c2) * bd;
+                const double rhs = tb + (tb + c3) * 0x1p-40;
+                if (okey(-f) > okey(rhs)) continue;
+            }
+        }
+        const double t = surface_distance(g, sid, type, side, on, x, y, z, s.d);
+        const long long tk = okey(t);
+        if (tk < ck || (tk == ck && c.level >= 0 && ei < c.entry)) {
+            ck = tk; c.d = t; c.level = l; c.surf = sid; c.side = side; c.dim = -1; c.dsign = 0; c.entry = ei;
+        }
+    }
+}
+
+__device__ __forceinline__ void dp_distance(const Tracker* t, const DevGeom& g, const St& s, int l, const Lv& L, int lat,
+                                            double x, double y, double z, long long hk, double hd, Hit& c,
+                                            long long& ck);
+
 // distance_to_surface over the levels (Table 1, Alg. 2): the smallest
 // distance wins; a tie goes to the top-most level, and within a level to the
 // first candidate in the level's order (rect levels: x, y, z faces in the
@@ -656,8 +814,9 @@ struct Hit {
 // a relative margin of 2^-40 over the rounding errors of c = rho^2 - r^2 and
 // of the distance formula (both a few ulp: inside a cylinder disc >= b^2), so
 // a skipped candidate is never the winner and the result is unchanged.
-template <bool CSG>
+template <int TK>
 __device__ __forceinline__ Hit distance_to_boundary(const DevGeom& g, const St& s) {
+    constexpr bool CSG = TK == TK_CSG;
     Hit h;
     h.d = DINF; h.level = -1; h.surf = -1; h.side = 0; h.dim = -1; h.dsign = 0; h.entry = -1;
     const long long kinf = okey(DINF);
@@ -686,118 +845,9 @@ __device__ __forceinline__ Hit distance_to_boundary(const DevGeom& g, const St& 
         c.d = DINF; c.level = -1; c.surf = -1; c.side = 0; c.dim = -1; c.dsign = 0; c.entry = -1;
         long long ck = kinf;
         const int4 ui = __ldg(g.u_info + L.u);
-        if (!CSG && ui.w >= 0) {
-            const int4 dm = __ldg(g.l_dim + ui.w), of = __ldg(g.l_off + ui.w);
-            const int n3[3] = {dm.x, dm.y, dm.z};
-            const int o3[3] = {of.x, of.y, of.z};
-            const int i3[3] = {L.i, L.j, L.k};
-            const double p3[3] = {x, y, z};
-            const double d3[3] = {s.d.u, s.d.v, s.d.w};
-            const double v3[3] = {s.d.iu, s.d.iv, s.d.iw};
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                double t = DINF;
-                int sg = 0;
-                if (d_gt0(d3[d])) {
-                    if (i3[d] < n3[d] - 1 || l == 0) { t = (__ldg(g.l_grid + o3[d] + i3[d] + 1) - p3[d]) * v3[d]; sg = 1; }
-                } else if (d_lt0(d3[d])) {
-                    if (i3[d] > 0 || l == 0) { t = (__ldg(g.l_grid + o3[d] + i3[d]) - p3[d]) * v3[d]; sg = -1; }
-                }
-                if (sg != 0) {
-                    if (d_lt0(t)) t = 0.0;
-                    const long long tk = okey(t);
-                    if (tk < ck) {
-                        ck = tk; c.d = t; c.level = l; c.surf = -1 - (2 * d + (sg > 0)); c.dim = d; c.dsign = sg;
-                        c.side = 0; c.entry = -1;
-                    }
-                }
-            }
-        } else {
-            const int2 rg = __ldg(g.c_range + L.cell);
-            int first = rg.x, cnt = rg.y & CS_COUNT_MASK;
-            const int* ents = g.cs;
-            bool by_index = false;
-            if (rg.y & CS_SLAB_FLAG) {
-                // Slab view: per dimension the one axis face the direction
-                // leaves through, as in the rect tracker; then the cell's other
-                // surfaces.  Ties go to the lower entry index, which is the
-                // cell-order scan's result.
-                const int4 s0 = __ldg(g.c_slab0 + L.cell), s1 = __ldg(g.c_slab1 + L.cell);
-                const int lo3[3] = {s0.x, s0.z, s1.x};
-                const int hi3[3] = {s0.y, s0.w, s1.y};
-                const double p3[3] = {x, y, z};
-                const double d3[3] = {s.d.u, s.d.v, s.d.w};
-                const double v3[3] = {s.d.iu, s.d.iv, s.d.iw};
-#pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    const int e = d_gt0(d3[d]) ? hi3[d] : (d_lt0(d3[d]) ? lo3[d] : -1);
-                    if (e < 0) continue;
-                    const int sid = cs_surface(__ldg(g.cs + e));
-                    if (s.on_lev == l && s.on_surf == sid) continue;
-                    double t = (__ldg(g.s_coef + 4 * sid) - p3[d]) * v3[d];
-                    if (d_lt0(t)) t = 0.0;
-                    const long long tk = okey(t);
-                    if (tk < ck || (tk == ck && c.level >= 0 && e < c.entry)) {
-                        ck = tk; c.d = t; c.level = l; c.surf = sid; c.side = d_gt0(d3[d]) ? -1 : 1;
-                        c.dim = -1; c.dsign = 0; c.entry = e;
-                    }
-                }
-                if (rg.y & CS_PAIR_FLAG) {
-                    // plane pairs: per pair the one face the direction leaves
-                    // through (n.u < 0: the "+" entry), the S_P distance of
-                    // surface_distance
-                    const int4 p0 = __ldg(g.c_pair + 2 * L.cell), p1 = __ldg(g.c_pair + 2 * L.cell + 1);
-                    const int lo3p[3] = {p0.x, p0.z, p1.x};
-                    const int hi3p[3] = {p0.y, p0.w, p1.y};
-#pragma unroll
-                    for (int f = 0; f < 3; ++f) {
-                        const int ea = lo3p[f] >= 0 ? lo3p[f] : hi3p[f];
-                        if (ea < 0) continue;
-                        double c0, c1, c2, c3;
-                        load_coef(g, cs_surface(__ldg(g.cs + ea)), c0, c1, c2, c3);
-                        const double den = (c0 * s.d.u + c1 * s.d.v) + c2 * s.d.w;
-                        const int e = d_lt0(den) ? lo3p[f] : (d_gt0(den) ? hi3p[f] : -1);
-                        if (e < 0) continue;
-                        const int sid = cs_surface(__ldg(g.cs + e));
-                        if (s.on_lev == l && s.on_surf == sid) continue;
-                        const double d3c = __ldg(g.s_coef + 4 * sid + 3);
-                        double t = (d3c - ((c0 * x + c1 * y) + c2 * z)) / den;
-                        if (d_lt0(t)) t = 0.0;
-                        const long long tk = okey(t);
-                        if (tk < ck || (tk == ck && c.level >= 0 && e < c.entry)) {
-                            ck = tk; c.d = t; c.level = l; c.surf = sid; c.side = d_lt0(den) ? 1 : -1;
-                            c.dim = -1; c.dsign = 0; c.entry = e;
-                        }
-                    }
-                }
-                const int2 rr = __ldg(g.c_rest + L.cell);
-                first = rr.x; cnt = rr.y; ents = g.rest_e; by_index = true;
-            }
-            // remaining entries (all of them for a cell without a view)
-            for (int k = 0; k < cnt; ++k) {
-                const int ei = by_index ? __ldg(ents + first + k) : first + k;
-                const int e = __ldg(g.cs + ei);
-                const int sid = cs_surface(e), side = cs_side(e), type = cs_type(e);
-                const bool on = (s.on_lev == l && s.on_surf == sid);
-                if (type == S_CZ && side < 0 && !on && (hk != kinf || ck != kinf)) {
-                    const double bd = ck < hk ? c.d : h.d;
-                    double c0, c1, c2, c3;
-                    load_coef(g, sid, c0, c1, c2, c3);
-                    const double qx = x - c0, qy = y - c1;
-                    const double f = (qx * qx + qy * qy) - c3;
-                    if (d_lt0(f)) {
-                        const double tb = (c2 + c2) * bd;
-                        const double rhs = tb + (tb + c3) * 0x1p-40;
-                        if (okey(-f) > okey(rhs)) continue;
-                    }
-                }
-                const double t = surface_distance(g, sid, type, side, on, x, y, z, s.d);
-                const long long tk = okey(t);
-                if (tk < ck || (tk == ck && c.level >= 0 && ei < c.entry)) {
-                    ck = tk; c.d = t; c.level = l; c.surf = sid; c.side = side; c.dim = -1; c.dsign = 0; c.entry = ei;
-                }
-            }
-        }
+        if constexpr (TK == TK_DP) dp_distance(get_tracker(g, ui), g, s, l, L, ui.w, x, y, z, hk, h.d, c, ck);
+        else if (!CSG && ui.w >= 0) dist_level_rect(g, s, l, L, ui.w, x, y, z, c, ck);
+        else dist_level_csg(g, s, l, L, x, y, z, hk, h.d, c, ck);
         if (c.level >= 0 && ck <= hk) { hk = ck; h = c; }
     }
     return h;
@@ -989,7 +1039,7 @@ __device__ __forceinline__ bool close_call(float a, float b) {
     return fabsf(a - b) <= CLOSE_REL * fmaxf(fmaxf(a, b) < FINF ? fmaxf(a, b) : 1.0f, 1.0f);
 }
 
-enum { CR_OK = 0, CR_REFLECT = 1, CR_ESCAPE = 2, CR_LOST = 3, CR_FIND = 4 };
+enum { CR_OK = 0, CR_REFLECT = 1, CR_ESCAPE = 2, CR_LOST = 3, CR_FIND = 4, CR_ENTER = 5 };
 
 __device__ __forceinline__ void reflect_plane(const DevGeom& g, St& s, int sid, int dim) {
     int type = dim;
@@ -1027,11 +1077,53 @@ __device__ __forceinline__ int csg_cross_search(const DevGeom& g, int u, int cel
     return csg_search(g, u, p, cell, xs, xsn);
 }
 
+// cross_surface in one rect array level (Alg. 6): the neighbouring element,
+// or at the root's outer face its boundary condition.  Returns CR_ENTER
+// with the element's daughter in dau, or a final result.
+__device__ __forceinline__ int cross_level_rect(const DevGeom& g, St& s, int l, Lv& L, int lat, const Hit& h, int& dau) {
+    int ijk[3] = {L.i, L.j, L.k};
+    const int4 dm = __ldg(g.l_dim + lat);
+    const int n3[3] = {dm.x, dm.y, dm.z};
+    int ni = 0, nn = 1;
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+        if (d == h.dim) { ijk[d] += h.dsign; ni = ijk[d]; nn = n3[d]; }
+    if (ni < 0 || ni >= nn) {
+        if (l != 0) return CR_LOST;
+        const int bc = (dm.w >> (2 * (2 * h.dim + (h.dsign > 0)))) & 3;
+        if (bc == BC_REFLECT) { reflect_plane(g, s, -1, h.dim); return CR_REFLECT; }
+        return CR_ESCAPE;
+    }
+    dau = enter_element(g, L, lat, ijk[0], ijk[1], ijk[2]);
+    return CR_ENTER;
+}
+
+// cross_surface in one CSG level (Alg. 4): the cell on the other side of the
+// crossed surface, or at the root its boundary condition.
+__device__ __forceinline__ int cross_level_csg(const DevGeom& g, St& s, int l, Lv& L, const Hit& h, int& dau) {
+    double x, y, z;
+    local_at(s, l, x, y, z);
+    const Pt p = make_pt(x, y, z);
+    const int c = csg_cross_search(g, L.u, L.cell, p, h.surf, -h.side, h.entry);
+    if (c < 0) {
+        if (l != 0) return CR_LOST;
+        const int bc = (__ldg(g.s_info + h.surf) >> 4) & 3;
+        if (bc == BC_REFLECT) { reflect_plane(g, s, h.surf, -1); return CR_REFLECT; }
+        return CR_ESCAPE;
+    }
+    dau = enter_cell(g, L, c);
+    return CR_ENTER;
+}
+
+__device__ __forceinline__ int dp_cross(const Tracker* t, const DevGeom& g, St& s, int l, Lv& L, int lat, const Hit& h,
+                                        int& dau);
+
 // Alg. 8 at the hit's level (Alg. 4 for CSG, Alg. 6 for rect).  Returns
 // CR_FIND when the levels below the crossing must be found again (the
 // caller runs find_from(find_level)), else a final result.
-template <bool CSG>
+template <int TK>
 __device__ __forceinline__ int cross_surface(const DevGeom& g, St& s, const Hit& h, int& find_level) {
+    constexpr bool CSG = TK == TK_CSG;
     find_level = -1;
     const int l = h.level;
     if (l < 0 || l >= MAXL) return CR_LOST;
@@ -1039,35 +1131,11 @@ __device__ __forceinline__ int cross_surface(const DevGeom& g, St& s, const Hit&
     const int4 ui = __ldg(g.u_info + L.u);
     s.on_lev = l;
     s.on_surf = h.surf;
-    int dau;
-    if (!CSG && ui.w >= 0) {
-        int ijk[3] = {L.i, L.j, L.k};
-        const int4 dm = __ldg(g.l_dim + ui.w);
-        const int n3[3] = {dm.x, dm.y, dm.z};
-        int ni = 0, nn = 1;
-#pragma unroll
-        for (int d = 0; d < 3; ++d)
-            if (d == h.dim) { ijk[d] += h.dsign; ni = ijk[d]; nn = n3[d]; }
-        if (ni < 0 || ni >= nn) {
-            if (l != 0) return CR_LOST;
-            const int bc = (dm.w >> (2 * (2 * h.dim + (h.dsign > 0)))) & 3;
-            if (bc == BC_REFLECT) { reflect_plane(g, s, -1, h.dim); return CR_REFLECT; }
-            return CR_ESCAPE;
-        }
-        dau = enter_element(g, L, ui.w, ijk[0], ijk[1], ijk[2]);
-    } else {
-        double x, y, z;
-        local_at(s, l, x, y, z);
-        const Pt p = make_pt(x, y, z);
-        const int c = csg_cross_search(g, L.u, L.cell, p, h.surf, -h.side, h.entry);
-        if (c < 0) {
-            if (l != 0) return CR_LOST;
-            const int bc = (__ldg(g.s_info + h.surf) >> 4) & 3;
-            if (bc == BC_REFLECT) { reflect_plane(g, s, h.surf, -1); return CR_REFLECT; }
-            return CR_ESCAPE;
-        }
-        dau = enter_cell(g, L, c);
-    }
+    int dau = 0, cr;
+    if constexpr (TK == TK_DP) cr = dp_cross(get_tracker(g, ui), g, s, l, L, ui.w, h, dau);
+    else if (!CSG && ui.w >= 0) cr = cross_level_rect(g, s, l, L, ui.w, h, dau);
+    else cr = cross_level_csg(g, s, l, L, h, dau);
+    if (cr != CR_ENTER) return cr;
     lv_set(s, l, L);
     if (dau < 0) {
         s.nlev = l + 1;
@@ -1077,6 +1145,75 @@ __device__ __forceinline__ int cross_surface(const DevGeom& g, St& s, const Hit&
     if (l + 1 < MAXL) lv_set_u(s, l + 1, dau);
     find_level = l + 1;
     return CR_FIND;
+}
+
+// ---------------------------------------------------------------------------
+// Dynamic polymorphism (the paper's DP method, Sec. 3.1): a tracker base
+// class with the per-universe operations of Table 1 as virtual methods, a
+// rect array tracker and a CSG tracker deriving from it, and get_tracker
+// returning the object for a universe's type.  The objects live in the
+// geometry's device memory (built there by a kernel, since their virtual
+// table pointers must be device addresses); the tracking kernels only see
+// base pointers, so every per-level operation is an indirect call.
+// ---------------------------------------------------------------------------
+struct Tracker {
+    __device__ virtual bool find(const DevGeom&, Lv&, int, const Pt&, bool, int&) const { return false; }
+    __device__ virtual void distance(const DevGeom&, const St&, int, const Lv&, int, double, double, double, long long,
+                                     double, Hit&, long long&) const {}
+    __device__ virtual int cross(const DevGeom&, St&, int, Lv&, int, const Hit&, int&) const { return CR_LOST; }
+};
+
+struct RectTracker final : Tracker {
+    __device__ bool find(const DevGeom& g, Lv& L, int lat, const Pt& p, bool root, int& dau) const override {
+        return find_level_rect(g, L, lat, p, root, dau);
+    }
+    __device__ void distance(const DevGeom& g, const St& s, int l, const Lv& L, int lat, double x, double y, double z,
+                             long long, double, Hit& c, long long& ck) const override {
+        dist_level_rect(g, s, l, L, lat, x, y, z, c, ck);
+    }
+    __device__ int cross(const DevGeom& g, St& s, int l, Lv& L, int lat, const Hit& h, int& dau) const override {
+        return cross_level_rect(g, s, l, L, lat, h, dau);
+    }
+};
+
+struct CsgTracker final : Tracker {
+    __device__ bool find(const DevGeom& g, Lv& L, int, const Pt& p, bool, int& dau) const override {
+        return find_level_csg(g, L, -1, p, dau);
+    }
+    __device__ void distance(const DevGeom& g, const St& s, int l, const Lv& L, int, double x, double y, double z,
+                             long long hk, double hd, Hit& c, long long& ck) const override {
+        dist_level_csg(g, s, l, L, x, y, z, hk, hd, c, ck);
+    }
+    __device__ int cross(const DevGeom& g, St& s, int l, Lv& L, int, const Hit& h, int& dau) const override {
+        return cross_level_csg(g, s, l, L, h, dau);
+    }
+};
+
+// The objects in the geometry's DP region: the table of base pointers
+// (index 0 rect arrays, 1 CSG universes, hex arrays included), then the objects.
+struct DpTable {
+    const Tracker* t[2];
+    alignas(16) unsigned char rect[16];
+    alignas(16) unsigned char csg[16];
+};
+static_assert(sizeof(RectTracker) <= 16 && sizeof(CsgTracker) <= 16, "tracker objects exceed their slots");
+static_assert(sizeof(DpTable) <= TRK_DP_BYTES, "DP region too small");
+
+__device__ __forceinline__ const Tracker* get_tracker(const DevGeom& g, const int4& ui) {
+    return static_cast<const DpTable*>(g.dp)->t[ui.w >= 0 ? 0 : 1];
+}
+__device__ __forceinline__ bool dp_find(const Tracker* t, const DevGeom& g, Lv& L, int lat, const Pt& p, bool root,
+                                        int& dau) {
+    return t->find(g, L, lat, p, root, dau);
+}
+__device__ __forceinline__ void dp_distance(const Tracker* t, const DevGeom& g, const St& s, int l, const Lv& L, int lat,
+                                            double x, double y, double z, long long hk, double hd, Hit& c,
+                                            long long& ck) {
+    t->distance(g, s, l, L, lat, x, y, z, hk, hd, c, ck);
+}
+__device__ __forceinline__ int dp_cross(const Tracker* t, const DevGeom& g, St& s, int l, Lv& L, int lat, const Hit& h,
+                                        int& dau) {
+    return t->cross(g, s, l, L, lat, h, dau);
 }
 
 // ---------------------------------------------------------------------------
@@ -1220,11 +1357,11 @@ struct Ctx {
 
 enum { A_CROSS = 0, A_COLLIDE = 1, A_FLY = 2, A_DONE = 3 };
 
-template <bool CSG, int FLAGS>
+template <int TK, int FLAGS>
 __device__ __forceinline__ int step_flight(const DevGeom& g, St& s, Hit& h, Ctx& c, const RunP& rp,
                                            unsigned long long* __restrict__ tally, Counts& cnt,
                                            int* __restrict__ tr_inst, double* __restrict__ tr_len, long long i) {
-    h = distance_to_boundary<CSG>(g, s);
+    h = distance_to_boundary<TK>(g, s);
     const double sig = __ldg(g.sigma + s.mat);
     const double dc = d_gt0(sig) ? s.tau / sig : DINF;
     const bool crossing = d_lt(h.d, dc);
@@ -1352,12 +1489,13 @@ __device__ __forceinline__ int step_flight_f32(const DevGeom& g, St& s, Hit& h, 
     return A_COLLIDE;
 }
 
-template <bool CSG, bool F32, int FLAGS>
+template <int TK, bool F32, int FLAGS>
 __device__ __forceinline__ int step_fly(const DevGeom& g, St& s, Hit& h, Ctx& c, const RunP& rp,
                                         unsigned long long* __restrict__ tally, Counts& cnt,
                                         int* __restrict__ tr_inst, double* __restrict__ tr_len, long long i) {
-    if (F32) return step_flight_f32<CSG, FLAGS>(g, s, h, c, rp, tally, cnt, tr_inst, tr_len, i);
-    return step_flight<CSG, FLAGS>(g, s, h, c, rp, tally, cnt, tr_inst, tr_len, i);
+    static_assert(!(F32 && TK == TK_DP), "the DP tracker is FP64 only");
+    if constexpr (F32) return step_flight_f32<TK == TK_CSG, FLAGS>(g, s, h, c, rp, tally, cnt, tr_inst, tr_len, i);
+    else return step_flight<TK, FLAGS>(g, s, h, c, rp, tally, cnt, tr_inst, tr_len, i);
 }
 
 __device__ __forceinline__ int after_step(Ctx& c, const RunP& rp, Counts& cnt) {
@@ -1365,11 +1503,11 @@ __device__ __forceinline__ int after_step(Ctx& c, const RunP& rp, Counts& cnt) {
     return A_FLY;
 }
 
-template <bool CSG>
+template <int TK>
 __device__ TRK_CROSS_INLINE int step_cross(const DevGeom& g, St& s, const Hit& h, Ctx& c, const RunP& rp, Counts& cnt) {
     int fl;
-    int cr = cross_surface<CSG>(g, s, h, fl);
-    if (cr == CR_FIND) cr = find_from<CSG>(g, s, fl) == 0 ? CR_OK : CR_LOST;
+    int cr = cross_surface<TK>(g, s, h, fl);
+    if (cr == CR_FIND) cr = find_from<TK>(g, s, fl) == 0 ? CR_OK : CR_LOST;
     if (cr == CR_ESCAPE) { c.status = TRK_P_ESCAPED; cnt.k[TRK_K_ESCAPED]++; return A_DONE; }
     if (cr == CR_LOST) { c.status = TRK_E_LOST; cnt.k[TRK_K_LOST]++; return A_DONE; }
     if (cr == CR_REFLECT) cnt.k[TRK_K_REFLECTIONS]++;

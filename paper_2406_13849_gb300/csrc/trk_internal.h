@@ -140,6 +140,7 @@ struct DevGeom {
     // materials
     const double* sigma;
     const double* nu;         // fission yield per material (0: none), power iteration
+    const void* dp;           // DP tracker objects (TRK_TRACKER_DP), built on the device by dp_install
     double src_lo[3], src_hi[3];
     int root, n_inst, n_mat, gid, max_depth, n_univ, n_cells, n_surf;
     int rect_ok;              // the array tracker applies (always 1: hex arrays by closed-form search)
@@ -164,6 +165,13 @@ int set_error(int st, const char* fmt, ...);
 }  // namespace trk
 
 // The library-owned host object behind trk_geom_t.
+namespace trk {
+// Bytes of the geometry's DP region, and the call that builds the DP
+// tracker objects there (a kernel on `stream`; returns a cudaError_t).
+constexpr size_t TRK_DP_BYTES = 64;
+int dp_install(void* dev, void* stream);
+}  // namespace trk
+
 struct trk_geom {
     trk::DevGeom dg;
     size_t bytes = 0;

@@ -19,6 +19,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <new>
 
 #include "trk.h"
 // In the history kernel (one history per lane, every step inline) an out-of-
@@ -49,7 +50,8 @@ namespace {
 
 
 // One history (Alg. 2): flight, then cross or collide, until it ends.
-template <bool CSG, bool F32, int FLAGS>
+// TK: tracker kind (TK_RECT, TK_CSG, TK_DP).
+template <int TK, bool F32, int FLAGS>
 __device__ __forceinline__ void history(const DevGeom& g, const ParticlesView& P, long long i, const RunP& rp,
                                         unsigned long long* __restrict__ tally, Counts& cnt,
                                         unsigned long long* __restrict__ rec, int* __restrict__ tr_inst,
@@ -66,15 +68,15 @@ __device__ __forceinline__ void history(const DevGeom& g, const ParticlesView& P
     } else {
         St s;
         load_birth(g, P, i, s);
-        if (find_from<CSG>(g, s, 0) != 0) {
+        if (find_from<TK>(g, s, 0) != 0) {
             c.status = TRK_E_LOST;
             cnt.k[TRK_K_LOST]++;
         } else {
             for (;;) {
                 Hit h;
-                int a = step_fly<CSG, F32, FLAGS>(g, s, h, c, rp, tally, cnt, tr_inst, tr_len, i);
+                int a = step_fly<TK, F32, FLAGS>(g, s, h, c, rp, tally, cnt, tr_inst, tr_len, i);
                 if (a == A_DONE) break;
-                a = (a == A_CROSS) ? step_cross<CSG>(g, s, h, c, rp, cnt) : step_collide(g, s, c, rp, cnt);
+                a = (a == A_CROSS) ? step_cross<TK>(g, s, h, c, rp, cnt) : step_collide(g, s, c, rp, cnt);
                 if (a == A_DONE) break;
             }
             if ((FLAGS & F_FISS) && c.status == TRK_P_ABSORBED) {
@@ -93,7 +95,7 @@ __device__ __forceinline__ void history(const DevGeom& g, const ParticlesView& P
     }
 }
 
-template <bool CSG, bool F32, int FLAGS>
+template <int TK, bool F32, int FLAGS>
 __global__ void TRK_HIST_BOUNDS k_history(const DevGeom g, const ParticlesView P, long long n, const RunP rp,
                                                  unsigned long long* __restrict__ tally,
                                                  unsigned long long* __restrict__ counters,
@@ -104,8 +106,15 @@ __global__ void TRK_HIST_BOUNDS k_history(const DevGeom g, const ParticlesView P
     for (int k = 0; k < NCOUNT; ++k) c.k[k] = 0;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-        history<CSG, F32, FLAGS>(g, P, i, rp, tally, c, rec, tr_inst, tr_len);
+        history<TK, F32, FLAGS>(g, P, i, rp, tally, c, rec, tr_inst, tr_len);
     flush_counts(c, counters);
+}
+
+// Builds the DP tracker objects in the geometry's DP region (one thread:
+// placement new gives them this module's device virtual tables).
+__global__ void k_dp_init(DpTable* t) {
+    t->t[0] = new (t->rect) RectTracker();
+    t->t[1] = new (t->csg) CsgTracker();
 }
 
 // ---------------------------------------------------------------------------
@@ -399,8 +408,9 @@ trk_status launch_error(const char* where) {
     return TRK_OK;
 }
 
-int resolve_tracker(trk_geom_t g, int tracker, trk_status* st) {
+int resolve_tracker(trk_geom_t g, int tracker, trk_status* st, bool allow_dp = false) {
     *st = TRK_OK;
+    if (tracker == TRK_TRACKER_DP && allow_dp) return tracker;
     // AUTO: the array tracker, except for geometries with hex arrays, where
     // the BVH-CSG tracker measured as fast or faster (its BVH walk and the
     // closed-form hex search cost about the same; the CSG kernels are smaller)
@@ -416,11 +426,11 @@ int resolve_tracker(trk_geom_t g, int tracker, trk_status* st) {
     return tracker;
 }
 
-template <bool CSG, bool F32, int FLAGS>
+template <int TK, bool F32, int FLAGS>
 trk_status launch_history(trk_geom_t g, const ParticlesView& P, long long n, const RunP& rp,
                           unsigned long long* tally, unsigned long long* cnt, unsigned long long* rec, int* ti,
                           double* tl, int block, int grid, cudaStream_t s) {
-    auto k = k_history<CSG, F32, FLAGS>;
+    auto k = k_history<TK, F32, FLAGS>;
     const int gr = persistent_grid(k, block, n, grid);
     k<<<gr, block, 0, s>>>(g->dg, P, n, rp, tally, cnt, rec, ti, tl);
     return launch_error("run_histories");
@@ -435,6 +445,11 @@ constexpr bool HAVE_F32 = true;
 #endif
 
 }  // namespace
+
+int trk::dp_install(void* dev, void* stream) {
+    k_dp_init<<<1, 1, 0, static_cast<cudaStream_t>(stream)>>>(static_cast<DpTable*>(dev));
+    return int(cudaGetLastError());
+}
 
 // ---------------------------------------------------------------------------
 // C-ABI
@@ -496,12 +511,17 @@ trk_status run_histories(trk_geom_t g, const void* dev_particles, int64_t n, uin
     trk_default_opts(&o);
     if (opts) o = *opts;
     trk_status st;
-    const int tracker = resolve_tracker(g, o.tracker, &st);
+    const int tracker = resolve_tracker(g, o.tracker, &st, true);
     if (tracker < 0) return st;
     if (o.mode != TRK_MODE_HISTORY && o.mode != TRK_MODE_EVENT)
         return trk_status(set_error(TRK_E_INVALID, "run_histories: unknown mode %d", o.mode));
     if (o.precision != TRK_FP64 && o.precision != TRK_FP32_LOCAL)
         return trk_status(set_error(TRK_E_INVALID, "run_histories: unknown precision %d", o.precision));
+    const bool dp = tracker == TRK_TRACKER_DP;
+    if (dp && (o.mode != TRK_MODE_HISTORY || o.precision != TRK_FP64 || o.mesh_tally ||
+               (o.max_path > 0.0 && o.max_path < DINF)))
+        return trk_status(set_error(TRK_E_UNSUPPORTED,
+                                    "run_histories: the DP tracker runs the FP64 history kernel without mesh tally or path cutoff"));
     const bool f32 = o.precision == TRK_FP32_LOCAL;
     if (f32 && !HAVE_F32)
         return trk_status(set_error(TRK_E_UNSUPPORTED, "run_histories: FP32-local is not in the exact (--fmad=false) build"));
@@ -539,6 +559,10 @@ trk_status run_histories(trk_geom_t g, const void* dev_particles, int64_t n, uin
     const int block = o.block > 0 ? o.block : 128;
     if (block > 128 || (block & 31)) return trk_status(set_error(TRK_E_INVALID, "run_histories: block must be a multiple of 32, <= 128"));
 #define TRK_LAUNCH(CSGV, F32V, F) return launch_history<CSGV, F32V, F>(g, P, n, rp, T, C, R, nullptr, nullptr, block, o.grid, s)
+    if (dp) {
+        if (flags & F_REC) TRK_LAUNCH(TK_DP, false, F_REC);
+        TRK_LAUNCH(TK_DP, false, 0);
+    }
     if (f32) {
 #ifndef TRK_EXACT
         if (csg) {

@@ -23,7 +23,7 @@ TRK_OK = 0
 STATUS = {0: "TRK_OK", -1: "TRK_E_INVALID", -2: "TRK_E_DESC", -3: "TRK_E_CUDA", -4: "TRK_E_NOMEM",
           -5: "TRK_E_LOST", -6: "TRK_E_MAX_SEGMENTS", -7: "TRK_E_TIMEOUT", -8: "TRK_E_UNSUPPORTED",
           -9: "TRK_E_SOURCE"}
-TRACKER_RECT, TRACKER_CSG, TRACKER_AUTO = 0, 1, 2
+TRACKER_RECT, TRACKER_CSG, TRACKER_AUTO, TRACKER_DP = 0, 1, 2, 3
 MODE_HISTORY, MODE_EVENT = 0, 1
 FP64, FP32_LOCAL = 0, 1
 NCOUNTERS = 16
