@@ -61,7 +61,7 @@ typedef enum {
  * CSG universes by search.  CSG: every array as its pseudo-array, searched
  * through a BVH of cell boxes (Sec. 4.3).  AUTO: RECT, or CSG for a geometry
  * with hex arrays (measured as fast or faster there).  DP: the paper's
- * dynamic-polymorphism method (Sec. 3.1), kept as a comparison: a rect array
+ * dynamic-polymorphism method (Sec. 4.1), kept as a comparison: a rect array
  * tracker object and a CSG tracker object (hex arrays included) behind one
  * base class, every per-level find, distance and crossing a virtual call;
  * results equal RECT's.  run_histories only, history mode, FP64, no mesh
@@ -188,7 +188,7 @@ trk_status power_iteration(trk_geom_t g, int64_t n, int inactive, int cycles, do
  * y planes, z planes]}, increasing planes per axis), 0 without one.  The mesh
  * tally (trk_run_opts.mesh_tally) walks each segment across the mesh planes
  * from its start and adds each piece inside the mesh to its bin (the paper's
- * active-cycle flux tally on a superimposed mesh, Sec. 5). */
+ * active-cycle flux tally on a superimposed mesh, Sec. 6). */
 trk_status geometry_mesh_bins(trk_geom_t g, int64_t* bins);
 
 /*

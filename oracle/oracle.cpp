@@ -20,7 +20,7 @@
 //   distance_to_surface, move_within_cell, change_direction: Table 1.
 //   pseudo-array universes (Sec. 4.3): in "csg" mode every array universe
 //                      is rewritten as a CSG universe of plane-bounded cells.
-//   cell tallies       track length per leaf cell instance (Sec. 6 cell
+//   cell tallies       track length per leaf cell instance (Sec. 7 cell
 //                      tallies), summed as 64-bit fixed point.
 // Where the paper is silent the oracle takes a fixed reading; each reading is
 // marked "Reading:" below and is the same one the CUDA path follows.
@@ -203,7 +203,7 @@ struct Universe {
 };
 
 // Superimposed rectilinear mesh for the track-length tally (the paper's
-// "active cycle" flux tally, Sec. 5): increasing plane lists per axis.
+// "active cycle" flux tally, Sec. 6): increasing plane lists per axis.
 struct Mesh {
     std::vector<double> grid[3];
     bool on() const { return !grid[0].empty(); }

@@ -602,7 +602,7 @@ __device__ __forceinline__ int hex_find(const DevGeom& g, int h, int u, const Pt
 // index, hex arrays by hex_find), the CSG tracker (every universe through
 // its cells), and the dynamic-polymorphism tracker (rect arrays and CSG
 // universes as two tracker objects reached through virtual calls per level,
-// the paper's DP method, Sec. 3.1; the per-level work is the array
+// the paper's DP method, Sec. 4.1; the per-level work is the array
 // tracker's, hex arrays are CSG universes).  A `bool` CSG argument converts
 // to the first two.
 enum { TK_RECT = 0, TK_CSG = 1, TK_DP = 2 };
@@ -1148,7 +1148,7 @@ __device__ __forceinline__ int cross_surface(const DevGeom& g, St& s, const Hit&
 }
 
 // ---------------------------------------------------------------------------
-// Dynamic polymorphism (the paper's DP method, Sec. 3.1): a tracker base
+// Dynamic polymorphism (the paper's DP method, Sec. 4.1): a tracker base
 // class with the per-universe operations of Table 1 as virtual methods, a
 // rect array tracker and a CSG tracker deriving from it, and get_tracker
 // returning the object for a universe's type.  The objects live in the

@@ -8,7 +8,7 @@ launches of one (tracker, mode, precision) on the three-level nested core
 count of the caller's choosing (default 3e6: 180 MB of particle state, more
 than the 129 MB L2, so DRAM counters still mean something).
 
-  python -m paper_2406_13849_gb300.profile_case [--tracker csg|rect]
+  python -m paper_2406_13849_gb300.profile_case [--tracker csg|rect|dp]
       [--mode event|history] [--precision fp64|fp32] [--particles N] [--launches L]
 
 Prints one line with segments, kernel milliseconds and segments/s per launch
@@ -27,7 +27,8 @@ from . import native as N
 
 def main() -> None:
     ap = argparse.ArgumentParser()
-    ap.add_argument("--tracker", default="csg", choices=["csg", "rect"])
+    ap.add_argument("--tracker", default="csg", choices=["csg", "rect", "dp"])
+    ap.add_argument("--trackers", default="", help="comma-separated trackers run one after another (overrides --tracker)")
     ap.add_argument("--mode", default="event", choices=["event", "history"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--particles", type=int, default=3_000_000)
@@ -36,11 +37,17 @@ def main() -> None:
     args = ap.parse_args()
     dev = torch.device("cuda", 0)
     g = N.Geometry(I.to_json(I.config2()), device=dev)
-    opts = N.default_opts(tracker=N.TRACKER_CSG if args.tracker == "csg" else N.TRACKER_RECT,
-                          mode=N.MODE_EVENT if args.mode == "event" else N.MODE_HISTORY,
-                          precision=N.FP64 if args.precision == "fp64" else N.FP32_LOCAL,
-                          seed=1, p_absorb=0.25, queue_depth=args.queue_depth)
+    trk = {"csg": N.TRACKER_CSG, "rect": N.TRACKER_RECT, "dp": N.TRACKER_DP}
+    names = args.trackers.split(",") if args.trackers else [args.tracker]
     n = args.particles
+    for name in names:
+        opts = N.default_opts(tracker=trk[name], mode=N.MODE_EVENT if args.mode == "event" else N.MODE_HISTORY,
+                              precision=N.FP64 if args.precision == "fp64" else N.FP32_LOCAL,
+                              seed=1, p_absorb=0.25, queue_depth=args.queue_depth)
+        run_case(g, dev, n, opts, args, name)
+
+
+def run_case(g, dev, n, opts, args, name):
     parts = torch.empty(g.particle_bytes(n), dtype=torch.uint8, device=dev)
     tally = torch.zeros(g.n_inst, dtype=torch.int64, device=dev)
     cnt = torch.zeros(N.NCOUNTERS, dtype=torch.int64, device=dev)
@@ -59,7 +66,7 @@ def main() -> None:
         seg = int(cnt.cpu()[0])
         ms = a.elapsed_time(b)
         out.append({"segments": seg, "ms": ms, "segments_per_s": seg / (ms / 1e3)})
-    print(json.dumps({"tracker": args.tracker, "mode": args.mode, "precision": args.precision,
+    print(json.dumps({"tracker": name, "mode": args.mode, "precision": args.precision,
                       "particles": n, "launches": out}), flush=True)
 
 

@@ -1,4 +1,4 @@
-"""The dynamic-polymorphism tracker (the paper's DP method, Sec. 3.1): rect
+"""The dynamic-polymorphism tracker (the paper's DP method, Sec. 4.1): rect
 array and CSG tracker objects behind one base class, each per-level find,
 distance and crossing a virtual call.  Its per-level arithmetic is the array
 tracker's, so its histories equal the oracle's rect mode bit for bit in the
