@@ -1203,6 +1203,9 @@ int build_host(const char* json, size_t len, Built& B) {
     o[16] = L.put(leaf.size() * 4);
     o[17] = L.put(G.sigma.size() * 8);
     o[39] = L.put(G.nu.size() * 8);
+    std::vector<double> rsigma;
+    for (double v : G.sigma) rsigma.push_back(v > 0.0 ? 1.0 / v : 0.0);
+    o[41] = L.put(rsigma.size() * 8);
     o[18] = L.put(s_key.size() * 8);
     o[19] = L.put(cs_adj.size() * sizeof(int2));
     o[20] = L.put(l_gkey.size() * 8);
@@ -1259,6 +1262,7 @@ int build_host(const char* json, size_t len, Built& B) {
     copy_into(B.image, o[16], leaf);
     copy_into(B.image, o[17], G.sigma);
     copy_into(B.image, o[39], G.nu);
+    copy_into(B.image, o[41], rsigma);
     copy_into(B.image, o[18], s_key);
     copy_into(B.image, o[19], cs_adj);
     copy_into(B.image, o[20], l_gkey);
@@ -1353,6 +1357,7 @@ trk_status geometry_build(const char* json, size_t len, void* dev_buf, size_t* d
     d.nodes = reinterpret_cast<const BvhNode*>(base + o[15]);
     d.leaf_cells = reinterpret_cast<const int*>(base + o[16]);
     d.sigma = reinterpret_cast<const double*>(base + o[17]);
+    d.rsigma = reinterpret_cast<const double*>(base + o[41]);
     d.nu = reinterpret_cast<const double*>(base + o[39]);
     d.s_key = reinterpret_cast<const long long*>(base + o[18]);
     d.cs_adj = reinterpret_cast<const int2*>(base + o[19]);

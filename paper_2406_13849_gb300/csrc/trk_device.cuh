@@ -464,6 +464,12 @@ struct St {
     Lv lv[MAXL];
 };
 
+// Collision distance in the fast build by the reciprocal cross section
+// (build knob; the exact build always divides).
+#ifndef TRK_FAST_RSIGMA
+#define TRK_FAST_RSIGMA 1
+#endif
+
 // Inlining of the less frequent steps (build knobs, measured per kernel):
 // out of line they leave the hot flight code a smaller footprint, at the
 // price of a call.
@@ -1363,7 +1369,13 @@ __device__ __forceinline__ int step_flight(const DevGeom& g, St& s, Hit& h, Ctx&
                                            int* __restrict__ tr_inst, double* __restrict__ tr_len, long long i) {
     h = distance_to_boundary<TK>(g, s);
     const double sig = __ldg(g.sigma + s.mat);
+#if defined(TRK_EXACT) || !TRK_FAST_RSIGMA
     const double dc = d_gt0(sig) ? s.tau / sig : DINF;
+#else
+    // fast build: tau times the material's reciprocal cross section, within
+    // an ulp of the quotient, without the division's instruction sequence
+    const double dc = d_gt0(sig) ? s.tau * __ldg(g.rsigma + s.mat) : DINF;
+#endif
     const bool crossing = d_lt(h.d, dc);
     double len = crossing ? h.d : dc;
     if (!d_finite_lt_inf(len)) { c.status = TRK_E_LOST; cnt.k[TRK_K_LOST]++; return A_DONE; }

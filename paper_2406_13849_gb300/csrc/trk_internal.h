@@ -139,6 +139,7 @@ struct DevGeom {
     const int* leaf_cells;
     // materials
     const double* sigma;
+    const double* rsigma;     // 1 / sigma (0 where sigma = 0): the fast build's collision distance
     const double* nu;         // fission yield per material (0: none), power iteration
     const void* dp;           // DP tracker objects (TRK_TRACKER_DP), built on the device by dp_install
     double src_lo[3], src_hi[3];
