@@ -64,9 +64,9 @@ typedef enum {
  * dynamic-polymorphism method (Sec. 4.1), kept as a comparison: a rect array
  * tracker object and a CSG tracker object (hex arrays included) behind one
  * base class, every per-level find, distance and crossing a virtual call;
- * results equal RECT's.  run_histories only, history mode, FP64, no mesh
- * tally or path cutoff (TRK_E_UNSUPPORTED otherwise); every other entry
- * point rejects it with TRK_E_INVALID. */
+ * results equal RECT's.  run_histories (history mode, FP64, no mesh tally
+ * or path cutoff; TRK_E_UNSUPPORTED otherwise) and trk_distance_to_surface
+ * only; every other entry point rejects it with TRK_E_INVALID. */
 enum { TRK_TRACKER_RECT = 0, TRK_TRACKER_CSG = 1, TRK_TRACKER_AUTO = 2, TRK_TRACKER_DP = 3 };
 enum { TRK_MODE_HISTORY = 0, TRK_MODE_EVENT = 1 };
 enum { TRK_FP64 = 0, TRK_FP32_LOCAL = 1 };
@@ -250,6 +250,30 @@ trk_status trk_find_cell(trk_geom_t g, int tracker, int64_t n, const double* dev
 trk_status trk_trace(trk_geom_t g, const void* dev_particles, int64_t n, int32_t cap,
                      int32_t* dev_inst, double* dev_len, uint64_t* dev_tally,
                      uint64_t* dev_counters, const trk_run_opts* opts, void* stream);
+
+/*
+ * trk_distance_to_surface - diagnostic: for n points with directions, the
+ * leaf cell by find_cell from the root (Alg. 7) and distance_to_surface
+ * over its levels (Table 1), with run_histories' tie rules (smallest
+ * distance; a tie goes to the top-most level, then to the first candidate
+ * in the level's order).  The point is taken as on no surface.
+ *   tracker    TRK_TRACKER_RECT, _CSG, _AUTO or _DP
+ *   dev_xyz    double[3n], global positions (x, y, z per point)
+ *   dev_dir    double[3n], unit directions
+ *   dev_dist   out double[n]: the distance in cm (+inf: no boundary ahead;
+ *              NaN: the point is in no cell)
+ *   dev_level  out int32[n] or NULL: level of the winning surface (-1: none)
+ *   dev_inst   out int64[n] or NULL: leaf cell instance (-1: in no cell)
+ * Errors: TRK_E_INVALID (bad handle, null buffers, n < 0, unknown tracker),
+ * TRK_E_UNSUPPORTED (array tracker unavailable), TRK_E_CUDA.
+ */
+trk_status trk_distance_to_surface(trk_geom_t g, int tracker, int64_t n, const double* dev_xyz, const double* dev_dir,
+                                   double* dev_dist, int32_t* dev_level, int64_t* dev_inst, void* stream);
+
+/* trk_sync_status - synchronises `stream` and returns the first kernel-level
+ * status a launch wrote to dev_counters[TRK_K_STATUS] (TRK_OK if none), the
+ * way tally_read reports it; reads 8 bytes from the device. */
+trk_status trk_sync_status(const uint64_t* dev_counters, void* stream);
 
 /*
  * transmission_fwd - deterministic rays without collisions: per-material

@@ -87,6 +87,7 @@ def _lib(counting: bool = False):
         lib.orc_trace.argtypes = [_P, _LL, _ULL, _D, _LL, _LL, _P, _P, _P, _P]
         lib.orc_find_cell.argtypes = [_P, _LL, _P, _P]
         lib.orc_find_cell_brute.argtypes = [_P, _LL, _P, _P, _P, _P]
+        lib.orc_distance.argtypes = [_P, _LL, _P, _P, _P, _P, _P]
         lib.orc_transmission.argtypes = [_P, _LL, _P, _P, _D, _P, _P, _P, _P, _P, _I]
         lib.orc_philox4x32_10.argtypes = [_P, _P, _P]
         lib.orc_uniform2.argtypes = [_U, _U, _U, _U, _U, _U, _P]
@@ -193,6 +194,18 @@ class Geometry:
         out = np.zeros(len(xyz), np.int64)
         self.lib.orc_find_cell(self.h, len(xyz), _ptr(xyz), _ptr(out))
         return out
+
+    def distance(self, xyz: np.ndarray, dirs: np.ndarray):
+        """distance_to_surface from points with directions: (distance,
+        level of the winning surface, leaf instance); NaN / -1 outside."""
+        xyz = np.ascontiguousarray(xyz, np.float64)
+        dirs = np.ascontiguousarray(dirs, np.float64)
+        n = len(xyz)
+        d = np.zeros(n, np.float64)
+        lev = np.zeros(n, np.int32)
+        inst = np.zeros(n, np.int64)
+        self.lib.orc_distance(self.h, n, _ptr(xyz), _ptr(dirs), _ptr(d), _ptr(lev), _ptr(inst))
+        return d, lev, inst
 
     def find_cell_brute(self, xyz: np.ndarray):
         xyz = np.ascontiguousarray(xyz, np.float64)

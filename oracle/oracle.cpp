@@ -1550,6 +1550,29 @@ int orc_find_cell(void* gp, long long n, const double* xyz, long long* inst) {
     return 0;
 }
 
+// distance_to_surface (Table 1) from global points with directions, the
+// point taken as on no surface: hierarchical find_cell, then the level scan
+// of distance_to_boundary.  dist NaN and level/inst -1 for a point in no cell.
+int orc_distance(void* gp, long long n, const double* xyz, const double* dir, double* dist, int* level,
+                 long long* inst) {
+    Geometry* g = static_cast<Geometry*>(gp);
+    for (long long i = 0; i < n; ++i) {
+        Particle p;
+        for (int d = 0; d < 3; ++d) { p.r[d] = xyz[3 * i + d]; p.dir[d] = dir[3 * i + d]; }
+        set_direction_inverse(p);
+        p.lv[0].u = g->root;
+        dist[i] = std::numeric_limits<double>::quiet_NaN();
+        level[i] = -1;
+        inst[i] = -1;
+        if (!find_cell_from(*g, p, 0)) continue;
+        const Hit h = distance_to_boundary(*g, p);
+        dist[i] = dv(h.d);
+        level[i] = h.level;
+        inst[i] = p.inst();
+    }
+    return 0;
+}
+
 // Brute force over every leaf instance: first containing instance (-1 none),
 // number of containing instances, and the distance from the point to the
 // nearest constraint surface of any containing instance (or of all when none).

@@ -182,6 +182,36 @@ __global__ void __launch_bounds__(128) k_find(const DevGeom g, long long n, cons
     }
 }
 
+// distance_to_surface for points (diagnostic): find_cell from the root, then
+// the distance over the levels with the tracking kernels' tie rules.
+template <int TK>
+__global__ void __launch_bounds__(128) k_distance(const DevGeom g, long long n, const double* __restrict__ xyz,
+                                                  const double* __restrict__ dir, double* __restrict__ dist,
+                                                  int32_t* __restrict__ level, int64_t* __restrict__ inst) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        St s;
+        clear_levels(s);
+        s.x = xyz[3 * i]; s.y = xyz[3 * i + 1]; s.z = xyz[3 * i + 2];
+        s.d.u = dir[3 * i]; s.d.v = dir[3 * i + 1]; s.d.w = dir[3 * i + 2];
+        set_inverse(s.d);
+        s.tau = 0.0;
+        s.lv[0].u = g.root;
+        double d = __longlong_as_double(0x7ff8000000000000LL);
+        int lev = -1;
+        long long in = -1;
+        if (find_from<TK>(g, s, 0) == 0) {
+            const Hit h = distance_to_boundary<TK>(g, s);
+            d = h.d;
+            lev = h.level;
+            in = instance(s);
+        }
+        dist[i] = d;
+        if (level) level[i] = lev;
+        if (inst) inst[i] = in;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Transmission along rays (no collisions) and its backward pass.
 // ---------------------------------------------------------------------------
@@ -668,6 +698,38 @@ trk_status trk_find_cell(trk_geom_t g, int tracker, int64_t n, const double* dev
         k_find<false><<<gr, 128, 0, s>>>(g->dg, n, dev_xyz, dev_inst);
     }
     return launch_error("trk_find_cell");
+}
+
+trk_status trk_distance_to_surface(trk_geom_t g, int tracker, int64_t n, const double* dev_xyz, const double* dev_dir,
+                                   double* dev_dist, int32_t* dev_level, int64_t* dev_inst, void* stream) {
+    if (!valid(g) || n < 0 || (n > 0 && (!dev_xyz || !dev_dir || !dev_dist)))
+        return trk_status(set_error(TRK_E_INVALID, "trk_distance_to_surface: bad arguments"));
+    trk_status st;
+    const int t = resolve_tracker(g, tracker, &st, true);
+    if (t < 0) return st;
+    if (n == 0) return TRK_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+#define TRK_DIST(TKV)                                                                                  \
+    do {                                                                                               \
+        const int gr = persistent_grid(k_distance<TKV>, 128, n, 0);                                    \
+        k_distance<TKV><<<gr, 128, 0, s>>>(g->dg, n, dev_xyz, dev_dir, dev_dist, dev_level, dev_inst); \
+    } while (0)
+    if (t == TRK_TRACKER_CSG) TRK_DIST(TK_CSG);
+    else if (t == TRK_TRACKER_DP) TRK_DIST(TK_DP);
+    else TRK_DIST(TK_RECT);
+#undef TRK_DIST
+    return launch_error("trk_distance_to_surface");
+}
+
+trk_status trk_sync_status(const uint64_t* dev_counters, void* stream) {
+    if (!dev_counters) return trk_status(set_error(TRK_E_INVALID, "trk_sync_status: null counters"));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint64_t status = 0;
+    cudaError_t e = cudaMemcpyAsync(&status, dev_counters + TRK_K_STATUS, 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return trk_status(set_error(TRK_E_CUDA, "trk_sync_status: %s", cudaGetErrorString(e)));
+    if (status != 0) return trk_status(set_error(int(int64_t(status)), "kernel reported status %lld", (long long)int64_t(status)));
+    return TRK_OK;
 }
 
 trk_status transmission_fwd(trk_geom_t g, int tracker, int64_t n, const double* dev_rays, const double* dev_sigma,

@@ -82,6 +82,8 @@ def library(exact: bool = False):
             "run_histories": (ctypes.c_int, [_P, _P, i64, _P, _P, _P, _P, sz, ctypes.POINTER(RunOpts), _P]),
             "tally_read": (ctypes.c_int, [_P, _P, _P, i64, _P, _P]),
             "trk_find_cell": (ctypes.c_int, [_P, ctypes.c_int, i64, _P, _P, _P]),
+            "trk_distance_to_surface": (ctypes.c_int, [_P, ctypes.c_int, i64, _P, _P, _P, _P, _P, _P]),
+            "trk_sync_status": (ctypes.c_int, [_P, _P]),
             "trk_trace": (ctypes.c_int, [_P, _P, i64, ctypes.c_int32, _P, _P, _P, _P,
                                          ctypes.POINTER(RunOpts), _P]),
             "transmission_fwd": (ctypes.c_int, [_P, ctypes.c_int, i64, _P, _P, _P, _P, _P]),
@@ -262,6 +264,19 @@ class Geometry:
                                                 _stream(stream)))
         return out
 
+    def distance_to_surface(self, xyz, dirs, tracker=TRACKER_AUTO, stream=None):
+        """(distance, level, leaf instance) per point: find_cell from the
+        root, then distance_to_surface over the levels."""
+        xyz = xyz.contiguous()
+        dirs = dirs.contiguous()
+        n = xyz.shape[0]
+        d = torch.empty(n, dtype=torch.float64, device=self.device)
+        lev = torch.empty(n, dtype=torch.int32, device=self.device)
+        inst = torch.empty(n, dtype=torch.int64, device=self.device)
+        _check(self.lib, self.lib.trk_distance_to_surface(self.h, tracker, n, _ptr(xyz), _ptr(dirs), _ptr(d),
+                                                          _ptr(lev), _ptr(inst), _stream(stream)))
+        return d, lev, inst
+
     def trace(self, particles, n: int, cap: int, opts: RunOpts | None = None, stream=None, **kw):
         opts = opts if opts is not None else default_opts(**kw)
         inst = torch.empty(n * cap, dtype=torch.int32, device=self.device)
@@ -376,6 +391,13 @@ def transmission_bwd_noalloc(geom: "Geometry", rays, sigma, pitch: float, gT, gr
     _check(geom.lib, geom.lib.transmission_bwd_noalloc(geom.h, tracker, rays.shape[0], _ptr(rays), _ptr(sigma),
                                                        float(pitch), _ptr(gT), _ptr(grad_out), _stream(stream)))
     return grad_out
+
+
+def sync_status(counters, stream=None, exact: bool = False) -> None:
+    """Synchronises the stream and raises TrkError if a kernel wrote a
+    status to counters[status] (trk_sync_status)."""
+    lib = library(exact)
+    _check(lib, lib.trk_sync_status(_ptr(counters), _stream(stream)))
 
 
 def unpack_records(rec: torch.Tensor):

@@ -510,3 +510,93 @@ def test_power_deterministic_and_sharded_threads():
 def test_power_without_fissile_material_stops():
     r = _geom(I.config1()).power(500, 1, 0.3, 1, 3)
     assert not r["ok"] and r["k"][0] == 0.0
+
+
+# ---------------------------------------------------------------------------
+# distance_to_surface from points (the diagnostic entry)
+# ---------------------------------------------------------------------------
+
+def _c1_distance_brute(p, w, pitch=1.26, n=17, radii=(0.41, 0.475), height=100.0):
+    """Configuration 1 by hand in the global frame: the element's four side
+    faces, the box's z planes and the pin's two cylinders (smallest positive
+    root of the quadratic); returns (distance, level: 0 faces, 1 cylinders)."""
+    grid = np.array([(i - n / 2.0) * pitch for i in range(n + 1)])
+    cand = []
+    for d in range(2):
+        i = int(np.searchsorted(grid, p[d], side="right") - 1)
+        if w[d] > 0:
+            cand.append(((grid[i + 1] - p[d]) / w[d], 0))
+        elif w[d] < 0:
+            cand.append(((grid[i] - p[d]) / w[d], 0))
+    if w[2] > 0:
+        cand.append(((height - p[2]) / w[2], 0))
+    elif w[2] < 0:
+        cand.append(((0.0 - p[2]) / w[2], 0))
+    ix = int(np.searchsorted(grid, p[0], side="right") - 1)
+    iy = int(np.searchsorted(grid, p[1], side="right") - 1)
+    cx, cy = 0.5 * (grid[ix] + grid[ix + 1]), 0.5 * (grid[iy] + grid[iy + 1])
+    qx, qy = p[0] - cx, p[1] - cy
+    a = w[0] ** 2 + w[1] ** 2
+    b = qx * w[0] + qy * w[1]
+    for r in radii:
+        c = qx * qx + qy * qy - r * r
+        disc = b * b - a * c
+        if a > 0 and disc > 0:
+            for t in ((-b - np.sqrt(disc)) / a, (-b + np.sqrt(disc)) / a):
+                if t > 1e-12:
+                    cand.append((t, 1))
+                    break
+    cand.sort()
+    return cand[0][0], cand[0][1], (cand[1][0] if len(cand) > 1 else np.inf)
+
+
+@pytest.mark.parametrize("mode", [O.MODE_RECT, O.MODE_CSG])
+def test_distance_against_hand_computed_config1(mode):
+    # random points and isotropic directions: the oracle's hierarchical
+    # distance equals the global-frame closed forms (ties excluded)
+    rng = np.random.default_rng(11)
+    n = 3000
+    xyz = np.column_stack([rng.uniform(-10.7, 10.7, n), rng.uniform(-10.7, 10.7, n), rng.uniform(0.1, 99.9, n)])
+    w = rng.normal(size=(n, 3))
+    w /= np.linalg.norm(w, axis=1)[:, None]
+    d, lev, inst = _geom(I.config1(), mode).distance(xyz, w)
+    checked = 0
+    for k in range(n):
+        t, l, t2 = _c1_distance_brute(xyz[k], w[k])
+        if t2 - t < 1e-9 * max(1.0, t):
+            continue
+        assert abs(d[k] - t) <= 1e-12 * max(1.0, t), (k, d[k], t)
+        assert lev[k] == l and inst[k] >= 0
+        checked += 1
+    assert checked > 0.99 * n
+
+
+def test_distance_closed_forms_and_outside():
+    g = _geom(I.config1(), O.MODE_RECT)
+    # from a pin's axis the fuel cylinder lies r / sqrt(u^2 + v^2) away
+    c = 0.5 * ((0 - 8.5) * 1.26 + (1 - 8.5) * 1.26)      # centre of element 8
+    xyz = np.array([[0.0, 0.0, 50.0], [c, c, 50.0], [c, 0.0, 20.0], [0.0, 0.0, 50.0]])
+    w = np.array([[1.0, 0.0, 0.0], [0.6, 0.0, 0.8], [0.0, -1.0, 0.0], [0.0, 0.0, 1.0]])
+    d, lev, _ = g.distance(xyz, w)
+    assert abs(d[0] - 0.41) <= 1e-15 and lev[0] == 1
+    assert abs(d[1] - 0.41 / 0.6) <= 1e-15 and lev[1] == 1
+    assert abs(d[2] - 0.41) <= 1e-15 and lev[2] == 1
+    # straight up the axis: the top of the box, at the root level
+    assert d[3] == 50.0 and lev[3] == 0
+    # outside the box: NaN, no level, no cell
+    d, lev, inst = g.distance(np.array([[11.0, 0.0, 5.0]]), np.array([[1.0, 0.0, 0.0]]))
+    assert np.isnan(d[0]) and lev[0] == -1 and inst[0] == -1
+
+
+def test_distance_rect_and_csg_modes_identical():
+    # pseudo-array planes are the lattice's own grid values in the same frames
+    rng = np.random.default_rng(12)
+    for desc in (I.small_core(), I.random_tiny(5)):
+        lo, hi = np.array(desc["source_box"][:3]), np.array(desc["source_box"][3:])
+        xyz = lo + rng.uniform(size=(2000, 3)) * (hi - lo)
+        w = rng.normal(size=(2000, 3))
+        w /= np.linalg.norm(w, axis=1)[:, None]
+        a = _geom(desc, O.MODE_RECT).distance(xyz, w)
+        b = _geom(desc, O.MODE_CSG).distance(xyz, w)
+        assert np.array_equal(a[0], b[0], equal_nan=True) and np.array_equal(a[1], b[1])
+        assert np.array_equal(a[2], b[2])
