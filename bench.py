@@ -335,6 +335,39 @@ def main() -> None:
         b.record(stream)
         torch.cuda.synchronize()
         pk = max(pk, ops / (a.elapsed_time(b) / 1e3) / 1e12)
+    # the other ceilings of the tracking kernels: FP32 FMA and u64 atomic adds
+    # into L2, spread over a tally-sized array and contended on 1024 bins
+    big = torch.empty(max(1 << 16, 8 * g.n_inst), dtype=torch.uint8, device=dev)
+
+    def peak_of(kind, blocks, iters, nbins, buf):
+        best = 0.0
+        for _ in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ops = N.peak_kernel(kind, blocks, iters, nbins, buf)
+            b.record(stream)
+            torch.cuda.synchronize()
+            best = max(best, ops / (a.elapsed_time(b) / 1e3))
+        return best
+    fp32_tf = peak_of(1, sms * 8, 4096, 0, scratch) / 1e12
+    atom_spread = peak_of(2, sms * 8, 256, g.n_inst, big)
+    atom_hot = peak_of(2, sms * 8, 64, 1024, big)
+    seg_rate_kernel = seg_per_launch / (kern_ms / 1e3)
+    traffic_launch = TRAFFIC_BYTES_PER_SEGMENT * seg_per_launch if TRAFFIC_BYTES_PER_SEGMENT else None
+    hbm_peak = None
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            hbm_peak = float(json.load(f)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        hbm_peak = 6800.0
+    util = {"fp64_pipe": achieved / pk if pk else None,
+            "l2_atomic": seg_rate_kernel / atom_spread if atom_spread else None,
+            "hbm": (traffic_launch / (kern_ms / 1e3) / 1e9 / hbm_peak) if traffic_launch else None}
+    util["max"] = max(v for v in util.values() if v is not None)
+    peaks = {"fp64_fma_tflops": pk, "fp32_fma_tflops": fp32_tf,
+             "u64_atomic_per_s_spread": atom_spread, "u64_atomic_per_s_1024_bins": atom_hot,
+             "hbm_gbs": hbm_peak, "source": "trk_peak_kernel in this run (CUDA events, best of 3); HBM from "
+                                             "the measured copy bandwidth"}
     roofline = {"bound": "alu", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
                 "frac": achieved / pk if pk else None,
                 "traffic": TRAFFIC_BYTES_PER_SEGMENT * seg_per_launch if TRAFFIC_BYTES_PER_SEGMENT else None,
@@ -344,7 +377,12 @@ def main() -> None:
                 "peak_source": "measured FP64 FMA rate (trk_peak_kernel, same run; of measured)",
                 "flops_per_segment": fps["per_segment"],
                 "flops_definition": "FP64 add/sub, mul, div, sqrt per segment counted by the oracle's counting "
-                                    "build in rect-tracker mode on this workload"}
+                                    "build in rect-tracker mode on this workload",
+                "utilisation": util,
+                "utilisation_definition": "fp64_pipe: frac; l2_atomic: tally atomics (one per segment) per second "
+                                          "over the spread u64 atomic rate; hbm: traffic per launch over the "
+                                          "launch time, over the measured copy bandwidth",
+                "peaks": peaks}
 
     # ---- configuration 1 size sweep and the transmission workload ----------
     sweep = run_config1_sweep(N, I, dev, stream, barrier)
