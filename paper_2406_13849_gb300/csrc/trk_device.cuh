@@ -164,15 +164,60 @@ __device__ __forceinline__ Pt make_pt(double x, double y, double z) {
     return p;
 }
 
+// Cylinder senses certified in FP32 before any FP64 evaluation (build knob;
+// results are unchanged either way).
+#ifndef TRK_CYL_SENSE_F32
+#define TRK_CYL_SENSE_F32 1
+#endif
+
+// x truncated toward zero to FP32 by integer operations on its bits (no
+// FP64 instruction): relative error below 2^-23; |x| < 2^-126 gives 0 and
+// |x| >= 2^128 gives NaN (which fails every comparison).
+__device__ __forceinline__ float trunc_to_f32(double x) {
+    const long long b = __double_as_longlong(x);
+    const unsigned hi = unsigned(b >> 32), lo = unsigned(b);
+    const int e = int((hi >> 20) & 0x7ffu);
+    const unsigned sign = hi & 0x80000000u;
+    if (e < 897) return __uint_as_float(sign);
+    if (e > 1150) return __uint_as_float(0x7fc00000u);
+    return __uint_as_float(sign | (unsigned(e - 896) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
+}
+
+// Sign of a cylinder's f = (qx qx + qy qy) - r r certified in FP32, without
+// the FP64 pipe: +1 or -1 when the FP32 value clears the error bound, 0 when
+// the FP64 evaluation must decide.  With X = |x| + |x0|, Y = |y| + |y0|: the
+// truncations and roundings give |q_f - q| <= 2^-22 X (resp. Y), so
+// |f32 - f| <= 2^-20 (X^2 + Y^2 + r^2) with the three FP32 roundings (or
+// fewer, contracted), and the FP64 value is within 2^-50 (X^2 + Y^2 + r^2)
+// of f; X^2 + Y^2 + r^2 <= 2.01 S for S = x_f^2 + y_f^2 + x0_f^2 + y0_f^2 +
+// r^2_f.  |f32| > 2^-15 S (4x the needed 2^-17 S) therefore fixes the sign
+// the FP64 evaluation would compute.
+__device__ __forceinline__ int cyl_sense_f32(const DevGeom& g, int s, const Pt& p) {
+    const float4 cf = __ldg(g.s_coeff + s);   // x0, y0, r*r, r
+    const float xf = trunc_to_f32(p.x), yf = trunc_to_f32(p.y);
+    const float qx = xf - cf.x, qy = yf - cf.y;
+    const float f = (qx * qx + qy * qy) - cf.z;
+    const float sm = ((xf * xf + yf * yf) + (cf.x * cf.x + cf.y * cf.y)) + cf.z;
+    const float bound = sm * 0x1p-15f;
+    return f > bound ? 1 : (f < -bound ? -1 : 0);
+}
+
 // Sense of the point relative to surface s (entry type `type`): f >= 0 is "+".
 //   px: x - g >= 0 <=> x >= g (integer key compare);
-//   p: ((nx x + ny y) + nz z) - d;  cz: (qx qx + qy qy) - r r.
+//   p: ((nx x + ny y) + nz z) - d;  cz: (qx qx + qy qy) - r r, decided in
+//   FP32 when the FP32 value certifies the sign (cyl_sense_f32).
 __device__ __forceinline__ int sense_at(const DevGeom& g, int s, int type, const Pt& p) {
     if (type <= S_PZ) {
         const long long kg = __ldg(g.s_key + s);
         const long long kp = type == S_PX ? p.kx : (type == S_PY ? p.ky : p.kz);
         return kp >= kg ? 1 : -1;
     }
+#if TRK_CYL_SENSE_F32
+    if (type == S_CZ) {
+        const int sf = cyl_sense_f32(g, s, p);
+        if (sf != 0) return sf;
+    }
+#endif
     double c0, c1, c2, c3;
     load_coef(g, s, c0, c1, c2, c3);
     double f;
