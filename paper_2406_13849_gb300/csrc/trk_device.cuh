@@ -169,6 +169,10 @@ __device__ __forceinline__ Pt make_pt(double x, double y, double z) {
 #ifndef TRK_CYL_SENSE_F32
 #define TRK_CYL_SENSE_F32 1
 #endif
+// and the distance scan's cylinder screen certified in FP32 first
+#ifndef TRK_CYL_SCREEN_F32
+#define TRK_CYL_SCREEN_F32 1
+#endif
 
 // x truncated toward zero to FP32 by integer operations on its bits (no
 // FP64 instruction): relative error below 2^-23; |x| < 2^-126 gives 0 and
@@ -200,6 +204,23 @@ __device__ __forceinline__ int cyl_sense_f32(const DevGeom& g, int s, const Pt& 
     const float sm = ((xf * xf + yf * yf) + (cf.x * cf.x + cf.y * cf.y)) + cf.z;
     const float bound = sm * 0x1p-15f;
     return f > bound ? 1 : (f < -bound ? -1 : 0);
+}
+
+// FP32 certificate for the distance scan's cylinder screen: true only when
+// the FP64 screen (-f > 2 r bd + (2 r bd + r^2) 2^-40) would hold, so the
+// candidate is skipped with the same result.  -f64 >= -f32 - 2^-15 S (the
+// bound of cyl_sense_f32), and the FP64 right-hand side is at most
+// 2 r bd (1 + 2^-19) + (2 r bd + r^2) 2^-38 with r and bd taken from FP32
+// copies within 2^-22 of them (a bd beyond FP32 range or a NaN fails).
+__device__ __forceinline__ bool cyl_beyond_f32(const DevGeom& g, int s, double x, double y, double bd) {
+    const float4 cf = __ldg(g.s_coeff + s);   // x0, y0, r*r, r
+    const float xf = trunc_to_f32(x), yf = trunc_to_f32(y), bf = trunc_to_f32(bd);
+    const float qx = xf - cf.x, qy = yf - cf.y;
+    const float f = (qx * qx + qy * qy) - cf.z;
+    const float sm = ((xf * xf + yf * yf) + (cf.x * cf.x + cf.y * cf.y)) + cf.z;
+    const float tb = (cf.w + cf.w) * bf;
+    const float rhs = tb * (1.0f + 0x1p-19f) + (tb + cf.z) * 0x1p-38f;
+    return -f - sm * 0x1p-15f > rhs;
 }
 
 // Sense of the point relative to surface s (entry type `type`): f >= 0 is "+".
@@ -829,6 +850,9 @@ __device__ __forceinline__ void dist_level_csg(const DevGeom& g, const St& s, in
         const bool on = (s.on_lev == l && s.on_surf == sid);
         if (type == S_CZ && side < 0 && !on && (hk != kinf || ck != kinf)) {
             const double bd = ck < hk ? c.d : hd;
+#if TRK_CYL_SCREEN_F32
+            if (cyl_beyond_f32(g, sid, x, y, bd)) continue;
+#endif
             double c0, c1, c2, c3;
             load_coef(g, sid, c0, c1, c2, c3);
             const double qx = x - c0, qy = y - c1;
