@@ -44,7 +44,7 @@ EVENT_SLOTS = 512
 # capture of the same kernel on the same geometry with 3e6 particles
 # (41.24 GB over 82,931,315 segments); scaled to a full launch by its
 # segments.  None whenever the kernel has changed since that capture.
-TRAFFIC_BYTES_PER_SEGMENT = (26.894978e9 + 14.296893e9) / 82931315
+TRAFFIC_BYTES_PER_SEGMENT = (26.819490e9 + 14.276296e9) / 82931315
 
 
 def _env_int(k, d):
