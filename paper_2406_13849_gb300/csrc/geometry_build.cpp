@@ -90,7 +90,16 @@ class Json {
         ++p_;
         return true;
     }
+    int depth_ = 0;
+    static const int MAX_DEPTH = 64;   // descriptions nest about five deep; this bounds the recursion
     int value() {
+        if (depth_ >= MAX_DEPTH) return bad("JSON nested too deeply");
+        ++depth_;
+        const int v = value_at();
+        --depth_;
+        return v;
+    }
+    int value_at() {
         skip();
         if (p_ >= e_) return bad("unexpected end of description");
         if (*p_ == '{') {
@@ -227,10 +236,27 @@ bool read_nums(const Json& J, int node, std::vector<double>& out) {
     return true;
 }
 
+bool finite_all(const std::vector<double>& v) {
+    for (double x : v) if (!std::isfinite(x)) return false;
+    return true;
+}
+
 bool num(const Json& J, int obj, const char* key, double& out) {
     int m = J.member(obj, key);
     if (m < 0 || J.at(m).t != 'd') return false;
     out = J.at(m).d;
+    return true;
+}
+
+// Optional integer member: absent leaves `out` as it is; present, it must be
+// a number holding an integer in [lo, hi].
+bool opt_int(const Json& J, int obj, const char* key, int lo, int hi, int& out) {
+    int m = J.member(obj, key);
+    if (m < 0) return true;
+    if (J.at(m).t != 'd') return false;
+    const double v = J.at(m).d;
+    if (!(v >= double(lo) && v <= double(hi)) || v != std::floor(v)) return false;
+    out = int(v);
     return true;
 }
 
@@ -242,7 +268,7 @@ int parse(const char* json, size_t len, HGeom& G) {
     const int root = 0;
     if (J.at(root).t != 'o') DESC_FAIL("description is not a JSON object");
     double x;
-    if (num(J, root, "geometry_id", x)) G.gid = int(x);
+    if (!opt_int(J, root, "geometry_id", 0, 0x7fffffff, G.gid)) DESC_FAIL("'geometry_id' must be an integer in [0, 2^31)");
     if (!read_nums(J, J.member(root, "sigma"), G.sigma) || G.sigma.empty()) DESC_FAIL("'sigma' missing or empty");
     for (double s : G.sigma) if (!(s >= 0.0) || !std::isfinite(s)) DESC_FAIL("sigma must be finite and >= 0");
     G.nu.assign(G.sigma.size(), 0.0);
@@ -274,8 +300,8 @@ int parse(const char* json, size_t len, HGeom& G) {
         if (s.type == S_CZ && !(s.c[2] > 0)) DESC_FAIL("surface %zu: cylinder radius must be > 0", i);
         s.bc = bc_code(J, J.member(so, "bc"));
         if (s.bc == BC_REFLECT && s.type == S_CZ) DESC_FAIL("surface %zu: reflecting cylinders are not supported", i);
-        if (num(J, so, "rparam", x)) s.rparam = int(x);
-        if (num(J, so, "pscale", x)) s.pscale = int(x);
+        if (!opt_int(J, so, "rparam", -1, TRK_NGEOM_PARAMS - 2, s.rparam)) DESC_FAIL("surface %zu: 'rparam' must be -1, 0, 1 or 2", i);
+        if (!opt_int(J, so, "pscale", 0, 1, s.pscale)) DESC_FAIL("surface %zu: 'pscale' must be 0 or 1", i);
         G.surf.push_back(s);
     }
     int ul = J.member(root, "universes");
@@ -299,9 +325,10 @@ int parse(const char* json, size_t len, HGeom& G) {
                 for (int pr : J.at(ss).kids) {
                     std::vector<double> v;
                     if (!read_nums(J, pr, v) || v.size() != 2) DESC_FAIL("universe %d cell %zu: bad surface pair", ui, ci);
-                    int sid = int(v[0]), sn = int(v[1]);
-                    if (sid < 0 || sid >= int(G.surf.size()) || double(sid) != v[0]) DESC_FAIL("universe %d cell %zu: bad surface id", ui, ci);
-                    if (sn != 1 && sn != -1) DESC_FAIL("universe %d cell %zu: sense must be +1 or -1", ui, ci);
+                    if (!(v[0] >= 0.0 && v[0] < double(G.surf.size())) || v[0] != std::floor(v[0]))
+                        DESC_FAIL("universe %d cell %zu: bad surface id", ui, ci);
+                    if (v[1] != 1.0 && v[1] != -1.0) DESC_FAIL("universe %d cell %zu: sense must be +1 or -1", ui, ci);
+                    const int sid = int(v[0]), sn = int(v[1]);
                     c.surf.push_back(sid);
                     c.sense.push_back(sn);
                 }
@@ -315,7 +342,7 @@ int parse(const char* json, size_t len, HGeom& G) {
                     std::vector<double> tr;
                     int tn2 = J.member(co, "translation");
                     if (tn2 >= 0) {
-                        if (!read_nums(J, tn2, tr) || tr.size() != 3) DESC_FAIL("universe %d cell %zu: bad translation", ui, ci);
+                        if (!read_nums(J, tn2, tr) || tr.size() != 3 || !finite_all(tr)) DESC_FAIL("universe %d cell %zu: bad translation", ui, ci);
                         for (int d = 0; d < 3; ++d) c.tr[d] = tr[size_t(d)];
                     }
                 } else DESC_FAIL("universe %d cell %zu: needs 'material' or 'fill'", ui, ci);
@@ -327,7 +354,8 @@ int parse(const char* json, size_t len, HGeom& G) {
             if (gl < 0 || J.at(gl).t != 'a' || J.at(gl).kids.size() != 3) DESC_FAIL("universe %d: rect needs 3 grids", ui);
             size_t ne = 1;
             for (int d = 0; d < 3; ++d) {
-                if (!read_nums(J, J.at(gl).kids[size_t(d)], U.grid[d]) || U.grid[d].size() < 2) DESC_FAIL("universe %d: bad grid %d", ui, d);
+                if (!read_nums(J, J.at(gl).kids[size_t(d)], U.grid[d]) || U.grid[d].size() < 2 || !finite_all(U.grid[d]))
+                    DESC_FAIL("universe %d: bad grid %d", ui, d);
                 for (size_t i = 1; i < U.grid[d].size(); ++i)
                     if (!(U.grid[d][i] > U.grid[d][i - 1])) DESC_FAIL("universe %d: grid %d not increasing", ui, d);
                 ne *= U.grid[d].size() - 1;
@@ -343,14 +371,15 @@ int parse(const char* json, size_t len, HGeom& G) {
                 if (J.at(bl).t != 'a' || J.at(bl).kids.size() != 6) DESC_FAIL("universe %d: rect bc needs 6 entries", ui);
                 for (int k = 0; k < 6; ++k) U.bc[k] = bc_code(J, J.at(bl).kids[size_t(k)]);
             }
-            if (num(J, uo, "pscale", x)) U.pscale = int(x);
+            if (!opt_int(J, uo, "pscale", 0, 1, U.pscale)) DESC_FAIL("universe %d: 'pscale' must be 0 or 1", ui);
         } else if (t == "hex") {
             U.type = UT_HEX;
             std::vector<double> a1, a2, zz;
             double rings, hp;
-            if (!num(J, uo, "rings", rings) || rings < 0 || rings > 64 || !read_nums(J, J.member(uo, "a1"), a1) ||
+            if (!num(J, uo, "rings", rings) || !(rings >= 0 && rings <= 64) || rings != std::floor(rings) || !read_nums(J, J.member(uo, "a1"), a1) ||
                 !read_nums(J, J.member(uo, "a2"), a2) || !read_nums(J, J.member(uo, "z"), zz) || a1.size() != 2 ||
-                a2.size() != 2 || zz.size() != 2 || !num(J, uo, "half_pitch", hp) || !(hp > 0) || !(zz[1] > zz[0]))
+                a2.size() != 2 || zz.size() != 2 || !num(J, uo, "half_pitch", hp) || !(hp > 0) || !std::isfinite(hp) ||
+                !finite_all(a1) || !finite_all(a2) || !finite_all(zz) || !(zz[1] > zz[0]))
                 DESC_FAIL("universe %d: malformed hex array", ui);
             U.rings = int(rings);
             U.a1[0] = a1[0]; U.a1[1] = a1[1]; U.a2[0] = a2[0]; U.a2[1] = a2[1];
@@ -360,7 +389,8 @@ int parse(const char* json, size_t len, HGeom& G) {
             if (nl < 0 || J.at(nl).t != 'a' || J.at(nl).kids.size() != 3) DESC_FAIL("universe %d: hex needs 3 normals", ui);
             for (int k = 0; k < 3; ++k) {
                 std::vector<double> nk;
-                if (!read_nums(J, J.at(nl).kids[size_t(k)], nk) || nk.size() != 2) DESC_FAIL("universe %d: bad hex normal", ui);
+                if (!read_nums(J, J.at(nl).kids[size_t(k)], nk) || nk.size() != 2 || !finite_all(nk) || !(nk[0] != 0.0 || nk[1] != 0.0))
+                    DESC_FAIL("universe %d: bad hex normal", ui);
                 U.nrm[k][0] = nk[0]; U.nrm[k][1] = nk[1];
             }
             const int R = U.rings;
@@ -385,7 +415,7 @@ int parse(const char* json, size_t len, HGeom& G) {
     if (!num(J, root, "root", x) || x < 0 || x >= nu || double(int(x)) != x) DESC_FAIL("'root' missing or out of range");
     G.root = int(x);
     std::vector<double> sb;
-    if (!read_nums(J, J.member(root, "source_box"), sb) || sb.size() != 6) DESC_FAIL("'source_box' needs 6 numbers");
+    if (!read_nums(J, J.member(root, "source_box"), sb) || sb.size() != 6 || !finite_all(sb)) DESC_FAIL("'source_box' needs 6 finite numbers");
     {
         const int ao = J.member(root, "accel");
         if (ao >= 0) {
@@ -902,6 +932,10 @@ int build_host(const char* json, size_t len, Built& B) {
     std::vector<char> busy(G.univ.size(), 0);
     st = count_instances(G, G.root, height, busy);
     if (st != TRK_OK) return st;
+    // every universe must be nested below the root: the flattening below
+    // places, boxes and numbers each one through its parents
+    for (size_t u = 0; u < G.univ.size(); ++u)
+        if (G.univ[u].ninst < 0) return set_error(TRK_E_DESC, "universe %zu is not reachable from the root", u);
     G.depth = height[size_t(G.root)] + 1;
     if (G.depth > MAXL)
         return set_error(TRK_E_UNSUPPORTED, "nesting depth %d exceeds the compiled maximum %d", G.depth, MAXL);

@@ -1,9 +1,11 @@
 """C-ABI checks that need no GPU: the library builds, loads and exports every
 entry point declared in include/*.h; host-side validation returns the
 documented status codes (no compute calls)."""
+import copy
 import ctypes
 import glob
 import os
+import random
 import re
 
 import pytest
@@ -93,3 +95,101 @@ def test_null_arguments():
     assert lib.source_init(None, 1, 0, 0, None, None, None) == -1
     st, _, err = _size("not json at all")
     assert st == -2 and "JSON" in err
+
+
+def _unreachable(d):
+    d["universes"].append(copy.deepcopy(d["universes"][0]))
+
+
+@pytest.mark.parametrize("mutate,needle", [
+    (_unreachable, "not reachable"),
+    (lambda d: d["surfaces"][0].update(rparam=5), "rparam"),
+    (lambda d: d["surfaces"][0].update(rparam=0.5), "rparam"),
+    (lambda d: d["surfaces"][0].update(pscale=2), "pscale"),
+    (lambda d: d["universes"][1].update(pscale=-1), "pscale"),
+    (lambda d: d.update(geometry_id=1e30), "geometry_id"),
+    (lambda d: d.update(geometry_id=-3), "geometry_id"),
+    (lambda d: d["universes"][0]["cells"][0]["surfaces"][0].__setitem__(0, 1e30), "surface id"),
+    (lambda d: d["universes"][0]["cells"][0]["surfaces"][0].__setitem__(1, 0.5), "sense"),
+    (lambda d: d["universes"][1]["grid"][0].__setitem__(0, -1e999), "grid"),
+    (lambda d: d.update(source_box=[0, 0, 0, 1e999, 1, 1]), "source_box"),
+])
+def test_rejects_out_of_range_fields(mutate, needle):
+    """Fields the builder packs into integers or uses as coordinates are range-checked:
+    each of these descriptions once reached undefined behaviour or an out-of-bounds read
+    on the host (found by the fuzz test below)."""
+    d = I.config1()
+    mutate(d)
+    st, _, err = _size(I.to_json(d).replace("Infinity", "1e999"))
+    assert st == -2 and needle in err, err
+
+
+def test_hex_fields_checked():
+    d = I.small_hex()
+    hx = next(u for u in d["universes"] if u["type"] == "hex")
+    hx["rings"] = 1.5
+    assert _size(I.to_json(d))[0] == -2
+    d = I.small_hex()
+    hx = next(u for u in d["universes"] if u["type"] == "hex")
+    hx["normals"][1] = [0.0, 0.0]
+    assert _size(I.to_json(d))[0] == -2
+
+
+def test_deeply_nested_json_is_an_error_not_a_crash():
+    st, _, err = _size("[" * 200000)
+    assert st == -2 and "deep" in err
+    st, _, err = _size('{"a":' * 100000)
+    assert st == -2 and "deep" in err
+
+
+_FUZZ_VALUES = [0, -1, 1, 2, 3, 0.5, -0.5, 1e308, -1e308, 1e30, 2**31, 2**31 - 1, -(2**31), 2**40, 7,
+                64, 65, 1e-300, "x", "reflect", "vacuum", None, True, [], [0], [0, 0], [0, 0, 0], {},
+                [[0, 1]]]
+
+
+def _fuzz_paths(o, pre=()):
+    yield pre
+    if isinstance(o, dict):
+        for k, v in o.items():
+            yield from _fuzz_paths(v, pre + (k,))
+    elif isinstance(o, list):
+        for i, v in enumerate(o):
+            yield from _fuzz_paths(v, pre + (i,))
+
+
+def _fuzz_mutate(d, rng):
+    path = rng.choice(list(_fuzz_paths(d))[1:])
+    parent = d
+    for k in path[:-1]:
+        parent = parent[k]
+    k = path[-1]
+    r = rng.random()
+    if r < 0.15:
+        del parent[k]
+    elif r < 0.3 and isinstance(parent, list):
+        parent.insert(k, copy.deepcopy(parent[k]))
+    else:
+        parent[k] = copy.deepcopy(rng.choice(_FUZZ_VALUES))
+
+
+def test_mutated_descriptions_never_crash_the_builder():
+    """Seeded mutations of valid descriptions (deleted, duplicated or retyped members,
+    extreme numbers, truncated text) through the host-only size query: every one is
+    accepted or rejected with a status; the process must survive all of them."""
+    rng = random.Random(2406)
+    bases = [I.config1(), I.single_pin(), I.small_hex(), I.small_core(), I.small_hex_core(),
+             I.with_mesh(I.single_pin(), 3, 3, 2), I.random_tiny(3), I.config4_member(5)[0],
+             I.with_nu(I.single_pin(), [2.0, 0.0, 0.0])]
+    seen = {}
+    for _ in range(1500):
+        d = copy.deepcopy(rng.choice(bases))
+        for _ in range(rng.randint(1, 3)):
+            _fuzz_mutate(d, rng)
+        txt = I.to_json(d)
+        if rng.random() < 0.05:
+            txt = txt[: rng.randrange(len(txt))]
+        st, nb, err = _size(txt)
+        assert st in (0, -2, -8), (st, err)
+        assert (st == 0) == (err == "") and (st != 0 or nb > 0)
+        seen[st] = seen.get(st, 0) + 1
+    assert seen.get(0, 0) > 20 and seen.get(-2, 0) > 1000
