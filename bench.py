@@ -149,6 +149,43 @@ def flops_per_segment(desc_json: str) -> dict:
     return {"per_segment": ops / seg, "counts_per_segment": {k: v / seg for k, v in fc.items()}}
 
 
+def tally_error(t32, t64, c32=None, c64=None) -> dict:
+    """Error of an FP32-local result against the FP64 result for the same
+    particles (same ids, seed and options).  t32, t64: lists of int64 tally
+    arrays (fixed point, 2^-32 cm) or single arrays; c32, c64: their counter
+    arrays.  The FP64 path is the oracle's arithmetic: bit-equal to it in the
+    exact build, within 1e-12 relative per distance in the fast build."""
+    import numpy as np
+    if not isinstance(t32, (list, tuple)):
+        t32, t64 = [t32], [t64]
+    a = np.concatenate([t.detach().cpu().numpy().view(np.uint64).astype(np.float64) for t in t32])
+    b = np.concatenate([t.detach().cpu().numpy().view(np.uint64).astype(np.float64) for t in t64])
+    d = np.abs(a - b)
+    hit = b > 0
+    rel = d[hit] / b[hit]
+    out = {"tally_l1_rel": float(d.sum() / b.sum()) if b.sum() > 0 else None,
+           "tally_linf_rel": float(rel.max()) if rel.size else None,
+           "tally_p99_rel": float(np.quantile(rel, 0.99)) if rel.size else None,
+           "tally_median_rel": float(np.median(rel)) if rel.size else None,
+           "bins": int(b.size), "bins_only_fp32": int(np.count_nonzero((a > 0) & ~hit))}
+    if c32 is not None and c64 is not None:
+        s32 = float(np.asarray(c32, dtype=np.float64)[0])
+        s64 = float(np.asarray(c64, dtype=np.float64)[0])
+        out["segments_rel_diff"] = (s32 - s64) / s64 if s64 else None
+        out["close_call_fraction"] = float(np.asarray(c32, dtype=np.float64)[10]) / max(1.0, s32)
+    out["against"] = "FP64 event kernel, same particles and seeds (per-bin relative error over bins the FP64 run hit)"
+    return out
+
+
+def _guarded(fn):
+    """Runs an auxiliary report; a Python-level failure becomes an error entry
+    instead of ending the benchmark line."""
+    try:
+        return fn()
+    except Exception as e:  # noqa: BLE001 - reported in the JSON line
+        return {"error": f"{type(e).__name__}: {e}"}
+
+
 # ---------------------------------------------------------------------------
 # reference arm: the CPU oracle as it stands
 # ---------------------------------------------------------------------------
@@ -296,6 +333,18 @@ def main() -> None:
     csg_ev_bih = timed(N.TRACKER_CSG, N.MODE_EVENT, k2, 3)
     g = g_bvh
 
+    # ---- FP32-local error against FP64 on the same particles (untimed) -----
+    def fp32_error_main():
+        t64, t32 = torch.zeros_like(tally), torch.zeros_like(tally)
+        c64, c32 = torch.zeros_like(cnt), torch.zeros_like(cnt)
+        g.source_init(n, seed=SEED, first_id=first_id, out=parts)
+        for prec, t, c in ((N.FP64, t64, c64), (N.FP32_LOCAL, t32, c32)):
+            o = make_opts(N.TRACKER_CSG, N.MODE_EVENT, prec)
+            g.run_histories(parts, n, tally=t, counters=c, opts=o, work=work_for(o))
+        torch.cuda.synchronize()
+        return tally_error(t32, t64, c32.cpu().numpy().view(np.uint64), c64.cpu().numpy().view(np.uint64))
+    fp32_err = _guarded(fp32_error_main)
+
     # ---- end to end through the C-ABI with host buffers ---------------------
     host_parts = torch.empty(parts.numel(), dtype=torch.uint8, pin_memory=True)
     g.source_init(n, seed=SEED, first_id=first_id, out=parts)
@@ -421,6 +470,7 @@ def main() -> None:
                 "dp_fp64_history": rate(dp_hist),
                 "dp_over_rect_history": rate(dp_hist) / rate(rect_hist),
                 "csg_fp32local_event": rate(csg_ev32),
+                "csg_fp32local_error_vs_fp64": fp32_err,
                 "csg_fp64_event_bih": rate(csg_ev_bih),
                 "bih_over_bvh_event": rate(csg_ev_bih) / rate(main_run),
                 "fp32local_close_call_fraction": float(csg_ev32["counters"][10]) / max(1, csg_ev32["segments"]),
@@ -474,9 +524,22 @@ def run_config4(N, I, dev, stream, barrier, rank, steps):
     ev32 = N.default_opts(seed=SEED, p_absorb=P_ABSORB, precision=N.FP32_LOCAL, mode=N.MODE_EVENT)
     ev32, chunk_ev, _ = b.autotune(ev32, reps=2)
     r_ev32 = graph_rate(ev32)
+    snap32 = ([t.clone() for t in b.tallies], b.counters.clone())
     ev64 = N.default_opts(seed=SEED, p_absorb=P_ABSORB, precision=N.FP64, mode=N.MODE_EVENT,
                           queue_depth=ev32.queue_depth)
     r_ev64 = graph_rate(ev64)
+    snap64 = ([t.clone() for t in b.tallies], b.counters.clone())
+
+    def batch_error():
+        c32 = snap32[1].cpu().numpy().view(np.uint64).reshape(-1, 16).sum(axis=0)
+        c64 = snap64[1].cpu().numpy().view(np.uint64).reshape(-1, 16).sum(axis=0)
+        err = tally_error(snap32[0], snap64[0], c32, c64)
+        per = [tally_error(t32, t64)["tally_l1_rel"] for t32, t64 in zip(snap32[0], snap64[0])]
+        per = [v for v in per if v is not None]
+        err["tally_l1_rel_worst_geometry"] = max(per) if per else None
+        err["against"] = "batched FP64 event kernel, same particles, seeds and queue depth"
+        return err
+    ev_err = _guarded(batch_error)
     hi32 = N.default_opts(seed=SEED, p_absorb=P_ABSORB, precision=N.FP32_LOCAL)
     hi32, chunk_hi, _ = b.autotune(hi32, reps=2)
     r_hi32 = graph_rate(hi32)
@@ -503,6 +566,7 @@ def run_config4(N, I, dev, stream, barrier, rank, steps):
     return {"workload": "64 geometries: 3x3..17x17 rect/hex lattices, 2-3 levels, 1e4..1e6 particles "
                         "(log-uniform), %d particles" % sum(counts),
             "batched_fp32local_graph_segments_per_s": r_ev32,
+            "batched_fp32local_error_vs_fp64": ev_err,
             "loop_fp64_history_segments_per_s": r_l,
             "batched_over_loop": r_ev32 / r_l,
             "batched_fp64_event_graph_segments_per_s": r_ev64,
@@ -570,8 +634,8 @@ def run_config3(N, I, dev, stream, barrier, steps):
     n = 10_000_000
     parts = torch.empty(g.particle_bytes(n), dtype=torch.uint8, device=dev)
     g.source_init(n, seed=SEED, out=parts)
-    tally = torch.zeros(g.n_inst, dtype=torch.int64, device=dev)
     cnt = torch.zeros(N.NCOUNTERS, dtype=torch.int64, device=dev)
+    tallies, counts = {}, {}
     out = {"workload": "hex core: 127 assemblies x 91 pins (rings 6 of ring-6 pin lattices turned 30 deg), "
                        "h=200, 5 materials, absorption 0.25, 1e7 particles", "unit": UNIT}
     g_bih = N.Geometry(I.to_json(dict(I.config3(), accel="bih")), device=dev)
@@ -582,8 +646,10 @@ def run_config3(N, I, dev, stream, barrier, steps):
         opts = N.default_opts(tracker=tr, mode=N.MODE_EVENT, precision=prec, seed=SEED,
                               p_absorb=P_ABSORB, queue_depth=EVENT_SLOTS)
         work = torch.empty(gg.work_bytes(n, opts) + 256, dtype=torch.uint8, device=dev)
+        tally = torch.zeros(g.n_inst, dtype=torch.int64, device=dev)
         gg.run_histories(parts, n, tally=tally, counters=cnt, opts=opts, work=work)
         cnt.zero_()
+        tally.zero_()
         barrier()
         a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
@@ -592,6 +658,7 @@ def run_config3(N, I, dev, stream, barrier, steps):
         e.record(stream)
         barrier()
         c = cnt.cpu().numpy().view(np.uint64)
+        tallies[name], counts[name] = tally, c.copy()
         out[name] = int(c[0]) / (a.elapsed_time(e) / 1e3)
         if prec == N.FP32_LOCAL:
             out["fp32local_close_call_fraction"] = float(c[10]) / max(1, int(c[0]))
@@ -599,6 +666,9 @@ def run_config3(N, I, dev, stream, barrier, steps):
             out["segments_per_particle"] = int(c[0]) / (n * steps)
         del work
     out["fp32local_over_fp64"] = out["csg_fp32local_event"] / out["csg_fp64_event"]
+    out["csg_fp32local_error_vs_fp64"] = _guarded(lambda: tally_error(
+        tallies["csg_fp32local_event"], tallies["csg_fp64_event"], counts["csg_fp32local_event"],
+        counts["csg_fp64_event"]))
     out["csg_over_array"] = out["csg_fp64_event"] / out["array_fp64_event"]
     out["bih_over_bvh"] = out["csg_fp64_event_bih"] / out["csg_fp64_event"]
     return out
