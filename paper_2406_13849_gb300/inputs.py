@@ -30,6 +30,16 @@ paper's Sec. 1 (Table 1, Fig. 3) and Sec. 3.2:
 
 The optional "rparam"/"pscale" tags name the design parameters a surface
 depends on (pin radii, lattice pitch) for the transmission gradient.
+
+Other optional keys: "geometry_id" (integer in [0, 2^31), keys the random
+numbers), "accel" ("bvh" or "bih"), "nu" (fission yield per material, in
+[0, 7]) and "mesh" ({"grid": [x planes, y planes, z planes]}).
+
+The builder rejects (TRK_E_DESC) a description in which a universe is not
+reached from the root, an index (surface, material, universe) is out of
+range or not an integer, a sense is not +1/-1, "rparam" is not -1, 0, 1 or
+2, "pscale" is not 0 or 1, a coordinate is not finite, or the JSON nests
+more than 64 deep.
 """
 from __future__ import annotations
 
