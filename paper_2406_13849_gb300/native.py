@@ -121,6 +121,33 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
+_I64 = tuple(d for d in (torch.int64, getattr(torch, "uint64", None)) if d is not None)
+_F64 = (torch.float64,)
+
+
+def _need(t, what: str, device, nbytes: int = 0, dtypes=None, cols: int = 0):
+    """Checks a tensor before its pointer goes to a kernel: on a CUDA device
+    (the geometry's, when that has an index), contiguous, of one of `dtypes`,
+    shaped (n, cols) when cols > 0, and holding at least nbytes bytes.  The C
+    ABI sees only a raw device pointer, so these are caught here, before any
+    launch, as TrkError(TRK_E_INVALID)."""
+    if not isinstance(t, torch.Tensor):
+        raise TrkError(-1, f"{what}: expected a torch tensor, got {type(t).__name__}")
+    if dtypes is not None and t.dtype not in dtypes:
+        raise TrkError(-1, f"{what}: dtype {t.dtype}, expected {' or '.join(str(d) for d in dtypes)}")
+    if cols and (t.dim() != 2 or t.shape[1] != cols):
+        raise TrkError(-1, f"{what}: shape {tuple(t.shape)}, expected (n, {cols})")
+    have = t.numel() * t.element_size()
+    if have < nbytes:
+        raise TrkError(-1, f"{what}: {have} bytes, need {nbytes}")
+    if not t.is_contiguous():
+        raise TrkError(-1, f"{what}: tensor is not contiguous")
+    if t.device.type != "cuda" or (device is not None and device.index is not None and
+                                   t.device.index != device.index):
+        raise TrkError(-1, f"{what}: tensor on {t.device}, expected {device or 'cuda'}")
+    return t
+
+
 def _stream(stream=None):
     s = stream if stream is not None else torch.cuda.current_stream()
     return ctypes.c_void_p(s.cuda_stream)
@@ -185,6 +212,7 @@ class Geometry:
         need = self.particle_bytes(n)
         if out is None:
             out = torch.empty(max(need, 8), dtype=torch.uint8, device=self.device)
+        _need(out, "source_init out", self.device, need)
         b = ctypes.c_size_t(out.numel() * out.element_size())
         _check(self.lib, self.lib.source_init(self.h, n, first_id, seed, _ptr(out), ctypes.byref(b),
                                               _stream(stream)))
@@ -215,17 +243,27 @@ class Geometry:
         if counters is None:
             counters = torch.zeros(NCOUNTERS, dtype=torch.int64, device=self.device)
         rec = torch.zeros(2 * n, dtype=torch.int64, device=self.device) if records else None
+        self._check_run(particles, n, tally, counters, mesh, "run_histories")
         wb = self.work_bytes(n, opts)
         if work is None and wb:
             work = torch.empty(wb + 256, dtype=torch.uint8, device=self.device)
         wp, wlen = None, 0
         if work is not None:
+            _need(work, "run_histories work", self.device)
             off = (-work.data_ptr()) % 256
             wp = ctypes.c_void_p(work.data_ptr() + off)
             wlen = work.numel() * work.element_size() - off
         _check(self.lib, self.lib.run_histories(self.h, _ptr(particles), n, _ptr(tally), _ptr(counters), _ptr(rec),
                                                 wp, wlen, ctypes.byref(opts), _stream(stream)))
         return tally, counters, rec
+
+    def _check_run(self, particles, n, tally, counters, mesh, what):
+        if n > 0 and particles is not None:
+            _need(particles, f"{what} particles", self.device, self.particle_bytes(n))
+        _need(tally, f"{what} tally", self.device, 8 * self.n_inst, _I64)
+        _need(counters, f"{what} counters", self.device, 8 * NCOUNTERS, _I64)
+        if mesh is not None:
+            _need(mesh, f"{what} mesh", self.device, 8 * self.mesh_bins, _I64)
 
     def power_iteration(self, n: int, inactive: int, cycles: int, tally=None, counters=None, mesh=None,
                         opts: RunOpts | None = None, stream=None, **kw):
@@ -239,6 +277,7 @@ class Geometry:
             tally = torch.zeros(self.n_inst, dtype=torch.int64, device=self.device)
         if counters is None:
             counters = torch.zeros(NCOUNTERS, dtype=torch.int64, device=self.device)
+        self._check_run(None, n, tally, counters, mesh, "power_iteration")
         k = torch.zeros(cycles, dtype=torch.float64, device=self.device)
         bank = torch.zeros(cycles, dtype=torch.int64, device=self.device)
         b = ctypes.c_size_t(0)
@@ -251,6 +290,9 @@ class Geometry:
         return k, bank, tally, counters
 
     def tally_read(self, tally, counters=None, stream=None) -> np.ndarray:
+        _need(tally, "tally_read tally", self.device, 8 * self.n_inst, _I64)
+        if counters is not None:
+            _need(counters, "tally_read counters", self.device, 8 * NCOUNTERS, _I64)
         out = np.zeros(self.n_inst, np.float64)
         _check(self.lib, self.lib.tally_read(self.h, _ptr(tally), out.ctypes.data_as(_P), self.n_inst,
                                              _ptr(counters), _stream(stream)))
@@ -258,7 +300,7 @@ class Geometry:
 
     # -- diagnostics ---------------------------------------------------------
     def find_cell(self, xyz, tracker=TRACKER_AUTO, stream=None):
-        xyz = xyz.contiguous()
+        xyz = _need(xyz.contiguous(), "find_cell xyz", self.device, 0, _F64, cols=3)
         out = torch.empty(xyz.shape[0], dtype=torch.int64, device=self.device)
         _check(self.lib, self.lib.trk_find_cell(self.h, tracker, xyz.shape[0], _ptr(xyz), _ptr(out),
                                                 _stream(stream)))
@@ -267,9 +309,9 @@ class Geometry:
     def distance_to_surface(self, xyz, dirs, tracker=TRACKER_AUTO, stream=None):
         """(distance, level, leaf instance) per point: find_cell from the
         root, then distance_to_surface over the levels."""
-        xyz = xyz.contiguous()
-        dirs = dirs.contiguous()
+        xyz = _need(xyz.contiguous(), "distance_to_surface xyz", self.device, 0, _F64, cols=3)
         n = xyz.shape[0]
+        dirs = _need(dirs.contiguous(), "distance_to_surface dirs", self.device, 24 * n, _F64, cols=3)
         d = torch.empty(n, dtype=torch.float64, device=self.device)
         lev = torch.empty(n, dtype=torch.int32, device=self.device)
         inst = torch.empty(n, dtype=torch.int64, device=self.device)
@@ -279,6 +321,8 @@ class Geometry:
 
     def trace(self, particles, n: int, cap: int, opts: RunOpts | None = None, stream=None, **kw):
         opts = opts if opts is not None else default_opts(**kw)
+        if n > 0:
+            _need(particles, "trace particles", self.device, self.particle_bytes(n))
         inst = torch.empty(n * cap, dtype=torch.int32, device=self.device)
         ln = torch.empty(n * cap, dtype=torch.float64, device=self.device)
         tally = torch.zeros(self.n_inst, dtype=torch.int64, device=self.device)
@@ -289,23 +333,26 @@ class Geometry:
 
     # -- transmission --------------------------------------------------------
     def transmission_fwd(self, rays, sigma, tracker=TRACKER_AUTO, lens: bool = True, stream=None):
-        rays = rays.contiguous()
+        rays = _need(rays.contiguous(), "transmission_fwd rays", self.device, 0, _F64, cols=6)
         n = rays.shape[0]
+        sigma = _need(sigma.contiguous(), "transmission_fwd sigma", self.device, 8 * self.n_mat, _F64)
         T = torch.empty(n, dtype=torch.float64, device=self.device)
         L = torch.empty(n, self.n_mat, dtype=torch.float64, device=self.device) if lens else None
-        _check(self.lib, self.lib.transmission_fwd(self.h, tracker, n, _ptr(rays), _ptr(sigma.contiguous()),
+        _check(self.lib, self.lib.transmission_fwd(self.h, tracker, n, _ptr(rays), _ptr(sigma),
                                                    _ptr(T), _ptr(L), _stream(stream)))
         return T, L
 
     def transmission_bwd(self, rays, sigma, pitch: float, gT, tracker=TRACKER_AUTO, stream=None):
-        rays = rays.contiguous()
+        rays = _need(rays.contiguous(), "transmission_bwd rays", self.device, 0, _F64, cols=6)
         n = rays.shape[0]
+        sigma = _need(sigma.contiguous(), "transmission_bwd sigma", self.device, 8 * self.n_mat, _F64)
+        gT = _need(gT.contiguous(), "transmission_bwd gT", self.device, 8 * n, _F64)
         b = ctypes.c_size_t(0)
         _check(self.lib, self.lib.transmission_bwd_work_bytes(self.h, n, ctypes.byref(b)))
         work = torch.empty(max(b.value, 8), dtype=torch.uint8, device=self.device)
         grad = torch.empty(self.n_mat + NGEOM_PARAMS, dtype=torch.float64, device=self.device)
-        _check(self.lib, self.lib.transmission_bwd(self.h, tracker, n, _ptr(rays), _ptr(sigma.contiguous()),
-                                                   float(pitch), _ptr(gT.contiguous()), _ptr(grad), _ptr(work),
+        _check(self.lib, self.lib.transmission_bwd(self.h, tracker, n, _ptr(rays), _ptr(sigma),
+                                                   float(pitch), _ptr(gT), _ptr(grad), _ptr(work),
                                                    work.numel(), _stream(stream)))
         return grad
 
@@ -329,6 +376,10 @@ class Batch:
         self.records = [torch.zeros(2 * max(c, 1), dtype=torch.int64, device=dev) for c in self.counts] \
             if records else None
         self.particles = list(particles)
+        if len(self.particles) != len(self.geoms) or len(self.counts) != len(self.geoms):
+            raise TrkError(-1, "Batch: one particle buffer and one count per geometry")
+        for k, (g, p, c) in enumerate(zip(self.geoms, self.particles, self.counts)):
+            _need(p, f"Batch particles[{k}]", g.device, g.particle_bytes(c) if c > 0 else 0)
         n = len(geoms)
         arr = ctypes.c_void_p * n
         hg = arr(*[g.h.value if isinstance(g.h, ctypes.c_void_p) else g.h for g in geoms])
@@ -388,6 +439,10 @@ def transmission_bwd_noalloc(geom: "Geometry", rays, sigma, pitch: float, gT, gr
                              stream=None):
     """transmission_bwd without a work buffer (its scratch lives in the
     library's fixed device array); writes grad_out (n_materials + 4)."""
+    rays = _need(rays, "transmission_bwd_noalloc rays", geom.device, 0, _F64, cols=6)
+    _need(sigma, "transmission_bwd_noalloc sigma", geom.device, 8 * geom.n_mat, _F64)
+    _need(gT, "transmission_bwd_noalloc gT", geom.device, 8 * rays.shape[0], _F64)
+    _need(grad_out, "transmission_bwd_noalloc grad_out", geom.device, 8 * (geom.n_mat + NGEOM_PARAMS), _F64)
     _check(geom.lib, geom.lib.transmission_bwd_noalloc(geom.h, tracker, rays.shape[0], _ptr(rays), _ptr(sigma),
                                                        float(pitch), _ptr(gT), _ptr(grad_out), _stream(stream)))
     return grad_out
@@ -397,6 +452,7 @@ def sync_status(counters, stream=None, exact: bool = False) -> None:
     """Synchronises the stream and raises TrkError if a kernel wrote a
     status to counters[status] (trk_sync_status)."""
     lib = library(exact)
+    _need(counters, "sync_status counters", None, 8 * NCOUNTERS, _I64)
     _check(lib, lib.trk_sync_status(_ptr(counters), _stream(stream)))
 
 
@@ -412,6 +468,7 @@ def unpack_records(rec: torch.Tensor):
 def peak_kernel(kind: int, blocks: int, iters: int, nbins: int, scratch, stream=None) -> float:
     """Launch one microbenchmark (trk_peak_kernel); returns its operation count."""
     lib = library()
+    _need(scratch, "peak_kernel scratch", None)
     ops = ctypes.c_double(0)
     _check(lib, lib.trk_peak_kernel(kind, blocks, iters, nbins, _ptr(scratch),
                                     scratch.numel() * scratch.element_size(), ctypes.byref(ops),

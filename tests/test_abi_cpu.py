@@ -9,6 +9,7 @@ import random
 import re
 
 import pytest
+import torch
 
 from paper_2406_13849_gb300 import inputs as I
 from paper_2406_13849_gb300 import native as N
@@ -193,3 +194,60 @@ def test_mutated_descriptions_never_crash_the_builder():
         assert (st == 0) == (err == "") and (st != 0 or nb > 0)
         seen[st] = seen.get(st, 0) + 1
     assert seen.get(0, 0) > 20 and seen.get(-2, 0) > 1000
+
+
+def _fake_geometry(n_inst=10, n_mat=3, mesh_bins=0):
+    """A Geometry object without a device image: enough for the binding's
+    checks, which run before any library call."""
+    g = object.__new__(N.Geometry)
+    g.lib, g.exact, g.h = N.library(), False, None
+    g.device = torch.device("cuda")
+    g.n_inst, g.n_mat, g.mesh_bins = n_inst, n_mat, mesh_bins
+    g.particle_bytes = lambda n: 60 * n
+    return g
+
+
+def _code_and_message(fn):
+    with pytest.raises(N.TrkError) as e:
+        fn()
+    return e.value.code, str(e.value)
+
+
+def test_binding_checks_tensors_before_any_launch():
+    """The C ABI sees raw device pointers, so the binding checks what a tensor
+    can tell: dtype, shape, size, layout and device, in that order (a CPU
+    tensor here is never on the GPU, so each case checks the first tensor a
+    call hands over, and one that passes the other checks stops at the device)."""
+    g = _fake_geometry()
+    i64, f64 = torch.int64, torch.float64
+    tally, cnt = torch.zeros(10, dtype=i64), torch.zeros(16, dtype=i64)
+    parts = torch.zeros(600, dtype=torch.uint8)
+    cases = [
+        (lambda: g.run_histories(parts[:599], 10, tally=tally, counters=cnt), "bytes, need 600"),
+        (lambda: g.run_histories(parts, 10, tally=tally, counters=cnt), "tensor on cpu"),
+        (lambda: g.run_histories(None, 10, tally=torch.zeros(9, dtype=i64), counters=cnt), "need 80"),
+        (lambda: g.run_histories(None, 10, tally=tally.double(), counters=cnt), "dtype"),
+        (lambda: N.sync_status(cnt[:8]), "need 128"),
+        (lambda: g.tally_read(torch.zeros(5, dtype=i64)), "need 80"),
+        (lambda: g.tally_read(tally), "tensor on cpu"),
+        (lambda: g.find_cell(torch.zeros(30, dtype=f64)), "expected (n, 3)"),
+        (lambda: g.find_cell(torch.zeros(10, 3, dtype=torch.float32)), "dtype"),
+        (lambda: g.distance_to_surface(torch.zeros(4, 2, dtype=f64), torch.zeros(4, 3, dtype=f64)), "expected (n, 3)"),
+        (lambda: g.transmission_fwd(torch.zeros(4, 3, dtype=f64), torch.zeros(3, dtype=f64)), "expected (n, 6)"),
+        (lambda: g.transmission_bwd(torch.zeros(4, 6, dtype=torch.float32), torch.zeros(3, dtype=f64), 1.26,
+                                    torch.zeros(4, dtype=f64)), "dtype"),
+        (lambda: g.source_init(10, out=torch.zeros(100, dtype=torch.uint8)), "need 600"),
+        (lambda: N.sync_status(torch.zeros(16, dtype=torch.float64)), "dtype"),
+        (lambda: N.transmission_bwd_noalloc(g, torch.zeros(4, 5, dtype=f64), torch.zeros(3, dtype=f64), 1.26,
+                                            torch.zeros(4, dtype=f64), torch.zeros(7, dtype=f64)), "expected (n, 6)"),
+    ]
+    for fn, needle in cases:
+        code, msg = _code_and_message(fn)
+        assert code == -1 and needle in msg, (needle, msg)
+    # a strided view is copied by .contiguous() where the binding owns the copy
+    code, msg = _code_and_message(lambda: g.find_cell(torch.zeros(4, 6, dtype=f64)[:, ::2]))
+    assert "tensor on cpu" in msg
+    # output buffers are written in place, so a strided one is refused
+    code, msg = _code_and_message(lambda: g.run_histories(None, 10, tally=torch.zeros(20, dtype=i64)[::2],
+                                                          counters=cnt))
+    assert "not contiguous" in msg
