@@ -360,6 +360,58 @@ def test_transmission_sigma_gradient_exact():
     assert np.allclose(res["T"], np.exp(-(res["lens"] * sigma).sum(1)), rtol=1e-15)
 
 
+def _inside_cylinder(o, d, cx, cy, r, t_end):
+    """Length of {t in [0, t_end]: (o + t d - c)_xy inside radius r}, from the
+    roots of the quadratic (no walk, no cells)."""
+    qx, qy = o[0] - cx, o[1] - cy
+    a = d[0] * d[0] + d[1] * d[1]
+    c = qx * qx + qy * qy - r * r
+    if a == 0.0:
+        return t_end if c < 0.0 else 0.0
+    b = qx * d[0] + qy * d[1]
+    disc = b * b - a * c
+    if disc <= 0.0:
+        return 0.0
+    s = math.sqrt(disc)
+    return max(0.0, min((-b + s) / a, t_end) - max((-b - s) / a, 0.0))
+
+
+@pytest.mark.parametrize("mode", [O.MODE_RECT, O.MODE_CSG])
+def test_transmission_lengths_by_closed_form(mode):
+    """Per-material lengths of transmission rays through the 17x17 pin lattice
+    in a vacuum box against a computation that never walks the geometry: the
+    box exit by the slab method, and per pin the ray's interval inside each
+    cylinder (fuel = r_fuel chord, clad = r_clad chord - r_fuel chord,
+    moderator = the rest).  A dropped segment, a swapped material or a wrong
+    element frame would each move a length by a chord."""
+    pitch, n, rf, rc, height = 1.26, 17, 0.41, 0.475, 100.0
+    desc = I.config1(bc="vacuum", pitch=pitch, n=n, r_fuel=rf, r_clad=rc, height=height)
+    half = n / 2.0 * pitch
+    lo, hi = np.array([-half, -half, 0.0]), np.array([half, half, height])
+    rng = np.random.default_rng(17)
+    m = 300
+    org = lo + rng.uniform(0.0, 1.0, (m, 3)) * (hi - lo)
+    w = rng.normal(size=(m, 3))
+    w /= np.linalg.norm(w, axis=1)[:, None]
+    w[:10] = np.eye(3)[rng.integers(0, 3, 10)] * rng.choice([-1.0, 1.0], (10, 1))   # axis-parallel rays
+    rays = np.concatenate([org, w], axis=1)
+    sigma = np.array(desc["sigma"])
+    res = _geom(desc, mode).transmission(rays, sigma, grad=False)
+    assert (res["status"] == 2).all()     # every ray leaves through the vacuum box (escaped)
+    centres = [(i - half / pitch + 0.5) * pitch for i in range(n)]
+    for k in range(m):
+        o, d = org[k], w[k]
+        t_exit = min(((hi[a] if d[a] > 0 else lo[a]) - o[a]) / d[a] for a in range(3) if d[a] != 0.0)
+        fuel = clad_out = 0.0
+        for cx in centres:
+            for cy in centres:
+                fuel += _inside_cylinder(o, d, cx, cy, rf, t_exit)
+                clad_out += _inside_cylinder(o, d, cx, cy, rc, t_exit)
+        expect = np.array([fuel, clad_out - fuel, t_exit - clad_out])
+        assert np.allclose(res["lens"][k], expect, rtol=1e-12, atol=1e-11), (k, res["lens"][k], expect)
+    assert np.allclose(res["T"], np.exp(-(res["lens"] * sigma).sum(1)), rtol=1e-15)
+
+
 def test_transmission_geometry_gradient_vs_fd():
     base = dict(n_core=3, n_assm=5, height=20.0)
     r_out = 0.5 * 3 * 5 * 1.26 * 1.2
