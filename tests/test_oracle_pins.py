@@ -315,6 +315,34 @@ def test_source_in_box_and_root():
     assert np.all(src[:, 6] >= 0)
 
 
+def test_source_distributions():
+    """Births are uniform over the root volume (Alg. 2), isotropic, with
+    tau ~ Exp(1): for the r = 170 cylinder of configuration 2 (source box the
+    circumscribed square), r^2/R^2, z/H and the azimuth are U(0, 1) when the
+    rejection step keeps whole points; each direction component is U(-1, 1)
+    (Archimedes); tau = -log(xi) is Exp(1).  A rejection loop that redrew one
+    coordinate, a swapped random stream or a wrong source box fails one of
+    these."""
+    from scipy import stats
+    g = _geom(I.config2(), O.MODE_CSG)
+    src, st = g.source(20000, 7)
+    assert np.all(st == 0)
+    R, H = 170.0, 366.0
+    x, y, z = src[:, 0], src[:, 1], src[:, 2]
+    checks = {
+        "r^2": (x * x + y * y) / (R * R),
+        "z": z / H,
+        "phi": (np.arctan2(y, x) + math.pi) / (2 * math.pi),
+        "u": (src[:, 3] + 1) / 2, "v": (src[:, 4] + 1) / 2, "w": (src[:, 5] + 1) / 2,
+    }
+    for name, vals in checks.items():
+        assert stats.kstest(vals, "uniform").pvalue > 1e-4, name
+    assert stats.kstest(src[:, 6], "expon").pvalue > 1e-4
+    # first_id shifts the stream: ids k..k+n-1 reproduce the tail of a longer run
+    tail, _ = g.source(100, 7, first_id=19900)
+    assert np.array_equal(tail, src[19900:])
+
+
 def test_max_segments_and_escape_status():
     g = _geom(I.config1())
     r = g.run(50, 1, 0.0, max_segments=10)
