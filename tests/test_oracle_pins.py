@@ -440,6 +440,58 @@ def test_transmission_lengths_by_closed_form(mode):
     assert np.allclose(res["T"], np.exp(-(res["lens"] * sigma).sum(1)), rtol=1e-15)
 
 
+@pytest.mark.parametrize("rot30", [False, True])
+@pytest.mark.parametrize("mode", [O.MODE_RECT, O.MODE_CSG])
+def test_transmission_lengths_hex_lattice_by_closed_form(rot30, mode):
+    """Per-material lengths through a rings-3 hex lattice of pins (vacuum):
+    the exit is the first point outside every hexagon (brute force over all
+    elements at the face-plane crossings along the ray; the lattice's outline
+    is not convex) and the fuel length is the sum over elements of the chord
+    through the pin at q a1 + r a2, clipped to that exit."""
+    rings, pitch, r_pin, height = 3, 1.0, 0.4, 5.0
+    desc = I.small_hex(rings=rings, pitch=pitch, r_pin=r_pin, height=height, rot30=rot30)
+    hx = desc["universes"][1]
+    a1, a2, nrm, hp = np.array(hx["a1"]), np.array(hx["a2"]), np.array(hx["normals"]), hx["half_pitch"]
+    centres = np.array([q * a1 + r * a2 for q, r in I.hex_elements(rings)])
+
+    def inside(pt):
+        rel = pt[None, :2] - centres
+        return bool((np.abs(rel @ nrm.T) <= hp).all(1).any()) and 0.0 <= pt[2] <= height
+
+    rng = np.random.default_rng(23)
+    m, rays = 120, []
+    while len(rays) < m:
+        c = centres[rng.integers(len(centres))]
+        xy = c + rng.uniform(-hp, hp, 2)
+        pt = np.array([xy[0], xy[1], rng.uniform(0.0, height)])
+        if not (np.abs((xy - c) @ nrm.T) < hp).all():
+            continue
+        w = rng.normal(size=3)
+        rays.append(np.concatenate([pt, w / np.linalg.norm(w)]))
+    rays = np.array(rays)
+    res = _geom(desc, mode).transmission(rays, np.array(desc["sigma"]), grad=False)
+    assert (res["status"] == 2).all()
+    jmax = 4 * (rings + 2)
+    for k in range(m):
+        o, d = rays[k, :3], rays[k, 3:]
+        t_z = (height - o[2]) / d[2] if d[2] > 0 else (-o[2] / d[2] if d[2] < 0 else np.inf)
+        cuts = [t_z]
+        for nk in nrm:
+            on, dn = nk @ o[:2], nk @ d[:2]
+            if dn != 0.0:
+                cuts += [(j * hp - on) / dn for j in range(-jmax, jmax + 1)]
+        cuts = np.unique([t for t in cuts if 0.0 < t <= t_z])
+        t_exit, prev = t_z, 0.0
+        for t in cuts:
+            if not inside(o + 0.5 * (prev + t) * d):
+                t_exit = prev
+                break
+            prev = t
+        fuel = sum(_inside_cylinder(o, d, c[0], c[1], r_pin, t_exit) for c in centres)
+        expect = np.array([fuel, t_exit - fuel])
+        assert np.allclose(res["lens"][k], expect, rtol=1e-12, atol=1e-11), (k, res["lens"][k], expect)
+
+
 def test_transmission_geometry_gradient_vs_fd():
     base = dict(n_core=3, n_assm=5, height=20.0)
     r_out = 0.5 * 3 * 5 * 1.26 * 1.2
