@@ -417,14 +417,12 @@ def test_transmission_lengths_by_closed_form(mode):
     res = _geom(desc, mode).transmission(rays, sigma, grad=False)
     assert (res["status"] == 2).all()     # every ray leaves through the vacuum box (escaped)
     centres = [(i - half / pitch + 0.5) * pitch for i in range(n)]
+    cxs, cys = (np.array(v).ravel() for v in np.meshgrid(centres, centres))
     for k in range(m):
         o, d = org[k], w[k]
         t_exit = min(((hi[a] if d[a] > 0 else lo[a]) - o[a]) / d[a] for a in range(3) if d[a] != 0.0)
-        fuel = clad_out = 0.0
-        for cx in centres:
-            for cy in centres:
-                fuel += _inside_cylinder(o, d, cx, cy, rf, t_exit)
-                clad_out += _inside_cylinder(o, d, cx, cy, rc, t_exit)
+        fuel = _chords(o, d, cxs, cys, rf, t_exit)
+        clad_out = _chords(o, d, cxs, cys, rc, t_exit)
         expect = np.array([fuel, clad_out - fuel, t_exit - clad_out])
         assert np.allclose(res["lens"][k], expect, rtol=1e-12, atol=1e-11), (k, res["lens"][k], expect)
     assert np.allclose(res["T"], np.exp(-(res["lens"] * sigma).sum(1)), rtol=1e-15)
