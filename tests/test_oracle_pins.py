@@ -537,6 +537,75 @@ def test_transmission_lengths_three_level_core_by_closed_form(mode):
         assert np.allclose(res["lens"][k], expect, rtol=0.0, atol=2e-10), (k, res["lens"][k], expect)
 
 
+def _crossings(o, d, cx, cy, r, t_end):
+    """Parameters t in (0, t_end) where the ray crosses the cylinders
+    (centres cx, cy, radius r), from the closest approach."""
+    qx, qy = o[0] - cx, o[1] - cy
+    a = d[0] * d[0] + d[1] * d[1]
+    if a == 0.0:
+        return np.zeros(0)
+    tc = -(qx * d[0] + qy * d[1]) / a
+    px, py = qx + tc * d[0], qy + tc * d[1]
+    h2 = (r * r - (px * px + py * py)) / a
+    hit = h2 > 0.0
+    s = np.sqrt(h2[hit])
+    t = np.concatenate([tc[hit] - s, tc[hit] + s])
+    return t[(t > 0.0) & (t < t_end)]
+
+
+@pytest.mark.parametrize("mode", [O.MODE_RECT, O.MODE_CSG])
+def test_straight_histories_segment_sequence_three_level_core(mode):
+    """Absolute segment counts and lengths on the benchmark's three-level core.
+    With every sigma = 0 a history is a straight ray from its birth point to
+    the vacuum boundary, and its segments end exactly where the ray crosses a
+    surface that bounds its cell: each pin cylinder (fuel and clad, or guide
+    tube), each pin-pitch plane inside the core square (an assembly's outer
+    face is the core lattice's plane: one crossing), the core square's four
+    planes anywhere inside the cylinder (they also bound the moderator
+    fillers), then the r = 170 cylinder or a z plane.  The segment lengths are
+    the gaps between the sorted crossings; the count is their number + 1."""
+    n_core, n_assm, pitch, R, H = 15, 17, 1.26, 170.0, 366.0
+    desc = I.config2(sigma=[0.0, 0.0, 0.0, 0.0])
+    g = _geom(desc, mode)
+    fill = np.array(desc["universes"][2]["fill"])
+    ca = (np.arange(n_assm) - n_assm / 2.0 + 0.5) * pitch
+    cc = (np.arange(n_core) - n_core / 2.0 + 0.5) * n_assm * pitch
+    pc = (cc[:, None] + ca[None, :]).ravel()
+    gx, gy = np.meshgrid(pc, pc, indexing="xy")
+    ai = np.tile(np.arange(n_assm), n_core)
+    guide = fill[ai[None, :] + n_assm * ai[:, None]] == 1
+    half = n_core * n_assm * pitch / 2.0
+    planes = -half + pitch * np.arange(n_core * n_assm + 1)
+    births, st = g.source(150, 3)
+    assert (st == 0).all()
+    total = 0
+    for pid in range(len(births)):
+        o, d = births[pid, :3], births[pid, 3:6]
+        t_z = (H - o[2]) / d[2] if d[2] > 0 else (-o[2] / d[2] if d[2] < 0 else np.inf)
+        a, b = d[0] ** 2 + d[1] ** 2, o[0] * d[0] + o[1] * d[1]
+        c = o[0] ** 2 + o[1] ** 2 - R * R
+        t_exit = min(t_z, (-b + math.sqrt(b * b - a * c)) / a if a > 0 else np.inf)
+        ts = [_crossings(o, d, gx[~guide], gy[~guide], 0.41, t_exit),
+              _crossings(o, d, gx[~guide], gy[~guide], 0.475, t_exit),
+              _crossings(o, d, gx[guide], gy[guide], 0.56, t_exit)]
+        for ax in (0, 1):
+            if d[ax] == 0.0:
+                continue
+            t = (planes - o[ax]) / d[ax]
+            t = t[(t > 0.0) & (t < t_exit)]
+            other = np.abs(o[1 - ax] + t * d[1 - ax])
+            outer = (np.abs(t * d[ax] + o[ax]) > half - 0.5 * pitch)      # the square's own planes
+            ts.append(t[(other < half) | outer])
+        cuts = np.sort(np.concatenate(ts))
+        expect = np.diff(np.concatenate([[0.0], cuts, [t_exit]]))
+        inst, ln, kind, status = g.trace(pid, 3, 0.3)
+        assert status == O.P_ESCAPED and (kind == 0).all()
+        assert len(ln) == len(expect), (pid, len(ln), len(expect))
+        assert np.allclose(ln, expect, rtol=0.0, atol=2e-10), pid
+        total += len(ln)
+    assert total > 150 * 100      # paths cross hundreds of surfaces on average
+
+
 def test_transmission_geometry_gradient_vs_fd():
     base = dict(n_core=3, n_assm=5, height=20.0)
     r_out = 0.5 * 3 * 5 * 1.26 * 1.2
