@@ -29,10 +29,10 @@
 // something other than itself (brute force over every leaf instance in the
 // global frame, closed-form chords, Cauchy's 4V/S law, track-length volumes,
 // the geometric collision-count law, Philox known-answer vectors, std::log).
-// Segment counts: on the benchmark's three-level core a collision-free
-// history's whole segment sequence is checked against the sorted surface
-// crossings of its straight path.  Parity unpinned: absolute segment counts
-// of histories with collisions and of the hex and batched configurations,
+// Segment counts: on the benchmark's three-level core and on the hex core a
+// collision-free history's whole segment sequence is checked against the
+// surface crossings of its straight path.  Parity unpinned: absolute segment
+// counts of histories with collisions and of the batched configurations,
 // which only self-consistency (rect vs CSG mode, thread-count invariance)
 // checks.
 //

@@ -606,6 +606,91 @@ def test_straight_histories_segment_sequence_three_level_core(mode):
     assert total > 150 * 100      # paths cross hundreds of surfaces on average
 
 
+def _hex_holder(pts, centres, nrm, hp):
+    """Index of the hexagon (centres, face normals, half pitch) whose interior
+    holds each 2-D point, -1 for none: brute force over every hexagon."""
+    proj = np.abs((pts[:, None, :] - centres[None, :, :]) @ nrm.T)
+    inside = (proj < hp).all(-1)
+    return np.where(inside.any(1), inside.argmax(1), -1)
+
+
+def _plane_cuts(o2, d2, nrm, hp, lo, hi, jmax):
+    """t in (lo, hi) where o2 + t d2 crosses a face plane n_k . x = j hp."""
+    out = []
+    for nk in nrm:
+        dn = nk @ d2
+        if dn != 0.0:
+            t = (np.arange(-jmax, jmax + 1) * hp - nk @ o2) / dn
+            out.append(t[(t > lo) & (t < hi)])
+    return np.concatenate(out) if out else np.zeros(0)
+
+
+@pytest.mark.parametrize("mode", [O.MODE_RECT, O.MODE_CSG])
+def test_straight_histories_segment_sequence_hex_core(mode):
+    """The hex core (127 assemblies of 127-element pin lattices turned by 30
+    degrees, pins in rings 0-5, ring 6 a fill clipped by the assembly
+    hexagon) with every sigma = 0: each history's segments against a
+    computation that never walks the geometry.  All candidate crossings
+    (face planes of the core lattice, face planes of the pin lattice of each
+    assembly the path enters, pin cylinders) split the straight path; the
+    identity of each piece (assembly hexagon, pin hexagon within it, inside
+    the pin or not) comes from brute-force classification of its midpoint; a
+    segment ends exactly where that identity changes (a face plane through
+    element centres splits nothing), and the path ends at the first piece
+    outside every assembly or at a z plane."""
+    desc = I.config3(sigma=[0.0] * 5)
+    g = _geom(desc, mode)
+    U = desc["universes"]
+    core, assm = U[-1], U[-2]
+    a1c, a2c, nrmc, hpc = np.array(core["a1"]), np.array(core["a2"]), np.array(core["normals"]), core["half_pitch"]
+    a1p, a2p, nrmp, hpp = np.array(assm["a1"]), np.array(assm["a2"]), np.array(assm["normals"]), assm["half_pitch"]
+    H = core["z"][1]
+    cc = np.array([q * a1c + r * a2c for q, r in I.hex_elements(core["rings"])])
+    pe = np.array([q * a1p + r * a2p for q, r in I.hex_elements(assm["rings"])])
+    has_pin = np.array([f != 3 for f in assm["fill"]])
+    r_pin = desc["surfaces"][0]["coef"][2]
+    births, st = g.source(100, 5)
+    assert (st == 0).all()
+    total = 0
+    for pid in range(len(births)):
+        o, d = births[pid, :3], births[pid, 3:6]
+        o2, d2 = o[:2], d[:2]
+        t_z = (H - o[2]) / d[2] if d[2] > 0 else (-o[2] / d[2] if d[2] < 0 else np.inf)
+        cuts = np.unique(np.concatenate([[0.0], _plane_cuts(o2, d2, nrmc, hpc, 0.0, t_z, 60), [t_z]]))
+        asm = _hex_holder(o2 + 0.5 * (cuts[:-1] + cuts[1:])[:, None] * d2, cc, nrmc, hpc)
+        assert asm[0] >= 0
+        out = np.flatnonzero(asm < 0)
+        t_exit = cuts[out[0]] if out.size else t_z
+        cand = [cuts[(cuts > 0.0) & (cuts < t_exit)]]
+        for A in np.unique(asm[asm >= 0]):
+            span = np.flatnonzero(asm == A)
+            lo, hi = cuts[span.min()], min(cuts[span.max() + 1], t_exit)
+            oa = o2 - cc[A]
+            cand.append(_plane_cuts(oa, d2, nrmp, hpp, lo, hi, 30))
+            cand.append(_crossings(np.array([oa[0], oa[1], 0.0]), d, pe[has_pin, 0], pe[has_pin, 1], r_pin, hi))
+        pts = np.unique(np.concatenate(cand))
+        pts = pts[(pts > 0.0) & (pts < t_exit)]
+        edges = np.concatenate([[0.0], pts, [t_exit]])
+        mid = o2 + 0.5 * (edges[:-1] + edges[1:])[:, None] * d2
+        ia = _hex_holder(mid, cc, nrmc, hpc)
+        assert (ia >= 0).all()
+        local = mid - cc[ia]
+        ip = _hex_holder(local, pe, nrmp, hpp)
+        assert (ip >= 0).all()
+        rr = np.hypot(*(local - pe[ip]).T)
+        inpin = has_pin[ip] & (rr < r_pin)
+        ident = np.stack([ia, ip, inpin.astype(int)], 1)
+        change = np.flatnonzero((ident[1:] != ident[:-1]).any(1))
+        bounds = np.concatenate([[0.0], pts[change], [t_exit]])
+        expect = np.diff(bounds)
+        inst, ln, kind, status = g.trace(pid, 5, 0.3)
+        assert status == O.P_ESCAPED and (kind == 0).all()
+        assert len(ln) == len(expect), (pid, len(ln), len(expect))
+        assert np.allclose(ln, expect, rtol=0.0, atol=1e-10), pid
+        total += len(ln)
+    assert total > 100 * 50
+
+
 def test_transmission_geometry_gradient_vs_fd():
     base = dict(n_core=3, n_assm=5, height=20.0)
     r_out = 0.5 * 3 * 5 * 1.26 * 1.2
