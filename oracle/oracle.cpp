@@ -31,10 +31,10 @@
 // the geometric collision-count law, Philox known-answer vectors, std::log).
 // Segment counts: on the benchmark's three-level core and on the hex core a
 // collision-free history's whole segment sequence is checked against the
-// surface crossings of its straight path.  Parity unpinned: absolute segment
-// counts of histories with collisions and of the batched configurations,
-// which only self-consistency (rect vs CSG mode, thread-count invariance)
-// checks.
+// surface crossings of its straight path, and on batch members against
+// brute-force cell membership along it.  Parity unpinned: absolute segment
+// counts of histories with collisions, which only self-consistency (rect vs
+// CSG mode, thread-count invariance) and the collision-count law check.
 //
 // Built with -O2 -ffp-contract=off so that no multiply-add is fused: every
 // floating-point operation below is one IEEE-754 double operation.

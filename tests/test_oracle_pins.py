@@ -691,6 +691,54 @@ def test_straight_histories_segment_sequence_hex_core(mode):
     assert total > 100 * 50
 
 
+def _members_by_kind():
+    """First configuration-4 members of each (lattice, levels) kind."""
+    seen = {}
+    for i in range(64):
+        d, _ = I.config4_member(i)
+        kind = (any(u["type"] == "hex" for u in d["universes"]), len(d["universes"]))
+        seen.setdefault(kind, i)
+    return sorted(seen.values())
+
+
+@pytest.mark.parametrize("member", _members_by_kind())
+@pytest.mark.parametrize("mode", [O.MODE_RECT, O.MODE_CSG])
+def test_straight_histories_against_brute_force_batch_members(member, mode):
+    """Configuration-4 members (rect and hex lattices, two and three levels)
+    with every sigma = 0: along each straight history, points at 2..98% of
+    every segment lie in that segment's cell instance by brute force over
+    every leaf in the global frame (a missed crossing would put some in
+    another cell), consecutive segments lie in different cells, every
+    segment ends on a bounding surface of its cell (an extra crossing or a
+    wrong length would not), and past the last one the path is outside
+    every cell (vacuum)."""
+    desc, _ = I.config4_member(member)
+    desc = dict(desc, sigma=[0.0] * len(desc["sigma"]))
+    g = _geom(desc, mode)
+    births, st = g.source(40, 11)
+    assert (st == 0).all()
+    fr = np.array([0.02, 0.25, 0.5, 0.75, 0.98])
+    nseg = 0
+    for pid in range(len(births)):
+        o, d = births[pid, :3], births[pid, 3:6]
+        inst, ln, kind, status = g.trace(pid, 11, 0.3)
+        assert status == O.P_ESCAPED and (kind == 0).all() and (ln > 0).all()
+        t0 = np.concatenate([[0.0], np.cumsum(ln)[:-1]])
+        pts = o + (t0[:, None] + fr[None, :] * ln[:, None]).reshape(-1, 1) * d
+        bi, cnt, _, _ = g.find_cell_brute(pts)
+        assert np.array_equal(bi.reshape(-1, len(fr)), np.repeat(inst[:, None], len(fr), 1)), pid
+        assert (cnt == 1).all()
+        assert (inst[1:] != inst[:-1]).all()
+        ends = o + np.cumsum(ln)[:-1, None] * d
+        if len(ends):
+            _, _, near, _ = g.find_cell_brute(ends - 1e-12 * d)
+            assert near.max() < 1e-9, pid
+        past, _, _, _ = g.find_cell_brute((o + (ln.sum() + 1e-7) * d)[None, :])
+        assert past[0] == -1
+        nseg += len(ln)
+    assert nseg > 40 * 3
+
+
 def test_transmission_geometry_gradient_vs_fd():
     base = dict(n_core=3, n_assm=5, height=20.0)
     r_out = 0.5 * 3 * 5 * 1.26 * 1.2
