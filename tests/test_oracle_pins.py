@@ -739,6 +739,82 @@ def test_straight_histories_against_brute_force_batch_members(member, mode):
     assert nseg > 40 * 3
 
 
+def _uniform2(pid, event, tag, k, seed, gid):
+    """Two doubles in (0, 1] from Philox4x32-10 with key (seed_lo32, geometry
+    id) and counter (particle, event, tag, k): xi = ((u64 >> 11) + 1) 2^-53
+    for u64 = (c1 << 32) | c0 and (c3 << 32) | c2."""
+    c = [int(x) for x in O.philox4x32_10([pid, event, tag, k], [seed & 0xffffffff, gid])]
+    return [(((c[hi] << 32 | c[lo]) >> 11) + 1) * 2.0 ** -53 for lo, hi in ((0, 1), (2, 3))]
+
+
+def _marsaglia(pid, event, seed, gid):
+    for k in range(64):
+        xa, xb = _uniform2(pid, event, 1, k, seed, gid)
+        u, v = 2.0 * xa - 1.0, 2.0 * xb - 1.0
+        s = u * u + v * v
+        if 0.0 < s < 1.0:
+            w = math.sqrt(1.0 - s)
+            return np.array([2.0 * u * w, 2.0 * v * w, 1.0 - 2.0 * s])
+    raise AssertionError("no direction in 64 attempts")
+
+
+@pytest.mark.parametrize("mode", [O.MODE_RECT, O.MODE_CSG])
+def test_histories_with_collisions_follow_the_flight_rules(mode):
+    """Whole histories of configuration 1 (reflecting box, three materials,
+    absorption 0.3) re-derived from the flight rules of Alg. 2 without the
+    oracle's walk: from the birth state, each segment's material is its
+    instance mod 3 (elements hold fuel, clad, moderator in that order); a
+    collision flight is exactly tau / Sigma and a crossing is shorter; tau
+    loses Sigma l at each crossing; at the e-th collision the absorption
+    test, the new tau and the Marsaglia direction come from the Philox
+    counters (pid, e, 2, 0) and (pid, e, 1, k); a crossing that ends on a
+    box face reverses that component.  Along the path rebuilt this way,
+    points at 2..98% of every segment lie in the segment's instance by
+    brute force over every leaf, and crossings end on a bounding surface."""
+    desc = I.config1()
+    g = _geom(desc, mode)
+    sigma = np.array(desc["sigma"])
+    seed, gid, pa = 13, desc["geometry_id"], 0.3
+    half, height = 17 * 1.26 / 2.0, 100.0
+    births, st = g.source(120, seed)
+    fr = np.array([0.02, 0.25, 0.5, 0.75, 0.98])
+    ncoll = 0
+    for pid in range(len(births)):
+        r, w, tau = births[pid, :3].copy(), births[pid, 3:6].copy(), births[pid, 6]
+        inst, ln, kind, status = g.trace(pid, seed, pa)
+        assert status == O.P_ABSORBED
+        pts = []
+        event = 0
+        for k in range(len(ln)):
+            sig = sigma[inst[k] % 3]
+            dc = tau / sig
+            pts.append(r + (fr * ln[k])[:, None] * w)
+            end = r + ln[k] * w
+            if kind[k] == 1:
+                assert abs(ln[k] - dc) <= 1e-12 * dc, (pid, k)
+                event += 1
+                ncoll += 1
+                xa, xt = _uniform2(pid, event, 2, 0, seed, gid)
+                if xa < pa:
+                    assert k == len(ln) - 1, (pid, k)
+                    break
+                w = _marsaglia(pid, event, seed, gid)
+                tau = -math.log(xt)
+            else:
+                assert kind[k] == 0 and ln[k] < dc * (1 + 1e-12), (pid, k)
+                tau = tau - sig * ln[k]
+                _, _, near, _ = g.find_cell_brute((end - 1e-12 * w)[None, :])
+                assert near[0] < 1e-9, (pid, k)
+                for ax, lim in ((0, half), (1, half), (2, height)):
+                    lo_face = 0.0 if ax == 2 else -lim
+                    if abs(end[ax] - lim) < 1e-9 or abs(end[ax] - lo_face) < 1e-9:
+                        w[ax] = -w[ax]
+            r = end
+        bi, cnt, _, _ = g.find_cell_brute(np.concatenate(pts))
+        assert np.array_equal(bi.reshape(-1, len(fr)), np.repeat(inst[:, None], len(fr), 1)), pid
+    assert ncoll > 120 * 2
+
+
 def test_transmission_geometry_gradient_vs_fd():
     base = dict(n_core=3, n_assm=5, height=20.0)
     r_out = 0.5 * 3 * 5 * 1.26 * 1.2
