@@ -758,35 +758,71 @@ def _marsaglia(pid, event, seed, gid):
     raise AssertionError("no direction in 64 attempts")
 
 
+def _leaf_materials(desc):
+    """Material of every leaf cell instance in the tally numbering: a
+    universe's cells in order (a daughter contributes all of its instances in
+    place), rect elements i fastest, then j, then k, hex elements in rows
+    r = -R..R with q ascending."""
+    U = desc["universes"]
+
+    def walk(u):
+        un = U[u]
+        if un["type"] == "csg":
+            out = []
+            for c in un["cells"]:
+                out += [c["material"]] if "material" in c else walk(c["fill"])
+            return out
+        return [m for f in un["fill"] for m in walk(f)]
+    return np.array(walk(desc["root"]))
+
+
+def _box_reflect(half, height):
+    def reflect(end, w):
+        for ax, lo, hi in ((0, -half, half), (1, -half, half), (2, 0.0, height)):
+            if abs(end[ax] - hi) < 1e-9 or abs(end[ax] - lo) < 1e-9:
+                w[ax] = -w[ax]
+    return reflect
+
+
+FLIGHT_CASES = {
+    "config1_reflecting": (lambda: I.config1(), 0.3, 120, _box_reflect(17 * 1.26 / 2.0, 100.0)),
+    "three_level_core": (lambda: I.small_core(), 0.25, 80, None),
+    "config3_hex_core": (lambda: I.config3(), 0.25, 25, None),
+}
+
+
+@pytest.mark.parametrize("case", list(FLIGHT_CASES))
 @pytest.mark.parametrize("mode", [O.MODE_RECT, O.MODE_CSG])
-def test_histories_with_collisions_follow_the_flight_rules(mode):
-    """Whole histories of configuration 1 (reflecting box, three materials,
-    absorption 0.3) re-derived from the flight rules of Alg. 2 without the
-    oracle's walk: from the birth state, each segment's material is its
-    instance mod 3 (elements hold fuel, clad, moderator in that order); a
-    collision flight is exactly tau / Sigma and a crossing is shorter; tau
-    loses Sigma l at each crossing; at the e-th collision the absorption
-    test, the new tau and the Marsaglia direction come from the Philox
-    counters (pid, e, 2, 0) and (pid, e, 1, k); a crossing that ends on a
+def test_histories_with_collisions_follow_the_flight_rules(case, mode):
+    """Whole histories re-derived from the flight rules of Alg. 2 without the
+    oracle's walk: from the birth state, each segment's material comes from
+    its instance (numbering rebuilt here from the description); a collision
+    flight is exactly tau / Sigma and a crossing is shorter; tau loses
+    Sigma l at each crossing; at the e-th collision the absorption test, the
+    new tau and the Marsaglia direction come from the Philox counters
+    (pid, e, 2, 0) and (pid, e, 1, k); a crossing that ends on a reflecting
     box face reverses that component.  Along the path rebuilt this way,
-    points at 2..98% of every segment lie in the segment's instance by
-    brute force over every leaf, and crossings end on a bounding surface."""
-    desc = I.config1()
+    points at 2..98% of every segment lie in the segment's instance by brute
+    force over every leaf, crossings end on a bounding surface, and an
+    escaping history's path then leaves every cell."""
+    make, pa, n, reflect = FLIGHT_CASES[case]
+    desc = make()
     g = _geom(desc, mode)
     sigma = np.array(desc["sigma"])
-    seed, gid, pa = 13, desc["geometry_id"], 0.3
-    half, height = 17 * 1.26 / 2.0, 100.0
-    births, st = g.source(120, seed)
+    mat = _leaf_materials(desc)
+    assert len(mat) == g.n_inst
+    seed, gid = 13, desc["geometry_id"]
+    births, st = g.source(n, seed)
     fr = np.array([0.02, 0.25, 0.5, 0.75, 0.98])
     ncoll = 0
     for pid in range(len(births)):
         r, w, tau = births[pid, :3].copy(), births[pid, 3:6].copy(), births[pid, 6]
         inst, ln, kind, status = g.trace(pid, seed, pa)
-        assert status == O.P_ABSORBED
-        pts = []
+        assert status in (O.P_ABSORBED, O.P_ESCAPED)
+        pts, ends, past = [], [], None
         event = 0
         for k in range(len(ln)):
-            sig = sigma[inst[k] % 3]
+            sig = sigma[mat[inst[k]]]
             dc = tau / sig
             pts.append(r + (fr * ln[k])[:, None] * w)
             end = r + ln[k] * w
@@ -796,23 +832,30 @@ def test_histories_with_collisions_follow_the_flight_rules(mode):
                 ncoll += 1
                 xa, xt = _uniform2(pid, event, 2, 0, seed, gid)
                 if xa < pa:
-                    assert k == len(ln) - 1, (pid, k)
+                    assert k == len(ln) - 1 and status == O.P_ABSORBED, (pid, k)
                     break
                 w = _marsaglia(pid, event, seed, gid)
                 tau = -math.log(xt)
             else:
                 assert kind[k] == 0 and ln[k] < dc * (1 + 1e-12), (pid, k)
                 tau = tau - sig * ln[k]
-                _, _, near, _ = g.find_cell_brute((end - 1e-12 * w)[None, :])
-                assert near[0] < 1e-9, (pid, k)
-                for ax, lim in ((0, half), (1, half), (2, height)):
-                    lo_face = 0.0 if ax == 2 else -lim
-                    if abs(end[ax] - lim) < 1e-9 or abs(end[ax] - lo_face) < 1e-9:
-                        w[ax] = -w[ax]
+                ends.append(end - 1e-12 * w)
+                if k == len(ln) - 1:
+                    assert status == O.P_ESCAPED
+                    past = end + 1e-7 * w
+                elif reflect is not None:
+                    reflect(end, w)
             r = end
-        bi, cnt, _, _ = g.find_cell_brute(np.concatenate(pts))
-        assert np.array_equal(bi.reshape(-1, len(fr)), np.repeat(inst[:, None], len(fr), 1)), pid
-    assert ncoll > 120 * 2
+        # one brute-force pass per history: points along the segments, just
+        # before each crossing, and past the exit
+        q = np.concatenate(pts + [np.array(ends).reshape(-1, 3), np.zeros((0, 3)) if past is None else past[None, :]])
+        bi, cnt, near, _ = g.find_cell_brute(q)
+        m = len(inst) * len(fr)
+        assert np.array_equal(bi[:m].reshape(-1, len(fr)), np.repeat(inst[:, None], len(fr), 1)), (pid, case)
+        assert (near[m:m + len(ends)] < 1e-9).all(), pid
+        if past is not None:
+            assert bi[-1] == -1
+    assert ncoll > n
 
 
 def test_transmission_geometry_gradient_vs_fd():
