@@ -997,6 +997,37 @@ def test_power_bank_size_matches_estimate():
     assert 0.3 < k.mean() < 2.4
 
 
+@pytest.mark.parametrize("mode", [O.MODE_RECT, O.MODE_CSG])
+def test_power_first_cycle_exact(mode):
+    """Cycle 0 of Alg. 1's iteration re-derived history by history: its
+    particles are the source's (ids 0..n-1), each history that ends in an
+    absorption at its e-th collision in a material with yield nu > 0 banks
+    min(8, floor(nu / 1 + xi)) sites (xi from Philox counter (pid, e, 3, 0))
+    and adds llrint(nu 2^32) to the cycle's production; k_0 is that integer
+    sum times 2^-32 over n."""
+    nu = (2.4, 0.0, 1.3, 0.0)
+    desc = I.with_nu(I.small_core(), nu)
+    g = _geom(desc, mode)
+    n, seed, pa = 400, 3, 0.25
+    r = g.power(n, seed, pa, 1, 2)
+    assert r["ok"]
+    mat = _leaf_materials(desc)
+    sites, prod = 0, 0
+    for pid in range(n):
+        inst, ln, kind, status = g.trace(pid, seed, pa)
+        if status != O.P_ABSORBED:
+            continue
+        m = mat[inst[-1]]
+        if nu[m] > 0.0:
+            e = int((kind == 1).sum())
+            xf, _ = _uniform2(pid, e, 3, 0, seed, desc["geometry_id"])
+            sites += min(8, int(math.floor(nu[m] / 1.0 + xf)))
+            prod += int(np.rint(nu[m] * 4294967296.0))
+    assert r["bank"][0] == sites
+    assert r["k"][0] == (float(prod) * 2.0 ** -32) / n
+    assert sites > n // 2
+
+
 def test_power_deterministic_and_sharded_threads():
     d = I.with_nu(I.config1(), (2.0, 0.0, 0.0))
     a = _geom(d).power(3000, 3, 0.3, 1, 3, threads=1)
