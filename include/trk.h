@@ -103,7 +103,9 @@ typedef struct {
     int max_rounds;         /* event mode: round limit per warp, 0 = from max_segments; past it the
                                kernel stops and reports TRK_E_TIMEOUT in counters[TRK_K_STATUS] */
     uint64_t seed;          /* low 32 bits key the Philox stream with the geometry id */
-    uint64_t first_id;      /* particle id of element 0 (ids key the random numbers) */
+    uint64_t first_id;      /* particle id of element 0 (ids key the random numbers; an id enters the
+                               Philox counter as one 32-bit word, so ids are taken modulo 2^32 and
+                               first_id + n <= 2^32 keeps every particle's stream distinct) */
     uint64_t max_segments;  /* per-particle segment cap (0 = 1e6) */
     double p_absorb;        /* absorption probability per collision */
     double max_path;        /* per-history path cutoff in cm (<= 0 or inf = none) */
@@ -197,7 +199,7 @@ trk_status geometry_mesh_bins(trk_geom_t g, int64_t* bins);
  *   Position uniform over the description's source box, rejected until it
  *   lies in a root cell; direction by Marsaglia's method; tau = -log(xi).
  *   Random numbers: Philox4x32-10, key (seed_lo32, geometry id), counter
- *   (first_id + i, event 0, tag, attempt).
+ *   ((first_id + i) mod 2^32, event 0, tag, attempt).
  *   dev_particles  caller buffer of *particle_bytes bytes (8-byte aligned),
  *                  NULL to query the size.  Layout (structure of arrays,
  *                  n entries each): double x,y,z,u,v,w,tau; int32 status.
