@@ -858,6 +858,83 @@ def test_histories_with_collisions_follow_the_flight_rules(case, mode):
     assert ncoll > n
 
 
+def _chord_end_rates(o, d, cx, cy, r, t_end, pitch):
+    """For cylinders (centres cx, cy, radius r) the sums over the chord ends
+    inside (0, t_end) of dt_end/dr and dt_end/dpitch, signed so that they add
+    up to d(length inside)/dtheta, with the centres at k pitch.  An end at
+    t = tc -+ s (s the half chord in t, P the closest-approach vector, w the
+    xy direction, a = |w|^2) moves by -+ (r/a)/s with r, and by
+    (w.c -+ P.c/s) / (a pitch) with the pitch; the entering end counts with
+    a minus sign.  Ends at 0 or t_end (fixed boundaries) do not move."""
+    qx, qy = o[0] - cx, o[1] - cy
+    wx, wy = d[0], d[1]
+    a = wx * wx + wy * wy
+    tc = -(qx * wx + qy * wy) / a
+    px, py = qx + tc * wx, qy + tc * wy
+    h2 = (r * r - (px * px + py * py)) / a
+    hit = h2 > 0.0
+    s = np.sqrt(np.where(hit, h2, 1.0))
+    t1, t2 = tc - s, tc + s
+    wc = (wx * cx + wy * cy) / a
+    pc = (px * cx + py * cy) / (a * s)
+    dr = dp = 0.0
+    inner = hit & (t1 > 0.0) & (t1 < t_end)        # entering end inside the path
+    outer = hit & (t2 > 0.0) & (t2 < t_end)        # leaving end inside the path
+    dr += ((r / a) / s)[inner].sum() + ((r / a) / s)[outer].sum()
+    dp += (-(wc - pc) / pitch)[inner].sum() + ((wc + pc) / pitch)[outer].sum()
+    return dr, dp, float(np.min(s[hit & (inner | outer)], initial=np.inf))
+
+
+def test_transmission_gradient_by_closed_form():
+    """The analytic transmission gradient (reading c19) against the
+    derivative of the closed-form chords on the reduced three-level core:
+    per material, d l / d r_j is the sum over moving chord ends of (r/a)/s
+    (fuel gains what clad loses, guide interior what moderator loses), and
+    d l / d pitch moves every pin centre c = k pitch; the outer cylinder and
+    the z planes are fixed, and the core-square planes separate moderator
+    from moderator.  dT/dtheta = -T sum_m sigma_m d l_m / d theta."""
+    pitch, n_core, n_assm, height = 1.26, 3, 5, 20.0
+    r_out = 0.5 * n_core * n_assm * pitch * 1.2
+    sigma = np.array([0.9, 0.4, 0.2, 0.6])
+    desc = I.small_core(height=height, r_outer=r_out, sigma=sigma)
+    rays = I.boundary_rays(300, r_outer=r_out, height=height, seed=8).packed()
+    res = _geom(desc).transmission(rays, sigma, pitch=pitch)
+    fill = np.array(desc["universes"][2]["fill"])
+    ca = (np.arange(n_assm) - n_assm / 2.0 + 0.5) * pitch
+    cc = (np.arange(n_core) - n_core / 2.0 + 0.5) * n_assm * pitch
+    pc = (cc[:, None] + ca[None, :]).ravel()
+    gx, gy = np.meshgrid(pc, pc, indexing="xy")
+    ai = np.tile(np.arange(n_assm), n_core)
+    guide = fill[ai[None, :] + n_assm * ai[:, None]] == 1
+    checked = 0
+    for k in range(len(rays)):
+        o, d = rays[k, :3], rays[k, 3:]
+        if d[0] * d[0] + d[1] * d[1] == 0.0:
+            continue
+        t_z = (height - o[2]) / d[2] if d[2] > 0 else (-o[2] / d[2] if d[2] < 0 else np.inf)
+        a = d[0] ** 2 + d[1] ** 2
+        b = o[0] * d[0] + o[1] * d[1]
+        t_exit = min(t_z, (-b + math.sqrt(b * b - a * (o[0] ** 2 + o[1] ** 2 - r_out ** 2))) / a)
+        drf, dpf, sf = _chord_end_rates(o, d, gx[~guide], gy[~guide], 0.41, t_exit, pitch)
+        drc, dpc, sc = _chord_end_rates(o, d, gx[~guide], gy[~guide], 0.475, t_exit, pitch)
+        drg, dpg, sg = _chord_end_rates(o, d, gx[guide], gy[guide], 0.56, t_exit, pitch)
+        if min(sf, sc, sg) < 1e-3:
+            continue                      # near-tangent chords: the rates grow like 1/s
+        # d l_m / d theta for theta = (r_fuel, r_clad, r_guide, pitch); materials 0 fuel, 1 clad, 2 moderator, 3 guide
+        dl = np.array([[drf, 0.0, 0.0, dpf],
+                       [-drf, drc, 0.0, dpc - dpf],
+                       [0.0, -drc, -drg, -dpc - dpg],
+                       [0.0, 0.0, drg, dpg]])
+        expect = -res["T"][k] * (sigma @ dl)
+        got = res["dT"][k, 4:]
+        # rounding: relative to the terms summed, plus 1e-12 T for the core-square planes, whose
+        # moderator-to-moderator crossings cancel in the oracle's per-crossing sum up to rounding
+        scale = res["T"][k] * (np.abs(sigma)[:, None] * np.abs(dl)).sum(0)
+        assert np.all(np.abs(got - expect) <= 1e-10 * scale + 1e-12 * res["T"][k]), (k, got, expect)
+        checked += 1
+    assert checked > 200
+
+
 def test_transmission_geometry_gradient_vs_fd():
     base = dict(n_core=3, n_assm=5, height=20.0)
     r_out = 0.5 * 3 * 5 * 1.26 * 1.2
