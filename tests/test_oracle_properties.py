@@ -9,8 +9,6 @@ materials 0, 1, 2 inside them and 3 outside.  Properties:
     every pin, clipped to the box exit (vacuum box);
   - the rect and CSG modes give identical histories.
 """
-import math
-
 import numpy as np
 import pytest
 
