@@ -279,6 +279,32 @@ def test_collision_count_geometric_and_path_exponential():
     assert stats.kstest(np.array(path), "expon", args=(0, 1 / (pa * sig))).pvalue > 1e-4
 
 
+@pytest.mark.parametrize("mode", [O.MODE_RECT, O.MODE_CSG])
+def test_counting_build_is_the_same_arithmetic(mode):
+    """The operation count behind the benchmark's roofline comes from the
+    oracle compiled on a counting scalar type: its histories must equal the
+    plain build's bit for bit, its counts must add up over disjoint particle
+    ranges, and they must cover what every segment needs at least (the
+    collision distance tau / Sigma: one division; the move r + l Omega:
+    three multiplications and three additions)."""
+    desc = I.to_json(I.small_core())
+    plain = O.Geometry(desc, mode).run(300, 5, 0.25)
+    gc = O.Geometry(desc, mode, counting=True)
+    gc.flop_counts(reset=True)
+    cnt = gc.run(300, 5, 0.25)
+    whole = gc.flop_counts()
+    assert np.array_equal(cnt["hash"], plain["hash"]) and np.array_equal(cnt["tally"], plain["tally"])
+    gc.flop_counts(reset=True)
+    gc.run(100, 5, 0.25)
+    part = gc.flop_counts()
+    gc.flop_counts(reset=True)
+    gc.run(200, 5, 0.25, first_id=100)
+    rest = gc.flop_counts()
+    assert all(part[k] + rest[k] == whole[k] for k in whole)
+    seg = int(plain["counters"][O.K_SEGMENTS])
+    assert whole["div"] >= seg and whole["mul"] >= 3 * seg and whole["add"] >= 3 * seg
+
+
 def test_rect_and_csg_modes_identical():
     for desc in (I.config1(), I.small_core(), I.random_tiny(3)):
         ra = _geom(desc, O.MODE_RECT).run(1500, 1, 0.3)
