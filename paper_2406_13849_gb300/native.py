@@ -370,16 +370,18 @@ class Batch:
         self.lib = geoms[0].lib
         self.geoms = list(geoms)
         self.counts = [int(c) for c in counts]
+        self.particles = list(particles)
+        if len(self.particles) != len(self.geoms) or len(self.counts) != len(self.geoms):
+            raise TrkError(-1, "Batch: one particle buffer and one count per geometry")
+        if any(g.lib is not self.lib for g in self.geoms):
+            raise TrkError(-1, "Batch: every geometry must come from the same library build (exact or fast)")
+        for k, (g, p, c) in enumerate(zip(self.geoms, self.particles, self.counts)):
+            _need(p, f"Batch particles[{k}]", g.device, g.particle_bytes(c) if c > 0 else 0)
         dev = geoms[0].device
         self.tallies = [torch.zeros(g.n_inst, dtype=torch.int64, device=dev) for g in geoms]
         self.counters = torch.zeros(len(geoms) * NCOUNTERS, dtype=torch.int64, device=dev)
         self.records = [torch.zeros(2 * max(c, 1), dtype=torch.int64, device=dev) for c in self.counts] \
             if records else None
-        self.particles = list(particles)
-        if len(self.particles) != len(self.geoms) or len(self.counts) != len(self.geoms):
-            raise TrkError(-1, "Batch: one particle buffer and one count per geometry")
-        for k, (g, p, c) in enumerate(zip(self.geoms, self.particles, self.counts)):
-            _need(p, f"Batch particles[{k}]", g.device, g.particle_bytes(c) if c > 0 else 0)
         n = len(geoms)
         arr = ctypes.c_void_p * n
         hg = arr(*[g.h.value if isinstance(g.h, ctypes.c_void_p) else g.h for g in geoms])

@@ -251,3 +251,15 @@ def test_binding_checks_tensors_before_any_launch():
     code, msg = _code_and_message(lambda: g.run_histories(None, 10, tally=torch.zeros(20, dtype=i64)[::2],
                                                           counters=cnt))
     assert "not contiguous" in msg
+
+
+def test_batch_checks_its_members_before_any_call():
+    fast, exact = _fake_geometry(), _fake_geometry()
+    exact.lib, exact.exact = N.library(True), True
+    parts = torch.zeros(600, dtype=torch.uint8)
+    code, msg = _code_and_message(lambda: N.Batch([fast, exact], [parts, parts], [10, 10]))
+    assert "same library build" in msg
+    code, msg = _code_and_message(lambda: N.Batch([fast, fast], [parts], [10, 10]))
+    assert "one particle buffer" in msg
+    code, msg = _code_and_message(lambda: N.Batch([fast], [parts[:100]], [10]))
+    assert "need 600" in msg
