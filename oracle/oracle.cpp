@@ -246,6 +246,20 @@ static bool nums(const oj::Val* v, std::vector<double>& out) {
     return true;
 }
 
+// A JSON number holding an integer in [lo, hi] (indices, tags, ring counts).
+static bool int_in(const oj::Val* v, double lo, double hi, int& out) {
+    if (!v || v->kind != oj::Val::NUM) return false;
+    const double x = v->num;
+    if (!(x >= lo && x <= hi) || x != std::floor(x)) return false;
+    out = int(x);
+    return true;
+}
+
+static bool finite_all(const std::vector<double>& v) {
+    for (double x : v) if (!std::isfinite(x)) return false;
+    return true;
+}
+
 static long long count_instances(Geometry& g, int u, int depth, std::string& err) {
     if (depth > 16) { err = "universe nesting too deep or cyclic"; return -1; }
     Universe& U = g.univ[u];
@@ -404,8 +418,9 @@ static Geometry* load_geometry(const char* json, size_t len, int mode, std::stri
     std::unique_ptr<Geometry> g(new Geometry);
     g->mode = mode;
     const oj::Val* v;
-    if ((v = doc.get("geometry_id")) && v->kind == oj::Val::NUM) g->gid = int(v->num);
+    if ((v = doc.get("geometry_id")) && !int_in(v, 0, 2147483647.0, g->gid)) { err = "bad geometry_id"; return nullptr; }
     if (!nums(doc.get("sigma"), g->sigma) || g->sigma.empty()) { err = "missing sigma"; return nullptr; }
+    for (double x : g->sigma) if (!(x >= 0.0) || !std::isfinite(x)) { err = "sigma must be finite and >= 0"; return nullptr; }
     g->nu.assign(g->sigma.size(), 0.0);
     if (doc.get("nu")) {
         if (!nums(doc.get("nu"), g->nu) || g->nu.size() != g->sigma.size()) { err = "bad nu"; return nullptr; }
@@ -425,12 +440,13 @@ static Geometry* load_geometry(const char* json, size_t len, int mode, std::stri
         else if (t->str == "p") { s.type = S_P; need = 4; }
         else if (t->str == "cz") { s.type = S_CZ; need = 3; }
         else { err = "unknown surface type " + t->str; return nullptr; }
-        if (cf.size() != need) { err = "wrong coefficient count"; return nullptr; }
+        if (cf.size() != need || !finite_all(cf)) { err = "wrong or non-finite coefficients"; return nullptr; }
         for (size_t i = 0; i < need; ++i) s.c[i] = cf[i];
         s.bc = parse_bc(sv.get("bc"));
         if (s.bc == BC_REFLECT && s.type == S_CZ) { err = "reflecting cylinders are not supported"; return nullptr; }
-        if ((t = sv.get("rparam")) && t->kind == oj::Val::NUM) s.rparam = int(t->num);
-        if ((t = sv.get("pscale")) && t->kind == oj::Val::NUM) s.pscale = int(t->num);
+        // rparam names one of the radius parameters r_0..r_2 of the transmission gradient (-1: none)
+        if ((t = sv.get("rparam")) && !int_in(t, -1, 2, s.rparam)) { err = "bad rparam"; return nullptr; }
+        if ((t = sv.get("pscale")) && !int_in(t, 0, 1, s.pscale)) { err = "bad pscale"; return nullptr; }
         g->surf.push_back(s);
     }
     v = doc.get("universes");
@@ -448,19 +464,20 @@ static Geometry* load_geometry(const char* json, size_t len, int mode, std::stri
                 const oj::Val* ss = cv.get("surfaces");
                 if (!ss || ss->kind != oj::Val::ARR) { err = "cell without surfaces"; return nullptr; }
                 for (auto& pr : ss->arr) {
-                    if (pr.kind != oj::Val::ARR || pr.arr.size() != 2) { err = "bad cell surface"; return nullptr; }
-                    int sid = int(pr.arr[0].num), sn = int(pr.arr[1].num);
-                    if (sid < 0 || sid >= int(g->surf.size()) || (sn != 1 && sn != -1)) { err = "bad cell surface"; return nullptr; }
+                    int sid, sn;
+                    if (pr.kind != oj::Val::ARR || pr.arr.size() != 2 || !int_in(&pr.arr[0], 0, double(g->surf.size()) - 1, sid) ||
+                        !int_in(&pr.arr[1], -1, 1, sn) || sn == 0) { err = "bad cell surface"; return nullptr; }
                     c.surf.push_back(sid); c.sense.push_back(sn);
                 }
                 const oj::Val* m = cv.get("material");
                 const oj::Val* f = cv.get("fill");
-                if (m && m->kind == oj::Val::NUM) c.material = int(m->num);
-                else if (f && f->kind == oj::Val::NUM) {
-                    c.daughter = int(f->num);
+                if (m && m->kind == oj::Val::NUM) {
+                    if (!int_in(m, 0, double(g->sigma.size()) - 1, c.material)) { err = "bad material"; return nullptr; }
+                } else if (f && f->kind == oj::Val::NUM) {
+                    if (!int_in(f, 0, 2147483647.0, c.daughter)) { err = "bad cell fill"; return nullptr; }
                     std::vector<double> tr;
                     if (nums(cv.get("translation"), tr)) {
-                        if (tr.size() != 3) { err = "bad translation"; return nullptr; }
+                        if (tr.size() != 3 || !finite_all(tr)) { err = "bad translation"; return nullptr; }
                         for (int d = 0; d < 3; ++d) c.tr[d] = tr[d];
                     }
                 } else { err = "cell needs material or fill"; return nullptr; }
@@ -472,43 +489,53 @@ static Geometry* load_geometry(const char* json, size_t len, int mode, std::stri
             if (!gr || gr->kind != oj::Val::ARR || gr->arr.size() != 3) { err = "rect needs 3 grids"; return nullptr; }
             size_t ne = 1;
             for (int d = 0; d < 3; ++d) {
-                if (!nums(&gr->arr[d], U.grid[d]) || U.grid[d].size() < 2) { err = "bad grid"; return nullptr; }
+                if (!nums(&gr->arr[d], U.grid[d]) || U.grid[d].size() < 2 || !finite_all(U.grid[d])) { err = "bad grid"; return nullptr; }
                 for (size_t i = 1; i < U.grid[d].size(); ++i)
                     if (!(U.grid[d][i] > U.grid[d][i - 1])) { err = "grid not increasing"; return nullptr; }
                 ne *= U.grid[d].size() - 1;
             }
             std::vector<double> fl;
             if (!nums(uv.get("fill"), fl) || fl.size() != ne) { err = "bad rect fill"; return nullptr; }
-            for (double x : fl) U.fill.push_back(int(x));
+            for (double x : fl) {
+                if (!(x >= 0.0 && x < 2147483647.0) || x != std::floor(x)) { err = "bad lattice fill"; return nullptr; }
+                U.fill.push_back(int(x));
+            }
             const oj::Val* b = uv.get("bc");
             if (b && b->kind == oj::Val::ARR && b->arr.size() == 6)
                 for (int i = 0; i < 6; ++i) U.bc[i] = parse_bc(&b->arr[i]);
-            if ((t = uv.get("pscale")) && t->kind == oj::Val::NUM) U.pscale = int(t->num);
+            if ((t = uv.get("pscale")) && !int_in(t, 0, 1, U.pscale)) { err = "bad pscale"; return nullptr; }
         } else if (t->str == "hex") {
             U.type = U_HEX;
             const oj::Val* r = uv.get("rings");
             std::vector<double> a1, a2, zz, fl;
-            if (!r || !nums(uv.get("a1"), a1) || !nums(uv.get("a2"), a2) || !nums(uv.get("z"), zz) ||
-                a1.size() != 2 || a2.size() != 2 || zz.size() != 2) { err = "bad hex lattice"; return nullptr; }
-            U.rings = int(r->num);
+            if (!int_in(r, 0, 64, U.rings) || !nums(uv.get("a1"), a1) || !nums(uv.get("a2"), a2) || !nums(uv.get("z"), zz) ||
+                a1.size() != 2 || a2.size() != 2 || zz.size() != 2 || !finite_all(a1) || !finite_all(a2) ||
+                !finite_all(zz) || !(zz[1] > zz[0]) || !(std::fabs(a1[0] * a2[1] - a2[0] * a1[1]) > 0.0)) {
+                err = "bad hex lattice"; return nullptr;
+            }
             U.a1[0] = a1[0]; U.a1[1] = a1[1]; U.a2[0] = a2[0]; U.a2[1] = a2[1];
             U.z[0] = zz[0]; U.z[1] = zz[1];
             const oj::Val* nv = uv.get("normals");
             if (!nv || nv->kind != oj::Val::ARR || nv->arr.size() != 3) { err = "hex needs 3 normals"; return nullptr; }
             for (int k = 0; k < 3; ++k) {
                 std::vector<double> nk;
-                if (!nums(&nv->arr[k], nk) || nk.size() != 2) { err = "bad hex normal"; return nullptr; }
+                if (!nums(&nv->arr[k], nk) || nk.size() != 2 || !finite_all(nk) || (nk[0] == 0.0 && nk[1] == 0.0)) {
+                    err = "bad hex normal"; return nullptr;
+                }
                 U.nrm[k][0] = nk[0]; U.nrm[k][1] = nk[1];
             }
             const oj::Val* hp = uv.get("half_pitch");
-            if (!hp || hp->kind != oj::Val::NUM) { err = "hex needs half_pitch"; return nullptr; }
+            if (!hp || hp->kind != oj::Val::NUM || !(hp->num > 0.0) || !std::isfinite(hp->num)) { err = "hex needs half_pitch > 0"; return nullptr; }
             U.half_pitch = hp->num;
             for (int rr = -U.rings; rr <= U.rings; ++rr)
                 for (int q = std::max(-U.rings, -U.rings - rr); q <= std::min(U.rings, U.rings - rr); ++q) {
                     U.hq.push_back(q); U.hr.push_back(rr);
                 }
             if (!nums(uv.get("fill"), fl) || fl.size() != U.hq.size()) { err = "bad hex fill"; return nullptr; }
-            for (double x : fl) U.fill.push_back(int(x));
+            for (double x : fl) {
+                if (!(x >= 0.0 && x < 2147483647.0) || x != std::floor(x)) { err = "bad lattice fill"; return nullptr; }
+                U.fill.push_back(int(x));
+            }
             const oj::Val* b = uv.get("bc");
             if (b && b->kind == oj::Val::ARR && b->arr.size() == 3) {
                 U.bc[0] = parse_bc(&b->arr[0]); U.bc[4] = parse_bc(&b->arr[1]); U.bc[5] = parse_bc(&b->arr[2]);
@@ -517,16 +544,17 @@ static Geometry* load_geometry(const char* json, size_t len, int mode, std::stri
         g->univ.push_back(U);
     }
     v = doc.get("root");
-    if (!v || v->kind != oj::Val::NUM) { err = "missing root"; return nullptr; }
-    g->root = int(v->num);
-    if (g->root < 0 || g->root >= int(g->univ.size())) { err = "bad root"; return nullptr; }
+    if (!int_in(v, 0, double(g->univ.size()) - 1, g->root)) { err = "missing or bad root"; return nullptr; }
     std::vector<double> sb;
-    if (!nums(doc.get("source_box"), sb) || sb.size() != 6) { err = "missing source_box"; return nullptr; }
+    if (!nums(doc.get("source_box"), sb) || sb.size() != 6 || !finite_all(sb) || !(sb[3] > sb[0]) || !(sb[4] > sb[1]) ||
+        !(sb[5] > sb[2])) { err = "missing or empty source_box"; return nullptr; }
     if ((v = doc.get("mesh"))) {
         const oj::Val* mg = v->get("grid");
         if (!mg || mg->kind != oj::Val::ARR || mg->arr.size() != 3) { err = "mesh needs 3 grids"; return nullptr; }
         for (int d = 0; d < 3; ++d) {
-            if (!nums(&mg->arr[size_t(d)], g->mesh.grid[d]) || g->mesh.grid[d].size() < 2) { err = "bad mesh grid"; return nullptr; }
+            if (!nums(&mg->arr[size_t(d)], g->mesh.grid[d]) || g->mesh.grid[d].size() < 2 || !finite_all(g->mesh.grid[d])) {
+                err = "bad mesh grid"; return nullptr;
+            }
             for (size_t i = 1; i < g->mesh.grid[d].size(); ++i)
                 if (!(g->mesh.grid[d][i] > g->mesh.grid[d][i - 1])) { err = "mesh grid not increasing"; return nullptr; }
         }
@@ -535,11 +563,14 @@ static Geometry* load_geometry(const char* json, size_t len, int mode, std::stri
     // references
     for (auto& U : g->univ) {
         for (auto& c : U.cells) {
-            if (c.daughter >= int(g->univ.size()) || (c.material >= int(g->sigma.size()))) { err = "bad cell fill"; return nullptr; }
+            if (c.daughter >= int(g->univ.size()) || c.material >= int(g->sigma.size()) ||
+                (c.material < 0 && c.daughter < 0)) { err = "bad cell fill"; return nullptr; }
         }
         for (int f : U.fill) if (f < 0 || f >= int(g->univ.size())) { err = "bad lattice fill"; return nullptr; }
     }
     if (count_instances(*g, g->root, 0, err) < 0) return nullptr;
+    for (size_t u = 0; u < g->univ.size(); ++u)
+        if (g->univ[u].ninst < 0) { err = "universe " + std::to_string(u) + " is not reachable from the root"; return nullptr; }
     g->max_depth = depth_of(*g, g->root);
     // CSG mode: every array as its pseudo-array.  Rect mode: rect arrays by
     // index (Alg. 5/6/9/10); hex arrays, for which the paper gives no array

@@ -390,6 +390,36 @@ def test_bad_descriptions_rejected():
         O.Geometry("{not json", O.MODE_RECT)
 
 
+def _negative_fill(cell):
+    del cell["material"]
+    cell["fill"] = -2
+
+
+@pytest.mark.parametrize("mutate", [
+    lambda d: d["universes"].append(dict(d["universes"][0])),                 # unreachable universe
+    lambda d: d.update(root=-0.5),                                              # not an integer index
+    lambda d: d["universes"][0]["cells"][0].update(material=-1),
+    lambda d: _negative_fill(d["universes"][0]["cells"][0]),
+    lambda d: d["universes"][0]["cells"][0]["surfaces"][0].__setitem__(0, 0.5),
+    lambda d: d["universes"][0]["cells"][0]["surfaces"][0].__setitem__(1, 0),
+    lambda d: d["surfaces"][0].update(rparam=3),
+    lambda d: d["universes"][1].update(pscale=2),
+    lambda d: d["universes"][1]["fill"].__setitem__(0, 0.5),
+    lambda d: d["universes"][1]["grid"][0].__setitem__(0, -1e999),
+    lambda d: d.update(source_box=[0, 0, 0, 0, 1, 1]),
+    lambda d: d.update(sigma=[0.8, -0.3, 0.1]),
+    lambda d: d.update(geometry_id=1e30),
+])
+def test_descriptions_with_bad_indices_or_numbers_rejected(mutate):
+    """The oracle's reader rejects what the library's builder rejects: a
+    universe the root never reaches, indices that are not integers in
+    range, tags out of range, non-finite or empty geometry."""
+    d = I.config1()
+    mutate(d)
+    with pytest.raises(ValueError):
+        O.Geometry(I.to_json(d).replace("Infinity", "1e999"), O.MODE_RECT)
+
+
 def test_rect_mode_tracks_hex_arrays_as_pseudo_arrays():
     # the rect-mode oracle keeps rect arrays by index and turns hex arrays
     # into pseudo-arrays: on hex geometries (two and three hex levels) it
