@@ -32,12 +32,11 @@
 // Segment counts: on the benchmark's three-level core and on the hex core a
 // collision-free history's whole segment sequence is checked against the
 // surface crossings of its straight path, and on batch members against
-// brute-force cell membership along it; on configuration 1, a reduced
-// three-level core and the hex core, whole histories with collisions (and
-// reflections) are re-derived from the flight rules and the Philox counters.
-// Parity unpinned: absolute segment counts of histories with collisions at
-// the largest sizes, checked through those pieces and self-consistency (rect
-// vs CSG mode, thread-count invariance) only.
+// brute-force cell membership along it; on every configuration, sampled
+// whole histories with collisions (and reflections) are re-derived from the
+// flight rules and the Philox counters.  Pinned only statistically (and by
+// thread-count determinism): the power iteration's cycles after the first,
+// whose births are drawn from the bank.
 //
 // Built with -O2 -ffp-contract=off so that no multiply-add is fused: every
 // floating-point operation below is one IEEE-754 double operation.

@@ -97,6 +97,16 @@ def test_isotropic_directions():
 # find_cell against brute force over every leaf instance
 # ---------------------------------------------------------------------------
 
+def _members_by_kind():
+    """First configuration-4 members of each (lattice, levels) kind."""
+    seen = {}
+    for i in range(64):
+        d, _ = I.config4_member(i)
+        kind = (any(u["type"] == "hex" for u in d["universes"]), len(d["universes"]))
+        seen.setdefault(kind, i)
+    return sorted(seen.values())
+
+
 def _points(desc, n, seed):
     lo = np.array(desc["source_box"][:3])
     hi = np.array(desc["source_box"][3:])
@@ -111,19 +121,23 @@ def _points(desc, n, seed):
     ("hex_rot", I.small_hex(rings=3, rot30=True), (O.MODE_CSG,)),
     ("tiny5", I.random_tiny(5), (O.MODE_RECT, O.MODE_CSG)),
     ("tiny11", I.random_tiny(11), (O.MODE_RECT, O.MODE_CSG)),
-])
+    ("c2", I.config2(), (O.MODE_RECT, O.MODE_CSG)),
+    ("c3", I.config3(), (O.MODE_RECT, O.MODE_CSG)),
+] + [(f"c4m{m}", I.config4_member(m)[0], (O.MODE_RECT, O.MODE_CSG)) for m in _members_by_kind()])
 def test_find_cell_matches_brute_force(name, desc, modes):
-    pts = _points(desc, 3000, 11)
+    # the full-size cores have 191,929 and 27,686 leaves: fewer points there
+    pts = _points(desc, {"c2": 300, "c3": 600}.get(name, 3000), 11)
+    # the leaves evaluated in the global frame are the same in both modes
+    brute, count, near, nleaf = _geom(desc, modes[0]).find_cell_brute(pts)
+    far = near > 1e-9
+    assert far.mean() > 0.99
+    # away from surfaces exactly one leaf instance holds the point
+    assert np.all(count[far & (brute >= 0)] == 1)
     for mode in modes:
         g = _geom(desc, mode)
-        hier = g.find_cell(pts)
-        brute, count, near, nleaf = g.find_cell_brute(pts)
         assert nleaf == g.n_inst
-        far = near > 1e-9
-        assert far.mean() > 0.99
-        # away from surfaces exactly one leaf instance holds the point
-        assert np.all(count[far & (brute >= 0)] == 1)
-        assert np.array_equal(hier[far], brute[far]), name
+        hier = g.find_cell(pts)
+        assert np.array_equal(hier[far], brute[far]), (name, mode)
 
 
 def test_instance_counts():
@@ -747,16 +761,6 @@ def test_straight_histories_segment_sequence_hex_core(mode):
     assert total > 100 * 50
 
 
-def _members_by_kind():
-    """First configuration-4 members of each (lattice, levels) kind."""
-    seen = {}
-    for i in range(64):
-        d, _ = I.config4_member(i)
-        kind = (any(u["type"] == "hex" for u in d["universes"]), len(d["universes"]))
-        seen.setdefault(kind, i)
-    return sorted(seen.values())
-
-
 @pytest.mark.parametrize("member", _members_by_kind())
 @pytest.mark.parametrize("mode", [O.MODE_RECT, O.MODE_CSG])
 def test_straight_histories_against_brute_force_batch_members(member, mode):
@@ -840,11 +844,18 @@ def _box_reflect(half, height):
     return reflect
 
 
+# (geometry, absorption, histories, reflection rule, membership by brute force?)  The full-size
+# benchmark core has 191,929 leaves: there membership comes from the hierarchical find_cell (pinned
+# against brute force on the same geometry) and crossing ends from distance_to_surface (pinned by
+# hand-worked rays), instead of brute force per point.
 FLIGHT_CASES = {
-    "config1_reflecting": (lambda: I.config1(), 0.3, 120, _box_reflect(17 * 1.26 / 2.0, 100.0)),
-    "three_level_core": (lambda: I.small_core(), 0.25, 80, None),
-    "config3_hex_core": (lambda: I.config3(), 0.25, 25, None),
+    "config1_reflecting": (lambda: I.config1(), 0.3, 120, _box_reflect(17 * 1.26 / 2.0, 100.0), True),
+    "three_level_core": (lambda: I.small_core(), 0.25, 80, None, True),
+    "config3_hex_core": (lambda: I.config3(), 0.25, 25, None, True),
+    "config2_full_core": (lambda: I.config2(), 0.25, 400, None, False),
 }
+for _m in _members_by_kind():     # configuration-4 members: rect and hex lattices, two and three levels
+    FLIGHT_CASES[f"config4_member{_m}"] = (lambda _m=_m: I.config4_member(_m)[0], 0.3, 100, None, False)
 
 
 @pytest.mark.parametrize("case", list(FLIGHT_CASES))
@@ -861,7 +872,7 @@ def test_histories_with_collisions_follow_the_flight_rules(case, mode):
     points at 2..98% of every segment lie in the segment's instance by brute
     force over every leaf, crossings end on a bounding surface, and an
     escaping history's path then leaves every cell."""
-    make, pa, n, reflect = FLIGHT_CASES[case]
+    make, pa, n, reflect, brute = FLIGHT_CASES[case]
     desc = make()
     g = _geom(desc, mode)
     sigma = np.array(desc["sigma"])
@@ -895,20 +906,29 @@ def test_histories_with_collisions_follow_the_flight_rules(case, mode):
             else:
                 assert kind[k] == 0 and ln[k] < dc * (1 + 1e-12), (pid, k)
                 tau = tau - sig * ln[k]
-                ends.append(end - 1e-12 * w)
+                ends.append((end - 1e-12 * w, end - 1e-9 * w, w.copy()))
                 if k == len(ln) - 1:
                     assert status == O.P_ESCAPED
                     past = end + 1e-7 * w
                 elif reflect is not None:
                     reflect(end, w)
             r = end
-        # one brute-force pass per history: points along the segments, just
-        # before each crossing, and past the exit
-        q = np.concatenate(pts + [np.array(ends).reshape(-1, 3), np.zeros((0, 3)) if past is None else past[None, :]])
-        bi, cnt, near, _ = g.find_cell_brute(q)
         m = len(inst) * len(fr)
+        if brute:
+            # one brute-force pass per history: points along the segments, just
+            # before each crossing, and past the exit
+            q = np.concatenate(pts + [np.array([e[0] for e in ends]).reshape(-1, 3),
+                                      np.zeros((0, 3)) if past is None else past[None, :]])
+            bi, cnt, near, _ = g.find_cell_brute(q)
+            assert (near[m:m + len(ends)] < 1e-9).all(), pid
+        else:
+            q = np.concatenate(pts + [np.zeros((0, 3)) if past is None else past[None, :]])
+            bi = g.find_cell(q)
+            if ends:
+                dd, _, di = g.distance(np.array([e[1] for e in ends]), np.array([e[2] for e in ends]))
+                assert np.all(np.abs(dd - 1e-9) < 1e-11), pid      # the boundary ahead is the crossing
+                assert np.array_equal(di, inst[kind[:len(inst)] == 0][:len(ends)]), pid
         assert np.array_equal(bi[:m].reshape(-1, len(fr)), np.repeat(inst[:, None], len(fr), 1)), (pid, case)
-        assert (near[m:m + len(ends)] < 1e-9).all(), pid
         if past is not None:
             assert bi[-1] == -1
     assert ncoll > n
