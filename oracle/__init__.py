@@ -85,6 +85,8 @@ def _lib(counting: bool = False):
         lib.orc_run.argtypes = [_P, _LL, _LL, _ULL, _D, _LL, _D, _I, _P, _P, _P, _P, _P, _P]
         lib.orc_trace.restype = _LL
         lib.orc_trace.argtypes = [_P, _LL, _ULL, _D, _LL, _LL, _P, _P, _P, _P]
+        lib.orc_trace_from_site.restype = _LL
+        lib.orc_trace_from_site.argtypes = [_P, _LL, _ULL, _D, _D, _P, _LL, _P, _P, _P, _P]
         lib.orc_find_cell.argtypes = [_P, _LL, _P, _P]
         lib.orc_find_cell_brute.argtypes = [_P, _LL, _P, _P, _P, _P]
         lib.orc_distance.argtypes = [_P, _LL, _P, _P, _P, _P, _P]
@@ -186,6 +188,19 @@ class Geometry:
         st = np.zeros(1, np.int32)
         k = int(self.lib.orc_trace(self.h, pid, seed, p_absorb, max_segments, cap, _ptr(inst), _ptr(ln),
                                    _ptr(kind), _ptr(st)))
+        k = min(k, cap)
+        return inst[:k], ln[:k], kind[:k], int(st[0])
+
+    def trace_from_site(self, pid: int, seed: int, p_absorb: float, knorm: float, site, cap: int = 100_000):
+        """One history born at `site` as the power iteration births its later
+        cycles (direction and tau from the particle's source counters)."""
+        inst = np.zeros(cap, np.int64)
+        ln = np.zeros(cap, np.float64)
+        kind = np.zeros(cap, np.int32)
+        st = np.zeros(1, np.int32)
+        site = np.ascontiguousarray(site, np.float64)
+        k = int(self.lib.orc_trace_from_site(self.h, pid, seed, p_absorb, knorm, _ptr(site), cap, _ptr(inst),
+                                             _ptr(ln), _ptr(kind), _ptr(st)))
         k = min(k, cap)
         return inst[:k], ln[:k], kind[:k], int(st[0])
 

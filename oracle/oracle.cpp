@@ -34,9 +34,9 @@
 // surface crossings of its straight path, and on batch members against
 // brute-force cell membership along it; on every configuration, sampled
 // whole histories with collisions (and reflections) are re-derived from the
-// flight rules and the Philox counters.  Pinned only statistically (and by
-// thread-count determinism): the power iteration's cycles after the first,
-// whose births are drawn from the bank.
+// flight rules and the Philox counters.  The power iteration's first two
+// cycles are rebuilt exactly (bank, site choice, births from the bank);
+// later cycles repeat that step and are pinned statistically.
 //
 // Built with -O2 -ffp-contract=off so that no multiply-add is fused: every
 // floating-point operation below is one IEEE-754 double operation.
@@ -1571,6 +1571,28 @@ long long orc_trace(void* gp, long long pid, unsigned long long seed, double p_a
                                if (k < cap) { inst[k] = i; len[k] = l; kind[k] = kd; }
                                ++k;
                            });
+    if (status) *status = h.status;
+    return k;
+}
+
+// One history born at a given site, the way the power iteration births its
+// later cycles from the bank (a bank of that one site): direction and tau
+// from the particle's source counters, fission sites counted against knorm.
+long long orc_trace_from_site(void* gp, long long pid, unsigned long long seed, double p_absorb, double knorm,
+                              const double* site, long long cap, long long* inst, double* len, int* kind,
+                              int* status) {
+    Geometry* g = static_cast<Geometry*>(gp);
+    RunOpts o;
+    o.p_absorb = p_absorb;
+    std::vector<uint64_t> tally(size_t(g->univ[g->root].ninst), 0);
+    unsigned long long cnt[K_NCOUNTERS] = {0};
+    const std::vector<double> bank(site, site + 3);
+    long long k = 0;
+    HistoryOut h = run_one(*g, uint32_t(pid), uint32_t(seed), o, tally.data(), cnt,
+                           [&](long long i, double l, int kd) {
+                               if (k < cap) { inst[k] = i; len[k] = l; kind[k] = kd; }
+                               ++k;
+                           }, nullptr, &bank, knorm);
     if (status) *status = h.status;
     return k;
 }

@@ -1181,6 +1181,57 @@ def test_power_first_cycle_exact(mode):
     assert sites > n // 2
 
 
+@pytest.mark.parametrize("mode", [O.MODE_RECT, O.MODE_CSG])
+def test_power_second_cycle_exact(mode):
+    """Cycle 1 of the power iteration rebuilt from cycle 0: the bank is the
+    absorption points of cycle 0's fissile absorptions in history order (each
+    point rebuilt here from the birth state, the traced segment lengths and
+    the Marsaglia directions of the collision counters), repeated by its site
+    count; particle i of cycle 1 (id n + i) takes site floor(xi B) with xi
+    from counter (pid, 0, 4, 0), and its own history, traced from that site,
+    banks floor(nu / k_0 + xi) sites.  Bank size and k of cycle 1 must equal
+    the iteration's."""
+    nu = (2.4, 0.0, 1.3, 0.0)
+    desc = I.with_nu(I.small_core(), nu)
+    g = _geom(desc, mode)
+    n, seed, pa = 300, 3, 0.25
+    gid = desc["geometry_id"]
+    r = g.power(n, seed, pa, 1, 2)
+    assert r["ok"]
+    mat = _leaf_materials(desc)
+    births, _ = g.source(n, seed)
+    bank = []
+    for pid in range(n):
+        inst, ln, kind, status = g.trace(pid, seed, pa)
+        if status != O.P_ABSORBED or nu[mat[inst[-1]]] <= 0.0:
+            continue
+        pos, w, e = births[pid, :3].copy(), births[pid, 3:6].copy(), 0
+        for k in range(len(ln)):
+            pos = pos + ln[k] * w
+            if kind[k] == 1:
+                e += 1
+                if k < len(ln) - 1:
+                    w = _marsaglia(pid, e, seed, gid)
+        xf, _ = _uniform2(pid, e, 3, 0, seed, gid)
+        bank += [pos] * min(8, int(math.floor(nu[mat[inst[-1]]] / 1.0 + xf)))
+    assert len(bank) == r["bank"][0]
+    k0, nb = r["k"][0], len(bank)
+    sites = prod = 0
+    for i in range(n):
+        pid = n + i
+        xb, _ = _uniform2(pid, 0, 4, 0, seed, gid)
+        site = bank[min(int(math.floor(xb * nb)), nb - 1)]
+        inst, ln, kind, status = g.trace_from_site(pid, seed, pa, k0, site)
+        if status != O.P_ABSORBED or nu[mat[inst[-1]]] <= 0.0:
+            continue
+        e = int((kind == 1).sum())
+        xf, _ = _uniform2(pid, e, 3, 0, seed, gid)
+        sites += min(8, int(math.floor(nu[mat[inst[-1]]] / k0 + xf)))
+        prod += int(np.rint(nu[mat[inst[-1]]] * 4294967296.0))
+    assert r["bank"][1] == sites
+    assert r["k"][1] == (float(prod) * 2.0 ** -32) / n
+
+
 def test_power_deterministic_and_sharded_threads():
     d = I.with_nu(I.config1(), (2.0, 0.0, 0.0))
     a = _geom(d).power(3000, 3, 0.3, 1, 3, threads=1)
