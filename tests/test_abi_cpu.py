@@ -263,3 +263,45 @@ def test_batch_checks_its_members_before_any_call():
     assert "one particle buffer" in msg
     code, msg = _code_and_message(lambda: N.Batch([fast], [parts[:100]], [10]))
     assert "need 600" in msg
+
+
+def test_every_entry_point_rejects_a_null_handle_on_the_host():
+    """Each entry point that takes a handle or output pointer validates it on
+    the host and returns TRK_E_INVALID (no launch, no device access): the
+    ABI's "calls return a status and never throw" convention, for all of
+    them.  Functions without arguments to validate are listed apart."""
+    lib = N.library()
+    o = N.default_opts()
+    calls = {
+        "geometry_build": (None, 0, None, None, None, None),
+        "geometry_destroy": (None,),
+        "geometry_info": (None, None, None, None, None),
+        "geometry_mesh_bins": (None, None),
+        "source_init": (None, 1, 0, 0, None, None, None),
+        "run_histories_work_bytes": (None, 1, ctypes.byref(o), None),
+        "run_histories": (None, None, 1, None, None, None, None, 0, ctypes.byref(o), None),
+        "power_iteration_work_bytes": (None, 1, ctypes.byref(o), None),
+        "power_iteration": (None, 1, 0, 1, None, None, None, None, None, 0, ctypes.byref(o), None),
+        "tally_read": (None, None, None, 0, None, None),
+        "trk_find_cell": (None, 0, 1, None, None, None),
+        "trk_distance_to_surface": (None, 0, 1, None, None, None, None, None, None),
+        "trk_sync_status": (None, None),
+        "trk_trace": (None, None, 1, 1, None, None, None, None, ctypes.byref(o), None),
+        "transmission_fwd": (None, 0, 1, None, None, None, None, None),
+        "transmission_bwd_work_bytes": (None, 1, None),
+        "transmission_bwd": (None, 0, 1, None, None, 1.26, None, None, None, 0, None),
+        "transmission_bwd_noalloc": (None, 0, 1, None, None, 1.26, None, None, None),
+        "batch_create": (None, 1, None, None, None, None, None, 0, None),
+        "batch_destroy": (None,),
+        "batch_work_bytes": (None, None),
+        "batch_upload": (None, None, 0, 512, None),
+        "run_batched": (None, None, ctypes.byref(o), None),
+        "batch_autotune": (None, None, 0, ctypes.byref(o), None, 1, None, None),
+        "trk_peak_kernel": (0, 1, 1, 0, None, 0, None, None),
+    }
+    no_arguments_to_check = {"trk_default_opts", "trk_last_error", "trk_exact_build"}
+    assert set(calls) | no_arguments_to_check == set(declared_functions())
+    for name, args in calls.items():
+        st = getattr(lib, name)(*args)
+        assert st == -1, (name, st)
+        assert lib.trk_last_error().decode(), name
