@@ -362,8 +362,16 @@ def main() -> None:
         g.tally_read(tally, cnt)          # device -> host, synchronises the stream
     e1.record(stream)
     barrier()
-    e2e_seg = int(cnt.cpu().numpy().view(np.uint64)[0])
-    e2e = {"value": world * e2e_seg / (e0.elapsed_time(e1) / 1e3), "unit": UNIT,
+    e2e_seg = float(cnt.cpu().numpy().view(np.uint64)[0])
+    e2e_ms = e0.elapsed_time(e1)
+    if world > 1:
+        # as for the main value: the slowest rank's time, the segments of all ranks
+        t_local = torch.tensor([e2e_ms, e2e_seg], dtype=torch.float64, device=dev)
+        tmax, tsum = t_local.clone(), t_local.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+        e2e_ms, e2e_seg = float(tmax[0]), float(tsum[1])
+    e2e = {"value": e2e_seg / (e2e_ms / 1e3), "unit": UNIT,
            "h2d_bytes_per_step": int(parts.numel()), "d2h_bytes_per_step": int(g.n_inst * 8 + 8)}
 
     # ---- batched: 64 geometries, FP32-local graph replay vs FP64 launch loop
