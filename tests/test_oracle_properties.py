@@ -8,6 +8,9 @@ materials 0, 1, 2 inside them and 3 outside.  Properties:
   - transmission lengths per material equal closed-form chords through
     every pin, clipped to the box exit (vacuum box);
   - the rect and CSG modes give identical histories.
+Hex lattices (rings 0..3, either orientation) of pins of one cylinder are
+drawn too: find_cell against brute force, and transmission lengths against
+chords clipped at the first exit from the union of hexagons.
 """
 import numpy as np
 import pytest
@@ -109,3 +112,75 @@ def _chords(o, d, cx, cy, r, t_end):
     s = np.sqrt(np.maximum(h2, 0.0))
     seg = np.minimum(tc + s, t_end) - np.maximum(tc - s, 0.0)
     return float(np.where(h2 > 0.0, np.maximum(seg, 0.0), 0.0).sum())
+
+
+@st.composite
+def hex_lattices(draw):
+    rings = draw(st.integers(0, 3))
+    pitch = draw(st.floats(0.5, 2.0))
+    rot30 = draw(st.booleans())
+    r_pin = draw(st.floats(0.1, 0.45)) * pitch
+    off = draw(st.floats(-0.02, 0.02)) * pitch, draw(st.floats(-0.02, 0.02)) * pitch
+    height = draw(st.floats(1.0, 6.0))
+    desc = I.small_hex(rings=rings, pitch=pitch, r_pin=r_pin, height=height, rot30=rot30,
+                       sigma=(draw(st.floats(0.05, 1.5)), draw(st.floats(0.05, 1.5))))
+    desc["surfaces"][0]["coef"][:2] = [off[0], off[1]]
+    return desc, r_pin, off
+
+
+@settings(max_examples=30, deadline=None, derandomize=True, database=None)
+@given(geo=hex_lattices(), seed=st.integers(0, 2**31))
+def test_hex_find_cell_equals_brute_force(geo, seed):
+    desc, _, _ = geo
+    lo, hi = np.array(desc["source_box"][:3]), np.array(desc["source_box"][3:])
+    pts = lo + np.random.default_rng(seed).uniform(size=(400, 3)) * (hi - lo)
+    for mode in (O.MODE_RECT, O.MODE_CSG):
+        g = O.Geometry(I.to_json(desc), mode)
+        bi, cnt, near, _ = g.find_cell_brute(pts)
+        far = near > 1e-9
+        assert np.array_equal(g.find_cell(pts)[far], bi[far])
+        assert (cnt[far] <= 1).all()
+
+
+@settings(max_examples=25, deadline=None, derandomize=True, database=None)
+@given(geo=hex_lattices(), seed=st.integers(0, 2**31))
+def test_hex_transmission_lengths_equal_chords(geo, seed):
+    desc, r_pin, off = geo
+    hx = desc["universes"][1]
+    a1, a2, nrm, hp = np.array(hx["a1"]), np.array(hx["a2"]), np.array(hx["normals"]), hx["half_pitch"]
+    height = hx["z"][1]
+    centres = np.array([q * a1 + r * a2 for q, r in I.hex_elements(hx["rings"])])
+
+    def holder(pts):
+        proj = np.abs((pts[:, None, :] - centres[None, :, :]) @ nrm.T)
+        inside = (proj < hp).all(-1)
+        return np.where(inside.any(1), inside.argmax(1), -1)
+
+    rng = np.random.default_rng(seed)
+    m = 30
+    el = rng.integers(0, len(centres), m)
+    org = np.zeros((m, 3))
+    for k in range(m):
+        while True:       # a point inside the drawn element's hexagon
+            xy = centres[el[k]] + rng.uniform(-hp, hp, 2)
+            if (np.abs((xy - centres[el[k]]) @ nrm.T) < hp).all():
+                break
+        org[k] = [xy[0], xy[1], rng.uniform(0.0, height)]
+    w = rng.normal(size=(m, 3))
+    w /= np.linalg.norm(w, axis=1)[:, None]
+    for mode in (O.MODE_RECT, O.MODE_CSG):
+        res = O.Geometry(I.to_json(desc), mode).transmission(np.concatenate([org, w], 1), desc["sigma"], grad=False)
+        for k in range(m):
+            o, d = org[k], w[k]
+            t_z = (height - o[2]) / d[2] if d[2] > 0 else (-o[2] / d[2] if d[2] < 0 else np.inf)
+            cuts = [t_z]
+            for nk in nrm:
+                dn = nk @ d[:2]
+                if dn != 0.0:
+                    cuts += list((np.arange(-40, 41) * hp - nk @ o[:2]) / dn)
+            cuts = np.unique([t for t in cuts if 0.0 < t <= t_z])
+            mids = np.concatenate([[0.0], cuts[:-1]]) + 0.5 * np.diff(np.concatenate([[0.0], cuts]))
+            out = np.flatnonzero(holder(o[:2] + mids[:, None] * d[:2]) < 0)
+            t_exit = (np.concatenate([[0.0], cuts])[out[0]]) if out.size else t_z
+            fuel = _chords(o, d, centres[:, 0] + off[0], centres[:, 1] + off[1], r_pin, t_exit)
+            assert np.allclose(res["lens"][k], [fuel, t_exit - fuel], rtol=0.0, atol=1e-11), (mode, k)
