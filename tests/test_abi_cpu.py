@@ -305,3 +305,34 @@ def test_every_entry_point_rejects_a_null_handle_on_the_host():
         st = getattr(lib, name)(*args)
         assert st == -1, (name, st)
         assert lib.trk_last_error().decode(), name
+
+
+def test_last_error_is_per_thread():
+    """trk_last_error is thread-local: threads failing at the same time for
+    different reasons each read their own message (ctypes releases the GIL
+    around the calls, so the calls overlap)."""
+    import threading
+    lib = N.library()
+    bad = {"json": ("not json", "JSON"), "root": (None, "root")}
+    d = I.config1()
+    d["root"] = 99
+    bad["root"] = (I.to_json(d), "root")
+    seen, errors = [], []
+
+    def worker(kind):
+        txt, needle = bad[kind]
+        raw = txt.encode()
+        for _ in range(300):
+            nb = ctypes.c_size_t(0)
+            st = lib.geometry_build(raw, len(raw), None, ctypes.byref(nb), None, None)
+            msg = lib.trk_last_error().decode()
+            if st != -2 or needle not in msg:
+                errors.append((kind, st, msg))
+        seen.append(kind)
+
+    threads = [threading.Thread(target=worker, args=(k,)) for k in ("json", "root") * 4]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert len(seen) == 8 and not errors, errors[:3]
