@@ -84,7 +84,8 @@ def _lib(counting: bool = False):
         lib.orc_source.argtypes = [_P, _LL, _LL, _ULL, _P, _P]
         lib.orc_run.argtypes = [_P, _LL, _LL, _ULL, _D, _LL, _D, _I, _P, _P, _P, _P, _P, _P]
         lib.orc_trace.restype = _LL
-        lib.orc_trace.argtypes = [_P, _LL, _ULL, _D, _LL, _LL, _P, _P, _P, _P]
+        lib.orc_trace.argtypes = [_P, _LL, _ULL, _D, _LL, _LL, _P, _P, _P, _P, _P]
+        lib.orc_clearance.argtypes = [_P, _LL, _P, _P, _P, _P]
         lib.orc_trace_from_site.restype = _LL
         lib.orc_trace_from_site.argtypes = [_P, _LL, _ULL, _D, _D, _P, _LL, _P, _P, _P, _P]
         lib.orc_find_cell.argtypes = [_P, _LL, _P, _P]
@@ -181,15 +182,38 @@ class Geometry:
                          _ptr(tally), _ptr(cnt), _ptr(rh), _ptr(rn), _ptr(rs), _ptr(rf))
         return {"tally": tally, "counters": cnt, "hash": rh, "nseg": rn, "status": rs, "final": rf}
 
-    def trace(self, pid: int, seed: int, p_absorb: float, cap: int = 100_000, max_segments: int = 1_000_000):
+    def trace(self, pid: int, seed: int, p_absorb: float, cap: int = 100_000, max_segments: int = 1_000_000,
+              geometry: bool = False):
+        """One history's segments: (leaf instance, length, kind, status), kind
+        0 crossing, 1 collision, 2 cut; with geometry=True also each segment's
+        start position, direction and material cross section, an (n, 7)
+        array."""
         inst = np.zeros(cap, np.int64)
         ln = np.zeros(cap, np.float64)
         kind = np.zeros(cap, np.int32)
         st = np.zeros(1, np.int32)
+        geo = np.zeros((cap, 7), np.float64) if geometry else None
         k = int(self.lib.orc_trace(self.h, pid, seed, p_absorb, max_segments, cap, _ptr(inst), _ptr(ln),
-                                   _ptr(kind), _ptr(st)))
+                                   _ptr(kind), _ptr(st), _ptr(geo)))
         k = min(k, cap)
+        if geometry:
+            return inst[:k], ln[:k], kind[:k], int(st[0]), geo[:k]
         return inst[:k], ln[:k], kind[:k], int(st[0])
+
+    def clearance(self, xyz: np.ndarray, dirs: np.ndarray, lens) -> np.ndarray:
+        """Distances of segments from the geometry's surfaces (global frame):
+        per segment (start xyz, unit direction, length) the smallest distance
+        from the start point to a surface and the smallest to any other
+        surface, the same two at the end point, the tangency |b - r| over the
+        cylinders whose axis is closest to the segment's line inside the
+        segment (inf if none), and the unit normal (sign arbitrary) of the
+        surface nearest to the end point: an (n, 8) array."""
+        xyz = np.ascontiguousarray(xyz, np.float64).reshape(-1, 3)
+        dirs = np.ascontiguousarray(dirs, np.float64).reshape(-1, 3)
+        lens = np.ascontiguousarray(lens, np.float64).reshape(-1)
+        out = np.zeros((len(xyz), 8), np.float64)
+        self.lib.orc_clearance(self.h, len(xyz), _ptr(xyz), _ptr(dirs), _ptr(lens), _ptr(out))
+        return out
 
     def trace_from_site(self, pid: int, seed: int, p_absorb: float, knorm: float, site, cap: int = 100_000):
         """One history born at `site` as the power iteration births its later

@@ -1157,7 +1157,7 @@ static HistoryOut run_one(const Geometry& g, uint32_t pid, uint32_t seed_lo, con
         double ld = dv(len);
         std::memcpy(&lb, &ld, 8);
         out.hash = fnv(fnv(out.hash, uint64_t(inst)), lb);
-        trace(inst, ld, crossing ? (stop_cut ? 2 : 0) : (stop_cut ? 2 : 1));
+        trace(inst, ld, crossing ? (stop_cut ? 2 : 0) : (stop_cut ? 2 : 1), p);
         for (int d = 0; d < 3; ++d) p.r[d] = p.r[d] + len * p.dir[d];
         out.nseg++;
         cnt[K_SEGMENTS]++;
@@ -1404,7 +1404,7 @@ int orc_run(void* gp, long long n, long long first_id, unsigned long long seed, 
         long long lo = n * t / nthreads, hi = n * (t + 1) / nthreads;
         for (long long i = lo; i < hi; ++i) {
             HistoryOut h = run_one(*g, uint32_t(first_id + i), uint32_t(seed), o, tl[size_t(t)].data(),
-                                   cl[size_t(t)].data(), [](long long, double, int) {});
+                                   cl[size_t(t)].data(), [](long long, double, int, const Particle&) {});
             if (rec_hash) rec_hash[i] = h.hash;
             if (rec_nseg) rec_nseg[i] = h.nseg;
             if (rec_status) rec_status[i] = h.status;
@@ -1449,7 +1449,7 @@ int orc_run_mesh(void* gp, long long n, long long first_id, unsigned long long s
         long long lo = n * t / nthreads, hi = n * (t + 1) / nthreads;
         for (long long i = lo; i < hi; ++i)
             run_one(*g, uint32_t(first_id + i), uint32_t(seed), o, tl[size_t(t)].data(), cl[size_t(t)].data(),
-                    [](long long, double, int) {}, ml[size_t(t)].data());
+                    [](long long, double, int, const Particle&) {}, ml[size_t(t)].data());
     };
     if (nthreads == 1) work(0);
     else {
@@ -1507,7 +1507,7 @@ int orc_power(void* gp, long long n, long long first_id, unsigned long long seed
             long long lo = n * t / nthreads, hi = n * (t + 1) / nthreads;
             for (long long i = lo; i < hi; ++i)
                 hist[size_t(i)] = run_one(*g, uint32_t(first_id + (long long)c * n + i), uint32_t(seed), o,
-                                          tl[size_t(t)].data(), cl[size_t(t)].data(), [](long long, double, int) {},
+                                          tl[size_t(t)].data(), cl[size_t(t)].data(), [](long long, double, int, const Particle&) {},
                                           nullptr, src, knorm);
         };
         if (nthreads == 1) work(0);
@@ -1557,8 +1557,12 @@ int orc_mesh_segment(void* gp, const double* r, const double* dir, double len, u
 long long orc_mesh_bins(void* gp) { return static_cast<Geometry*>(gp)->mesh.bins(); }
 
 // Per-segment trace of one history: instance, length, kind (0 cross, 1 collide, 2 cutoff).
+// One history's segments: leaf instance, length and kind (0 crossing, 1
+// collision, 2 cut) per segment and, when `geo` is given, the segment's start
+// position and direction in the global frame and its material's cross
+// section (7 doubles per segment).
 long long orc_trace(void* gp, long long pid, unsigned long long seed, double p_absorb, long long max_segments,
-                    long long cap, long long* inst, double* len, int* kind, int* status) {
+                    long long cap, long long* inst, double* len, int* kind, int* status, double* geo) {
     Geometry* g = static_cast<Geometry*>(gp);
     RunOpts o;
     o.p_absorb = p_absorb;
@@ -1567,8 +1571,17 @@ long long orc_trace(void* gp, long long pid, unsigned long long seed, double p_a
     unsigned long long cnt[K_NCOUNTERS] = {0};
     long long k = 0;
     HistoryOut h = run_one(*g, uint32_t(pid), uint32_t(seed), o, tally.data(), cnt,
-                           [&](long long i, double l, int kd) {
-                               if (k < cap) { inst[k] = i; len[k] = l; kind[k] = kd; }
+                           [&](long long i, double l, int kd, const Particle& p) {
+                               if (k < cap) {
+                                   inst[k] = i; len[k] = l; kind[k] = kd;
+                                   if (geo) {
+                                       for (int d = 0; d < 3; ++d) {
+                                           geo[7 * k + d] = dv(p.r[d]);
+                                           geo[7 * k + 3 + d] = dv(p.dir[d]);
+                                       }
+                                       geo[7 * k + 6] = dv(g->sigma[size_t(p.material)]);
+                                   }
+                               }
                                ++k;
                            });
     if (status) *status = h.status;
@@ -1589,7 +1602,7 @@ long long orc_trace_from_site(void* gp, long long pid, unsigned long long seed, 
     const std::vector<double> bank(site, site + 3);
     long long k = 0;
     HistoryOut h = run_one(*g, uint32_t(pid), uint32_t(seed), o, tally.data(), cnt,
-                           [&](long long i, double l, int kd) {
+                           [&](long long i, double l, int kd, const Particle&) {
                                if (k < cap) { inst[k] = i; len[k] = l; kind[k] = kd; }
                                ++k;
                            }, nullptr, &bank, knorm);
@@ -1663,6 +1676,114 @@ int orc_find_cell_brute(void* gp, long long n, const double* xyz, long long* ins
         if (near) near[i] = cntv ? nd : nd_all;
     }
     return int(leaves.size());
+}
+
+// Clearance of segments from the geometry's surfaces in the global frame,
+// for telling whether a decision was taken close to a surface (test
+// infrastructure: the tracking method itself never calls it).  Every leaf
+// instance's constraint chain is moved into the global frame (as for the
+// brute-force find_cell) and the distinct surfaces are kept.  For segment i
+// (start xyz[3i..], unit direction dir[3i..], length len[i]):
+//   out[8i+0], out[8i+1]  smallest distance from the start point to a
+//                         surface (|f| / |grad f| for planes, |rho - r| for
+//                         cylinders, rho the distance from the axis), and the
+//                         smallest to any other surface
+//   out[8i+2], out[8i+3]  the same at the end point xyz + len * dir
+//   out[8i+4]             tangency: smallest |b - r| over the cylinders whose
+//                         axis is closest to the segment's line (in the xy
+//                         projection) at a point of the segment, b that
+//                         closest distance; +inf when there is none
+//   out[8i+5..7]          the unit normal n of the surface nearest to the
+//                         end point, there (sign arbitrary; 0 when there is
+//                         no surface)
+int orc_clearance(void* gp, long long n, const double* xyz, const double* dir, const double* len, double* out) {
+    Geometry* g = static_cast<Geometry*>(gp);
+    std::vector<GLeaf> leaves;
+    std::vector<GConstraint> chain;
+    double T0[3] = {0, 0, 0};
+    enumerate_leaves(*g, g->root, T0, chain, true, leaves);
+    std::vector<GConstraint> surf;
+    for (auto& L : leaves)
+        for (auto& k : L.cons) surf.push_back(k);
+    auto key_less = [](const GConstraint& a, const GConstraint& b) {
+        if (a.type != b.type) return a.type < b.type;
+        for (int i = 0; i < 4; ++i)
+            if (a.c[i] != b.c[i]) return a.c[i] < b.c[i];
+        return false;
+    };
+    auto key_eq = [](const GConstraint& a, const GConstraint& b) {
+        if (a.type != b.type) return false;
+        for (int i = 0; i < 4; ++i)
+            if (a.c[i] != b.c[i]) return false;
+        return true;
+    };
+    std::sort(surf.begin(), surf.end(), key_less);
+    surf.erase(std::unique(surf.begin(), surf.end(), key_eq), surf.end());
+    // The same physical surface can reach the list more than once with its
+    // global coefficients rounded differently (a plane shared by cells of
+    // different levels): the second distance skips every surface within
+    // 1e-9 (relative to the coefficients' size) of the nearest one.
+    auto same = [](const GConstraint& a, const GConstraint& b) {
+        if (a.type != b.type) return false;
+        for (int i = 0; i < 4; ++i)
+            if (std::fabs(a.c[i] - b.c[i]) > 1e-9 * std::max(1.0, std::fabs(a.c[i]))) return false;
+        return true;
+    };
+    auto two_smallest = [&](const double x[3], double& m1, double& m2, size_t* nearest = nullptr) {
+        m1 = INF; m2 = INF;
+        size_t best = 0;
+        for (size_t i = 0; i < surf.size(); ++i) {
+            double gr;
+            const double d = std::fabs(gc_f(surf[i], x, &gr)) / gr;
+            if (d < m1) { m1 = d; best = i; }
+        }
+        if (surf.empty()) return;
+        if (nearest) *nearest = best;
+        for (size_t i = 0; i < surf.size(); ++i) {
+            if (same(surf[i], surf[best])) continue;
+            double gr;
+            m2 = std::min(m2, std::fabs(gc_f(surf[i], x, &gr)) / gr);
+        }
+    };
+    for (long long i = 0; i < n; ++i) {
+        const double* p = xyz + 3 * i;
+        const double* w = dir + 3 * i;
+        const double L = len[i];
+        const double q[3] = {p[0] + L * w[0], p[1] + L * w[1], p[2] + L * w[2]};
+        double* o6 = out + 8 * i;
+        two_smallest(p, o6[0], o6[1]);
+        size_t ns = surf.size();
+        two_smallest(q, o6[2], o6[3], &ns);
+        o6[5] = o6[6] = o6[7] = 0.0;
+        if (ns < surf.size()) {
+            const GConstraint& k = surf[ns];
+            double nrm[3] = {0.0, 0.0, 0.0};
+            if (k.type <= S_PZ) nrm[k.type] = 1.0;
+            else if (k.type == S_P) {
+                const double nn = std::sqrt(k.c[0] * k.c[0] + k.c[1] * k.c[1] + k.c[2] * k.c[2]);
+                for (int d = 0; d < 3; ++d) nrm[d] = k.c[d] / nn;
+            } else {
+                const double qx = q[0] - k.c[0], qy = q[1] - k.c[1];
+                const double rr = std::sqrt(qx * qx + qy * qy);
+                if (rr > 0.0) { nrm[0] = qx / rr; nrm[1] = qy / rr; }
+            }
+            for (int d = 0; d < 3; ++d) o6[5 + d] = nrm[d];
+        }
+        double tang = INF;
+        const double a = w[0] * w[0] + w[1] * w[1];
+        if (a > 0.0) {
+            for (auto& k : surf) {
+                if (k.type != S_CZ) continue;
+                const double qx = p[0] - k.c[0], qy = p[1] - k.c[1];
+                const double ts = -(qx * w[0] + qy * w[1]) / a;
+                if (!(ts >= 0.0 && ts <= L)) continue;
+                const double cx = qx + ts * w[0], cy = qy + ts * w[1];
+                tang = std::min(tang, std::fabs(std::sqrt(cx * cx + cy * cy) - k.c[2]));
+            }
+        }
+        o6[4] = tang;
+    }
+    return int(surf.size());
 }
 
 int orc_transmission(void* gp, long long n, const double* rays, const double* sigma, double pitch,

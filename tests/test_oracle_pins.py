@@ -1333,3 +1333,119 @@ def test_distance_rect_and_csg_modes_identical():
         b = _geom(desc, O.MODE_CSG).distance(xyz, w)
         assert np.array_equal(a[0], b[0], equal_nan=True) and np.array_equal(a[1], b[1])
         assert np.array_equal(a[2], b[2])
+
+
+# ---------------------------------------------------------------------------
+# test infrastructure of the near-surface rule: the oracle's segment geometry
+# and its clearance query
+# ---------------------------------------------------------------------------
+
+def test_trace_geometry_chains_through_collisions():
+    # each segment starts where the previous one ended (same FP64 operations:
+    # r + len * dir per component), births are source_init's, and after a
+    # collision the direction is the Marsaglia direction of that event
+    desc = I.config1()
+    o = O.Geometry(I.to_json(desc), O.MODE_CSG)
+    births, _ = o.source(40, 1)
+    for pid in range(40):
+        inst, ln, kind, st, geo = o.trace(pid, 1, 0.3, geometry=True)
+        assert np.array_equal(geo[0, :3], births[pid, :3]) and np.array_equal(geo[0, 3:6], births[pid, 3:6])
+        event = 0
+        for k in range(len(ln) - 1):
+            end = geo[k, :3] + ln[k] * geo[k, 3:6]
+            assert np.array_equal(geo[k + 1, :3], end)
+            if kind[k] == 1:
+                event += 1
+                d, ok = O.isotropic(pid, event, 1, desc["geometry_id"])
+                assert ok and np.array_equal(geo[k + 1, 3:6], d)
+            else:
+                # a crossing keeps the direction except at a reflecting wall,
+                # where one component changes sign
+                flip = geo[k + 1, 3:6] != geo[k, 3:6]
+                assert flip.sum() <= 1 and np.array_equal(np.abs(geo[k + 1, 3:6]), np.abs(geo[k, 3:6]))
+
+
+def test_clearance_by_hand_single_pin():
+    # one pin (cylinders r = 0.41, 0.475 about the z axis) in the box
+    # [-0.63, 0.63]^2 x [0, 10]: distances worked by hand
+    o = O.Geometry(I.to_json(I.single_pin(bc="vacuum")), O.MODE_CSG)
+    pts = np.array([[0.2, 0.0, 5.0], [0.41, 0.0, 5.0], [0.6, 0.0, 9.99], [0.0, 0.3, 0.001]])
+    cl = o.clearance(pts, np.tile([1.0, 0.0, 0.0], (4, 1)), np.zeros(4))
+    want = [(0.21, 0.275), (0.0, 0.065), (0.01, 0.03), (0.001, 0.11)]
+    for (c1, c2), row in zip(want, cl):
+        assert row[0] == pytest.approx(c1, abs=1e-12) and row[1] == pytest.approx(c2, abs=1e-12)
+        # the end point of a zero-length segment is its start
+        assert row[2] == row[0] and row[3] == row[1]
+    # end point: 0.5 cm along +x from (0.2, 0, 5) is (0.7, 0, 5), outside the
+    # box by 0.07; the nearest surface is the x = 0.63 face
+    cl = o.clearance(pts[:1], np.array([[1.0, 0.0, 0.0]]), np.array([0.5]))
+    assert cl[0, 2] == pytest.approx(0.07, abs=1e-12) and cl[0, 3] == pytest.approx(0.225, abs=1e-12)
+
+
+def test_clearance_tangency_by_hand():
+    o = O.Geometry(I.to_json(I.single_pin(bc="vacuum")), O.MODE_CSG)
+    # a line along +x at impact parameter b passes closest to the axis at x = 0
+    for b in (0.4, 0.47, 0.2):
+        start = np.array([[-0.5, b, 5.0]])
+        cl = o.clearance(start, np.array([[1.0, 0.0, 0.0]]), np.array([1.0]))
+        assert cl[0, 4] == pytest.approx(min(abs(b - 0.41), abs(b - 0.475)), abs=1e-12)
+        # the closest approach lies beyond a shorter segment: no tangency
+        cl = o.clearance(start, np.array([[1.0, 0.0, 0.0]]), np.array([0.4]))
+        assert cl[0, 4] == np.inf
+    # an oblique ray: the xy projection decides; (-0.3, 0.45) + t (0.6, 0)
+    # is closest to the axis at t = 0.5 (x = 0), distance 0.45
+    cl = o.clearance(np.array([[-0.3, 0.45, 2.0]]), np.array([[0.6, 0.0, 0.8]]), np.array([1.0]))
+    assert cl[0, 4] == pytest.approx(0.025, abs=1e-12)
+    # a ray along the axis direction has no xy closest approach
+    cl = o.clearance(np.array([[0.1, 0.1, 2.0]]), np.array([[0.0, 0.0, 1.0]]), np.array([3.0]))
+    assert cl[0, 4] == np.inf
+
+
+def test_clearance_general_planes_hex():
+    # a hex lattice element's faces are general planes n.x = d: a point at the
+    # element centre plus s along a face normal is (pitch/2 - s) from that face
+    desc = I.small_hex(rings=0, pitch=1.0, r_pin=0.3)
+    o = O.Geometry(I.to_json(desc), O.MODE_CSG)
+    a1, a2, nrm = I._hex_frame(1.0, rot30=False)
+    nx, ny = nrm[0]
+    s = 0.42
+    pt = np.array([[s * nx, s * ny, 2.5]])
+    cl = o.clearance(pt, np.array([[0.0, 0.0, 1.0]]), np.zeros(1))
+    # nearest: the face at 0.5 - 0.42 = 0.08; then the pin at 0.42 - 0.3 = 0.12
+    assert cl[0, 0] == pytest.approx(0.08, abs=1e-12)
+    assert cl[0, 1] == pytest.approx(0.12, abs=1e-12)
+
+
+def test_trace_comparison_flags_planted_mistakes():
+    # the near-surface comparison (oracle.compare) on the oracle's own traces:
+    # identical rows match; a changed instance or a length off by 1e-7 cm
+    # fails (the decision points are not near any surface); a length change
+    # far below the propagated rounding bound still matches
+    from oracle import compare as C
+    desc = I.config1()
+    o = O.Geometry(I.to_json(desc), O.MODE_CSG)
+    n, cap = 60, 2048
+    rows_i = np.full((n, cap), -1, np.int32)
+    rows_l = np.zeros((n, cap))
+    for pid in range(n):
+        inst, ln, kind, st = o.trace(pid, 1, 0.3, cap=cap)
+        rows_i[pid, :len(inst)] = inst
+        rows_l[pid, :len(ln)] = ln
+    res = C.compare_traces(o, np.arange(n), rows_i, rows_l, 1, 0.3, cap)
+    assert res["matched"] == n and not res["failed"]
+    long_ = [p for p in range(n) if (rows_i[p] >= 0).sum() > 12]
+    a, b, c = long_[:3]
+    bad_i, bad_l = rows_i.copy(), rows_l.copy()
+    # a different cell after segment 6 (the neighbour's instance number)
+    bad_i[a, 7] = bad_i[a, 7] + 1 if bad_i[a, 7] + 1 != bad_i[a, 6] else bad_i[a, 7] + 2
+    bad_l[b, 4] += 1e-7
+    bad_l[c, 4] *= 1.0 + 1e-15
+    res = C.compare_traces(o, np.array([a, b, c]), bad_i[[a, b, c]], bad_l[[a, b, c]], 1, 0.3, cap)
+    failed = {r["pid"] for r in res["failed"]}
+    assert failed == {a, b} and res["matched"] == 1
+    # a history cut short (one segment missing at the end) is a mismatch too
+    short_i, short_l = rows_i[[a]].copy(), rows_l[[a]].copy()
+    k = int((short_i[0] >= 0).sum())
+    short_i[0, k - 1] = -1
+    res = C.compare_traces(o, np.array([a]), short_i, short_l, 1, 0.3, cap)
+    assert res["matched"] == 0
