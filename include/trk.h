@@ -244,14 +244,23 @@ trk_status tally_read(trk_geom_t g, const uint64_t* dev_tally, double* host_out,
 trk_status trk_find_cell(trk_geom_t g, int tracker, int64_t n, const double* dev_xyz,
                          int64_t* dev_inst, void* stream);
 
-/* trk_trace - run_histories (history mode, FP64 or FP32-local) that also logs each
- * particle's segments: for particle i and segment k < cap,
- * dev_inst[i*cap+k] (int32 leaf instance, -1 past the end) and
- * dev_len[i*cap+k] (segment length, cm).  Tallies and counters as in
- * run_histories. */
+/* trk_trace - run_histories (Alg. 2) that also logs each particle's
+ * segments: for particle i and segment k < cap, dev_inst[i*cap+k] (int32
+ * leaf instance, -1 past the end) and dev_len[i*cap+k] (segment length, cm).
+ * opts->mode selects the kernel: history mode (FP64 or FP32-local), or event
+ * mode, which runs the persistent event kernel in the launch shape
+ * run_histories uses for the same options (tracker, precision, queue depth,
+ * grid), so the logged segments are those of that kernel.  Tallies and
+ * counters as in run_histories.
+ *   dev_work, work_bytes  event mode: scratch of run_histories_work_bytes for
+ *                         the same n and opts (256-byte aligned); history
+ *                         mode: NULL, 0.
+ * Errors: TRK_E_INVALID, TRK_E_NOMEM (event-mode work buffer too small),
+ * TRK_E_UNSUPPORTED (FP32-local in the exact build), TRK_E_CUDA. */
 trk_status trk_trace(trk_geom_t g, const void* dev_particles, int64_t n, int32_t cap,
                      int32_t* dev_inst, double* dev_len, uint64_t* dev_tally,
-                     uint64_t* dev_counters, const trk_run_opts* opts, void* stream);
+                     uint64_t* dev_counters, void* dev_work, size_t work_bytes,
+                     const trk_run_opts* opts, void* stream);
 
 /*
  * trk_distance_to_surface - diagnostic: for n points with directions, the
@@ -374,8 +383,10 @@ trk_status batch_autotune(trk_batch_t b, void* dev_work, size_t work_bytes, trk_
  *   The caller still provides rays, sigma, dev_gT and dev_grad.
  *   Allocates nothing (no cudaMalloc/cudaFree, no allocating library call).
  *   The first call on a device looks up the array's address on that device;
- *   make it before any stream capture.  All calls share the array: calls
- *   whose kernels overlap on the GPU race on it.
+ *   make it before any stream capture.  The address is kept for the life of
+ *   the process, so the entry point must not be used on a device after
+ *   cudaDeviceReset.  All calls share the array: calls whose kernels overlap
+ *   on the GPU race on it.
  * Errors: TRK_E_NOMEM when n needs more scratch than the array holds (about
  * 5.5 million rays with 8 materials; the message gives this geometry's
  * limit), TRK_E_INVALID, TRK_E_CUDA, and those of transmission_bwd.

@@ -220,12 +220,12 @@ __global__ void TRK_EV_BOUNDS k_batched_ev(BatchHeader* __restrict__ hdr, const 
                         c.status = TRK_E_LOST;
                         cnt.k[TRK_K_LOST]++;
                     } else {
-                        unsigned char* r = rec_at<CSG>(B, slot);
+                        unsigned char* r = rec_at<FLAGS>(B, slot);
                         D2(r, R_XY) = make_double2(s.x, s.y);
                         D2(r, R_ZT) = make_double2(s.z, s.tau);
                         store_dir(r, s);
-                        store_levels<CSG>(r, s, 0);
-                        store_ctx<FLAGS>(r, int(pidx), c, 0);
+                        store_levels<CSG>(g, r, s, 0);
+                        store_ctx<FLAGS>(r, int(pidx), c, make_misc(0, s, 0));
                         ok = true;
                     }
                 }
@@ -255,15 +255,16 @@ __global__ void TRK_EV_BOUNDS k_batched_ev(BatchHeader* __restrict__ hdr, const 
             int a = A_DONE, slot = 0, hl = -1;
             if (k < n_fly) {
                 slot = slot0 + fly[k];
-                unsigned char* r = rec_at<CSG>(B, slot);
+                unsigned char* r = rec_at<FLAGS>(B, slot);
                 St s;
                 const double2 xy = D2(r, R_XY), zt = D2(r, R_ZT);
                 s.x = xy.x; s.y = xy.y; s.z = zt.x; s.tau = zt.y;
                 load_dir(r, s);
-                load_levels<CSG>(g, r, s);
                 Ctx c;
-                int hpack;
-                const int pidx = load_ctx<FLAGS>(r, c, hpack, rp);
+                unsigned misc;
+                const int pidx = load_ctx<FLAGS>(r, c, misc, rp);
+                int4 su = I4(r, R_SU);
+                load_levels<CSG>(g, r, s, misc, su);
                 Hit h;
                 a = step_fly<CSG, F32, FLAGS>(g, s, h, c, rp, E.tally, cnt, nullptr, nullptr, 0);
                 if (a == A_DONE) {
@@ -273,10 +274,11 @@ __global__ void TRK_EV_BOUNDS k_batched_ev(BatchHeader* __restrict__ hdr, const 
                     D2(r, R_ZT) = make_double2(s.z, s.tau);
                     if (a == A_CROSS) {
                         hl = h.level;
-                        store_ctx<FLAGS>(r, pidx, c, pack_hit(h));
-                        I4(r, R_HT) = make_int4(h.surf, h.entry, 0, 0);
+                        store_ctx<FLAGS>(r, pidx, c, misc_with_hit(misc, pack_hit(h)));
+                        su.y = hit_ref(h);
+                        I4(r, R_SU) = su;
                     } else {
-                        store_ctx<FLAGS>(r, pidx, c, hpack);
+                        store_ctx<FLAGS>(r, pidx, c, misc);
                     }
                 }
             }
@@ -296,25 +298,27 @@ __global__ void TRK_EV_BOUNDS k_batched_ev(BatchHeader* __restrict__ hdr, const 
             int a = A_DONE, slot = 0;
             if (k < n_cross[lq]) {
                 slot = slot0 + qx[lq * slots + k];
-                unsigned char* r = rec_at<CSG>(B, slot);
+                unsigned char* r = rec_at<FLAGS>(B, slot);
                 St s;
                 const double2 xy = D2(r, R_XY), zt = D2(r, R_ZT);
                 s.x = xy.x; s.y = xy.y; s.z = zt.x; s.tau = zt.y;
                 load_dir(r, s);
-                load_levels<CSG>(g, r, s);
                 Ctx c;
-                int hpack;
-                const int pidx = load_ctx<FLAGS>(r, c, hpack, rp);
+                unsigned misc;
+                const int pidx = load_ctx<FLAGS>(r, c, misc, rp);
+                const int4 su = I4(r, R_SU);
+                load_levels<CSG>(g, r, s, misc, su);
                 Hit h;
-                unpack_hit(hpack, h);
-                const int4 ht = I4(r, R_HT);
-                h.surf = ht.x; h.entry = ht.y; h.d = 0.0;
+                unpack_hit(misc_hpack(misc), h);
+                hit_from_ref(g, su.y, h);
+                h.d = 0.0;
                 const unsigned refl0 = cnt.k[TRK_K_REFLECTIONS];
                 a = step_cross<CSG>(g, s, h, c, rp, cnt);
                 if (a == A_DONE) {
                     if (rec) finish<FLAGS>(pidx, c, rec);
                 } else {
-                    store_levels<CSG>(r, s, 0);
+                    store_levels<CSG>(g, r, s, 0);
+                    store_ctx<FLAGS>(r, pidx, c, make_misc(0, s, 0));
                     if (cnt.k[TRK_K_REFLECTIONS] != refl0) store_dir(r, s);
                 }
             }
@@ -327,11 +331,11 @@ __global__ void TRK_EV_BOUNDS k_batched_ev(BatchHeader* __restrict__ hdr, const 
             int a = A_DONE, slot = 0;
             if (k < n_coll) {
                 slot = slot0 + qc[k];
-                unsigned char* r = rec_at<CSG>(B, slot);
+                unsigned char* r = rec_at<FLAGS>(B, slot);
                 St s;
                 Ctx c;
-                int hpack;
-                const int pidx = load_ctx<FLAGS>(r, c, hpack, rp);
+                unsigned misc;
+                const int pidx = load_ctx<FLAGS>(r, c, misc, rp);
                 a = step_collide(g, s, c, rp, cnt);
                 if (a == A_DONE) {
                     if (rec) finish<FLAGS>(pidx, c, rec);
@@ -339,9 +343,10 @@ __global__ void TRK_EV_BOUNDS k_batched_ev(BatchHeader* __restrict__ hdr, const 
                     store_dir(r, s);
                     const double z = D2(r, R_ZT).x;
                     D2(r, R_ZT) = make_double2(z, s.tau);
-                    const int4 lv = I4(r, R_LV);
-                    I4(r, R_LV) = make_int4(lv.x, -1, -1, lv.w);
-                    store_ctx<FLAGS>(r, pidx, c, hpack);
+                    int4 su = I4(r, R_SU);
+                    su.x = -1;
+                    I4(r, R_SU) = su;
+                    store_ctx<FLAGS>(r, pidx, c, misc_off_surface(misc));
                 }
             }
             const bool live = k < n_coll;
@@ -364,6 +369,7 @@ struct trk_batch {
     int n_geom = 0;
     int chunk = 0;                     // chunk size the uploaded table was built for
     bool uploaded = false;
+    int event_unfit = -1;              // first geometry the event kernels' slot record cannot hold
     void* work = nullptr;
     size_t work_bytes = 0;
     unsigned magic = 0;
@@ -397,6 +403,10 @@ trk_status run_batched_event(trk_batch_t b, void* dev_work, const trk_run_opts& 
     const int slots = o.queue_depth > 0 ? o.queue_depth : 256;
     if (slots < 32 || slots > BEV_MAX_SLOTS) return trk_status(set_error(TRK_E_INVALID, "run_batched: queue_depth must be in [32, 512]"));
     if (o.max_rounds < 0) return trk_status(set_error(TRK_E_INVALID, "run_batched: max_rounds must be >= 0"));
+    if (b->event_unfit >= 0)
+        return trk_status(set_error(TRK_E_UNSUPPORTED, "run_batched (event): geometry %d does not fit the event kernels' "
+                                    "slot record (at most %d universes, %d materials, %d elements per array axis)",
+                                    b->event_unfit, ev::REC_MAX_UNIV, ev::REC_MAX_MAT, ev::REC_MAX_DIM));
     const int grid = event_grid(slots);
     const size_t need = event_bytes(b->n_geom, slots);
     if (b->work_bytes < need)
@@ -485,6 +495,7 @@ trk_status batch_create(const trk_geom_t* geoms, int n_geom, const void* const* 
         e.records = dev_records ? reinterpret_cast<unsigned long long*>(dev_records[k]) : nullptr;
         e.n = n;
         e.csg = use_csg(k) ? 1 : 0;
+        if (b->event_unfit < 0 && event_fits(geoms[k], e.csg != 0, nullptr) != TRK_OK) b->event_unfit = k;
         b->entries.push_back(e);
         b->order.push_back(k);
     }

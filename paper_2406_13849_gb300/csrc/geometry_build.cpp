@@ -892,6 +892,74 @@ class BvhBuilder {
     }
 };
 
+// Host validation of the built search structures (the tracking kernels read
+// them without bounds checks): every cell of a universe sits in exactly one
+// leaf of its BVH and of its BIH, a leaf holds only that universe's cells,
+// every BVH node box on the way to a leaf contains the leaf's cell boxes, and
+// every BIH clip plane on the way bounds them on its side.  A failure is a
+// builder defect, reported as TRK_E_DESC before anything is copied to the
+// device.
+int validate_hierarchy(const BvhBuilder& bvh, int first_cell, int ncells, int bvh_root, int bih_root,
+                       const std::vector<Box>& boxes, int u) {
+    struct Item { int ref; std::vector<int> path; };   // path: node index * 2 + child side
+    for (int kind = 0; kind < 2; ++kind) {
+        const int root = kind == 0 ? bvh_root : bih_root;
+        if (root == -1) continue;
+        std::vector<int> seen(size_t(ncells), 0);
+        std::vector<Item> stack;
+        stack.push_back(Item{root, {}});
+        while (!stack.empty()) {
+            Item it = std::move(stack.back());
+            stack.pop_back();
+            if (it.ref >= 0) {
+                if (kind == 0 && size_t(it.ref) >= bvh.nodes.size()) return set_error(TRK_E_DESC, "universe %d: BVH node %d out of range", u, it.ref);
+                if (kind == 1 && size_t(it.ref) >= bvh.bih.size()) return set_error(TRK_E_DESC, "universe %d: BIH node %d out of range", u, it.ref);
+                if (it.path.size() > size_t(BVH_STACK)) return set_error(TRK_E_DESC, "universe %d: hierarchy deeper than %d", u, BVH_STACK);
+                const int r0 = kind == 0 ? bvh.nodes[size_t(it.ref)].ref0 : bvh.bih[size_t(it.ref)].ref0;
+                const int r1 = kind == 0 ? bvh.nodes[size_t(it.ref)].ref1 : (bvh.bih[size_t(it.ref)].ref1_axis >> 2);
+                for (int side = 0; side < 2; ++side) {
+                    Item ch{side == 0 ? r0 : r1, it.path};
+                    ch.path.push_back(it.ref * 2 + side);
+                    stack.push_back(std::move(ch));
+                }
+                continue;
+            }
+            const int leaf = -1 - it.ref, first = leaf >> 4, cnt = leaf & 15;
+            if (first < 0 || size_t(first) + size_t(cnt) > bvh.leaf_cells.size())
+                return set_error(TRK_E_DESC, "universe %d: leaf range out of bounds", u);
+            for (int k = 0; k < cnt; ++k) {
+                const int c = bvh.leaf_cells[size_t(first + k)];
+                if (c < first_cell || c >= first_cell + ncells)
+                    return set_error(TRK_E_DESC, "universe %d: a leaf holds cell %d of another universe", u, c);
+                seen[size_t(c - first_cell)]++;
+                const Box& b = boxes[size_t(c)];
+                for (int pe : it.path) {
+                    const int nd = pe >> 1, side = pe & 1;
+                    bool ok = true;
+                    if (kind == 0) {
+                        const BvhNode& N = bvh.nodes[size_t(nd)];
+                        const float* lo = side == 0 ? N.lo0 : N.lo1;
+                        const float* hi = side == 0 ? N.hi0 : N.hi1;
+                        for (int a = 0; a < 3; ++a) ok = ok && double(lo[a]) <= b.lo[a] && double(hi[a]) >= b.hi[a];
+                    } else {
+                        const BihNode& N = bvh.bih[size_t(nd)];
+                        const int axis = N.ref1_axis & 3;
+                        ok = side == 0 ? double(N.clip_l) >= b.hi[axis] : double(N.clip_r) <= b.lo[axis];
+                    }
+                    if (!ok)
+                        return set_error(TRK_E_DESC, "universe %d: %s node %d does not bound cell %d", u,
+                                         kind == 0 ? "BVH" : "BIH", nd, c);
+                }
+            }
+        }
+        for (int i = 0; i < ncells; ++i)
+            if (seen[size_t(i)] != 1)
+                return set_error(TRK_E_DESC, "universe %d: cell %d appears %d times in its %s", u, first_cell + i,
+                                 seen[size_t(i)], kind == 0 ? "BVH" : "BIH");
+    }
+    return TRK_OK;
+}
+
 // Order key of a double (see okey_bits): integer comparisons of keys agree
 // with IEEE comparisons of the values, -0 equal to +0.
 long long okey(double v) {
@@ -998,6 +1066,12 @@ int build_host(const char* json, size_t len, Built& B) {
     }
     if (bvh.bih_depth >= BVH_STACK) return set_error(TRK_E_DESC, "BIH depth %d exceeds %d", bvh.bih_depth, BVH_STACK);
     if (bvh.max_depth >= BVH_STACK) return set_error(TRK_E_DESC, "BVH depth %d exceeds %d", bvh.max_depth, BVH_STACK);
+    for (size_t u = 0; u < G.univ.size(); ++u) {
+        const HUniv& U = G.univ[u];
+        if (U.bvh < 0) continue;
+        st = validate_hierarchy(bvh, U.first_cell, int(U.cells.size()), U.bvh, U.bih, boxes, int(u));
+        if (st != TRK_OK) return st;
+    }
     B.n_nodes = int(bvh.nodes.size());
 
     // SoA arrays
@@ -1446,6 +1520,9 @@ trk_status geometry_build(const char* json, size_t len, void* dev_buf, size_t* d
     h->rect_ok = d.rect_ok;
     for (auto& U : G.univ) h->has_hex |= U.type == UT_HEX ? 1 : 0;
     h->n_nodes = B.n_nodes;
+    for (auto& U : G.univ)
+        if (U.type == UT_RECT)
+            for (int k = 0; k < 3; ++k) h->max_rect_dim = std::max(h->max_rect_dim, int(U.grid[k].size()) - 1);
     h->magic = TRK_GEOM_MAGIC;
     *out = h;
     return TRK_OK;

@@ -1308,6 +1308,9 @@ struct RunP {
     double* fis_pos;            // 3 per history
     int* fis_n;                 // sites per history
     unsigned long long* nu_sum;
+    // segment log of the event kernel (F_TRACE): trace_cap entries per particle
+    int* tr_inst = nullptr;
+    double* tr_len = nullptr;
 };
 
 // Per-thread event counts (32-bit: one thread tracks far fewer than 2^32

@@ -97,18 +97,19 @@ __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, lo
                         c.status = TRK_E_LOST;
                         cnt.k[TRK_K_LOST]++;
                     } else {
-                        unsigned char* r = rec_at<CSG>(B, slot);
+                        unsigned char* r = rec_at<FLAGS>(B, slot);
                         cls = flight_class<CSG>(g, s);
                         D2(r, R_XY) = make_double2(s.x, s.y);
                         D2(r, R_ZT) = make_double2(s.z, s.tau);
                         store_dir(r, s);
-                        store_levels<CSG>(r, s, cls);
-                        store_ctx<FLAGS>(r, int(pidx), c, 0);
+                        store_levels<CSG>(g, r, s, 0);
+                        store_ctx<FLAGS>(r, int(pidx), c, make_misc(0, s, cls));
                         ok = true;
                     }
                 }
                 if (!ok) {
                     finish<FLAGS>(pidx, c, rec);
+                    trace_tail<FLAGS>(pidx, c, rp);
                     if (FLAGS & F_FISS) fission_out(rp, pidx, 0, 0.0, 0.0, 0.0);
                 }
             }
@@ -145,29 +146,32 @@ __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, lo
                 for (int c = 0; c < NFC - 1; ++c)
                     if (q == c && kk >= n_fl[c]) { kk -= n_fl[c]; q = c + 1; }
                 slot = slot0 + qfl[q * slots + kk];
-                unsigned char* r = rec_at<CSG>(B, slot);
+                unsigned char* r = rec_at<FLAGS>(B, slot);
                 St s;
                 const double2 xy = D2(r, R_XY), zt = D2(r, R_ZT);
                 s.x = xy.x; s.y = xy.y; s.z = zt.x; s.tau = zt.y;
                 load_dir(r, s);
-                load_levels<CSG>(g, r, s);
                 Ctx c;
-                int hpack;
-                const int pidx = load_ctx<FLAGS>(r, c, hpack, rp);
+                unsigned misc;
+                const int pidx = load_ctx<FLAGS>(r, c, misc, rp);
+                int4 su = I4(r, R_SU);
+                load_levels<CSG>(g, r, s, misc, su);
                 Hit h;
-                a = step_fly<CSG, F32, FLAGS>(g, s, h, c, rp, tally, cnt, nullptr, nullptr, 0);
+                a = step_fly<CSG, F32, FLAGS>(g, s, h, c, rp, tally, cnt, rp.tr_inst, rp.tr_len, pidx);
                 if (a == A_DONE) {
                     finish<FLAGS>(pidx, c, rec);
+                    trace_tail<FLAGS>(pidx, c, rp);
                     if (FLAGS & F_FISS) fission_out(rp, pidx, 0, 0.0, 0.0, 0.0);
                 } else {
                     D2(r, R_XY) = make_double2(s.x, s.y);
                     D2(r, R_ZT) = make_double2(s.z, s.tau);
                     if (a == A_CROSS) {
                         hl = h.level;
-                        store_ctx<FLAGS>(r, pidx, c, pack_hit(h));
-                        I4(r, R_HT) = make_int4(h.surf, h.entry, 0, 0);
+                        store_ctx<FLAGS>(r, pidx, c, misc_with_hit(misc, pack_hit(h)));
+                        su.y = hit_ref(h);
+                        I4(r, R_SU) = su;
                     } else {
-                        store_ctx<FLAGS>(r, pidx, c, hpack);
+                        store_ctx<FLAGS>(r, pidx, c, misc);
                     }
                 }
             }
@@ -190,27 +194,30 @@ __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, lo
             int a = A_DONE, slot = 0, cls = 0;
             if (k < n_cross[lq]) {
                 slot = slot0 + qx[lq * slots + k];
-                unsigned char* r = rec_at<CSG>(B, slot);
+                unsigned char* r = rec_at<FLAGS>(B, slot);
                 St s;
                 const double2 xy = D2(r, R_XY), zt = D2(r, R_ZT);
                 s.x = xy.x; s.y = xy.y; s.z = zt.x; s.tau = zt.y;
                 load_dir(r, s);
-                load_levels<CSG>(g, r, s);
                 Ctx c;
-                int hpack;
-                const int pidx = load_ctx<FLAGS>(r, c, hpack, rp);
+                unsigned misc;
+                const int pidx = load_ctx<FLAGS>(r, c, misc, rp);
+                const int4 su = I4(r, R_SU);
+                load_levels<CSG>(g, r, s, misc, su);
                 Hit h;
-                unpack_hit(hpack, h);
-                const int4 ht = I4(r, R_HT);
-                h.surf = ht.x; h.entry = ht.y; h.d = 0.0;
+                unpack_hit(misc_hpack(misc), h);
+                hit_from_ref(g, su.y, h);
+                h.d = 0.0;
                 const unsigned refl0 = cnt.k[TRK_K_REFLECTIONS];
                 a = step_cross<CSG>(g, s, h, c, rp, cnt);
                 if (a == A_DONE) {
                     finish<FLAGS>(pidx, c, rec);
+                    trace_tail<FLAGS>(pidx, c, rp);
                     if (FLAGS & F_FISS) fission_out(rp, pidx, 0, 0.0, 0.0, 0.0);
                 } else {
                     cls = flight_class<CSG>(g, s);
-                    store_levels<CSG>(r, s, cls);
+                    store_levels<CSG>(g, r, s, 0);
+                    store_ctx<FLAGS>(r, pidx, c, make_misc(0, s, cls));
                     if (cnt.k[TRK_K_REFLECTIONS] != refl0) store_dir(r, s);
                 }
             }
@@ -224,21 +231,22 @@ __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, lo
             int a = A_DONE, slot = 0, cls = 0;
             if (k < n_coll) {
                 slot = slot0 + qc[k];
-                unsigned char* r = rec_at<CSG>(B, slot);
+                unsigned char* r = rec_at<FLAGS>(B, slot);
                 St s;
                 Ctx c;
-                int hpack;
-                const int pidx = load_ctx<FLAGS>(r, c, hpack, rp);
+                unsigned misc;
+                const int pidx = load_ctx<FLAGS>(r, c, misc, rp);
                 a = step_collide(g, s, c, rp, cnt);
                 if (a == A_DONE) {
                     finish<FLAGS>(pidx, c, rec);
+                    trace_tail<FLAGS>(pidx, c, rp);
                     if (FLAGS & F_FISS) {
                         int nf = 0;
                         double fx = 0.0, fy = 0.0, fz = 0.0;
                         if (c.status == TRK_P_ABSORBED) {
                             const double2 xy = D2(r, R_XY), zt = D2(r, R_ZT);
                             fx = xy.x; fy = xy.y; fz = zt.x;
-                            nf = fission_sites(g, c.pid, c.event, I4(r, R_LV).w, rp);
+                            nf = fission_sites(g, c.pid, c.event, misc_mat(misc), rp);
                         }
                         fission_out(rp, pidx, nf, fx, fy, fz);
                     }
@@ -246,10 +254,11 @@ __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, lo
                     store_dir(r, s);
                     const double z = D2(r, R_ZT).x;
                     D2(r, R_ZT) = make_double2(z, s.tau);
-                    const int4 lv = I4(r, R_LV);
-                    cls = lv.x >> 16;
-                    I4(r, R_LV) = make_int4(lv.x, -1, -1, lv.w);
-                    store_ctx<FLAGS>(r, pidx, c, hpack);
+                    cls = misc_cls(misc);
+                    int4 su = I4(r, R_SU);
+                    su.x = -1;
+                    I4(r, R_SU) = su;
+                    store_ctx<FLAGS>(r, pidx, c, misc_off_surface(misc));
                 }
             }
             const bool live = k < n_coll;
@@ -287,10 +296,25 @@ int event_grid(int slots) {
 
 size_t event_work_bytes(int slots, int grid) { return buf_bytes((long long)slots * EV_WARPS * grid); }
 
+// The slot record packs universes, materials and rect element indices into
+// narrow fields; a geometry beyond them is refused before any launch.
+trk_status event_fits(trk_geom_t g, bool csg, const char* where) {
+    if (g->dg.n_univ > REC_MAX_UNIV || g->n_mat > REC_MAX_MAT || (!csg && g->max_rect_dim > REC_MAX_DIM)) {
+        if (!where) return TRK_E_UNSUPPORTED;
+        return trk_status(set_error(TRK_E_UNSUPPORTED,
+                                    "%s: the event kernels take at most %d universes, %d materials and (array "
+                                    "tracker) %d elements per array axis",
+                                    where, REC_MAX_UNIV, REC_MAX_MAT, REC_MAX_DIM));
+    }
+    return TRK_OK;
+}
+
 trk_status launch_event(trk_geom_t g, const ParticlesView& P, long long n, const RunP& rp, bool csg, bool f32,
                         int flags, unsigned long long* tally, unsigned long long* cnt, unsigned long long* rec,
                         void* work, size_t work_bytes, int slots, int grid, int max_rounds_opt, cudaStream_t s) {
     const long long T = (long long)slots * EV_WARPS * grid;
+    const trk_status fit = event_fits(g, csg, "run_histories (event)");
+    if (fit != TRK_OK) return fit;
     if (work_bytes < buf_bytes(T) || !work)
         return trk_status(set_error(TRK_E_NOMEM, "run_histories (event): work buffer needs %zu bytes", buf_bytes(T)));
     if ((reinterpret_cast<uintptr_t>(work) & 255) != 0)
@@ -313,15 +337,18 @@ trk_status launch_event(trk_geom_t g, const ParticlesView& P, long long n, const
     if (f32) {
 #ifndef TRK_EXACT
         if (csg) {
-            if (flags & F_REC) TRK_EV(true, true, F_REC);
+            if (flags & F_TRACE) TRK_EV(true, true, F_TRACE);
+            else if (flags & F_REC) TRK_EV(true, true, F_REC);
             else TRK_EV(true, true, 0);
         } else {
-            if (flags & F_REC) TRK_EV(false, true, F_REC);
+            if (flags & F_TRACE) TRK_EV(false, true, F_TRACE);
+            else if (flags & F_REC) TRK_EV(false, true, F_REC);
             else TRK_EV(false, true, 0);
         }
 #endif
     } else if (csg) {
         switch (flags) {
+            case F_TRACE: TRK_EV(true, false, F_TRACE); break;
             case 0: TRK_EV(true, false, 0); break;
             case F_REC: TRK_EV(true, false, F_REC); break;
             case F_CUT: TRK_EV(true, false, F_CUT); break;
@@ -333,6 +360,7 @@ trk_status launch_event(trk_geom_t g, const ParticlesView& P, long long n, const
         }
     } else {
         switch (flags) {
+            case F_TRACE: TRK_EV(false, false, F_TRACE); break;
             case 0: TRK_EV(false, false, 0); break;
             case F_REC: TRK_EV(false, false, F_REC); break;
             case F_CUT: TRK_EV(false, false, F_CUT); break;

@@ -46,24 +46,29 @@ constexpr int EV_QUEUES = NFC + 2 + MAXL;   // flight by class, collide, free, c
 
 // Slot record: one 16-byte-aligned record per slot, read and written in
 // 16-byte chunks (a lane's fields share sectors whatever order the queues
-// put the slots in).  Only what a history needs between operations is kept:
-// per level the universe and cell (rect levels also i, j, k); translations
-// and instance offsets are reloaded from the geometry tables.
-static_assert(MAXL == 4, "the slot record keeps one int4 per level field");
-constexpr int R_XY = 0,     // x, y
-              R_ZT = 16,    // z, tau
-              R_UV = 32,    // u, v
-              R_WI = 48,    // w, 1/u
-              R_II = 64,    // 1/v, 1/w
-              R_HP = 80,    // record hash, path length (only with records / path cutoff)
-              R_LV = 96,    // nlev | flight class << 16, on_lev, on_surf, mat
-              R_CT = 112,   // particle index, event, segments, packed hit (level, side, dim, sign)
-              R_HT = 128,   // hit surface, hit entry
-              R_LU = 144,   // universe per level
-              R_LC = 160,   // cell (rect: element) per level
-              R_LI = 176, R_LJ = 192, R_LK = 208;   // rect levels: i, j, k
-template <bool CSG>
-__host__ __device__ constexpr int rec_bytes() { return CSG ? 176 : 224; }
+// put the slots in).  Only what a history needs between operations is kept,
+// packed so that the records of all slots stay small next to the L2 cache:
+//    0  x, y                16  z, tau
+//   32  u, v                48  w, 1/u
+//   64  1/v, 1/w            80  per level the cell (rect levels: i | j << 10 | k << 20)
+//   96  particle index, event, segments, misc
+//  112  on-surface surface, hit reference, universes of levels 0|1, 2|3 (16 bits each)
+//  128  record hash, path length (only with records or a path cutoff)
+// misc: hit level, side, dim, sign (9 bits) | levels << 9 | (on-surface level
+// + 1) << 12 | flight class << 15 | material << 17.  The hit reference is the
+// crossed entry of the cell's surface list, or for a rect array face its
+// negative face code (the surface follows from either).  Translations and
+// instance offsets are reloaded from the geometry tables.
+static_assert(MAXL == 4, "the slot record keeps one int4 of cells");
+constexpr int R_XY = 0, R_ZT = 16, R_UV = 32, R_WI = 48, R_II = 64, R_LC = 80, R_CT = 96, R_SU = 112, R_HP = 128;
+// Limits of the packed fields (checked on the host before an event launch).
+constexpr int REC_MAX_DIM = 1024;        // rect array elements per axis
+constexpr int REC_MAX_UNIV = 1 << 16;    // universes
+constexpr int REC_MAX_MAT = 1 << 15;     // materials
+
+template <int FLAGS>
+__host__ __device__ constexpr int rec_bytes() { return (FLAGS & (F_REC | F_CUT)) ? 144 : 128; }
+constexpr int REC_BYTES_MAX = 144;
 
 struct EvBuf {
     unsigned char* rec;
@@ -73,7 +78,7 @@ struct EvBuf {
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-inline size_t buf_bytes(long long T) { return 256 + align256(size_t(T) * size_t(rec_bytes<false>())); }
+inline size_t buf_bytes(long long T) { return 256 + align256(size_t(T) * size_t(REC_BYTES_MAX)); }
 
 inline EvBuf make_buf(void* work, long long T) {
     unsigned char* b = static_cast<unsigned char*>(work);
@@ -84,9 +89,9 @@ inline EvBuf make_buf(void* work, long long T) {
     return e;
 }
 
-template <bool CSG>
+template <int FLAGS>
 __device__ __forceinline__ unsigned char* rec_at(const EvBuf& B, int s) {
-    return B.rec + (size_t)s * rec_bytes<CSG>();
+    return B.rec + (size_t)s * rec_bytes<FLAGS>();
 }
 __device__ __forceinline__ double2& D2(unsigned char* r, int off) { return *reinterpret_cast<double2*>(r + off); }
 __device__ __forceinline__ int4& I4(unsigned char* r, int off) { return *reinterpret_cast<int4*>(r + off); }
@@ -98,6 +103,23 @@ __device__ __forceinline__ int pack_hit(const Hit& h) {
 __device__ __forceinline__ void unpack_hit(int p, Hit& h) {
     h.level = (p & 7) - 1; h.side = ((p >> 3) & 3) - 1; h.dim = ((p >> 5) & 3) - 1; h.dsign = ((p >> 7) & 3) - 1;
 }
+__device__ __forceinline__ int hit_ref(const Hit& h) { return h.surf < 0 ? h.surf : h.entry; }
+__device__ __forceinline__ void hit_from_ref(const DevGeom& g, int ref, Hit& h) {
+    if (ref < 0) { h.surf = ref; h.entry = -1; }
+    else { h.entry = ref; h.surf = cs_surface(__ldg(g.cs + ref)); }
+}
+
+__device__ __forceinline__ unsigned make_misc(int hpack, const St& st, int cls) {
+    return unsigned(hpack) | (unsigned(st.nlev) << 9) | (unsigned(st.on_lev + 1) << 12) | (unsigned(cls) << 15) |
+           (unsigned(st.mat) << 17);
+}
+__device__ __forceinline__ int misc_hpack(unsigned m) { return int(m & 511u); }
+__device__ __forceinline__ int misc_cls(unsigned m) { return int((m >> 15) & 3u); }
+__device__ __forceinline__ int misc_mat(unsigned m) { return int(m >> 17); }
+// misc with the hit replaced
+__device__ __forceinline__ unsigned misc_with_hit(unsigned m, int hpack) { return (m & ~511u) | unsigned(hpack); }
+// misc with the on-surface level cleared (after a collision)
+__device__ __forceinline__ unsigned misc_off_surface(unsigned m) { return m & ~(7u << 12); }
 
 // Translation and instance offset of every occupied level, from the tables
 // the find and cross steps take them from (the same values, bit for bit).
@@ -110,6 +132,8 @@ __device__ __forceinline__ void reload_frames(const DevGeom& g, St& st) {
         const int lat = CSG ? -1 : __ldg(g.u_info + L.u).w;
         if (lat >= 0) {
             const int4 of = __ldg(g.l_off + lat);
+            const int4 dm = __ldg(g.l_dim + lat);
+            L.cell = L.i + dm.x * (L.j + dm.y * L.k);
             L.off = __ldg(g.l_eoff + of.w + L.cell);
             L.tx = __ldg(g.l_ctr + of.x + L.i);
             L.ty = __ldg(g.l_ctr + of.y + L.j);
@@ -123,19 +147,27 @@ __device__ __forceinline__ void reload_frames(const DevGeom& g, St& st) {
     }
 }
 
+// Level stack from the cells chunk, the misc word and the universes chunk.
+// A rect level's cell word holds i, j, k; its element index is rebuilt.
 template <bool CSG>
-__device__ __forceinline__ void load_levels(const DevGeom& g, unsigned char* r, St& st) {
-    const int4 lv = I4(r, R_LV);
-    st.nlev = lv.x & 0xffff; st.on_lev = lv.y; st.on_surf = lv.z; st.mat = lv.w;
-    const int4 lu = I4(r, R_LU), lc = I4(r, R_LC);
-    const int u4[4] = {lu.x, lu.y, lu.z, lu.w}, c4[4] = {lc.x, lc.y, lc.z, lc.w};
+__device__ __forceinline__ void load_levels(const DevGeom& g, unsigned char* r, St& st, unsigned misc, const int4& su) {
+    st.nlev = int((misc >> 9) & 7u);
+    st.on_lev = int((misc >> 12) & 7u) - 1;
+    st.mat = misc_mat(misc);
+    st.on_surf = su.x;
+    const int4 lc = I4(r, R_LC);
+    const int c4[4] = {lc.x, lc.y, lc.z, lc.w};
+    const int u4[4] = {su.z & 0xffff, int(unsigned(su.z) >> 16), su.w & 0xffff, int(unsigned(su.w) >> 16)};
 #pragma unroll
-    for (int l = 0; l < MAXL; ++l) { st.lv[l].u = u4[l]; st.lv[l].cell = c4[l]; st.lv[l].i = st.lv[l].j = st.lv[l].k = 0; }
-    if (!CSG) {
-        const int4 li = I4(r, R_LI), lj = I4(r, R_LJ), lk = I4(r, R_LK);
-        const int i4[4] = {li.x, li.y, li.z, li.w}, j4[4] = {lj.x, lj.y, lj.z, lj.w}, k4[4] = {lk.x, lk.y, lk.z, lk.w};
-#pragma unroll
-        for (int l = 0; l < MAXL; ++l) { st.lv[l].i = i4[l]; st.lv[l].j = j4[l]; st.lv[l].k = k4[l]; }
+    for (int l = 0; l < MAXL; ++l) {
+        st.lv[l].u = u4[l];
+        st.lv[l].cell = c4[l];
+        st.lv[l].i = st.lv[l].j = st.lv[l].k = 0;
+        if (!CSG) {
+            st.lv[l].i = c4[l] & 1023;
+            st.lv[l].j = (c4[l] >> 10) & 1023;
+            st.lv[l].k = (c4[l] >> 20) & 1023;
+        }
     }
     reload_frames<CSG>(g, st);
 }
@@ -150,17 +182,22 @@ __device__ __forceinline__ int flight_class(const DevGeom& g, const St& st) {
     return c < NFC ? c : NFC - 1;
 }
 
-// The level fields; the flight class rides in the upper half of nlev's word.
+// The cells chunk and the universes word (on-surface surface, hit reference,
+// universes); rect levels store i, j, k in the cell word.
 template <bool CSG>
-__device__ __forceinline__ void store_levels(unsigned char* r, const St& st, int cls) {
-    I4(r, R_LV) = make_int4(st.nlev | (cls << 16), st.on_lev, st.on_surf, st.mat);
-    I4(r, R_LU) = make_int4(st.lv[0].u, st.lv[1].u, st.lv[2].u, st.lv[3].u);
-    I4(r, R_LC) = make_int4(st.lv[0].cell, st.lv[1].cell, st.lv[2].cell, st.lv[3].cell);
-    if (!CSG) {
-        I4(r, R_LI) = make_int4(st.lv[0].i, st.lv[1].i, st.lv[2].i, st.lv[3].i);
-        I4(r, R_LJ) = make_int4(st.lv[0].j, st.lv[1].j, st.lv[2].j, st.lv[3].j);
-        I4(r, R_LK) = make_int4(st.lv[0].k, st.lv[1].k, st.lv[2].k, st.lv[3].k);
+__device__ __forceinline__ int4 store_levels(const DevGeom& g, unsigned char* r, const St& st, int href) {
+    int c4[4];
+#pragma unroll
+    for (int l = 0; l < MAXL; ++l) {
+        c4[l] = st.lv[l].cell;
+        if (!CSG && l < st.nlev && __ldg(g.u_info + st.lv[l].u).w >= 0)
+            c4[l] = st.lv[l].i | (st.lv[l].j << 10) | (st.lv[l].k << 20);
     }
+    I4(r, R_LC) = make_int4(c4[0], c4[1], c4[2], c4[3]);
+    const int4 su = make_int4(st.on_surf, href, (st.lv[0].u & 0xffff) | (st.lv[1].u << 16),
+                              (st.lv[2].u & 0xffff) | (st.lv[3].u << 16));
+    I4(r, R_SU) = su;
+    return su;
 }
 
 __device__ __forceinline__ void load_dir(unsigned char* r, St& st) {
@@ -174,15 +211,15 @@ __device__ __forceinline__ void store_dir(unsigned char* r, const St& st) {
     D2(r, R_II) = make_double2(st.d.iv, st.d.iw);
 }
 
-// Context of a live history (status is 0 while it lives).  Returns the
-// particle's index in this launch.
+// Context of a live history (status is 0 while it lives) from the ctx
+// chunk; returns the particle's index in this launch and sets misc.
 template <int FLAGS>
-__device__ __forceinline__ int load_ctx(unsigned char* r, Ctx& c, int& hpack, const RunP& rp) {
+__device__ __forceinline__ int load_ctx(unsigned char* r, Ctx& c, unsigned& misc, const RunP& rp) {
     const int4 ct = I4(r, R_CT);
     c.pid = uint32_t(rp.first_id + uint64_t(uint32_t(ct.x)));
     c.event = uint32_t(ct.y);
     c.nseg = (long long)(uint32_t)ct.z;
-    hpack = ct.w;
+    misc = unsigned(ct.w);
     c.status = 0;
     c.hash = 0; c.path = 0.0;
     if (FLAGS & (F_REC | F_CUT)) {
@@ -194,8 +231,8 @@ __device__ __forceinline__ int load_ctx(unsigned char* r, Ctx& c, int& hpack, co
 }
 
 template <int FLAGS>
-__device__ __forceinline__ void store_ctx(unsigned char* r, int pidx, const Ctx& c, int hpack) {
-    I4(r, R_CT) = make_int4(pidx, int(c.event), int(uint32_t(c.nseg)), hpack);
+__device__ __forceinline__ void store_ctx(unsigned char* r, int pidx, const Ctx& c, unsigned misc) {
+    I4(r, R_CT) = make_int4(pidx, int(c.event), int(uint32_t(c.nseg)), int(misc));
     if (FLAGS & (F_REC | F_CUT)) L2(r, R_HP) = make_longlong2((long long)c.hash, __double_as_longlong(c.path));
 }
 
@@ -217,6 +254,18 @@ __device__ __forceinline__ void finish(long long pidx, const Ctx& c, unsigned lo
     if (FLAGS & F_REC) {
         rec[2 * pidx] = c.hash;
         rec[2 * pidx + 1] = (uint64_t(c.nseg) << 32) | uint32_t(c.status);
+    }
+}
+
+// Segment log (F_TRACE): entries past a finished history's last segment
+// read instance -1, length 0.
+template <int FLAGS>
+__device__ __forceinline__ void trace_tail(long long pidx, const Ctx& c, const RunP& rp) {
+    if (FLAGS & F_TRACE) {
+        for (long long k = c.nseg; k < rp.trace_cap; ++k) {
+            rp.tr_inst[pidx * rp.trace_cap + k] = -1;
+            rp.tr_len[pidx * rp.trace_cap + k] = 0.0;
+        }
     }
 }
 

@@ -180,6 +180,7 @@ struct trk_geom {
     int n_mat = 0, depth = 0, rect_ok = 0;
     int has_hex = 0;          // hex arrays present: TRK_TRACKER_AUTO picks the CSG tracker
     int n_nodes = 0;
+    int max_rect_dim = 0;     // most elements along one axis of a rect array
     unsigned magic = 0;
 };
 constexpr unsigned TRK_GEOM_MAGIC = 0x7472'6b67u;

@@ -626,8 +626,8 @@ trk_status run_histories(trk_geom_t g, const void* dev_particles, int64_t n, uin
 }
 
 trk_status trk_trace(trk_geom_t g, const void* dev_particles, int64_t n, int32_t cap, int32_t* dev_inst,
-                     double* dev_len, uint64_t* dev_tally, uint64_t* dev_counters, const trk_run_opts* opts,
-                     void* stream) {
+                     double* dev_len, uint64_t* dev_tally, uint64_t* dev_counters, void* dev_work,
+                     size_t work_bytes, const trk_run_opts* opts, void* stream) {
     if (!valid(g) || n < 0 || cap <= 0 ||
         (n > 0 && (!dev_particles || !dev_inst || !dev_len || !dev_tally || !dev_counters)))
         return trk_status(set_error(TRK_E_INVALID, "trk_trace: bad arguments"));
@@ -650,6 +650,23 @@ trk_status trk_trace(trk_geom_t g, const void* dev_particles, int64_t n, int32_t
     auto* C = reinterpret_cast<unsigned long long*>(dev_counters);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const ParticlesView P = view_of(dev_particles, n);
+    if (o.precision != TRK_FP64 && o.precision != TRK_FP32_LOCAL)
+        return trk_status(set_error(TRK_E_INVALID, "trk_trace: unknown precision %d", o.precision));
+    if (o.mode == TRK_MODE_EVENT) {
+        // the persistent event kernel in the launch shape run_histories uses
+        // for these options, with the segment log switched on
+        if (o.precision == TRK_FP32_LOCAL && !HAVE_F32)
+            return trk_status(set_error(TRK_E_UNSUPPORTED, "trk_trace: FP32-local is not in the exact build"));
+        const int slots = event_slots(o);
+        if (slots < 32 || slots > 512) return trk_status(set_error(TRK_E_INVALID, "queue_depth must be in [32, 512]"));
+        const int grid = o.grid > 0 ? o.grid : event_grid(slots);
+        if (o.max_rounds < 0) return trk_status(set_error(TRK_E_INVALID, "max_rounds must be >= 0"));
+        rp.tr_inst = dev_inst;
+        rp.tr_len = dev_len;
+        return launch_event(g, P, n, rp, tracker == TRK_TRACKER_CSG, o.precision == TRK_FP32_LOCAL, F_TRACE, T, C,
+                            nullptr, dev_work, work_bytes, slots, grid, o.max_rounds, s);
+    }
+    if (o.mode != TRK_MODE_HISTORY) return trk_status(set_error(TRK_E_INVALID, "trk_trace: unknown mode %d", o.mode));
     if (o.precision == TRK_FP32_LOCAL) {
 #ifndef TRK_EXACT
         if (tracker == TRK_TRACKER_CSG)

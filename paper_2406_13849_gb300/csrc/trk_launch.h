@@ -13,6 +13,10 @@ namespace trk {
 // GPU at the kernel's occupancy), and the work bytes that needs.
 int event_grid(int slots);
 size_t event_work_bytes(int slots, int grid);
+// TRK_OK if the geometry fits the event kernels' slot record (the CSG or the
+// array tracker), else TRK_E_UNSUPPORTED (with the message set, naming
+// `where`, unless where is NULL).
+trk_status event_fits(trk_geom_t g, bool csg, const char* where);
 
 trk_status launch_event(trk_geom_t g, const ParticlesView& P, long long n, const dev::RunP& rp, bool csg, bool f32,
                         int flags,

@@ -84,7 +84,7 @@ def library(exact: bool = False):
             "trk_find_cell": (ctypes.c_int, [_P, ctypes.c_int, i64, _P, _P, _P]),
             "trk_distance_to_surface": (ctypes.c_int, [_P, ctypes.c_int, i64, _P, _P, _P, _P, _P, _P]),
             "trk_sync_status": (ctypes.c_int, [_P, _P]),
-            "trk_trace": (ctypes.c_int, [_P, _P, i64, ctypes.c_int32, _P, _P, _P, _P,
+            "trk_trace": (ctypes.c_int, [_P, _P, i64, ctypes.c_int32, _P, _P, _P, _P, _P, sz,
                                          ctypes.POINTER(RunOpts), _P]),
             "transmission_fwd": (ctypes.c_int, [_P, ctypes.c_int, i64, _P, _P, _P, _P, _P]),
             "transmission_bwd_work_bytes": (ctypes.c_int, [_P, i64, psz]),
@@ -265,11 +265,19 @@ class Geometry:
         if mesh is not None:
             _need(mesh, f"{what} mesh", self.device, 8 * self.mesh_bins, _I64)
 
+    def power_iteration_work_bytes(self, n: int, opts: RunOpts | None = None, **kw) -> int:
+        opts = opts if opts is not None else default_opts(**kw)
+        b = ctypes.c_size_t(0)
+        _check(self.lib, self.lib.power_iteration_work_bytes(self.h, n, ctypes.byref(opts), ctypes.byref(b)))
+        return b.value
+
     def power_iteration(self, n: int, inactive: int, cycles: int, tally=None, counters=None, mesh=None,
-                        opts: RunOpts | None = None, stream=None, **kw):
+                        opts: RunOpts | None = None, stream=None, work=None, **kw):
         """Alg. 1 with the synthetic fission source ("nu" in the description):
         returns (k per cycle, sites banked per cycle) as device tensors, and
-        the tally and counters of the active cycles."""
+        the tally and counters of the active cycles.  work: a caller device
+        buffer of power_iteration_work_bytes (+256 for alignment) reused
+        across calls; allocated per call when None."""
         opts = RunOpts.from_buffer_copy(opts) if opts is not None else default_opts(**kw)
         if mesh is not None:
             opts.mesh_tally = mesh.data_ptr()
@@ -280,13 +288,9 @@ class Geometry:
         self._check_run(None, n, tally, counters, mesh, "power_iteration")
         k = torch.zeros(cycles, dtype=torch.float64, device=self.device)
         bank = torch.zeros(cycles, dtype=torch.int64, device=self.device)
-        b = ctypes.c_size_t(0)
-        _check(self.lib, self.lib.power_iteration_work_bytes(self.h, n, ctypes.byref(opts), ctypes.byref(b)))
-        work = torch.empty(b.value + 256, dtype=torch.uint8, device=self.device)
-        off = (-work.data_ptr()) % 256
+        wp, wlen = self._work_arg(work, self.power_iteration_work_bytes(n, opts), "power_iteration work")
         _check(self.lib, self.lib.power_iteration(self.h, n, inactive, cycles, _ptr(k), _ptr(bank), _ptr(tally),
-                                                  _ptr(counters), ctypes.c_void_p(work.data_ptr() + off), b.value,
-                                                  ctypes.byref(opts), _stream(stream)))
+                                                  _ptr(counters), wp, wlen, ctypes.byref(opts), _stream(stream)))
         return k, bank, tally, counters
 
     def tally_read(self, tally, counters=None, stream=None) -> np.ndarray:
@@ -319,7 +323,10 @@ class Geometry:
                                                           _ptr(lev), _ptr(inst), _stream(stream)))
         return d, lev, inst
 
-    def trace(self, particles, n: int, cap: int, opts: RunOpts | None = None, stream=None, **kw):
+    def trace(self, particles, n: int, cap: int, opts: RunOpts | None = None, stream=None, work=None, **kw):
+        """Segment log per particle (trk_trace): (instances (n, cap) int32,
+        lengths (n, cap), tally, counters).  opts.mode picks the history or
+        the event kernel; an event-mode work buffer is allocated unless given."""
         opts = opts if opts is not None else default_opts(**kw)
         if n > 0:
             _need(particles, "trace particles", self.device, self.particle_bytes(n))
@@ -327,9 +334,26 @@ class Geometry:
         ln = torch.empty(n * cap, dtype=torch.float64, device=self.device)
         tally = torch.zeros(self.n_inst, dtype=torch.int64, device=self.device)
         cnt = torch.zeros(NCOUNTERS, dtype=torch.int64, device=self.device)
+        wp, wlen = self._work_arg(work, self.work_bytes(n, opts), "trace work")
         _check(self.lib, self.lib.trk_trace(self.h, _ptr(particles), n, cap, _ptr(inst), _ptr(ln), _ptr(tally),
-                                            _ptr(cnt), ctypes.byref(opts), _stream(stream)))
+                                            _ptr(cnt), wp, wlen, ctypes.byref(opts), _stream(stream)))
         return inst.view(n, cap), ln.view(n, cap), tally, cnt
+
+    def _work_arg(self, work, need: int, what: str):
+        """(256-byte aligned pointer, usable bytes) of a caller work tensor,
+        allocating one of `need` bytes when none is given and need > 0."""
+        if work is None:
+            if not need:
+                return None, 0
+            work = torch.empty(need + 256, dtype=torch.uint8, device=self.device)
+        _need(work, what, self.device)
+        off = (-work.data_ptr()) % 256
+        have = work.numel() * work.element_size() - off
+        if have < need:
+            raise TrkError(-4, f"{what}: {have} usable bytes after 256-byte alignment, need {need}")
+        # keep the buffer alive for the asynchronous launch
+        self._last_work = work
+        return ctypes.c_void_p(work.data_ptr() + off), have
 
     # -- transmission --------------------------------------------------------
     def transmission_fwd(self, rays, sigma, tracker=TRACKER_AUTO, lens: bool = True, stream=None):
@@ -342,18 +366,30 @@ class Geometry:
                                                    _ptr(T), _ptr(L), _stream(stream)))
         return T, L
 
-    def transmission_bwd(self, rays, sigma, pitch: float, gT, tracker=TRACKER_AUTO, stream=None):
+    def transmission_bwd_work_bytes(self, n: int) -> int:
+        b = ctypes.c_size_t(0)
+        _check(self.lib, self.lib.transmission_bwd_work_bytes(self.h, n, ctypes.byref(b)))
+        return b.value
+
+    def transmission_bwd(self, rays, sigma, pitch: float, gT, tracker=TRACKER_AUTO, stream=None, work=None,
+                         grad=None):
+        """dL/dtheta (n_materials + 4) from dL/dT per ray.  work: a caller
+        device buffer of transmission_bwd_work_bytes bytes reused across
+        calls (allocated per call when None); grad: the output tensor."""
         rays = _need(rays.contiguous(), "transmission_bwd rays", self.device, 0, _F64, cols=6)
         n = rays.shape[0]
         sigma = _need(sigma.contiguous(), "transmission_bwd sigma", self.device, 8 * self.n_mat, _F64)
         gT = _need(gT.contiguous(), "transmission_bwd gT", self.device, 8 * n, _F64)
-        b = ctypes.c_size_t(0)
-        _check(self.lib, self.lib.transmission_bwd_work_bytes(self.h, n, ctypes.byref(b)))
-        work = torch.empty(max(b.value, 8), dtype=torch.uint8, device=self.device)
-        grad = torch.empty(self.n_mat + NGEOM_PARAMS, dtype=torch.float64, device=self.device)
+        need = max(self.transmission_bwd_work_bytes(n), 8)
+        if work is None:
+            work = torch.empty(need, dtype=torch.uint8, device=self.device)
+        _need(work, "transmission_bwd work", self.device, need)
+        if grad is None:
+            grad = torch.empty(self.n_mat + NGEOM_PARAMS, dtype=torch.float64, device=self.device)
+        _need(grad, "transmission_bwd grad", self.device, 8 * (self.n_mat + NGEOM_PARAMS), _F64)
         _check(self.lib, self.lib.transmission_bwd(self.h, tracker, n, _ptr(rays), _ptr(sigma),
                                                    float(pitch), _ptr(gT), _ptr(grad), _ptr(work),
-                                                   work.numel(), _stream(stream)))
+                                                   work.numel() * work.element_size(), _stream(stream)))
         return grad
 
 
@@ -445,8 +481,11 @@ def transmission_bwd_noalloc(geom: "Geometry", rays, sigma, pitch: float, gT, gr
     _need(sigma, "transmission_bwd_noalloc sigma", geom.device, 8 * geom.n_mat, _F64)
     _need(gT, "transmission_bwd_noalloc gT", geom.device, 8 * rays.shape[0], _F64)
     _need(grad_out, "transmission_bwd_noalloc grad_out", geom.device, 8 * (geom.n_mat + NGEOM_PARAMS), _F64)
-    _check(geom.lib, geom.lib.transmission_bwd_noalloc(geom.h, tracker, rays.shape[0], _ptr(rays), _ptr(sigma),
-                                                       float(pitch), _ptr(gT), _ptr(grad_out), _stream(stream)))
+    # the fixed scratch array is looked up on the current device: make it the
+    # geometry's
+    with torch.cuda.device(rays.device):
+        _check(geom.lib, geom.lib.transmission_bwd_noalloc(geom.h, tracker, rays.shape[0], _ptr(rays), _ptr(sigma),
+                                                           float(pitch), _ptr(gT), _ptr(grad_out), _stream(stream)))
     return grad_out
 
 
