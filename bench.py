@@ -734,12 +734,15 @@ def run_power(N, I, dev, stream, barrier, steps, plain_hist_per_s):
                           queue_depth=EVENT_SLOTS)
     tally = torch.zeros(g.n_inst, dtype=torch.int64, device=dev)
     cnt = torch.zeros(N.NCOUNTERS, dtype=torch.int64, device=dev)
-    k, bank, _, _ = g.power_iteration(n, inactive, cycles, tally=tally, counters=cnt, opts=opts, stream=stream)
+    work = torch.empty(g.power_iteration_work_bytes(n, opts) + 256, dtype=torch.uint8, device=dev)
+    k, bank, _, _ = g.power_iteration(n, inactive, cycles, tally=tally, counters=cnt, opts=opts, stream=stream,
+                                      work=work)
     barrier()
     a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
     for _ in range(steps):
-        k, bank, _, _ = g.power_iteration(n, inactive, cycles, tally=tally, counters=cnt, opts=opts, stream=stream)
+        k, bank, _, _ = g.power_iteration(n, inactive, cycles, tally=tally, counters=cnt, opts=opts, stream=stream,
+                                          work=work)
     e.record(stream)
     barrier()
     ms = a.elapsed_time(e)
@@ -747,7 +750,7 @@ def run_power(N, I, dev, stream, barrier, steps, plain_hist_per_s):
     st = int(cnt.cpu().numpy().view(np.uint64)[N.K["status"]])
     hps = steps * n * cycles / (ms / 1e3)
     return {"workload": "main workload, fuel nu = 2.4, 2e6 histories per cycle, 2 inactive + 6 active cycles "
-                        "per step, BVH-CSG, event kernel, FP64 (includes the work buffer allocation per call)",
+                        "per step, BVH-CSG, event kernel, FP64 (one work buffer reused by every call)",
             "histories_per_s": hps, "ms_per_cycle": ms / (steps * cycles),
             "over_plain_run": hps / plain_hist_per_s,
             "k_per_cycle": [float(x) for x in kk], "k_active_mean": float(kk[inactive:].mean()),
@@ -765,9 +768,10 @@ def run_config5(N, I, dev, stream, barrier, steps):
     sigma = torch.tensor(desc["sigma"], dtype=torch.float64, device=dev)
     gT = torch.ones(R.shape[0], dtype=torch.float64, device=dev)
     pitch = 1.26
+    work = torch.empty(max(8, g.transmission_bwd_work_bytes(R.shape[0])), dtype=torch.uint8, device=dev)
     for _ in range(2):
         T, _ = g.transmission_fwd(R, sigma, lens=False)
-        g.transmission_bwd(R, sigma, pitch, gT)
+        g.transmission_bwd(R, sigma, pitch, gT, work=work)
     barrier()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     fwd = bwd = 0.0
@@ -775,7 +779,7 @@ def run_config5(N, I, dev, stream, barrier, steps):
         ev[0].record(stream)
         T, _ = g.transmission_fwd(R, sigma, lens=False)
         ev[1].record(stream)
-        g.transmission_bwd(R, sigma, pitch, gT)
+        g.transmission_bwd(R, sigma, pitch, gT, work=work)
         ev[2].record(stream)
         barrier()
         fwd += ev[0].elapsed_time(ev[1])

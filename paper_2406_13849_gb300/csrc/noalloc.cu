@@ -18,7 +18,10 @@
 //    on one stream, or use transmission_bwd with separate work buffers;
 //  - the first call on a device looks up the array's device address (once
 //    per device, with that device current); make that first call before
-//    any stream capture.
+//    any stream capture.  The address is kept for the life of the process:
+//    after cudaDeviceReset (or a release of the device's primary context)
+//    the module is loaded again elsewhere, so do not call this entry point
+//    on a device that has been reset.
 // The partial sums are written in full before they are read, so nothing in
 // the array needs clearing between calls.
 #include <cstdint>
