@@ -40,6 +40,9 @@ SEED = 1
 CPU_SAMPLE = 4_000_000
 CPU_SAMPLE_ONE_CORE = 200_000
 EVENT_SLOTS = 512
+# near-surface comparison of the benchmarked launch with the oracle
+NEAR_RULE_SAMPLE = 300
+TRACE_CAP = 96
 # DRAM bytes (read + write) per segment of the dominant kernel, from one ncu
 # capture of the same kernel on the same geometry with 3e6 particles
 # (41.24 GB over 82,931,315 segments); scaled to a full launch by its
@@ -115,8 +118,13 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU oracle baseline (bounded sample)
 # ---------------------------------------------------------------------------
-def cpu_baseline(desc_json: str, n: int, n_one: int, first_id: int = 0) -> dict:
-    """The oracle on all host cores (n particles) and on one core (n_one)."""
+def cpu_baseline(desc_json: str, n: int, n_one: int, first_id: int = 0, traced=None) -> dict:
+    """The oracle on all host cores (n particles) and on one core (n_one).
+
+    traced: optional (particle ids, instance rows, length rows, cap) from the
+    benchmarked event kernel's segment log; after the timing, those particles
+    are compared one by one with the oracle under the near-surface rule
+    (oracle.compare) and the counts are returned under "near_surface_rule"."""
     import oracle as O
     g = O.Geometry(desc_json, O.MODE_CSG)
     cores = host_cores()
@@ -128,11 +136,21 @@ def cpu_baseline(desc_json: str, n: int, n_one: int, first_id: int = 0) -> dict:
     r1 = g.run(n_one, SEED, P_ABSORB, first_id=first_id, threads=1, records=False)
     dt1 = time.perf_counter() - t0
     seg1 = int(r1["counters"][O.K_SEGMENTS])
-    return {"value": seg / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "one_core": seg1 / dt1,
-            "sample": f"{n} particles (ids {first_id}..{first_id + n - 1}) of the same workload, CSG-mode "
-                      f"oracle, {seg} segments in {dt:.2f} s on {cores} threads; one core: {n_one} particles, "
-                      f"{seg1} segments in {dt1:.2f} s"}
+    out = {"value": seg / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "one_core": seg1 / dt1,
+           "sample": f"{n} particles (ids {first_id}..{first_id + n - 1}) of the same workload, CSG-mode "
+                     f"oracle, {seg} segments in {dt:.2f} s on {cores} threads; one core: {n_one} particles, "
+                     f"{seg1} segments in {dt1:.2f} s"}
+    if traced is not None:
+        from oracle import compare as C
+        ids, rows_i, rows_l, cap = traced
+        res = C.compare_traces(g, ids, rows_i, rows_l, SEED, P_ABSORB, cap)
+        out["near_surface_rule"] = {
+            "compared": res["compared"], "matched": res["matched"], "near_surface": len(res["near_surface"]),
+            "drift": len(res["drift"]), "failed": len(res["failed"]),
+            "segments_matched": res["segments_compared"], "max_rel_matched": res["max_rel_matched"],
+            "findings": (res["near_surface"] + res["drift"] + res["failed"])[:10]}
+    return out
 
 
 def flops_per_segment(desc_json: str) -> dict:
@@ -449,9 +467,33 @@ def main() -> None:
     power = run_power(N, I, dev, stream, barrier, 2, n * args.steps / (main_run["ms"] / 1e3))
 
     cpu = None
+    near_rule = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(desc, CPU_SAMPLE, CPU_SAMPLE_ONE_CORE)
+        # the benchmarked launch (fast build, event kernel, CSG, queue depth
+        # 512, all particles) with its segment log on: a sample of particles
+        # is compared with the oracle under the near-surface rule
+        def traced_sample():
+            import numpy as np
+            g.source_init(n, seed=SEED, first_id=first_id, out=parts)
+            inst, ln, _, _ = g.trace(parts, n, TRACE_CAP, opts=make_opts(N.TRACKER_CSG, N.MODE_EVENT),
+                                     work=work_for(make_opts(N.TRACKER_CSG, N.MODE_EVENT)))
+            ids = np.sort(np.random.default_rng(23).choice(n, NEAR_RULE_SAMPLE, replace=False))
+            r = torch.from_numpy(ids).to(dev)
+            rows = (inst[r].cpu().numpy(), ln[r].cpu().numpy())
+            del inst, ln
+            torch.cuda.empty_cache()
+            return (ids + first_id, rows[0], rows[1], TRACE_CAP)
+        traced = _guarded(traced_sample)
+        cpu = cpu_baseline(desc, CPU_SAMPLE, CPU_SAMPLE_ONE_CORE,
+                           traced=traced if isinstance(traced, tuple) else None)
         cpu["gpu_core_equivalents"] = value / cpu["one_core"]
+        near_rule = cpu.pop("near_surface_rule", traced if isinstance(traced, dict) else None)
+        if isinstance(near_rule, dict) and "compared" in near_rule:
+            near_rule["sample"] = (f"{NEAR_RULE_SAMPLE} particles drawn from the benchmarked launch ({n} particles, "
+                                   f"fast build, event kernel, BVH-CSG, queue depth {EVENT_SLOTS}) traced to "
+                                   f"{TRACE_CAP} segments each, compared one by one with the oracle")
+            near_rule["rule"] = ("instances equal and lengths within 1e-12 relative or the propagated rounding "
+                                 "bound; else the first mismatch within 1e-9 cm of the deciding surface")
 
     if rank == 0:
         line = {
@@ -468,6 +510,7 @@ def main() -> None:
             "gpu_launches": 2 * args.steps,
             "roofline": roofline,
             "cpu_baseline": cpu,
+            "fast_build_near_surface_mismatches": near_rule,
             "variants": {
                 "csg_fp64_event": rate(main_run),
                 "rect_fp64_event": rate(rect_ev),

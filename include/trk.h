@@ -269,17 +269,26 @@ trk_status trk_trace(trk_geom_t g, const void* dev_particles, int64_t n, int32_t
  * distance; a tie goes to the top-most level, then to the first candidate
  * in the level's order).  The point is taken as on no surface.
  *   tracker    TRK_TRACKER_RECT, _CSG, _AUTO or _DP
+ *   precision  TRK_FP64, or TRK_FP32_LOCAL: the distance the FP32-local
+ *              flight takes (fast build; array or CSG tracker): FP32 in the
+ *              level frames, a plane crossing re-evaluated in FP64, a close
+ *              call (two candidates within 2e-5 relative) or an
+ *              ill-conditioned cylinder redone by the FP64 scan
  *   dev_xyz    double[3n], global positions (x, y, z per point)
  *   dev_dir    double[3n], unit directions
  *   dev_dist   out double[n]: the distance in cm (+inf: no boundary ahead;
  *              NaN: the point is in no cell)
  *   dev_level  out int32[n] or NULL: level of the winning surface (-1: none)
  *   dev_inst   out int64[n] or NULL: leaf cell instance (-1: in no cell)
- * Errors: TRK_E_INVALID (bad handle, null buffers, n < 0, unknown tracker),
- * TRK_E_UNSUPPORTED (array tracker unavailable), TRK_E_CUDA.
+ *   dev_close  out int32[n] or NULL: 1 where the FP32-local distance was
+ *              redone in FP64, else 0
+ * Errors: TRK_E_INVALID (bad handle, null buffers, n < 0, unknown tracker or
+ * precision), TRK_E_UNSUPPORTED (array tracker unavailable; FP32-local in
+ * the exact build or with the DP tracker), TRK_E_CUDA.
  */
-trk_status trk_distance_to_surface(trk_geom_t g, int tracker, int64_t n, const double* dev_xyz, const double* dev_dir,
-                                   double* dev_dist, int32_t* dev_level, int64_t* dev_inst, void* stream);
+trk_status trk_distance_to_surface(trk_geom_t g, int tracker, int precision, int64_t n, const double* dev_xyz,
+                                   const double* dev_dir, double* dev_dist, int32_t* dev_level, int64_t* dev_inst,
+                                   int32_t* dev_close, void* stream);
 
 /* trk_sync_status - synchronises `stream` and returns the first kernel-level
  * status a launch wrote to dev_counters[TRK_K_STATUS] (TRK_OK if none), the
@@ -388,7 +397,7 @@ trk_status batch_autotune(trk_batch_t b, void* dev_work, size_t work_bytes, trk_
  *   cudaDeviceReset.  All calls share the array: calls whose kernels overlap
  *   on the GPU race on it.
  * Errors: TRK_E_NOMEM when n needs more scratch than the array holds (about
- * 5.5 million rays with 8 materials; the message gives this geometry's
+ * 44 million rays with 8 materials; the message gives this geometry's
  * limit), TRK_E_INVALID, TRK_E_CUDA, and those of transmission_bwd.
  */
 trk_status transmission_bwd_noalloc(trk_geom_t g, int tracker, int64_t n, const double* dev_rays,

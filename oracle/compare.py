@@ -197,15 +197,22 @@ def compare_traces(o, pids, g_inst: np.ndarray, g_len: np.ndarray, seed: int, p_
 
 def classify_distances(o, xyz, dirs, d_oracle, lev_oracle, d_gpu, lev_gpu) -> dict:
     """Per-point distance_to_surface of the fast build against the oracle:
-    distances within 1e-12 relative (to max(1, d)) and the same winning
-    level, or else the oracle shows a near-tie or a near-tangency: the hit
-    point d_oracle along the ray lies within NEAR of a second surface, or the
-    ray passes within NEAR of a cylinder's tangency on its way there.  The
-    start point carries no propagated error, so no drift is allowed here."""
+    distances within 1e-12 relative to the coordinates' size (max(1 cm, d,
+    the point's largest coordinate): a distance computed from coordinates of
+    size |x| cannot be more accurate than their rounding, ~1e-16 |x|, times
+    the formula's conditioning) and the same winning level, or else the
+    oracle shows the distance is decided near a surface:
+    the start point lies within NEAR of a surface (its distance to it is then
+    a difference of nearly equal squares, as ill-conditioned as a decision
+    there), the hit point d_oracle along the ray lies within NEAR of a second
+    surface (a near-tie), or the ray passes within NEAR of a cylinder's
+    tangency on its way there.  The start point carries no propagated error,
+    so no drift is allowed here."""
     inside = np.isfinite(d_oracle) | np.isfinite(d_gpu)
     rel = np.zeros(len(d_oracle))
     both = np.isfinite(d_oracle) & np.isfinite(d_gpu)
-    rel[both] = np.abs(d_gpu[both] - d_oracle[both]) / np.maximum(1.0, np.abs(d_oracle[both]))
+    scale = np.maximum(np.maximum(1.0, np.abs(d_oracle)), np.abs(xyz).max(axis=1)) if len(xyz) else np.ones(0)
+    rel[both] = np.abs(d_gpu[both] - d_oracle[both]) / scale[both]
     bad = inside & ((~both) | (rel > REL) | (lev_gpu != lev_oracle))
     idx = np.nonzero(bad)[0]
     res = {"points": int(inside.sum()), "outside_bar": len(idx), "near": [], "failed": [],
@@ -218,7 +225,7 @@ def classify_distances(o, xyz, dirs, d_oracle, lev_oracle, d_gpu, lev_gpu) -> di
         hit = xyz[idx] + far[:, None] * dirs[idx]
         cl_hit = o.clearance(hit, dirs[idx], np.zeros(len(idx)))
         for k, i in enumerate(idx):
-            margin = min(float(cl_hit[k, 1]), float(cl[k, 4]))
+            margin = min(float(cl[k, 0]), float(cl_hit[k, 1]), float(cl[k, 4]))
             rec = {"point": int(i), "margin_cm": margin, "rel": float(rel[i]),
                    "level": (int(lev_oracle[i]), int(lev_gpu[i]))}
             (res["near"] if margin < NEAR else res["failed"]).append(rec)

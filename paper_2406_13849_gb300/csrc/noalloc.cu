@@ -4,14 +4,14 @@
 // whose device memory is handed out entirely by another framework's
 // allocator, or a tight loop that cannot pay for cudaMalloc's implicit
 // device synchronisation.  For them this file keeps the backward pass's
-// scratch (one row of partial gradient sums per 128-ray block) in a
+// scratch (one row of partial gradient sums per 1024-ray block) in a
 // fixed-size array that lives in the library's own device image.  The
 // caller still provides the rays, sigma, dL/dT and the gradient output.
 //
 // Costs and limits, stated for users:
 //  - every GPU that loads the library holds NOALLOC_SCRATCH_BYTES for this
 //    array until the process exits;
-//  - n is limited so that the partial sums fit in the array (about 5.5
+//  - n is limited so that the partial sums fit in the array (about 44
 //    million rays with 8 materials; more with fewer materials);
 //  - all calls share the array: two calls whose kernels overlap on the GPU
 //    (different streams, no ordering between them) race on it.  Order them
@@ -29,6 +29,7 @@
 
 #include "trk.h"
 #include "trk_internal.h"
+#include "trk_launch.h"
 
 namespace {
 
@@ -72,7 +73,7 @@ trk_status transmission_bwd_noalloc(trk_geom_t g, int tracker, int64_t n, const 
     if (st != TRK_OK) return st;
     if (need > NOALLOC_SCRATCH_BYTES) {
         const long long per_block = (long long)(g->n_mat + TRK_NGEOM_PARAMS) * 8;
-        const long long max_rays = (long long)(NOALLOC_SCRATCH_BYTES / size_t(per_block)) * 128;
+        const long long max_rays = (long long)(NOALLOC_SCRATCH_BYTES / size_t(per_block)) * trk::TRK_RAYS_PER_BLOCK;
         return trk_status(trk::set_error(TRK_E_NOMEM,
                                          "transmission_bwd_noalloc: %lld rays need %zu scratch bytes, the fixed array "
                                          "holds %zu (at most %lld rays for this geometry); use transmission_bwd",

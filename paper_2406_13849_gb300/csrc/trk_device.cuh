@@ -997,19 +997,45 @@ __device__ __forceinline__ float surface_distance_f(const DevGeom& g, int s, int
     return t < 0.f ? 0.f : t;
 }
 
+// Candidates whose FP32 evaluation would work with a coordinate or a face
+// offset above F32_EXTENT cm (a tall lattice's z faces, a core-size
+// cylinder) are evaluated in FP64 instead: FP32 keeps its 1e-5 relative
+// accuracy only where the frame coordinates are small.
+constexpr float F32_EXTENT = 16.0f;
+// max(|x|, |y|, |z|) > F32_EXTENT, by integer compares of the magnitudes' bits
+__device__ __forceinline__ bool beyond_f32_extent(double x, double y, double z) {
+    const long long m = 0x7fffffffffffffffLL, c = __double_as_longlong(double(F32_EXTENT));
+    return (dbits(x) & m) > c || (dbits(y) & m) > c || (dbits(z) & m) > c;
+}
+
 struct Best2 {
     float d1, d2;
     bool ill;
+    bool xact;           // the winner was evaluated in FP64 (its length in tx)
     Hit h;
     double wx, wy, wz;   // FP64 coordinates of the winner's level frame
+    double tx;
     __device__ __forceinline__ void offer(float t, int level, int surf, int side, int dim, int dsign, int entry,
                                           double x, double y, double z) {
         if (t < d1) {
             d2 = d1; d1 = t;
             h.level = level; h.surf = surf; h.side = side; h.dim = dim; h.dsign = dsign; h.entry = entry;
             wx = x; wy = y; wz = z;
+            xact = false;
         } else if (t < d2) {
             d2 = t;
+        }
+    }
+    // a candidate evaluated in FP64
+    __device__ __forceinline__ void offer64(double t, int level, int surf, int side, int dim, int dsign, int entry,
+                                            double x, double y, double z) {
+        const float tf = d_finite_lt_inf(t) ? float(t) : FINF;
+        if (tf < d1) {
+            offer(tf, level, surf, side, dim, dsign, entry, x, y, z);
+            xact = true;
+            tx = t;
+        } else if (tf < d2) {
+            d2 = tf;
         }
     }
 };
@@ -1017,7 +1043,7 @@ struct Best2 {
 template <bool CSG>
 __device__ __forceinline__ Best2 distance_f32(const DevGeom& g, const St& s, const DirF& df) {
     Best2 b;
-    b.d1 = FINF; b.d2 = FINF; b.ill = false; b.wx = b.wy = b.wz = 0.0;
+    b.d1 = FINF; b.d2 = FINF; b.ill = false; b.xact = false; b.wx = b.wy = b.wz = 0.0; b.tx = 0.0;
     b.h.d = DINF; b.h.level = -1; b.h.surf = -1; b.h.side = 0; b.h.dim = -1; b.h.dsign = 0; b.h.entry = -1;
     double x = s.x, y = s.y, z = s.z;
     const float d3[3] = {df.u, df.v, df.w};
@@ -1035,18 +1061,19 @@ __device__ __forceinline__ Best2 distance_f32(const DevGeom& g, const St& s, con
             const int o3[3] = {of.x, of.y, of.z};
             const int i3[3] = {L.i, L.j, L.k};
             const float e3[3] = {float(xn), float(yn), float(zn)};
+            const double p3[3] = {x, y, z};
+            const double w3[3] = {s.d.iu, s.d.iv, s.d.iw};
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                if (d3[d] > 0.f) {
-                    if (i3[d] < n3[d] - 1 || l == 0) {
-                        float t = (__ldg(g.l_hif + o3[d] + i3[d]) - e3[d]) * v3[d];
-                        b.offer(t < 0.f ? 0.f : t, l, -1 - (2 * d + 1), 0, d, 1, -1, x, y, z);
-                    }
-                } else if (d3[d] < 0.f) {
-                    if (i3[d] > 0 || l == 0) {
-                        float t = (__ldg(g.l_lof + o3[d] + i3[d]) - e3[d]) * v3[d];
-                        b.offer(t < 0.f ? 0.f : t, l, -1 - (2 * d), 0, d, -1, -1, x, y, z);
-                    }
+                const bool up = d3[d] > 0.f;
+                if (!(up ? (i3[d] < n3[d] - 1 || l == 0) : (d3[d] < 0.f && (i3[d] > 0 || l == 0)))) continue;
+                const float fo = __ldg((up ? g.l_hif : g.l_lof) + o3[d] + i3[d]);
+                if (fabsf(fo) > F32_EXTENT) {
+                    double t = (__ldg(g.l_grid + o3[d] + i3[d] + (up ? 1 : 0)) - p3[d]) * w3[d];
+                    b.offer64(d_lt0(t) ? 0.0 : t, l, -1 - (2 * d + (up ? 1 : 0)), 0, d, up ? 1 : -1, -1, x, y, z);
+                } else {
+                    const float t = (fo - e3[d]) * v3[d];
+                    b.offer(t < 0.f ? 0.f : t, l, -1 - (2 * d + (up ? 1 : 0)), 0, d, up ? 1 : -1, -1, x, y, z);
                 }
             }
         } else {
@@ -1058,6 +1085,8 @@ __device__ __forceinline__ Best2 distance_f32(const DevGeom& g, const St& s, con
                 const int lo3[3] = {s0.x, s0.z, s1.x};
                 const int hi3[3] = {s0.y, s0.w, s1.y};
                 const float e3[3] = {float(xn), float(yn), float(zn)};
+                const double p3[3] = {x, y, z};
+                const double w3[3] = {s.d.iu, s.d.iv, s.d.iw};
                 const float* fs = g.c_slabf + 6 * L.cell;
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
@@ -1066,10 +1095,37 @@ __device__ __forceinline__ Best2 distance_f32(const DevGeom& g, const St& s, con
                     if (e < 0) continue;
                     const int sid = cs_surface(__ldg(g.cs + e));
                     if (s.on_lev == l && s.on_surf == sid) continue;
-                    const float t = (__ldg(fs + 2 * d + (up ? 1 : 0)) - e3[d]) * v3[d];
-                    b.offer(t < 0.f ? 0.f : t, l, sid, up ? -1 : 1, -1, 0, e, x, y, z);
+                    const float fo = __ldg(fs + 2 * d + (up ? 1 : 0));
+                    if (fabsf(fo) > F32_EXTENT) {
+                        const double t = (__ldg(g.s_coef + 4 * sid) - p3[d]) * w3[d];
+                        b.offer64(d_lt0(t) ? 0.0 : t, l, sid, up ? -1 : 1, -1, 0, e, x, y, z);
+                    } else {
+                        const float t = (fo - e3[d]) * v3[d];
+                        b.offer(t < 0.f ? 0.f : t, l, sid, up ? -1 : 1, -1, 0, e, x, y, z);
+                    }
                 }
-                if (rg.y & CS_PAIR_FLAG) {
+                // general planes and the remaining surfaces are measured in the
+                // universe's frame: FP64 where it is large
+                const bool big = beyond_f32_extent(x, y, z);
+                if ((rg.y & CS_PAIR_FLAG) && big) {
+                    const int4 p0 = __ldg(g.c_pair + 2 * L.cell), p1 = __ldg(g.c_pair + 2 * L.cell + 1);
+                    const int lo3p[3] = {p0.x, p0.z, p1.x};
+                    const int hi3p[3] = {p0.y, p0.w, p1.y};
+#pragma unroll
+                    for (int f = 0; f < 3; ++f) {
+                        const int ea = lo3p[f] >= 0 ? lo3p[f] : hi3p[f];
+                        if (ea < 0) continue;
+                        double c0, c1, c2, c3;
+                        load_coef(g, cs_surface(__ldg(g.cs + ea)), c0, c1, c2, c3);
+                        const double den = (c0 * s.d.u + c1 * s.d.v) + c2 * s.d.w;
+                        const int e = d_lt0(den) ? lo3p[f] : (d_gt0(den) ? hi3p[f] : -1);
+                        if (e < 0) continue;
+                        const int sid = cs_surface(__ldg(g.cs + e));
+                        if (s.on_lev == l && s.on_surf == sid) continue;
+                        const double t = (__ldg(g.s_coef + 4 * sid + 3) - ((c0 * x + c1 * y) + c2 * z)) / den;
+                        b.offer64(d_lt0(t) ? 0.0 : t, l, sid, d_lt0(den) ? 1 : -1, -1, 0, e, x, y, z);
+                    }
+                } else if (rg.y & CS_PAIR_FLAG) {
                     const float xf = float(x), yf = float(y), zf = float(z);
                     const int4 p0 = __ldg(g.c_pair + 2 * L.cell), p1 = __ldg(g.c_pair + 2 * L.cell + 1);
                     const int lo3p[3] = {p0.x, p0.z, p1.x};
@@ -1093,14 +1149,20 @@ __device__ __forceinline__ Best2 distance_f32(const DevGeom& g, const St& s, con
                 first = rr.x; cnt = rr.y; by_index = true;
             }
             if (cnt > 0) {
+                const bool big = beyond_f32_extent(x, y, z);
                 const float xf = float(x), yf = float(y), zf = float(z);
                 for (int k = 0; k < cnt; ++k) {
                     const int ei = by_index ? __ldg(g.rest_e + first + k) : first + k;
                     const int e = __ldg(g.cs + ei);
                     const int sid = cs_surface(e), side = cs_side(e);
                     const bool on = (s.on_lev == l && s.on_surf == sid);
-                    const float t = surface_distance_f(g, sid, cs_type(e), side, on, xf, yf, zf, df, b.ill);
-                    b.offer(t, l, sid, side, -1, 0, ei, x, y, z);
+                    if (big) {
+                        b.offer64(surface_distance(g, sid, cs_type(e), side, on, x, y, z, s.d), l, sid, side, -1, 0,
+                                  ei, x, y, z);
+                    } else {
+                        const float t = surface_distance_f(g, sid, cs_type(e), side, on, xf, yf, zf, df, b.ill);
+                        b.offer(t, l, sid, side, -1, 0, ei, x, y, z);
+                    }
                 }
             }
         }
@@ -1481,6 +1543,49 @@ __device__ __forceinline__ int step_flight(const DevGeom& g, St& s, Hit& h, Ctx&
     return A_COLLIDE;
 }
 
+// Length of an FP32-local crossing.  A plane crossing is re-evaluated in
+// FP64 from the FP64 frame coordinates (the same arithmetic as the FP64
+// path), so the particle lands on the plane and the array and universe
+// searches that follow see what they would in FP64 (exact = true).  Cylinder
+// crossings keep the FP32 length: only small linear cell scans follow them.
+__device__ __forceinline__ double f32_crossing_length(const DevGeom& g, const St& s, const Best2& b, bool& exact) {
+    const Hit& h = b.h;
+    if (b.xact) { exact = true; return b.tx; }
+    double t = 0.0;
+    bool plane = false;
+    if (h.surf < 0) {
+        int lat = 0, idx = 0;
+#pragma unroll
+        for (int l = 0; l < MAXL; ++l)
+            if (l == h.level) {
+                lat = __ldg(g.u_info + s.lv[l].u).w;
+                idx = h.dim == 0 ? s.lv[l].i : (h.dim == 1 ? s.lv[l].j : s.lv[l].k);
+            }
+        const int4 of = __ldg(g.l_off + lat);
+        const int go = h.dim == 0 ? of.x : (h.dim == 1 ? of.y : of.z);
+        const double gv = __ldg(g.l_grid + go + idx + (h.dsign > 0 ? 1 : 0));
+        const double pv = h.dim == 0 ? b.wx : (h.dim == 1 ? b.wy : b.wz);
+        const double iv = h.dim == 0 ? s.d.iu : (h.dim == 1 ? s.d.iv : s.d.iw);
+        t = (gv - pv) * iv;
+        plane = true;
+    } else {
+        const int type = __ldg(g.s_info + h.surf) & 15;
+        if (type <= S_PZ) {
+            const double gv = __ldg(g.s_coef + 4 * h.surf);
+            const double pv = type == S_PX ? b.wx : (type == S_PY ? b.wy : b.wz);
+            const double iv = type == S_PX ? s.d.iu : (type == S_PY ? s.d.iv : s.d.iw);
+            t = (gv - pv) * iv;
+            plane = true;
+        } else if (type == S_P) {
+            t = surface_distance(g, h.surf, type, h.side, false, b.wx, b.wy, b.wz, s.d);
+            plane = true;
+        }
+    }
+    exact = plane;
+    if (!plane) return double(b.d1);
+    return d_lt0(t) ? 0.0 : t;
+}
+
 // FP32-local flight: distances and the flight decision in FP32, position
 // and tau in FP64; close calls are redone by the FP64 step.
 template <bool CSG, int FLAGS>
@@ -1501,48 +1606,7 @@ __device__ __forceinline__ int step_flight_f32(const DevGeom& g, St& s, Hit& h, 
     const float lenf = crossing ? b.d1 : dcf;
     double len = double(lenf);
     bool exact_len = false;
-    if (crossing) {
-        // A plane crossing is re-evaluated in FP64 from the FP64 frame
-        // coordinates (the same arithmetic as the FP64 path), so the particle
-        // lands on the plane and the array and universe searches that follow
-        // see what they would in FP64.  Cylinder crossings keep the FP32
-        // length: only small linear cell scans follow them.
-        double t = 0.0;
-        bool plane = false;
-        if (h.surf < 0) {
-            int lat = 0, idx = 0;
-#pragma unroll
-            for (int l = 0; l < MAXL; ++l)
-                if (l == h.level) {
-                    lat = __ldg(g.u_info + s.lv[l].u).w;
-                    idx = h.dim == 0 ? s.lv[l].i : (h.dim == 1 ? s.lv[l].j : s.lv[l].k);
-                }
-            const int4 of = __ldg(g.l_off + lat);
-            const int go = h.dim == 0 ? of.x : (h.dim == 1 ? of.y : of.z);
-            const double gv = __ldg(g.l_grid + go + idx + (h.dsign > 0 ? 1 : 0));
-            const double pv = h.dim == 0 ? b.wx : (h.dim == 1 ? b.wy : b.wz);
-            const double iv = h.dim == 0 ? s.d.iu : (h.dim == 1 ? s.d.iv : s.d.iw);
-            t = (gv - pv) * iv;
-            plane = true;
-        } else {
-            const int type = __ldg(g.s_info + h.surf) & 15;
-            if (type <= S_PZ) {
-                const double gv = __ldg(g.s_coef + 4 * h.surf);
-                const double pv = type == S_PX ? b.wx : (type == S_PY ? b.wy : b.wz);
-                const double iv = type == S_PX ? s.d.iu : (type == S_PY ? s.d.iv : s.d.iw);
-                t = (gv - pv) * iv;
-                plane = true;
-            } else if (type == S_P) {
-                t = surface_distance(g, h.surf, type, h.side, false, b.wx, b.wy, b.wz, s.d);
-                plane = true;
-            }
-        }
-        if (plane) {
-            if (d_lt0(t)) t = 0.0;
-            len = t;
-            exact_len = true;
-        }
-    }
+    if (crossing) len = f32_crossing_length(g, s, b, exact_len);
     const int inst = instance(s);
     bool stop_cut = false;
     if (FLAGS & F_CUT) {

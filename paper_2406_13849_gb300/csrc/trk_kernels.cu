@@ -183,11 +183,15 @@ __global__ void __launch_bounds__(128) k_find(const DevGeom g, long long n, cons
 }
 
 // distance_to_surface for points (diagnostic): find_cell from the root, then
-// the distance over the levels with the tracking kernels' tie rules.
-template <int TK>
+// the distance over the levels with the tracking kernels' tie rules.  F32:
+// the FP32-local flight's distance (FP32 in the level frames, plane
+// crossings re-evaluated in FP64, a close call or an ill-conditioned
+// cylinder redone by the FP64 scan; close[i] = 1 then).
+template <int TK, bool F32>
 __global__ void __launch_bounds__(128) k_distance(const DevGeom g, long long n, const double* __restrict__ xyz,
                                                   const double* __restrict__ dir, double* __restrict__ dist,
-                                                  int32_t* __restrict__ level, int64_t* __restrict__ inst) {
+                                                  int32_t* __restrict__ level, int64_t* __restrict__ inst,
+                                                  int32_t* __restrict__ close) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         St s;
@@ -198,17 +202,33 @@ __global__ void __launch_bounds__(128) k_distance(const DevGeom g, long long n, 
         s.tau = 0.0;
         s.lv[0].u = g.root;
         double d = __longlong_as_double(0x7ff8000000000000LL);
-        int lev = -1;
+        int lev = -1, cc = 0;
         long long in = -1;
         if (find_from<TK>(g, s, 0) == 0) {
-            const Hit h = distance_to_boundary<TK>(g, s);
-            d = h.d;
-            lev = h.level;
+            bool redo = true;
+            if constexpr (F32) {
+                const DirF df = dir_f32(s.d);
+                const Best2 b = distance_f32<TK == TK_CSG>(g, s, df);
+                if (!(b.ill || close_call(b.d1, b.d2)) && b.d1 < FINF) {
+                    bool exact;
+                    d = f32_crossing_length(g, s, b, exact);
+                    lev = b.h.level;
+                    redo = false;
+                } else {
+                    cc = 1;
+                }
+            }
+            if (redo) {
+                const Hit h = distance_to_boundary<TK>(g, s);
+                d = h.d;
+                lev = h.level;
+            }
             in = instance(s);
         }
         dist[i] = d;
         if (level) level[i] = lev;
         if (inst) inst[i] = in;
+        if (close) close[i] = cc;
     }
 }
 
@@ -270,102 +290,142 @@ __device__ __forceinline__ void hit_derivative(const DevGeom& g, const St& s, co
     }
 }
 
-// Walks one ray; accumulates per-material lengths and, for BWD, the
-// sigma-weighted derivative of the optical depth with respect to theta.
-template <bool CSG, bool BWD>
-__device__ __forceinline__ int walk_ray(const DevGeom& g, const double* ray, const double* sigma, double pitch,
-                                        double lens[MAXMAT], double dtau[NGP]) {
-#pragma unroll
-    for (int m = 0; m < MAXMAT; ++m) lens[m] = 0.0;
-#pragma unroll
-    for (int j = 0; j < NGP; ++j) dtau[j] = 0.0;
+// One ray's walk as a resumable state: the tracker state, per-material
+// lengths and, for BWD, the sigma-weighted derivative of the optical depth
+// with respect to theta (din: the derivative of the current segment's entry
+// point).  ray_start places the ray (find_cell); ray_step walks one segment
+// and returns false once the ray has left the geometry or ended otherwise.
+struct RayWalk {
     St s;
-    clear_levels(s);
-    s.x = ray[0]; s.y = ray[1]; s.z = ray[2];
-    s.d.u = ray[3]; s.d.v = ray[4]; s.d.w = ray[5];
-    s.tau = 0.0;
-    set_inverse(s.d);
-    s.lv[0].u = g.root;
-    if (find_from<CSG>(g, s, 0) != 0) return TRK_E_LOST;
-    double din[NGP] = {0.0, 0.0, 0.0, 0.0};
-    for (int seg = 0; seg < 10000000; ++seg) {
-        const Hit h = distance_to_boundary<CSG>(g, s);
-        if (!d_finite_lt_inf(h.d)) return TRK_E_LOST;
-        const int m = s.mat;
-#pragma unroll
-        for (int k = 0; k < MAXMAT; ++k)
-            if (k == m) lens[k] += h.d;
-        s.x = s.x + h.d * s.d.u;
-        s.y = s.y + h.d * s.d.v;
-        s.z = s.z + h.d * s.d.w;
-        if (BWD) {
-            double dout[NGP];
-            hit_derivative<CSG>(g, s, h, pitch, dout);
-            const double sg = __ldg(sigma + m);
-#pragma unroll
-            for (int j = 0; j < NGP; ++j) { dtau[j] += sg * (dout[j] - din[j]); din[j] = dout[j]; }
-        }
-        int fl;
-        int cr = cross_surface<CSG>(g, s, h, fl);
-        if (cr == CR_FIND) cr = find_from<CSG>(g, s, fl) == 0 ? CR_OK : CR_LOST;
-        if (cr == CR_ESCAPE) return TRK_P_ESCAPED;
-        if (cr == CR_LOST) return TRK_E_LOST;
-    }
-    return TRK_E_MAX_SEGMENTS;
-}
+    double lens[MAXMAT], dtau[NGP], din[NGP];
+    int nseg;
+};
 
 template <bool CSG>
-__global__ void __launch_bounds__(128) k_transmission(const DevGeom g, long long n, const double* __restrict__ rays,
-                                                      const double* __restrict__ sigma, double* __restrict__ T,
-                                                      double* __restrict__ lens_out) {
-    const long long stride = (long long)gridDim.x * blockDim.x;
+__device__ __forceinline__ bool ray_start(const DevGeom& g, const double* ray, RayWalk& r) {
+#pragma unroll
+    for (int m = 0; m < MAXMAT; ++m) r.lens[m] = 0.0;
+#pragma unroll
+    for (int j = 0; j < NGP; ++j) { r.dtau[j] = 0.0; r.din[j] = 0.0; }
+    r.nseg = 0;
+    clear_levels(r.s);
+    r.s.x = ray[0]; r.s.y = ray[1]; r.s.z = ray[2];
+    r.s.d.u = ray[3]; r.s.d.v = ray[4]; r.s.d.w = ray[5];
+    r.s.tau = 0.0;
+    set_inverse(r.s.d);
+    r.s.lv[0].u = g.root;
+    return find_from<CSG>(g, r.s, 0) == 0;
+}
+
+template <bool CSG, bool BWD>
+__device__ __forceinline__ bool ray_step(const DevGeom& g, const double* sigma, double pitch, RayWalk& r) {
+    St& s = r.s;
+    if (r.nseg >= 10000000) return false;
+    ++r.nseg;
+    const Hit h = distance_to_boundary<CSG>(g, s);
+    if (!d_finite_lt_inf(h.d)) return false;
+    const int m = s.mat;
+#pragma unroll
+    for (int k = 0; k < MAXMAT; ++k)
+        if (k == m) r.lens[k] += h.d;
+    s.x = s.x + h.d * s.d.u;
+    s.y = s.y + h.d * s.d.v;
+    s.z = s.z + h.d * s.d.w;
+    if (BWD) {
+        double dout[NGP];
+        hit_derivative<CSG>(g, s, h, pitch, dout);
+        const double sg = __ldg(sigma + m);
+#pragma unroll
+        for (int j = 0; j < NGP; ++j) { r.dtau[j] += sg * (dout[j] - r.din[j]); r.din[j] = dout[j]; }
+    }
+    int fl;
+    int cr = cross_surface<CSG>(g, s, h, fl);
+    if (cr == CR_FIND) cr = find_from<CSG>(g, s, fl) == 0 ? CR_OK : CR_LOST;
+    return cr != CR_ESCAPE && cr != CR_LOST;
+}
+
+// Rays per thread: each thread walks a fixed list of RAYS_PER_THREAD rays as
+// one loop (a lane whose ray ends starts its next one at once), so the lanes
+// of a warp stay busy until their lists run out instead of waiting for the
+// warp's longest ray; the lists are fixed, so the order of every sum is too.
+// Block b holds rays [b * RAY_TILE, (b + 1) * RAY_TILE), its thread t the
+// rays b * RAY_TILE + t + k * RAY_BLOCK, k < RAYS_PER_THREAD.
+constexpr int RAY_BLOCK = 128;
+constexpr int RAYS_PER_THREAD = 8;
+constexpr long long RAY_TILE = (long long)RAY_BLOCK * RAYS_PER_THREAD;
+static_assert(RAY_TILE == TRK_RAYS_PER_BLOCK, "the work-buffer layout assumes this tile");
+
+template <bool CSG>
+__global__ void __launch_bounds__(RAY_BLOCK) k_transmission(const DevGeom g, long long n, const double* __restrict__ rays,
+                                                            const double* __restrict__ sigma, double* __restrict__ T,
+                                                            double* __restrict__ lens_out) {
     const int nm = g.n_mat;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        double lens[MAXMAT], dtau[NGP];
-        walk_ray<CSG, false>(g, rays + 6 * i, sigma, 0.0, lens, dtau);
+    const long long base = (long long)blockIdx.x * RAY_TILE + threadIdx.x;
+    int k = 0;
+    long long i = base;
+    bool have = i < n;
+    RayWalk r;
+    bool live = have && ray_start<CSG>(g, rays + 6 * i, r);
+    while (have) {
+        if (live) live = ray_step<CSG, false>(g, sigma, 0.0, r);
+        if (live) continue;
         double opt = 0.0;
 #pragma unroll
         for (int m = 0; m < MAXMAT; ++m)
-            if (m < nm) opt += __ldg(sigma + m) * lens[m];
+            if (m < nm) opt += __ldg(sigma + m) * r.lens[m];
         T[i] = exp(-opt);
         if (lens_out) {
 #pragma unroll
             for (int m = 0; m < MAXMAT; ++m)
-                if (m < nm) lens_out[i * nm + m] = lens[m];
+                if (m < nm) lens_out[i * nm + m] = r.lens[m];
         }
+        ++k;
+        i = base + (long long)k * RAY_BLOCK;
+        have = k < RAYS_PER_THREAD && i < n;
+        live = have && ray_start<CSG>(g, rays + 6 * i, r);
     }
 }
 
-// Per block: sum over its rays of gT * dT/dtheta (fixed tree order) into
-// partial[block][nm + NGP]; a second kernel adds the partials in block order.
-constexpr int BWD_BLOCK = 128;
+// Per block: the sum over its rays of gT * dT/dtheta into
+// partial[block][nm + NGP] (each thread adds its rays in list order, then a
+// fixed tree over the block's threads); a second kernel adds the partials in
+// block order.
 template <bool CSG>
-__global__ void __launch_bounds__(BWD_BLOCK) k_transmission_bwd(const DevGeom g, long long n,
+__global__ void __launch_bounds__(RAY_BLOCK) k_transmission_bwd(const DevGeom g, long long n,
                                                                 const double* __restrict__ rays,
                                                                 const double* __restrict__ sigma, double pitch,
                                                                 const double* __restrict__ gT,
                                                                 double* __restrict__ partial) {
     const int nm = g.n_mat;
     const int nq = nm + NGP;
-    __shared__ double red[BWD_BLOCK];
+    __shared__ double red[RAY_BLOCK];
     double acc[MAXMAT + NGP];
 #pragma unroll
     for (int j = 0; j < MAXMAT + NGP; ++j) acc[j] = 0.0;
-    const long long i = (long long)blockIdx.x * BWD_BLOCK + threadIdx.x;
-    if (i < n) {
-        double lens[MAXMAT], dtau[NGP];
-        walk_ray<CSG, true>(g, rays + 6 * i, sigma, pitch, lens, dtau);
+    const long long base = (long long)blockIdx.x * RAY_TILE + threadIdx.x;
+    int k = 0;
+    long long i = base;
+    bool have = i < n;
+    RayWalk r;
+    bool live = have && ray_start<CSG>(g, rays + 6 * i, r);
+    while (have) {
+        if (live) live = ray_step<CSG, true>(g, sigma, pitch, r);
+        if (live) continue;
         double opt = 0.0;
 #pragma unroll
         for (int m = 0; m < MAXMAT; ++m)
-            if (m < nm) opt += __ldg(sigma + m) * lens[m];
+            if (m < nm) opt += __ldg(sigma + m) * r.lens[m];
         const double Tv = exp(-opt);
         const double gi = gT[i];
 #pragma unroll
         for (int m = 0; m < MAXMAT; ++m)
-            if (m < nm) acc[m] = gi * (-lens[m] * Tv);
+            if (m < nm) acc[m] += gi * (-r.lens[m] * Tv);
 #pragma unroll
-        for (int j = 0; j < NGP; ++j) acc[MAXMAT + j] = gi * (-Tv * dtau[j]);
+        for (int j = 0; j < NGP; ++j) acc[MAXMAT + j] += gi * (-Tv * r.dtau[j]);
+        ++k;
+        i = base + (long long)k * RAY_BLOCK;
+        have = k < RAYS_PER_THREAD && i < n;
+        live = have && ray_start<CSG>(g, rays + 6 * i, r);
     }
     for (int q = 0; q < nq; ++q) {
         const int slot = q < nm ? q : MAXMAT + (q - nm);
@@ -375,7 +435,7 @@ __global__ void __launch_bounds__(BWD_BLOCK) k_transmission_bwd(const DevGeom g,
             if (j == slot) v = acc[j];
         red[threadIdx.x] = v;
         __syncthreads();
-        for (int w = BWD_BLOCK / 2; w > 0; w >>= 1) {
+        for (int w = RAY_BLOCK / 2; w > 0; w >>= 1) {
             if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
             __syncthreads();
         }
@@ -717,23 +777,36 @@ trk_status trk_find_cell(trk_geom_t g, int tracker, int64_t n, const double* dev
     return launch_error("trk_find_cell");
 }
 
-trk_status trk_distance_to_surface(trk_geom_t g, int tracker, int64_t n, const double* dev_xyz, const double* dev_dir,
-                                   double* dev_dist, int32_t* dev_level, int64_t* dev_inst, void* stream) {
+trk_status trk_distance_to_surface(trk_geom_t g, int tracker, int precision, int64_t n, const double* dev_xyz,
+                                   const double* dev_dir, double* dev_dist, int32_t* dev_level, int64_t* dev_inst,
+                                   int32_t* dev_close, void* stream) {
     if (!valid(g) || n < 0 || (n > 0 && (!dev_xyz || !dev_dir || !dev_dist)))
         return trk_status(set_error(TRK_E_INVALID, "trk_distance_to_surface: bad arguments"));
+    if (precision != TRK_FP64 && precision != TRK_FP32_LOCAL)
+        return trk_status(set_error(TRK_E_INVALID, "trk_distance_to_surface: unknown precision %d", precision));
     trk_status st;
     const int t = resolve_tracker(g, tracker, &st, true);
     if (t < 0) return st;
+    const bool f32 = precision == TRK_FP32_LOCAL;
+    if (f32 && (!HAVE_F32 || t == TRK_TRACKER_DP))
+        return trk_status(set_error(TRK_E_UNSUPPORTED, "trk_distance_to_surface: FP32-local needs the fast build and "
+                                                       "the array or CSG tracker"));
     if (n == 0) return TRK_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-#define TRK_DIST(TKV)                                                                                  \
-    do {                                                                                               \
-        const int gr = persistent_grid(k_distance<TKV>, 128, n, 0);                                    \
-        k_distance<TKV><<<gr, 128, 0, s>>>(g->dg, n, dev_xyz, dev_dir, dev_dist, dev_level, dev_inst); \
+#define TRK_DIST(TKV, F32V)                                                                                        \
+    do {                                                                                                           \
+        const int gr = persistent_grid(k_distance<TKV, F32V>, 128, n, 0);                                          \
+        k_distance<TKV, F32V><<<gr, 128, 0, s>>>(g->dg, n, dev_xyz, dev_dir, dev_dist, dev_level, dev_inst,        \
+                                                 dev_close);                                                       \
     } while (0)
-    if (t == TRK_TRACKER_CSG) TRK_DIST(TK_CSG);
-    else if (t == TRK_TRACKER_DP) TRK_DIST(TK_DP);
-    else TRK_DIST(TK_RECT);
+    if (f32) {
+#ifndef TRK_EXACT
+        if (t == TRK_TRACKER_CSG) TRK_DIST(TK_CSG, true);
+        else TRK_DIST(TK_RECT, true);
+#endif
+    } else if (t == TRK_TRACKER_CSG) TRK_DIST(TK_CSG, false);
+    else if (t == TRK_TRACKER_DP) TRK_DIST(TK_DP, false);
+    else TRK_DIST(TK_RECT, false);
 #undef TRK_DIST
     return launch_error("trk_distance_to_surface");
 }
@@ -759,19 +832,17 @@ trk_status transmission_fwd(trk_geom_t g, int tracker, int64_t n, const double* 
     if (t < 0) return st;
     if (n == 0) return TRK_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (t == TRK_TRACKER_CSG) {
-        const int gr = persistent_grid(k_transmission<true>, 128, n, 0);
-        k_transmission<true><<<gr, 128, 0, s>>>(g->dg, n, dev_rays, dev_sigma, dev_T, dev_lens);
-    } else {
-        const int gr = persistent_grid(k_transmission<false>, 128, n, 0);
-        k_transmission<false><<<gr, 128, 0, s>>>(g->dg, n, dev_rays, dev_sigma, dev_T, dev_lens);
-    }
+    const long long nb = (n + RAY_TILE - 1) / RAY_TILE;
+    if (t == TRK_TRACKER_CSG)
+        k_transmission<true><<<unsigned(nb), RAY_BLOCK, 0, s>>>(g->dg, n, dev_rays, dev_sigma, dev_T, dev_lens);
+    else
+        k_transmission<false><<<unsigned(nb), RAY_BLOCK, 0, s>>>(g->dg, n, dev_rays, dev_sigma, dev_T, dev_lens);
     return launch_error("transmission_fwd");
 }
 
 trk_status transmission_bwd_work_bytes(trk_geom_t g, int64_t n, size_t* bytes) {
     if (!valid(g) || n < 0 || !bytes) return trk_status(set_error(TRK_E_INVALID, "transmission_bwd_work_bytes: bad arguments"));
-    const long long nb = (n + BWD_BLOCK - 1) / BWD_BLOCK;
+    const long long nb = (n + RAY_TILE - 1) / RAY_TILE;
     *bytes = size_t(nb > 0 ? nb : 1) * size_t(g->n_mat + NGP) * sizeof(double);
     return TRK_OK;
 }
@@ -789,7 +860,7 @@ trk_status transmission_bwd(trk_geom_t g, int tracker, int64_t n, const double* 
     const int t = resolve_tracker(g, tracker, &st);
     if (t < 0) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const long long nb = (n + BWD_BLOCK - 1) / BWD_BLOCK;
+    const long long nb = (n + RAY_TILE - 1) / RAY_TILE;
     const int nq = g->n_mat + NGP;
     double* partial = static_cast<double*>(dev_work);
     if (nb == 0) {
@@ -797,9 +868,9 @@ trk_status transmission_bwd(trk_geom_t g, int tracker, int64_t n, const double* 
         return launch_error("transmission_bwd");
     }
     if (t == TRK_TRACKER_CSG)
-        k_transmission_bwd<true><<<unsigned(nb), BWD_BLOCK, 0, s>>>(g->dg, n, dev_rays, dev_sigma, pitch, dev_gT, partial);
+        k_transmission_bwd<true><<<unsigned(nb), RAY_BLOCK, 0, s>>>(g->dg, n, dev_rays, dev_sigma, pitch, dev_gT, partial);
     else
-        k_transmission_bwd<false><<<unsigned(nb), BWD_BLOCK, 0, s>>>(g->dg, n, dev_rays, dev_sigma, pitch, dev_gT, partial);
+        k_transmission_bwd<false><<<unsigned(nb), RAY_BLOCK, 0, s>>>(g->dg, n, dev_rays, dev_sigma, pitch, dev_gT, partial);
     trk_status e = launch_error("transmission_bwd");
     if (e != TRK_OK) return e;
     k_reduce_partials<<<1, 32, 0, s>>>(partial, nb, nq, dev_grad);

@@ -9,6 +9,10 @@
 
 namespace trk {
 
+// Rays per block of the transmission kernels (128 threads, 8 rays each); the
+// backward pass keeps one row of partial sums per block in its work buffer.
+constexpr long long TRK_RAYS_PER_BLOCK = 1024;
+
 // Event kernel: CTAs to launch for `slots` particle slots per CTA (fills the
 // GPU at the kernel's occupancy), and the work bytes that needs.
 int event_grid(int slots);

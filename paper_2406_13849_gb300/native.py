@@ -82,7 +82,8 @@ def library(exact: bool = False):
             "run_histories": (ctypes.c_int, [_P, _P, i64, _P, _P, _P, _P, sz, ctypes.POINTER(RunOpts), _P]),
             "tally_read": (ctypes.c_int, [_P, _P, _P, i64, _P, _P]),
             "trk_find_cell": (ctypes.c_int, [_P, ctypes.c_int, i64, _P, _P, _P]),
-            "trk_distance_to_surface": (ctypes.c_int, [_P, ctypes.c_int, i64, _P, _P, _P, _P, _P, _P]),
+            "trk_distance_to_surface": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, i64, _P, _P, _P, _P, _P, _P,
+                                                       _P]),
             "trk_sync_status": (ctypes.c_int, [_P, _P]),
             "trk_trace": (ctypes.c_int, [_P, _P, i64, ctypes.c_int32, _P, _P, _P, _P, _P, sz,
                                          ctypes.POINTER(RunOpts), _P]),
@@ -310,17 +311,24 @@ class Geometry:
                                                 _stream(stream)))
         return out
 
-    def distance_to_surface(self, xyz, dirs, tracker=TRACKER_AUTO, stream=None):
+    def distance_to_surface(self, xyz, dirs, tracker=TRACKER_AUTO, stream=None, precision=FP64,
+                            with_close=False):
         """(distance, level, leaf instance) per point: find_cell from the
-        root, then distance_to_surface over the levels."""
+        root, then distance_to_surface over the levels; precision=FP32_LOCAL
+        gives the FP32-local flight's distance, and with_close=True adds the
+        per-point flag of distances redone in FP64."""
         xyz = _need(xyz.contiguous(), "distance_to_surface xyz", self.device, 0, _F64, cols=3)
         n = xyz.shape[0]
         dirs = _need(dirs.contiguous(), "distance_to_surface dirs", self.device, 24 * n, _F64, cols=3)
         d = torch.empty(n, dtype=torch.float64, device=self.device)
         lev = torch.empty(n, dtype=torch.int32, device=self.device)
         inst = torch.empty(n, dtype=torch.int64, device=self.device)
-        _check(self.lib, self.lib.trk_distance_to_surface(self.h, tracker, n, _ptr(xyz), _ptr(dirs), _ptr(d),
-                                                          _ptr(lev), _ptr(inst), _stream(stream)))
+        close = torch.empty(n, dtype=torch.int32, device=self.device) if with_close else None
+        _check(self.lib, self.lib.trk_distance_to_surface(self.h, tracker, precision, n, _ptr(xyz), _ptr(dirs),
+                                                          _ptr(d), _ptr(lev), _ptr(inst), _ptr(close),
+                                                          _stream(stream)))
+        if with_close:
+            return d, lev, inst, close
         return d, lev, inst
 
     def trace(self, particles, n: int, cap: int, opts: RunOpts | None = None, stream=None, work=None, **kw):

@@ -284,7 +284,7 @@ def test_every_entry_point_rejects_a_null_handle_on_the_host():
         "power_iteration": (None, 1, 0, 1, None, None, None, None, None, 0, ctypes.byref(o), None),
         "tally_read": (None, None, None, 0, None, None),
         "trk_find_cell": (None, 0, 1, None, None, None),
-        "trk_distance_to_surface": (None, 0, 1, None, None, None, None, None, None),
+        "trk_distance_to_surface": (None, 0, 0, 1, None, None, None, None, None, None, None),
         "trk_sync_status": (None, None),
         "trk_trace": (None, None, 1, 1, None, None, None, None, None, 0, ctypes.byref(o), None),
         "transmission_fwd": (None, 0, 1, None, None, None, None, None),

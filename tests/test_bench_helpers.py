@@ -71,3 +71,26 @@ def test_tally_error_summary():
     # a list of per-geometry tallies is summarised as one concatenated tally
     assert B.tally_error([t32, t32], [t64, t64])["tally_l1_rel"] == e["tally_l1_rel"]
     assert B._guarded(lambda: 1 / 0) == {"error": "ZeroDivisionError: division by zero"}
+
+
+def test_cpu_baseline_compares_traced_rows_under_the_near_surface_rule():
+    # rows equal to the oracle's own traces all match; a planted length
+    # error in one row is reported as a failure, not hidden
+    import oracle as O
+    from paper_2406_13849_gb300 import inputs as I
+    B = _bench()
+    desc = I.to_json(I.small_core())
+    o = O.Geometry(desc, O.MODE_CSG)
+    ids, cap = np.arange(5, 25), 64
+    rows_i = np.full((len(ids), cap), -1, np.int32)
+    rows_l = np.zeros((len(ids), cap))
+    for r, pid in enumerate(ids):
+        inst, ln, kind, st = o.trace(int(pid), B.SEED, B.P_ABSORB, cap=cap)
+        rows_i[r, :len(inst)] = inst
+        rows_l[r, :len(ln)] = ln
+    out = B.cpu_baseline(desc, 2000, 500, traced=(ids, rows_i, rows_l, cap))
+    rule = out["near_surface_rule"]
+    assert rule["compared"] == len(ids) and rule["matched"] == len(ids) and rule["failed"] == 0
+    rows_l[3, 2] += 1e-6
+    rule = B.cpu_baseline(desc, 2000, 500, traced=(ids, rows_i, rows_l, cap))["near_surface_rule"]
+    assert rule["failed"] == 1 and rule["findings"][0]["pid"] == int(ids[3])

@@ -78,3 +78,54 @@ def test_distance_at_cylinder_surfaces_and_screen_threshold(tracker, mode):
     # the outer cylinder wins from some of the points just inside it: the screen's threshold is crossed
     band = np.arange(len(xyz)) >= 60_000
     assert ((ol == 0) & band).sum() > 100 and ((ol > 0) & band).sum() > 100
+
+
+def _near_tangent(xyz, n_frac, seed):
+    """Directions: isotropic, except a fraction turned nearly perpendicular
+    to the radius of the nearest pin axis (grazing rays)."""
+    rng = np.random.default_rng(seed)
+    n = len(xyz)
+    w = _directions(n, seed)
+    k = rng.uniform(size=n) < n_frac
+    # radial direction from the nearest pin axis (the 15 x 17 = 255 pins per
+    # row are centred on the origin: axes at multiples of the pitch)
+    cx = np.round(xyz[:, 0] / PITCH) * PITCH
+    cy = np.round(xyz[:, 1] / PITCH) * PITCH
+    rx, ry = xyz[:, 0] - cx, xyz[:, 1] - cy
+    rn = np.hypot(rx, ry) + 1e-300
+    tx, ty = -ry / rn, rx / rn
+    tilt = 10.0 ** rng.uniform(-9.0, -1.0, n) * rng.choice([-1.0, 1.0], n)
+    wz = rng.uniform(-0.9, 0.9, n)
+    sxy = np.sqrt(1.0 - wz * wz)
+    gx, gy = tx + tilt * rx / rn, ty + tilt * ry / rn
+    gn = np.hypot(gx, gy)
+    w[k] = np.stack([sxy * gx / gn, sxy * gy / gn, wz], 1)[k]
+    return w
+
+
+def test_fast_build_distances_near_cylinders_and_tangents():
+    # the fast build (contracted multiply-adds) near every cylinder of the
+    # core and at grazing incidence, where the cylinder formulas lose the
+    # most digits: every distance within 1e-12 of the oracle's (relative to
+    # the coordinates' size) with the same winning level, unless the oracle
+    # confirms a decision near a surface (oracle.compare.classify_distances)
+    from oracle import compare as C
+    desc = I.config2()
+    xyz = np.concatenate([_near_cylinders(desc, 100_000, 41), _inside_outer(20_000, 42)])
+    w = _near_tangent(xyz, 0.5, 43)
+    o = O.Geometry(I.to_json(desc), O.MODE_CSG)
+    od, ol, oi = o.distance(xyz, w)
+    g = N.Geometry(I.to_json(desc), exact=False)
+    d, lev, inst = g.distance_to_surface(torch.from_numpy(xyz).cuda(), torch.from_numpy(w).cuda(),
+                                         tracker=N.TRACKER_CSG)
+    torch.cuda.synchronize()
+    gd, gl, gi = d.cpu().numpy(), lev.cpu().numpy(), inst.cpu().numpy()
+    diff = np.nonzero(gi != oi)[0]
+    if len(diff):
+        cl = o.clearance(xyz[diff], w[diff], np.zeros(len(diff)))
+        assert (cl[:, 0] < C.NEAR).all(), cl[:, 0]
+    same = gi == oi
+    res = C.classify_distances(o, xyz[same], w[same], od[same], ol[same], gd[same], gl[same])
+    print(f"\npoints {res['points']}, outside the bar {res['outside_bar']}, near {len(res['near'])}, "
+          f"failed {len(res['failed'])}, max rel within bar {res['max_rel_within_bar']:.3g}, cell differs {len(diff)}")
+    assert not res["failed"], res["failed"][:5]

@@ -62,7 +62,7 @@ def test_noalloc_rejects_too_many_rays():
     # suffice: nothing can launch even if the check were to regress (the
     # backward pass would then refuse the null pointers).
     g, rays, sigma = _case()
-    n_big = 40_000_000
+    n_big = 1_000_000_000
     st = g.lib.transmission_bwd_noalloc(g.h, N.TRACKER_AUTO, n_big, None, None, ctypes.c_double(1.26), None, None,
                                         N._stream())
     assert st == -4
