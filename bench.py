@@ -337,6 +337,42 @@ def main() -> None:
         total_ms, total_seg = main_run["ms"], float(main_run["segments"])
     value = total_seg / (total_ms / 1e3)
 
+    # ---- the exchange a sharded run needs: the integer tallies and counters
+    # of every rank merged into one (outside the timed region).  Rank 0
+    # checks the merge on a sample: every rank tracks the first ids of its
+    # range, and rank 0 tracks all of them alone.
+    exchange = None
+    if world > 1:
+        from paper_2406_13849_gb300 import sharding as SH
+        m_t, m_c = tally.clone(), cnt.clone()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record(stream)
+        SH.merge_tallies(m_t, m_c)
+        e1.record(stream)
+        barrier()
+        n_s = 20_000
+        opts_s = make_opts(N.TRACKER_CSG, N.MODE_EVENT)
+        sp = g.source_init(n_s, seed=SEED, first_id=first_id)
+        st_t, st_c, _ = g.run_histories(sp, n_s, opts=opts_s, work=work_for(opts_s))
+        SH.merge_tallies(st_t, st_c)
+        ok = None
+        if rank == 0:
+            ref_t = torch.zeros_like(st_t)
+            ref_c = torch.zeros_like(st_c)
+            for r in range(world):
+                o_r = N.default_opts(tracker=N.TRACKER_CSG, mode=N.MODE_EVENT, seed=SEED, first_id=r * n,
+                                     p_absorb=P_ABSORB, queue_depth=EVENT_SLOTS)
+                rp = g.source_init(n_s, seed=SEED, first_id=r * n)
+                g.run_histories(rp, n_s, tally=ref_t, counters=ref_c, opts=o_r, work=work_for(o_r))
+            torch.cuda.synchronize()
+            ok = bool(torch.equal(ref_t, st_t) and torch.equal(ref_c, st_c))
+        exchange = {"what": "all-reduce of the uint64 cell tally (SUM) and counters (SUM; status MIN)",
+                    "bytes_per_rank": int(m_t.numel() * 8 + m_c.numel() * 8), "ms": e0.elapsed_time(e1),
+                    "merged_segments": int(m_c[0]),
+                    "check": ("a %d-particle sample per rank merged equals rank 0 tracking all of them: %s"
+                              % (n_s, ok)) if rank == 0 else None}
+
     # ---- companions on the same workload ----------------------------------
     k2 = max(2, args.steps // 2)
     rect_ev = timed(N.TRACKER_RECT, N.MODE_EVENT, k2, 3)
@@ -393,7 +429,7 @@ def main() -> None:
            "h2d_bytes_per_step": int(parts.numel()), "d2h_bytes_per_step": int(g.n_inst * 8 + 8)}
 
     # ---- batched: 64 geometries, FP32-local graph replay vs FP64 launch loop
-    batch = run_config4(N, I, dev, stream, barrier, rank, k2)
+    batch = run_config4(N, I, dev, stream, barrier, rank, k2, world)
 
     # ---- roofline of the dominant kernel (the event kernel, CSG, FP64) ------
     fps = flops_per_segment(desc)
@@ -511,6 +547,7 @@ def main() -> None:
             "roofline": roofline,
             "cpu_baseline": cpu,
             "fast_build_near_surface_mismatches": near_rule,
+            "exchange": exchange,
             "variants": {
                 "csg_fp64_event": rate(main_run),
                 "rect_fp64_event": rate(rect_ev),
@@ -540,14 +577,20 @@ def main() -> None:
         dist.destroy_process_group()
 
 
-def run_config4(N, I, dev, stream, barrier, rank, steps):
+def run_config4(N, I, dev, stream, barrier, rank, steps, world=1):
     """64 geometries (3x3..17x17 rect/hex, 2-3 levels, 1e4..1e6 particles):
     the batched event kernel (warp queues over chunks of one geometry at a
     time), FP32-local, autotuned and replayed from a CUDA graph, against the
-    plain FP64 history kernel launched once per geometry."""
+    plain FP64 history kernel launched once per geometry.  With several
+    ranks the geometries are split between them (whole problems per rank,
+    balanced by particle count) and each rank reports its share."""
     import numpy as np
     import torch
     members = I.config4()
+    if world > 1:
+        from paper_2406_13849_gb300 import sharding as SH
+        mine = SH.shard_geometries([c for _, c in members], world)[rank]
+        members = [members[k] for k in mine]
     geoms = [N.Geometry(I.to_json(d), device=dev) for d, _ in members]
     counts = [c for _, c in members]
     parts = [g.source_init(c, seed=SEED) for g, c in zip(geoms, counts)]
@@ -577,7 +620,7 @@ def run_config4(N, I, dev, stream, barrier, rank, steps):
     r_ev32 = graph_rate(ev32)
     snap32 = ([t.clone() for t in b.tallies], b.counters.clone())
     ev64 = N.default_opts(seed=SEED, p_absorb=P_ABSORB, precision=N.FP64, mode=N.MODE_EVENT,
-                          queue_depth=ev32.queue_depth)
+                          queue_depth=ev32.queue_depth, sort_interval=ev32.sort_interval)
     r_ev64 = graph_rate(ev64)
     snap64 = ([t.clone() for t in b.tallies], b.counters.clone())
 
@@ -600,20 +643,27 @@ def run_config4(N, I, dev, stream, barrier, rank, steps):
     a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
     def loop_rate(opts, reps):
+        wb = geoms[0].work_bytes(counts[0], opts)
+        work = torch.empty(wb + 256, dtype=torch.uint8, device=dev) if wb else None
         for gg, pp, cc, tt in zip(geoms, parts, counts, tallies):
-            gg.run_histories(pp, cc, tally=tt, counters=cnt, opts=opts)
+            gg.run_histories(pp, cc, tally=tt, counters=cnt, opts=opts, work=work)
         cnt.zero_()
         barrier()
         a.record(stream)
         for _ in range(reps):
             for gg, pp, cc, tt in zip(geoms, parts, counts, tallies):
-                gg.run_histories(pp, cc, tally=tt, counters=cnt, opts=opts)
+                gg.run_histories(pp, cc, tally=tt, counters=cnt, opts=opts, work=work)
         e.record(stream)
         barrier()
         return int(cnt.cpu().numpy().view(np.uint64)[0]) / (a.elapsed_time(e) / 1e3)
 
     r_l = loop_rate(N.default_opts(seed=SEED, p_absorb=P_ABSORB, precision=N.FP64, mode=N.MODE_HISTORY), steps)
     r_l32 = loop_rate(N.default_opts(seed=SEED, p_absorb=P_ABSORB, precision=N.FP32_LOCAL, mode=N.MODE_HISTORY), 1)
+    # the same event kernel launched once per geometry (what the batch saves
+    # over a loop of the single-geometry event kernel)
+    r_le32 = loop_rate(N.default_opts(seed=SEED, p_absorb=P_ABSORB, precision=N.FP32_LOCAL, mode=N.MODE_EVENT,
+                                      queue_depth=ev32.queue_depth, sort_interval=ev32.sort_interval), 1)
+    seg_per_particle = float(snap32[1].cpu().numpy().view(np.uint64).reshape(-1, 16)[:, 0].sum()) / max(1, sum(counts))
     return {"workload": "64 geometries: 3x3..17x17 rect/hex lattices, 2-3 levels, 1e4..1e6 particles "
                         "(log-uniform), %d particles" % sum(counts),
             "batched_fp32local_graph_segments_per_s": r_ev32,
@@ -623,9 +673,14 @@ def run_config4(N, I, dev, stream, barrier, rank, steps):
             "batched_fp64_event_graph_segments_per_s": r_ev64,
             "batched_fp32local_history_graph_segments_per_s": r_hi32,
             "loop_fp32local_history_segments_per_s": r_l32,
-            "autotuned": {"event": {"queue_depth": ev32.queue_depth, "chunk": chunk_ev},
+            "loop_fp32local_event_segments_per_s": r_le32,
+            "batched_over_event_loop": r_ev32 / r_le32,
+            "segments_per_particle": seg_per_particle,
+            "autotuned": {"event": {"queue_depth": ev32.queue_depth, "chunk": chunk_ev,
+                                    "sort_interval": ev32.sort_interval},
                           "history": {"block": hi32.block, "chunk": chunk_hi}},
-            "launches_per_pass": {"batched_event": 2, "batched_history": 1, "loop": len(geoms)}}
+            "launches_per_pass": {"batched_event": 2, "batched_history": 1, "loop": len(geoms)},
+            "geometries_on_this_rank": len(geoms)}
 
 
 def run_config1_sweep(N, I, dev, stream, barrier):

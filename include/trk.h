@@ -98,8 +98,10 @@ typedef struct {
     int block;              /* threads per block, 0 = default */
     int grid;               /* blocks, 0 = default (a multiple of the SM count) */
     int queue_depth;        /* event mode: particle slots per warp (32..512), 0 = default 256 */
-    int sort_interval;      /* reserved, ignored: the event kernel groups crossings by level every
-                               round; flight queues sorted by leaf-cell class are a build option */
+    int sort_interval;      /* event mode: every sort_interval rounds each warp reorders its flight
+                               queue by the class of the particles' leaf cells (no curved surface, one
+                               cylinder from inside, from outside, other) so a flight batch runs one
+                               code path; 0 = never (crossings are grouped by level every round) */
     int max_rounds;         /* event mode: round limit per warp, 0 = from max_segments; past it the
                                kernel stops and reports TRK_E_TIMEOUT in counters[TRK_K_STATUS] */
     uint64_t seed;          /* low 32 bits key the Philox stream with the geometry id */
@@ -358,8 +360,8 @@ trk_status batch_work_bytes(trk_batch_t b, size_t* bytes);
 trk_status batch_upload(trk_batch_t b, void* dev_work, size_t work_bytes, int chunk, void* stream);
 
 /* Persistent launches over the whole batch (opts: mode, precision, block,
- * grid, queue_depth, max_rounds, seed, first_id, p_absorb, max_segments;
- * path cutoff ignored).  History mode: one kernel, one history per lane,
+ * grid, queue_depth, sort_interval, max_rounds, seed, first_id, p_absorb,
+ * max_segments; path cutoff ignored).  History mode: one kernel, one history per lane,
  * warps pull chunks of one geometry.  Event mode: the event kernel's queues
  * and slot records per warp, each warp working through chunks of one
  * geometry at a time (a chunk of another geometry starts once the warp's
@@ -372,11 +374,12 @@ trk_status run_batched(trk_batch_t b, void* dev_work, const trk_run_opts* opts, 
 
 /* Autotuner: times block sizes {64, 96, 128} x chunk sizes {128, 512, 2048}
  * (history mode) or queue depths {256, 384, 512} x chunk sizes {4096, 16384,
- * 65536} (event mode, opts->mode) on the batch itself (CUDA events, `reps`
- * launches each) and writes the fastest to opts->block or opts->queue_depth
- * and *chunk_out, leaving the table uploaded for it; *best_ms (optional) gets
- * its time.  The trial launches add to the tallies and counters: clear them
- * afterwards.  Synchronises `stream`. */
+ * 65536} x sort intervals {0, 4} (event mode, opts->mode) on the batch itself
+ * (CUDA events, `reps` launches each) and writes the fastest to opts->block
+ * or opts->queue_depth and opts->sort_interval, and *chunk_out, leaving the
+ * table uploaded for it; *best_ms (optional) gets its time.  The trial
+ * launches add to the tallies and counters: clear them afterwards.
+ * Synchronises `stream`. */
 trk_status batch_autotune(trk_batch_t b, void* dev_work, size_t work_bytes, trk_run_opts* opts,
                           int* chunk_out, int reps, double* best_ms, void* stream);
 

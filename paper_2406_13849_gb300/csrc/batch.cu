@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(128) k_batched(BatchHeader* __restrict__ hdr, 
 // and CSG-tracker entries run as two launches (the rect chunks come first).
 // ---------------------------------------------------------------------------
 using namespace trk::ev;
-constexpr int BEV_QUEUES = 4 + MAXL;   // flight, next flight, collide, free, cross per level
+constexpr int BEV_QUEUES = 4 + MAXL;   // flight, next flight, collide (sort scratch), free, cross per level
 
 __device__ __forceinline__ int entry_of(const BatchEntry* table, int ng, unsigned long long c) {
     int lo = 0, hi = ng - 1;
@@ -142,15 +142,16 @@ template <bool CSG, bool F32, int FLAGS>
 __global__ void TRK_EV_BOUNDS k_batched_ev(BatchHeader* __restrict__ hdr, const BatchEntry* __restrict__ table,
                                            const RunP rp, const EvBuf B, int slots, int side,
                                            unsigned long long c_begin, unsigned long long c_end,
-                                           unsigned long long max_rounds) {
+                                           unsigned long long max_rounds, int sort_interval) {
     extern __shared__ QIdx smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     QIdx* base_q = smem + warp * BEV_QUEUES * slots;
-    QIdx* fly = base_q;
+    QIdx* fly = base_q;                  // slot | leaf class << QSLOT_BITS
     QIdx* next = base_q + slots;
-    QIdx* qc = base_q + 2 * slots;
+    QIdx* qc = base_q + 2 * slots;       // collide (at a sort: scratch)
     QIdx* qf = base_q + 3 * slots;
     QIdx* qx = base_q + 4 * slots;
+    const bool sorting = sort_interval > 0;
     const int slot0 = (blockIdx.x * (EV_BLOCK / 32) + warp) * slots;
     const int ng = hdr->n_geom;
     const long long chunk = hdr->chunk;
@@ -202,7 +203,7 @@ __global__ void TRK_EV_BOUNDS k_batched_ev(BatchHeader* __restrict__ hdr, const 
         for (int b = 0; b < got; b += 32) {
             const int k = b + lane;
             bool ok = false;
-            int slot = 0;
+            int slot = 0, cls = 0;
             if (k < got) {
                 slot = slot0 + qf[n_free - got + k];
                 const long long pidx = first + k;
@@ -225,13 +226,14 @@ __global__ void TRK_EV_BOUNDS k_batched_ev(BatchHeader* __restrict__ hdr, const 
                         D2(r, R_ZT) = make_double2(s.z, s.tau);
                         store_dir(r, s);
                         store_levels<CSG>(g, r, s, 0);
-                        store_ctx<FLAGS>(r, int(pidx), c, make_misc(0, s, 0));
+                        cls = sorting ? flight_class<CSG>(g, s) : 0;
+                        store_ctx<FLAGS>(r, int(pidx), c, make_misc(0, s, cls));
                         ok = true;
                     }
                 }
                 if (!ok && rec) finish<FLAGS>(pidx, c, rec);
             }
-            wpush(ok, slot - slot0, fly, n_fly);
+            wpush(ok, (slot - slot0) | (cls << QSLOT_BITS), fly, n_fly);
             wpush(k < got && !ok, slot - slot0, next, n_park);
         }
         __syncwarp();
@@ -247,6 +249,12 @@ __global__ void TRK_EV_BOUNDS k_batched_ev(BatchHeader* __restrict__ hdr, const 
             break;
         }
         // ---- flight ------------------------------------------------------------
+        // every sort_interval rounds the flight list is reordered by class
+        if (sorting && n_fly > 32 && round % (unsigned long long)sort_interval == 0) {
+            sort_by_class(fly, n_fly, qc);
+            for (int k = lane; k < n_fly; k += 32) fly[k] = qc[k];
+            __syncwarp();
+        }
         int n_cross[MAXL], n_coll = 0;
 #pragma unroll
         for (int l = 0; l < MAXL; ++l) n_cross[l] = 0;
@@ -254,7 +262,7 @@ __global__ void TRK_EV_BOUNDS k_batched_ev(BatchHeader* __restrict__ hdr, const 
             const int k = b + lane;
             int a = A_DONE, slot = 0, hl = -1;
             if (k < n_fly) {
-                slot = slot0 + fly[k];
+                slot = slot0 + int(unsigned(fly[k]) & QSLOT_MASK);
                 unsigned char* r = rec_at<FLAGS>(B, slot);
                 St s;
                 const double2 xy = D2(r, R_XY), zt = D2(r, R_ZT);
@@ -295,7 +303,7 @@ __global__ void TRK_EV_BOUNDS k_batched_ev(BatchHeader* __restrict__ hdr, const 
         for (int lq = 0; lq < MAXL; ++lq)
         for (int b = 0; b < n_cross[lq]; b += 32) {
             const int k = b + lane;
-            int a = A_DONE, slot = 0;
+            int a = A_DONE, slot = 0, cls = 0;
             if (k < n_cross[lq]) {
                 slot = slot0 + qx[lq * slots + k];
                 unsigned char* r = rec_at<FLAGS>(B, slot);
@@ -317,18 +325,19 @@ __global__ void TRK_EV_BOUNDS k_batched_ev(BatchHeader* __restrict__ hdr, const 
                 if (a == A_DONE) {
                     if (rec) finish<FLAGS>(pidx, c, rec);
                 } else {
+                    cls = sorting ? flight_class<CSG>(g, s) : 0;
                     store_levels<CSG>(g, r, s, 0);
-                    store_ctx<FLAGS>(r, pidx, c, make_misc(0, s, 0));
+                    store_ctx<FLAGS>(r, pidx, c, make_misc(0, s, cls));
                     if (cnt.k[TRK_K_REFLECTIONS] != refl0) store_dir(r, s);
                 }
             }
             const bool live = k < n_cross[lq];
-            wpush(live && a == A_FLY, slot - slot0, next, n_next);
+            wpush(live && a == A_FLY, (slot - slot0) | (cls << QSLOT_BITS), next, n_next);
             wpush(live && a == A_DONE, slot - slot0, qf, n_free);
         }
         for (int b = 0; b < n_coll; b += 32) {
             const int k = b + lane;
-            int a = A_DONE, slot = 0;
+            int a = A_DONE, slot = 0, cls = 0;
             if (k < n_coll) {
                 slot = slot0 + qc[k];
                 unsigned char* r = rec_at<FLAGS>(B, slot);
@@ -346,11 +355,12 @@ __global__ void TRK_EV_BOUNDS k_batched_ev(BatchHeader* __restrict__ hdr, const 
                     int4 su = I4(r, R_SU);
                     su.x = -1;
                     I4(r, R_SU) = su;
+                    cls = misc_cls(misc);
                     store_ctx<FLAGS>(r, pidx, c, misc_off_surface(misc));
                 }
             }
             const bool live = k < n_coll;
-            wpush(live && a == A_FLY, slot - slot0, next, n_next);
+            wpush(live && a == A_FLY, (slot - slot0) | (cls << QSLOT_BITS), next, n_next);
             wpush(live && a == A_DONE, slot - slot0, qf, n_free);
         }
         __syncwarp();
@@ -403,6 +413,7 @@ trk_status run_batched_event(trk_batch_t b, void* dev_work, const trk_run_opts& 
     const int slots = o.queue_depth > 0 ? o.queue_depth : 256;
     if (slots < 32 || slots > BEV_MAX_SLOTS) return trk_status(set_error(TRK_E_INVALID, "run_batched: queue_depth must be in [32, 512]"));
     if (o.max_rounds < 0) return trk_status(set_error(TRK_E_INVALID, "run_batched: max_rounds must be >= 0"));
+    if (o.sort_interval < 0) return trk_status(set_error(TRK_E_INVALID, "run_batched: sort_interval must be >= 0"));
     if (b->event_unfit >= 0)
         return trk_status(set_error(TRK_E_UNSUPPORTED, "run_batched (event): geometry %d does not fit the event kernels' "
                                     "slot record (at most %d universes, %d materials, %d elements per array axis)",
@@ -431,7 +442,7 @@ trk_status run_batched_event(trk_batch_t b, void* dev_work, const trk_run_opts& 
         if (c1 <= c0) return;
         if (smem > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         kernel<<<grid, EV_BLOCK, smem, s>>>(hdr, table, rp, B, slots, side, (unsigned long long)c0,
-                                            (unsigned long long)c1, max_rounds);
+                                            (unsigned long long)c1, max_rounds, o.sort_interval);
     };
     if (f32) {
 #ifndef TRK_EXACT
@@ -623,51 +634,58 @@ trk_status batch_autotune(trk_batch_t b, void* dev_work, size_t work_bytes, trk_
     if (!valid_batch(b) || !dev_work || !opts || !chunk_out) return trk_status(set_error(TRK_E_INVALID, "batch_autotune: bad arguments"));
     if (reps <= 0) reps = 2;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    // history mode: (block, chunk); event mode: (queue depth, chunk), with
-    // chunks large enough that a warp rarely drains between chunks
+    // history mode: (block, chunk); event mode: (queue depth, chunk, sort
+    // interval), with chunks large enough that a warp rarely drains between
+    // chunks
     const bool event = opts->mode == TRK_MODE_EVENT;
     const int hist_blocks[] = {64, 96, 128}, hist_chunks[] = {128, 512, 2048};
     const int ev_depths[] = {256, 384, 512}, ev_chunks[] = {4096, 16384, 65536};
+    const int sort_intervals[] = {0, 4};
     const int* blocks = event ? ev_depths : hist_blocks;
     const int* chunks = event ? ev_chunks : hist_chunks;
+    const int n_sort = event ? 2 : 1;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return trk_status(set_error(TRK_E_CUDA, "batch_autotune: cudaEventCreate failed"));
     float best = 1e30f;
-    int best_block = event ? 256 : 128, best_chunk = event ? 16384 : 512;
+    int best_block = event ? 256 : 128, best_chunk = event ? 16384 : 512, best_sort = 0;
     trk_status st = TRK_OK;
-    for (int ci = 0; ci < 3; ++ci) {
+    for (int ci = 0; ci < 3 && st == TRK_OK; ++ci) {
         const int ch = chunks[ci];
         st = batch_upload(b, dev_work, work_bytes, ch, stream);
         if (st != TRK_OK) break;
-        for (int bi = 0; bi < 3; ++bi) {
-            const int bl = blocks[bi];
-            trk_run_opts o = *opts;
-            if (event) o.queue_depth = bl;
-            else o.block = bl;
-            o.grid = 0;
-            st = run_batched(b, dev_work, &o, stream);
-            if (st != TRK_OK) break;
-            cudaEventRecord(e0, s);
-            for (int r = 0; r < reps; ++r) {
+        for (int bi = 0; bi < 3 && st == TRK_OK; ++bi) {
+            for (int si = 0; si < n_sort; ++si) {
+                const int bl = blocks[bi];
+                trk_run_opts o = *opts;
+                if (event) { o.queue_depth = bl; o.sort_interval = sort_intervals[si]; }
+                else o.block = bl;
+                o.grid = 0;
                 st = run_batched(b, dev_work, &o, stream);
                 if (st != TRK_OK) break;
+                cudaEventRecord(e0, s);
+                for (int r = 0; r < reps; ++r) {
+                    st = run_batched(b, dev_work, &o, stream);
+                    if (st != TRK_OK) break;
+                }
+                cudaEventRecord(e1, s);
+                if (cudaEventSynchronize(e1) != cudaSuccess) {
+                    st = trk_status(set_error(TRK_E_CUDA, "batch_autotune: sync failed"));
+                    break;
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                ms /= float(reps);
+                if (ms < best) { best = ms; best_block = bl; best_chunk = ch; best_sort = o.sort_interval; }
             }
-            cudaEventRecord(e1, s);
-            if (cudaEventSynchronize(e1) != cudaSuccess) { st = trk_status(set_error(TRK_E_CUDA, "batch_autotune: sync failed")); break; }
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            ms /= float(reps);
-            if (ms < best) { best = ms; best_block = bl; best_chunk = ch; }
         }
-        if (st != TRK_OK) break;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != TRK_OK) return st;
     st = batch_upload(b, dev_work, work_bytes, best_chunk, stream);
     if (st != TRK_OK) return st;
-    if (event) opts->queue_depth = best_block;
+    if (event) { opts->queue_depth = best_block; opts->sort_interval = best_sort; }
     else opts->block = best_block;
     opts->grid = 0;
     *chunk_out = best_chunk;

@@ -405,7 +405,19 @@ static __device__ TRK_HOLDS_INLINE bool cell_holds(const DevGeom& g, int c, cons
 #else
 #define TRK_SEARCH_INLINE __forceinline__
 #endif
-static __device__ TRK_SEARCH_INLINE int bvh_search(const DevGeom& g, int root, const Pt& p, int ex, int xs, int xsn) {
+// Kernels that stage the BVH nodes in shared memory (TRK_BVH_SMEM, the
+// event kernels) leave their address here at launch, or nullptr when the
+// geometry's nodes do not fit; the walk then reads the staged copy.
+#ifndef TRK_BVH_SMEM
+#define TRK_BVH_SMEM 0
+#endif
+#if TRK_BVH_SMEM
+__shared__ const BvhNode* s_bvh_nodes;
+#endif
+
+template <bool SMEM>
+__device__ __forceinline__ int bvh_walk(const DevGeom& g, const BvhNode* nodes, int root, const Pt& p, int ex, int xs,
+                                        int xsn) {
     float xl, xh, yl, yh, zl, zh;
     f32_bounds(p.x, xl, xh);
     f32_bounds(p.y, yl, yh);
@@ -415,9 +427,16 @@ static __device__ TRK_SEARCH_INLINE int bvh_search(const DevGeom& g, int root, c
     int ref = root;
     for (;;) {
         if (ref >= 0) {
-            const float4* np = reinterpret_cast<const float4*>(g.nodes + ref);
-            const float4 a = __ldg(np), b = __ldg(np + 1), c = __ldg(np + 2);
-            const int4 r = __ldg(reinterpret_cast<const int4*>(np + 3));
+            const float4* np = reinterpret_cast<const float4*>(nodes + ref);
+            float4 a, b, c;
+            int4 r;
+            if (SMEM) {
+                a = np[0]; b = np[1]; c = np[2];
+                r = *reinterpret_cast<const int4*>(np + 3);
+            } else {
+                a = __ldg(np); b = __ldg(np + 1); c = __ldg(np + 2);
+                r = __ldg(reinterpret_cast<const int4*>(np + 3));
+            }
             // child 0: lo (a.x, a.y, a.z), hi (a.w, b.x, b.y); child 1: lo (b.z, b.w, c.x), hi (c.y, c.z, c.w)
             const bool in0 = xh >= a.x && xl <= a.w && yh >= a.y && yl <= b.x && zh >= a.z && zl <= b.y;
             const bool in1 = xh >= b.z && xl <= c.y && yh >= b.w && yl <= c.z && zh >= c.x && zl <= c.w;
@@ -441,6 +460,13 @@ static __device__ TRK_SEARCH_INLINE int bvh_search(const DevGeom& g, int root, c
         if (sp == 0) return -1;
         ref = stack[--sp];
     }
+}
+
+static __device__ TRK_SEARCH_INLINE int bvh_search(const DevGeom& g, int root, const Pt& p, int ex, int xs, int xsn) {
+#if TRK_BVH_SMEM
+    if (s_bvh_nodes) return bvh_walk<true>(g, s_bvh_nodes, root, p, ex, xs, xsn);
+#endif
+    return bvh_walk<false>(g, g.nodes, root, p, ex, xs, xsn);
 }
 
 // Walk of universe u's bounding interval hierarchy (Sec. 4.3): at each node
@@ -956,8 +982,22 @@ __device__ __forceinline__ DirF dir_f32(const Dir& d) {
 // terms it cancels (near-tangent rays amplify FP32 rounding by 1/sqrt(disc)).
 constexpr float ILL_DISC = 1e-3f;
 
+// Error estimates of the FP32 distances: the magnitudes that meet in a
+// candidate's formula times a rounding scale, over the formula's
+// denominator.  A plane's (g - x) / u, with g and x each rounded once to FP32
+// and one rounding per operation, is off by at most 2^-24 (|g| + |x|) / |u|
+// plus a few ulp of t: F32_ERR (2^-23) is twice that.  A cylinder's root
+// moves by about (|dc| + 2 t |db|) / (2 sqrt(disc)) for errors dc, db of the
+// quadratic's terms: F32_ERR_CYL (2^-22) times their magnitudes.
+constexpr float F32_ERR = 0x1p-23f;
+constexpr float F32_ERR_CYL = 0x1p-22f;
+// Largest estimated error of the FP32 winner, relative to max(1 cm, d),
+// before the flight is redone in FP64 (below the variant's 1e-5 bar).
+constexpr float F32_ERR_MAX = 8e-6f;
+
+
 __device__ __forceinline__ float surface_distance_f(const DevGeom& g, int s, int type, int side, bool on, float x,
-                                                    float y, float z, const DirF& d, bool& ill) {
+                                                    float y, float z, const DirF& d, bool& ill, float& err) {
     const float4 c = __ldg(g.s_coeff + s);
     float t;
     if (type <= S_PZ) {
@@ -967,18 +1007,26 @@ __device__ __forceinline__ float surface_distance_f(const DevGeom& g, int s, int
         const float xx = type == S_PX ? x : (type == S_PY ? y : z);
         const float ii = type == S_PX ? d.iu : (type == S_PY ? d.iv : d.iw);
         t = (c.x - xx) * ii;
+        err = F32_ERR * (fabsf(c.x) + fabsf(xx)) * fabsf(ii);
     } else if (type == S_P) {
         if (on) return FINF;
         const float den = (c.x * d.u + c.y * d.v) + c.z * d.w;
         if (!(side > 0 ? den < 0.f : den > 0.f)) return FINF;
         t = (c.w - ((c.x * x + c.y * y) + c.z * z)) / den;
+        err = F32_ERR * (((fabsf(c.x * x) + fabsf(c.y * y)) + fabsf(c.z * z)) + fabsf(c.w)) / fabsf(den);
     } else {
         const float qx = x - c.x, qy = y - c.y;
         const float a = d.u * d.u + d.v * d.v;
         const float b = qx * d.u + qy * d.v;
+        // the quadratic's terms carry rounding of their size: t moves by
+        // about (|dc| + 2 t |db|) / (2 sqrt(disc)), near-tangent rays (small
+        // disc) and large frames (big q, r) blowing it up
+        const float bsz = fabsf(qx * d.u) + fabsf(qy * d.v);
+        const float csz = (qx * qx + qy * qy) + c.z;
         if (on) {
             if (side < 0 && b < 0.f) t = (-2.0f * b) / a;
             else return FINF;
+            err = F32_ERR_CYL * 2.0f * bsz / a;
         } else {
             const float cc = (qx * qx + qy * qy) - c.z;
             if (a == 0.f) return FINF;
@@ -992,50 +1040,23 @@ __device__ __forceinline__ float surface_distance_f(const DevGeom& g, int s, int
                 if (!(b < 0.f)) return FINF;
                 t = cc / (-b + sq);
             }
+            err = F32_ERR_CYL * (csz + 2.0f * fabsf(t) * bsz) / (2.0f * sq) + F32_ERR_CYL * fabsf(t);
         }
     }
     return t < 0.f ? 0.f : t;
 }
 
-// Candidates whose FP32 evaluation would work with a coordinate or a face
-// offset above F32_EXTENT cm (a tall lattice's z faces, a core-size
-// cylinder) are evaluated in FP64 instead: FP32 keeps its 1e-5 relative
-// accuracy only where the frame coordinates are small.
-constexpr float F32_EXTENT = 16.0f;
-// max(|x|, |y|, |z|) > F32_EXTENT, by integer compares of the magnitudes' bits
-__device__ __forceinline__ bool beyond_f32_extent(double x, double y, double z) {
-    const long long m = 0x7fffffffffffffffLL, c = __double_as_longlong(double(F32_EXTENT));
-    return (dbits(x) & m) > c || (dbits(y) & m) > c || (dbits(z) & m) > c;
-}
-
 struct Best2 {
-    float d1, d2;
+    float d1, d2, e1, e2;   // the two smallest distances and their error estimates
     bool ill;
-    bool xact;           // the winner was evaluated in FP64 (its length in tx)
     Hit h;
-    double wx, wy, wz;   // FP64 coordinates of the winner's level frame
-    double tx;
-    __device__ __forceinline__ void offer(float t, int level, int surf, int side, int dim, int dsign, int entry,
-                                          double x, double y, double z) {
+    __device__ __forceinline__ void offer(float t, float err, int level, int surf, int side, int dim, int dsign,
+                                          int entry) {
         if (t < d1) {
-            d2 = d1; d1 = t;
+            d2 = d1; e2 = e1; d1 = t; e1 = err;
             h.level = level; h.surf = surf; h.side = side; h.dim = dim; h.dsign = dsign; h.entry = entry;
-            wx = x; wy = y; wz = z;
-            xact = false;
         } else if (t < d2) {
-            d2 = t;
-        }
-    }
-    // a candidate evaluated in FP64
-    __device__ __forceinline__ void offer64(double t, int level, int surf, int side, int dim, int dsign, int entry,
-                                            double x, double y, double z) {
-        const float tf = d_finite_lt_inf(t) ? float(t) : FINF;
-        if (tf < d1) {
-            offer(tf, level, surf, side, dim, dsign, entry, x, y, z);
-            xact = true;
-            tx = t;
-        } else if (tf < d2) {
-            d2 = tf;
+            d2 = t; e2 = err;
         }
     }
 };
@@ -1043,7 +1064,7 @@ struct Best2 {
 template <bool CSG>
 __device__ __forceinline__ Best2 distance_f32(const DevGeom& g, const St& s, const DirF& df) {
     Best2 b;
-    b.d1 = FINF; b.d2 = FINF; b.ill = false; b.xact = false; b.wx = b.wy = b.wz = 0.0; b.tx = 0.0;
+    b.d1 = FINF; b.d2 = FINF; b.e1 = 0.f; b.e2 = 0.f; b.ill = false;
     b.h.d = DINF; b.h.level = -1; b.h.surf = -1; b.h.side = 0; b.h.dim = -1; b.h.dsign = 0; b.h.entry = -1;
     double x = s.x, y = s.y, z = s.z;
     const float d3[3] = {df.u, df.v, df.w};
@@ -1061,20 +1082,14 @@ __device__ __forceinline__ Best2 distance_f32(const DevGeom& g, const St& s, con
             const int o3[3] = {of.x, of.y, of.z};
             const int i3[3] = {L.i, L.j, L.k};
             const float e3[3] = {float(xn), float(yn), float(zn)};
-            const double p3[3] = {x, y, z};
-            const double w3[3] = {s.d.iu, s.d.iv, s.d.iw};
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 const bool up = d3[d] > 0.f;
                 if (!(up ? (i3[d] < n3[d] - 1 || l == 0) : (d3[d] < 0.f && (i3[d] > 0 || l == 0)))) continue;
                 const float fo = __ldg((up ? g.l_hif : g.l_lof) + o3[d] + i3[d]);
-                if (fabsf(fo) > F32_EXTENT) {
-                    double t = (__ldg(g.l_grid + o3[d] + i3[d] + (up ? 1 : 0)) - p3[d]) * w3[d];
-                    b.offer64(d_lt0(t) ? 0.0 : t, l, -1 - (2 * d + (up ? 1 : 0)), 0, d, up ? 1 : -1, -1, x, y, z);
-                } else {
-                    const float t = (fo - e3[d]) * v3[d];
-                    b.offer(t < 0.f ? 0.f : t, l, -1 - (2 * d + (up ? 1 : 0)), 0, d, up ? 1 : -1, -1, x, y, z);
-                }
+                const float t = (fo - e3[d]) * v3[d];
+                b.offer(t < 0.f ? 0.f : t, F32_ERR * (fabsf(fo) + fabsf(e3[d])) * fabsf(v3[d]), l,
+                        -1 - (2 * d + (up ? 1 : 0)), 0, d, up ? 1 : -1, -1);
             }
         } else {
             const int2 rg = __ldg(g.c_range + L.cell);
@@ -1085,8 +1100,6 @@ __device__ __forceinline__ Best2 distance_f32(const DevGeom& g, const St& s, con
                 const int lo3[3] = {s0.x, s0.z, s1.x};
                 const int hi3[3] = {s0.y, s0.w, s1.y};
                 const float e3[3] = {float(xn), float(yn), float(zn)};
-                const double p3[3] = {x, y, z};
-                const double w3[3] = {s.d.iu, s.d.iv, s.d.iw};
                 const float* fs = g.c_slabf + 6 * L.cell;
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
@@ -1096,36 +1109,11 @@ __device__ __forceinline__ Best2 distance_f32(const DevGeom& g, const St& s, con
                     const int sid = cs_surface(__ldg(g.cs + e));
                     if (s.on_lev == l && s.on_surf == sid) continue;
                     const float fo = __ldg(fs + 2 * d + (up ? 1 : 0));
-                    if (fabsf(fo) > F32_EXTENT) {
-                        const double t = (__ldg(g.s_coef + 4 * sid) - p3[d]) * w3[d];
-                        b.offer64(d_lt0(t) ? 0.0 : t, l, sid, up ? -1 : 1, -1, 0, e, x, y, z);
-                    } else {
-                        const float t = (fo - e3[d]) * v3[d];
-                        b.offer(t < 0.f ? 0.f : t, l, sid, up ? -1 : 1, -1, 0, e, x, y, z);
-                    }
+                    const float t = (fo - e3[d]) * v3[d];
+                    b.offer(t < 0.f ? 0.f : t, F32_ERR * (fabsf(fo) + fabsf(e3[d])) * fabsf(v3[d]), l, sid,
+                            up ? -1 : 1, -1, 0, e);
                 }
-                // general planes and the remaining surfaces are measured in the
-                // universe's frame: FP64 where it is large
-                const bool big = beyond_f32_extent(x, y, z);
-                if ((rg.y & CS_PAIR_FLAG) && big) {
-                    const int4 p0 = __ldg(g.c_pair + 2 * L.cell), p1 = __ldg(g.c_pair + 2 * L.cell + 1);
-                    const int lo3p[3] = {p0.x, p0.z, p1.x};
-                    const int hi3p[3] = {p0.y, p0.w, p1.y};
-#pragma unroll
-                    for (int f = 0; f < 3; ++f) {
-                        const int ea = lo3p[f] >= 0 ? lo3p[f] : hi3p[f];
-                        if (ea < 0) continue;
-                        double c0, c1, c2, c3;
-                        load_coef(g, cs_surface(__ldg(g.cs + ea)), c0, c1, c2, c3);
-                        const double den = (c0 * s.d.u + c1 * s.d.v) + c2 * s.d.w;
-                        const int e = d_lt0(den) ? lo3p[f] : (d_gt0(den) ? hi3p[f] : -1);
-                        if (e < 0) continue;
-                        const int sid = cs_surface(__ldg(g.cs + e));
-                        if (s.on_lev == l && s.on_surf == sid) continue;
-                        const double t = (__ldg(g.s_coef + 4 * sid + 3) - ((c0 * x + c1 * y) + c2 * z)) / den;
-                        b.offer64(d_lt0(t) ? 0.0 : t, l, sid, d_lt0(den) ? 1 : -1, -1, 0, e, x, y, z);
-                    }
-                } else if (rg.y & CS_PAIR_FLAG) {
+                if (rg.y & CS_PAIR_FLAG) {
                     const float xf = float(x), yf = float(y), zf = float(z);
                     const int4 p0 = __ldg(g.c_pair + 2 * L.cell), p1 = __ldg(g.c_pair + 2 * L.cell + 1);
                     const int lo3p[3] = {p0.x, p0.z, p1.x};
@@ -1142,32 +1130,33 @@ __device__ __forceinline__ Best2 distance_f32(const DevGeom& g, const St& s, con
                         if (s.on_lev == l && s.on_surf == sid) continue;
                         const float dw = __ldg(g.s_coeff + sid).w;
                         const float t = (dw - ((cf.x * xf + cf.y * yf) + cf.z * zf)) / den;
-                        b.offer(t < 0.f ? 0.f : t, l, sid, den < 0.f ? 1 : -1, -1, 0, e, x, y, z);
+                        const float err =
+                            F32_ERR * (((fabsf(cf.x * xf) + fabsf(cf.y * yf)) + fabsf(cf.z * zf)) + fabsf(dw)) /
+                            fabsf(den);
+                        b.offer(t < 0.f ? 0.f : t, err, l, sid, den < 0.f ? 1 : -1, -1, 0, e);
                     }
                 }
                 const int2 rr = __ldg(g.c_rest + L.cell);
                 first = rr.x; cnt = rr.y; by_index = true;
             }
             if (cnt > 0) {
-                const bool big = beyond_f32_extent(x, y, z);
                 const float xf = float(x), yf = float(y), zf = float(z);
                 for (int k = 0; k < cnt; ++k) {
                     const int ei = by_index ? __ldg(g.rest_e + first + k) : first + k;
                     const int e = __ldg(g.cs + ei);
                     const int sid = cs_surface(e), side = cs_side(e);
                     const bool on = (s.on_lev == l && s.on_surf == sid);
-                    if (big) {
-                        b.offer64(surface_distance(g, sid, cs_type(e), side, on, x, y, z, s.d), l, sid, side, -1, 0,
-                                  ei, x, y, z);
-                    } else {
-                        const float t = surface_distance_f(g, sid, cs_type(e), side, on, xf, yf, zf, df, b.ill);
-                        b.offer(t, l, sid, side, -1, 0, ei, x, y, z);
-                    }
+                    float err = 0.f;
+                    const float t = surface_distance_f(g, sid, cs_type(e), side, on, xf, yf, zf, df, b.ill, err);
+                    b.offer(t, err, l, sid, side, -1, 0, ei);
                 }
             }
         }
         x = xn; y = yn; z = zn;
     }
+    // the winner must be accurate to F32_ERR_MAX and certainly ahead of the
+    // runner-up; else the caller redoes the flight in FP64
+    if (b.d1 < FINF && (b.e1 > F32_ERR_MAX * fmaxf(1.0f, b.d1) || b.d2 - b.d1 <= b.e1 + b.e2)) b.ill = true;
     b.h.d = double(b.d1);
     return b;
 }
@@ -1550,7 +1539,9 @@ __device__ __forceinline__ int step_flight(const DevGeom& g, St& s, Hit& h, Ctx&
 // crossings keep the FP32 length: only small linear cell scans follow them.
 __device__ __forceinline__ double f32_crossing_length(const DevGeom& g, const St& s, const Best2& b, bool& exact) {
     const Hit& h = b.h;
-    if (b.xact) { exact = true; return b.tx; }
+    // FP64 coordinates of the winner's level frame (the chain the scan took)
+    double wx, wy, wz;
+    local_at(s, h.level, wx, wy, wz);
     double t = 0.0;
     bool plane = false;
     if (h.surf < 0) {
@@ -1564,7 +1555,7 @@ __device__ __forceinline__ double f32_crossing_length(const DevGeom& g, const St
         const int4 of = __ldg(g.l_off + lat);
         const int go = h.dim == 0 ? of.x : (h.dim == 1 ? of.y : of.z);
         const double gv = __ldg(g.l_grid + go + idx + (h.dsign > 0 ? 1 : 0));
-        const double pv = h.dim == 0 ? b.wx : (h.dim == 1 ? b.wy : b.wz);
+        const double pv = h.dim == 0 ? wx : (h.dim == 1 ? wy : wz);
         const double iv = h.dim == 0 ? s.d.iu : (h.dim == 1 ? s.d.iv : s.d.iw);
         t = (gv - pv) * iv;
         plane = true;
@@ -1572,18 +1563,29 @@ __device__ __forceinline__ double f32_crossing_length(const DevGeom& g, const St
         const int type = __ldg(g.s_info + h.surf) & 15;
         if (type <= S_PZ) {
             const double gv = __ldg(g.s_coef + 4 * h.surf);
-            const double pv = type == S_PX ? b.wx : (type == S_PY ? b.wy : b.wz);
+            const double pv = type == S_PX ? wx : (type == S_PY ? wy : wz);
             const double iv = type == S_PX ? s.d.iu : (type == S_PY ? s.d.iv : s.d.iw);
             t = (gv - pv) * iv;
             plane = true;
         } else if (type == S_P) {
-            t = surface_distance(g, h.surf, type, h.side, false, b.wx, b.wy, b.wz, s.d);
+            t = surface_distance(g, h.surf, type, h.side, false, wx, wy, wz, s.d);
             plane = true;
         }
     }
     exact = plane;
     if (!plane) return double(b.d1);
     return d_lt0(t) ? 0.0 : t;
+}
+
+// The FP64 flight as a call, for the FP32-local flight's close calls (a
+// fraction of a percent of the flights): inlined there it would double the
+// FP32 kernel's code and registers.
+template <bool CSG, int FLAGS>
+static __device__ __noinline__ int step_flight_fp64_call(const DevGeom& g, St& s, Hit& h, Ctx& c, const RunP& rp,
+                                                         unsigned long long* __restrict__ tally, Counts& cnt,
+                                                         int* __restrict__ tr_inst, double* __restrict__ tr_len,
+                                                         long long i) {
+    return step_flight<CSG, FLAGS>(g, s, h, c, rp, tally, cnt, tr_inst, tr_len, i);
 }
 
 // FP32-local flight: distances and the flight decision in FP32, position
@@ -1599,7 +1601,7 @@ __device__ __forceinline__ int step_flight_f32(const DevGeom& g, St& s, Hit& h, 
     const float dcf = sigf > 0.f ? float(s.tau) / sigf : FINF;
     if (b.ill || close_call(b.d1, b.d2) || close_call(b.d1, dcf) || !(fminf(b.d1, dcf) < FINF)) {
         cnt.k[TRK_K_CLOSE_CALLS]++;
-        return step_flight<CSG, FLAGS>(g, s, h, c, rp, tally, cnt, tr_inst, tr_len, i);
+        return step_flight_fp64_call<CSG, FLAGS>(g, s, h, c, rp, tally, cnt, tr_inst, tr_len, i);
     }
     h = b.h;
     const bool crossing = b.d1 < dcf;

@@ -19,6 +19,10 @@
 // bit for bit.
 #include <cstdint>
 
+// the event kernels read the BVH from a shared-memory copy (see k_event)
+#ifndef TRK_BVH_SMEM
+#define TRK_BVH_SMEM 1
+#endif
 #include "trk.h"
 #include "trk_device.cuh"
 #include "trk_internal.h"
@@ -33,27 +37,42 @@ namespace {
 
 // Each warp owns `slots` particle slots and its own queues in shared memory;
 // warps never synchronise with each other.
+// n_snodes > 0: the geometry's BVH nodes (all n_snodes of them) are copied
+// into shared memory after the queues at launch, and every BVH walk of the
+// block reads that copy (Sec. 4.3's search, its nodes next to the SM).
 template <bool CSG, bool F32, int FLAGS>
 __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, long long n, const RunP rp,
                                       const EvBuf B, int slots, unsigned long long max_rounds,
                                       unsigned long long* __restrict__ tally,
                                       unsigned long long* __restrict__ counters,
-                                      unsigned long long* __restrict__ rec) {
+                                      unsigned long long* __restrict__ rec, int n_snodes, int sort_interval) {
     extern __shared__ QIdx smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#if TRK_BVH_SMEM
+    {
+        BvhNode* sn = reinterpret_cast<BvhNode*>(smem + EV_QUEUES * slots * (EV_BLOCK / 32));
+        const float4* src = reinterpret_cast<const float4*>(g.nodes);
+        float4* dst = reinterpret_cast<float4*>(sn);
+        for (int k = threadIdx.x; k < 4 * n_snodes; k += EV_BLOCK) dst[k] = __ldg(src + k);
+        if (threadIdx.x == 0) s_bvh_nodes = n_snodes > 0 ? sn : nullptr;
+        __syncthreads();
+    }
+#endif
     QIdx* base_q = smem + warp * EV_QUEUES * slots;
-    QIdx* qfl = base_q;                  // NFC flight queues
-    QIdx* qc = base_q + NFC * slots;     // collide (at refill: failed births)
-    QIdx* qf = base_q + (NFC + 1) * slots;
-    QIdx* qx = base_q + (NFC + 2) * slots;   // MAXL cross queues, one per crossing level
+    QIdx* qfl = base_q;                  // flight (slot | leaf class << QSLOT_BITS)
+    QIdx* qc = base_q + slots;           // collide (at refill: failed births; at a sort: scratch)
+    QIdx* qf = base_q + 2 * slots;
+    QIdx* qx = base_q + 3 * slots;       // MAXL cross queues, one per crossing level
     const int slot0 = (blockIdx.x * (EV_BLOCK / 32) + warp) * slots;
+#ifndef TRK_EV_SORT
+#define TRK_EV_SORT 1
+#endif
+    const bool sorting = TRK_EV_SORT && sort_interval > 0;
     Counts cnt;
 #pragma unroll
     for (int k = 0; k < NCOUNT; ++k) cnt.k[k] = 0;
     for (int k = lane; k < slots; k += 32) qf[k] = QIdx(k);
-    int n_fl[NFC];
-#pragma unroll
-    for (int c = 0; c < NFC; ++c) n_fl[c] = 0;
+    int n_fly = 0;
     int n_free = slots;
     bool exhausted = false;
     __syncwarp();
@@ -62,12 +81,9 @@ __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, lo
         // in batches of at least a warp's width (birth runs the universe
         // searches from the root, whose lanes diverge least when the batch
         // is full), unless the flight queues are running low
-        int n_live = 0;
-#pragma unroll
-        for (int q = 0; q < NFC; ++q) n_live += n_fl[q];
         int got = 0;
         unsigned long long first = 0;
-        if (!exhausted && n_free > 0 && (n_free >= TRK_EV_REFILL_MIN || n_live < 32)) {
+        if (!exhausted && n_free > 0 && (n_free >= TRK_EV_REFILL_MIN || n_fly < 32)) {
             if (lane == 0) first = atomicAdd(B.ctr, (unsigned long long)n_free);
             first = __shfl_sync(0xffffffffu, first, 0);
             long long avail = (long long)n - (long long)first;
@@ -98,7 +114,7 @@ __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, lo
                         cnt.k[TRK_K_LOST]++;
                     } else {
                         unsigned char* r = rec_at<FLAGS>(B, slot);
-                        cls = flight_class<CSG>(g, s);
+                        cls = sorting ? flight_class<CSG>(g, s) : 0;
                         D2(r, R_XY) = make_double2(s.x, s.y);
                         D2(r, R_ZT) = make_double2(s.z, s.tau);
                         store_dir(r, s);
@@ -113,8 +129,7 @@ __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, lo
                     if (FLAGS & F_FISS) fission_out(rp, pidx, 0, 0.0, 0.0, 0.0);
                 }
             }
-#pragma unroll
-            for (int q = 0; q < NFC; ++q) wpush(ok && cls == q, slot - slot0, qfl + q * slots, n_fl[q]);
+            wpush(ok, (slot - slot0) | (cls << QSLOT_BITS), qfl, n_fly);
             wpush(k < got && !ok, slot - slot0, qc, n_park);
         }
         __syncwarp();
@@ -124,16 +139,19 @@ __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, lo
             wpush(k < n_park, k < n_park ? qc[k] : 0, qf, n_free);
         }
         __syncwarp();
-        int n_fly = 0;
-#pragma unroll
-        for (int q = 0; q < NFC; ++q) n_fly += n_fl[q];
         if (n_fly == 0 && exhausted) break;
         if (round >= max_rounds) {
             if (lane == 0) kernel_status(counters, TRK_E_TIMEOUT);
             break;
         }
         // ---- flight: distance_to_surface, tally, move ----------------------
-        // the class queues are walked as one concatenated list
+        // every sort_interval rounds the flight list is reordered by class
+        // (through the collide queue, empty until the flight pass fills it)
+        if (sorting && n_fly > 32 && round % (unsigned long long)sort_interval == 0) {
+            sort_by_class(qfl, n_fly, qc);
+            for (int k = lane; k < n_fly; k += 32) qfl[k] = qc[k];
+            __syncwarp();
+        }
         int n_cross[MAXL], n_coll = 0;
 #pragma unroll
         for (int l = 0; l < MAXL; ++l) n_cross[l] = 0;
@@ -141,11 +159,7 @@ __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, lo
             const int k = b + lane;
             int a = A_DONE, slot = 0, hl = -1;
             if (k < n_fly) {
-                int q = 0, kk = k;
-#pragma unroll
-                for (int c = 0; c < NFC - 1; ++c)
-                    if (q == c && kk >= n_fl[c]) { kk -= n_fl[c]; q = c + 1; }
-                slot = slot0 + qfl[q * slots + kk];
+                slot = slot0 + int(unsigned(qfl[k]) & QSLOT_MASK);
                 unsigned char* r = rec_at<FLAGS>(B, slot);
                 St s;
                 const double2 xy = D2(r, R_XY), zt = D2(r, R_ZT);
@@ -184,8 +198,7 @@ __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, lo
             wpush(live && a == A_DONE, slot - slot0, qf, n_free);
         }
         __syncwarp();
-#pragma unroll
-        for (int q = 0; q < NFC; ++q) n_fl[q] = 0;
+        n_fly = 0;
         // ---- cross_surface, then change_direction ---------------------------
 #pragma unroll 1
         for (int lq = 0; lq < MAXL; ++lq)
@@ -215,15 +228,14 @@ __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, lo
                     trace_tail<FLAGS>(pidx, c, rp);
                     if (FLAGS & F_FISS) fission_out(rp, pidx, 0, 0.0, 0.0, 0.0);
                 } else {
-                    cls = flight_class<CSG>(g, s);
+                    cls = sorting ? flight_class<CSG>(g, s) : 0;
                     store_levels<CSG>(g, r, s, 0);
                     store_ctx<FLAGS>(r, pidx, c, make_misc(0, s, cls));
                     if (cnt.k[TRK_K_REFLECTIONS] != refl0) store_dir(r, s);
                 }
             }
             const bool live = k < n_cross[lq];
-#pragma unroll
-            for (int q = 0; q < NFC; ++q) wpush(live && a == A_FLY && cls == q, slot - slot0, qfl + q * slots, n_fl[q]);
+            wpush(live && a == A_FLY, (slot - slot0) | (cls << QSLOT_BITS), qfl, n_fly);
             wpush(live && a == A_DONE, slot - slot0, qf, n_free);
         }
         for (int b = 0; b < n_coll; b += 32) {
@@ -262,8 +274,7 @@ __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, lo
                 }
             }
             const bool live = k < n_coll;
-#pragma unroll
-            for (int q = 0; q < NFC; ++q) wpush(live && a == A_FLY && cls == q, slot - slot0, qfl + q * slots, n_fl[q]);
+            wpush(live && a == A_FLY, (slot - slot0) | (cls << QSLOT_BITS), qfl, n_fly);
             wpush(live && a == A_DONE, slot - slot0, qf, n_free);
         }
         __syncwarp();
@@ -280,13 +291,17 @@ constexpr int EV_WARPS = EV_BLOCK / 32;
 // Resident CTAs per SM: the register budget's minimum (TRK_EV_MINB), capped
 // by shared memory.  Deterministic, so the work-buffer size a caller queries
 // always matches the launch.
+// BVH nodes staged in shared memory per block at most (64 B each); a
+// geometry with more nodes walks them from global memory.
+constexpr int EV_SMEM_NODES = TRK_BVH_SMEM ? 384 : 0;
+
 int event_grid(int slots) {
     int dev = 0, sms = 152, smem_sm = 228 * 1024;
     if (cudaGetDevice(&dev) == cudaSuccess) {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     }
-    const size_t smem = size_t(EV_QUEUES) * slots * EV_WARPS * sizeof(QIdx);
+    const size_t smem = size_t(EV_QUEUES) * slots * EV_WARPS * sizeof(QIdx) + size_t(EV_SMEM_NODES) * sizeof(BvhNode);
     const int by_smem = int(size_t(smem_sm) / (smem + 1024));
     int per_sm = TRK_EV_MINB > 0 ? TRK_EV_MINB : 1;
     if (per_sm > by_smem) per_sm = by_smem;
@@ -311,7 +326,8 @@ trk_status event_fits(trk_geom_t g, bool csg, const char* where) {
 
 trk_status launch_event(trk_geom_t g, const ParticlesView& P, long long n, const RunP& rp, bool csg, bool f32,
                         int flags, unsigned long long* tally, unsigned long long* cnt, unsigned long long* rec,
-                        void* work, size_t work_bytes, int slots, int grid, int max_rounds_opt, cudaStream_t s) {
+                        void* work, size_t work_bytes, int slots, int grid, int max_rounds_opt, int sort_interval,
+                        cudaStream_t s) {
     const long long T = (long long)slots * EV_WARPS * grid;
     const trk_status fit = event_fits(g, csg, "run_histories (event)");
     if (fit != TRK_OK) return fit;
@@ -322,7 +338,8 @@ trk_status launch_event(trk_geom_t g, const ParticlesView& P, long long n, const
     const EvBuf B = make_buf(work, T);
     cudaError_t e = cudaMemsetAsync(B.ctr, 0, 8, s);
     if (e != cudaSuccess) return trk_status(set_error(TRK_E_CUDA, "run_histories (event): %s", cudaGetErrorString(e)));
-    const size_t smem = size_t(EV_QUEUES) * slots * EV_WARPS * sizeof(QIdx);
+    const int n_snodes = (g->dg.accel == 0 && g->n_nodes <= EV_SMEM_NODES) ? g->n_nodes : 0;
+    const size_t smem = size_t(EV_QUEUES) * slots * EV_WARPS * sizeof(QIdx) + size_t(n_snodes) * sizeof(BvhNode);
     // a particle needs at most max_segments + 1 flight rounds; a warp holds
     // `slots` particles at a time and refills every round
     const unsigned long long per_warp = (unsigned long long)(n / (T / slots) + slots + 1);
@@ -332,7 +349,8 @@ trk_status launch_event(trk_geom_t g, const ParticlesView& P, long long n, const
     do {                                                                                                     \
         auto k = k_event<C, F32V, F>;                                                                        \
         if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)); \
-        k<<<grid, EV_BLOCK, smem, s>>>(g->dg, P, n, rp, B, slots, max_rounds, tally, cnt, rec);             \
+        k<<<grid, EV_BLOCK, smem, s>>>(g->dg, P, n, rp, B, slots, max_rounds, tally, cnt, rec, n_snodes,     \
+                                        sort_interval);                                                     \
     } while (0)
     if (f32) {
 #ifndef TRK_EXACT

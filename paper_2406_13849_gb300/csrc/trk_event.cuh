@@ -14,22 +14,24 @@ namespace ev {
 using namespace trk::dev;
 
 constexpr int EV_BLOCK = 256;
-// Flight queues by the class of the particle's leaf cell (cells whose
-// distance code takes the same path: no curved surface, one cylinder from
-// inside, one from outside, other), so a flight batch's lanes mostly run the
-// same branches; the classes are concatenated in one pass, so a partial batch
-// occurs only once per flight phase.  Measured on the three-level core, the
-// sorting does not pay for its extra queue traffic (4 classes: -2 to -5%), so
-// the default is one class.
-#ifndef TRK_EV_NFC
-#define TRK_EV_NFC 1
-#endif
-constexpr int NFC = TRK_EV_NFC;
+// Flight queue entries carry the class of the particle's leaf cell (cells
+// whose distance code takes the same path: no curved surface, one cylinder
+// from inside, one from outside, other) above the slot index; every
+// sort_interval rounds (trk_run_opts) the warp reorders its flight queue by
+// that class before the flight pass, so a flight batch's lanes mostly run
+// the same branches.
+constexpr int QSLOT_BITS = 12;
+constexpr unsigned QSLOT_MASK = (1u << QSLOT_BITS) - 1u;
+constexpr int NCLASS = 4;
+// Queue entries are slot indices within the warp's own range (< 512) and,
+// in the flight queue, the class bits above them: 16 bits each, half the
+// shared memory of 32-bit entries, which the L1 cache gets.
+using QIdx = unsigned short;
 // Free slots a warp collects before it refills them (see the refill step).
 #ifndef TRK_EV_REFILL_MIN
 #define TRK_EV_REFILL_MIN 32
 #endif
-constexpr int EV_QUEUES = NFC + 2 + MAXL;   // flight by class, collide, free, cross per level
+constexpr int EV_QUEUES = 3 + MAXL;   // flight, collide (sort scratch), free, cross per level
 
 // Minimum resident CTAs per SM the register allocation must allow (0: let
 // the compiler choose).  Two CTAs (16 warps, 128 registers a thread) hide
@@ -175,11 +177,41 @@ __device__ __forceinline__ void load_levels(const DevGeom& g, unsigned char* r, 
 // Flight class of the particle's leaf cell (a rect-array leaf is class 0).
 template <bool CSG>
 __device__ __forceinline__ int flight_class(const DevGeom& g, const St& st) {
-    if (NFC == 1) return 0;
     const Lv L = lv_get(st, st.nlev - 1);
     if (!CSG && __ldg(g.u_info + L.u).w >= 0) return 0;
     const int c = __ldg(g.c_fcls + L.cell);
-    return c < NFC ? c : NFC - 1;
+    return c < NCLASS ? c : NCLASS - 1;
+}
+
+// Stable counting sort of a warp's queue list[0..n) by the class bits of its
+// entries into out[0..n) (all 32 lanes call; ballots keep lane order).
+__device__ __forceinline__ void sort_by_class(const QIdx* list, int n, QIdx* out) {
+    const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    int off[NCLASS];
+#pragma unroll
+    for (int c = 0; c < NCLASS; ++c) off[c] = 0;
+    for (int b = 0; b < n; b += 32) {
+        const int k = b + lane;
+        const int c = k < n ? int(unsigned(list[k]) >> QSLOT_BITS) : NCLASS;
+#pragma unroll
+        for (int q = 0; q < NCLASS; ++q) off[q] += __popc(__ballot_sync(0xffffffffu, c == q));
+    }
+    int start = 0;
+#pragma unroll
+    for (int q = 0; q < NCLASS; ++q) { const int t = off[q]; off[q] = start; start += t; }
+    for (int b = 0; b < n; b += 32) {
+        const int k = b + lane;
+        const QIdx e = k < n ? list[k] : QIdx(0);
+        const int c = k < n ? int(unsigned(e) >> QSLOT_BITS) : NCLASS;
+#pragma unroll
+        for (int q = 0; q < NCLASS; ++q) {
+            const unsigned m = __ballot_sync(0xffffffffu, c == q);
+            if (c == q) out[off[q] + __popc(m & below)] = e;
+            off[q] += __popc(m);
+        }
+    }
+    __syncwarp();
 }
 
 // The cells chunk and the universes word (on-surface surface, hit reference,
@@ -238,10 +270,6 @@ __device__ __forceinline__ void store_ctx(unsigned char* r, int pidx, const Ctx&
 
 // Warp-level append of `v` to `list` when `flag` (all 32 lanes call);
 // `count` is warp-uniform and advanced in every lane.
-// Queue entries are slot indices within the warp's own range (< 512), 16 bits
-// each: half the shared memory of 32-bit entries, which the L1 cache gets.
-using QIdx = unsigned short;
-
 __device__ __forceinline__ void wpush(bool flag, int v, QIdx* list, int& count) {
     const unsigned m = __ballot_sync(0xffffffffu, flag);
     const int lane = threadIdx.x & 31;

@@ -644,7 +644,9 @@ trk_status run_histories(trk_geom_t g, const void* dev_particles, int64_t n, uin
         if (slots < 32 || slots > 512) return trk_status(set_error(TRK_E_INVALID, "queue_depth must be in [32, 512]"));
         const int grid = o.grid > 0 ? o.grid : event_grid(slots);
         if (o.max_rounds < 0) return trk_status(set_error(TRK_E_INVALID, "max_rounds must be >= 0"));
-        return launch_event(g, P, n, rp, csg, f32, flags, T, C, R, dev_work, work_bytes, slots, grid, o.max_rounds, s);
+        if (o.sort_interval < 0) return trk_status(set_error(TRK_E_INVALID, "sort_interval must be >= 0"));
+        return launch_event(g, P, n, rp, csg, f32, flags, T, C, R, dev_work, work_bytes, slots, grid, o.max_rounds,
+                            o.sort_interval, s);
     }
     const int block = o.block > 0 ? o.block : 128;
     if (block > 128 || (block & 31)) return trk_status(set_error(TRK_E_INVALID, "run_histories: block must be a multiple of 32, <= 128"));
@@ -724,7 +726,7 @@ trk_status trk_trace(trk_geom_t g, const void* dev_particles, int64_t n, int32_t
         rp.tr_inst = dev_inst;
         rp.tr_len = dev_len;
         return launch_event(g, P, n, rp, tracker == TRK_TRACKER_CSG, o.precision == TRK_FP32_LOCAL, F_TRACE, T, C,
-                            nullptr, dev_work, work_bytes, slots, grid, o.max_rounds, s);
+                            nullptr, dev_work, work_bytes, slots, grid, o.max_rounds, o.sort_interval, s);
     }
     if (o.mode != TRK_MODE_HISTORY) return trk_status(set_error(TRK_E_INVALID, "trk_trace: unknown mode %d", o.mode));
     if (o.precision == TRK_FP32_LOCAL) {
@@ -1128,7 +1130,7 @@ trk_status power_iteration(trk_geom_t g, int64_t n, int inactive, int cycles, do
             const int slots = event_slots(o);
             const int grid = o.grid > 0 ? o.grid : event_grid(slots);
             st = launch_event(g, P, n, rp, csg, false, flags, T, C, nullptr, w + L.ev, L.total - L.ev, slots, grid,
-                              o.max_rounds, s);
+                              o.max_rounds, o.sort_interval, s);
         } else {
             const int block = o.block > 0 ? o.block : 128;
             if (block > 128 || (block & 31)) return trk_status(set_error(TRK_E_INVALID, "power_iteration: block must be a multiple of 32, <= 128"));

@@ -25,6 +25,6 @@ trk_status event_fits(trk_geom_t g, bool csg, const char* where);
 trk_status launch_event(trk_geom_t g, const ParticlesView& P, long long n, const dev::RunP& rp, bool csg, bool f32,
                         int flags,
                         unsigned long long* tally, unsigned long long* cnt, unsigned long long* rec, void* work,
-                        size_t work_bytes, int slots, int grid, int max_rounds, cudaStream_t s);
+                        size_t work_bytes, int slots, int grid, int max_rounds, int sort_interval, cudaStream_t s);
 
 }  // namespace trk

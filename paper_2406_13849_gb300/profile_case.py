@@ -46,6 +46,7 @@ def main() -> None:
     ap.add_argument("--particles", type=int, default=3_000_000)
     ap.add_argument("--launches", type=int, default=1)
     ap.add_argument("--queue-depth", type=int, default=512)
+    ap.add_argument("--sort-interval", type=int, default=0)
     ap.add_argument("--members", type=int, default=8)
     ap.add_argument("--chunk", type=int, default=4096)
     ap.add_argument("--rays", type=int, default=1 << 18)
@@ -65,7 +66,7 @@ def main() -> None:
     for name in names:
         opts = N.default_opts(tracker=trk[name], mode=N.MODE_EVENT if args.mode == "event" else N.MODE_HISTORY,
                               precision=N.FP64 if args.precision == "fp64" else N.FP32_LOCAL,
-                              seed=1, p_absorb=0.25, queue_depth=args.queue_depth)
+                              seed=1, p_absorb=0.25, queue_depth=args.queue_depth, sort_interval=args.sort_interval)
         run_case(g, dev, n, opts, args, name)
 
 
@@ -85,11 +86,13 @@ def run_case(g, dev, n, opts, args, name):
         g.run_histories(parts, n, tally=tally, counters=cnt, opts=opts, work=work)
         b.record(stream)
         torch.cuda.synchronize()
-        seg = int(cnt.cpu()[0])
+        c = cnt.cpu()
+        seg = int(c[0])
         ms = a.elapsed_time(b)
-        out.append({"segments": seg, "ms": ms, "segments_per_s": seg / (ms / 1e3)})
+        out.append({"segments": seg, "ms": ms, "segments_per_s": seg / (ms / 1e3),
+                    "redone_in_fp64": int(c[N.K["close_calls"]]) / max(1, seg)})
     print(json.dumps({"workload": args.workload, "tracker": name, "mode": args.mode, "precision": args.precision,
-                      "particles": n, "launches": out}), flush=True)
+                      "particles": n, "sort_interval": args.sort_interval, "launches": out}), flush=True)
 
 
 def run_batch(dev, args):

@@ -157,13 +157,19 @@ def test_fp32_local_distance_per_point(name, tracker, mode):
     d, lev, inst, close = g.distance_to_surface(torch.from_numpy(xyz).cuda(), torch.from_numpy(w).cuda(),
                                                 tracker=tracker, precision=N.FP32_LOCAL, with_close=True)
     gd, gl, gi, cc = d.cpu().numpy(), lev.cpu().numpy(), inst.cpu().numpy(), close.cpu().numpy().astype(bool)
-    assert np.array_equal(gi, oi)
-    inside = oi >= 0
+    # find_cell (FP64 in both precisions): a point within rounding of a
+    # surface may land on either side, and must then be near it
+    diff = np.nonzero(gi != oi)[0]
+    if len(diff):
+        cl = o.clearance(xyz[diff], w[diff], np.zeros(len(diff)))
+        assert (cl[:, 0] < C.NEAR).all(), (diff[:5], cl[:5, 0])
+    inside = (oi >= 0) & (gi == oi)
     f32 = inside & ~cc & np.isfinite(od)
     rel = np.abs(gd[f32] - od[f32]) / np.maximum(1.0, np.abs(od[f32]))
     lev_ok = gl[f32] == ol[f32]
     print(f"\n{name} tracker {tracker}: points {inside.sum()}, FP32 {f32.sum()}, redone in FP64 {(inside & cc).sum()}, "
-          f"max rel {rel.max():.3g}, p99.9 {np.quantile(rel, 0.999):.3g}, level differs {(~lev_ok).sum()}")
+          f"max rel {rel.max():.3g}, p99.9 {np.quantile(rel, 0.999):.3g}, level differs {(~lev_ok).sum()}, "
+          f"cell differs {len(diff)}")
     assert (rel <= 1e-5).all() and lev_ok.all()
     # the redone ones: the FP64 rule
     red = inside & cc
