@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(128) k_batched(BatchHeader* __restrict__ hdr, 
 // and CSG-tracker entries run as two launches (the rect chunks come first).
 // ---------------------------------------------------------------------------
 using namespace trk::ev;
-constexpr int BEV_QUEUES = 4 + MAXL;   // flight, next flight, collide (sort scratch), free, cross per level
+constexpr int BEV_QUEUES = 4 + MAXL;   // flight, collide, free, FP64 redo, cross per level
 
 __device__ __forceinline__ int entry_of(const BatchEntry* table, int ng, unsigned long long c) {
     int lo = 0, hi = ng - 1;
@@ -147,10 +147,10 @@ __global__ void TRK_EV_BOUNDS k_batched_ev(BatchHeader* __restrict__ hdr, const 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     QIdx* base_q = smem + warp * BEV_QUEUES * slots;
     QIdx* fly = base_q;                  // slot | leaf class << QSLOT_BITS
-    QIdx* next = base_q + slots;
-    QIdx* qc = base_q + 2 * slots;       // collide (at a sort: scratch)
-    QIdx* qf = base_q + 3 * slots;
-    QIdx* qx = base_q + 4 * slots;
+    QIdx* qc = base_q + slots;           // collide
+    QIdx* qf = base_q + 2 * slots;       // free
+    QIdx* qr = base_q + 3 * slots;       // FP32-local flights to redo in FP64
+    QIdx* qx = base_q + 4 * slots;       // cross, one queue per level
     const bool sorting = sort_interval > 0;
     const int slot0 = (blockIdx.x * (EV_BLOCK / 32) + warp) * slots;
     const int ng = hdr->n_geom;
@@ -159,7 +159,12 @@ __global__ void TRK_EV_BOUNDS k_batched_ev(BatchHeader* __restrict__ hdr, const 
 #pragma unroll
     for (int k = 0; k < NCOUNT; ++k) cnt.k[k] = 0;
     for (int k = lane; k < slots; k += 32) qf[k] = QIdx(k);
-    int n_fly = 0, n_free = slots;
+    // queue counts (warp-uniform); every queue keeps what a pass leaves
+    // (batch_run) for the next round
+    int n_fly = 0, n_coll = 0, n_redo = 0, n_free = slots;
+    int n_cross[MAXL];
+#pragma unroll
+    for (int l = 0; l < MAXL; ++l) n_cross[l] = 0;
     int ge = -1;                   // current entry, warp-uniform
     long long pn = 0, pb = 0;      // next particle and end of the current chunk
     long long pend = -1;           // chunk pulled for another entry
@@ -174,9 +179,12 @@ __global__ void TRK_EV_BOUNDS k_batched_ev(BatchHeader* __restrict__ hdr, const 
             if (c >= c_end) exhausted = true;
             else pend = (long long)c;
         }
+        int queued = n_fly + n_coll + n_redo;
+#pragma unroll
+        for (int l = 0; l < MAXL; ++l) queued += n_cross[l];
         if (pend >= 0) {
             const int e = entry_of(table, ng, (unsigned long long)pend);
-            if (e == ge || n_fly == 0) {
+            if (e == ge || queued == 0) {
                 if (e != ge) {
                     if (ge >= 0) flush_counts(cnt, table[ge].counters);
 #pragma unroll
@@ -233,36 +241,52 @@ __global__ void TRK_EV_BOUNDS k_batched_ev(BatchHeader* __restrict__ hdr, const 
                 }
                 if (!ok && rec) finish<FLAGS>(pidx, c, rec);
             }
+            // failed births park past the collide queue's entries (room:
+            // got <= n_free <= slots - n_coll)
             wpush(ok, (slot - slot0) | (cls << QSLOT_BITS), fly, n_fly);
-            wpush(k < got && !ok, slot - slot0, next, n_park);
+            wpush(k < got && !ok, slot - slot0, qc + n_coll, n_park);
         }
         __syncwarp();
         n_free -= got;
+        queued += got - n_park;
         for (int b = 0; b < n_park; b += 32) {
             const int k = b + lane;
-            wpush(k < n_park, k < n_park ? next[k] : 0, qf, n_free);
+            wpush(k < n_park, k < n_park ? qc[n_coll + k] : 0, qf, n_free);
         }
         __syncwarp();
-        if (n_fly == 0 && exhausted && pend < 0 && pn >= pb) break;
+        if (queued == 0 && exhausted && pend < 0 && pn >= pb) break;
+        bool full = n_fly >= 32 || n_coll >= 32 || n_redo >= 32;
+#pragma unroll
+        for (int l = 0; l < MAXL; ++l) full = full || n_cross[l] >= 32;
+        // tails run too when the chunk is used up and no more of this
+        // geometry follows (the source is exhausted, or the next chunk waits
+        // for the slots to drain), or when no queue holds a full batch (so
+        // every round advances: a full batch, or every queued particle)
+        const bool drain = (pn >= pb && (exhausted || pend >= 0)) || !full;
         if (round >= max_rounds) {
             if (lane == 0) kernel_status(E.counters, TRK_E_TIMEOUT);
             break;
         }
         // ---- flight ------------------------------------------------------------
         // every sort_interval rounds the flight list is reordered by class
+        // (through the free queue's unused tail: slots - n_free >= n_fly)
         if (sorting && n_fly > 32 && round % (unsigned long long)sort_interval == 0) {
-            sort_by_class(fly, n_fly, qc);
-            for (int k = lane; k < n_fly; k += 32) fly[k] = qc[k];
+            sort_by_class(fly, n_fly, qf + n_free);
+            for (int k = lane; k < n_fly; k += 32) fly[k] = qf[n_free + k];
             __syncwarp();
         }
-        int n_cross[MAXL], n_coll = 0;
-#pragma unroll
-        for (int l = 0; l < MAXL; ++l) n_cross[l] = 0;
-        for (int b = 0; b < n_fly; b += 32) {
+        // FP32-local flights that need FP64 (A_REDO) wait in their own queue
+        // and are redone in a second pass over full batches (one FP64 step
+        // per 32 of them, not per batch holding one)
+#pragma unroll 1
+        for (int pass = 0; pass < (F32 ? 2 : 1); ++pass) {
+        QIdx* list = pass == 0 ? fly : qr;
+        const int n_list = batch_run(pass == 0 ? n_fly : n_redo, drain);
+        for (int b = 0; b < n_list; b += 32) {
             const int k = b + lane;
             int a = A_DONE, slot = 0, hl = -1;
-            if (k < n_fly) {
-                slot = slot0 + int(unsigned(fly[k]) & QSLOT_MASK);
+            if (k < n_list) {
+                slot = slot0 + int(unsigned(list[k]) & QSLOT_MASK);
                 unsigned char* r = rec_at<FLAGS>(B, slot);
                 St s;
                 const double2 xy = D2(r, R_XY), zt = D2(r, R_ZT);
@@ -274,8 +298,10 @@ __global__ void TRK_EV_BOUNDS k_batched_ev(BatchHeader* __restrict__ hdr, const 
                 int4 su = I4(r, R_SU);
                 load_levels<CSG>(g, r, s, misc, su);
                 Hit h;
-                a = step_fly<CSG, F32, FLAGS>(g, s, h, c, rp, E.tally, cnt, nullptr, nullptr, 0);
-                if (a == A_DONE) {
+                if (F32 && pass) a = step_flight_fp64_call<CSG, FLAGS>(g, s, h, c, rp, E.tally, cnt, nullptr, nullptr, 0);
+                else a = step_fly<CSG, F32, FLAGS, true>(g, s, h, c, rp, E.tally, cnt, nullptr, nullptr, 0);
+                if (a == A_REDO) {
+                } else if (a == A_DONE) {
                     if (rec) finish<FLAGS>(pidx, c, rec);
                 } else {
                     D2(r, R_XY) = make_double2(s.x, s.y);
@@ -290,21 +316,25 @@ __global__ void TRK_EV_BOUNDS k_batched_ev(BatchHeader* __restrict__ hdr, const 
                     }
                 }
             }
-            const bool live = k < n_fly;
+            const bool live = k < n_list;
 #pragma unroll
             for (int l = 0; l < MAXL; ++l) wpush(live && hl == l, slot - slot0, qx + l * slots, n_cross[l]);
             wpush(live && a == A_COLLIDE, slot - slot0, qc, n_coll);
             wpush(live && a == A_DONE, slot - slot0, qf, n_free);
+            if (F32) wpush(live && a == A_REDO, slot - slot0, qr, n_redo);
         }
         __syncwarp();
+        if (pass == 0) carry_tail(fly, n_list, n_fly);
+        else carry_tail(qr, n_list, n_redo);
+        }
         // ---- cross_surface, then change_direction -------------------------------
-        int n_next = 0;
 #pragma unroll 1
-        for (int lq = 0; lq < MAXL; ++lq)
-        for (int b = 0; b < n_cross[lq]; b += 32) {
+        for (int lq = 0; lq < MAXL; ++lq) {
+        const int n_list = batch_run(n_cross[lq], drain);
+        for (int b = 0; b < n_list; b += 32) {
             const int k = b + lane;
             int a = A_DONE, slot = 0, cls = 0;
-            if (k < n_cross[lq]) {
+            if (k < n_list) {
                 slot = slot0 + qx[lq * slots + k];
                 unsigned char* r = rec_at<FLAGS>(B, slot);
                 St s;
@@ -331,14 +361,18 @@ __global__ void TRK_EV_BOUNDS k_batched_ev(BatchHeader* __restrict__ hdr, const 
                     if (cnt.k[TRK_K_REFLECTIONS] != refl0) store_dir(r, s);
                 }
             }
-            const bool live = k < n_cross[lq];
-            wpush(live && a == A_FLY, (slot - slot0) | (cls << QSLOT_BITS), next, n_next);
+            const bool live = k < n_list;
+            wpush(live && a == A_FLY, (slot - slot0) | (cls << QSLOT_BITS), fly, n_fly);
             wpush(live && a == A_DONE, slot - slot0, qf, n_free);
         }
-        for (int b = 0; b < n_coll; b += 32) {
+        __syncwarp();
+        carry_tail(qx + lq * slots, n_list, n_cross[lq]);
+        }
+        const int n_crun = batch_run(n_coll, drain);
+        for (int b = 0; b < n_crun; b += 32) {
             const int k = b + lane;
             int a = A_DONE, slot = 0, cls = 0;
-            if (k < n_coll) {
+            if (k < n_crun) {
                 slot = slot0 + qc[k];
                 unsigned char* r = rec_at<FLAGS>(B, slot);
                 St s;
@@ -359,13 +393,12 @@ __global__ void TRK_EV_BOUNDS k_batched_ev(BatchHeader* __restrict__ hdr, const 
                     store_ctx<FLAGS>(r, pidx, c, misc_off_surface(misc));
                 }
             }
-            const bool live = k < n_coll;
-            wpush(live && a == A_FLY, (slot - slot0) | (cls << QSLOT_BITS), next, n_next);
+            const bool live = k < n_crun;
+            wpush(live && a == A_FLY, (slot - slot0) | (cls << QSLOT_BITS), fly, n_fly);
             wpush(live && a == A_DONE, slot - slot0, qf, n_free);
         }
         __syncwarp();
-        QIdx* t = fly; fly = next; next = t;
-        n_fly = n_next;
+        carry_tail(qc, n_crun, n_coll);
     }
     if (ge >= 0) flush_counts(cnt, table[ge].counters);
 }
@@ -435,7 +468,9 @@ trk_status run_batched_event(trk_batch_t b, void* dev_work, const trk_run_opts& 
         npart += en.n;
     }
     if (split < 0) split = total;
-    unsigned long long max_rounds = (rp.max_segments + 2ULL) * (unsigned long long)(npart / 32 + 2);
+    // a particle takes at most 3 (max_segments + 2) queue steps; outside a
+    // drain a warp runs at least one full batch of 32 of them a round
+    unsigned long long max_rounds = (rp.max_segments + 2ULL) * (unsigned long long)(npart / 32 + 2) * 4ULL;
     if (o.max_rounds > 0) max_rounds = (unsigned long long)o.max_rounds;
     const size_t smem = size_t(BEV_QUEUES) * slots * (EV_BLOCK / 32) * sizeof(QIdx);
     auto launch = [&](auto kernel, int side, long long c0, long long c1) {

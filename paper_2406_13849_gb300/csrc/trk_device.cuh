@@ -415,7 +415,9 @@ static __device__ TRK_HOLDS_INLINE bool cell_holds(const DevGeom& g, int c, cons
 __shared__ const BvhNode* s_bvh_nodes;
 #endif
 
-template <bool SMEM>
+// One walk for both copies: in the event kernels `nodes` is a generic
+// pointer to either the shared-memory copy or the global array (plain loads
+// serve both), elsewhere the global array read through the read-only path.
 __device__ __forceinline__ int bvh_walk(const DevGeom& g, const BvhNode* nodes, int root, const Pt& p, int ex, int xs,
                                         int xsn) {
     float xl, xh, yl, yh, zl, zh;
@@ -428,15 +430,13 @@ __device__ __forceinline__ int bvh_walk(const DevGeom& g, const BvhNode* nodes, 
     for (;;) {
         if (ref >= 0) {
             const float4* np = reinterpret_cast<const float4*>(nodes + ref);
-            float4 a, b, c;
-            int4 r;
-            if (SMEM) {
-                a = np[0]; b = np[1]; c = np[2];
-                r = *reinterpret_cast<const int4*>(np + 3);
-            } else {
-                a = __ldg(np); b = __ldg(np + 1); c = __ldg(np + 2);
-                r = __ldg(reinterpret_cast<const int4*>(np + 3));
-            }
+#if TRK_BVH_SMEM
+            const float4 a = np[0], b = np[1], c = np[2];
+            const int4 r = *reinterpret_cast<const int4*>(np + 3);
+#else
+            const float4 a = __ldg(np), b = __ldg(np + 1), c = __ldg(np + 2);
+            const int4 r = __ldg(reinterpret_cast<const int4*>(np + 3));
+#endif
             // child 0: lo (a.x, a.y, a.z), hi (a.w, b.x, b.y); child 1: lo (b.z, b.w, c.x), hi (c.y, c.z, c.w)
             const bool in0 = xh >= a.x && xl <= a.w && yh >= a.y && yl <= b.x && zh >= a.z && zl <= b.y;
             const bool in1 = xh >= b.z && xl <= c.y && yh >= b.w && yl <= c.z && zh >= c.x && zl <= c.w;
@@ -464,9 +464,10 @@ __device__ __forceinline__ int bvh_walk(const DevGeom& g, const BvhNode* nodes, 
 
 static __device__ TRK_SEARCH_INLINE int bvh_search(const DevGeom& g, int root, const Pt& p, int ex, int xs, int xsn) {
 #if TRK_BVH_SMEM
-    if (s_bvh_nodes) return bvh_walk<true>(g, s_bvh_nodes, root, p, ex, xs, xsn);
+    return bvh_walk(g, s_bvh_nodes ? s_bvh_nodes : g.nodes, root, p, ex, xs, xsn);
+#else
+    return bvh_walk(g, g.nodes, root, p, ex, xs, xsn);
 #endif
-    return bvh_walk<false>(g, g.nodes, root, p, ex, xs, xsn);
 }
 
 // Walk of universe u's bounding interval hierarchy (Sec. 4.3): at each node
@@ -669,8 +670,10 @@ __device__ __forceinline__ int enter_cell(const DevGeom& g, Lv& L, int c) {
 // pseudo-array cell (its face planes' senses, as the CSG search evaluates
 // them) and of its six neighbours; if none holds, the universe search.  In a
 // lattice whose cells partition its region the holding cell is unique, so
-// this returns what the pseudo-array scan returns.
-__device__ __forceinline__ int hex_find(const DevGeom& g, int h, int u, const Pt& p) {
+// this returns what the pseudo-array scan returns.  Out of line: inlined at
+// every find site it would put its cell tests into the instruction
+// footprint of array-tracker kernels whose geometries have no hex arrays.
+static __device__ __noinline__ int hex_find(const DevGeom& g, int h, int u, const Pt& p) {
     const double2* hp = reinterpret_cast<const double2*>(g.hx + h);
     const double2 m0 = __ldg(hp), m1 = __ldg(hp + 1);
     const int4 hi = __ldg(reinterpret_cast<const int4*>(g.hx + h) + 2);
@@ -1484,7 +1487,10 @@ struct Ctx {
     int status;
 };
 
-enum { A_CROSS = 0, A_COLLIDE = 1, A_FLY = 2, A_DONE = 3 };
+// A_REDO: an FP32-local flight that must be redone in FP64, left untouched
+// for the caller to queue (the event kernels redo such flights together, in
+// full warps, after the flight pass).
+enum { A_CROSS = 0, A_COLLIDE = 1, A_FLY = 2, A_DONE = 3, A_REDO = 4 };
 
 template <int TK, int FLAGS>
 __device__ __forceinline__ int step_flight(const DevGeom& g, St& s, Hit& h, Ctx& c, const RunP& rp,
@@ -1589,8 +1595,9 @@ static __device__ __noinline__ int step_flight_fp64_call(const DevGeom& g, St& s
 }
 
 // FP32-local flight: distances and the flight decision in FP32, position
-// and tau in FP64; close calls are redone by the FP64 step.
-template <bool CSG, int FLAGS>
+// and tau in FP64; close calls are redone by the FP64 step, at once or (DEFER)
+// by the caller after A_REDO, with nothing of the particle changed.
+template <bool CSG, int FLAGS, bool DEFER = false>
 __device__ __forceinline__ int step_flight_f32(const DevGeom& g, St& s, Hit& h, Ctx& c, const RunP& rp,
                                                unsigned long long* __restrict__ tally, Counts& cnt,
                                                int* __restrict__ tr_inst, double* __restrict__ tr_len, long long i) {
@@ -1601,6 +1608,7 @@ __device__ __forceinline__ int step_flight_f32(const DevGeom& g, St& s, Hit& h, 
     const float dcf = sigf > 0.f ? float(s.tau) / sigf : FINF;
     if (b.ill || close_call(b.d1, b.d2) || close_call(b.d1, dcf) || !(fminf(b.d1, dcf) < FINF)) {
         cnt.k[TRK_K_CLOSE_CALLS]++;
+        if (DEFER) return A_REDO;
         return step_flight_fp64_call<CSG, FLAGS>(g, s, h, c, rp, tally, cnt, tr_inst, tr_len, i);
     }
     h = b.h;
@@ -1639,12 +1647,13 @@ __device__ __forceinline__ int step_flight_f32(const DevGeom& g, St& s, Hit& h, 
     return A_COLLIDE;
 }
 
-template <int TK, bool F32, int FLAGS>
+template <int TK, bool F32, int FLAGS, bool DEFER = false>
 __device__ __forceinline__ int step_fly(const DevGeom& g, St& s, Hit& h, Ctx& c, const RunP& rp,
                                         unsigned long long* __restrict__ tally, Counts& cnt,
                                         int* __restrict__ tr_inst, double* __restrict__ tr_len, long long i) {
     static_assert(!(F32 && TK == TK_DP), "the DP tracker is FP64 only");
-    if constexpr (F32) return step_flight_f32<TK == TK_CSG, FLAGS>(g, s, h, c, rp, tally, cnt, tr_inst, tr_len, i);
+    if constexpr (F32)
+        return step_flight_f32<TK == TK_CSG, FLAGS, DEFER>(g, s, h, c, rp, tally, cnt, tr_inst, tr_len, i);
     else return step_flight<TK, FLAGS>(g, s, h, c, rp, tally, cnt, tr_inst, tr_len, i);
 }
 

@@ -4,14 +4,15 @@
 // vector of histories, one operation at a time) on top of Alg. 2-10.
 //
 // GB300 design.  Each warp owns `slots` particle slots whose state lives in
-// the caller's work buffer (one compact record per slot, 176 bytes for the
-// CSG tracker, sized to stay in L2) and keeps its
+// the caller's work buffer (one 128-byte record per slot) and keeps its
 // own queues of slot indices in shared memory: flight (distance_to_surface +
-// move_within_cell + tally), cross (cross_surface + find_cell below),
-// collide (change_direction), free.  A round runs refill, then flight over
-// the whole flight queue, then cross and collide over theirs, all 32 lanes
-// on one kind of operation, so the warp stays converged where the history
-// kernel diverges.  Queue counts are warp-uniform registers advanced by
+// move_within_cell + tally), cross (cross_surface + find_cell below, one
+// queue per level), collide (change_direction), FP64 redo (FP32-local
+// flights too close to call), free.  A round runs refill, then flight, redo,
+// cross and collide over full 32-lane batches of their queues (the tail of
+// each waits for a later round until the warp's source is exhausted), all
+// 32 lanes on one kind of operation, so the warp stays converged where the
+// history kernel diverges.  Queue counts are warp-uniform registers advanced by
 // ballot/popc; empty slots take new particles from one global counter.  No
 // warp ever waits for another (only __syncwarp), and a round limit turns a
 // runaway into TRK_E_TIMEOUT.
@@ -60,9 +61,10 @@ __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, lo
 #endif
     QIdx* base_q = smem + warp * EV_QUEUES * slots;
     QIdx* qfl = base_q;                  // flight (slot | leaf class << QSLOT_BITS)
-    QIdx* qc = base_q + slots;           // collide (at refill: failed births; at a sort: scratch)
-    QIdx* qf = base_q + 2 * slots;
-    QIdx* qx = base_q + 3 * slots;       // MAXL cross queues, one per crossing level
+    QIdx* qc = base_q + slots;           // collide
+    QIdx* qf = base_q + 2 * slots;       // free
+    QIdx* qr = base_q + 3 * slots;       // FP32-local flights to redo in FP64
+    QIdx* qx = base_q + 4 * slots;       // MAXL cross queues, one per crossing level
     const int slot0 = (blockIdx.x * (EV_BLOCK / 32) + warp) * slots;
 #ifndef TRK_EV_SORT
 #define TRK_EV_SORT 1
@@ -72,7 +74,12 @@ __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, lo
 #pragma unroll
     for (int k = 0; k < NCOUNT; ++k) cnt.k[k] = 0;
     for (int k = lane; k < slots; k += 32) qf[k] = QIdx(k);
-    int n_fly = 0;
+    // queue counts (warp-uniform); every queue keeps what a pass leaves
+    // (batch_run) for the next round
+    int n_fly = 0, n_coll = 0, n_redo = 0;
+    int n_cross[MAXL];
+#pragma unroll
+    for (int l = 0; l < MAXL; ++l) n_cross[l] = 0;
     int n_free = slots;
     bool exhausted = false;
     __syncwarp();
@@ -129,37 +136,55 @@ __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, lo
                     if (FLAGS & F_FISS) fission_out(rp, pidx, 0, 0.0, 0.0, 0.0);
                 }
             }
+            // failed births park past the collide queue's entries (room:
+            // got <= n_free <= slots - n_coll)
             wpush(ok, (slot - slot0) | (cls << QSLOT_BITS), qfl, n_fly);
-            wpush(k < got && !ok, slot - slot0, qc, n_park);
+            wpush(k < got && !ok, slot - slot0, qc + n_coll, n_park);
         }
         __syncwarp();
         n_free -= got;
         for (int b = 0; b < n_park; b += 32) {
             const int k = b + lane;
-            wpush(k < n_park, k < n_park ? qc[k] : 0, qf, n_free);
+            wpush(k < n_park, k < n_park ? qc[n_coll + k] : 0, qf, n_free);
         }
         __syncwarp();
-        if (n_fly == 0 && exhausted) break;
+        int queued = n_fly + n_coll + n_redo;
+        bool full = n_fly >= 32 || n_coll >= 32 || n_redo >= 32;
+#pragma unroll
+        for (int l = 0; l < MAXL; ++l) {
+            queued += n_cross[l];
+            full = full || n_cross[l] >= 32;
+        }
+        if (queued == 0 && exhausted) break;
+        // tails run too once the source is exhausted, or when no queue holds
+        // a full batch (so every round advances: a full batch, or every
+        // queued particle)
+        const bool drain = exhausted || !full;
         if (round >= max_rounds) {
             if (lane == 0) kernel_status(counters, TRK_E_TIMEOUT);
             break;
         }
         // ---- flight: distance_to_surface, tally, move ----------------------
         // every sort_interval rounds the flight list is reordered by class
-        // (through the collide queue, empty until the flight pass fills it)
+        // (through the free queue's unused tail: slots - n_free >= n_fly)
         if (sorting && n_fly > 32 && round % (unsigned long long)sort_interval == 0) {
-            sort_by_class(qfl, n_fly, qc);
-            for (int k = lane; k < n_fly; k += 32) qfl[k] = qc[k];
+            sort_by_class(qfl, n_fly, qf + n_free);
+            for (int k = lane; k < n_fly; k += 32) qfl[k] = qf[n_free + k];
             __syncwarp();
         }
-        int n_cross[MAXL], n_coll = 0;
-#pragma unroll
-        for (int l = 0; l < MAXL; ++l) n_cross[l] = 0;
-        for (int b = 0; b < n_fly; b += 32) {
+        // FP32-local flights that need FP64 (A_REDO) wait in their own queue
+        // and are redone in a second pass over full batches, so a warp pays
+        // for the FP64 step once per 32 of them rather than once per batch
+        // holding one
+#pragma unroll 1
+        for (int pass = 0; pass < (F32 ? 2 : 1); ++pass) {
+        QIdx* list = pass == 0 ? qfl : qr;
+        const int n_list = batch_run(pass == 0 ? n_fly : n_redo, drain);
+        for (int b = 0; b < n_list; b += 32) {
             const int k = b + lane;
             int a = A_DONE, slot = 0, hl = -1;
-            if (k < n_fly) {
-                slot = slot0 + int(unsigned(qfl[k]) & QSLOT_MASK);
+            if (k < n_list) {
+                slot = slot0 + int(unsigned(list[k]) & QSLOT_MASK);
                 unsigned char* r = rec_at<FLAGS>(B, slot);
                 St s;
                 const double2 xy = D2(r, R_XY), zt = D2(r, R_ZT);
@@ -171,8 +196,10 @@ __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, lo
                 int4 su = I4(r, R_SU);
                 load_levels<CSG>(g, r, s, misc, su);
                 Hit h;
-                a = step_fly<CSG, F32, FLAGS>(g, s, h, c, rp, tally, cnt, rp.tr_inst, rp.tr_len, pidx);
-                if (a == A_DONE) {
+                if (F32 && pass) a = step_flight_fp64_call<CSG, FLAGS>(g, s, h, c, rp, tally, cnt, rp.tr_inst, rp.tr_len, pidx);
+                else a = step_fly<CSG, F32, FLAGS, true>(g, s, h, c, rp, tally, cnt, rp.tr_inst, rp.tr_len, pidx);
+                if (a == A_REDO) {
+                } else if (a == A_DONE) {
                     finish<FLAGS>(pidx, c, rec);
                     trace_tail<FLAGS>(pidx, c, rp);
                     if (FLAGS & F_FISS) fission_out(rp, pidx, 0, 0.0, 0.0, 0.0);
@@ -189,23 +216,27 @@ __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, lo
                     }
                 }
             }
-            const bool live = k < n_fly;
+            const bool live = k < n_list;
             // crossings are queued by level, so each pass runs one code path
             // (array index step, universe search, pin cell test)
 #pragma unroll
             for (int l = 0; l < MAXL; ++l) wpush(live && hl == l, slot - slot0, qx + l * slots, n_cross[l]);
             wpush(live && a == A_COLLIDE, slot - slot0, qc, n_coll);
             wpush(live && a == A_DONE, slot - slot0, qf, n_free);
+            if (F32) wpush(live && a == A_REDO, slot - slot0, qr, n_redo);
         }
         __syncwarp();
-        n_fly = 0;
+        if (pass == 0) carry_tail(qfl, n_list, n_fly);
+        else carry_tail(qr, n_list, n_redo);
+        }
         // ---- cross_surface, then change_direction ---------------------------
 #pragma unroll 1
-        for (int lq = 0; lq < MAXL; ++lq)
-        for (int b = 0; b < n_cross[lq]; b += 32) {
+        for (int lq = 0; lq < MAXL; ++lq) {
+        const int n_list = batch_run(n_cross[lq], drain);
+        for (int b = 0; b < n_list; b += 32) {
             const int k = b + lane;
             int a = A_DONE, slot = 0, cls = 0;
-            if (k < n_cross[lq]) {
+            if (k < n_list) {
                 slot = slot0 + qx[lq * slots + k];
                 unsigned char* r = rec_at<FLAGS>(B, slot);
                 St s;
@@ -234,14 +265,18 @@ __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, lo
                     if (cnt.k[TRK_K_REFLECTIONS] != refl0) store_dir(r, s);
                 }
             }
-            const bool live = k < n_cross[lq];
+            const bool live = k < n_list;
             wpush(live && a == A_FLY, (slot - slot0) | (cls << QSLOT_BITS), qfl, n_fly);
             wpush(live && a == A_DONE, slot - slot0, qf, n_free);
         }
-        for (int b = 0; b < n_coll; b += 32) {
+        __syncwarp();
+        carry_tail(qx + lq * slots, n_list, n_cross[lq]);
+        }
+        const int n_crun = batch_run(n_coll, drain);
+        for (int b = 0; b < n_crun; b += 32) {
             const int k = b + lane;
             int a = A_DONE, slot = 0, cls = 0;
-            if (k < n_coll) {
+            if (k < n_crun) {
                 slot = slot0 + qc[k];
                 unsigned char* r = rec_at<FLAGS>(B, slot);
                 St s;
@@ -273,11 +308,12 @@ __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, lo
                     store_ctx<FLAGS>(r, pidx, c, misc_off_surface(misc));
                 }
             }
-            const bool live = k < n_coll;
+            const bool live = k < n_crun;
             wpush(live && a == A_FLY, (slot - slot0) | (cls << QSLOT_BITS), qfl, n_fly);
             wpush(live && a == A_DONE, slot - slot0, qf, n_free);
         }
         __syncwarp();
+        carry_tail(qc, n_crun, n_coll);
     }
     flush_counts(cnt, counters);
 }
@@ -340,10 +376,12 @@ trk_status launch_event(trk_geom_t g, const ParticlesView& P, long long n, const
     if (e != cudaSuccess) return trk_status(set_error(TRK_E_CUDA, "run_histories (event): %s", cudaGetErrorString(e)));
     const int n_snodes = (g->dg.accel == 0 && g->n_nodes <= EV_SMEM_NODES) ? g->n_nodes : 0;
     const size_t smem = size_t(EV_QUEUES) * slots * EV_WARPS * sizeof(QIdx) + size_t(n_snodes) * sizeof(BvhNode);
-    // a particle needs at most max_segments + 1 flight rounds; a warp holds
-    // `slots` particles at a time and refills every round
+    // a particle takes at most 3 (max_segments + 2) queue steps (flight,
+    // redo, cross or collide); until its source runs out a warp runs at
+    // least one full batch of 32 steps a round, after that every queued
+    // particle advances every round
     const unsigned long long per_warp = (unsigned long long)(n / (T / slots) + slots + 1);
-    unsigned long long max_rounds = (rp.max_segments + 2ULL) * (per_warp / slots + 2ULL) * 4ULL;
+    unsigned long long max_rounds = (rp.max_segments + 2ULL) * (per_warp / 32ULL + 2ULL) * 4ULL;
     if (max_rounds_opt > 0) max_rounds = (unsigned long long)max_rounds_opt;
 #define TRK_EV(C, F32V, F)                                                                                   \
     do {                                                                                                     \

@@ -31,7 +31,7 @@ using QIdx = unsigned short;
 #ifndef TRK_EV_REFILL_MIN
 #define TRK_EV_REFILL_MIN 32
 #endif
-constexpr int EV_QUEUES = 3 + MAXL;   // flight, collide (sort scratch), free, cross per level
+constexpr int EV_QUEUES = 4 + MAXL;   // flight, collide, free, FP64 redo, cross per level
 
 // Minimum resident CTAs per SM the register allocation must allow (0: let
 // the compiler choose).  Two CTAs (16 warps, 128 registers a thread) hide
@@ -266,6 +266,26 @@ template <int FLAGS>
 __device__ __forceinline__ void store_ctx(unsigned char* r, int pidx, const Ctx& c, unsigned misc) {
     I4(r, R_CT) = make_int4(pidx, int(c.event), int(uint32_t(c.nseg)), int(misc));
     if (FLAGS & (F_REC | F_CUT)) L2(r, R_HP) = make_longlong2((long long)c.hash, __double_as_longlong(c.path));
+}
+
+// Entries of a queue a pass runs: whole 32-lane batches only, the tail
+// staying queued for a later round, unless the round drains (the warp's
+// source is exhausted, or no queue holds a full batch), when everything
+// runs.  A pass then spends a warp-wide step on a batch with a few live
+// lanes only where nothing else is left to run, and every round advances.
+__device__ __forceinline__ int batch_run(int n, bool drain) { return drain ? n : (n & ~31); }
+
+// Moves the n - done entries left after a pass (fewer than 32, with done a
+// multiple of 32, or none) to the front of the queue; all 32 lanes call.
+__device__ __forceinline__ void carry_tail(QIdx* q, int done, int& n) {
+    const int lane = threadIdx.x & 31;
+    const int rem = n - done;
+    if (done > 0 && rem > 0) {
+        // rem < 32 <= done: the source and destination ranges are disjoint
+        if (lane < rem) q[lane] = q[done + lane];
+    }
+    n = rem;
+    __syncwarp();
 }
 
 // Warp-level append of `v` to `list` when `flag` (all 32 lanes call);
