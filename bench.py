@@ -45,9 +45,9 @@ NEAR_RULE_SAMPLE = 300
 TRACE_CAP = 96
 # DRAM bytes (read + write) per segment of the dominant kernel, from one ncu
 # capture of the same kernel on the same geometry with 3e6 particles
-# (41.24 GB over 82,931,315 segments); scaled to a full launch by its
+# (19.33 GB over 82,931,315 segments); scaled to a full launch by its
 # segments.  None whenever the kernel has changed since that capture.
-TRAFFIC_BYTES_PER_SEGMENT = (26.819490e9 + 14.276296e9) / 82931315
+TRAFFIC_BYTES_PER_SEGMENT = (9.320092e9 + 10.007729e9) / 82931315
 
 
 def _env_int(k, d):

@@ -498,13 +498,18 @@ trk_status launch_error(const char* where) {
     return TRK_OK;
 }
 
-int resolve_tracker(trk_geom_t g, int tracker, trk_status* st, bool allow_dp = false) {
+int resolve_tracker(trk_geom_t g, int tracker, trk_status* st, bool allow_dp = false, bool event = false) {
     *st = TRK_OK;
     if (tracker == TRK_TRACKER_DP && allow_dp) return tracker;
-    // AUTO: the array tracker, except for geometries with hex arrays, where
-    // the BVH-CSG tracker measured as fast or faster (its BVH walk and the
-    // closed-form hex search cost about the same; the CSG kernels are smaller)
-    if (tracker == TRK_TRACKER_AUTO) return (g->rect_ok && !g->has_hex) ? TRK_TRACKER_RECT : TRK_TRACKER_CSG;
+    // AUTO: the array tracker for the history kernels, except for geometries
+    // with hex arrays, where the BVH-CSG tracker measured as fast or faster
+    // (its BVH walk and the closed-form hex search cost about the same; the
+    // CSG kernels are smaller).  The event kernels take the CSG tracker
+    // everywhere: its kernel is the smaller (slab cells stand in for the
+    // array levels) and measured 1.25x the array tracker's on the 15 x 15
+    // assembly core.  Both trackers give the same histories bit for bit.
+    if (tracker == TRK_TRACKER_AUTO)
+        return (g->rect_ok && !g->has_hex && !event) ? TRK_TRACKER_RECT : TRK_TRACKER_CSG;
     if (tracker == TRK_TRACKER_RECT && !g->rect_ok) {
         *st = trk_status(set_error(TRK_E_UNSUPPORTED, "array tracker not available for this geometry"));
         return -1;
@@ -601,7 +606,7 @@ trk_status run_histories(trk_geom_t g, const void* dev_particles, int64_t n, uin
     trk_default_opts(&o);
     if (opts) o = *opts;
     trk_status st;
-    const int tracker = resolve_tracker(g, o.tracker, &st, true);
+    const int tracker = resolve_tracker(g, o.tracker, &st, true, o.mode == TRK_MODE_EVENT);
     if (tracker < 0) return st;
     if (o.mode != TRK_MODE_HISTORY && o.mode != TRK_MODE_EVENT)
         return trk_status(set_error(TRK_E_INVALID, "run_histories: unknown mode %d", o.mode));
@@ -1066,7 +1071,7 @@ trk_status power_iteration(trk_geom_t g, int64_t n, int inactive, int cycles, do
     trk_default_opts(&o);
     if (opts) o = *opts;
     trk_status st;
-    const int tracker = resolve_tracker(g, o.tracker, &st);
+    const int tracker = resolve_tracker(g, o.tracker, &st, false, o.mode == TRK_MODE_EVENT);
     if (tracker < 0) return st;
     if (o.precision != TRK_FP64) return trk_status(set_error(TRK_E_UNSUPPORTED, "power_iteration: FP64 only"));
     if (o.mode != TRK_MODE_HISTORY && o.mode != TRK_MODE_EVENT)
