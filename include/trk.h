@@ -376,8 +376,8 @@ trk_status batch_upload(trk_batch_t b, void* dev_work, size_t work_bytes, int ch
 trk_status run_batched(trk_batch_t b, void* dev_work, const trk_run_opts* opts, void* stream);
 
 /* Autotuner: times block sizes {64, 96, 128} x chunk sizes {128, 512, 2048}
- * (history mode) or queue depths {256, 384, 512} x chunk sizes {4096, 16384,
- * 65536} x sort intervals {0, 4} (event mode, opts->mode) on the batch itself
+ * (history mode) or queue depths {384, 512} x chunk sizes {1024, 2048, 4096,
+ * 16384} x sort intervals {0, 4} (event mode, opts->mode) on the batch itself
  * (CUDA events, `reps` launches each) and writes the fastest to opts->block
  * or opts->queue_depth and opts->sort_interval, and *chunk_out, leaving the
  * table uploaded for it; *best_ms (optional) gets its time.  The trial

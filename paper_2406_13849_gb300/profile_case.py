@@ -19,7 +19,7 @@ launch instead.  Workloads:
 
   python -m paper_2406_13849_gb300.profile_case [--workload core|hex|batch|transmission]
       [--tracker csg|rect|dp] [--mode event|history] [--precision fp64|fp32]
-      [--particles N] [--launches L] [--members M] [--rays R]
+      [--particles N] [--launches L] [--members M] [--chunk C] [--batch-tracker auto|csg] [--rays R]
 
 Prints one line with segments (or rays), kernel milliseconds and rates per
 launch (CUDA events; meaningless under a profiler).
@@ -49,6 +49,7 @@ def main() -> None:
     ap.add_argument("--sort-interval", type=int, default=0)
     ap.add_argument("--members", type=int, default=8)
     ap.add_argument("--chunk", type=int, default=4096)
+    ap.add_argument("--batch-tracker", default="auto", choices=["auto", "csg"])
     ap.add_argument("--rays", type=int, default=1 << 18)
     args = ap.parse_args()
     dev = torch.device("cuda", 0)
@@ -100,7 +101,7 @@ def run_batch(dev, args):
     geoms = [N.Geometry(I.to_json(d), device=dev) for d, _ in members]
     counts = [c for _, c in members]
     parts = [g.source_init(c, seed=1) for g, c in zip(geoms, counts)]
-    b = N.Batch(geoms, parts, counts)
+    b = N.Batch(geoms, parts, counts, tracker=N.TRACKER_CSG if args.batch_tracker == "csg" else N.TRACKER_AUTO)
     b.upload(args.chunk)
     opts = N.default_opts(seed=1, p_absorb=0.25, queue_depth=args.queue_depth,
                           mode=N.MODE_EVENT if args.mode == "event" else N.MODE_HISTORY,
@@ -118,7 +119,8 @@ def run_batch(dev, args):
         ms = a.elapsed_time(e)
         out.append({"segments": seg, "ms": ms, "segments_per_s": seg / (ms / 1e3)})
     print(json.dumps({"workload": "batch", "members": len(geoms), "particles": sum(counts), "mode": args.mode,
-                      "precision": args.precision, "chunk": args.chunk, "launches": out}), flush=True)
+                      "precision": args.precision, "chunk": args.chunk, "queue_depth": args.queue_depth,
+                      "batch_tracker": args.batch_tracker, "launches": out}), flush=True)
 
 
 def run_transmission(dev, args):
