@@ -48,6 +48,24 @@ TRACE_CAP = 96
 # (19.33 GB over 82,931,315 segments); scaled to a full launch by its
 # segments.  None whenever the kernel has changed since that capture.
 TRAFFIC_BYTES_PER_SEGMENT = (9.320092e9 + 10.007729e9) / 82931315
+# the same for the other rooflines' kernels, from small-case captures:
+# k_event<CSG,FP32-local> on the same 3e6-particle case; the two
+# k_batched_ev<*,FP32-local> launches of one 64-geometry pass (chunk 4096,
+# queue depth 512); k_transmission_bwd on 2^18 rays of the transmission
+# workload (traffic scales with rays)
+TRAFFIC_BYTES_PER_SEGMENT_FP32 = (14.747693e9 + 16.041718e9) / 82931442
+TRAFFIC_BYTES_PER_SEGMENT_BATCH = (17.187394e9 + 21.090474e9 + 20.138322e9 + 25.544987e9) / 301969347
+TRAFFIC_BYTES_PER_RAY_BWD = (15.207424e6 + 4.624384e6) / 262144
+# Algorithmic FP64 operations per unit of work, the rooflines' numerators,
+# from `python -m oracle.flop_counts` (the oracle's counting build in
+# array-tracker mode; add/sub, mul, div and sqrt count one each): per
+# segment of the main workload; per segment of the 64-geometry batch (its
+# array-lattice members' figure, which undercounts the hex members); per ray
+# of the transmission workload (the segment arithmetic the backward kernel
+# recomputes; its derivative terms are not counted).
+OPS_PER_SEGMENT = 100.74230573512504
+OPS_PER_SEGMENT_BATCH = 70.55553343953962
+OPS_PER_RAY_TRANSMISSION = 41880.890625
 
 
 def _env_int(k, d):
@@ -151,20 +169,6 @@ def cpu_baseline(desc_json: str, n: int, n_one: int, first_id: int = 0, traced=N
             "segments_matched": res["segments_compared"], "max_rel_matched": res["max_rel_matched"],
             "findings": (res["near_surface"] + res["drift"] + res["failed"])[:10]}
     return out
-
-
-def flops_per_segment(desc_json: str) -> dict:
-    """Algorithmic FP64 operations per segment: the counting build of the
-    oracle in rect-tracker mode (the fewest operations the method needs) on
-    a sample of the workload; add/sub, mul, div and sqrt each count one."""
-    import oracle as O
-    g = O.Geometry(desc_json, O.MODE_RECT, counting=True)
-    g.flop_counts(reset=True)
-    r = g.run(2000, SEED, P_ABSORB, threads=1, records=False)
-    fc = g.flop_counts()
-    seg = float(r["counters"][O.K_SEGMENTS])
-    ops = fc["add"] + fc["mul"] + fc["div"] + fc["sqrt"]
-    return {"per_segment": ops / seg, "counts_per_segment": {k: v / seg for k, v in fc.items()}}
 
 
 def tally_error(t32, t64, c32=None, c64=None) -> dict:
@@ -432,10 +436,9 @@ def main() -> None:
     batch = run_config4(N, I, dev, stream, barrier, rank, k2, world)
 
     # ---- roofline of the dominant kernel (the event kernel, CSG, FP64) ------
-    fps = flops_per_segment(desc)
     kern_ms = statistics.mean(main_run["kernel_ms"])
     seg_per_launch = main_run["segments"] / args.steps
-    achieved = fps["per_segment"] * seg_per_launch / (kern_ms / 1e3) / 1e12
+    achieved = OPS_PER_SEGMENT * seg_per_launch / (kern_ms / 1e3) / 1e12
     scratch = torch.empty(1 << 16, dtype=torch.uint8, device=dev)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     pk = 0.0
@@ -486,9 +489,9 @@ def main() -> None:
                                   "particles, scaled by segments per launch",
                 "kernel": "k_event<CSG,FP64> (run_histories, event mode)",
                 "peak_source": "measured FP64 FMA rate (trk_peak_kernel, same run; of measured)",
-                "flops_per_segment": fps["per_segment"],
+                "flops_per_segment": OPS_PER_SEGMENT,
                 "flops_definition": "FP64 add/sub, mul, div, sqrt per segment counted by the oracle's counting "
-                                    "build in rect-tracker mode on this workload",
+                                    "build in rect-tracker mode on this workload (python -m oracle.flop_counts)",
                 "utilisation": util,
                 "utilisation_definition": "fp64_pipe: frac; l2_atomic: tally atomics (one per segment) per second "
                                           "over the spread u64 atomic rate; hbm: traffic per launch over the "
@@ -531,6 +534,39 @@ def main() -> None:
             near_rule["rule"] = ("instances equal and lengths within 1e-12 relative or the propagated rounding "
                                  "bound; else the first mismatch within 1e-9 cm of the deciding surface")
 
+    # ---- rooflines of the other kernels (same definitions; FP64 FMA peak) ---
+    def alu_roofline(kernel, ops_per_unit, units, seconds, traffic, traffic_source, unit_name, time_source):
+        ach = ops_per_unit * units / seconds / 1e12
+        return {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk if pk else None,
+                "traffic": traffic, "traffic_source": traffic_source, "kernel": kernel,
+                "flops_per_unit": ops_per_unit, "work_unit": unit_name, "units_per_launch": units,
+                "time_source": time_source,
+                "peak_source": "measured FP64 FMA rate (trk_peak_kernel, same run; of measured)"}
+    seg32 = csg_ev32["segments"] / k2
+    rooflines = {
+        "fp32local_event": alu_roofline(
+            "k_event<CSG,FP32-local> (run_histories, event mode, main workload)", OPS_PER_SEGMENT, seg32,
+            statistics.mean(csg_ev32["kernel_ms"]) / 1e3, TRAFFIC_BYTES_PER_SEGMENT_FP32 * seg32,
+            "ncu dram bytes of one 3e6-particle launch, scaled by segments", "segment",
+            "CUDA events around run_histories"),
+    }
+    if batch and batch.get("batched_fp32local_graph_segments_per_s"):
+        seg_b = batch["segments_per_particle"] * batch["particles"]
+        rooflines["batched_event_fp32local"] = alu_roofline(
+            "k_batched_ev<rect,FP32-local> + k_batched_ev<CSG,FP32-local> (one 64-geometry pass)",
+            OPS_PER_SEGMENT_BATCH, seg_b, seg_b / batch["batched_fp32local_graph_segments_per_s"],
+            TRAFFIC_BYTES_PER_SEGMENT_BATCH * seg_b,
+            "ncu dram bytes of one pass's two launches (chunk 4096), scaled by segments", "segment",
+            "CUDA events around the graph replay")
+    if trans:
+        rooflines["transmission_bwd"] = alu_roofline(
+            "k_transmission_bwd (2^20 rays)", OPS_PER_RAY_TRANSMISSION, trans["rays"], trans["bwd_ms"] / 1e3,
+            TRAFFIC_BYTES_PER_RAY_BWD * trans["rays"], "ncu dram bytes of one 2^18-ray launch, scaled by rays",
+            "ray", "CUDA events around transmission_bwd")
+        rooflines["transmission_fwd"] = alu_roofline(
+            "k_transmission (2^20 rays)", OPS_PER_RAY_TRANSMISSION, trans["rays"], trans["fwd_ms"] / 1e3,
+            None, "no capture", "ray", "CUDA events around transmission_fwd")
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -545,6 +581,7 @@ def main() -> None:
             "e2e": e2e,
             "gpu_launches": 2 * args.steps,
             "roofline": roofline,
+            "rooflines": rooflines,
             "cpu_baseline": cpu,
             "fast_build_near_surface_mismatches": near_rule,
             "exchange": exchange,
@@ -676,6 +713,7 @@ def run_config4(N, I, dev, stream, barrier, rank, steps, world=1):
             "loop_fp32local_event_segments_per_s": r_le32,
             "batched_over_event_loop": r_ev32 / r_le32,
             "segments_per_particle": seg_per_particle,
+            "particles": sum(counts),
             "autotuned": {"event": {"queue_depth": ev32.queue_depth, "chunk": chunk_ev,
                                     "sort_interval": ev32.sort_interval},
                           "history": {"block": hi32.block, "chunk": chunk_hi}},

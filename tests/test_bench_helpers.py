@@ -94,3 +94,16 @@ def test_cpu_baseline_compares_traced_rows_under_the_near_surface_rule():
     rows_l[3, 2] += 1e-6
     rule = B.cpu_baseline(desc, 2000, 500, traced=(ids, rows_i, rows_l, cap))["near_surface_rule"]
     assert rule["failed"] == 1 and rule["findings"][0]["pid"] == int(ids[3])
+
+
+def test_roofline_numerators_match_the_counting_oracle():
+    # the operation counts bench.py states are what oracle.flop_counts
+    # computes (same samples), so a change of the oracle's arithmetic or of
+    # the workloads shows up here
+    bench = _bench()
+    from oracle import flop_counts as F
+    from paper_2406_13849_gb300 import inputs as I
+    c2, _ = F.per_segment(I.config2(), 2000)
+    assert c2 == bench.OPS_PER_SEGMENT
+    assert F.batch_per_segment(200)["rect"] == bench.OPS_PER_SEGMENT_BATCH
+    assert F.transmission_per_ray(512) == bench.OPS_PER_RAY_TRANSMISSION
