@@ -354,8 +354,9 @@ trk_status batch_create(const trk_geom_t* geoms, int n_geom, const void* const* 
 trk_status batch_destroy(trk_batch_t b);
 
 /* Bytes of the caller-owned work buffer (256-byte aligned): the device table
- * and, for event mode, the slot records of the batched event kernel at the
- * largest queue depth (512); enough for every mode and queue depth. */
+ * and, for event mode, the slot records of the batched event kernel's two
+ * launches at the largest queue depth (512); enough for every mode and queue
+ * depth. */
 trk_status batch_work_bytes(trk_batch_t b, size_t* bytes);
 
 /* Writes the device table for chunks of `chunk` particles (0 = 512) into
@@ -368,9 +369,14 @@ trk_status batch_upload(trk_batch_t b, void* dev_work, size_t work_bytes, int ch
  * warps pull chunks of one geometry.  Event mode: the event kernel's queues
  * and slot records per warp, each warp working through chunks of one
  * geometry at a time (a chunk of another geometry starts once the warp's
- * slots have drained); rect-tracker and CSG entries are two launches.
- * Issues memsets and kernels on `stream` and nothing else, so after
- * batch_upload it can be captured in a CUDA graph and replayed.  A kernel
+ * slots have drained); rect-tracker and CSG entries are two launches, the
+ * CSG one on the batch's own side stream forked from `stream` by an event and
+ * joined back to it (so it fills the SMs the first launch's last warps free),
+ * each launch with its own slot records.  Issues memsets, kernels and that
+ * fork/join on `stream` and nothing else, so after batch_upload it can be
+ * captured in a CUDA graph (the fork and join become graph edges) and
+ * replayed; the side stream, created at the first event-mode call, lives
+ * until batch_destroy.  A kernel
  * that reaches the round limit writes TRK_E_TIMEOUT to the status counter of
  * the geometry it was on. */
 trk_status run_batched(trk_batch_t b, void* dev_work, const trk_run_opts* opts, void* stream);

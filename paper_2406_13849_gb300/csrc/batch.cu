@@ -416,6 +416,16 @@ struct trk_batch {
     void* work = nullptr;
     size_t work_bytes = 0;
     unsigned magic = 0;
+    // event mode: the CSG-tracker launch runs on a second stream, forked
+    // from and joined to the caller's, so that it fills the SMs the
+    // array-tracker launch's last warps leave idle (created at first use)
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    ~trk_batch() {
+        if (fork) cudaEventDestroy(fork);
+        if (join) cudaEventDestroy(join);
+        if (side) cudaStreamDestroy(side);
+    }
 };
 constexpr unsigned TRK_BATCH_MAGIC = 0x74726b62u;
 
@@ -431,8 +441,9 @@ int sm_count_b() {
 
 size_t table_bytes(int n) { return a256(sizeof(BatchHeader)) + a256(size_t(n) * sizeof(BatchEntry)); }
 
-// Event mode: slot records after the table, `slots` per warp.
-size_t event_bytes(int n, int slots) { return table_bytes(n) + event_work_bytes(slots, event_grid(slots)); }
+// Event mode: slot records after the table, `slots` per warp, one set for
+// each of the two launches (they may run at the same time).
+size_t event_bytes(int n, int slots) { return table_bytes(n) + 2 * event_work_bytes(slots, event_grid(slots)); }
 constexpr int BEV_MAX_SLOTS = 512;
 
 }  // namespace
@@ -440,7 +451,9 @@ constexpr int BEV_MAX_SLOTS = 512;
 namespace {
 
 // Event mode: the rect-tracker chunks [0, split) and the CSG ones
-// [split, total) as two launches of the batched event kernel.
+// [split, total) as two launches of the batched event kernel, the second on
+// the batch's side stream between a fork and a join event (graph capture
+// records the same fork and join), each with its own slot records.
 trk_status run_batched_event(trk_batch_t b, void* dev_work, const trk_run_opts& o, const RunP& rp, bool f32, bool rec,
                              cudaStream_t s) {
     const int slots = o.queue_depth > 0 ? o.queue_depth : 256;
@@ -458,9 +471,17 @@ trk_status run_batched_event(trk_batch_t b, void* dev_work, const trk_run_opts& 
     BatchHeader* hdr = static_cast<BatchHeader*>(dev_work);
     const BatchEntry* table = reinterpret_cast<const BatchEntry*>(static_cast<unsigned char*>(dev_work) + a256(sizeof(BatchHeader)));
     const long long T = (long long)slots * (EV_BLOCK / 32) * grid;
-    const EvBuf B = make_buf(static_cast<unsigned char*>(dev_work) + table_bytes(b->n_geom), T);
+    unsigned char* rec_base = static_cast<unsigned char*>(dev_work) + table_bytes(b->n_geom);
+    const EvBuf B0 = make_buf(rec_base, T);
+    const EvBuf B1 = make_buf(rec_base + event_work_bytes(slots, grid), T);
     cudaError_t e = cudaMemsetAsync(hdr->next_ev, 0, sizeof(hdr->next_ev), s);
     if (e != cudaSuccess) return trk_status(set_error(TRK_E_CUDA, "run_batched: %s", cudaGetErrorString(e)));
+    if (!b->side) {
+        if (cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming) != cudaSuccess)
+            return trk_status(set_error(TRK_E_CUDA, "run_batched: cannot create the side stream"));
+    }
     long long total = 0, split = -1, npart = 0;
     for (auto& en : b->entries) {
         if (en.csg && split < 0) split = en.first_chunk;
@@ -473,11 +494,19 @@ trk_status run_batched_event(trk_batch_t b, void* dev_work, const trk_run_opts& 
     unsigned long long max_rounds = (rp.max_segments + 2ULL) * (unsigned long long)(npart / 32 + 2) * 4ULL;
     if (o.max_rounds > 0) max_rounds = (unsigned long long)o.max_rounds;
     const size_t smem = size_t(BEV_QUEUES) * slots * (EV_BLOCK / 32) * sizeof(QIdx);
+    // side 1 waits for everything before it on s (the counters' reset)
+    const bool both = split > 0 && total > split;
+    if (both) {
+        if (cudaEventRecord(b->fork, s) != cudaSuccess || cudaStreamWaitEvent(b->side, b->fork, 0) != cudaSuccess)
+            return trk_status(set_error(TRK_E_CUDA, "run_batched: fork failed"));
+    }
     auto launch = [&](auto kernel, int side, long long c0, long long c1) {
         if (c1 <= c0) return;
         if (smem > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-        kernel<<<grid, EV_BLOCK, smem, s>>>(hdr, table, rp, B, slots, side, (unsigned long long)c0,
-                                            (unsigned long long)c1, max_rounds, o.sort_interval);
+        cudaStream_t st = (side == 1 && both) ? b->side : s;
+        kernel<<<grid, EV_BLOCK, smem, st>>>(hdr, table, rp, side == 1 ? B1 : B0, slots, side,
+                                             (unsigned long long)c0, (unsigned long long)c1, max_rounds,
+                                             o.sort_interval);
     };
     if (f32) {
 #ifndef TRK_EXACT
@@ -487,6 +516,10 @@ trk_status run_batched_event(trk_batch_t b, void* dev_work, const trk_run_opts& 
     } else {
         if (rec) { launch(k_batched_ev<false, false, F_REC>, 0, 0, split); launch(k_batched_ev<true, false, F_REC>, 1, split, total); }
         else { launch(k_batched_ev<false, false, 0>, 0, 0, split); launch(k_batched_ev<true, false, 0>, 1, split, total); }
+    }
+    if (both) {
+        if (cudaEventRecord(b->join, b->side) != cudaSuccess || cudaStreamWaitEvent(s, b->join, 0) != cudaSuccess)
+            return trk_status(set_error(TRK_E_CUDA, "run_batched: join failed"));
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return trk_status(set_error(TRK_E_CUDA, "run_batched: %s", cudaGetErrorString(e)));
