@@ -109,6 +109,34 @@ def test_batched_event_graph_replay_fp32():
     assert np.array_equal(_u64(b.counters), 2 * once_c)
 
 
+def test_batched_event_first_call_captured():
+    # the first event-mode call of a batch (which creates its side stream)
+    # made inside a graph capture: the replay equals an uncaptured run of an
+    # identical batch; hex (CSG) and array members, so both launches and the
+    # fork/join are captured
+    members = _members(6, 3_000)
+    counts = [n for _, n in members]
+    opts = _ev(queue_depth=256)
+    ref_geoms, ref_parts = _build(members, exact=True)
+    ref = N.Batch(ref_geoms, ref_parts, counts)
+    ref.upload(1024)
+    ref.run(opts)
+    torch.cuda.synchronize()
+    geoms, parts = _build(members, exact=True)
+    b = N.Batch(geoms, parts, counts)
+    b.upload(1024)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        b.run(opts)
+    graph.replay()
+    torch.cuda.synchronize()
+    for k in range(len(geoms)):
+        assert np.array_equal(_u64(b.tallies[k]), _u64(ref.tallies[k])), k
+    assert np.array_equal(_u64(b.counters), _u64(ref.counters))
+
+
 def test_batched_event_autotune_then_exact():
     members = _members(10, 3_000)
     geoms, parts = _build(members, exact=True)
