@@ -388,7 +388,7 @@ def test_event_bit_exact_hex(name):
     assert np.array_equal(h, o["hash"]) and np.array_equal(_u64(tally), o["tally"])
 
 
-@pytest.mark.parametrize("depth,grid", [(32, 1), (64, 3), (128, 0), (512, 2)])
+@pytest.mark.parametrize("depth,grid", [(32, 1), (64, 3), (100, 0), (128, 0), (512, 2)])
 def test_event_queue_shapes(depth, grid):
     desc, pa, n = CASES["small_core"]
     n = 2_999
@@ -401,6 +401,29 @@ def test_event_queue_shapes(depth, grid):
     assert np.array_equal(_u64(ref[2]), _u64(got[2]))
     assert np.array_equal(_u64(ref[0]), _u64(got[0]))
     assert np.array_equal(_u64(ref[1]), _u64(got[1]))
+
+
+@pytest.mark.parametrize("depth", [32, 100, 512])
+@pytest.mark.parametrize("tracker", [N.TRACKER_CSG, N.TRACKER_RECT])
+def test_fp32_local_event_equals_history(depth, tracker):
+    # FP32-local, fast build: the event kernel queues the flights it redoes
+    # in FP64 and runs them in a later pass, the history kernel redoes them
+    # at once; each particle's arithmetic is the same, so the records,
+    # tallies and counters are identical at every queue depth (full batches,
+    # carried tails and the redo queue included)
+    desc, pa, n = CASES["small_core"]
+    n = 4_001
+    g = _gpu(desc, exact=False)
+    parts = g.source_init(n, seed=SEED)
+    kw = dict(records=True, tracker=tracker, precision=N.FP32_LOCAL, p_absorb=pa, seed=SEED)
+    ref = g.run_histories(parts, n, **kw)
+    got = g.run_histories(parts, n, mode=N.MODE_EVENT, queue_depth=depth, **kw)
+    torch.cuda.synchronize()
+    assert np.array_equal(_u64(ref[2]), _u64(got[2]))
+    assert np.array_equal(_u64(ref[0]), _u64(got[0]))
+    c_ref, c_got = _u64(ref[1]), _u64(got[1])
+    assert np.array_equal(c_ref, c_got)
+    assert c_ref[N.K["close_calls"]] > 0   # the redo path ran
 
 
 def test_event_cutoff_segment_cap_and_tiny_n():
