@@ -93,7 +93,8 @@ def run_case(g, dev, n, opts, args, name):
         out.append({"segments": seg, "ms": ms, "segments_per_s": seg / (ms / 1e3),
                     "redone_in_fp64": int(c[N.K["close_calls"]]) / max(1, seg)})
     print(json.dumps({"workload": args.workload, "tracker": name, "mode": args.mode, "precision": args.precision,
-                      "particles": n, "sort_interval": args.sort_interval, "launches": out}), flush=True)
+                      "particles": n, "sort_interval": args.sort_interval, "queue_depth": args.queue_depth,
+                      "launches": out}), flush=True)
 
 
 def run_batch(dev, args):
