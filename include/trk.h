@@ -354,9 +354,9 @@ trk_status batch_create(const trk_geom_t* geoms, int n_geom, const void* const* 
 trk_status batch_destroy(trk_batch_t b);
 
 /* Bytes of the caller-owned work buffer (256-byte aligned): the device table
- * and, for event mode, the slot records of the batched event kernel's two
- * launches at the largest queue depth (512); enough for every mode and queue
- * depth. */
+ * and, for event mode, the per-geometry chunk counters and the slot records
+ * of the batched event kernel's two launches at the largest queue depth
+ * (512); enough for every mode and queue depth. */
 trk_status batch_work_bytes(trk_batch_t b, size_t* bytes);
 
 /* Writes the device table for chunks of `chunk` particles (0 = 512) into
@@ -368,8 +368,10 @@ trk_status batch_upload(trk_batch_t b, void* dev_work, size_t work_bytes, int ch
  * max_segments; path cutoff ignored).  History mode: one kernel, one history per lane,
  * warps pull chunks of one geometry.  Event mode: the event kernel's queues
  * and slot records per warp, each warp working through chunks of one
- * geometry at a time (a chunk of another geometry starts once the warp's
- * slots have drained); rect-tracker and CSG entries are two launches, the
+ * geometry at a time: it starts on the geometry its share of the particles
+ * falls in and keeps to it while it has chunks (per-geometry counters), then
+ * takes the next geometry with chunks left, whose first chunk starts once the
+ * warp's slots have drained; rect-tracker and CSG entries are two launches, the
  * CSG one on the batch's own side stream forked from `stream` by an event and
  * joined back to it (so it fills the SMs the first launch's last warps free),
  * each launch with its own slot records.  Issues memsets, kernels and that
@@ -382,8 +384,8 @@ trk_status batch_upload(trk_batch_t b, void* dev_work, size_t work_bytes, int ch
 trk_status run_batched(trk_batch_t b, void* dev_work, const trk_run_opts* opts, void* stream);
 
 /* Autotuner: times block sizes {64, 96, 128} x chunk sizes {128, 512, 2048}
- * (history mode) or queue depths {384, 512} x chunk sizes {1024, 2048, 4096,
- * 16384} x sort intervals {0, 4} (event mode, opts->mode) on the batch itself
+ * (history mode) or queue depths {384, 512} x chunk sizes {128, 256, 512,
+ * 2048} x sort intervals {0, 4} (event mode, opts->mode) on the batch itself
  * (CUDA events, `reps` launches each) and writes the fastest to opts->block
  * or opts->queue_depth and opts->sort_interval, and *chunk_out, leaving the
  * table uploaded for it; *best_ms (optional) gets its time.  The trial

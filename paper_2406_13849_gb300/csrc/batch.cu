@@ -37,6 +37,7 @@ struct BatchEntry {
     unsigned long long* records;
     long long n;
     long long first_chunk;   // prefix sum of chunks before this entry (in chunk order)
+    long long part_first;    // event mode: particles of the same tracker's entries before this one
     int csg;
     int pad;
 };
@@ -46,8 +47,6 @@ struct BatchHeader {
     unsigned long long total_chunks;
     int n_geom;
     int chunk;
-    unsigned long long next_ev[2];   // event mode: chunk counters of the rect and CSG launches
-    unsigned long long split;        // first chunk of the CSG-tracker entries
 };
 
 size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -120,29 +119,24 @@ __global__ void __launch_bounds__(128) k_batched(BatchHeader* __restrict__ hdr, 
 // ---------------------------------------------------------------------------
 // Event mode: each warp runs the event loop of the single-geometry event
 // kernel (slot records, queues by operation) over chunks of one geometry at
-// a time.  It keeps refilling from the next chunk while that chunk belongs
-// to the same geometry; a chunk of another geometry waits until the warp's
+// a time.  Chunks come from per-entry counters: a warp starts on the entry
+// its share of the launch's particle range falls in (warps spread over the
+// entries in proportion to their particles) and keeps pulling that entry's
+// chunks, refilling without a break; when the entry runs out it takes the
+// next entry that has chunks left, whose first chunk waits until the warp's
 // slots have drained, so the geometry and tracker stay warp-uniform.  Rect-
-// and CSG-tracker entries run as two launches (the rect chunks come first).
+// and CSG-tracker entries run as two launches.
 // ---------------------------------------------------------------------------
 using namespace trk::ev;
 constexpr int BEV_QUEUES = 4 + MAXL;   // flight, collide, free, FP64 redo, cross per level
 
-__device__ __forceinline__ int entry_of(const BatchEntry* table, int ng, unsigned long long c) {
-    int lo = 0, hi = ng - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if ((unsigned long long)table[mid].first_chunk <= c) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
 
 template <bool CSG, bool F32, int FLAGS>
 __global__ void TRK_EV_BOUNDS k_batched_ev(BatchHeader* __restrict__ hdr, const BatchEntry* __restrict__ table,
-                                           const RunP rp, const EvBuf B, int slots, int side,
-                                           unsigned long long c_begin, unsigned long long c_end,
-                                           unsigned long long max_rounds, int sort_interval) {
+                                           unsigned long long* __restrict__ ectr,
+                                           const RunP rp, const EvBuf B, int slots, int e_begin, int e_end,
+                                           long long side_parts, unsigned long long max_rounds,
+                                           int sort_interval) {
     extern __shared__ QIdx smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     QIdx* base_q = smem + warp * BEV_QUEUES * slots;
@@ -153,8 +147,24 @@ __global__ void TRK_EV_BOUNDS k_batched_ev(BatchHeader* __restrict__ hdr, const 
     QIdx* qx = base_q + 4 * slots;       // cross, one queue per level
     const bool sorting = sort_interval > 0;
     const int slot0 = (blockIdx.x * (EV_BLOCK / 32) + warp) * slots;
-    const int ng = hdr->n_geom;
     const long long chunk = hdr->chunk;
+    // the entry this warp starts on: warps are spread over the entries in
+    // proportion to their particles (the warp's share of the side's particle
+    // range), so most warps work through chunks of one geometry and switch
+    // (draining their slots) only when it runs out
+    int pref = e_begin;
+    {
+        const long long W = (long long)gridDim.x * (EV_BLOCK / 32);
+        const long long gw = (long long)blockIdx.x * (EV_BLOCK / 32) + warp;
+        const long long target = (long long)(((double)gw + 0.5) * (double)side_parts / (double)W);
+        int lo = e_begin, hi = e_end - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (table[mid].part_first <= target) lo = mid;
+            else hi = mid - 1;
+        }
+        pref = lo;
+    }
     Counts cnt;
 #pragma unroll
     for (int k = 0; k < NCOUNT; ++k) cnt.k[k] = 0;
@@ -167,23 +177,33 @@ __global__ void TRK_EV_BOUNDS k_batched_ev(BatchHeader* __restrict__ hdr, const 
     for (int l = 0; l < MAXL; ++l) n_cross[l] = 0;
     int ge = -1;                   // current entry, warp-uniform
     long long pn = 0, pb = 0;      // next particle and end of the current chunk
-    long long pend = -1;           // chunk pulled for another entry
+    int pend_e = -1;               // entry and chunk pulled, waiting to start
+    long long pend_c = 0;
     bool exhausted = false;
     __syncwarp();
     for (unsigned long long round = 0;; ++round) {
         // ---- chunks: pull the next one when the current is used up ----------
-        if (pn >= pb && pend < 0 && !exhausted) {
-            unsigned long long c = 0;
-            if (lane == 0) c = c_begin + atomicAdd(&hdr->next_ev[side], 1ULL);
-            c = __shfl_sync(0xffffffffu, c, 0);
-            if (c >= c_end) exhausted = true;
-            else pend = (long long)c;
+        if (pn >= pb && pend_e < 0 && !exhausted) {
+            // the next chunk of the preferred entry, else of the following
+            // entries in turn (per-entry counters)
+            int e = pref;
+            long long c = -1;
+            for (int t = e_begin; t < e_end; ++t) {
+                unsigned long long v = 0;
+                if (lane == 0) v = atomicAdd(ectr + e, 1ULL);
+                v = __shfl_sync(0xffffffffu, v, 0);
+                const long long nch = (table[e].n + chunk - 1) / chunk;
+                if ((long long)v < nch) { c = (long long)v; break; }
+                e = e + 1 < e_end ? e + 1 : e_begin;
+            }
+            if (c < 0) exhausted = true;
+            else { pend_e = e; pend_c = c; pref = e; }
         }
         int queued = n_fly + n_coll + n_redo;
 #pragma unroll
         for (int l = 0; l < MAXL; ++l) queued += n_cross[l];
-        if (pend >= 0) {
-            const int e = entry_of(table, ng, (unsigned long long)pend);
+        if (pend_e >= 0) {
+            const int e = pend_e;
             if (e == ge || queued == 0) {
                 if (e != ge) {
                     if (ge >= 0) flush_counts(cnt, table[ge].counters);
@@ -191,9 +211,9 @@ __global__ void TRK_EV_BOUNDS k_batched_ev(BatchHeader* __restrict__ hdr, const 
                     for (int k = 0; k < NCOUNT; ++k) cnt.k[k] = 0;
                     ge = e;
                 }
-                pn = (pend - table[e].first_chunk) * chunk;
+                pn = pend_c * chunk;
                 pb = pn + chunk < table[e].n ? pn + chunk : table[e].n;
-                pend = -1;
+                pend_e = -1;
             }
         }
         if (ge < 0) break;   // no chunk at all for this warp
@@ -254,7 +274,7 @@ __global__ void TRK_EV_BOUNDS k_batched_ev(BatchHeader* __restrict__ hdr, const 
             wpush(k < n_park, k < n_park ? qc[n_coll + k] : 0, qf, n_free);
         }
         __syncwarp();
-        if (queued == 0 && exhausted && pend < 0 && pn >= pb) break;
+        if (queued == 0 && exhausted && pend_e < 0 && pn >= pb) break;
         bool full = n_fly >= 32 || n_coll >= 32 || n_redo >= 32;
 #pragma unroll
         for (int l = 0; l < MAXL; ++l) full = full || n_cross[l] >= 32;
@@ -262,7 +282,7 @@ __global__ void TRK_EV_BOUNDS k_batched_ev(BatchHeader* __restrict__ hdr, const 
         // geometry follows (the source is exhausted, or the next chunk waits
         // for the slots to drain), or when no queue holds a full batch (so
         // every round advances: a full batch, or every queued particle)
-        const bool drain = (pn >= pb && (exhausted || pend >= 0)) || !full;
+        const bool drain = (pn >= pb && (exhausted || pend_e >= 0)) || !full;
         if (round >= max_rounds) {
             if (lane == 0) kernel_status(E.counters, TRK_E_TIMEOUT);
             break;
@@ -441,16 +461,20 @@ int sm_count_b() {
 
 size_t table_bytes(int n) { return a256(sizeof(BatchHeader)) + a256(size_t(n) * sizeof(BatchEntry)); }
 
-// Event mode: slot records after the table, `slots` per warp, one set for
-// each of the two launches (they may run at the same time).
-size_t event_bytes(int n, int slots) { return table_bytes(n) + 2 * event_work_bytes(slots, event_grid(slots)); }
+// Event mode: per-entry chunk counters after the table, then slot records,
+// `slots` per warp, one set for each of the two launches (they may run at
+// the same time).
+size_t counters_bytes(int n) { return a256(size_t(n) * sizeof(unsigned long long)); }
+size_t event_bytes(int n, int slots) {
+    return table_bytes(n) + counters_bytes(n) + 2 * event_work_bytes(slots, event_grid(slots));
+}
 constexpr int BEV_MAX_SLOTS = 512;
 
 }  // namespace
 
 namespace {
 
-// Event mode: the rect-tracker chunks [0, split) and the CSG ones
+// Event mode: the rect-tracker entries [0, split) and the CSG ones
 // [split, total) as two launches of the batched event kernel, the second on
 // the batch's side stream between a fork and a join event (graph capture
 // records the same fork and join), each with its own slot records.
@@ -471,10 +495,12 @@ trk_status run_batched_event(trk_batch_t b, void* dev_work, const trk_run_opts& 
     BatchHeader* hdr = static_cast<BatchHeader*>(dev_work);
     const BatchEntry* table = reinterpret_cast<const BatchEntry*>(static_cast<unsigned char*>(dev_work) + a256(sizeof(BatchHeader)));
     const long long T = (long long)slots * (EV_BLOCK / 32) * grid;
-    unsigned char* rec_base = static_cast<unsigned char*>(dev_work) + table_bytes(b->n_geom);
+    unsigned long long* ectr =
+        reinterpret_cast<unsigned long long*>(static_cast<unsigned char*>(dev_work) + table_bytes(b->n_geom));
+    unsigned char* rec_base = static_cast<unsigned char*>(dev_work) + table_bytes(b->n_geom) + counters_bytes(b->n_geom);
     const EvBuf B0 = make_buf(rec_base, T);
     const EvBuf B1 = make_buf(rec_base + event_work_bytes(slots, grid), T);
-    cudaError_t e = cudaMemsetAsync(hdr->next_ev, 0, sizeof(hdr->next_ev), s);
+    cudaError_t e = cudaMemsetAsync(ectr, 0, size_t(b->n_geom) * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return trk_status(set_error(TRK_E_CUDA, "run_batched: %s", cudaGetErrorString(e)));
     if (!b->side) {
         if (cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess ||
@@ -482,32 +508,33 @@ trk_status run_batched_event(trk_batch_t b, void* dev_work, const trk_run_opts& 
             cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming) != cudaSuccess)
             return trk_status(set_error(TRK_E_CUDA, "run_batched: cannot create the side stream"));
     }
-    long long total = 0, split = -1, npart = 0;
+    // entries [0, n_rect) run with the array tracker, [n_rect, n_geom) with CSG
+    int n_rect = 0;
+    long long npart = 0, parts_side[2] = {0, 0};
     for (auto& en : b->entries) {
-        if (en.csg && split < 0) split = en.first_chunk;
-        total = en.first_chunk + (en.n + b->chunk - 1) / b->chunk;
+        if (!en.csg) ++n_rect;
         npart += en.n;
+        parts_side[en.csg ? 1 : 0] += en.n;
     }
-    if (split < 0) split = total;
     // a particle takes at most 3 (max_segments + 2) queue steps; outside a
     // drain a warp runs at least one full batch of 32 of them a round
     unsigned long long max_rounds = (rp.max_segments + 2ULL) * (unsigned long long)(npart / 32 + 2) * 4ULL;
     if (o.max_rounds > 0) max_rounds = (unsigned long long)o.max_rounds;
     const size_t smem = size_t(BEV_QUEUES) * slots * (EV_BLOCK / 32) * sizeof(QIdx);
     // side 1 waits for everything before it on s (the counters' reset)
-    const bool both = split > 0 && total > split;
+    const bool both = n_rect > 0 && n_rect < b->n_geom;
     if (both) {
         if (cudaEventRecord(b->fork, s) != cudaSuccess || cudaStreamWaitEvent(b->side, b->fork, 0) != cudaSuccess)
             return trk_status(set_error(TRK_E_CUDA, "run_batched: fork failed"));
     }
-    auto launch = [&](auto kernel, int side, long long c0, long long c1) {
-        if (c1 <= c0) return;
+    auto launch = [&](auto kernel, int side, int e0, int e1) {
+        if (e1 <= e0) return;
         if (smem > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         cudaStream_t st = (side == 1 && both) ? b->side : s;
-        kernel<<<grid, EV_BLOCK, smem, st>>>(hdr, table, rp, side == 1 ? B1 : B0, slots, side,
-                                             (unsigned long long)c0, (unsigned long long)c1, max_rounds,
-                                             o.sort_interval);
+        kernel<<<grid, EV_BLOCK, smem, st>>>(hdr, table, ectr, rp, side == 1 ? B1 : B0, slots, e0, e1,
+                                             parts_side[side], max_rounds, o.sort_interval);
     };
+    const int split = n_rect, total = b->n_geom;
     if (f32) {
 #ifndef TRK_EXACT
         if (rec) { launch(k_batched_ev<false, true, F_REC>, 0, 0, split); launch(k_batched_ev<true, true, F_REC>, 1, split, total); }
@@ -604,11 +631,13 @@ trk_status batch_upload(trk_batch_t b, void* dev_work, size_t work_bytes, int ch
         return trk_status(set_error(TRK_E_INVALID, "batch_upload: work buffer must be 256-byte aligned"));
     if (chunk <= 0) chunk = 512;
     if (chunk < 32 || chunk > (1 << 20)) return trk_status(set_error(TRK_E_INVALID, "batch_upload: chunk must be in [32, 2^20]"));
-    long long total = 0, split = -1;
+    long long total = 0, split = -1, pf[2] = {0, 0};
     for (auto& e : b->entries) {
         if (e.csg && split < 0) split = total;
         e.first_chunk = total;
         total += (e.n + chunk - 1) / chunk;
+        e.part_first = pf[e.csg ? 1 : 0];
+        pf[e.csg ? 1 : 0] += e.n;
     }
     if (split < 0) split = total;
     std::vector<unsigned char> img(table_bytes(b->n_geom), 0);
@@ -618,7 +647,6 @@ trk_status batch_upload(trk_batch_t b, void* dev_work, size_t work_bytes, int ch
     h.total_chunks = (unsigned long long)total;
     h.n_geom = b->n_geom;
     h.chunk = chunk;
-    h.split = (unsigned long long)split;
     std::memcpy(img.data(), &h, sizeof h);
     std::memcpy(img.data() + a256(sizeof(BatchHeader)), b->entries.data(), b->entries.size() * sizeof(BatchEntry));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -703,12 +731,12 @@ trk_status batch_autotune(trk_batch_t b, void* dev_work, size_t work_bytes, trk_
     if (reps <= 0) reps = 2;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // history mode: (block, chunk); event mode: (queue depth, chunk, sort
-    // interval).  Event chunks trade the drains between geometries (small
-    // chunks) against the imbalance of the last chunks (large ones): on the
-    // 64-geometry batch 2048 measured best, 16% ahead of 4096.
+    // interval).  Event warps keep to one entry's chunks, so small chunks
+    // cost no drains and even out the warps' last chunks: on the
+    // 64-geometry batch 256 and 512 measured best, 13% ahead of 2048.
     const bool event = opts->mode == TRK_MODE_EVENT;
     const int hist_blocks[] = {64, 96, 128}, hist_chunks[] = {128, 512, 2048};
-    const int ev_depths[] = {384, 512}, ev_chunks[] = {1024, 2048, 4096, 16384};
+    const int ev_depths[] = {384, 512}, ev_chunks[] = {128, 256, 512, 2048};
     const int sort_intervals[] = {0, 4};
     const int* blocks = event ? ev_depths : hist_blocks;
     const int* chunks = event ? ev_chunks : hist_chunks;
@@ -718,7 +746,7 @@ trk_status batch_autotune(trk_batch_t b, void* dev_work, size_t work_bytes, trk_
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return trk_status(set_error(TRK_E_CUDA, "batch_autotune: cudaEventCreate failed"));
     float best = 1e30f;
-    int best_block = event ? 512 : 128, best_chunk = event ? 2048 : 512, best_sort = 0;
+    int best_block = event ? 512 : 128, best_chunk = event ? 512 : 512, best_sort = 0;
     trk_status st = TRK_OK;
     for (int ci = 0; ci < n_chunks && st == TRK_OK; ++ci) {
         const int ch = chunks[ci];
