@@ -342,7 +342,9 @@ trk_status transmission_bwd(trk_geom_t g, int tracker, int64_t n, const double* 
  *   dev_tallies[k]    its tally (uint64[n_instances of geometry k]),
  *   dev_counters      uint64[n_geom * TRK_NCOUNTERS], geometry k at k*16,
  *   dev_records       NULL or per-geometry record arrays (as run_histories),
- *   tracker           TRK_TRACKER_AUTO (as run_histories), _RECT or _CSG.
+ *   tracker           TRK_TRACKER_AUTO, _RECT or _CSG.  AUTO: in event mode every
+ *                     entry runs with the CSG tracker, in one launch; in history
+ *                     mode each entry as run_histories' AUTO would.
  * Tallies and counters are added to, not cleared.  Particle ids restart at
  * first_id for every geometry (each geometry keys its own random numbers
  * with its geometry id).  The pointer arrays are host memory, read here.
@@ -371,7 +373,8 @@ trk_status batch_upload(trk_batch_t b, void* dev_work, size_t work_bytes, int ch
  * geometry at a time: it starts on the geometry its share of the particles
  * falls in and keeps to it while it has chunks (per-geometry counters), then
  * takes the next geometry with chunks left, whose first chunk starts once the
- * warp's slots have drained; rect-tracker and CSG entries are two launches, the
+ * warp's slots have drained; rect-tracker and CSG entries (a batch created
+ * with _RECT) are two launches, the
  * CSG one on the batch's own side stream forked from `stream` by an event and
  * joined back to it (so it fills the SMs the first launch's last warps free),
  * each launch with its own slot records.  Issues memsets, kernels and that

@@ -37,7 +37,8 @@ struct BatchEntry {
     unsigned long long* records;
     long long n;
     long long first_chunk;   // prefix sum of chunks before this entry (in chunk order)
-    long long part_first;    // event mode: particles of the same tracker's entries before this one
+    long long part_first[2]; // event mode: particles before this entry among the same tracker's
+                             // entries [0], among all entries [1]
     int csg;
     int pad;
 };
@@ -135,7 +136,7 @@ template <bool CSG, bool F32, int FLAGS>
 __global__ void TRK_EV_BOUNDS k_batched_ev(BatchHeader* __restrict__ hdr, const BatchEntry* __restrict__ table,
                                            unsigned long long* __restrict__ ectr,
                                            const RunP rp, const EvBuf B, int slots, int e_begin, int e_end,
-                                           long long side_parts, unsigned long long max_rounds,
+                                           long long side_parts, int pf_sel, unsigned long long max_rounds,
                                            int sort_interval) {
     extern __shared__ QIdx smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -160,7 +161,7 @@ __global__ void TRK_EV_BOUNDS k_batched_ev(BatchHeader* __restrict__ hdr, const 
         int lo = e_begin, hi = e_end - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (table[mid].part_first <= target) lo = mid;
+            if (table[mid].part_first[pf_sel] <= target) lo = mid;
             else hi = mid - 1;
         }
         pref = lo;
@@ -184,17 +185,35 @@ __global__ void TRK_EV_BOUNDS k_batched_ev(BatchHeader* __restrict__ hdr, const 
     for (unsigned long long round = 0;; ++round) {
         // ---- chunks: pull the next one when the current is used up ----------
         if (pn >= pb && pend_e < 0 && !exhausted) {
-            // the next chunk of the preferred entry, else of the following
-            // entries in turn (per-entry counters)
+            // the next chunk of the preferred entry; when it has none left,
+            // of the entry with the most chunks left (the counters read
+            // lane by lane), so the warps that finish early help the
+            // geometries that take longest
             int e = pref;
             long long c = -1;
-            for (int t = e_begin; t < e_end; ++t) {
+            for (int attempt = 0; attempt < 2 * (e_end - e_begin) + 1 && e >= 0; ++attempt) {
                 unsigned long long v = 0;
                 if (lane == 0) v = atomicAdd(ectr + e, 1ULL);
                 v = __shfl_sync(0xffffffffu, v, 0);
-                const long long nch = (table[e].n + chunk - 1) / chunk;
-                if ((long long)v < nch) { c = (long long)v; break; }
-                e = e + 1 < e_end ? e + 1 : e_begin;
+                if ((long long)v < (table[e].n + chunk - 1) / chunk) { c = (long long)v; break; }
+                long long best_left = 0;
+                int best = -1;
+                for (int t = e_begin + lane; t < e_end; t += 32) {
+                    const long long nch = (table[t].n + chunk - 1) / chunk;
+                    const long long taken = (long long)*reinterpret_cast<volatile unsigned long long*>(ectr + t);
+                    const long long left = nch - (taken < nch ? taken : nch);
+                    if (left > best_left) { best_left = left; best = t; }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const long long l2 = __shfl_down_sync(0xffffffffu, best_left, o);
+                    const int b2 = __shfl_down_sync(0xffffffffu, best, o);
+                    if (l2 > best_left || (l2 == best_left && b2 >= 0 && (best < 0 || b2 < best))) {
+                        best_left = l2;
+                        best = b2;
+                    }
+                }
+                e = __shfl_sync(0xffffffffu, best, 0);
             }
             if (c < 0) exhausted = true;
             else { pend_e = e; pend_c = c; pref = e; }
@@ -433,6 +452,8 @@ struct trk_batch {
     int chunk = 0;                     // chunk size the uploaded table was built for
     bool uploaded = false;
     int event_unfit = -1;              // first geometry the event kernels' slot record cannot hold
+    int event_unfit_csg = -1;          // the same for the CSG tracker on every entry
+    bool auto_tracker = false;         // created with TRK_TRACKER_AUTO
     void* work = nullptr;
     size_t work_bytes = 0;
     unsigned magic = 0;
@@ -484,10 +505,16 @@ trk_status run_batched_event(trk_batch_t b, void* dev_work, const trk_run_opts& 
     if (slots < 32 || slots > BEV_MAX_SLOTS) return trk_status(set_error(TRK_E_INVALID, "run_batched: queue_depth must be in [32, 512]"));
     if (o.max_rounds < 0) return trk_status(set_error(TRK_E_INVALID, "run_batched: max_rounds must be >= 0"));
     if (o.sort_interval < 0) return trk_status(set_error(TRK_E_INVALID, "run_batched: sort_interval must be >= 0"));
-    if (b->event_unfit >= 0)
+    // AUTO: the CSG tracker for every entry, one launch (its kernel measured
+    // 5% faster on the 64-geometry batch than the array-tracker launch with
+    // the CSG one beside it: one kernel's code in the instruction caches);
+    // the history kernels keep the per-entry choice
+    const bool all_csg = b->auto_tracker;
+    const int unfit = all_csg ? b->event_unfit_csg : b->event_unfit;
+    if (unfit >= 0)
         return trk_status(set_error(TRK_E_UNSUPPORTED, "run_batched (event): geometry %d does not fit the event kernels' "
                                     "slot record (at most %d universes, %d materials, %d elements per array axis)",
-                                    b->event_unfit, ev::REC_MAX_UNIV, ev::REC_MAX_MAT, ev::REC_MAX_DIM));
+                                    unfit, ev::REC_MAX_UNIV, ev::REC_MAX_MAT, ev::REC_MAX_DIM));
     const int grid = event_grid(slots);
     const size_t need = event_bytes(b->n_geom, slots);
     if (b->work_bytes < need)
@@ -516,6 +543,11 @@ trk_status run_batched_event(trk_batch_t b, void* dev_work, const trk_run_opts& 
         npart += en.n;
         parts_side[en.csg ? 1 : 0] += en.n;
     }
+    if (all_csg) {
+        n_rect = 0;
+        parts_side[0] = 0;
+        parts_side[1] = npart;
+    }
     // a particle takes at most 3 (max_segments + 2) queue steps; outside a
     // drain a warp runs at least one full batch of 32 of them a round
     unsigned long long max_rounds = (rp.max_segments + 2ULL) * (unsigned long long)(npart / 32 + 2) * 4ULL;
@@ -532,7 +564,7 @@ trk_status run_batched_event(trk_batch_t b, void* dev_work, const trk_run_opts& 
         if (smem > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         cudaStream_t st = (side == 1 && both) ? b->side : s;
         kernel<<<grid, EV_BLOCK, smem, st>>>(hdr, table, ectr, rp, side == 1 ? B1 : B0, slots, e0, e1,
-                                             parts_side[side], max_rounds, o.sort_interval);
+                                             parts_side[side], all_csg ? 1 : 0, max_rounds, o.sort_interval);
     };
     const int split = n_rect, total = b->n_geom;
     if (f32) {
@@ -583,9 +615,11 @@ trk_status batch_create(const trk_geom_t* geoms, int n_geom, const void* const* 
         if (tracker == TRK_TRACKER_CSG) return true;
         return !geoms[k]->rect_ok || geoms[k]->has_hex != 0;
     };
-    // rect-tracker geometries first, larger populations first within a type
+    // larger populations first; with the array tracker requested, its
+    // geometries first (the event mode's two launches take contiguous
+    // ranges of entries)
     std::stable_sort(idx.begin(), idx.end(), [&](int a, int c) {
-        if (use_csg(a) != use_csg(c)) return !use_csg(a);
+        if (tracker == TRK_TRACKER_RECT && use_csg(a) != use_csg(c)) return !use_csg(a);
         return counts[a] > counts[c];
     });
     for (int k : idx) {
@@ -602,10 +636,12 @@ trk_status batch_create(const trk_geom_t* geoms, int n_geom, const void* const* 
         e.n = n;
         e.csg = use_csg(k) ? 1 : 0;
         if (b->event_unfit < 0 && event_fits(geoms[k], e.csg != 0, nullptr) != TRK_OK) b->event_unfit = k;
+        if (b->event_unfit_csg < 0 && event_fits(geoms[k], true, nullptr) != TRK_OK) b->event_unfit_csg = k;
         b->entries.push_back(e);
         b->order.push_back(k);
     }
     b->n_geom = n_geom;
+    b->auto_tracker = tracker == TRK_TRACKER_AUTO;
     b->magic = TRK_BATCH_MAGIC;
     *out = b;
     return TRK_OK;
@@ -636,7 +672,8 @@ trk_status batch_upload(trk_batch_t b, void* dev_work, size_t work_bytes, int ch
         if (e.csg && split < 0) split = total;
         e.first_chunk = total;
         total += (e.n + chunk - 1) / chunk;
-        e.part_first = pf[e.csg ? 1 : 0];
+        e.part_first[0] = pf[e.csg ? 1 : 0];
+        e.part_first[1] = pf[0] + pf[1];
         pf[e.csg ? 1 : 0] += e.n;
     }
     if (split < 0) split = total;
