@@ -717,7 +717,7 @@ def run_config4(N, I, dev, stream, barrier, rank, steps, world=1):
             "autotuned": {"event": {"queue_depth": ev32.queue_depth, "chunk": chunk_ev,
                                     "sort_interval": ev32.sort_interval},
                           "history": {"block": hi32.block, "chunk": chunk_hi}},
-            "launches_per_pass": {"batched_event": 2, "batched_history": 1, "loop": len(geoms)},
+            "launches_per_pass": {"batched_event": 1, "batched_history": 1, "loop": len(geoms)},
             "geometries_on_this_rank": len(geoms)}
 
 

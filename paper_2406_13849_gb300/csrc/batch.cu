@@ -37,10 +37,16 @@ struct BatchEntry {
     unsigned long long* records;
     long long n;
     long long first_chunk;   // prefix sum of chunks before this entry (in chunk order)
-    long long part_first[2]; // event mode: particles before this entry among the same tracker's
-                             // entries [0], among all entries [1]
+    long long part_first;    // event mode: particles before this entry among the same tracker's entries
     int csg;
     int pad;
+};
+
+// Population order of all entries, for a single event launch over them:
+// entry index and the particles of the entries before it in that order.
+struct EvOrder {
+    long long part_first;
+    int entry, pad;
 };
 
 struct BatchHeader {
@@ -136,8 +142,8 @@ template <bool CSG, bool F32, int FLAGS>
 __global__ void TRK_EV_BOUNDS k_batched_ev(BatchHeader* __restrict__ hdr, const BatchEntry* __restrict__ table,
                                            unsigned long long* __restrict__ ectr,
                                            const RunP rp, const EvBuf B, int slots, int e_begin, int e_end,
-                                           long long side_parts, int pf_sel, unsigned long long max_rounds,
-                                           int sort_interval) {
+                                           long long side_parts, const EvOrder* __restrict__ evo,
+                                           unsigned long long max_rounds, int sort_interval) {
     extern __shared__ QIdx smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     QIdx* base_q = smem + warp * BEV_QUEUES * slots;
@@ -153,6 +159,8 @@ __global__ void TRK_EV_BOUNDS k_batched_ev(BatchHeader* __restrict__ hdr, const 
     // proportion to their particles (the warp's share of the side's particle
     // range), so most warps work through chunks of one geometry and switch
     // (draining their slots) only when it runs out
+    // (evo: a launch over all entries takes them in population order instead
+    // of the table's)
     int pref = e_begin;
     {
         const long long W = (long long)gridDim.x * (EV_BLOCK / 32);
@@ -161,10 +169,10 @@ __global__ void TRK_EV_BOUNDS k_batched_ev(BatchHeader* __restrict__ hdr, const 
         int lo = e_begin, hi = e_end - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (table[mid].part_first[pf_sel] <= target) lo = mid;
+            if ((evo ? evo[mid].part_first : table[mid].part_first) <= target) lo = mid;
             else hi = mid - 1;
         }
-        pref = lo;
+        pref = evo ? evo[lo].entry : lo;
     }
     Counts cnt;
 #pragma unroll
@@ -480,7 +488,9 @@ int sm_count_b() {
     return v > 0 ? v : 152;
 }
 
-size_t table_bytes(int n) { return a256(sizeof(BatchHeader)) + a256(size_t(n) * sizeof(BatchEntry)); }
+size_t evo_offset(int n) { return a256(sizeof(BatchHeader)) + a256(size_t(n) * sizeof(BatchEntry)); }
+// header, entries, the entries' population order
+size_t table_bytes(int n) { return evo_offset(n) + a256(size_t(n) * sizeof(EvOrder)); }
 
 // Event mode: per-entry chunk counters after the table, then slot records,
 // `slots` per warp, one set for each of the two launches (they may run at
@@ -525,6 +535,7 @@ trk_status run_batched_event(trk_batch_t b, void* dev_work, const trk_run_opts& 
     unsigned long long* ectr =
         reinterpret_cast<unsigned long long*>(static_cast<unsigned char*>(dev_work) + table_bytes(b->n_geom));
     unsigned char* rec_base = static_cast<unsigned char*>(dev_work) + table_bytes(b->n_geom) + counters_bytes(b->n_geom);
+    const EvOrder* evo = reinterpret_cast<const EvOrder*>(static_cast<unsigned char*>(dev_work) + evo_offset(b->n_geom));
     const EvBuf B0 = make_buf(rec_base, T);
     const EvBuf B1 = make_buf(rec_base + event_work_bytes(slots, grid), T);
     cudaError_t e = cudaMemsetAsync(ectr, 0, size_t(b->n_geom) * sizeof(unsigned long long), s);
@@ -564,7 +575,8 @@ trk_status run_batched_event(trk_batch_t b, void* dev_work, const trk_run_opts& 
         if (smem > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         cudaStream_t st = (side == 1 && both) ? b->side : s;
         kernel<<<grid, EV_BLOCK, smem, st>>>(hdr, table, ectr, rp, side == 1 ? B1 : B0, slots, e0, e1,
-                                             parts_side[side], all_csg ? 1 : 0, max_rounds, o.sort_interval);
+                                             parts_side[side], all_csg ? evo : nullptr, max_rounds,
+                                             o.sort_interval);
     };
     const int split = n_rect, total = b->n_geom;
     if (f32) {
@@ -615,11 +627,13 @@ trk_status batch_create(const trk_geom_t* geoms, int n_geom, const void* const* 
         if (tracker == TRK_TRACKER_CSG) return true;
         return !geoms[k]->rect_ok || geoms[k]->has_hex != 0;
     };
-    // larger populations first; with the array tracker requested, its
-    // geometries first (the event mode's two launches take contiguous
-    // ranges of entries)
+    // array-tracker geometries first (the event mode's two launches take
+    // contiguous ranges of entries, and history-mode warps keep to one
+    // tracker's code), larger populations first within a type; the event
+    // mode's single CSG launch of an AUTO batch reads its own population
+    // order (evo, batch_upload)
     std::stable_sort(idx.begin(), idx.end(), [&](int a, int c) {
-        if (tracker == TRK_TRACKER_RECT && use_csg(a) != use_csg(c)) return !use_csg(a);
+        if (use_csg(a) != use_csg(c)) return !use_csg(a);
         return counts[a] > counts[c];
     });
     for (int k : idx) {
@@ -672,8 +686,7 @@ trk_status batch_upload(trk_batch_t b, void* dev_work, size_t work_bytes, int ch
         if (e.csg && split < 0) split = total;
         e.first_chunk = total;
         total += (e.n + chunk - 1) / chunk;
-        e.part_first[0] = pf[e.csg ? 1 : 0];
-        e.part_first[1] = pf[0] + pf[1];
+        e.part_first = pf[e.csg ? 1 : 0];
         pf[e.csg ? 1 : 0] += e.n;
     }
     if (split < 0) split = total;
@@ -686,6 +699,21 @@ trk_status batch_upload(trk_batch_t b, void* dev_work, size_t work_bytes, int ch
     h.chunk = chunk;
     std::memcpy(img.data(), &h, sizeof h);
     std::memcpy(img.data() + a256(sizeof(BatchHeader)), b->entries.data(), b->entries.size() * sizeof(BatchEntry));
+    {
+        // all entries by population, larger first (ties in table order)
+        std::vector<int> ord(b->entries.size());
+        for (size_t k = 0; k < ord.size(); ++k) ord[k] = int(k);
+        std::stable_sort(ord.begin(), ord.end(), [&](int a, int c) { return b->entries[a].n > b->entries[c].n; });
+        std::vector<EvOrder> evo(ord.size());
+        long long acc = 0;
+        for (size_t k = 0; k < ord.size(); ++k) {
+            evo[k].part_first = acc;
+            evo[k].entry = ord[k];
+            evo[k].pad = 0;
+            acc += b->entries[ord[k]].n;
+        }
+        if (!evo.empty()) std::memcpy(img.data() + evo_offset(b->n_geom), evo.data(), evo.size() * sizeof(EvOrder));
+    }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemcpyAsync(dev_work, img.data(), img.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
