@@ -49,12 +49,12 @@ TRACE_CAP = 96
 # segments.  None whenever the kernel has changed since that capture.
 TRAFFIC_BYTES_PER_SEGMENT = (9.320092e9 + 10.007729e9) / 82931315
 # the same for the other rooflines' kernels, from small-case captures:
-# k_event<CSG,FP32-local> on the same 3e6-particle case; the two
-# k_batched_ev<*,FP32-local> launches of one 64-geometry pass (chunk 4096,
+# k_event<CSG,FP32-local> on the same 3e6-particle case; the one
+# k_batched_ev<CSG,FP32-local> launch of a 64-geometry pass (chunk 512,
 # queue depth 512); k_transmission_bwd on 2^18 rays of the transmission
 # workload (traffic scales with rays)
 TRAFFIC_BYTES_PER_SEGMENT_FP32 = (14.747693e9 + 16.041718e9) / 82931442
-TRAFFIC_BYTES_PER_SEGMENT_BATCH = (17.187394e9 + 21.090474e9 + 20.138322e9 + 25.544987e9) / 301969347
+TRAFFIC_BYTES_PER_SEGMENT_BATCH = (59.753099e9 + 54.239671e9) / 301969347
 TRAFFIC_BYTES_PER_RAY_BWD = (15.207424e6 + 4.624384e6) / 262144
 # Algorithmic FP64 operations per unit of work, the rooflines' numerators,
 # from `python -m oracle.flop_counts` (the oracle's counting build in
@@ -553,10 +553,10 @@ def main() -> None:
     if batch and batch.get("batched_fp32local_graph_segments_per_s"):
         seg_b = batch["segments_per_particle"] * batch["particles"]
         rooflines["batched_event_fp32local"] = alu_roofline(
-            "k_batched_ev<rect,FP32-local> + k_batched_ev<CSG,FP32-local> (one 64-geometry pass)",
+            "k_batched_ev<CSG,FP32-local> (one 64-geometry pass)",
             OPS_PER_SEGMENT_BATCH, seg_b, seg_b / batch["batched_fp32local_graph_segments_per_s"],
             TRAFFIC_BYTES_PER_SEGMENT_BATCH * seg_b,
-            "ncu dram bytes of one pass's two launches (chunk 4096), scaled by segments", "segment",
+            "ncu dram bytes of one pass (chunk 512), scaled by segments", "segment",
             "CUDA events around the graph replay")
     if trans:
         rooflines["transmission_bwd"] = alu_roofline(
