@@ -135,6 +135,9 @@ __global__ void __launch_bounds__(128) k_batched(BatchHeader* __restrict__ hdr, 
 // and CSG-tracker entries run as two launches.
 // ---------------------------------------------------------------------------
 using namespace trk::ev;
+#ifndef TRK_BATCH_SM_GROUP
+#define TRK_BATCH_SM_GROUP 1
+#endif
 constexpr int BEV_QUEUES = 4 + MAXL;   // flight, collide, free, FP64 redo, cross per level
 
 
@@ -143,7 +146,7 @@ __global__ void TRK_EV_BOUNDS k_batched_ev(BatchHeader* __restrict__ hdr, const 
                                            unsigned long long* __restrict__ ectr,
                                            const RunP rp, const EvBuf B, int slots, int e_begin, int e_end,
                                            long long side_parts, const EvOrder* __restrict__ evo,
-                                           unsigned long long max_rounds, int sort_interval) {
+                                           unsigned long long max_rounds, int sort_interval, int per_sm) {
     extern __shared__ QIdx smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     QIdx* base_q = smem + warp * BEV_QUEUES * slots;
@@ -164,7 +167,14 @@ __global__ void TRK_EV_BOUNDS k_batched_ev(BatchHeader* __restrict__ hdr, const 
     int pref = e_begin;
     {
         const long long W = (long long)gridDim.x * (EV_BLOCK / 32);
+#if TRK_BATCH_SM_GROUP
+        // the CTAs of one SM (blocks b, b + nsm, ... of the first wave) take
+        // neighbouring shares, so an SM's warps mostly track one geometry
+        const int nsm = gridDim.x / per_sm;
+        const long long gw = ((long long)(blockIdx.x % nsm) * per_sm + blockIdx.x / nsm) * (EV_BLOCK / 32) + warp;
+#else
         const long long gw = (long long)blockIdx.x * (EV_BLOCK / 32) + warp;
+#endif
         const long long target = (long long)(((double)gw + 0.5) * (double)side_parts / (double)W);
         int lo = e_begin, hi = e_end - 1;
         while (lo < hi) {
@@ -526,6 +536,9 @@ trk_status run_batched_event(trk_batch_t b, void* dev_work, const trk_run_opts& 
                                     "slot record (at most %d universes, %d materials, %d elements per array axis)",
                                     unfit, ev::REC_MAX_UNIV, ev::REC_MAX_MAT, ev::REC_MAX_DIM));
     const int grid = event_grid(slots);
+    int sms = 152, dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int per_sm = grid % sms == 0 && grid >= sms ? grid / sms : 1;
     const size_t need = event_bytes(b->n_geom, slots);
     if (b->work_bytes < need)
         return trk_status(set_error(TRK_E_NOMEM, "run_batched (event): work buffer needs %zu bytes", need));
@@ -576,7 +589,7 @@ trk_status run_batched_event(trk_batch_t b, void* dev_work, const trk_run_opts& 
         cudaStream_t st = (side == 1 && both) ? b->side : s;
         kernel<<<grid, EV_BLOCK, smem, st>>>(hdr, table, ectr, rp, side == 1 ? B1 : B0, slots, e0, e1,
                                              parts_side[side], all_csg ? evo : nullptr, max_rounds,
-                                             o.sort_interval);
+                                             o.sort_interval, per_sm);
     };
     const int split = n_rect, total = b->n_geom;
     if (f32) {
