@@ -54,7 +54,7 @@ TRAFFIC_BYTES_PER_SEGMENT = (9.320092e9 + 10.007729e9) / 82931315
 # queue depth 512); k_transmission_bwd on 2^18 rays of the transmission
 # workload (traffic scales with rays)
 TRAFFIC_BYTES_PER_SEGMENT_FP32 = (14.747693e9 + 16.041718e9) / 82931442
-TRAFFIC_BYTES_PER_SEGMENT_BATCH = (59.753099e9 + 54.239671e9) / 301969347
+TRAFFIC_BYTES_PER_SEGMENT_BATCH = (58.925292e9 + 54.138522e9) / 301969347
 TRAFFIC_BYTES_PER_RAY_BWD = (15.207424e6 + 4.624384e6) / 262144
 # Algorithmic FP64 operations per unit of work, the rooflines' numerators,
 # from `python -m oracle.flop_counts` (the oracle's counting build in
