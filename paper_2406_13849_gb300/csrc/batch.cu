@@ -694,15 +694,13 @@ trk_status batch_upload(trk_batch_t b, void* dev_work, size_t work_bytes, int ch
         return trk_status(set_error(TRK_E_INVALID, "batch_upload: work buffer must be 256-byte aligned"));
     if (chunk <= 0) chunk = 512;
     if (chunk < 32 || chunk > (1 << 20)) return trk_status(set_error(TRK_E_INVALID, "batch_upload: chunk must be in [32, 2^20]"));
-    long long total = 0, split = -1, pf[2] = {0, 0};
+    long long total = 0, pf[2] = {0, 0};
     for (auto& e : b->entries) {
-        if (e.csg && split < 0) split = total;
         e.first_chunk = total;
         total += (e.n + chunk - 1) / chunk;
         e.part_first = pf[e.csg ? 1 : 0];
         pf[e.csg ? 1 : 0] += e.n;
     }
-    if (split < 0) split = total;
     std::vector<unsigned char> img(table_bytes(b->n_geom), 0);
     BatchHeader h;
     std::memset(&h, 0, sizeof h);
