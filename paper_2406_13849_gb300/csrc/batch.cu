@@ -260,7 +260,7 @@ __global__ void TRK_EV_BOUNDS k_batched_ev(BatchHeader* __restrict__ hdr, const 
         // ---- refill free slots from the current chunk ------------------------
         int got = 0;
         const long long first = pn;
-        if (n_free > 0 && pn < pb && (n_free >= TRK_EV_REFILL_MIN || n_fly < 32)) {
+        if (n_free > 0 && pn < pb && (n_free >= TRK_BEV_REFILL_MIN || n_fly < 32)) {
             got = pb - pn < (long long)n_free ? int(pb - pn) : n_free;
             pn += got;
         }

@@ -85,9 +85,9 @@ __global__ void TRK_EV_BOUNDS k_event(const DevGeom g, const ParticlesView P, lo
     __syncwarp();
     for (unsigned long long round = 0;; ++round) {
         // ---- refill free slots with new particles --------------------------
-        // in batches of at least a warp's width (birth runs the universe
-        // searches from the root, whose lanes diverge least when the batch
-        // is full), unless the flight queues are running low
+        // in batches of at least TRK_EV_REFILL_MIN (birth runs the universe
+        // searches from the root, whose lanes diverge least when the batches
+        // are full), unless the flight queues are running low
         int got = 0;
         unsigned long long first = 0;
         if (!exhausted && n_free > 0 && (n_free >= TRK_EV_REFILL_MIN || n_fly < 32)) {
