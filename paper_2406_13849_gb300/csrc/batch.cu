@@ -130,16 +130,16 @@ __global__ void __launch_bounds__(128) k_batched(BatchHeader* __restrict__ hdr, 
 // its share of the launch's particle range falls in (warps spread over the
 // entries in proportion to their particles) and keeps pulling that entry's
 // chunks, refilling without a break; when the entry runs out it takes the
-// next entry that has chunks left, whose first chunk waits until the warp's
-// slots have drained, so the geometry and tracker stay warp-uniform.  Rect-
-// and CSG-tracker entries run as two launches.
+// entry with the most chunks left, whose first chunk waits until the warp's
+// slots have drained, so the geometry and tracker stay warp-uniform.  An
+// AUTO or CSG batch is one launch (the CSG tracker for every entry); a batch
+// created for the array tracker runs its array and CSG entries as two.
 // ---------------------------------------------------------------------------
 using namespace trk::ev;
 #ifndef TRK_BATCH_SM_GROUP
 #define TRK_BATCH_SM_GROUP 1
 #endif
 constexpr int BEV_QUEUES = 4 + MAXL;   // flight, collide, free, FP64 redo, cross per level
-
 
 template <bool CSG, bool F32, int FLAGS>
 __global__ void TRK_EV_BOUNDS k_batched_ev(BatchHeader* __restrict__ hdr, const BatchEntry* __restrict__ table,
