@@ -6,13 +6,16 @@
 //
 // Design.  The caller's work buffer holds a device table: one entry per
 // geometry (its flattened geometry view, particle buffer, tally, counters,
-// tracker) and the prefix sums of its particle chunks.  Warps pull chunk
-// indices from one global counter; a chunk is `chunk` particles of a single
-// geometry, so the geometry and the tracker type are uniform across the warp
-// (warp-level dispatch: one branch per chunk, never per particle).  Chunks
-// are numbered with every rect-tracker geometry before every CSG one, so
-// neighbouring chunks share code.  run_batched issues only a memset and the
-// kernel: after batch_upload it can be captured in a CUDA graph and replayed.
+// tracker) and the prefix sums of its particle chunks.  History mode: warps
+// pull chunk indices from one global counter; a chunk is `chunk` particles
+// of a single geometry, so the geometry and the tracker type are uniform
+// across the warp (warp-level dispatch: one branch per chunk, never per
+// particle), and chunks are numbered with every rect-tracker geometry before
+// every CSG one, so neighbouring chunks share code.  Event mode: per-geometry
+// chunk counters (see k_batched_ev).  run_batched issues only memsets, the
+// kernels and, for an array-tracker batch in event mode, a fork/join with a
+// side stream: after batch_upload it can be captured in a CUDA graph and
+// replayed.
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
